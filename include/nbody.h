@@ -1,0 +1,189 @@
+/*
+ * nbody.h -- C ABI of libnbody, the GB300 (sm_103a) differentiable
+ * direct-sum N-body library.
+ *
+ * The method is the one of "Differentiable N-body code for Galactic Dynamics
+ * Odisseo" (arXiv 2511.22468):
+ *   - softened direct pairwise gravity, no tree or multipole (Sec. 1,
+ *     "N-body codes"):  a_i = -G sum_j m_j (x_i - x_j) (|x_i - x_j|^2 + eps^2)^(-3/2)
+ *   - external potential of MWPotential2014's NFW halo and Miyamoto-Nagai
+ *     disk (Sec. 2.2.1)
+ *   - second-order Velocity-Verlet (kick-drift-kick) with a fixed number of
+ *     steps (Sec. 2.2.1)
+ *   - reverse-mode gradients of the final state with respect to the initial
+ *     conditions, the time step (integration time), the particle masses and
+ *     the potential masses (Sec. 2; the parameter vector of Sec. 2.2.1 and
+ *     Fig. 2).
+ *
+ * Conventions for every call:
+ *   - Return value: NBODY_OK (0) or a negative NBODY_E* code; no call exits,
+ *     throws or traps.  nbody_strerror() names a code.
+ *   - Layout: per-particle vectors are structure-of-arrays FP64, x[d*n + i]
+ *     for d = 0, 1, 2 (3 x n doubles); masses are n doubles.
+ *   - Pointers marked "host or device" may be either: the library copies
+ *     through unified addressing (cudaMemcpyDefault).  Pinned host memory
+ *     keeps copies asynchronous.
+ *   - Stream: all device work of a context runs on the CUDA stream given to
+ *     nbody_create (0 = legacy default stream).  Calls that return data to
+ *     host memory synchronise that stream before returning; the others are
+ *     asynchronous with respect to the host.
+ *   - Ownership: the library owns the context and its device buffers
+ *     (state, staging arrays, partial sums, tape); it never frees or keeps
+ *     caller memory beyond the call.
+ *   - A context is not thread-safe: one host thread at a time.
+ *   - Requires an sm_103a device (GB300); eps must be > 0.
+ */
+#ifndef NBODY_H
+#define NBODY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define NBODY_API __attribute__((visibility("default")))
+#else
+#define NBODY_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define NBODY_OK 0
+#define NBODY_EINVAL (-1)   /* bad argument: size, pointer, eps <= 0 ... */
+#define NBODY_ENOMEM (-2)   /* device or host allocation failed */
+#define NBODY_ECUDA (-3)    /* a CUDA runtime call failed */
+#define NBODY_ETIMEOUT (-4) /* a bounded device wait expired */
+#define NBODY_ENAN (-5)     /* a non-finite value appeared in the state */
+#define NBODY_ESTATE (-6)   /* call out of order (e.g. vjp without a tape) */
+#define NBODY_ENODEV (-7)   /* no usable sm_103a device */
+
+/* ---- external potential components (Sec. 2.2.1) ---- */
+#define NBODY_EXT_NFW 1u /* NFW halo: Phi = -G M ln(1 + r/r_s) / r          */
+#define NBODY_EXT_MN 2u  /* Miyamoto-Nagai: Phi = -G M / sqrt(R^2 + (a + sqrt(z^2 + b^2))^2) */
+
+/* ---- FP32 recentring origin of the pair sum ---- */
+#define NBODY_CENTER_FIXED 0u /* origin = params.center for every step       */
+#define NBODY_CENTER_GUIDE 1u /* origin follows a test particle started at
+                                 (center, center_vel) in the external
+                                 potential with the same steps             */
+
+/* ---- tape modes ---- */
+#define NBODY_TAPE_KEEP_LAST 0u /* the forward pass keeps the last segment's
+                                   tape, so the reverse sweep recomputes
+                                   every segment but the last             */
+#define NBODY_TAPE_LEAN 1u      /* keep checkpoints only; the reverse sweep
+                                   recomputes every segment               */
+
+typedef struct nbody_params {
+  double G;                 /* gravitational constant                        */
+  double eps;               /* Plummer softening length, > 0                 */
+  double dt;                /* time step; may be negative (backward orbit)   */
+  int64_t checkpoint_every; /* K >= 1: integrate() records an adjoint tape
+                               with a checkpoint every K steps; 0: no tape   */
+  uint32_t ext_flags;       /* NBODY_EXT_NFW | NBODY_EXT_MN                   */
+  uint32_t center_mode;     /* NBODY_CENTER_FIXED or NBODY_CENTER_GUIDE      */
+  uint32_t tape_mode;       /* NBODY_TAPE_KEEP_LAST or NBODY_TAPE_LEAN       */
+  uint32_t reserved;        /* must be 0                                     */
+  double nfw_M;             /* NFW scale mass 4 pi rho_0 r_s^3               */
+  double nfw_rs;            /* NFW scale radius                              */
+  double mn_M;              /* disk mass                                     */
+  double mn_a;              /* disk scale length                             */
+  double mn_b;              /* disk scale height                             */
+  double center[3];         /* FP64 origin subtracted before the FP32 pair
+                               sum (fixed) or the guide's start position     */
+  double center_vel[3];     /* guide start velocity (CENTER_GUIDE)           */
+} nbody_params;
+
+typedef struct nbody_ctx nbody_ctx; /* opaque, owned by the library */
+
+/* Create a context for n >= 1 particles with the given parameters; work runs
+ * on cuda_stream (a cudaStream_t, NULL = legacy default stream) of the
+ * current device.  The state is zero until nbody_set_state.
+ * Errors: EINVAL (n < 1, p NULL, eps <= 0, reserved != 0), ENODEV, ENOMEM. */
+NBODY_API int nbody_create(nbody_ctx **out, int64_t n, const nbody_params *p,
+                 void *cuda_stream);
+
+/* Release every device buffer of the context; NULL is a no-op. */
+NBODY_API void nbody_destroy(nbody_ctx *c);
+
+/* Replace the parameters (same n).  Invalidates the tape and the cached
+ * acceleration.  Errors: EINVAL. */
+NBODY_API int nbody_set_params(nbody_ctx *c, const nbody_params *p);
+
+/* Copy positions x (3 x n), velocities v (3 x n) and masses m (n) into the
+ * context (host or device pointers; the caller keeps ownership).  Resets
+ * the guide to params.center / center_vel and invalidates the tape.
+ * Errors: EINVAL (NULL pointer), ECUDA. */
+NBODY_API int nbody_set_state(nbody_ctx *c, const double *x, const double *v,
+                    const double *m);
+
+/* Copy the current state out (host or device pointers; either may be NULL).
+ * Synchronises the context stream.  Errors: ECUDA. */
+NBODY_API int nbody_get_state(nbody_ctx *c, double *x, double *v);
+
+/* Advance k >= 0 kick-drift-kick steps of params.dt (Sec. 2.2.1) without
+ * recording a tape.  Errors: EINVAL, ECUDA, ENAN (sticky, see get_status). */
+NBODY_API int nbody_step(nbody_ctx *c, int64_t k);
+
+/* Advance n_steps >= 1 steps and, when checkpoint_every > 0, record the
+ * adjoint tape of exactly this call (checkpoints every K steps).  x_out and
+ * v_out (host or device, may be NULL) receive the final state; when either
+ * is given the call synchronises.  Errors: EINVAL, ENOMEM, ECUDA, ENAN. */
+NBODY_API int nbody_integrate(nbody_ctx *c, int64_t n_steps, double *x_out,
+                    double *v_out);
+
+/* Reverse sweep of the last nbody_integrate call (Sec. 2, reverse-mode
+ * gradients), discrete adjoint of the kick-drift-kick map with
+ * recomputation of tape segments.  Inputs: xbar, vbar = dL/dx_T, dL/dv_T
+ * (3 x n, host or device; NULL means zero).  Outputs (host or device):
+ * x0bar, v0bar = dL/dx_0, dL/dv_0 (3 x n each, may be NULL); mbar_or_null
+ * must be NULL (per-particle mass gradients are not provided);
+ * theta_bar (host, 4 doubles) = { dL/d dt,
+ *                                 sum_j m_j dL/dm_j (common mass scale),
+ *                                 dL/d nfw_M, dL/d mn_M }.
+ * The state after the call is the final state of the integration.
+ * Synchronises the context stream.
+ * Errors: ESTATE (no tape), EINVAL, ECUDA, ENAN. */
+NBODY_API int nbody_vjp(nbody_ctx *c, const double *xbar, const double *vbar,
+              double *x0bar, double *v0bar, double *mbar_or_null,
+              double theta_bar[4]);
+
+/* Diagnostics of the current state: out = { K = sum m v^2 / 2,
+ * W_pair = -G sum_{i<j} m_i m_j / sqrt(r_ij^2 + eps^2),
+ * W_ext = sum m Phi_ext(x), |P| = |sum m v| } (host).  The pair term uses
+ * the FP32 pair kernel with FP64 accumulation.  Synchronises.
+ * Errors: ECUDA. */
+NBODY_API int nbody_energy(nbody_ctx *c, double out[4]);
+
+/* Total momentum sum m v (host, 3 doubles).  Synchronises. */
+NBODY_API int nbody_momentum(nbody_ctx *c, double out[3]);
+
+/* Sticky device status of the context: NBODY_OK, or NBODY_ENAN when a
+ * non-finite value was written to the state.  Synchronises. */
+NBODY_API int nbody_get_status(nbody_ctx *c);
+
+/* Static text for a status code. */
+NBODY_API const char *nbody_strerror(int code);
+
+/* Number of kernels this library has launched in the calling process
+ * (all contexts); a monotonically increasing counter for accounting. */
+NBODY_API int64_t nbody_launch_count(void);
+
+/* ---- stateless kernels (device pointers only, stream = cuda_stream) ---- */
+
+/* Softened pair acceleration of n particles (Sec. 1), the FP32 hot loop:
+ * positions are recentred on center (FP64, 3 doubles, host), rounded to
+ * FP32 and summed in FP32 within a j-tile, in FP64 across tiles.
+ * x (3 x n) and m (n) in device memory; acc (3 x n, device) receives a_i.
+ * Allocates and frees scratch (cudaMallocAsync) on the stream.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+NBODY_API int nbody_pair_accel(int64_t n, const double *x, const double *m, double G,
+                     double eps, const double center[3], double *acc,
+                     void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NBODY_H */

@@ -1,0 +1,686 @@
+// nbody_api.cu -- the C ABI of libnbody (declared in include/nbody.h): the
+// context, its device memory, the forward driver (kick-drift-kick with
+// checkpoints and tape) and the reverse sweep (discrete adjoint with
+// segment recomputation).
+//
+// Forward (Velocity-Verlet, paper Sec. 2.2.1), points k = 0..n:
+//   pair pass at x_k (FP32, pair_force.cu) -> update kernel: a = a_pair +
+//   a_ext(x_k); v += c_k a (c_k = dt/2 at k = 0 and k = n, dt between: the
+//   closing and opening half kicks at one point merged); if k < n:
+//   x += dt v and restage x_{k+1} for the next pair pass.
+// The acceleration at the final point is kept (first-same-as-last) and
+// reused by the next call.
+//
+// Tape (reverse-mode gradients, Sec. 2): checkpoint c at point cK stores
+// (x_k, v before the kick at k, a_pair(x_k)); the end point is one more
+// checkpoint.  A segment buffer holds, for the K points of one segment,
+// x_k, a_pair(x_k) and the half-step velocities.  The reverse sweep walks
+// the segments backward, recomputing each from its checkpoint (K - 1 pair
+// passes: both end accelerations are in the checkpoints), and at every
+// point k runs the pair VJP and the adjoint update.  Every kernel sums in a
+// fixed order, so the recomputation reproduces the forward pass bit for bit.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "nbody_internal.cuh"
+
+namespace nb {
+static std::atomic<long long> g_launches{0};
+void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+}  // namespace nb
+
+using nb::DevParams;
+
+struct nbody_ctx {
+  int dev = 0;
+  int sm_count = 0;
+  int64_t n = 0, npad = 0;
+  cudaStream_t stream = nullptr;
+  nbody_params p{};
+  DevParams hp{};
+  DevParams* dp = nullptr;
+
+  double* x = nullptr;  // [3][npad]
+  double* v = nullptr;
+  double* m = nullptr;  // [npad]
+  double* acc = nullptr;  // FSAL a_pair cache [3][npad]
+  bool acc_valid = false;
+  float4* st = nullptr;   // [npad]
+  float4* vst = nullptr;  // [2*npad]
+  double* part = nullptr; // [Smax][3][npad]
+  double* pot = nullptr;  // [Sf][npad]
+  int Smax = 0;
+  nb::PairCfg fcfg{}, vcfg{};
+
+  double* guide = nullptr;       // [6] current guide (x, v)
+  double* fixed_center = nullptr;  // [3]
+  double* centers = nullptr;     // [(cap+1)*3]
+  int64_t centers_cap = 0;
+
+  // tape
+  int64_t tape_steps = 0;
+  int64_t K = 0, nseg = 0;
+  bool last_seg_valid = false;
+  double* cp = nullptr;  // [(nseg+1)][9][npad]
+  int64_t cp_cap = 0;    // checkpoints allocated
+  double* seg = nullptr; // [3K][3][npad]
+  int64_t seg_cap = 0;   // K allocated
+  double* xw = nullptr;  // recompute work state [3][npad] x2
+  double* vw = nullptr;
+
+  // adjoint
+  double* xbar = nullptr;
+  double* vbar = nullptr;
+  double* blk = nullptr;  // [nblk][6]
+  double* red = nullptr;  // [8]
+  int nblk = 0;
+  int* status = nullptr;
+};
+
+namespace {
+
+#define CK(call)                              \
+  do {                                        \
+    cudaError_t e_ = (call);                  \
+    if (e_ != cudaSuccess) return NBODY_ECUDA; \
+  } while (0)
+
+int check_params(const nbody_params* p) {
+  if (!p) return NBODY_EINVAL;
+  if (!(p->eps > 0.0) || !std::isfinite(p->eps)) return NBODY_EINVAL;
+  if (!std::isfinite(p->G) || !std::isfinite(p->dt)) return NBODY_EINVAL;
+  if (p->checkpoint_every < 0) return NBODY_EINVAL;
+  if (p->ext_flags & ~(NBODY_EXT_NFW | NBODY_EXT_MN)) return NBODY_EINVAL;
+  if (p->center_mode > NBODY_CENTER_GUIDE) return NBODY_EINVAL;
+  if (p->tape_mode > NBODY_TAPE_LEAN) return NBODY_EINVAL;
+  if (p->reserved != 0) return NBODY_EINVAL;
+  if ((p->ext_flags & NBODY_EXT_NFW) && !(p->nfw_rs > 0.0)) return NBODY_EINVAL;
+  if ((p->ext_flags & NBODY_EXT_MN) && !(p->mn_b >= 0.0 && p->mn_a >= 0.0))
+    return NBODY_EINVAL;
+  return NBODY_OK;
+}
+
+DevParams to_dev(const nbody_params& p) {
+  DevParams d{};
+  d.G = p.G;
+  d.eps2 = p.eps * p.eps;
+  d.dt = p.dt;
+  d.ext = p.ext_flags;
+  d.nfw_GM = (p.ext_flags & NBODY_EXT_NFW) ? p.G * p.nfw_M : 0.0;
+  d.nfw_rs = (p.ext_flags & NBODY_EXT_NFW) ? p.nfw_rs : 1.0;
+  d.mn_GM = (p.ext_flags & NBODY_EXT_MN) ? p.G * p.mn_M : 0.0;
+  d.mn_a = p.mn_a;
+  d.mn_b = p.mn_b;
+  d.eps2f = (float)(p.eps * p.eps);
+  return d;
+}
+
+template <class T>
+int dalloc(T** ptr, size_t count) {
+  *ptr = nullptr;
+  if (count == 0) count = 1;
+  if (cudaMalloc((void**)ptr, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return NBODY_ENOMEM;
+  }
+  return NBODY_OK;
+}
+
+template <class T>
+void dfree(T*& ptr) {
+  if (ptr) cudaFree(ptr);
+  ptr = nullptr;
+}
+
+int upload_params(nbody_ctx* c) {
+  c->hp = to_dev(c->p);
+  CK(cudaMemcpyAsync(c->dp, &c->hp, sizeof(DevParams), cudaMemcpyHostToDevice,
+                     c->stream));
+  double g[6] = {c->p.center[0], c->p.center[1], c->p.center[2],
+                 c->p.center_vel[0], c->p.center_vel[1], c->p.center_vel[2]};
+  CK(cudaMemcpyAsync(c->fixed_center, c->p.center, 3 * sizeof(double),
+                     cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->guide, g, 6 * sizeof(double), cudaMemcpyHostToDevice,
+                     c->stream));
+  // pageable sources: make the copies complete before the host arrays die
+  CK(cudaStreamSynchronize(c->stream));
+  return NBODY_OK;
+}
+
+// centre of point k of the current call
+const double* center_at(nbody_ctx* c, int64_t k) {
+  if (c->p.center_mode == NBODY_CENTER_GUIDE) return c->centers + 3 * k;
+  return c->fixed_center;
+}
+
+int ensure_centers(nbody_ctx* c, int64_t n_steps) {
+  if (c->centers_cap >= n_steps && c->centers) return NBODY_OK;
+  dfree(c->centers);
+  c->centers_cap = 0;
+  int rc = dalloc(&c->centers, (size_t)(n_steps + 1) * 3);
+  if (rc) return rc;
+  c->centers_cap = n_steps;
+  return NBODY_OK;
+}
+
+int ensure_tape(nbody_ctx* c, int64_t nseg, int64_t K) {
+  const size_t slot = (size_t)3 * c->npad;
+  if (c->cp_cap < nseg + 1 || !c->cp) {
+    dfree(c->cp);
+    c->cp_cap = 0;
+    int rc = dalloc(&c->cp, (size_t)(nseg + 1) * 3 * slot);
+    if (rc) return rc;
+    c->cp_cap = nseg + 1;
+  }
+  if (c->seg_cap < K || !c->seg) {
+    dfree(c->seg);
+    c->seg_cap = 0;
+    int rc = dalloc(&c->seg, (size_t)3 * K * slot);
+    if (rc) return rc;
+    c->seg_cap = K;
+  }
+  if (!c->xw) {
+    int rc = dalloc(&c->xw, slot);
+    if (rc) return rc;
+    rc = dalloc(&c->vw, slot);
+    if (rc) return rc;
+  }
+  return NBODY_OK;
+}
+
+struct Tape {
+  nbody_ctx* c;
+  size_t slot;
+  double* cpx(int64_t i) const { return c->cp + (size_t)i * 3 * slot; }
+  double* cpv(int64_t i) const { return cpx(i) + slot; }
+  double* cpa(int64_t i) const { return cpx(i) + 2 * slot; }
+  double* sx(int64_t j) const { return c->seg + (size_t)j * slot; }
+  double* sa(int64_t j) const { return c->seg + (size_t)(c->K + j) * slot; }
+  double* svh(int64_t j) const {  // j = 1..K
+    return c->seg + (size_t)(2 * c->K + j - 1) * slot;
+  }
+};
+
+nb::UpdateArgs base_update(nbody_ctx* c, double* x, double* v) {
+  nb::UpdateArgs a{};
+  a.P = c->dp;
+  a.n = c->n;
+  a.npad = c->npad;
+  a.x = x;
+  a.v = v;
+  a.part = c->part;
+  a.S = c->fcfg.S;
+  a.part_is_final = 0;
+  a.st = c->st;
+  a.status = c->status;
+  return a;
+}
+
+// Forward over points 0..n_steps from the live state; with_tape records
+// checkpoints (and the last segment unless the tape is lean).
+int run_forward(nbody_ctx* c, int64_t n_steps, bool with_tape) {
+  cudaStream_t s = c->stream;
+  int rc = ensure_centers(c, n_steps);
+  if (rc) return rc;
+  if (c->p.center_mode == NBODY_CENTER_GUIDE)
+    CK(nb::launch_guide(c->dp, c->guide, n_steps, c->centers, c->guide, s));
+  const int64_t K = with_tape ? c->p.checkpoint_every : 0;
+  int64_t nseg = 0, ls = 0;
+  if (with_tape) {
+    nseg = (n_steps + K - 1) / K;
+    ls = nseg - 1;
+    rc = ensure_tape(c, nseg, K);
+    if (rc) return rc;
+    c->K = K;
+    c->nseg = nseg;
+  }
+  Tape T{c, (size_t)3 * c->npad};
+  const bool keep_last = with_tape && c->p.tape_mode == NBODY_TAPE_KEEP_LAST;
+  for (int64_t k = 0; k <= n_steps; ++k) {
+    nb::UpdateArgs a = base_update(c, c->x, c->v);
+    if (k == 0 && c->acc_valid) {
+      a.part = c->acc;
+      a.S = 1;
+      a.part_is_final = 1;
+    } else {
+      if (k == 0)
+        CK(nb::launch_stage(c->x, c->m, center_at(c, 0), c->n, c->npad, c->st, s));
+      CK(nb::launch_pair_accel(c->fcfg, c->st, c->npad, c->hp.eps2f, c->part,
+                               nullptr, s));
+    }
+    a.acc_out = (k == n_steps) ? c->acc : nullptr;
+    a.kick = (k == 0 || k == n_steps) ? 0.5 : 1.0;
+    a.drift = k < n_steps;
+    a.c_next = a.drift ? center_at(c, k + 1) : nullptr;
+    if (with_tape) {
+      if (k % K == 0 || k == n_steps) {
+        const int64_t ci = (k == n_steps) ? nseg : k / K;
+        a.cp_x = T.cpx(ci);
+        a.cp_v = T.cpv(ci);
+        a.cp_a = T.cpa(ci);
+      }
+      if (keep_last && k >= ls * K && k < n_steps) {
+        const int64_t j = k - ls * K;
+        a.tape_x = T.sx(j);
+        a.tape_a = T.sa(j);
+        a.tape_vh = T.svh(j + 1);
+      }
+    }
+    CK(nb::launch_update(a, s));
+  }
+  c->acc_valid = true;
+  if (with_tape) {
+    c->tape_steps = n_steps;
+    c->last_seg_valid = keep_last;
+  } else {
+    c->tape_steps = 0;
+    c->last_seg_valid = false;
+  }
+  return NBODY_OK;
+}
+
+// Recompute segment sg from its checkpoint into the segment buffer.
+int recompute_segment(nbody_ctx* c, int64_t sg) {
+  cudaStream_t s = c->stream;
+  Tape T{c, (size_t)3 * c->npad};
+  const int64_t K = c->K, n = c->tape_steps;
+  const int64_t k0 = sg * K;
+  const int64_t Ks = (k0 + K <= n) ? K : n - k0;
+  const size_t bytes = (size_t)3 * c->npad * sizeof(double);
+  CK(cudaMemcpyAsync(c->xw, T.cpx(sg), bytes, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(c->vw, T.cpv(sg), bytes, cudaMemcpyDeviceToDevice, s));
+  for (int64_t j = 0; j < Ks; ++j) {
+    const int64_t k = k0 + j;
+    nb::UpdateArgs a = base_update(c, c->xw, c->vw);
+    if (j == 0) {
+      a.part = T.cpa(sg);
+      a.S = 1;
+      a.part_is_final = 1;
+    } else {
+      CK(nb::launch_pair_accel(c->fcfg, c->st, c->npad, c->hp.eps2f, c->part,
+                               nullptr, s));
+    }
+    a.kick = (k == 0) ? 0.5 : 1.0;
+    a.drift = 1;
+    a.c_next = center_at(c, k + 1);
+    a.tape_x = T.sx(j);
+    a.tape_a = T.sa(j);
+    a.tape_vh = T.svh(j + 1);
+    CK(nb::launch_update(a, s));
+  }
+  return NBODY_OK;
+}
+
+int copy_in(double* dst, const double* src, size_t count, cudaStream_t s) {
+  CK(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDefault, s));
+  return NBODY_OK;
+}
+
+// copy a [3][n] caller array into a [3][npad] device array
+int copy_in3(nbody_ctx* c, double* dst, const double* src) {
+  for (int d = 0; d < 3; ++d) {
+    int rc = copy_in(dst + (size_t)d * c->npad, src + (size_t)d * c->n,
+                     (size_t)c->n, c->stream);
+    if (rc) return rc;
+  }
+  return NBODY_OK;
+}
+
+int copy_out3(nbody_ctx* c, double* dst, const double* src) {
+  for (int d = 0; d < 3; ++d)
+    CK(cudaMemcpyAsync(dst + (size_t)d * c->n, src + (size_t)d * c->npad,
+                       (size_t)c->n * sizeof(double), cudaMemcpyDefault,
+                       c->stream));
+  return NBODY_OK;
+}
+
+void free_all(nbody_ctx* c) {
+  dfree(c->dp);
+  dfree(c->x);
+  dfree(c->v);
+  dfree(c->m);
+  dfree(c->acc);
+  dfree(c->st);
+  dfree(c->vst);
+  dfree(c->part);
+  dfree(c->pot);
+  dfree(c->guide);
+  dfree(c->fixed_center);
+  dfree(c->centers);
+  dfree(c->cp);
+  dfree(c->seg);
+  dfree(c->xw);
+  dfree(c->vw);
+  dfree(c->xbar);
+  dfree(c->vbar);
+  dfree(c->blk);
+  dfree(c->red);
+  dfree(c->status);
+}
+
+int check_device(int* dev, int* sms) {
+  if (cudaGetDevice(dev) != cudaSuccess) {
+    cudaGetLastError();
+    return NBODY_ENODEV;
+  }
+  int maj = 0, min = 0;
+  if (cudaDeviceGetAttribute(&maj, cudaDevAttrComputeCapabilityMajor, *dev) ||
+      cudaDeviceGetAttribute(&min, cudaDevAttrComputeCapabilityMinor, *dev) ||
+      cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, *dev)) {
+    cudaGetLastError();
+    return NBODY_ENODEV;
+  }
+  if (maj != 10 || min != 3) return NBODY_ENODEV;
+  return NBODY_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* nbody_strerror(int code) {
+  switch (code) {
+    case NBODY_OK: return "ok";
+    case NBODY_EINVAL: return "invalid argument";
+    case NBODY_ENOMEM: return "out of memory";
+    case NBODY_ECUDA: return "CUDA runtime error";
+    case NBODY_ETIMEOUT: return "bounded device wait expired";
+    case NBODY_ENAN: return "non-finite value in the state";
+    case NBODY_ESTATE: return "call out of order (no tape recorded)";
+    case NBODY_ENODEV: return "no sm_103a device";
+    default: return "unknown status";
+  }
+}
+
+int64_t nbody_launch_count(void) { return nb::g_launches.load(); }
+
+int nbody_create(nbody_ctx** out, int64_t n, const nbody_params* p,
+                 void* cuda_stream) {
+  if (!out) return NBODY_EINVAL;
+  *out = nullptr;
+  if (n < 1) return NBODY_EINVAL;
+  int rc = check_params(p);
+  if (rc) return rc;
+  int dev = 0, sms = 0;
+  rc = check_device(&dev, &sms);
+  if (rc) return rc;
+  nbody_ctx* c = new (std::nothrow) nbody_ctx();
+  if (!c) return NBODY_ENOMEM;
+  c->dev = dev;
+  c->sm_count = sms;
+  c->n = n;
+  c->npad = ((n + nb::kPad - 1) / nb::kPad) * nb::kPad;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->p = *p;
+  c->fcfg = nb::choose_pair_cfg(c->npad, sms, false);
+  c->vcfg = nb::choose_pair_cfg(c->npad, sms, true);
+  c->Smax = c->fcfg.S > c->vcfg.S ? c->fcfg.S : c->vcfg.S;
+  const size_t np = (size_t)c->npad;
+  c->nblk = nb::adjoint_blocks(n);
+  if ((rc = dalloc(&c->dp, 1)) || (rc = dalloc(&c->x, 3 * np)) ||
+      (rc = dalloc(&c->v, 3 * np)) || (rc = dalloc(&c->m, np)) ||
+      (rc = dalloc(&c->acc, 3 * np)) || (rc = dalloc(&c->st, np)) ||
+      (rc = dalloc(&c->vst, 2 * np)) ||
+      (rc = dalloc(&c->part, (size_t)c->Smax * 3 * np)) ||
+      (rc = dalloc(&c->pot, (size_t)c->fcfg.S * np)) ||
+      (rc = dalloc(&c->guide, 6)) || (rc = dalloc(&c->fixed_center, 3)) ||
+      (rc = dalloc(&c->xbar, 3 * np)) || (rc = dalloc(&c->vbar, 3 * np)) ||
+      (rc = dalloc(&c->blk, (size_t)c->nblk * 6)) || (rc = dalloc(&c->red, 8)) ||
+      (rc = dalloc(&c->status, 1))) {
+    free_all(c);
+    delete c;
+    return rc;
+  }
+  cudaStream_t s = c->stream;
+  if (cudaMemsetAsync(c->x, 0, 3 * np * sizeof(double), s) ||
+      cudaMemsetAsync(c->v, 0, 3 * np * sizeof(double), s) ||
+      cudaMemsetAsync(c->m, 0, np * sizeof(double), s) ||
+      cudaMemsetAsync(c->xbar, 0, 3 * np * sizeof(double), s) ||
+      cudaMemsetAsync(c->vbar, 0, 3 * np * sizeof(double), s) ||
+      cudaMemsetAsync(c->st, 0, np * sizeof(float4), s) ||
+      cudaMemsetAsync(c->vst, 0, 2 * np * sizeof(float4), s) ||
+      cudaMemsetAsync(c->status, 0, sizeof(int), s) || upload_params(c)) {
+    free_all(c);
+    delete c;
+    return NBODY_ECUDA;
+  }
+  *out = c;
+  return NBODY_OK;
+}
+
+void nbody_destroy(nbody_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+}
+
+int nbody_set_params(nbody_ctx* c, const nbody_params* p) {
+  if (!c) return NBODY_EINVAL;
+  int rc = check_params(p);
+  if (rc) return rc;
+  c->p = *p;
+  c->acc_valid = false;
+  c->tape_steps = 0;
+  c->last_seg_valid = false;
+  return upload_params(c);
+}
+
+int nbody_set_state(nbody_ctx* c, const double* x, const double* v,
+                    const double* m) {
+  if (!c || !x || !v || !m) return NBODY_EINVAL;
+  int rc;
+  if ((rc = copy_in3(c, c->x, x)) || (rc = copy_in3(c, c->v, v)) ||
+      (rc = copy_in(c->m, m, (size_t)c->n, c->stream)))
+    return rc;
+  c->acc_valid = false;
+  c->tape_steps = 0;
+  c->last_seg_valid = false;
+  rc = upload_params(c);  // resets the guide; synchronises (pageable inputs)
+  if (rc) return rc;
+  // stage masses (and positions) once; the update kernel rewrites positions
+  CK(nb::launch_stage(c->x, c->m, c->fixed_center, c->n, c->npad, c->st,
+                      c->stream));
+  CK(cudaMemsetAsync(c->vst, 0, 2 * (size_t)c->npad * sizeof(float4), c->stream));
+  return NBODY_OK;
+}
+
+int nbody_get_state(nbody_ctx* c, double* x, double* v) {
+  if (!c) return NBODY_EINVAL;
+  int rc;
+  if (x && (rc = copy_out3(c, x, c->x))) return rc;
+  if (v && (rc = copy_out3(c, v, c->v))) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  return NBODY_OK;
+}
+
+int nbody_step(nbody_ctx* c, int64_t k) {
+  if (!c || k < 0) return NBODY_EINVAL;
+  if (k == 0) return NBODY_OK;
+  return run_forward(c, k, false);
+}
+
+int nbody_integrate(nbody_ctx* c, int64_t n_steps, double* x_out,
+                    double* v_out) {
+  if (!c || n_steps < 1) return NBODY_EINVAL;
+  int rc = run_forward(c, n_steps, c->p.checkpoint_every > 0);
+  if (rc) return rc;
+  if (x_out || v_out) return nbody_get_state(c, x_out, v_out);
+  return NBODY_OK;
+}
+
+int nbody_vjp(nbody_ctx* c, const double* xbar, const double* vbar,
+              double* x0bar, double* v0bar, double* mbar_or_null,
+              double theta_bar[4]) {
+  if (!c || !theta_bar) return NBODY_EINVAL;
+  if (mbar_or_null) return NBODY_EINVAL;
+  if (c->tape_steps < 1) return NBODY_ESTATE;
+  cudaStream_t s = c->stream;
+  const size_t np = (size_t)c->npad;
+  int rc;
+  CK(cudaMemsetAsync(c->xbar, 0, 3 * np * sizeof(double), s));
+  CK(cudaMemsetAsync(c->vbar, 0, 3 * np * sizeof(double), s));
+  if (xbar && (rc = copy_in3(c, c->xbar, xbar))) return rc;
+  if (vbar && (rc = copy_in3(c, c->vbar, vbar))) return rc;
+  CK(cudaMemsetAsync(c->blk, 0, (size_t)c->nblk * 4 * sizeof(double), s));
+
+  Tape T{c, 3 * np};
+  const int64_t n = c->tape_steps, K = c->K, nseg = c->nseg;
+  CK(nb::launch_stage_vjp(T.cpx(nseg), c->m, c->vbar, center_at(c, n), c->n,
+                          c->npad, c->vst, s));
+  nb::AdjointArgs a{};
+  a.P = c->dp;
+  a.n = c->n;
+  a.npad = c->npad;
+  a.xbar = c->xbar;
+  a.vbar = c->vbar;
+  a.gpart = c->part;
+  a.S = c->vcfg.S;
+  a.m = c->m;
+  a.vst = c->vst;
+  a.blk = c->blk;
+  a.status = c->status;
+  for (int64_t sg = nseg - 1; sg >= 0; --sg) {
+    const int64_t k0 = sg * K;
+    const int64_t Ks = (k0 + K <= n) ? K : n - k0;
+    if (!(sg == nseg - 1 && c->last_seg_valid)) {
+      rc = recompute_segment(c, sg);
+      if (rc) return rc;
+    }
+    for (int64_t j = Ks; j >= 1; --j) {
+      const int64_t k = k0 + j;
+      CK(nb::launch_pair_vjp(c->vcfg, c->vst, c->npad, c->hp.eps2f, c->part, s));
+      a.xk = (j == Ks) ? T.cpx(sg + 1) : T.sx(j);
+      a.ak = (j == Ks) ? T.cpa(sg + 1) : T.sa(j);
+      a.ck = (k == n) ? 0.5 : 1.0;
+      a.drift = 1;
+      a.vh_prev = T.svh(j);
+      a.x_prev = T.sx(j - 1);
+      a.c_prev = center_at(c, k - 1);
+      CK(nb::launch_adjoint(a, s));
+    }
+  }
+  // point 0: opening half kick of the first step
+  CK(nb::launch_pair_vjp(c->vcfg, c->vst, c->npad, c->hp.eps2f, c->part, s));
+  a.xk = T.cpx(0);
+  a.ak = T.cpa(0);
+  a.ck = 0.5;
+  a.drift = 0;
+  a.vh_prev = nullptr;
+  a.x_prev = nullptr;
+  a.c_prev = nullptr;
+  CK(nb::launch_adjoint(a, s));
+  c->last_seg_valid = false;  // the segment buffer now holds segment 0
+
+  CK(nb::launch_reduce_rows(c->blk, c->nblk, 4, c->red, s));
+  if (x0bar && (rc = copy_out3(c, x0bar, c->xbar))) return rc;
+  if (v0bar && (rc = copy_out3(c, v0bar, c->vbar))) return rc;
+  double h[4];
+  CK(cudaMemcpyAsync(h, c->red, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int q = 0; q < 4; ++q) theta_bar[q] = h[q];
+  int st = 0;
+  CK(cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st & nb::kStatusNaN) return NBODY_ENAN;
+  return NBODY_OK;
+}
+
+int nbody_energy(nbody_ctx* c, double out[4]) {
+  if (!c || !out) return NBODY_EINVAL;
+  cudaStream_t s = c->stream;
+  const double* cen = (c->p.center_mode == NBODY_CENTER_GUIDE) ? c->guide
+                                                               : c->fixed_center;
+  CK(nb::launch_stage(c->x, c->m, cen, c->n, c->npad, c->st, s));
+  CK(nb::launch_pair_accel(c->fcfg, c->st, c->npad, c->hp.eps2f, c->part,
+                           c->pot, s));
+  const int nb_ = nb::energy_blocks(c->n);
+  CK(cudaMemsetAsync(c->blk, 0, (size_t)nb_ * 6 * sizeof(double), s));
+  CK(nb::launch_energy(c->dp, c->x, c->v, c->m, c->n, c->pot, c->fcfg.S,
+                       c->npad, c->blk, nb_, s));
+  CK(nb::launch_reduce_rows(c->blk, nb_, 6, c->red, s));
+  double h[6];
+  CK(cudaMemcpyAsync(h, c->red, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  out[0] = h[0];
+  out[1] = h[1];
+  out[2] = h[2];
+  out[3] = std::sqrt(h[3] * h[3] + h[4] * h[4] + h[5] * h[5]);
+  return NBODY_OK;
+}
+
+int nbody_momentum(nbody_ctx* c, double out[3]) {
+  if (!c || !out) return NBODY_EINVAL;
+  double e[4];
+  int rc = nbody_energy(c, e);
+  if (rc) return rc;
+  double h[8];
+  CK(cudaMemcpy(h, c->red, 6 * sizeof(double), cudaMemcpyDeviceToHost));
+  out[0] = h[3];
+  out[1] = h[4];
+  out[2] = h[5];
+  return NBODY_OK;
+}
+
+int nbody_get_status(nbody_ctx* c) {
+  if (!c) return NBODY_EINVAL;
+  int st = 0;
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st & nb::kStatusNaN) return NBODY_ENAN;
+  if (st & nb::kStatusTimeout) return NBODY_ETIMEOUT;
+  return NBODY_OK;
+}
+
+int nbody_pair_accel(int64_t n, const double* x, const double* m, double G,
+                     double eps, const double center[3], double* acc,
+                     void* cuda_stream) {
+  if (n < 1 || !x || !m || !acc || !center || !(eps > 0.0)) return NBODY_EINVAL;
+  int dev = 0, sms = 0;
+  int rc = check_device(&dev, &sms);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const int64_t npad = ((n + nb::kPad - 1) / nb::kPad) * nb::kPad;
+  const nb::PairCfg cfg = nb::choose_pair_cfg(npad, sms, false);
+  // scratch: padded SoA copy of x and m, centre, staging, partials
+  const size_t bytes_x = (size_t)4 * npad * sizeof(double);
+  const size_t bytes_st = (size_t)npad * sizeof(float4);
+  const size_t bytes_part = (size_t)cfg.S * 3 * npad * sizeof(double);
+  char* buf = nullptr;
+  if (cudaMallocAsync((void**)&buf, bytes_x + 256 + bytes_st + bytes_part, s) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return NBODY_ENOMEM;
+  }
+  double* xp = (double*)buf;
+  double* mp = xp + 3 * npad;
+  double* cen = (double*)(buf + bytes_x);
+  float4* st = (float4*)(buf + bytes_x + 256);
+  double* part = (double*)(buf + bytes_x + 256 + bytes_st);
+  rc = NBODY_OK;
+  cudaError_t e = cudaMemsetAsync(xp, 0, bytes_x, s);
+  for (int d = 0; d < 3 && e == cudaSuccess; ++d)
+    e = cudaMemcpyAsync(xp + (size_t)d * npad, x + (size_t)d * n,
+                        (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(mp, m, (size_t)n * sizeof(double),
+                        cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(cen, center, 3 * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = nb::launch_stage(xp, mp, cen, n, npad, st, s);
+  if (e == cudaSuccess)
+    e = nb::launch_pair_accel(cfg, st, npad, (float)(eps * eps), part, nullptr, s);
+  if (e == cudaSuccess) e = nb::launch_reduce_partials(part, cfg.S, npad, n, G, acc, s);
+  if (e != cudaSuccess) rc = NBODY_ECUDA;
+  // the centre copy reads host memory: finish it before returning
+  if (cudaStreamSynchronize(s) != cudaSuccess) rc = NBODY_ECUDA;
+  cudaFreeAsync(buf, s);
+  return rc;
+}
+
+}  // extern "C"

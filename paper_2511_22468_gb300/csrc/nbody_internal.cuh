@@ -1,0 +1,143 @@
+// nbody_internal.cuh -- internal declarations of libnbody (not installed).
+//
+// Data layout in device memory (all owned by a context):
+//   x, v          FP64 SoA [3][npad]          positions / velocities
+//   m             FP64 [npad]                 masses (pads have m = 0)
+//   st            float4 [npad]               forward staging, pair layout:
+//                   st[2p]   = (x_{2p}, x_{2p+1}, y_{2p}, y_{2p+1})
+//                   st[2p+1] = (z_{2p}, z_{2p+1}, m_{2p}, m_{2p+1})
+//                 coordinates are FP32 (x - c), c the FP64 recentring origin
+//   vst           float4 [2*npad]             adjoint staging, pair layout:
+//                   vst[4p]..vst[4p+1] as st, vst[4p+2] = (lx, lx', ly, ly'),
+//                   vst[4p+3] = (lz, lz', 0, 0), lambda the FP32 cotangent
+//   part          FP64 [S][3][npad]           pair-kernel partial sums, one
+//                                             slice per j-chunk, reduced in
+//                                             fixed order by the consumer
+// npad is n rounded up to a multiple of kPad; pad particles sit at the
+// origin with zero mass and zero cotangent, so they add exactly nothing.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nbody.h"
+
+namespace nb {
+
+constexpr int kPad = 1024;
+
+// Parameters read by the kernels from device memory, so that captured CUDA
+// graphs stay valid when the parameters change.
+struct DevParams {
+  double G;
+  double eps2;
+  double dt;
+  double nfw_GM, nfw_rs;
+  double mn_GM, mn_a, mn_b;
+  uint32_t ext;
+  uint32_t pad0;
+  float eps2f;
+  float pad1;
+};
+
+enum : int { kStatusNaN = 1, kStatusTimeout = 2 };
+
+// ---- launch accounting ----
+void count_launch(int k = 1);
+
+// ---- pair kernels (pair_force.cu, pair_vjp.cu) ----
+enum PairVariant : int { kTile = 0, kWarp = 1 };
+
+struct PairCfg {
+  int variant;  // kTile: i-particles in registers, j-tiles in shared memory;
+                // kWarp: lanes split j, warp-shuffle reduction (small n)
+  int nt;       // threads per block
+  int r;        // i-particles per thread (kTile) or per warp (kWarp)
+  int S;        // number of j-chunks (grid.y); partial-sum slices
+};
+
+PairCfg choose_pair_cfg(int64_t npad, int sm_count, bool vjp);
+
+// Raw sums R_i = sum_j m_j (x_j - x_i) s_ij^-3 (no G) into part[S][3][npad];
+// with pot != NULL also P_i = sum_j m_j / s_ij (self term included) into
+// pot[S][npad].
+cudaError_t launch_pair_accel(const PairCfg& cfg, const float4* st,
+                              int64_t npad, float eps2, double* part,
+                              double* pot, cudaStream_t s);
+
+// Raw sums Q_k = sum_j [s^-3 u - 3 s^-5 d (d.u)], u = m_j l_k - m_k l_j,
+// d = x_j - x_k, into part[S][3][npad].  (J_pair^T l)_k = -G Q_k.
+cudaError_t launch_pair_vjp(const PairCfg& cfg, const float4* vst,
+                            int64_t npad, float eps2, double* part,
+                            cudaStream_t s);
+
+// ---- per-particle kernels (update.cu) ----
+cudaError_t launch_stage(const double* x, const double* m, const double* c,
+                         int64_t n, int64_t npad, float4* st, cudaStream_t s);
+
+struct UpdateArgs {
+  const DevParams* P;
+  int64_t n, npad;
+  double* x;            // state, updated in place
+  double* v;
+  const double* part;   // pair partial sums (raw) or a final a_pair
+  int S;                // slices in part
+  int part_is_final;    // part holds G-scaled a_pair (one slice)
+  double* acc_out;      // receives a_pair (FSAL cache), may be NULL
+  double kick;          // v += kick * a
+  int drift;            // 1: x += dt * v after the kick, then restage
+  const double* c_next; // recentring origin of the restaged positions
+  float4* st;           // restaged positions
+  double* cp_x;         // checkpoint slot (x, v before the kick, a_pair) or NULL
+  double* cp_v;
+  double* cp_a;
+  double* tape_x;       // segment tape slot for this point (x, a_pair) or NULL
+  double* tape_a;
+  double* tape_vh;      // segment tape slot of the half-step velocity or NULL
+  int* status;
+};
+cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
+
+cudaError_t launch_stage_vjp(const double* x, const double* m,
+                             const double* lam, const double* c, int64_t n,
+                             int64_t npad, float4* vst, cudaStream_t s);
+
+struct AdjointArgs {
+  const DevParams* P;
+  int64_t n, npad;
+  double* xbar;          // running cotangents, updated in place
+  double* vbar;
+  const double* gpart;   // pair-VJP partial sums (raw)
+  int S;
+  const double* xk;      // positions at this point
+  const double* ak;      // a_pair at this point
+  double ck;             // kick coefficient (dt/2 at the ends, dt inside)
+  int drift;             // 1: also take the drift of the previous step
+  const double* vh_prev; // v_{k-1/2}
+  const double* x_prev;  // positions at the previous point (restaging)
+  const double* c_prev;  // their recentring origin
+  const double* m;
+  float4* vst;           // restaged positions + new cotangent
+  double* blk;           // [nblocks][4] accumulators
+  int* status;
+};
+cudaError_t launch_adjoint(const AdjointArgs& a, cudaStream_t s);
+int adjoint_blocks(int64_t n);
+
+cudaError_t launch_reduce_rows(const double* blk, int nblk, int ncol,
+                               double* out, cudaStream_t s);
+
+cudaError_t launch_guide(const DevParams* P, const double* g0, int64_t n_steps,
+                         double* centers, double* g_out, cudaStream_t s);
+
+cudaError_t launch_energy(const DevParams* P, const double* x,
+                          const double* v, const double* m, int64_t n,
+                          const double* pot_part, int S, int64_t npad,
+                          double* blk, int nblk, cudaStream_t s);
+int energy_blocks(int64_t n);
+
+cudaError_t launch_reduce_partials(const double* part, int S, int64_t npad,
+                                   int64_t n, double G, double* acc,
+                                   cudaStream_t s);
+
+}  // namespace nb

@@ -1,0 +1,281 @@
+// pair_force.cu -- softened direct-sum pair acceleration, the O(N^2) hot
+// loop of the method (paper Sec. 1, "N-body codes": exact pairwise forces
+// with softening, no tree or multipole):
+//
+//   a_i = G sum_j m_j (x_j - x_i) (|x_j - x_i|^2 + eps^2)^(-3/2)
+//
+// FP32 CUDA-core work (not a contraction, so no tensor cores).  The j = i
+// term is exactly zero because eps > 0, so the loop has no branch.
+//
+// Tile variant: each thread keeps R i-particles in registers; a block
+// streams j-pairs through shared memory in tiles of kTJ pairs.  Two j's are
+// processed together with the packed FP32x2 instructions of sm_100+
+// (add/fma/mul .f32x2), which halve the issue slots of the FP32 pipe, so the
+// loop is bound by the FP32 pipe itself (12 FP32 operations and one MUFU
+// rsqrt per interaction).  Sums are FP32 within a tile and FP64 across
+// tiles; each j-chunk (grid.y) writes its own FP64 partial slice, reduced
+// later in fixed order, so results are bitwise reproducible.
+//
+// Warp variant (small N): a warp owns R i-particles and its 32 lanes split
+// the j-range; lane sums are combined by a fixed xor-shuffle butterfly.
+#include "nbody_internal.cuh"
+
+namespace nb {
+
+namespace {
+
+constexpr int kTJ = 128;  // j-pairs per shared-memory tile (256 particles)
+
+__device__ __forceinline__ float rsqrt_ftz(float v) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(v));
+  return y;
+}
+
+__device__ __forceinline__ float2 rsqrt2(float2 v) {
+  return make_float2(rsqrt_ftz(v.x), rsqrt_ftz(v.y));
+}
+
+// one j-pair against one i: accumulates m_j (x_j - x_i) s^-3 into (ax, ay,
+// az) and optionally m_j / s into ph.
+template <bool POT>
+__device__ __forceinline__ void body(float2 xj, float2 yj, float2 zj,
+                                     float2 mj, float2 nx, float2 ny,
+                                     float2 nz, float2 e2, float2& ax,
+                                     float2& ay, float2& az, float2& ph) {
+  const float2 dx = __fadd2_rn(xj, nx);
+  const float2 dy = __fadd2_rn(yj, ny);
+  const float2 dz = __fadd2_rn(zj, nz);
+  float2 s2 = __ffma2_rn(dx, dx, e2);
+  s2 = __ffma2_rn(dy, dy, s2);
+  s2 = __ffma2_rn(dz, dz, s2);
+  const float2 inv = rsqrt2(s2);
+  const float2 inv2 = __fmul2_rn(inv, inv);
+  float2 w = __fmul2_rn(mj, inv);
+  if (POT) ph = __fadd2_rn(ph, w);
+  w = __fmul2_rn(w, inv2);
+  ax = __ffma2_rn(dx, w, ax);
+  ay = __ffma2_rn(dy, w, ay);
+  az = __ffma2_rn(dz, w, az);
+}
+
+__device__ __forceinline__ void load_i(const float4* __restrict__ st,
+                                       int64_t i, float& x, float& y,
+                                       float& z) {
+  const float4 A = st[2 * (i >> 1)];
+  const float4 B = st[2 * (i >> 1) + 1];
+  const bool odd = (i & 1) != 0;
+  x = odd ? A.y : A.x;
+  y = odd ? A.w : A.z;
+  z = odd ? B.y : B.x;
+}
+
+template <int NT, int R, bool POT>
+__global__ void __launch_bounds__(NT)
+    k_pair_tile(const float4* __restrict__ st, int ntiles, float eps2,
+                int64_t npad, double* __restrict__ part,
+                double* __restrict__ pot) {
+  __shared__ float4 sj[2 * kTJ];
+  const int t = threadIdx.x;
+  const int64_t i0 = (int64_t)blockIdx.x * (NT * R) + t;
+  const int S = gridDim.y;
+  const int tile_b = (int)(((int64_t)blockIdx.y * ntiles) / S);
+  const int tile_e = (int)(((int64_t)(blockIdx.y + 1) * ntiles) / S);
+
+  float2 nx[R], ny[R], nz[R];
+  double dax[R], day[R], daz[R], dph[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    float xi, yi, zi;
+    load_i(st, i0 + r * NT, xi, yi, zi);
+    nx[r] = make_float2(-xi, -xi);
+    ny[r] = make_float2(-yi, -yi);
+    nz[r] = make_float2(-zi, -zi);
+    dax[r] = day[r] = daz[r] = dph[r] = 0.0;
+  }
+  const float2 e2 = make_float2(eps2, eps2);
+
+  for (int tile = tile_b; tile < tile_e; ++tile) {
+    __syncthreads();
+    const float4* src = st + (int64_t)tile * (2 * kTJ);
+#pragma unroll
+    for (int q = t; q < 2 * kTJ; q += NT) sj[q] = src[q];
+    __syncthreads();
+
+    float2 ax[R], ay[R], az[R], ph[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      ax[r] = ay[r] = az[r] = ph[r] = make_float2(0.f, 0.f);
+#pragma unroll 2
+    for (int jj = 0; jj < kTJ; ++jj) {
+      const float4 A = sj[2 * jj];
+      const float4 B = sj[2 * jj + 1];
+      const float2 xj = make_float2(A.x, A.y), yj = make_float2(A.z, A.w);
+      const float2 zj = make_float2(B.x, B.y), mj = make_float2(B.z, B.w);
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        body<POT>(xj, yj, zj, mj, nx[r], ny[r], nz[r], e2, ax[r], ay[r],
+                  az[r], ph[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      dax[r] += (double)ax[r].x + (double)ax[r].y;
+      day[r] += (double)ay[r].x + (double)ay[r].y;
+      daz[r] += (double)az[r].x + (double)az[r].y;
+      if (POT) dph[r] += (double)ph[r].x + (double)ph[r].y;
+    }
+  }
+
+  double* p = part + (int64_t)blockIdx.y * 3 * npad;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int64_t i = i0 + r * NT;
+    p[i] = dax[r];
+    p[npad + i] = day[r];
+    p[2 * npad + i] = daz[r];
+    if (POT) pot[(int64_t)blockIdx.y * npad + i] = dph[r];
+  }
+}
+
+// Warp variant: block of 8 warps; warp w owns i = (blockIdx.x*8 + w)*R + r.
+template <int R, bool POT>
+__global__ void __launch_bounds__(256)
+    k_pair_warp(const float4* __restrict__ st, int64_t npairs, float eps2,
+                int64_t npad, double* __restrict__ part,
+                double* __restrict__ pot) {
+  const int lane = threadIdx.x & 31;
+  const int64_t ib = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * R;
+  const int S = gridDim.y;
+  const int64_t pb = ((int64_t)blockIdx.y * npairs) / S;
+  const int64_t pe = ((int64_t)(blockIdx.y + 1) * npairs) / S;
+
+  float2 nx[R], ny[R], nz[R], ax[R], ay[R], az[R], ph[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    float xi, yi, zi;
+    load_i(st, ib + r, xi, yi, zi);
+    nx[r] = make_float2(-xi, -xi);
+    ny[r] = make_float2(-yi, -yi);
+    nz[r] = make_float2(-zi, -zi);
+    ax[r] = ay[r] = az[r] = ph[r] = make_float2(0.f, 0.f);
+  }
+  const float2 e2 = make_float2(eps2, eps2);
+  for (int64_t p = pb + lane; p < pe; p += 32) {
+    const float4 A = st[2 * p];
+    const float4 B = st[2 * p + 1];
+    const float2 xj = make_float2(A.x, A.y), yj = make_float2(A.z, A.w);
+    const float2 zj = make_float2(B.x, B.y), mj = make_float2(B.z, B.w);
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      body<POT>(xj, yj, zj, mj, nx[r], ny[r], nz[r], e2, ax[r], ay[r], az[r],
+                ph[r]);
+  }
+  double* out = part + (int64_t)blockIdx.y * 3 * npad;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    double sx = (double)ax[r].x + (double)ax[r].y;
+    double sy = (double)ay[r].x + (double)ay[r].y;
+    double sz = (double)az[r].x + (double)az[r].y;
+    double sp = POT ? (double)ph[r].x + (double)ph[r].y : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sx += __shfl_xor_sync(0xffffffffu, sx, o);
+      sy += __shfl_xor_sync(0xffffffffu, sy, o);
+      sz += __shfl_xor_sync(0xffffffffu, sz, o);
+      if (POT) sp += __shfl_xor_sync(0xffffffffu, sp, o);
+    }
+    if (lane == 0) {
+      const int64_t i = ib + r;
+      out[i] = sx;
+      out[npad + i] = sy;
+      out[2 * npad + i] = sz;
+      if (POT) pot[(int64_t)blockIdx.y * npad + i] = sp;
+    }
+  }
+}
+
+template <bool POT>
+cudaError_t launch_impl(const PairCfg& c, const float4* st, int64_t npad,
+                        float eps2, double* part, double* pot,
+                        cudaStream_t s) {
+  if (c.variant == kTile) {
+    const int ntiles = (int)(npad / (2 * kTJ));
+    const int per_block = c.nt * c.r;
+    dim3 grid((unsigned)(npad / per_block), (unsigned)c.S);
+    if (c.nt == 128 && c.r == 4)
+      k_pair_tile<128, 4, POT><<<grid, 128, 0, s>>>(st, ntiles, eps2, npad, part, pot);
+    else if (c.nt == 128 && c.r == 8)
+      k_pair_tile<128, 8, POT><<<grid, 128, 0, s>>>(st, ntiles, eps2, npad, part, pot);
+    else if (c.nt == 256 && c.r == 4)
+      k_pair_tile<256, 4, POT><<<grid, 256, 0, s>>>(st, ntiles, eps2, npad, part, pot);
+    else if (c.nt == 256 && c.r == 2)
+      k_pair_tile<256, 2, POT><<<grid, 256, 0, s>>>(st, ntiles, eps2, npad, part, pot);
+    else
+      return cudaErrorInvalidValue;
+  } else {
+    dim3 grid((unsigned)(npad / (8 * c.r)), (unsigned)c.S);
+    if (c.r == 4)
+      k_pair_warp<4, POT><<<grid, 256, 0, s>>>(st, npad / 2, eps2, npad, part, pot);
+    else if (c.r == 8)
+      k_pair_warp<8, POT><<<grid, 256, 0, s>>>(st, npad / 2, eps2, npad, part, pot);
+    else
+      return cudaErrorInvalidValue;
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_pair_accel(const PairCfg& cfg, const float4* st,
+                              int64_t npad, float eps2, double* part,
+                              double* pot, cudaStream_t s) {
+  if (pot) return launch_impl<true>(cfg, st, npad, eps2, part, pot, s);
+  return launch_impl<false>(cfg, st, npad, eps2, part, nullptr, s);
+}
+
+// Launch shape: the tile variant when there are enough i-tiles to keep every
+// SM busy, otherwise the warp variant; S (j-chunks) is chosen so that the
+// number of blocks covers the resident-block slots of the GPU in whole
+// waves as nearly as possible.
+PairCfg choose_pair_cfg(int64_t npad, int sm_count, bool vjp) {
+  PairCfg c;
+  const int64_t slots_tile = (int64_t)sm_count * (vjp ? 3 : 4);
+  if (npad >= 65536) {
+    c.variant = kTile;
+    c.nt = 128;
+    c.r = vjp ? 2 : 4;
+    if (vjp) c.nt = 256;
+    const int64_t itiles = npad / (c.nt * c.r);
+    const int64_t ntiles = npad / (2 * kTJ);
+    // pick S in [1, 32] minimising idle slots of the last wave, with a mild
+    // preference for fewer chunks (less partial-sum traffic)
+    double best = 1e30;
+    int bestS = 1;
+    for (int S = 1; S <= 32 && S <= ntiles; ++S) {
+      const int64_t blocks = itiles * S;
+      const int64_t waves = (blocks + slots_tile - 1) / slots_tile;
+      const double eff = (double)blocks / (double)(waves * slots_tile);
+      const double cost = (1.0 / eff) * (1.0 + 0.002 * S);
+      if (cost < best - 1e-12) {
+        best = cost;
+        bestS = S;
+      }
+    }
+    c.S = bestS;
+  } else {
+    c.variant = kWarp;
+    c.nt = 256;
+    c.r = 4;
+    const int64_t blocks_x = npad / (8 * c.r);
+    const int64_t want = (int64_t)sm_count * 8;  // 8 blocks of 8 warps per SM
+    int64_t S = (want + blocks_x - 1) / blocks_x;
+    const int64_t max_s = (npad / 2) / 64;  // at least 64 pairs per chunk
+    if (S > max_s) S = max_s;
+    if (S < 1) S = 1;
+    c.S = (int)S;
+  }
+  return c;
+}
+
+}  // namespace nb

@@ -1,0 +1,208 @@
+// pair_vjp.cu -- vector-Jacobian product of the softened pair acceleration,
+// the second O(N^2) loop (reverse-mode gradients, paper Sec. 2).
+//
+// With a_i = -G sum_j m_j r_ij s_ij^-3, r_ij = x_i - x_j,
+// s^2 = |r|^2 + eps^2, the Jacobian blocks are built from the tidal tensor
+// K(r) = s^-3 I - 3 s^-5 r r^T (even in r, symmetric):
+//   d a_i / d x_i = -G sum_j m_j K(r_ij),   d a_i / d x_k = G m_k K(r_ik),
+// so for cotangents l the product (J^T l)_k is
+//   g_k = -G sum_j K(r_kj) (m_j l_k - m_k l_j).
+// The kernel returns Q_k = sum_j [s^-3 u - 3 s^-5 d (d.u)],
+// u = m_j l_k - m_k l_j, d = x_j - x_k, so that g_k = -G Q_k; the j = k term
+// vanishes (u = 0).  Same tiling, packed FP32x2 arithmetic and FP32/FP64
+// two-level summation as the forward kernel; 26 FP32 operations and one
+// rsqrt per interaction.
+#include "nbody_internal.cuh"
+
+namespace nb {
+
+namespace {
+
+constexpr int kTJ = 64;  // j-pairs per shared-memory tile (4 float4 each)
+
+__device__ __forceinline__ float rsqrt_ftz(float v) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(v));
+  return y;
+}
+
+struct IState {
+  float2 nx, ny, nz;  // (-x_k, -x_k) ...
+  float2 lx, ly, lz;  // (l_k, l_k)
+  float2 nm;          // (-m_k, -m_k)
+};
+
+__device__ __forceinline__ void vjp_body(const float4& A, const float4& B,
+                                         const float4& L1, const float4& L2,
+                                         const IState& s, float2 e2,
+                                         float2& qx, float2& qy, float2& qz) {
+  const float2 dx = __fadd2_rn(make_float2(A.x, A.y), s.nx);
+  const float2 dy = __fadd2_rn(make_float2(A.z, A.w), s.ny);
+  const float2 dz = __fadd2_rn(make_float2(B.x, B.y), s.nz);
+  const float2 mj = make_float2(B.z, B.w);
+  float2 s2 = __ffma2_rn(dx, dx, e2);
+  s2 = __ffma2_rn(dy, dy, s2);
+  s2 = __ffma2_rn(dz, dz, s2);
+  const float2 inv = make_float2(rsqrt_ftz(s2.x), rsqrt_ftz(s2.y));
+  const float2 inv2 = __fmul2_rn(inv, inv);
+  const float2 inv3 = __fmul2_rn(inv2, inv);
+  // u = m_j l_k - m_k l_j
+  const float2 ux = __ffma2_rn(mj, s.lx, __fmul2_rn(make_float2(L1.x, L1.y), s.nm));
+  const float2 uy = __ffma2_rn(mj, s.ly, __fmul2_rn(make_float2(L1.z, L1.w), s.nm));
+  const float2 uz = __ffma2_rn(mj, s.lz, __fmul2_rn(make_float2(L2.x, L2.y), s.nm));
+  float2 du = __fmul2_rn(dx, ux);
+  du = __ffma2_rn(dy, uy, du);
+  du = __ffma2_rn(dz, uz, du);
+  // c = -3 s^-5 (d.u)
+  const float2 c = __fmul2_rn(__fmul2_rn(inv3, __fmul2_rn(inv2, make_float2(-3.f, -3.f))), du);
+  qx = __ffma2_rn(c, dx, __ffma2_rn(inv3, ux, qx));
+  qy = __ffma2_rn(c, dy, __ffma2_rn(inv3, uy, qy));
+  qz = __ffma2_rn(c, dz, __ffma2_rn(inv3, uz, qz));
+}
+
+__device__ __forceinline__ IState load_k(const float4* __restrict__ vst,
+                                         int64_t k) {
+  const int64_t p = k >> 1;
+  const bool odd = (k & 1) != 0;
+  const float4 A = vst[4 * p], B = vst[4 * p + 1];
+  const float4 L1 = vst[4 * p + 2], L2 = vst[4 * p + 3];
+  const float x = odd ? A.y : A.x, y = odd ? A.w : A.z, z = odd ? B.y : B.x;
+  const float m = odd ? B.w : B.z;
+  const float lx = odd ? L1.y : L1.x, ly = odd ? L1.w : L1.z;
+  const float lz = odd ? L2.y : L2.x;
+  IState s;
+  s.nx = make_float2(-x, -x);
+  s.ny = make_float2(-y, -y);
+  s.nz = make_float2(-z, -z);
+  s.lx = make_float2(lx, lx);
+  s.ly = make_float2(ly, ly);
+  s.lz = make_float2(lz, lz);
+  s.nm = make_float2(-m, -m);
+  return s;
+}
+
+template <int NT, int R>
+__global__ void __launch_bounds__(NT)
+    k_vjp_tile(const float4* __restrict__ vst, int ntiles, float eps2,
+               int64_t npad, double* __restrict__ part) {
+  __shared__ float4 sj[4 * kTJ];
+  const int t = threadIdx.x;
+  const int64_t k0 = (int64_t)blockIdx.x * (NT * R) + t;
+  const int S = gridDim.y;
+  const int tile_b = (int)(((int64_t)blockIdx.y * ntiles) / S);
+  const int tile_e = (int)(((int64_t)(blockIdx.y + 1) * ntiles) / S);
+
+  IState st[R];
+  double gx[R], gy[R], gz[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    st[r] = load_k(vst, k0 + r * NT);
+    gx[r] = gy[r] = gz[r] = 0.0;
+  }
+  const float2 e2 = make_float2(eps2, eps2);
+  for (int tile = tile_b; tile < tile_e; ++tile) {
+    __syncthreads();
+    const float4* src = vst + (int64_t)tile * (4 * kTJ);
+#pragma unroll
+    for (int q = t; q < 4 * kTJ; q += NT) sj[q] = src[q];
+    __syncthreads();
+    float2 qx[R], qy[R], qz[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) qx[r] = qy[r] = qz[r] = make_float2(0.f, 0.f);
+#pragma unroll 2
+    for (int jj = 0; jj < kTJ; ++jj) {
+      const float4 A = sj[4 * jj], B = sj[4 * jj + 1];
+      const float4 L1 = sj[4 * jj + 2], L2 = sj[4 * jj + 3];
+#pragma unroll
+      for (int r = 0; r < R; ++r) vjp_body(A, B, L1, L2, st[r], e2, qx[r], qy[r], qz[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      gx[r] += (double)qx[r].x + (double)qx[r].y;
+      gy[r] += (double)qy[r].x + (double)qy[r].y;
+      gz[r] += (double)qz[r].x + (double)qz[r].y;
+    }
+  }
+  double* p = part + (int64_t)blockIdx.y * 3 * npad;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int64_t k = k0 + r * NT;
+    p[k] = gx[r];
+    p[npad + k] = gy[r];
+    p[2 * npad + k] = gz[r];
+  }
+}
+
+template <int R>
+__global__ void __launch_bounds__(256)
+    k_vjp_warp(const float4* __restrict__ vst, int64_t npairs, float eps2,
+               int64_t npad, double* __restrict__ part) {
+  const int lane = threadIdx.x & 31;
+  const int64_t kb = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * R;
+  const int S = gridDim.y;
+  const int64_t pb = ((int64_t)blockIdx.y * npairs) / S;
+  const int64_t pe = ((int64_t)(blockIdx.y + 1) * npairs) / S;
+  IState st[R];
+  float2 qx[R], qy[R], qz[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    st[r] = load_k(vst, kb + r);
+    qx[r] = qy[r] = qz[r] = make_float2(0.f, 0.f);
+  }
+  const float2 e2 = make_float2(eps2, eps2);
+  for (int64_t p = pb + lane; p < pe; p += 32) {
+    const float4 A = vst[4 * p], B = vst[4 * p + 1];
+    const float4 L1 = vst[4 * p + 2], L2 = vst[4 * p + 3];
+#pragma unroll
+    for (int r = 0; r < R; ++r) vjp_body(A, B, L1, L2, st[r], e2, qx[r], qy[r], qz[r]);
+  }
+  double* out = part + (int64_t)blockIdx.y * 3 * npad;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    double sx = (double)qx[r].x + (double)qx[r].y;
+    double sy = (double)qy[r].x + (double)qy[r].y;
+    double sz = (double)qz[r].x + (double)qz[r].y;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sx += __shfl_xor_sync(0xffffffffu, sx, o);
+      sy += __shfl_xor_sync(0xffffffffu, sy, o);
+      sz += __shfl_xor_sync(0xffffffffu, sz, o);
+    }
+    if (lane == 0) {
+      const int64_t k = kb + r;
+      out[k] = sx;
+      out[npad + k] = sy;
+      out[2 * npad + k] = sz;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_pair_vjp(const PairCfg& c, const float4* vst, int64_t npad,
+                            float eps2, double* part, cudaStream_t s) {
+  if (c.variant == kTile) {
+    const int ntiles = (int)(npad / (2 * kTJ));
+    dim3 grid((unsigned)(npad / (c.nt * c.r)), (unsigned)c.S);
+    if (c.nt == 256 && c.r == 2)
+      k_vjp_tile<256, 2><<<grid, 256, 0, s>>>(vst, ntiles, eps2, npad, part);
+    else if (c.nt == 128 && c.r == 4)
+      k_vjp_tile<128, 4><<<grid, 128, 0, s>>>(vst, ntiles, eps2, npad, part);
+    else if (c.nt == 128 && c.r == 2)
+      k_vjp_tile<128, 2><<<grid, 128, 0, s>>>(vst, ntiles, eps2, npad, part);
+    else
+      return cudaErrorInvalidValue;
+  } else {
+    dim3 grid((unsigned)(npad / (8 * c.r)), (unsigned)c.S);
+    if (c.r == 4)
+      k_vjp_warp<4><<<grid, 256, 0, s>>>(vst, npad / 2, eps2, npad, part);
+    else if (c.r == 2)
+      k_vjp_warp<2><<<grid, 256, 0, s>>>(vst, npad / 2, eps2, npad, part);
+    else
+      return cudaErrorInvalidValue;
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace nb

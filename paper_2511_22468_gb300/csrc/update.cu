@@ -1,0 +1,498 @@
+// update.cu -- O(N) kernels of the integrator and its adjoint.
+//
+//  * external potential of MWPotential2014's halo and disk (paper
+//    Sec. 2.2.1), in FP64: NFW  Phi = -G M ln(1 + r/r_s) / r and
+//    Miyamoto-Nagai  Phi = -G M / sqrt(R^2 + (a + sqrt(z^2 + b^2))^2),
+//    their accelerations and the Jacobian-vector products of the
+//    accelerations;
+//  * the fused kick-drift-kick update (Velocity-Verlet, Sec. 2.2.1) with
+//    first-same-as-last kicks: at point k the closing half kick of step k-1
+//    and the opening half kick of step k are one kick of dt (dt/2 at the
+//    ends), followed by the drift and the FP32 restaging of the positions
+//    for the next pair pass; the same pass writes checkpoints and tape;
+//  * the adjoint update (reverse-mode gradients, Sec. 2): at point k
+//    xbar += c_k J(x_k)^T vbar with J = J_pair + J_ext, then the adjoint of
+//    the drift vbar += dt xbar, plus the parameter-gradient sums;
+//  * the guide orbit that carries the FP32 recentring origin;
+//  * energy / momentum diagnostics and fixed-order reductions.
+// State is FP64 throughout; one thread per particle.
+#include <cmath>
+
+#include "nbody_internal.cuh"
+
+namespace nb {
+
+namespace {
+
+// ---------------------------------------------------------------- potential
+// Unit-mass (G M = 1) accelerations of the halo and the disk.
+struct ExtUnit {
+  double n[3];
+  double d[3];
+};
+
+__device__ __forceinline__ double nfw_f(double r, double rs) {
+  // a_NFW = -G M f(r) x, f(r) = ln(1 + r/r_s)/r^3 - 1/(r^2 (r + r_s));
+  // below r = 1e-4 r_s the two terms cancel and the Taylor series is used.
+  const double u = r / rs;
+  if (u < 1e-4) {
+    const double rs2 = rs * rs, rs3 = rs2 * rs;
+    return (0.5 / rs2) / r - (2.0 / 3.0) / rs3 + (0.75 / (rs3 * rs)) * r -
+           (0.8 / (rs3 * rs2)) * r * r;
+  }
+  return (log1p(u) / r - 1.0 / (r + rs)) / (r * r);
+}
+
+__device__ __forceinline__ double nfw_fprime_over_r(double r, double rs) {
+  // f'(r)/r with f' = 1/(r^3 (r+r_s)) - 3 ln(1+r/r_s)/r^4
+  //                   + (3 r + 2 r_s)/(r^3 (r+r_s)^2)
+  const double u = r / rs;
+  if (u < 1e-4) {
+    const double rs2 = rs * rs, rs4 = rs2 * rs2;
+    return (-0.5 / rs2) / (r * r * r) + (0.75 / rs4) / r - 1.6 / (rs4 * rs);
+  }
+  const double rp = r + rs;
+  const double r3 = r * r * r;
+  return (1.0 / (r3 * rp) - 3.0 * log1p(u) / (r3 * r) +
+          (3.0 * r + 2.0 * rs) / (r3 * rp * rp)) / r;
+}
+
+__device__ __forceinline__ void ext_unit(const DevParams& P, double x,
+                                         double y, double z, ExtUnit& e) {
+  e.n[0] = e.n[1] = e.n[2] = 0.0;
+  e.d[0] = e.d[1] = e.d[2] = 0.0;
+  if (P.ext & NBODY_EXT_NFW) {
+    const double r = sqrt(x * x + y * y + z * z);
+    if (r > 0.0) {
+      const double f = nfw_f(r, P.nfw_rs);
+      e.n[0] = -f * x;
+      e.n[1] = -f * y;
+      e.n[2] = -f * z;
+    }
+  }
+  if (P.ext & NBODY_EXT_MN) {
+    const double B = sqrt(z * z + P.mn_b * P.mn_b);
+    const double aB = P.mn_a + B;
+    const double S2 = x * x + y * y + aB * aB;
+    const double iS3 = 1.0 / (S2 * sqrt(S2));
+    e.d[0] = -x * iS3;
+    e.d[1] = -y * iS3;
+    e.d[2] = -z * aB / B * iS3;
+  }
+}
+
+// (d a_ext / d x) l, full accelerations (G M included); the Jacobian is
+// symmetric so this is also J^T l.
+__device__ __forceinline__ void ext_jvp(const DevParams& P, double x, double y,
+                                        double z, const double l[3],
+                                        double out[3]) {
+  out[0] = out[1] = out[2] = 0.0;
+  if (P.ext & NBODY_EXT_NFW) {
+    const double r = sqrt(x * x + y * y + z * z);
+    if (r > 0.0) {
+      // J = -G M [ f I + (f'/r) x x^T ]
+      const double f = nfw_f(r, P.nfw_rs);
+      const double g = nfw_fprime_over_r(r, P.nfw_rs);
+      const double xl = x * l[0] + y * l[1] + z * l[2];
+      out[0] -= P.nfw_GM * (f * l[0] + g * xl * x);
+      out[1] -= P.nfw_GM * (f * l[1] + g * xl * y);
+      out[2] -= P.nfw_GM * (f * l[2] + g * xl * z);
+    }
+  }
+  if (P.ext & NBODY_EXT_MN) {
+    // a = -G M q / S^3 with q = (x, y, z (a+B)/B), S^2 = R^2 + (a+B)^2:
+    // J = -G M [ dq/dx / S^3 - 3 q q^T / S^5 ],
+    // dq/dx = diag(1, 1, 1 + a b^2 / B^3)
+    const double b2 = P.mn_b * P.mn_b;
+    const double B = sqrt(z * z + b2);
+    const double aB = P.mn_a + B;
+    const double S2 = x * x + y * y + aB * aB;
+    const double iS = 1.0 / sqrt(S2);
+    const double iS3 = iS * iS * iS;
+    const double iS5 = iS3 * iS * iS;
+    const double q2 = z * aB / B;
+    const double ql = x * l[0] + y * l[1] + q2 * l[2];
+    const double dz = 1.0 + P.mn_a * b2 / (B * B * B);
+    out[0] -= P.mn_GM * (l[0] * iS3 - 3.0 * x * ql * iS5);
+    out[1] -= P.mn_GM * (l[1] * iS3 - 3.0 * y * ql * iS5);
+    out[2] -= P.mn_GM * (dz * l[2] * iS3 - 3.0 * q2 * ql * iS5);
+  }
+}
+
+__device__ __forceinline__ double ext_potential(const DevParams& P, double x,
+                                                double y, double z) {
+  double phi = 0.0;
+  if (P.ext & NBODY_EXT_NFW) {
+    const double r = sqrt(x * x + y * y + z * z);
+    phi -= P.nfw_GM * (r > 0.0 ? log1p(r / P.nfw_rs) / r : 1.0 / P.nfw_rs);
+  }
+  if (P.ext & NBODY_EXT_MN) {
+    const double B = sqrt(z * z + P.mn_b * P.mn_b);
+    const double aB = P.mn_a + B;
+    phi -= P.mn_GM / sqrt(x * x + y * y + aB * aB);
+  }
+  return phi;
+}
+
+// ------------------------------------------------------------------ staging
+__device__ __forceinline__ void put_stage(float4* st, int64_t i, float x,
+                                          float y, float z, float m) {
+  float* f = reinterpret_cast<float*>(st) + 8 * (i >> 1) + (i & 1);
+  f[0] = x;
+  f[2] = y;
+  f[4] = z;
+  f[6] = m;
+}
+
+__device__ __forceinline__ void put_stage_xyz(float4* st, int64_t i, float x,
+                                              float y, float z) {
+  float* f = reinterpret_cast<float*>(st) + 8 * (i >> 1) + (i & 1);
+  f[0] = x;
+  f[2] = y;
+  f[4] = z;
+}
+
+__device__ __forceinline__ void put_vstage(float4* vst, int64_t i, float x,
+                                           float y, float z, float m, float lx,
+                                           float ly, float lz) {
+  float* f = reinterpret_cast<float*>(vst) + 16 * (i >> 1) + (i & 1);
+  f[0] = x;
+  f[2] = y;
+  f[4] = z;
+  f[6] = m;
+  f[8] = lx;
+  f[10] = ly;
+  f[12] = lz;
+  f[14] = 0.f;
+}
+
+__global__ void k_stage(const double* __restrict__ x,
+                        const double* __restrict__ m,
+                        const double* __restrict__ c, int64_t n, int64_t npad,
+                        float4* __restrict__ st) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npad) return;
+  if (i < n)
+    put_stage(st, i, (float)(x[i] - c[0]), (float)(x[npad + i] - c[1]),
+              (float)(x[2 * npad + i] - c[2]), (float)m[i]);
+  else
+    put_stage(st, i, 0.f, 0.f, 0.f, 0.f);
+}
+
+__global__ void k_stage_vjp(const double* __restrict__ x,
+                            const double* __restrict__ m,
+                            const double* __restrict__ lam,
+                            const double* __restrict__ c, int64_t n,
+                            int64_t npad, float4* __restrict__ vst) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npad) return;
+  if (i < n)
+    put_vstage(vst, i, (float)(x[i] - c[0]), (float)(x[npad + i] - c[1]),
+               (float)(x[2 * npad + i] - c[2]), (float)m[i], (float)lam[i],
+               (float)lam[npad + i], (float)lam[2 * npad + i]);
+  else
+    put_vstage(vst, i, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
+}
+
+// ------------------------------------------------------------------- update
+__global__ void __launch_bounds__(256) k_update(UpdateArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const DevParams& P = *a.P;
+  const int64_t np = a.npad;
+  double ap[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (a.part_is_final) {
+      ap[d] = a.part[d * np + i];
+    } else {
+      double s = 0.0;
+      for (int q = 0; q < a.S; ++q) s += a.part[((int64_t)q * 3 + d) * np + i];
+      ap[d] = P.G * s;
+    }
+  }
+  double x[3], v[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    x[d] = a.x[d * np + i];
+    v[d] = a.v[d * np + i];
+    if (a.acc_out) a.acc_out[d * np + i] = ap[d];
+    if (a.cp_x) {
+      a.cp_x[d * np + i] = x[d];
+      a.cp_v[d * np + i] = v[d];
+      a.cp_a[d * np + i] = ap[d];
+    }
+    if (a.tape_x) {
+      a.tape_x[d * np + i] = x[d];
+      a.tape_a[d * np + i] = ap[d];
+    }
+  }
+  ExtUnit e;
+  ext_unit(P, x[0], x[1], x[2], e);
+  const double kick = a.kick * P.dt;
+  bool bad = false;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double acc = ap[d] + P.nfw_GM * e.n[d] + P.mn_GM * e.d[d];
+    v[d] += kick * acc;
+  }
+  if (a.drift) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (a.tape_vh) a.tape_vh[d * np + i] = v[d];
+      x[d] += P.dt * v[d];
+      a.x[d * np + i] = x[d];
+    }
+    put_stage_xyz(a.st, i, (float)(x[0] - a.c_next[0]),
+                  (float)(x[1] - a.c_next[1]), (float)(x[2] - a.c_next[2]));
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    a.v[d * np + i] = v[d];
+    bad |= !isfinite(v[d]) || !isfinite(x[d]);
+  }
+  if (bad) atomicOr(a.status, kStatusNaN);
+}
+
+// deterministic block sum of NV doubles; thread 0 adds the block total to
+// out[blockIdx.x * NV + q]
+template <int NV>
+__device__ __forceinline__ void block_accumulate(double (&val)[NV],
+                                                 double* out) {
+  __shared__ double sh[NV][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      val[q] += __shfl_down_sync(0xffffffffu, val[q], o);
+    if (lane == 0) sh[q][w] = val[q];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double s = 0.0;
+      for (int k = 0; k < nw; ++k) s += sh[q][k];
+      out[(int64_t)blockIdx.x * NV + q] += s;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ adjoint
+__global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const DevParams& P = *a.P;
+  const int64_t np = a.npad;
+  double contrib[4] = {0.0, 0.0, 0.0, 0.0};
+  if (i < a.n) {
+    double lam[3], x[3], ap[3], g[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      lam[d] = a.vbar[d * np + i];
+      x[d] = a.xk[d * np + i];
+      ap[d] = a.ak[d * np + i];
+      double s = 0.0;
+      for (int q = 0; q < a.S; ++q) s += a.gpart[((int64_t)q * 3 + d) * np + i];
+      g[d] = -P.G * s;
+    }
+    ExtUnit e;
+    ext_unit(P, x[0], x[1], x[2], e);
+    double jl[3];
+    ext_jvp(P, x[0], x[1], x[2], lam, jl);
+    const double ck = a.ck * P.dt;
+    double xb[3];
+    double la = 0.0, lp = 0.0, ln = 0.0, lm = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      xb[d] = a.xbar[d * np + i] + ck * (g[d] + jl[d]);
+      lp += lam[d] * ap[d];
+      ln += lam[d] * e.n[d];
+      lm += lam[d] * e.d[d];
+    }
+    la = lp + P.nfw_GM * ln + P.mn_GM * lm;
+    contrib[0] = a.ck * la;          // dL/d dt from the kick(s)
+    contrib[1] = ck * lp;            // sum_j m_j dL/dm_j
+    contrib[2] = ck * P.G * ln;      // dL/d M_NFW
+    contrib[3] = ck * P.G * lm;      // dL/d M_MN
+    double vb[3] = {lam[0], lam[1], lam[2]};
+    if (a.drift) {
+      double xv = 0.0;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        xv += xb[d] * a.vh_prev[d * np + i];
+        vb[d] += P.dt * xb[d];
+        a.vbar[d * np + i] = vb[d];
+      }
+      contrib[0] += xv;              // dL/d dt from the drift
+      put_vstage(a.vst, i, (float)(a.x_prev[i] - a.c_prev[0]),
+                 (float)(a.x_prev[np + i] - a.c_prev[1]),
+                 (float)(a.x_prev[2 * np + i] - a.c_prev[2]), (float)a.m[i],
+                 (float)vb[0], (float)vb[1], (float)vb[2]);
+    }
+    bool bad = false;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      a.xbar[d * np + i] = xb[d];
+      bad |= !isfinite(xb[d]) || !isfinite(vb[d]);
+    }
+    if (bad) atomicOr(a.status, kStatusNaN);
+  }
+  block_accumulate<4>(contrib, a.blk);
+}
+
+// ------------------------------------------------------------ reductions etc
+__global__ void __launch_bounds__(256)
+    k_reduce_rows(const double* __restrict__ blk, int nblk, int ncol,
+                  double* __restrict__ out) {
+  __shared__ double sh[256];
+  for (int q = 0; q < ncol; ++q) {
+    double s = 0.0;
+    for (int r = threadIdx.x; r < nblk; r += 256) s += blk[(int64_t)r * ncol + q];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[q] = sh[0];
+    __syncthreads();
+  }
+}
+
+__global__ void k_guide(const DevParams* __restrict__ Pp,
+                        const double* __restrict__ g0, int64_t n_steps,
+                        double* __restrict__ centers, double* __restrict__ gout) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const DevParams P = *Pp;
+  double x[3] = {g0[0], g0[1], g0[2]};
+  double v[3] = {g0[3], g0[4], g0[5]};
+  ExtUnit e;
+  ext_unit(P, x[0], x[1], x[2], e);
+  for (int d = 0; d < 3; ++d) centers[d] = x[d];
+  for (int64_t s = 0; s < n_steps; ++s) {
+    for (int d = 0; d < 3; ++d) {
+      v[d] += 0.5 * P.dt * (P.nfw_GM * e.n[d] + P.mn_GM * e.d[d]);
+      x[d] += P.dt * v[d];
+    }
+    ext_unit(P, x[0], x[1], x[2], e);
+    for (int d = 0; d < 3; ++d) {
+      v[d] += 0.5 * P.dt * (P.nfw_GM * e.n[d] + P.mn_GM * e.d[d]);
+      centers[3 * (s + 1) + d] = x[d];
+    }
+  }
+  for (int d = 0; d < 3; ++d) {
+    gout[d] = x[d];
+    gout[3 + d] = v[d];
+  }
+}
+
+__global__ void __launch_bounds__(256)
+    k_energy(const DevParams* __restrict__ Pp, const double* __restrict__ x,
+             const double* __restrict__ v, const double* __restrict__ m,
+             int64_t n, const double* __restrict__ pot, int S, int64_t np,
+             double* __restrict__ blk) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const DevParams& P = *Pp;
+  double val[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  if (i < n) {
+    const double mi = m[i];
+    double v2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      const double vd = v[d * np + i];
+      v2 += vd * vd;
+      val[3 + d] = mi * vd;
+    }
+    val[0] = 0.5 * mi * v2;
+    double s = 0.0;
+    for (int q = 0; q < S; ++q) s += pot[(int64_t)q * np + i];
+    // remove the self term m_i / eps that the pair loop includes
+    val[1] = -0.5 * P.G * mi * (s - mi / sqrt(P.eps2));
+    val[2] = mi * ext_potential(P, x[i], x[np + i], x[2 * np + i]);
+  }
+  block_accumulate<6>(val, blk);
+}
+
+__global__ void k_reduce_partials(const double* __restrict__ part, int S,
+                                  int64_t np, int64_t n, double G,
+                                  double* __restrict__ acc) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int d = 0; d < 3; ++d) {
+    double s = 0.0;
+    for (int q = 0; q < S; ++q) s += part[((int64_t)q * 3 + d) * np + i];
+    acc[d * n + i] = G * s;
+  }
+}
+
+inline unsigned blocks_for(int64_t n, int t) {
+  return (unsigned)((n + t - 1) / t);
+}
+
+}  // namespace
+
+cudaError_t launch_stage(const double* x, const double* m, const double* c,
+                         int64_t n, int64_t npad, float4* st, cudaStream_t s) {
+  k_stage<<<blocks_for(npad, 256), 256, 0, s>>>(x, m, c, n, npad, st);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s) {
+  k_update<<<blocks_for(a.n, 256), 256, 0, s>>>(a);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stage_vjp(const double* x, const double* m,
+                             const double* lam, const double* c, int64_t n,
+                             int64_t npad, float4* vst, cudaStream_t s) {
+  k_stage_vjp<<<blocks_for(npad, 256), 256, 0, s>>>(x, m, lam, c, n, npad, vst);
+  count_launch();
+  return cudaGetLastError();
+}
+
+int adjoint_blocks(int64_t n) { return (int)blocks_for(n, 256); }
+
+cudaError_t launch_adjoint(const AdjointArgs& a, cudaStream_t s) {
+  k_adjoint<<<adjoint_blocks(a.n), 256, 0, s>>>(a);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_rows(const double* blk, int nblk, int ncol,
+                               double* out, cudaStream_t s) {
+  k_reduce_rows<<<1, 256, 0, s>>>(blk, nblk, ncol, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_guide(const DevParams* P, const double* g0, int64_t n_steps,
+                         double* centers, double* g_out, cudaStream_t s) {
+  k_guide<<<1, 32, 0, s>>>(P, g0, n_steps, centers, g_out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+int energy_blocks(int64_t n) { return (int)blocks_for(n, 256); }
+
+cudaError_t launch_energy(const DevParams* P, const double* x,
+                          const double* v, const double* m, int64_t n,
+                          const double* pot_part, int S, int64_t npad,
+                          double* blk, int nblk, cudaStream_t s) {
+  (void)nblk;
+  k_energy<<<energy_blocks(n), 256, 0, s>>>(P, x, v, m, n, pot_part, S, npad, blk);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_partials(const double* part, int S, int64_t npad,
+                                   int64_t n, double G, double* acc,
+                                   cudaStream_t s) {
+  k_reduce_partials<<<blocks_for(n, 256), 256, 0, s>>>(part, S, npad, n, G, acc);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace nb

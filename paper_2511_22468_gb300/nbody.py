@@ -1,0 +1,261 @@
+"""Thin Python binding of libnbody (include/nbody.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of the library.  Functions carry the C names; arrays are torch
+tensors (device or pinned/pageable host) or numpy arrays, FP64, laid out
+structure-of-arrays: positions and velocities (3, n), masses (n,).
+The library is loaded on first use and a missing library raises, so no
+call can silently fall back to another implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "_build", "libnbody.so")
+
+NBODY_OK = 0
+NBODY_EINVAL = -1
+NBODY_ENOMEM = -2
+NBODY_ECUDA = -3
+NBODY_ETIMEOUT = -4
+NBODY_ENAN = -5
+NBODY_ESTATE = -6
+NBODY_ENODEV = -7
+
+NBODY_EXT_NFW = 1
+NBODY_EXT_MN = 2
+NBODY_CENTER_FIXED = 0
+NBODY_CENTER_GUIDE = 1
+NBODY_TAPE_KEEP_LAST = 0
+NBODY_TAPE_LEAN = 1
+
+EXPORTED = ("nbody_create", "nbody_destroy", "nbody_set_params",
+            "nbody_set_state", "nbody_get_state", "nbody_step",
+            "nbody_integrate", "nbody_vjp", "nbody_energy", "nbody_momentum",
+            "nbody_get_status", "nbody_strerror", "nbody_launch_count",
+            "nbody_pair_accel")
+
+
+class nbody_params(C.Structure):
+    _fields_ = [("G", C.c_double), ("eps", C.c_double), ("dt", C.c_double),
+                ("checkpoint_every", C.c_int64), ("ext_flags", C.c_uint32),
+                ("center_mode", C.c_uint32), ("tape_mode", C.c_uint32),
+                ("reserved", C.c_uint32), ("nfw_M", C.c_double),
+                ("nfw_rs", C.c_double), ("mn_M", C.c_double),
+                ("mn_a", C.c_double), ("mn_b", C.c_double),
+                ("center", C.c_double * 3), ("center_vel", C.c_double * 3)]
+
+
+def make_params(G, eps, dt, checkpoint_every=0, ext_flags=0, nfw_M=0.0,
+                nfw_rs=1.0, mn_M=0.0, mn_a=0.0, mn_b=0.0, center=(0, 0, 0),
+                center_vel=(0, 0, 0), center_mode=NBODY_CENTER_FIXED,
+                tape_mode=NBODY_TAPE_KEEP_LAST) -> nbody_params:
+    p = nbody_params()
+    p.G, p.eps, p.dt = G, eps, dt
+    p.checkpoint_every = int(checkpoint_every)
+    p.ext_flags, p.center_mode, p.tape_mode, p.reserved = ext_flags, center_mode, tape_mode, 0
+    p.nfw_M, p.nfw_rs, p.mn_M, p.mn_a, p.mn_b = nfw_M, nfw_rs, mn_M, mn_a, mn_b
+    p.center[:] = [float(c) for c in center]
+    p.center_vel[:] = [float(c) for c in center_vel]
+    return p
+
+
+class NBodyError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (what, nbody_strerror(code), code))
+
+
+_lib = None
+
+
+def lib():
+    """Load libnbody.so; raise if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libnbody.so is not built (%s); run "
+                               "paper_2511_22468_gb300.build.build()" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        P = C.POINTER(nbody_params)
+        vp, i64, dp = C.c_void_p, C.c_int64, C.POINTER(C.c_double)
+        L.nbody_create.argtypes = [C.POINTER(vp), i64, P, vp]
+        L.nbody_destroy.argtypes = [vp]
+        L.nbody_destroy.restype = None
+        L.nbody_set_params.argtypes = [vp, P]
+        L.nbody_set_state.argtypes = [vp, vp, vp, vp]
+        L.nbody_get_state.argtypes = [vp, vp, vp]
+        L.nbody_step.argtypes = [vp, i64]
+        L.nbody_integrate.argtypes = [vp, i64, vp, vp]
+        L.nbody_vjp.argtypes = [vp, vp, vp, vp, vp, vp, dp]
+        L.nbody_energy.argtypes = [vp, dp]
+        L.nbody_momentum.argtypes = [vp, dp]
+        L.nbody_get_status.argtypes = [vp]
+        L.nbody_strerror.argtypes = [C.c_int]
+        L.nbody_strerror.restype = C.c_char_p
+        L.nbody_launch_count.argtypes = []
+        L.nbody_launch_count.restype = i64
+        L.nbody_pair_accel.argtypes = [i64, vp, vp, C.c_double, C.c_double,
+                                       dp, vp, vp]
+        _lib = L
+    return _lib
+
+
+def _ptr(a, shape=None):
+    """Raw address of a float64 contiguous torch tensor or numpy array."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):  # torch
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("expected a contiguous float64 tensor")
+        if shape is not None and tuple(a.shape) != tuple(shape):
+            raise ValueError("expected shape %s, got %s" % (shape, tuple(a.shape)))
+        return C.c_void_p(a.data_ptr())
+    import numpy as np
+    if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError("expected a C-contiguous float64 array")
+    if shape is not None and tuple(a.shape) != tuple(shape):
+        raise ValueError("expected shape %s, got %s" % (shape, tuple(a.shape)))
+    return C.c_void_p(a.ctypes.data)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _check(rc, what):
+    if rc != NBODY_OK:
+        raise NBodyError(rc, what)
+
+
+def nbody_strerror(code: int) -> str:
+    return lib().nbody_strerror(code).decode()
+
+
+def nbody_launch_count() -> int:
+    return lib().nbody_launch_count()
+
+
+def nbody_create(n: int, params: nbody_params, stream=None):
+    h = C.c_void_p()
+    _check(lib().nbody_create(C.byref(h), n, C.byref(params), _stream(stream)),
+           "nbody_create")
+    return h
+
+
+def nbody_destroy(h):
+    lib().nbody_destroy(h)
+
+
+def nbody_set_params(h, params: nbody_params):
+    _check(lib().nbody_set_params(h, C.byref(params)), "nbody_set_params")
+
+
+def nbody_set_state(h, x, v, m):
+    n = m.shape[0]
+    _check(lib().nbody_set_state(h, _ptr(x, (3, n)), _ptr(v, (3, n)), _ptr(m, (n,))),
+           "nbody_set_state")
+
+
+def nbody_get_state(h, x=None, v=None):
+    _check(lib().nbody_get_state(h, _ptr(x), _ptr(v)), "nbody_get_state")
+
+
+def nbody_step(h, k: int):
+    _check(lib().nbody_step(h, k), "nbody_step")
+
+
+def nbody_integrate(h, n_steps: int, x_out=None, v_out=None):
+    _check(lib().nbody_integrate(h, n_steps, _ptr(x_out), _ptr(v_out)),
+           "nbody_integrate")
+
+
+def nbody_vjp(h, xbar, vbar, x0bar=None, v0bar=None):
+    """Returns theta_bar = (dL/d dt, sum_j m_j dL/dm_j, dL/dM_NFW, dL/dM_MN)."""
+    tb = (C.c_double * 4)()
+    _check(lib().nbody_vjp(h, _ptr(xbar), _ptr(vbar), _ptr(x0bar), _ptr(v0bar),
+                           None, tb), "nbody_vjp")
+    return list(tb)
+
+
+def nbody_energy(h):
+    """(K, W_pair, W_ext, |P|)."""
+    out = (C.c_double * 4)()
+    _check(lib().nbody_energy(h, out), "nbody_energy")
+    return list(out)
+
+
+def nbody_momentum(h):
+    out = (C.c_double * 3)()
+    _check(lib().nbody_momentum(h, out), "nbody_momentum")
+    return list(out)
+
+
+def nbody_get_status(h) -> int:
+    return lib().nbody_get_status(h)
+
+
+def nbody_pair_accel(x, m, G, eps, center, acc, stream=None):
+    """a_i of the softened pair sum for device tensors x (3, n), m (n,)
+    into acc (3, n)."""
+    n = m.shape[0]
+    cen = (C.c_double * 3)(*[float(c) for c in center])
+    _check(lib().nbody_pair_accel(n, _ptr(x, (3, n)), _ptr(m, (n,)), G, eps,
+                                  cen, _ptr(acc, (3, n)), _stream(stream)),
+           "nbody_pair_accel")
+
+
+class Simulation:
+    """Owning wrapper of one context (create / destroy)."""
+
+    def __init__(self, n, params, stream=None):
+        self.n = n
+        self.params = params
+        self.h = nbody_create(n, params, stream)
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            nbody_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        self.params = params
+        nbody_set_params(self.h, params)
+
+    def set_state(self, x, v, m):
+        nbody_set_state(self.h, x, v, m)
+
+    def get_state(self, x=None, v=None):
+        nbody_get_state(self.h, x, v)
+
+    def step(self, k):
+        nbody_step(self.h, k)
+
+    def integrate(self, n_steps, x_out=None, v_out=None):
+        nbody_integrate(self.h, n_steps, x_out, v_out)
+
+    def vjp(self, xbar, vbar, x0bar=None, v0bar=None):
+        return nbody_vjp(self.h, xbar, vbar, x0bar, v0bar)
+
+    def energy(self):
+        return nbody_energy(self.h)
+
+    def momentum(self):
+        return nbody_momentum(self.h)
+
+    def status(self):
+        return nbody_get_status(self.h)

@@ -1,0 +1,245 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (needs a GB300).
+
+Tolerances (stated for the method's FP32 pair sum with FP64 state):
+  * acceleration: |a_gpu - a_orc| / (|a_orc| + 1e-3 rms|a_orc|) <= 1e-5 per
+    particle;
+  * positions after 100 steps: max |dx| / r_scale <= 1e-6 (r_scale = the
+    Plummer scale radius);
+  * energy and momentum drift within 1e-6 of the oracle's;
+  * gradients: relative 1e-4 of the oracle adjoint (norm-wise per array,
+    element-wise per scalar).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import core as orc  # noqa: E402
+from paper_2511_22468_gb300 import nbody as nb  # noqa: E402
+from paper_2511_22468_gb300.configs import C1, C3  # noqa: E402
+from paper_2511_22468_gb300.inputs import plummer_sphere  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_22468_gb300 import build
+    build.build()
+    nb.lib()
+
+
+def to_gpu(a):
+    """(n, 3) numpy -> (3, n) float64 device tensor; (n,) -> (n,)."""
+    a = np.asarray(a, np.float64)
+    if a.ndim == 2:
+        a = a.T
+    return torch.tensor(np.ascontiguousarray(a), device=DEV)
+
+
+def to_np(t):
+    a = t.detach().cpu().numpy()
+    return a.T.copy() if a.ndim == 2 else a.copy()
+
+
+def acc_err(a, ref):
+    scale = np.linalg.norm(ref, axis=1) + 1e-3 * np.sqrt(np.mean(np.sum(ref * ref, axis=1)))
+    return np.max(np.linalg.norm(a - ref, axis=1) / scale)
+
+
+# -------------------------------------------------------------- pair force --
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 33, 1023, 1025, 4999, 70001])
+def test_pair_accel_matches_oracle(n):
+    x, v, m = plummer_sphere(max(n, 2), 100 + n, 1.0, 1.0, 1.0)
+    x, m = x[:n], m[:n] * np.linspace(0.5, 1.5, n)
+    eps = 0.01
+    acc = torch.empty((3, n), dtype=torch.float64, device=DEV)
+    nb.nbody_pair_accel(to_gpu(x), to_gpu(m), 1.0, eps, (0, 0, 0), acc)
+    torch.cuda.synchronize()
+    a = to_np(acc)
+    rows = None if n <= 5000 else np.random.default_rng(n).choice(n, 512, replace=False)
+    ref = orc.pair_accel(x, m, 1.0, eps, rows=rows)
+    got = a if rows is None else a[rows]
+    if n == 1:
+        assert np.all(got == 0.0)
+        return
+    assert acc_err(got, ref) <= 1e-5
+
+
+def test_pair_accel_full_size_sampled():
+    """The throughput workload (N = 1e6 Plummer sphere, 50 pc, eps 0.5 pc, at
+    the stream progenitor's position) in the launch shape the benchmark uses,
+    on 384 sampled particles the oracle computes one by one."""
+    n = C3.n
+    x, v, m = plummer_sphere(n, C3.seed, C3.G, C3.M, C3.a, center=C3.X0)
+    acc = torch.empty((3, n), dtype=torch.float64, device=DEV)
+    nb.nbody_pair_accel(to_gpu(x), to_gpu(m), C3.G, C3.eps, C3.X0, acc)
+    torch.cuda.synchronize()
+    rows = np.random.default_rng(7).choice(n, 384, replace=False)
+    ref = orc.pair_accel(x, m, C3.G, C3.eps, rows=rows)
+    assert acc_err(to_np(acc)[rows], ref) <= 1e-5
+
+
+# --------------------------------------------------------------- trajectory --
+def _sim(n, G, eps, dt, K=0, ext=0, pot=None, center=(0, 0, 0), center_vel=(0, 0, 0),
+         guide=False, lean=False):
+    kw = {}
+    if pot is not None:
+        kw = dict(nfw_M=pot.nfw_M, nfw_rs=pot.nfw_rs, mn_M=pot.mn_M, mn_a=pot.mn_a,
+                  mn_b=pot.mn_b)
+    p = nb.make_params(G, eps, dt, checkpoint_every=K, ext_flags=ext, center=center,
+                       center_vel=center_vel,
+                       center_mode=nb.NBODY_CENTER_GUIDE if guide else nb.NBODY_CENTER_FIXED,
+                       tape_mode=nb.NBODY_TAPE_LEAN if lean else nb.NBODY_TAPE_KEEP_LAST, **kw)
+    return nb.Simulation(n, p)
+
+
+def test_plummer_trajectory_energy_momentum():
+    """Isolated Plummer sphere (N = 1024, eps = 0.01, dt = 1e-3): positions
+    after 100 steps, energy and momentum drift against the oracle."""
+    n, eps, dt, steps = 1024, 0.01, 1e-3, 100
+    x, v, m = plummer_sphere(n, 0, 1.0, 1.0, 1.0)
+    sim = _sim(n, 1.0, eps, dt)
+    sim.set_state(to_gpu(x), to_gpu(v), to_gpu(m))
+    e0 = sim.energy()
+    P0 = np.array(sim.momentum())
+    xo = torch.empty((3, n), dtype=torch.float64, device=DEV)
+    vo = torch.empty_like(xo)
+    sim.integrate(steps, xo, vo)
+    e1 = sim.energy()
+    P1 = np.array(sim.momentum())
+    ph = orc.Physics(G=1.0, eps=eps)
+    xr, vr = orc.integrate(ph, x, v, m, dt, steps)
+    assert np.abs(to_np(xo) - xr).max() / 1.0 <= 1e-6
+    E0o = orc.energy(ph, x, v, m)
+    E1o = orc.energy(ph, xr, vr, m)
+    assert e0[0] + e0[1] + e0[2] == pytest.approx(E0o["E"], rel=1e-6)
+    dE_gpu = (e1[0] + e1[1] + e1[2]) / (e0[0] + e0[1] + e0[2]) - 1
+    dE_orc = E1o["E"] / E0o["E"] - 1
+    assert abs(dE_gpu - dE_orc) <= 1e-6
+    sig = np.sqrt(np.mean(np.sum(v * v, axis=1)))
+    assert np.abs(P1 - P0).max() / (m.sum() * sig) <= 1e-6
+    assert sim.status() == 0
+
+
+def test_step_calls_equal_one_integrate_call():
+    """Two 25-step calls continue the same trajectory as one 50-step call
+    (cached first-same-as-last acceleration), to rounding of the split kick."""
+    n = 512
+    x, v, m = plummer_sphere(n, 4, 1.0, 1.0, 1.0)
+    a = _sim(n, 1.0, 0.02, 2e-3)
+    b = _sim(n, 1.0, 0.02, 2e-3)
+    for s in (a, b):
+        s.set_state(to_gpu(x), to_gpu(v), to_gpu(m))
+    a.step(50)
+    b.step(25)
+    b.step(25)
+    xa = torch.empty((3, n), dtype=torch.float64, device=DEV)
+    xb = torch.empty_like(xa)
+    a.get_state(xa)
+    b.get_state(xb)
+    assert (xa - xb).abs().max().item() <= 1e-12
+
+
+def test_external_potential_stream_segment():
+    """Stream progenitor (N = 2048, 10 pc, eps = 1 pc) on its orbit in
+    NFW + MN, 100 steps of 0.5 Myr, guided recentring: positions against the
+    oracle."""
+    n, steps = 2048, 100
+    x, v, m = plummer_sphere(n, 3, C1.G, C1.M_prog, C1.a_prog, center=C1.X0, velocity=C1.V0)
+    p = C1.pot
+    sim = _sim(n, C1.G, C1.eps, 0.5, ext=3, pot=p, center=C1.X0, center_vel=C1.V0, guide=True)
+    sim.set_state(to_gpu(x), to_gpu(v), to_gpu(m))
+    xo = torch.empty((3, n), dtype=torch.float64, device=DEV)
+    sim.integrate(steps, xo)
+    ph = orc.Physics(G=C1.G, eps=C1.eps, ext=orc.NFW | orc.MN, nfw_M=p.nfw_M,
+                     nfw_rs=p.nfw_rs, mn_M=p.mn_M, mn_a=p.mn_a, mn_b=p.mn_b)
+    xr, vr = orc.integrate(ph, x, v, m, 0.5, steps)
+    d = np.linalg.norm(to_np(xo) - xr, axis=1)
+    # positions relative error per particle, and the internal structure:
+    # rms displacement error against the 10 pc Plummer scale (the worst
+    # particle sits near 1e-6 a after ~15 dynamical times: FP32 rounding of
+    # x - c, 2e-9 kpc at 20 pc, amplified by the cluster's chaos)
+    assert np.max(d / np.linalg.norm(xr, axis=1)) <= 1e-6
+    assert np.sqrt(np.mean(d * d)) / C1.a_prog <= 1e-6
+    assert np.max(d) / C1.a_prog <= 1e-5
+
+
+def test_bitwise_reproducible():
+    n = 3000
+    x, v, m = plummer_sphere(n, 8, 1.0, 1.0, 1.0)
+    outs = []
+    for _ in range(2):
+        s = _sim(n, 1.0, 0.01, 1e-3)
+        s.set_state(to_gpu(x), to_gpu(v), to_gpu(m))
+        o = torch.empty((3, n), dtype=torch.float64, device=DEV)
+        s.integrate(30, o)
+        outs.append(o)
+    assert torch.equal(outs[0], outs[1])
+
+
+# ------------------------------------------------------------------ adjoint --
+@pytest.mark.parametrize("K,lean,ext", [(7, False, 0), (10, True, 0), (50, False, 3), (4, True, 3)])
+def test_adjoint_matches_oracle(K, lean, ext):
+    """Discrete adjoint against the oracle's: dL/dx0, dL/dv0, dL/ddt, the mass
+    scale, dL/dM_NFW, dL/dM_MN; ragged last segments (50 = 7*7 + 1)."""
+    n, steps = 256, 50
+    if ext:
+        x, v, m = plummer_sphere(n, 12, C1.G, C1.M_prog, C1.a_prog, center=C1.X0,
+                                 velocity=C1.V0)
+        G, eps, dt, pot = C1.G, C1.eps, 0.5, C1.pot
+    else:
+        x, v, m = plummer_sphere(n, 12, 1.0, 1.0, 1.0)
+        G, eps, dt, pot = 1.0, 0.05, 2e-3, None
+    sim = _sim(n, G, eps, dt, K=K, ext=ext, pot=pot, center=x.mean(axis=0),
+               center_vel=v.mean(axis=0), guide=bool(ext), lean=lean)
+    sim.set_state(to_gpu(x), to_gpu(v), to_gpu(m))
+    sim.integrate(steps)
+    rng = np.random.default_rng(K)
+    wx = rng.normal(size=(n, 3))
+    wv = rng.normal(size=(n, 3))
+    x0b = torch.empty((3, n), dtype=torch.float64, device=DEV)
+    v0b = torch.empty_like(x0b)
+    tb = sim.vjp(to_gpu(wx), to_gpu(wv), x0b, v0b)
+    if ext:
+        ph = orc.Physics(G=G, eps=eps, ext=orc.NFW | orc.MN, nfw_M=pot.nfw_M,
+                         nfw_rs=pot.nfw_rs, mn_M=pot.mn_M, mn_a=pot.mn_a, mn_b=pot.mn_b)
+    else:
+        ph = orc.Physics(G=G, eps=eps)
+    r = orc.vjp(ph, x, v, m, dt, steps, wx, wv)
+    for got, ref in ((to_np(x0b), r["x0bar"]), (to_np(v0b), r["v0bar"])):
+        assert np.linalg.norm(got - ref) <= 1e-4 * np.linalg.norm(ref)
+    assert tb[0] == pytest.approx(r["dt_bar"], rel=1e-4)
+    assert tb[1] == pytest.approx(np.dot(m, r["mbar"]), rel=1e-4)
+    if ext:
+        assert tb[2] == pytest.approx(r["nfw_M_bar"], rel=1e-4)
+        assert tb[3] == pytest.approx(r["mn_M_bar"], rel=1e-4)
+    # a second reverse sweep over the same tape gives the same result
+    tb2 = sim.vjp(to_gpu(wx), to_gpu(wv), x0b2 := torch.empty_like(x0b), None)
+    assert torch.equal(x0b, x0b2) and tb2 == tb
+
+
+# ------------------------------------------------------------ error paths --
+def test_errors_are_reported():
+    p = nb.make_params(1.0, 0.0, 1e-3)
+    with pytest.raises(nb.NBodyError) as e:
+        nb.Simulation(10, p)
+    assert e.value.code == nb.NBODY_EINVAL
+    sim = _sim(10, 1.0, 0.1, 1e-3)
+    x, v, m = plummer_sphere(10, 1, 1.0, 1.0, 1.0)
+    sim.set_state(to_gpu(x), to_gpu(v), to_gpu(m))
+    sim.integrate(3)
+    with pytest.raises(nb.NBodyError) as e:  # no tape (checkpoint_every = 0)
+        sim.vjp(to_gpu(x), None)
+    assert e.value.code == nb.NBODY_ESTATE
+    with pytest.raises(nb.NBodyError):
+        sim.integrate(0)
+    # a non-finite input is caught by the update kernel and reported
+    x[3, 1] = np.nan
+    sim.set_state(to_gpu(x), to_gpu(v), to_gpu(m))
+    sim.step(2)
+    assert sim.status() == nb.NBODY_ENAN
