@@ -1,0 +1,390 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the differentiable direct-sum N-body path.
+
+Workload: an N = 1e6 Plummer sphere (1e6 Msun, a = 50 pc, eps = 0.5 pc) at
+the stream progenitor's present-day phase-space point in the NFW + MN
+potential, dt = 0.5 Myr, adjoint checkpoints every 10 steps, FP32 pair
+interactions with FP64 state.  That job is 100 kick-drift-kick steps forward
+plus the reverse sweep.  One benchmark step is one checkpoint segment of it:
+nbody_integrate(10 steps) continuing the trajectory, then nbody_vjp over
+those 10 steps with the lean tape (the segment is recomputed from its
+checkpoint, as every segment but the last is in the full job).
+
+value = fwd+adjoint pair interactions/s = 2 * N^2 * 10 / step time, summed
+over ranks (independent replicas, one per GPU); the kernel-level forward
+rate and the fraction of the FP32 CUDA-core peak are reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("pair interactions/s (fwd, fwd+adjoint) at N=1e6 and % FP32 peak; "
+          "batched sims/s")
+UNIT = "interactions/s"
+SEG = 10                  # KDK steps per benchmark step (= checkpoint spacing)
+FLOPS_PAIR = 20           # flops per interaction, forward convention
+FLOPS_VJP = 41            # flops per interaction of the pair VJP kernel
+FP32_LANES = 128          # FP32 FMA lanes per SM
+L2_BYTES = 129 * 2 ** 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_arrays():
+    from paper_2511_22468_gb300.configs import C3
+    from paper_2511_22468_gb300.inputs import plummer_sphere
+    x, v, m = plummer_sphere(C3.n, C3.seed, C3.G, C3.M, C3.a, center=C3.X0,
+                             velocity=C3.V0)
+    rng = np.random.default_rng(C3.seed + 1)
+    xbar = rng.normal(size=x.shape)
+    return C3, x, v, m, xbar
+
+
+def config_json(C3):
+    return {"workload": C3.name, "n": C3.n, "M_msun": C3.M, "a_kpc": C3.a,
+            "eps_kpc": C3.eps, "dt_myr": C3.dt, "potential": "NFW+MN",
+            "job_steps": C3.n_steps, "checkpoint_every": C3.checkpoint_every,
+            "bench_step": "integrate %d KDK steps + vjp over them (lean tape: "
+                          "segment recomputed)" % SEG,
+            "interactions_per_step": "2*N^2*%d (fwd + adjoint)" % SEG,
+            "l2": "inputs larger than L2: state + tape touched per step "
+                  "%.1f GB > 129 MB" % ((48 + 72 * SEG + 72) * C3.n / 1e9)}
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), float(f[3]), f[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[3][k].lower() == "active"})
+        load = [r for r in rows if r[2] > 200.0] or rows
+        return {"sm_mhz": statistics.median(r[0] for r in load),
+                "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_median": statistics.median(r[2] for r in load),
+                "samples": len(rows), "reasons": reasons}
+
+
+# ------------------------------------------------------------ cpu baseline --
+def oracle_sample(x, m, G, eps, rows_acc, rows_vjp, seed=0):
+    """Time the FP64 oracle on a row sample of the pair force and pair VJP at
+    full N; returns (seconds for one benchmark step's pair work, details)."""
+    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+    from oracle import core as orc
+    n = x.shape[0]
+    rng = np.random.default_rng(seed)
+    ra = np.sort(rng.choice(n, rows_acc, replace=False))
+    rv = np.sort(rng.choice(n, rows_vjp, replace=False))
+    lam = rng.normal(size=x.shape)
+    t0 = time.perf_counter()
+    orc.pair_accel(x, m, G, eps, rows=ra)
+    ta = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    orc.pair_vjp(x, m, G, eps, lam, rows=rv)
+    tv = time.perf_counter() - t0
+    # one benchmark step: SEG forward + (SEG-1) recomputed pair passes and
+    # SEG+1 VJP passes over all N rows
+    step_s = (2 * SEG - 1) * ta * n / rows_acc + (SEG + 1) * tv * n / rows_vjp
+    return step_s, ta + tv
+
+
+def cpu_cores():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+# -------------------------------------------------------------- reference --
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    C3, x, v, m, _ = workload_arrays()
+    from oracle.build import build_oracle
+    build_oracle()
+    ra, rv = 1024, 128
+    n = C3.n
+    for _ in range(args.warmup):
+        oracle_sample(x, m, C3.G, C3.eps, ra, rv)
+    steps = []
+    wall = 0.0
+    for k in range(args.steps):
+        s, w = oracle_sample(x, m, C3.G, C3.eps, ra, rv, seed=k + 1)
+        steps.append(s)
+        wall += w
+    step_s = float(np.mean(steps))
+    value = 2.0 * n * n * SEG / step_s
+    sample = ("per step: oracle pair force on %d and pair VJP on %d sampled rows "
+              "against all N = %d, scaled to the %d forward + %d recomputed + %d "
+              "VJP passes of one step" % (ra, rv, n, SEG, SEG - 1, SEG + 1))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_json(C3),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(),
+                             "kind": "oracle", "sample": sample,
+                             "wall_s": wall},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------- ours --
+def traffic_record(kernel):
+    """Per-launch DRAM traffic of a kernel from the committed ncu summary,
+    valid only while the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = {"pair": "pair_force.cu", "vjp": "pair_vjp.cu"}.get(kernel)
+    if src is None:
+        return None
+    h = hashlib.sha256(open(os.path.join(ROOT, "paper_2511_22468_gb300", "csrc", src),
+                            "rb").read()).hexdigest()[:16]
+    for line in open(path):
+        kv = dict(t.split("=", 1) for t in line.split() if "=" in t)
+        if kv.get("kernel") == kernel and kv.get("source_sha256_16") == h:
+            return float(kv["bytes_per_launch"])
+    return None
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2511_22468_gb300 import build, nbody as nb
+    build.build()
+    C3, x, v, m, xbar = workload_arrays()
+    n = C3.n
+    p = C3.pot
+    prm = nb.make_params(C3.G, C3.eps, C3.dt, checkpoint_every=SEG, ext_flags=3,
+                         nfw_M=p.nfw_M, nfw_rs=p.nfw_rs, mn_M=p.mn_M, mn_a=p.mn_a,
+                         mn_b=p.mn_b, center=C3.X0, center_vel=C3.V0,
+                         center_mode=nb.NBODY_CENTER_GUIDE,
+                         tape_mode=nb.NBODY_TAPE_LEAN)
+    X = torch.tensor(x.T.copy(), device=dev)
+    V = torch.tensor(v.T.copy(), device=dev)
+    M = torch.tensor(m, device=dev)
+    XB = torch.tensor(xbar.T.copy(), device=dev)
+    X0B = torch.empty_like(X)
+    V0B = torch.empty_like(X)
+    stream = torch.cuda.current_stream(dev)
+    sim = nb.Simulation(n, prm, stream)
+    sim.set_state(X, V, M)
+    nb.nbody_set_timing(sim.h, True)
+
+    def step():
+        sim.integrate(SEG)
+        return sim.vjp(XB, None, X0B, V0B)
+
+    for _ in range(args.warmup):
+        step()
+    nb.nbody_kernel_times(sim.h)  # reset the per-kernel sums
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    launches0 = nb.nbody_launch_count()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        ev[3 * k].record(stream)
+        sim.integrate(SEG)
+        ev[3 * k + 1].record(stream)
+        sim.vjp(XB, None, X0B, V0B)
+        ev[3 * k + 2].record(stream)
+    t_end.record(stream)
+    barrier()
+    launches = nb.nbody_launch_count() - launches0
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    fwd_ms = sum(ev[3 * k].elapsed_time(ev[3 * k + 1]) for k in range(args.steps))
+    bwd_ms = sum(ev[3 * k + 1].elapsed_time(ev[3 * k + 2]) for k in range(args.steps))
+    kt = nb.nbody_kernel_times(sim.h)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    units = 2.0 * n * n * SEG * args.steps * world
+    value = units / (total_ms / 1e3)
+
+    # roofline of the dominant kernel (FP32 CUDA-core bound, "alu")
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peak_max = sms * FP32_LANES * 2 * 2070e6 / 1e12
+    kernels = {}
+    for name, flops in (("pair", FLOPS_PAIR), ("vjp", FLOPS_VJP)):
+        ms, cnt = kt[name]
+        if cnt:
+            avg_s = ms / cnt / 1e3
+            ach = flops * n * n / avg_s / 1e12
+            kernels[name] = {"launches": cnt, "total_ms": ms, "avg_ms": avg_s * 1e3,
+                             "flops_per_interaction": flops,
+                             "interactions_per_s": n * n / avg_s,
+                             "achieved_tflops": ach, "frac_of_peak_at_2070MHz": ach / peak_max}
+    for name in ("update", "adjoint"):
+        ms, cnt = kt[name]
+        kernels[name] = {"launches": cnt, "total_ms": ms,
+                         "avg_ms": ms / cnt if cnt else None}
+    dom = max(("pair", "vjp"), key=lambda k: kt[k][0])
+    d = kernels[dom]
+    sm_mhz = clk["sm_mhz"] if clk else None
+    roofline = {"bound": "alu", "kernel": dom, "achieved": d["achieved_tflops"],
+                "peak": peak_max, "unit": "TFLOP/s",
+                "frac": d["achieved_tflops"] / peak_max,
+                "traffic": traffic_record(dom),
+                "peak_basis": "%d SMs x %d FP32 lanes x 2 flop x 2070 MHz (max SM clock)"
+                              % (sms, FP32_LANES),
+                "frac_at_measured_clock": (d["achieved_tflops"] / (peak_max * sm_mhz / 2070.0))
+                if sm_mhz else None}
+
+    # end to end through the C ABI with pinned host buffers
+    xh = torch.tensor(x.T.copy()).pin_memory()
+    vh = torch.tensor(v.T.copy()).pin_memory()
+    mh = torch.tensor(m).pin_memory()
+    xbh = torch.tensor(xbar.T.copy()).pin_memory()
+    x0h = torch.empty((3, n), dtype=torch.float64).pin_memory()
+    v0h = torch.empty((3, n), dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, args.e2e_steps)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sim.set_state(xh, vh, mh)
+        sim.integrate(SEG)
+        sim.vjp(xbh, None, x0h, v0h)
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": 2.0 * n * n * SEG * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int((3 + 3 + 1 + 3) * n * 8),
+           "d2h_bytes_per_step": int((3 + 3) * n * 8 + 4 * 8),
+           "steps": e2e_steps, "ms_per_step": e2e_s * 1e3}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ra, rv = 8192, 1024
+        step_s, wall = oracle_sample(x, m, C3.G, C3.eps, ra, rv)
+        cpu = {"value": 2.0 * n * n * SEG / step_s, "unit": UNIT, "cores": cpu_cores(),
+               "kind": "oracle",
+               "sample": "oracle pair force on %d and pair VJP on %d sampled rows "
+                         "against all N = %d, scaled to one step's %d forward + %d "
+                         "recomputed + %d VJP passes" % (ra, rv, n, SEG, SEG - 1, SEG + 1),
+               "wall_s": wall}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "state_dtype": "f64",
+                "data": "synthetic (seeded Plummer sphere)", "config": config_json(C3),
+                "fwd_interactions_per_s": n * n * SEG * args.steps * world / (fwd_ms / 1e3),
+                "adjoint_ms_per_step": bwd_ms / args.steps,
+                "fwd_ms_per_step": fwd_ms / args.steps,
+                "pct_fp32_peak": {k: 100.0 * kernels[k]["frac_of_peak_at_2070MHz"]
+                                  for k in ("pair", "vjp") if k in kernels},
+                "batched_sims_per_s": None,
+                "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu,
+                "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
+                "parallelism": "replicas" if world > 1 else "single"}
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.steps < 1 or args.warmup < 0:
+        raise SystemExit("--steps must be >= 1")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -171,6 +171,25 @@ NBODY_API const char *nbody_strerror(int code);
  * (all contexts); a monotonically increasing counter for accounting. */
 NBODY_API int64_t nbody_launch_count(void);
 
+/* ---- per-kernel timing (CUDA events on the context stream) ---- */
+#define NBODY_KCLASS_PAIR 0    /* pair-force kernel (forward and recompute)   */
+#define NBODY_KCLASS_VJP 1     /* pair VJP kernel                             */
+#define NBODY_KCLASS_UPDATE 2  /* kick-drift-kick update kernel               */
+#define NBODY_KCLASS_ADJOINT 3 /* adjoint update kernel                       */
+#define NBODY_NKCLASS 4
+
+/* Enable (1) or disable (0) event timing of the context's kernels: when
+ * enabled, every launch of the four classes above is bracketed by two CUDA
+ * events recorded on the context stream.  Errors: EINVAL. */
+NBODY_API int nbody_set_timing(nbody_ctx *c, int enable);
+
+/* Sum of the event-timed durations (ms) and launch counts per class since
+ * the previous call (or since timing was enabled), then reset.  ms and
+ * launches are host arrays of NBODY_NKCLASS entries; launches may be NULL.
+ * Synchronises the context stream.  Errors: EINVAL, ECUDA. */
+NBODY_API int nbody_kernel_times(nbody_ctx *c, double ms[NBODY_NKCLASS],
+                                 int64_t launches[NBODY_NKCLASS]);
+
 /* ---- stateless kernels (device pointers only, stream = cuda_stream) ---- */
 
 /* Softened pair acceleration of n particles (Sec. 1), the FP32 hot loop:

@@ -26,6 +26,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <utility>
+#include <vector>
 
 #include "nbody_internal.cuh"
 
@@ -80,6 +82,11 @@ struct nbody_ctx {
   double* red = nullptr;  // [8]
   int nblk = 0;
   int* status = nullptr;
+
+  // per-kernel event timing
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[NBODY_NKCLASS];
+  size_t ev_used[NBODY_NKCLASS] = {};
 };
 
 namespace {
@@ -151,6 +158,33 @@ int upload_params(nbody_ctx* c) {
   // pageable sources: make the copies complete before the host arrays die
   CK(cudaStreamSynchronize(c->stream));
   return NBODY_OK;
+}
+
+// Launch through f(), bracketed by two events on the context stream when
+// timing is enabled.
+template <class F>
+cudaError_t timed(nbody_ctx* c, int cls, F&& f) {
+  if (!c->timing) return f();
+  auto& pool = c->ev[cls];
+  const size_t k = c->ev_used[cls];
+  if (k == pool.size()) {
+    cudaEvent_t a, b;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreate(&b);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(a);
+      return e;
+    }
+    pool.emplace_back(a, b);
+  }
+  cudaError_t e = cudaEventRecord(pool[k].first, c->stream);
+  if (e != cudaSuccess) return e;
+  e = f();
+  if (e != cudaSuccess) return e;
+  e = cudaEventRecord(pool[k].second, c->stream);
+  c->ev_used[cls] = k + 1;
+  return e;
 }
 
 // centre of point k of the current call
@@ -251,8 +285,10 @@ int run_forward(nbody_ctx* c, int64_t n_steps, bool with_tape) {
     } else {
       if (k == 0)
         CK(nb::launch_stage(c->x, c->m, center_at(c, 0), c->n, c->npad, c->st, s));
-      CK(nb::launch_pair_accel(c->fcfg, c->st, c->npad, c->hp.eps2f, c->part,
-                               nullptr, s));
+      CK(timed(c, NBODY_KCLASS_PAIR, [&] {
+        return nb::launch_pair_accel(c->fcfg, c->st, c->npad, c->hp.eps2f,
+                                     c->part, nullptr, s);
+      }));
     }
     a.acc_out = (k == n_steps) ? c->acc : nullptr;
     a.kick = (k == 0 || k == n_steps) ? 0.5 : 1.0;
@@ -272,7 +308,7 @@ int run_forward(nbody_ctx* c, int64_t n_steps, bool with_tape) {
         a.tape_vh = T.svh(j + 1);
       }
     }
-    CK(nb::launch_update(a, s));
+    CK(timed(c, NBODY_KCLASS_UPDATE, [&] { return nb::launch_update(a, s); }));
   }
   c->acc_valid = true;
   if (with_tape) {
@@ -303,8 +339,10 @@ int recompute_segment(nbody_ctx* c, int64_t sg) {
       a.S = 1;
       a.part_is_final = 1;
     } else {
-      CK(nb::launch_pair_accel(c->fcfg, c->st, c->npad, c->hp.eps2f, c->part,
-                               nullptr, s));
+      CK(timed(c, NBODY_KCLASS_PAIR, [&] {
+        return nb::launch_pair_accel(c->fcfg, c->st, c->npad, c->hp.eps2f,
+                                     c->part, nullptr, s);
+      }));
     }
     a.kick = (k == 0) ? 0.5 : 1.0;
     a.drift = 1;
@@ -312,7 +350,7 @@ int recompute_segment(nbody_ctx* c, int64_t sg) {
     a.tape_x = T.sx(j);
     a.tape_a = T.sa(j);
     a.tape_vh = T.svh(j + 1);
-    CK(nb::launch_update(a, s));
+    CK(timed(c, NBODY_KCLASS_UPDATE, [&] { return nb::launch_update(a, s); }));
   }
   return NBODY_OK;
 }
@@ -341,6 +379,11 @@ int copy_out3(nbody_ctx* c, double* dst, const double* src) {
 }
 
 void free_all(nbody_ctx* c) {
+  for (auto& pool : c->ev)
+    for (auto& pr : pool) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
   dfree(c->dp);
   dfree(c->x);
   dfree(c->v);
@@ -555,7 +598,9 @@ int nbody_vjp(nbody_ctx* c, const double* xbar, const double* vbar,
     }
     for (int64_t j = Ks; j >= 1; --j) {
       const int64_t k = k0 + j;
-      CK(nb::launch_pair_vjp(c->vcfg, c->vst, c->npad, c->hp.eps2f, c->part, s));
+      CK(timed(c, NBODY_KCLASS_VJP, [&] {
+        return nb::launch_pair_vjp(c->vcfg, c->vst, c->npad, c->hp.eps2f, c->part, s);
+      }));
       a.xk = (j == Ks) ? T.cpx(sg + 1) : T.sx(j);
       a.ak = (j == Ks) ? T.cpa(sg + 1) : T.sa(j);
       a.ck = (k == n) ? 0.5 : 1.0;
@@ -563,11 +608,13 @@ int nbody_vjp(nbody_ctx* c, const double* xbar, const double* vbar,
       a.vh_prev = T.svh(j);
       a.x_prev = T.sx(j - 1);
       a.c_prev = center_at(c, k - 1);
-      CK(nb::launch_adjoint(a, s));
+      CK(timed(c, NBODY_KCLASS_ADJOINT, [&] { return nb::launch_adjoint(a, s); }));
     }
   }
   // point 0: opening half kick of the first step
-  CK(nb::launch_pair_vjp(c->vcfg, c->vst, c->npad, c->hp.eps2f, c->part, s));
+  CK(timed(c, NBODY_KCLASS_VJP, [&] {
+        return nb::launch_pair_vjp(c->vcfg, c->vst, c->npad, c->hp.eps2f, c->part, s);
+      }));
   a.xk = T.cpx(0);
   a.ak = T.cpa(0);
   a.ck = 0.5;
@@ -575,7 +622,7 @@ int nbody_vjp(nbody_ctx* c, const double* xbar, const double* vbar,
   a.vh_prev = nullptr;
   a.x_prev = nullptr;
   a.c_prev = nullptr;
-  CK(nb::launch_adjoint(a, s));
+  CK(timed(c, NBODY_KCLASS_ADJOINT, [&] { return nb::launch_adjoint(a, s); }));
   c->last_seg_valid = false;  // the segment buffer now holds segment 0
 
   CK(nb::launch_reduce_rows(c->blk, c->nblk, 4, c->red, s));
@@ -634,6 +681,31 @@ int nbody_get_status(nbody_ctx* c) {
   CK(cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost));
   if (st & nb::kStatusNaN) return NBODY_ENAN;
   if (st & nb::kStatusTimeout) return NBODY_ETIMEOUT;
+  return NBODY_OK;
+}
+
+int nbody_set_timing(nbody_ctx* c, int enable) {
+  if (!c) return NBODY_EINVAL;
+  c->timing = enable != 0;
+  for (auto& u : c->ev_used) u = 0;
+  return NBODY_OK;
+}
+
+int nbody_kernel_times(nbody_ctx* c, double ms[NBODY_NKCLASS],
+                       int64_t launches[NBODY_NKCLASS]) {
+  if (!c || !ms) return NBODY_EINVAL;
+  CK(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < NBODY_NKCLASS; ++k) {
+    double t = 0.0;
+    for (size_t i = 0; i < c->ev_used[k]; ++i) {
+      float e = 0.f;
+      CK(cudaEventElapsedTime(&e, c->ev[k][i].first, c->ev[k][i].second));
+      t += e;
+    }
+    ms[k] = t;
+    if (launches) launches[k] = (int64_t)c->ev_used[k];
+    c->ev_used[k] = 0;
+  }
   return NBODY_OK;
 }
 

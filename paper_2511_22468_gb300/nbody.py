@@ -35,7 +35,9 @@ EXPORTED = ("nbody_create", "nbody_destroy", "nbody_set_params",
             "nbody_set_state", "nbody_get_state", "nbody_step",
             "nbody_integrate", "nbody_vjp", "nbody_energy", "nbody_momentum",
             "nbody_get_status", "nbody_strerror", "nbody_launch_count",
-            "nbody_pair_accel")
+            "nbody_pair_accel", "nbody_set_timing", "nbody_kernel_times")
+
+NBODY_KCLASS = ("pair", "vjp", "update", "adjoint")
 
 
 class nbody_params(C.Structure):
@@ -99,6 +101,8 @@ def lib():
         L.nbody_launch_count.restype = i64
         L.nbody_pair_accel.argtypes = [i64, vp, vp, C.c_double, C.c_double,
                                        dp, vp, vp]
+        L.nbody_set_timing.argtypes = [vp, C.c_int]
+        L.nbody_kernel_times.argtypes = [vp, dp, C.POINTER(i64)]
         _lib = L
     return _lib
 
@@ -211,6 +215,18 @@ def nbody_pair_accel(x, m, G, eps, center, acc, stream=None):
     _check(lib().nbody_pair_accel(n, _ptr(x, (3, n)), _ptr(m, (n,)), G, eps,
                                   cen, _ptr(acc, (3, n)), _stream(stream)),
            "nbody_pair_accel")
+
+
+def nbody_set_timing(h, enable: bool):
+    _check(lib().nbody_set_timing(h, int(bool(enable))), "nbody_set_timing")
+
+
+def nbody_kernel_times(h):
+    """{class: (ms, launches)} summed since the previous call."""
+    ms = (C.c_double * 4)()
+    cnt = (C.c_int64 * 4)()
+    _check(lib().nbody_kernel_times(h, ms, cnt), "nbody_kernel_times")
+    return {k: (ms[i], cnt[i]) for i, k in enumerate(NBODY_KCLASS)}
 
 
 class Simulation:
