@@ -58,6 +58,7 @@ extern "C" {
 #define NBODY_ENAN (-5)     /* a non-finite value appeared in the state */
 #define NBODY_ESTATE (-6)   /* call out of order (e.g. vjp without a tape) */
 #define NBODY_ENODEV (-7)   /* no usable sm_103a device */
+#define NBODY_ESIZE (-8)    /* problem larger than a fixed-size buffer holds */
 
 /* ---- external potential components (Sec. 2.2.1) ---- */
 #define NBODY_EXT_NFW 1u /* NFW halo: Phi = -G M ln(1 + r/r_s) / r          */
@@ -201,6 +202,38 @@ NBODY_API int nbody_kernel_times(nbody_ctx *c, double ms[NBODY_NKCLASS],
 NBODY_API int nbody_pair_accel(int64_t n, const double *x, const double *m, double G,
                      double eps, const double center[3], double *acc,
                      void *cuda_stream);
+
+/* ---- allocation-free variant (no counterpart in the paper) ---- */
+
+/* Largest n accepted by nbody_pair_accel_noalloc. */
+#define NBODY_NOALLOC_MAX_N 32768
+
+/* The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory when they need forces -- an application
+ * that reserves all of its device memory up front under a fixed budget, or
+ * a hot loop that must not take the allocator's locks or pay its latency.
+ *
+ * Same result, kernels and launch shapes as nbody_pair_accel, but the
+ * call makes no device allocation (no cudaMalloc, cudaMallocAsync or
+ * cudaFree, no allocating library routine): its scratch is one 4 MiB
+ * device array inside the library, which every GPU that loads the library
+ * holds until the process exits.  x (3 x n), m (n) and acc (3 x n) are
+ * caller-owned device memory; center is 3 host doubles.
+ *
+ * - n must be in [1, NBODY_NOALLOC_MAX_N]; a larger n returns NBODY_ESIZE
+ *   and launches nothing.
+ * - The first call on a device looks up the device address of the array
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture on the device.
+ * - Asynchronous: acc is complete when cuda_stream reaches the end of the
+ *   call.  Every call on a device shares the one array, so calls that may
+ *   overlap on the GPU (issued to different streams without ordering)
+ *   race and give undefined results; calls on one stream are safe.
+ * Errors: EINVAL, ESIZE, ENODEV, ECUDA. */
+NBODY_API int nbody_pair_accel_noalloc(int64_t n, const double *x,
+                                       const double *m, double G, double eps,
+                                       const double center[3], double *acc,
+                                       void *cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -437,6 +437,7 @@ const char* nbody_strerror(int code) {
     case NBODY_ENAN: return "non-finite value in the state";
     case NBODY_ESTATE: return "call out of order (no tape recorded)";
     case NBODY_ENODEV: return "no sm_103a device";
+    case NBODY_ESIZE: return "size exceeds the fixed buffer of this call";
     default: return "unknown status";
   }
 }

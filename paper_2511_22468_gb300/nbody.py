@@ -23,6 +23,8 @@ NBODY_ETIMEOUT = -4
 NBODY_ENAN = -5
 NBODY_ESTATE = -6
 NBODY_ENODEV = -7
+NBODY_ESIZE = -8
+NBODY_NOALLOC_MAX_N = 32768
 
 NBODY_EXT_NFW = 1
 NBODY_EXT_MN = 2
@@ -35,7 +37,8 @@ EXPORTED = ("nbody_create", "nbody_destroy", "nbody_set_params",
             "nbody_set_state", "nbody_get_state", "nbody_step",
             "nbody_integrate", "nbody_vjp", "nbody_energy", "nbody_momentum",
             "nbody_get_status", "nbody_strerror", "nbody_launch_count",
-            "nbody_pair_accel", "nbody_set_timing", "nbody_kernel_times")
+            "nbody_pair_accel", "nbody_set_timing", "nbody_kernel_times",
+            "nbody_pair_accel_noalloc")
 
 NBODY_KCLASS = ("pair", "vjp", "update", "adjoint")
 
@@ -101,6 +104,8 @@ def lib():
         L.nbody_launch_count.restype = i64
         L.nbody_pair_accel.argtypes = [i64, vp, vp, C.c_double, C.c_double,
                                        dp, vp, vp]
+        L.nbody_pair_accel_noalloc.argtypes = [i64, vp, vp, C.c_double,
+                                               C.c_double, dp, vp, vp]
         L.nbody_set_timing.argtypes = [vp, C.c_int]
         L.nbody_kernel_times.argtypes = [vp, dp, C.POINTER(i64)]
         _lib = L
@@ -215,6 +220,19 @@ def nbody_pair_accel(x, m, G, eps, center, acc, stream=None):
     _check(lib().nbody_pair_accel(n, _ptr(x, (3, n)), _ptr(m, (n,)), G, eps,
                                   cen, _ptr(acc, (3, n)), _stream(stream)),
            "nbody_pair_accel")
+
+
+def nbody_pair_accel_noalloc(x, m, G, eps, center, acc, stream=None):
+    """nbody_pair_accel without device allocation, for callers that cannot
+    allocate when they need forces (fixed up-front memory budget, or a loop
+    that must avoid the allocator); scratch lives in a fixed 4 MiB device
+    array of the library, n <= NBODY_NOALLOC_MAX_N.  Asynchronous on the
+    stream; calls overlapping on the GPU race on the shared array."""
+    n = m.shape[0]
+    cen = (C.c_double * 3)(*[float(c) for c in center])
+    _check(lib().nbody_pair_accel_noalloc(n, _ptr(x, (3, n)), _ptr(m, (n,)), G, eps,
+                                          cen, _ptr(acc, (3, n)), _stream(stream)),
+           "nbody_pair_accel_noalloc")
 
 
 def nbody_set_timing(h, enable: bool):
