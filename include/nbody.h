@@ -203,6 +203,71 @@ NBODY_API int nbody_pair_accel(int64_t n, const double *x, const double *m, doub
                      double eps, const double center[3], double *acc,
                      void *cuda_stream);
 
+/* ---- the mock-stream pipeline (Fig. 2, Sec. 2.2.1) ---- */
+
+/* Loss L(Theta), Theta = { t_end, M_Plummer, M_NFW, M_MN } (Sec. 2.2.1):
+ *  1. the progenitor's present-day centre of mass (X0, V0) is integrated
+ *     backward for t_end as a single particle in the NFW + MN potential
+ *     (n_steps kick-drift-kick steps of -t_end/n_steps; Fig. 2 step 2);
+ *  2. a unit Plummer sample (xhat, vhat) is scaled and shifted there:
+ *     x = a xhat + X, v = sqrt(G M_Plummer / a) vhat + V, m = M_Plummer / n
+ *     (Fig. 2 step 3);
+ *  3. the n-body system is integrated forward n_steps steps of
+ *     t_end/n_steps with pair forces and the potential (Sec. 2.2.1);
+ *  4. positions are projected to sky angles seen from `observer` in the
+ *     frame e1 = unit(X0 - observer), pole = unit((X0 - observer) x V0),
+ *     phi1 = atan2(d.e2, d.e1), phi2 = asin(d.pole / |d|);
+ *  5. a Gaussian-smoothed nb1 x nb2 histogram (sigma = half a bin, each bin
+ *     receiving the normal-CDF mass between its edges, weights 1/n) is
+ *     compared with a target: L = mean_b (rho_b - target_b)^2.
+ * The paper compares point clouds with an MMD (Fig. 2 step 4); the binned
+ * density is this library's smooth stand-in. */
+typedef struct nbody_stream_cfg {
+  int64_t n;                /* progenitor particles, >= 1                    */
+  int64_t n_steps;          /* steps of the orbit and of the n-body run      */
+  int64_t checkpoint_every; /* adjoint checkpoint spacing K >= 1             */
+  double G;                 /* gravitational constant                        */
+  double eps;               /* softening length, > 0                         */
+  double a_prog;            /* Plummer scale radius of the progenitor, > 0   */
+  double nfw_rs;            /* NFW scale radius (fixed)                      */
+  double mn_a, mn_b;        /* disk scale length and height (fixed)          */
+  double X0[3], V0[3];      /* present-day centre of mass                    */
+  double observer[3];       /* observer position                             */
+  int32_t nb1, nb2;         /* histogram bins in phi1 and phi2, 1..64        */
+  double phi1_lo, phi1_hi;  /* phi1 window (radians)                         */
+  double phi2_lo, phi2_hi;  /* phi2 window (radians)                         */
+} nbody_stream_cfg;
+
+typedef struct nbody_stream nbody_stream; /* opaque, owned by the library */
+
+/* Create the pipeline for a unit Plummer sample xhat, vhat (3 x n each,
+ * host or device; copied).  The target starts at zero.
+ * Errors: EINVAL, ENODEV, ENOMEM, ECUDA. */
+NBODY_API int nbody_stream_create(nbody_stream **out,
+                                  const nbody_stream_cfg *cfg,
+                                  const double *xhat, const double *vhat,
+                                  void *cuda_stream);
+
+/* Replace the target density (nb1 * nb2 doubles, row-major [b1][b2], host
+ * or device).  Errors: EINVAL, ECUDA. */
+NBODY_API int nbody_stream_set_target(nbody_stream *s, const double *target);
+
+/* Run steps 1-5 at theta (host, 4 doubles, all > 0).  loss (host, may be
+ * NULL) receives L; density (host or device, nb1 * nb2, may be NULL) the
+ * histogram.  Records what nbody_stream_grad needs.  Synchronises.
+ * Errors: EINVAL, ENOMEM, ECUDA, ENAN. */
+NBODY_API int nbody_stream_forward(nbody_stream *s, const double theta[4],
+                                   double *loss, double *density);
+
+/* dL/dTheta at the theta of the last nbody_stream_forward (host, 4
+ * doubles), by the discrete adjoint of every step: head, n-body reverse
+ * sweep (nbody_vjp), Plummer shift and backward orbit.  Synchronises.
+ * Errors: ESTATE (no forward), ECUDA, ENAN. */
+NBODY_API int nbody_stream_grad(nbody_stream *s, double theta_bar[4]);
+
+/* Release the pipeline; NULL is a no-op. */
+NBODY_API void nbody_stream_destroy(nbody_stream *s);
+
 /* ---- allocation-free variant (no counterpart in the paper) ---- */
 
 /* Largest n accepted by nbody_pair_accel_noalloc. */

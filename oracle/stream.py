@@ -179,6 +179,9 @@ class StreamModel:
                       np.asarray(self.cfg.X0, float)[None, :],
                       np.asarray(self.cfg.V0, float)[None, :], np.ones(1),
                       -t_acc / n, n, Xb[None, :], Vb[None, :], want_mbar=False)
+        # t_end enters twice, through the forward run's dt and the backward
+        # orbit's -dt; the two parts are kept for error bounds
+        self.t_end_parts = (r["dt_bar"] / n, -ro["dt_bar"] / n)
         grad = np.array([
             r["dt_bar"] / n - ro["dt_bar"] / n,
             Mb,

@@ -1,0 +1,124 @@
+// ext_potential.cuh -- FP64 device functions of the external potential:
+// MWPotential2014's NFW halo and Miyamoto-Nagai disk (paper Sec. 2.2.1),
+//   NFW  Phi = -G M ln(1 + r/r_s) / r,
+//   MN   Phi = -G M / sqrt(R^2 + (a + sqrt(z^2 + b^2))^2),
+// their accelerations (per unit G M and full) and the Jacobian-vector
+// product of the acceleration.  Shared by the integrator, the adjoint and
+// the single-orbit kernels.
+#pragma once
+
+#include "nbody_internal.cuh"
+
+namespace nb {
+
+// Unit-mass (G M = 1) accelerations of the halo and the disk.
+struct ExtUnit {
+  double n[3];
+  double d[3];
+};
+
+static __device__ __forceinline__ double nfw_f(double r, double rs) {
+  // a_NFW = -G M f(r) x, f(r) = ln(1 + r/r_s)/r^3 - 1/(r^2 (r + r_s));
+  // below r = 1e-4 r_s the two terms cancel and the Taylor series is used.
+  const double u = r / rs;
+  if (u < 1e-4) {
+    const double rs2 = rs * rs, rs3 = rs2 * rs;
+    return (0.5 / rs2) / r - (2.0 / 3.0) / rs3 + (0.75 / (rs3 * rs)) * r -
+           (0.8 / (rs3 * rs2)) * r * r;
+  }
+  return (log1p(u) / r - 1.0 / (r + rs)) / (r * r);
+}
+
+static __device__ __forceinline__ double nfw_fprime_over_r(double r, double rs) {
+  // f'(r)/r with f' = 1/(r^3 (r+r_s)) - 3 ln(1+r/r_s)/r^4
+  //                   + (3 r + 2 r_s)/(r^3 (r+r_s)^2)
+  const double u = r / rs;
+  if (u < 1e-4) {
+    const double rs2 = rs * rs, rs4 = rs2 * rs2;
+    return (-0.5 / rs2) / (r * r * r) + (0.75 / rs4) / r - 1.6 / (rs4 * rs);
+  }
+  const double rp = r + rs;
+  const double r3 = r * r * r;
+  return (1.0 / (r3 * rp) - 3.0 * log1p(u) / (r3 * r) +
+          (3.0 * r + 2.0 * rs) / (r3 * rp * rp)) / r;
+}
+
+static __device__ __forceinline__ void ext_unit(const DevParams& P, double x,
+                                         double y, double z, ExtUnit& e) {
+  e.n[0] = e.n[1] = e.n[2] = 0.0;
+  e.d[0] = e.d[1] = e.d[2] = 0.0;
+  if (P.ext & NBODY_EXT_NFW) {
+    const double r = sqrt(x * x + y * y + z * z);
+    if (r > 0.0) {
+      const double f = nfw_f(r, P.nfw_rs);
+      e.n[0] = -f * x;
+      e.n[1] = -f * y;
+      e.n[2] = -f * z;
+    }
+  }
+  if (P.ext & NBODY_EXT_MN) {
+    const double B = sqrt(z * z + P.mn_b * P.mn_b);
+    const double aB = P.mn_a + B;
+    const double S2 = x * x + y * y + aB * aB;
+    const double iS3 = 1.0 / (S2 * sqrt(S2));
+    e.d[0] = -x * iS3;
+    e.d[1] = -y * iS3;
+    e.d[2] = -z * aB / B * iS3;
+  }
+}
+
+// (d a_ext / d x) l, full accelerations (G M included); the Jacobian is
+// symmetric so this is also J^T l.
+static __device__ __forceinline__ void ext_jvp(const DevParams& P, double x, double y,
+                                        double z, const double l[3],
+                                        double out[3]) {
+  out[0] = out[1] = out[2] = 0.0;
+  if (P.ext & NBODY_EXT_NFW) {
+    const double r = sqrt(x * x + y * y + z * z);
+    if (r > 0.0) {
+      // J = -G M [ f I + (f'/r) x x^T ]
+      const double f = nfw_f(r, P.nfw_rs);
+      const double g = nfw_fprime_over_r(r, P.nfw_rs);
+      const double xl = x * l[0] + y * l[1] + z * l[2];
+      out[0] -= P.nfw_GM * (f * l[0] + g * xl * x);
+      out[1] -= P.nfw_GM * (f * l[1] + g * xl * y);
+      out[2] -= P.nfw_GM * (f * l[2] + g * xl * z);
+    }
+  }
+  if (P.ext & NBODY_EXT_MN) {
+    // a = -G M q / S^3 with q = (x, y, z (a+B)/B), S^2 = R^2 + (a+B)^2:
+    // J = -G M [ dq/dx / S^3 - 3 q q^T / S^5 ],
+    // dq/dx = diag(1, 1, 1 + a b^2 / B^3)
+    const double b2 = P.mn_b * P.mn_b;
+    const double B = sqrt(z * z + b2);
+    const double aB = P.mn_a + B;
+    const double S2 = x * x + y * y + aB * aB;
+    const double iS = 1.0 / sqrt(S2);
+    const double iS3 = iS * iS * iS;
+    const double iS5 = iS3 * iS * iS;
+    const double q2 = z * aB / B;
+    const double ql = x * l[0] + y * l[1] + q2 * l[2];
+    const double dz = 1.0 + P.mn_a * b2 / (B * B * B);
+    out[0] -= P.mn_GM * (l[0] * iS3 - 3.0 * x * ql * iS5);
+    out[1] -= P.mn_GM * (l[1] * iS3 - 3.0 * y * ql * iS5);
+    out[2] -= P.mn_GM * (dz * l[2] * iS3 - 3.0 * q2 * ql * iS5);
+  }
+}
+
+static __device__ __forceinline__ double ext_potential(const DevParams& P, double x,
+                                                double y, double z) {
+  double phi = 0.0;
+  if (P.ext & NBODY_EXT_NFW) {
+    const double r = sqrt(x * x + y * y + z * z);
+    phi -= P.nfw_GM * (r > 0.0 ? log1p(r / P.nfw_rs) / r : 1.0 / P.nfw_rs);
+  }
+  if (P.ext & NBODY_EXT_MN) {
+    const double B = sqrt(z * z + P.mn_b * P.mn_b);
+    const double aB = P.mn_a + B;
+    phi -= P.mn_GM / sqrt(x * x + y * y + aB * aB);
+  }
+  return phi;
+}
+
+
+}  // namespace nb

@@ -80,6 +80,7 @@ struct nbody_ctx {
   double* vbar = nullptr;
   double* blk = nullptr;  // [nblk][6]
   double* red = nullptr;  // [8]
+  double* lsc = nullptr;  // cotangent scales [kLscDoubles]
   int nblk = 0;
   int* status = nullptr;
 
@@ -404,6 +405,7 @@ void free_all(nbody_ctx* c) {
   dfree(c->vbar);
   dfree(c->blk);
   dfree(c->red);
+  dfree(c->lsc);
   dfree(c->status);
 }
 
@@ -475,7 +477,7 @@ int nbody_create(nbody_ctx** out, int64_t n, const nbody_params* p,
       (rc = dalloc(&c->pot, (size_t)c->fcfg.S * np)) ||
       (rc = dalloc(&c->guide, 6)) || (rc = dalloc(&c->fixed_center, 3)) ||
       (rc = dalloc(&c->xbar, 3 * np)) || (rc = dalloc(&c->vbar, 3 * np)) ||
-      (rc = dalloc(&c->blk, (size_t)c->nblk * 6)) || (rc = dalloc(&c->red, 8)) ||
+      (rc = dalloc(&c->blk, (size_t)c->nblk * 6)) || (rc = dalloc(&c->red, 8)) || (rc = dalloc(&c->lsc, nb::kLscDoubles)) ||
       (rc = dalloc(&c->status, 1))) {
     free_all(c);
     delete c;
@@ -576,8 +578,10 @@ int nbody_vjp(nbody_ctx* c, const double* xbar, const double* vbar,
 
   Tape T{c, 3 * np};
   const int64_t n = c->tape_steps, K = c->K, nseg = c->nseg;
+  CK(cudaMemsetAsync(c->lsc, 0, nb::kLscDoubles * sizeof(double), s));
+  CK(nb::launch_lam_absmax(c->vbar, c->n, c->npad, c->lsc, (int)(n & 1), s));
   CK(nb::launch_stage_vjp(T.cpx(nseg), c->m, c->vbar, center_at(c, n), c->n,
-                          c->npad, c->vst, s));
+                          c->npad, c->vst, c->lsc, (int)(n & 1), s));
   nb::AdjointArgs a{};
   a.P = c->dp;
   a.n = c->n;
@@ -589,6 +593,7 @@ int nbody_vjp(nbody_ctx* c, const double* xbar, const double* vbar,
   a.m = c->m;
   a.vst = c->vst;
   a.blk = c->blk;
+  a.lsc = c->lsc;
   a.status = c->status;
   for (int64_t sg = nseg - 1; sg >= 0; --sg) {
     const int64_t k0 = sg * K;
@@ -609,6 +614,8 @@ int nbody_vjp(nbody_ctx* c, const double* xbar, const double* vbar,
       a.vh_prev = T.svh(j);
       a.x_prev = T.sx(j - 1);
       a.c_prev = center_at(c, k - 1);
+      a.slot = (int)(k & 1);
+      CK(cudaMemsetAsync(c->lsc + 2 + (1 - a.slot), 0, sizeof(double), s));
       CK(timed(c, NBODY_KCLASS_ADJOINT, [&] { return nb::launch_adjoint(a, s); }));
     }
   }
@@ -623,6 +630,7 @@ int nbody_vjp(nbody_ctx* c, const double* xbar, const double* vbar,
   a.vh_prev = nullptr;
   a.x_prev = nullptr;
   a.c_prev = nullptr;
+  a.slot = 0;
   CK(timed(c, NBODY_KCLASS_ADJOINT, [&] { return nb::launch_adjoint(a, s); }));
   c->last_seg_valid = false;  // the segment buffer now holds segment 0
 

@@ -98,9 +98,25 @@ struct UpdateArgs {
 };
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
 
+// FP32 cotangent scaling of the reverse sweep: the cotangents staged for the
+// pair VJP are multiplied by an exact power of two s = 2^-e chosen from the
+// largest |lambda| of the previous point, so their FP32 copies never
+// overflow or underflow while the FP64 cotangents grow or shrink (chaotic
+// systems grow them exponentially).  lsc[0..1] holds the scale of the
+// cotangents staged for points of even / odd index, lsc[2..3] (as unsigned
+// 64-bit patterns of non-negative doubles) their running maxima.
+constexpr int kLscDoubles = 4;
+
+// lsc[2 + (p & 1)] = max |lam| over particles (atomic max of bit patterns)
+cudaError_t launch_lam_absmax(const double* lam, int64_t n, int64_t npad,
+                              double* lsc, int slot, cudaStream_t s);
+
+// stages (x - c, m, s lam) with s derived from lsc[2 + slot]; writes s to
+// lsc[slot]
 cudaError_t launch_stage_vjp(const double* x, const double* m,
                              const double* lam, const double* c, int64_t n,
-                             int64_t npad, float4* vst, cudaStream_t s);
+                             int64_t npad, float4* vst, double* lsc, int slot,
+                             cudaStream_t s);
 
 struct AdjointArgs {
   const DevParams* P;
@@ -119,6 +135,8 @@ struct AdjointArgs {
   const double* m;
   float4* vst;           // restaged positions + new cotangent
   double* blk;           // [nblocks][4] accumulators
+  double* lsc;           // cotangent scales (see kLscDoubles)
+  int slot;              // parity of this point's index
   int* status;
 };
 cudaError_t launch_adjoint(const AdjointArgs& a, cudaStream_t s);

@@ -1,0 +1,574 @@
+// stream.cu -- the mock-stream pipeline of the paper's inference (Fig. 2,
+// Sec. 2.2.1) and its discrete adjoint (Sec. 2), on the GPU:
+//
+//   backward orbit of the progenitor centre (1 particle, NFW + MN)  k_orbit
+//   Plummer scale-and-shift to the recovered phase-space point      k_ic
+//   n-body forward run (pair forces + potential, KDK)               nbody_integrate
+//   projection to (phi1, phi2), soft 2-D histogram, squared error   k_head_weights,
+//                                                                   k_hist, k_loss
+// and in reverse: k_head_vjp -> nbody_vjp -> k_ic_vjp -> k_orbit_vjp ->
+// k_theta_bar.  All arithmetic is FP64 (the n-body pair sums are the FP32
+// kernels behind nbody_integrate / nbody_vjp); every reduction has a fixed
+// order.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "block_reduce.cuh"
+#include "ext_potential.cuh"
+#include "nbody_internal.cuh"
+
+namespace {
+
+using nb::DevParams;
+using nb::ExtUnit;
+
+constexpr int kMaxBins = 64;
+
+struct HeadGeom {
+  double obs[3], e1[3], e2[3], nv[3];
+  double lo1, h1, lo2, h2;  // bin edges lo + b h
+  int nb1, nb2;
+};
+
+__device__ __forceinline__ double dot3(const double* a, const double* b) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+// ------------------------------------------------------------------ orbit
+// single particle, external potential only: v += dt/2 a; x += dt v;
+// v += dt/2 a.  Stores x_0..x_n and the half-step velocities.
+__global__ void k_orbit(DevParams P, double X0, double X1, double X2,
+                        double V0, double V1, double V2, int64_t ns,
+                        double* __restrict__ ox, double* __restrict__ ovh,
+                        double* __restrict__ g6) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double x[3] = {X0, X1, X2}, v[3] = {V0, V1, V2};
+  ExtUnit e;
+  nb::ext_unit(P, x[0], x[1], x[2], e);
+  for (int d = 0; d < 3; ++d) ox[d] = x[d];
+  for (int64_t k = 0; k < ns; ++k) {
+    for (int d = 0; d < 3; ++d) {
+      v[d] += 0.5 * P.dt * (P.nfw_GM * e.n[d] + P.mn_GM * e.d[d]);
+      ovh[3 * k + d] = v[d];
+      x[d] += P.dt * v[d];
+      ox[3 * (k + 1) + d] = x[d];
+    }
+    nb::ext_unit(P, x[0], x[1], x[2], e);
+    for (int d = 0; d < 3; ++d)
+      v[d] += 0.5 * P.dt * (P.nfw_GM * e.n[d] + P.mn_GM * e.d[d]);
+  }
+  for (int d = 0; d < 3; ++d) {
+    g6[d] = x[d];
+    g6[3 + d] = v[d];
+  }
+}
+
+// adjoint of one half kick v' = v + (dt/2) a(x) with cotangent vb = vbar'
+__device__ __forceinline__ void orbit_kick_adj(const DevParams& P,
+                                               const double* x,
+                                               const double* vb, double* xb,
+                                               double* acc3) {
+  ExtUnit e;
+  nb::ext_unit(P, x[0], x[1], x[2], e);
+  double jl[3];
+  nb::ext_jvp(P, x[0], x[1], x[2], vb, jl);
+  double ln = 0.0, lm = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    xb[d] += 0.5 * P.dt * jl[d];
+    ln += vb[d] * e.n[d];
+    lm += vb[d] * e.d[d];
+  }
+  acc3[0] += 0.5 * (P.nfw_GM * ln + P.mn_GM * lm);  // d/d dt
+  acc3[1] += 0.5 * P.dt * P.G * ln;                  // d/d M_NFW
+  acc3[2] += 0.5 * P.dt * P.G * lm;                  // d/d M_MN
+}
+
+// reverse of k_orbit from cotangents (Xbar, Vbar) of its final state:
+// out = { dL/d dt_orbit, dL/d M_NFW, dL/d M_MN } (orbit part)
+__global__ void k_orbit_vjp(DevParams P, const double* __restrict__ ox,
+                            const double* __restrict__ ovh, int64_t ns,
+                            const double* __restrict__ cot,
+                            double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double xb[3] = {cot[0], cot[1], cot[2]};
+  double vb[3] = {cot[3], cot[4], cot[5]};
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int64_t k = ns - 1; k >= 0; --k) {
+    orbit_kick_adj(P, &ox[3 * (k + 1)], vb, xb, acc);  // closing kick
+    for (int d = 0; d < 3; ++d) acc[0] += xb[d] * ovh[3 * k + d];
+    for (int d = 0; d < 3; ++d) vb[d] += P.dt * xb[d];   // drift
+    orbit_kick_adj(P, &ox[3 * k], vb, xb, acc);         // opening kick
+  }
+  out[0] = acc[0];
+  out[1] = acc[1];
+  out[2] = acc[2];
+}
+
+// ---------------------------------------------------------- Plummer shift
+__global__ void k_ic(const double* __restrict__ xh, const double* __restrict__ vh,
+                     const double* __restrict__ g6, double a, double vscale,
+                     double mass, int64_t n, double* __restrict__ x0,
+                     double* __restrict__ v0, double* __restrict__ m) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int d = 0; d < 3; ++d) {
+    x0[d * n + i] = a * xh[d * n + i] + g6[d];
+    v0[d * n + i] = vscale * vh[d * n + i] + g6[3 + d];
+  }
+  m[i] = mass;
+}
+
+// sums of x0bar, v0bar and of v0bar . vhat
+__global__ void __launch_bounds__(256)
+    k_ic_vjp(const double* __restrict__ x0b, const double* __restrict__ v0b,
+             const double* __restrict__ vh, int64_t n, double* __restrict__ blk) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double val[7] = {0, 0, 0, 0, 0, 0, 0};
+  if (i < n) {
+    for (int d = 0; d < 3; ++d) {
+      val[d] = x0b[d * n + i];
+      val[3 + d] = v0b[d * n + i];
+      val[6] += v0b[d * n + i] * vh[d * n + i];
+    }
+  }
+  nb::block_accumulate<7>(val, blk);
+}
+
+// ------------------------------------------------------------------- head
+__global__ void k_head_weights(HeadGeom g, const double* __restrict__ x,
+                               int64_t n, double* __restrict__ phi,
+                               double* __restrict__ w) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double d[3];
+  for (int k = 0; k < 3; ++k) d[k] = x[k * n + i] - g.obs[k];
+  const double p1 = dot3(d, g.e1), p2 = dot3(d, g.e2), p3 = dot3(d, g.nv);
+  const double r = sqrt(dot3(d, d));
+  const double f1 = atan2(p2, p1);
+  const double f2 = asin(p3 / r);
+  phi[i] = f1;
+  phi[n + i] = f2;
+  const int nbt = g.nb1 + g.nb2;
+  const double s1 = 0.5 * g.h1, s2 = 0.5 * g.h2;
+  double c_prev = normcdf((g.lo1 - f1) / s1);
+  for (int b = 0; b < g.nb1; ++b) {
+    const double c = normcdf((g.lo1 + (b + 1) * g.h1 - f1) / s1);
+    w[i * nbt + b] = c - c_prev;
+    c_prev = c;
+  }
+  c_prev = normcdf((g.lo2 - f2) / s2);
+  for (int b = 0; b < g.nb2; ++b) {
+    const double c = normcdf((g.lo2 + (b + 1) * g.h2 - f2) / s2);
+    w[i * nbt + g.nb1 + b] = c - c_prev;
+    c_prev = c;
+  }
+}
+
+// rho[b1][b2] = (1/n) sum_i w1[i][b1] w2[i][b2]; one block per b1
+__global__ void __launch_bounds__(256)
+    k_hist(const double* __restrict__ w, int64_t n, int nb1, int nb2,
+           double* __restrict__ rho) {
+  __shared__ double sh[8][32];
+  const int b1 = blockIdx.x;
+  const int nbt = nb1 + nb2;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  for (int c0 = 0; c0 < nb2; c0 += 32) {
+    double acc[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) acc[k] = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += 256) {
+      const double w1 = w[i * nbt + b1];
+      const double* w2 = &w[i * nbt + nb1 + c0];
+#pragma unroll
+      for (int k = 0; k < 32; ++k)
+        if (c0 + k < nb2) acc[k] += w1 * w2[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      double v = acc[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) sh[wp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32 && c0 + (int)threadIdx.x < nb2) {
+      double s = 0.0;
+      for (int q = 0; q < 8; ++q) s += sh[q][threadIdx.x];
+      rho[b1 * nb2 + c0 + threadIdx.x] = s / (double)n;
+    }
+    __syncthreads();
+  }
+}
+
+// L = mean (rho - t)^2 and rbar = dL/drho (one block of 256)
+__global__ void __launch_bounds__(256)
+    k_loss(const double* __restrict__ rho, const double* __restrict__ t, int nb,
+           double* __restrict__ loss, double* __restrict__ rbar) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += 256) {
+    const double d = rho[b] - t[b];
+    s += d * d;
+    rbar[b] = 2.0 * d / (double)nb;
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = 128; k > 0; k >>= 1) {
+    if ((int)threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) loss[0] = sh[0] / (double)nb;
+}
+
+__device__ __forceinline__ double npdf(double z) {
+  return 0.3989422804014327 * exp(-0.5 * z * z);
+}
+
+// per particle: phi-bar from rbar, then x-bar through the projection
+__global__ void __launch_bounds__(256)
+    k_head_vjp(HeadGeom g, const double* __restrict__ x,
+               const double* __restrict__ phi, const double* __restrict__ w,
+               const double* __restrict__ rbar, int64_t n,
+               double* __restrict__ xbar) {
+  __shared__ double sr[kMaxBins * kMaxBins];
+  const int nb1 = g.nb1, nb2 = g.nb2, nbt = nb1 + nb2;
+  for (int k = threadIdx.x; k < nb1 * nb2; k += blockDim.x) sr[k] = rbar[k];
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double f1 = phi[i], f2 = phi[n + i];
+  const double s1 = 0.5 * g.h1, s2 = 0.5 * g.h2;
+  const double* wi = &w[i * nbt];
+  // g1 = (1/n) sum_b1 dw1[b1] sum_b2 rbar[b1][b2] w2[b2],
+  // dw1[b] = -(pdf(z_{b+1}) - pdf(z_b)) / s1
+  double g1 = 0.0;
+  double p_prev = npdf((g.lo1 - f1) / s1);
+  for (int b1 = 0; b1 < nb1; ++b1) {
+    const double p = npdf((g.lo1 + (b1 + 1) * g.h1 - f1) / s1);
+    const double dw = -(p - p_prev) / s1;
+    p_prev = p;
+    double t = 0.0;
+    for (int b2 = 0; b2 < nb2; ++b2) t += sr[b1 * nb2 + b2] * wi[nb1 + b2];
+    g1 += dw * t;
+  }
+  double g2 = 0.0;
+  p_prev = npdf((g.lo2 - f2) / s2);
+  for (int b2 = 0; b2 < nb2; ++b2) {
+    const double p = npdf((g.lo2 + (b2 + 1) * g.h2 - f2) / s2);
+    const double dw = -(p - p_prev) / s2;
+    p_prev = p;
+    double t = 0.0;
+    for (int b1 = 0; b1 < nb1; ++b1) t += sr[b1 * nb2 + b2] * wi[b1];
+    g2 += dw * t;
+  }
+  g1 /= (double)n;
+  g2 /= (double)n;
+  double d[3];
+  for (int k = 0; k < 3; ++k) d[k] = x[k * n + i] - g.obs[k];
+  const double p1 = dot3(d, g.e1), p2 = dot3(d, g.e2), p3 = dot3(d, g.nv);
+  const double q2 = p1 * p1 + p2 * p2;
+  const double r2 = dot3(d, d);
+  const double den = r2 * sqrt(r2 - p3 * p3);
+  for (int k = 0; k < 3; ++k) {
+    const double dphi1 = (p1 * g.e2[k] - p2 * g.e1[k]) / q2;
+    const double dphi2 = (g.nv[k] * r2 - p3 * d[k]) / den;
+    xbar[k * n + i] = g1 * dphi1 + g2 * dphi2;
+  }
+}
+
+__global__ void k_theta_bar(double tb0, double tb1, double tb2, double tb3,
+                            int64_t ns, double G, double a, double M,
+                            const double* __restrict__ red,
+                            const double* __restrict__ orb,
+                            double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  // t_end: dt = t/n in the n-body run, dt_b = -t/n in the orbit
+  out[0] = tb0 / (double)ns - orb[0] / (double)ns;
+  // M_Plummer: v = sqrt(G M / a) vhat + V and m_j = M / n
+  out[1] = 0.5 * sqrt(G / (a * M)) * red[6] + tb1 / M;
+  out[2] = tb2 + orb[1];
+  out[3] = tb3 + orb[2];
+}
+
+unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+struct nbody_stream {
+  nbody_stream_cfg cfg{};
+  cudaStream_t s = nullptr;
+  int64_t n = 0, nb = 0;
+  nbody_ctx* ctx = nullptr;
+  HeadGeom geom{};
+  double *xhat = nullptr, *vhat = nullptr;
+  double *x0 = nullptr, *v0 = nullptr, *m = nullptr, *xT = nullptr;
+  double *ox = nullptr, *ovh = nullptr, *g6 = nullptr;
+  double *phi = nullptr, *w = nullptr;
+  double *rho = nullptr, *target = nullptr, *rbar = nullptr, *loss = nullptr;
+  double *xbar = nullptr, *x0bar = nullptr, *v0bar = nullptr;
+  double *blk = nullptr, *red = nullptr, *orb = nullptr, *tbar = nullptr;
+  int nblk = 0;
+  double theta[4] = {0, 0, 0, 0};
+  bool have_forward = false;
+};
+
+namespace {
+
+#define SCK(call)                              \
+  do {                                         \
+    cudaError_t e_ = (call);                   \
+    if (e_ != cudaSuccess) return NBODY_ECUDA; \
+  } while (0)
+
+template <class T>
+int salloc(T** p, size_t count) {
+  if (cudaMalloc((void**)p, (count ? count : 1) * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return NBODY_ENOMEM;
+  }
+  return NBODY_OK;
+}
+
+template <class T>
+void sfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+void free_stream(nbody_stream* s) {
+  if (s->ctx) nbody_destroy(s->ctx);
+  s->ctx = nullptr;
+  sfree(s->xhat); sfree(s->vhat); sfree(s->x0); sfree(s->v0); sfree(s->m);
+  sfree(s->xT); sfree(s->ox); sfree(s->ovh); sfree(s->g6); sfree(s->phi);
+  sfree(s->w); sfree(s->rho); sfree(s->target); sfree(s->rbar); sfree(s->loss);
+  sfree(s->xbar); sfree(s->x0bar); sfree(s->v0bar); sfree(s->blk); sfree(s->red);
+  sfree(s->orb); sfree(s->tbar);
+}
+
+void unit3(const double* a, double* out) {
+  const double r = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+  for (int k = 0; k < 3; ++k) out[k] = a[k] / r;
+}
+
+void cross3(const double* a, const double* b, double* c) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+DevParams orbit_params(const nbody_stream* s) {
+  DevParams P{};
+  P.G = s->cfg.G;
+  P.dt = -s->theta[0] / (double)s->cfg.n_steps;
+  P.ext = NBODY_EXT_NFW | NBODY_EXT_MN;
+  P.nfw_GM = s->cfg.G * s->theta[2];
+  P.nfw_rs = s->cfg.nfw_rs;
+  P.mn_GM = s->cfg.G * s->theta[3];
+  P.mn_a = s->cfg.mn_a;
+  P.mn_b = s->cfg.mn_b;
+  return P;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nbody_stream_create(nbody_stream** out, const nbody_stream_cfg* cfg,
+                        const double* xhat, const double* vhat,
+                        void* cuda_stream) {
+  if (!out || !cfg || !xhat || !vhat) return NBODY_EINVAL;
+  *out = nullptr;
+  const nbody_stream_cfg& c = *cfg;
+  if (c.n < 1 || c.n_steps < 1 || c.checkpoint_every < 1 || !(c.eps > 0.0) ||
+      !(c.a_prog > 0.0) || !(c.nfw_rs > 0.0) || c.mn_a < 0.0 || c.mn_b < 0.0 ||
+      c.nb1 < 1 || c.nb2 < 1 || c.nb1 > kMaxBins || c.nb2 > kMaxBins ||
+      !(c.phi1_hi > c.phi1_lo) || !(c.phi2_hi > c.phi2_lo))
+    return NBODY_EINVAL;
+  double d[3] = {c.X0[0] - c.observer[0], c.X0[1] - c.observer[1],
+                 c.X0[2] - c.observer[2]};
+  double pole[3];
+  cross3(d, c.V0, pole);
+  if (!(pole[0] * pole[0] + pole[1] * pole[1] + pole[2] * pole[2] > 0.0))
+    return NBODY_EINVAL;
+  nbody_stream* s = new (std::nothrow) nbody_stream();
+  if (!s) return NBODY_ENOMEM;
+  s->cfg = c;
+  s->s = (cudaStream_t)cuda_stream;
+  s->n = c.n;
+  s->nb = (int64_t)c.nb1 * c.nb2;
+  HeadGeom& g = s->geom;
+  for (int k = 0; k < 3; ++k) g.obs[k] = c.observer[k];
+  unit3(d, g.e1);
+  unit3(pole, g.nv);
+  cross3(g.nv, g.e1, g.e2);
+  g.lo1 = c.phi1_lo;
+  g.h1 = (c.phi1_hi - c.phi1_lo) / c.nb1;
+  g.lo2 = c.phi2_lo;
+  g.h2 = (c.phi2_hi - c.phi2_lo) / c.nb2;
+  g.nb1 = c.nb1;
+  g.nb2 = c.nb2;
+
+  nbody_params p{};
+  p.G = c.G;
+  p.eps = c.eps;
+  p.dt = 1.0;
+  p.checkpoint_every = c.checkpoint_every;
+  p.ext_flags = NBODY_EXT_NFW | NBODY_EXT_MN;
+  p.center_mode = NBODY_CENTER_GUIDE;
+  p.nfw_M = 0.0;
+  p.nfw_rs = c.nfw_rs;
+  p.mn_a = c.mn_a;
+  p.mn_b = c.mn_b;
+  int rc = nbody_create(&s->ctx, c.n, &p, cuda_stream);
+  const size_t n3 = (size_t)3 * c.n;
+  const size_t ns = (size_t)c.n_steps;
+  s->nblk = (int)blocks_for(c.n, 256);
+  if (rc || (rc = salloc(&s->xhat, n3)) || (rc = salloc(&s->vhat, n3)) ||
+      (rc = salloc(&s->x0, n3)) || (rc = salloc(&s->v0, n3)) ||
+      (rc = salloc(&s->m, (size_t)c.n)) || (rc = salloc(&s->xT, n3)) ||
+      (rc = salloc(&s->ox, 3 * (ns + 1))) || (rc = salloc(&s->ovh, 3 * ns)) ||
+      (rc = salloc(&s->g6, 6)) || (rc = salloc(&s->phi, 2 * (size_t)c.n)) ||
+      (rc = salloc(&s->w, (size_t)c.n * (c.nb1 + c.nb2))) ||
+      (rc = salloc(&s->rho, (size_t)s->nb)) || (rc = salloc(&s->target, (size_t)s->nb)) ||
+      (rc = salloc(&s->rbar, (size_t)s->nb)) || (rc = salloc(&s->loss, 1)) ||
+      (rc = salloc(&s->xbar, n3)) || (rc = salloc(&s->x0bar, n3)) ||
+      (rc = salloc(&s->v0bar, n3)) || (rc = salloc(&s->blk, (size_t)s->nblk * 7)) ||
+      (rc = salloc(&s->red, 8)) || (rc = salloc(&s->orb, 3)) ||
+      (rc = salloc(&s->tbar, 4))) {
+    free_stream(s);
+    delete s;
+    return rc ? rc : NBODY_ENOMEM;
+  }
+  if (cudaMemcpyAsync(s->xhat, xhat, n3 * sizeof(double), cudaMemcpyDefault, s->s) ||
+      cudaMemcpyAsync(s->vhat, vhat, n3 * sizeof(double), cudaMemcpyDefault, s->s) ||
+      cudaMemsetAsync(s->target, 0, (size_t)s->nb * sizeof(double), s->s) ||
+      cudaStreamSynchronize(s->s)) {
+    free_stream(s);
+    delete s;
+    return NBODY_ECUDA;
+  }
+  *out = s;
+  return NBODY_OK;
+}
+
+void nbody_stream_destroy(nbody_stream* s) {
+  if (!s) return;
+  cudaStreamSynchronize(s->s);
+  free_stream(s);
+  delete s;
+}
+
+int nbody_stream_set_target(nbody_stream* s, const double* target) {
+  if (!s || !target) return NBODY_EINVAL;
+  SCK(cudaMemcpyAsync(s->target, target, (size_t)s->nb * sizeof(double),
+                      cudaMemcpyDefault, s->s));
+  SCK(cudaStreamSynchronize(s->s));
+  return NBODY_OK;
+}
+
+int nbody_stream_forward(nbody_stream* s, const double theta[4], double* loss,
+                         double* density) {
+  if (!s || !theta) return NBODY_EINVAL;
+  for (int k = 0; k < 4; ++k)
+    if (!(theta[k] > 0.0) || !std::isfinite(theta[k])) return NBODY_EINVAL;
+  s->have_forward = false;
+  for (int k = 0; k < 4; ++k) s->theta[k] = theta[k];
+  const nbody_stream_cfg& c = s->cfg;
+  const int64_t n = s->n, ns = c.n_steps;
+  // 1. backward orbit of the centre of mass
+  const DevParams P = orbit_params(s);
+  k_orbit<<<1, 32, 0, s->s>>>(P, c.X0[0], c.X0[1], c.X0[2], c.V0[0], c.V0[1],
+                              c.V0[2], ns, s->ox, s->ovh, s->g6);
+  nb::count_launch();
+  SCK(cudaGetLastError());
+  // 2. Plummer sphere at the recovered point
+  k_ic<<<blocks_for(n, 256), 256, 0, s->s>>>(
+      s->xhat, s->vhat, s->g6, c.a_prog, std::sqrt(c.G * theta[1] / c.a_prog),
+      theta[1] / (double)n, n, s->x0, s->v0, s->m);
+  nb::count_launch();
+  SCK(cudaGetLastError());
+  double g6[6];
+  SCK(cudaMemcpyAsync(g6, s->g6, sizeof(g6), cudaMemcpyDeviceToHost, s->s));
+  SCK(cudaStreamSynchronize(s->s));
+  // 3. forward n-body run; the FP32 recentring origin follows the orbit
+  nbody_params p{};
+  p.G = c.G;
+  p.eps = c.eps;
+  p.dt = theta[0] / (double)ns;
+  p.checkpoint_every = c.checkpoint_every;
+  p.ext_flags = NBODY_EXT_NFW | NBODY_EXT_MN;
+  p.center_mode = NBODY_CENTER_GUIDE;
+  p.tape_mode = NBODY_TAPE_KEEP_LAST;
+  p.nfw_M = theta[2];
+  p.nfw_rs = c.nfw_rs;
+  p.mn_M = theta[3];
+  p.mn_a = c.mn_a;
+  p.mn_b = c.mn_b;
+  for (int k = 0; k < 3; ++k) {
+    p.center[k] = g6[k];
+    p.center_vel[k] = g6[3 + k];
+  }
+  int rc = nbody_set_params(s->ctx, &p);
+  if (!rc) rc = nbody_set_state(s->ctx, s->x0, s->v0, s->m);
+  if (!rc) rc = nbody_integrate(s->ctx, ns, s->xT, nullptr);
+  if (rc) return rc;
+  // 4-5. head
+  k_head_weights<<<blocks_for(n, 128), 128, 0, s->s>>>(s->geom, s->xT, n, s->phi, s->w);
+  nb::count_launch();
+  SCK(cudaGetLastError());
+  k_hist<<<c.nb1, 256, 0, s->s>>>(s->w, n, c.nb1, c.nb2, s->rho);
+  nb::count_launch();
+  SCK(cudaGetLastError());
+  k_loss<<<1, 256, 0, s->s>>>(s->rho, s->target, (int)s->nb, s->loss, s->rbar);
+  nb::count_launch();
+  SCK(cudaGetLastError());
+  if (density)
+    SCK(cudaMemcpyAsync(density, s->rho, (size_t)s->nb * sizeof(double),
+                        cudaMemcpyDefault, s->s));
+  double L = 0.0;
+  SCK(cudaMemcpyAsync(&L, s->loss, sizeof(double), cudaMemcpyDeviceToHost, s->s));
+  SCK(cudaStreamSynchronize(s->s));
+  if (!std::isfinite(L)) return NBODY_ENAN;
+  if (loss) *loss = L;
+  s->have_forward = true;
+  return NBODY_OK;
+}
+
+int nbody_stream_grad(nbody_stream* s, double theta_bar[4]) {
+  if (!s || !theta_bar) return NBODY_EINVAL;
+  if (!s->have_forward) return NBODY_ESTATE;
+  const nbody_stream_cfg& c = s->cfg;
+  const int64_t n = s->n, ns = c.n_steps;
+  k_head_vjp<<<blocks_for(n, 128), 128, 0, s->s>>>(s->geom, s->xT, s->phi, s->w,
+                                                   s->rbar, n, s->xbar);
+  nb::count_launch();
+  SCK(cudaGetLastError());
+  double tb[4];
+  int rc = nbody_vjp(s->ctx, s->xbar, nullptr, s->x0bar, s->v0bar, nullptr, tb);
+  if (rc) return rc;
+  SCK(cudaMemsetAsync(s->blk, 0, (size_t)s->nblk * 7 * sizeof(double), s->s));
+  k_ic_vjp<<<s->nblk, 256, 0, s->s>>>(s->x0bar, s->v0bar, s->vhat, n, s->blk);
+  nb::count_launch();
+  SCK(cudaGetLastError());
+  SCK(nb::launch_reduce_rows(s->blk, s->nblk, 7, s->red, s->s));
+  const DevParams P = orbit_params(s);
+  k_orbit_vjp<<<1, 32, 0, s->s>>>(P, s->ox, s->ovh, ns, s->red, s->orb);
+  nb::count_launch();
+  SCK(cudaGetLastError());
+  k_theta_bar<<<1, 32, 0, s->s>>>(tb[0], tb[1], tb[2], tb[3], ns, c.G, c.a_prog,
+                                  s->theta[1], s->red, s->orb, s->tbar);
+  nb::count_launch();
+  SCK(cudaGetLastError());
+  SCK(cudaMemcpyAsync(theta_bar, s->tbar, 4 * sizeof(double),
+                      cudaMemcpyDeviceToHost, s->s));
+  SCK(cudaStreamSynchronize(s->s));
+  for (int k = 0; k < 4; ++k)
+    if (!std::isfinite(theta_bar[k])) return NBODY_ENAN;
+  return NBODY_OK;
+}
+
+}  // extern "C"

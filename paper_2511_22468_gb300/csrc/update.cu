@@ -18,121 +18,13 @@
 // State is FP64 throughout; one thread per particle.
 #include <cmath>
 
+#include "block_reduce.cuh"
+#include "ext_potential.cuh"
 #include "nbody_internal.cuh"
 
 namespace nb {
 
 namespace {
-
-// ---------------------------------------------------------------- potential
-// Unit-mass (G M = 1) accelerations of the halo and the disk.
-struct ExtUnit {
-  double n[3];
-  double d[3];
-};
-
-__device__ __forceinline__ double nfw_f(double r, double rs) {
-  // a_NFW = -G M f(r) x, f(r) = ln(1 + r/r_s)/r^3 - 1/(r^2 (r + r_s));
-  // below r = 1e-4 r_s the two terms cancel and the Taylor series is used.
-  const double u = r / rs;
-  if (u < 1e-4) {
-    const double rs2 = rs * rs, rs3 = rs2 * rs;
-    return (0.5 / rs2) / r - (2.0 / 3.0) / rs3 + (0.75 / (rs3 * rs)) * r -
-           (0.8 / (rs3 * rs2)) * r * r;
-  }
-  return (log1p(u) / r - 1.0 / (r + rs)) / (r * r);
-}
-
-__device__ __forceinline__ double nfw_fprime_over_r(double r, double rs) {
-  // f'(r)/r with f' = 1/(r^3 (r+r_s)) - 3 ln(1+r/r_s)/r^4
-  //                   + (3 r + 2 r_s)/(r^3 (r+r_s)^2)
-  const double u = r / rs;
-  if (u < 1e-4) {
-    const double rs2 = rs * rs, rs4 = rs2 * rs2;
-    return (-0.5 / rs2) / (r * r * r) + (0.75 / rs4) / r - 1.6 / (rs4 * rs);
-  }
-  const double rp = r + rs;
-  const double r3 = r * r * r;
-  return (1.0 / (r3 * rp) - 3.0 * log1p(u) / (r3 * r) +
-          (3.0 * r + 2.0 * rs) / (r3 * rp * rp)) / r;
-}
-
-__device__ __forceinline__ void ext_unit(const DevParams& P, double x,
-                                         double y, double z, ExtUnit& e) {
-  e.n[0] = e.n[1] = e.n[2] = 0.0;
-  e.d[0] = e.d[1] = e.d[2] = 0.0;
-  if (P.ext & NBODY_EXT_NFW) {
-    const double r = sqrt(x * x + y * y + z * z);
-    if (r > 0.0) {
-      const double f = nfw_f(r, P.nfw_rs);
-      e.n[0] = -f * x;
-      e.n[1] = -f * y;
-      e.n[2] = -f * z;
-    }
-  }
-  if (P.ext & NBODY_EXT_MN) {
-    const double B = sqrt(z * z + P.mn_b * P.mn_b);
-    const double aB = P.mn_a + B;
-    const double S2 = x * x + y * y + aB * aB;
-    const double iS3 = 1.0 / (S2 * sqrt(S2));
-    e.d[0] = -x * iS3;
-    e.d[1] = -y * iS3;
-    e.d[2] = -z * aB / B * iS3;
-  }
-}
-
-// (d a_ext / d x) l, full accelerations (G M included); the Jacobian is
-// symmetric so this is also J^T l.
-__device__ __forceinline__ void ext_jvp(const DevParams& P, double x, double y,
-                                        double z, const double l[3],
-                                        double out[3]) {
-  out[0] = out[1] = out[2] = 0.0;
-  if (P.ext & NBODY_EXT_NFW) {
-    const double r = sqrt(x * x + y * y + z * z);
-    if (r > 0.0) {
-      // J = -G M [ f I + (f'/r) x x^T ]
-      const double f = nfw_f(r, P.nfw_rs);
-      const double g = nfw_fprime_over_r(r, P.nfw_rs);
-      const double xl = x * l[0] + y * l[1] + z * l[2];
-      out[0] -= P.nfw_GM * (f * l[0] + g * xl * x);
-      out[1] -= P.nfw_GM * (f * l[1] + g * xl * y);
-      out[2] -= P.nfw_GM * (f * l[2] + g * xl * z);
-    }
-  }
-  if (P.ext & NBODY_EXT_MN) {
-    // a = -G M q / S^3 with q = (x, y, z (a+B)/B), S^2 = R^2 + (a+B)^2:
-    // J = -G M [ dq/dx / S^3 - 3 q q^T / S^5 ],
-    // dq/dx = diag(1, 1, 1 + a b^2 / B^3)
-    const double b2 = P.mn_b * P.mn_b;
-    const double B = sqrt(z * z + b2);
-    const double aB = P.mn_a + B;
-    const double S2 = x * x + y * y + aB * aB;
-    const double iS = 1.0 / sqrt(S2);
-    const double iS3 = iS * iS * iS;
-    const double iS5 = iS3 * iS * iS;
-    const double q2 = z * aB / B;
-    const double ql = x * l[0] + y * l[1] + q2 * l[2];
-    const double dz = 1.0 + P.mn_a * b2 / (B * B * B);
-    out[0] -= P.mn_GM * (l[0] * iS3 - 3.0 * x * ql * iS5);
-    out[1] -= P.mn_GM * (l[1] * iS3 - 3.0 * y * ql * iS5);
-    out[2] -= P.mn_GM * (dz * l[2] * iS3 - 3.0 * q2 * ql * iS5);
-  }
-}
-
-__device__ __forceinline__ double ext_potential(const DevParams& P, double x,
-                                                double y, double z) {
-  double phi = 0.0;
-  if (P.ext & NBODY_EXT_NFW) {
-    const double r = sqrt(x * x + y * y + z * z);
-    phi -= P.nfw_GM * (r > 0.0 ? log1p(r / P.nfw_rs) / r : 1.0 / P.nfw_rs);
-  }
-  if (P.ext & NBODY_EXT_MN) {
-    const double B = sqrt(z * z + P.mn_b * P.mn_b);
-    const double aB = P.mn_a + B;
-    phi -= P.mn_GM / sqrt(x * x + y * y + aB * aB);
-  }
-  return phi;
-}
 
 // ------------------------------------------------------------------ staging
 __device__ __forceinline__ void put_stage(float4* st, int64_t i, float x,
@@ -179,17 +71,54 @@ __global__ void k_stage(const double* __restrict__ x,
     put_stage(st, i, 0.f, 0.f, 0.f, 0.f);
 }
 
+// power-of-two scale 2^-e bringing the largest |lambda| (bit pattern) near 1
+__device__ __forceinline__ double lam_scale_from(unsigned long long bits) {
+  const double mx = __longlong_as_double((long long)bits);
+  if (!(mx > 0.0) || !isfinite(mx)) return 1.0;
+  return ldexp(1.0, -ilogb(mx));
+}
+
+__device__ __forceinline__ void block_absmax(double v, unsigned long long* out) {
+  __shared__ double sh[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) mx = fmax(mx, sh[k]);
+    if (mx > 0.0 && isfinite(mx))
+      atomicMax(out, (unsigned long long)__double_as_longlong(mx));
+  }
+}
+
+__global__ void __launch_bounds__(256)
+    k_lam_absmax(const double* __restrict__ lam, int64_t n, int64_t npad,
+                 double* __restrict__ lsc, int slot) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double v = 0.0;
+  if (i < n)
+    v = fmax(fabs(lam[i]), fmax(fabs(lam[npad + i]), fabs(lam[2 * npad + i])));
+  block_absmax(v, reinterpret_cast<unsigned long long*>(lsc + 2) + slot);
+}
+
 __global__ void k_stage_vjp(const double* __restrict__ x,
                             const double* __restrict__ m,
                             const double* __restrict__ lam,
                             const double* __restrict__ c, int64_t n,
-                            int64_t npad, float4* __restrict__ vst) {
+                            int64_t npad, float4* __restrict__ vst,
+                            double* __restrict__ lsc, int slot) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const double sc =
+      lam_scale_from(reinterpret_cast<const unsigned long long*>(lsc + 2)[slot]);
+  if (i == 0) lsc[slot] = sc;
   if (i >= npad) return;
   if (i < n)
     put_vstage(vst, i, (float)(x[i] - c[0]), (float)(x[npad + i] - c[1]),
-               (float)(x[2 * npad + i] - c[2]), (float)m[i], (float)lam[i],
-               (float)lam[npad + i], (float)lam[2 * npad + i]);
+               (float)(x[2 * npad + i] - c[2]), (float)m[i],
+               (float)(sc * lam[i]), (float)(sc * lam[npad + i]),
+               (float)(sc * lam[2 * npad + i]));
   else
     put_vstage(vst, i, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
 }
@@ -254,38 +183,19 @@ __global__ void __launch_bounds__(256) k_update(UpdateArgs a) {
   if (bad) atomicOr(a.status, kStatusNaN);
 }
 
-// deterministic block sum of NV doubles; thread 0 adds the block total to
-// out[blockIdx.x * NV + q]
-template <int NV>
-__device__ __forceinline__ void block_accumulate(double (&val)[NV],
-                                                 double* out) {
-  __shared__ double sh[NV][32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int q = 0; q < NV; ++q) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-      val[q] += __shfl_down_sync(0xffffffffu, val[q], o);
-    if (lane == 0) sh[q][w] = val[q];
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const int nw = blockDim.x >> 5;
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      double s = 0.0;
-      for (int k = 0; k < nw; ++k) s += sh[q][k];
-      out[(int64_t)blockIdx.x * NV + q] += s;
-    }
-  }
-}
-
 // ------------------------------------------------------------------ adjoint
 __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const DevParams& P = *a.P;
   const int64_t np = a.npad;
   double contrib[4] = {0.0, 0.0, 0.0, 0.0};
+  // scale of the cotangents this point's VJP was computed with, and the one
+  // for the cotangents staged now (from the largest |lambda| at this point)
+  const double s_here = a.lsc[a.slot];
+  const unsigned long long* maxbits =
+      reinterpret_cast<const unsigned long long*>(a.lsc + 2);
+  const double s_next = a.drift ? lam_scale_from(maxbits[a.slot]) : 1.0;
+  double vmax = 0.0;
   if (i < a.n) {
     double lam[3], x[3], ap[3], g[3];
 #pragma unroll
@@ -295,7 +205,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
       ap[d] = a.ak[d * np + i];
       double s = 0.0;
       for (int q = 0; q < a.S; ++q) s += a.gpart[((int64_t)q * 3 + d) * np + i];
-      g[d] = -P.G * s;
+      g[d] = -P.G * (s / s_here);
     }
     ExtUnit e;
     ext_unit(P, x[0], x[1], x[2], e);
@@ -324,12 +234,14 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
         xv += xb[d] * a.vh_prev[d * np + i];
         vb[d] += P.dt * xb[d];
         a.vbar[d * np + i] = vb[d];
+        vmax = fmax(vmax, fabs(vb[d]));
       }
       contrib[0] += xv;              // dL/d dt from the drift
       put_vstage(a.vst, i, (float)(a.x_prev[i] - a.c_prev[0]),
                  (float)(a.x_prev[np + i] - a.c_prev[1]),
                  (float)(a.x_prev[2 * np + i] - a.c_prev[2]), (float)a.m[i],
-                 (float)vb[0], (float)vb[1], (float)vb[2]);
+                 (float)(s_next * vb[0]), (float)(s_next * vb[1]),
+                 (float)(s_next * vb[2]));
     }
     bool bad = false;
 #pragma unroll
@@ -340,6 +252,10 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
     if (bad) atomicOr(a.status, kStatusNaN);
   }
   block_accumulate<4>(contrib, a.blk);
+  if (a.drift) {
+    if (i == 0) a.lsc[1 - a.slot] = s_next;
+    block_absmax(vmax, reinterpret_cast<unsigned long long*>(a.lsc + 2) + (1 - a.slot));
+  }
 }
 
 // ------------------------------------------------------------ reductions etc
@@ -445,10 +361,19 @@ cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_lam_absmax(const double* lam, int64_t n, int64_t npad,
+                              double* lsc, int slot, cudaStream_t s) {
+  k_lam_absmax<<<blocks_for(n, 256), 256, 0, s>>>(lam, n, npad, lsc, slot);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_stage_vjp(const double* x, const double* m,
                              const double* lam, const double* c, int64_t n,
-                             int64_t npad, float4* vst, cudaStream_t s) {
-  k_stage_vjp<<<blocks_for(npad, 256), 256, 0, s>>>(x, m, lam, c, n, npad, vst);
+                             int64_t npad, float4* vst, double* lsc, int slot,
+                             cudaStream_t s) {
+  k_stage_vjp<<<blocks_for(npad, 256), 256, 0, s>>>(x, m, lam, c, n, npad, vst,
+                                                    lsc, slot);
   count_launch();
   return cudaGetLastError();
 }

@@ -38,7 +38,9 @@ EXPORTED = ("nbody_create", "nbody_destroy", "nbody_set_params",
             "nbody_integrate", "nbody_vjp", "nbody_energy", "nbody_momentum",
             "nbody_get_status", "nbody_strerror", "nbody_launch_count",
             "nbody_pair_accel", "nbody_set_timing", "nbody_kernel_times",
-            "nbody_pair_accel_noalloc")
+            "nbody_pair_accel_noalloc", "nbody_stream_create",
+            "nbody_stream_set_target", "nbody_stream_forward", "nbody_stream_grad",
+            "nbody_stream_destroy")
 
 NBODY_KCLASS = ("pair", "vjp", "update", "adjoint")
 
@@ -51,6 +53,17 @@ class nbody_params(C.Structure):
                 ("nfw_rs", C.c_double), ("mn_M", C.c_double),
                 ("mn_a", C.c_double), ("mn_b", C.c_double),
                 ("center", C.c_double * 3), ("center_vel", C.c_double * 3)]
+
+
+class nbody_stream_cfg(C.Structure):
+    _fields_ = [("n", C.c_int64), ("n_steps", C.c_int64),
+                ("checkpoint_every", C.c_int64), ("G", C.c_double),
+                ("eps", C.c_double), ("a_prog", C.c_double), ("nfw_rs", C.c_double),
+                ("mn_a", C.c_double), ("mn_b", C.c_double),
+                ("X0", C.c_double * 3), ("V0", C.c_double * 3),
+                ("observer", C.c_double * 3), ("nb1", C.c_int32), ("nb2", C.c_int32),
+                ("phi1_lo", C.c_double), ("phi1_hi", C.c_double),
+                ("phi2_lo", C.c_double), ("phi2_hi", C.c_double)]
 
 
 def make_params(G, eps, dt, checkpoint_every=0, ext_flags=0, nfw_M=0.0,
@@ -106,6 +119,13 @@ def lib():
                                        dp, vp, vp]
         L.nbody_pair_accel_noalloc.argtypes = [i64, vp, vp, C.c_double,
                                                C.c_double, dp, vp, vp]
+        SC = C.POINTER(nbody_stream_cfg)
+        L.nbody_stream_create.argtypes = [C.POINTER(vp), SC, vp, vp, vp]
+        L.nbody_stream_set_target.argtypes = [vp, vp]
+        L.nbody_stream_forward.argtypes = [vp, dp, dp, vp]
+        L.nbody_stream_grad.argtypes = [vp, dp]
+        L.nbody_stream_destroy.argtypes = [vp]
+        L.nbody_stream_destroy.restype = None
         L.nbody_set_timing.argtypes = [vp, C.c_int]
         L.nbody_kernel_times.argtypes = [vp, dp, C.POINTER(i64)]
         _lib = L
@@ -245,6 +265,38 @@ def nbody_kernel_times(h):
     cnt = (C.c_int64 * 4)()
     _check(lib().nbody_kernel_times(h, ms, cnt), "nbody_kernel_times")
     return {k: (ms[i], cnt[i]) for i, k in enumerate(NBODY_KCLASS)}
+
+
+def nbody_stream_create(cfg: nbody_stream_cfg, xhat, vhat, stream=None):
+    h = C.c_void_p()
+    n = cfg.n
+    _check(lib().nbody_stream_create(C.byref(h), C.byref(cfg), _ptr(xhat, (3, n)),
+                                     _ptr(vhat, (3, n)), _stream(stream)),
+           "nbody_stream_create")
+    return h
+
+
+def nbody_stream_set_target(h, target):
+    _check(lib().nbody_stream_set_target(h, _ptr(target)), "nbody_stream_set_target")
+
+
+def nbody_stream_forward(h, theta, density=None):
+    """Loss at theta = (t_end, M_Plummer, M_NFW, M_MN); fills density if given."""
+    th = (C.c_double * 4)(*[float(t) for t in theta])
+    loss = C.c_double()
+    _check(lib().nbody_stream_forward(h, th, C.byref(loss), _ptr(density)),
+           "nbody_stream_forward")
+    return loss.value
+
+
+def nbody_stream_grad(h):
+    tb = (C.c_double * 4)()
+    _check(lib().nbody_stream_grad(h, tb), "nbody_stream_grad")
+    return list(tb)
+
+
+def nbody_stream_destroy(h):
+    lib().nbody_stream_destroy(h)
 
 
 class Simulation:

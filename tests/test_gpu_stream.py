@@ -1,0 +1,98 @@
+"""The mock-stream pipeline on the GPU (backward orbit, Plummer shift,
+n-body run, sky projection, soft histogram, loss) and its adjoint against
+the FP64 oracle (needs a GB300).
+
+Tolerances: density element-wise 1e-8 absolute (densities are O(1e-3));
+loss 1e-4 relative; each dL/dTheta component 1e-4 relative of the oracle
+adjoint and of the oracle's central differences (Richardson).  dL/dt_end is
+the difference of two parts, through the forward run's dt and through the
+backward orbit's -dt, which cancel to first order (the centre of mass comes
+back to X0); its error is bounded by 1e-4 of the sum of the parts' sizes.
+"""
+
+
+def assert_grad_close(g, g_ref, parts):
+    scale = np.abs(np.asarray(g_ref, float))
+    scale[0] = abs(parts[0]) + abs(parts[1])
+    assert np.all(np.abs(np.asarray(g) - g_ref) <= 1e-4 * scale), (g, g_ref, parts)
+import dataclasses
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import stream as ostream  # noqa: E402
+from paper_2511_22468_gb300.configs import C1  # noqa: E402
+from paper_2511_22468_gb300.inputs import plummer_unit  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_22468_gb300 import build, nbody
+    build.build()
+    nbody.lib()
+
+
+def _case(n=384, t_acc=30.0, n_steps=60):
+    cfg = dataclasses.replace(C1, n=n, t_acc=t_acc, n_steps=n_steps)
+    xh, vh = plummer_unit(n, 1)
+    return cfg, xh, vh
+
+
+@pytest.mark.parametrize("K", [8, 60])
+def test_stream_loss_and_gradient_match_oracle(K):
+    from paper_2511_22468_gb300.stream import StreamModel
+    cfg, xh, vh = _case()
+    orc = ostream.StreamModel(cfg, xh, vh)
+    truth = np.array(cfg.theta_true, float)
+    target = orc.density(truth)
+    th = truth * np.array([1.05, 0.9, 1.1, 0.95])
+    L_ref, g_ref = orc.loss_and_grad(th, target)
+
+    gpu = StreamModel(cfg, xh, vh, checkpoint_every=K)
+    gpu.set_target(target)
+    rho = gpu.density(th).cpu().numpy()
+    np.testing.assert_allclose(rho, orc.density(th), rtol=0, atol=1e-8)
+    L, g = gpu.loss_and_grad(th)
+    assert L == pytest.approx(L_ref, rel=1e-4)
+    assert_grad_close(g, g_ref, orc.t_end_parts)
+
+    # against the oracle's central differences (Richardson-extrapolated)
+    for k in range(4):
+        h = 1e-4 * th[k]
+        def f(s):
+            t = th.copy()
+            t[k] += s
+            return orc.loss(t, target)
+        d1 = (f(h) - f(-h)) / (2 * h)
+        d2 = (f(h / 2) - f(-h / 2)) / h
+        fd = (4 * d2 - d1) / 3
+        tol = 1e-4 * (abs(fd) if k else sum(abs(p) for p in orc.t_end_parts))
+        assert abs(g[k] - fd) <= tol, (k, g[k], fd)
+    gpu.close()
+
+
+def test_stream_autograd_function():
+    from paper_2511_22468_gb300.stream import StreamLoss, StreamModel
+    cfg, xh, vh = _case(n=256, t_acc=20.0, n_steps=40)
+    orc = ostream.StreamModel(cfg, xh, vh)
+    truth = np.array(cfg.theta_true, float)
+    gpu = StreamModel(cfg, xh, vh, checkpoint_every=7)
+    gpu.set_target(orc.density(truth))
+    theta = torch.tensor(truth * np.array([0.95, 1.1, 0.9, 1.05]), dtype=torch.float64,
+                         requires_grad=True)
+    L = StreamLoss.apply(theta, gpu)
+    L.backward()
+    L_ref, g_ref = orc.loss_and_grad(theta.detach().numpy(), orc.density(truth))
+    assert L.item() == pytest.approx(L_ref, rel=1e-4)
+    assert_grad_close(theta.grad.numpy(), g_ref, orc.t_end_parts)
+    # at the truth the loss and its gradient vanish up to the FP32 pair
+    # sums' rounding (the target is the oracle's density)
+    assert gpu.loss(truth) <= 1e-6 * L_ref
+    assert np.all(np.abs(gpu.grad()) <= 1e-3 * np.abs(g_ref))
+    gpu.close()
