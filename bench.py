@@ -52,6 +52,7 @@ def parse_args():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
     return ap.parse_args()
 
 
@@ -196,6 +197,105 @@ def run_reference(args):
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+# -------------------------------------------------------------- ensemble --
+def ensemble_members():
+    """The 64-simulation ensemble: N log-uniform in [2048, 32768], the four
+    stream parameters uniform within +-30 % of the stream workload's, each a
+    Plummer progenitor (a = 10 pc, eps = 1 pc) at the present-day point,
+    dt = t_end / 6000."""
+    from paper_2511_22468_gb300.configs import C1, C2
+    from paper_2511_22468_gb300.inputs import (log_uniform_sizes, plummer_sphere,
+                                               uniform_factors)
+    sizes = log_uniform_sizes(C2.n_sims, C2.n_lo, C2.n_hi, C2.seed_sizes)
+    fac = uniform_factors(C2.n_sims, C2.width, 4, C2.seed_params)
+    truth = np.array(C1.theta_true)
+    out = []
+    for s in range(C2.n_sims):
+        th = truth * fac[s]
+        x, v, m = plummer_sphere(int(sizes[s]), C2.seed_ics + s, C1.G, th[1], C1.a_prog,
+                                 center=C1.X0, velocity=C1.V0)
+        out.append((x, v, m, th))
+    return out
+
+
+def measure_ensemble(dev, gpu_name, plain_subset=8, plain_steps=200):
+    import torch
+    from paper_2511_22468_gb300 import autotune, nbody as nb
+    from paper_2511_22468_gb300.configs import C1, C2
+    mem = ensemble_members()
+    pot = C1.pot
+
+    def prm(th):
+        return nb.make_params(C1.G, C1.eps, th[0] / C2.steps_per_t_acc, ext_flags=3,
+                              nfw_M=th[2], nfw_rs=pot.nfw_rs, mn_M=th[3], mn_a=pot.mn_a,
+                              mn_b=pot.mn_b, center=C1.X0, center_vel=C1.V0,
+                              center_mode=nb.NBODY_CENTER_GUIDE)
+    sizes = [x.shape[0] for x, _, _, _ in mem]
+    offs = np.cumsum([0] + sizes)
+    X = torch.tensor(np.concatenate([a[0] for a in mem]).T.copy(), device=dev)
+    V = torch.tensor(np.concatenate([a[1] for a in mem]).T.copy(), device=dev)
+    M = torch.tensor(np.concatenate([a[2] for a in mem]), device=dev)
+    stream = torch.cuda.current_stream(dev)
+    h = nb.nbody_create_batch(offs, [prm(a[3]) for a in mem], stream)
+    nb.nbody_set_state(h, X, V, M)
+    choice, src, ms = autotune.tune(h, sizes, gpu_name, probe_steps=2)
+    steps = C2.n_steps
+    nb.nbody_integrate(h, steps)            # captures the graph, warm-up
+    nb.nbody_set_state(h, X, V, M)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    nb.nbody_integrate(h, steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t = e0.elapsed_time(e1) / 1e3
+    ok = nb.nbody_get_status(h) == 0
+    nb.nbody_destroy(h)
+    inter = float(np.sum(np.asarray(sizes, float) ** 2)) * steps
+
+    # the same members, a subset, one simulation per launch sequence vs batched
+    idx = np.argsort(sizes)[:: max(1, len(sizes) // plain_subset)][:plain_subset]
+    sub = [mem[k] for k in idx]
+    t_plain = 0.0
+    for x, v, m, th in sub:
+        sim = nb.Simulation(x.shape[0], prm(th), stream)
+        sim.set_state(torch.tensor(x.T.copy(), device=dev), torch.tensor(v.T.copy(), device=dev),
+                      torch.tensor(m, device=dev))
+        sim.step(5)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        sim.step(plain_steps)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        t_plain += e0.elapsed_time(e1) / 1e3
+        sim.close()
+    so = np.cumsum([0] + [a[0].shape[0] for a in sub])
+    hb = nb.nbody_create_batch(so, [prm(a[3]) for a in sub], stream)
+    nb.nbody_set_state(hb, torch.tensor(np.concatenate([a[0] for a in sub]).T.copy(), device=dev),
+                       torch.tensor(np.concatenate([a[1] for a in sub]).T.copy(), device=dev),
+                       torch.tensor(np.concatenate([a[2] for a in sub]), device=dev))
+    nb.nbody_set_tuning(hb, choice)
+    nb.nbody_integrate(hb, plain_steps)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    nb.nbody_integrate(hb, plain_steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_batch_sub = e0.elapsed_time(e1) / 1e3
+    nb.nbody_destroy(hb)
+    return {"workload": C2.name, "n_sims": len(sizes), "steps": steps,
+            "sizes_min_max": [int(min(sizes)), int(max(sizes))],
+            "seconds_per_run": t, "sims_per_s": len(sizes) / t,
+            "interactions_per_s": inter / t, "status_ok": ok,
+            "tuning": {"choice": choice, "source": src, "ms_per_candidate": ms},
+            "plain_vs_batched_subset": {
+                "sims": plain_subset, "steps": plain_steps,
+                "sizes": [int(mem[k][0].shape[0]) for k in idx],
+                "plain_s": t_plain, "batched_s": t_batch_sub,
+                "speedup": t_plain / t_batch_sub}}
 
 
 # ------------------------------------------------------------------- ours --
@@ -344,6 +444,10 @@ def run_ours(args):
            "d2h_bytes_per_step": int((3 + 3) * n * 8 + 4 * 8),
            "steps": e2e_steps, "ms_per_step": e2e_s * 1e3}
 
+    ens = None
+    if not args.no_ensemble:
+        ens = measure_ensemble(dev, props.name)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ra, rv = 8192, 1024
@@ -366,7 +470,8 @@ def run_ours(args):
                 "fwd_ms_per_step": fwd_ms / args.steps,
                 "pct_fp32_peak": {k: 100.0 * kernels[k]["frac_of_peak_at_2070MHz"]
                                   for k in ("pair", "vjp") if k in kernels},
-                "batched_sims_per_s": None,
+                "batched_sims_per_s": ens["sims_per_s"] * world if ens else None,
+                "ensemble": ens,
                 "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu,
                 "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
                 "parallelism": "replicas" if world > 1 else "single"}

@@ -172,6 +172,44 @@ NBODY_API const char *nbody_strerror(int code);
  * (all contexts); a monotonically increasing counter for accounting. */
 NBODY_API int64_t nbody_launch_count(void);
 
+/* ---- batched ensemble ---- */
+
+/* Create a context holding n_sims >= 1 independent simulations of uneven
+ * size: simulation s owns particles offsets[s] .. offsets[s+1]-1 (host
+ * array of n_sims + 1 increasing values, offsets[0] = 0) and has its own
+ * parameters p[s] (G, eps, dt, potential, centre; checkpoint_every and
+ * tape_mode must be 0: a batch records no tape).  Every step runs one
+ * persistent pair-force launch over all simulations (a work list of
+ * (simulation, i-tile, j-chunk) items, largest first, taken through an
+ * atomic counter) and one batched update; nbody_integrate replays the whole
+ * step loop as one CUDA graph, captured on its first call for a given
+ * step count.  On a batch context, nbody_set_params takes an array of
+ * n_sims parameter sets; nbody_set_state / nbody_get_state use arrays laid
+ * out 3 x offsets[n_sims] (simulations concatenated); nbody_vjp,
+ * nbody_energy, nbody_momentum and the timing calls return EINVAL.
+ * Errors: EINVAL, ENODEV, ENOMEM, ECUDA. */
+NBODY_API int nbody_create_batch(nbody_ctx **out, int n_sims,
+                                 const int64_t *offsets, const nbody_params *p,
+                                 void *cuda_stream);
+
+/* Launch-shape candidates of the batched pair kernel (threads per block,
+ * i-particles per thread, j-chunk length). */
+#define NBODY_NTUNE 8
+
+/* Time every candidate on the batch's current positions (probe_steps pair
+ * launches each; the state is not advanced), select the fastest and return
+ * its index in *best (may be NULL); ms (host, NBODY_NTUNE entries, may be
+ * NULL) receives the time per launch of each.  Batch contexts only.
+ * Synchronises.  Errors: EINVAL, ENOMEM, ECUDA. */
+NBODY_API int nbody_autotune(nbody_ctx *c, int64_t probe_steps, int *best,
+                             double ms[NBODY_NTUNE]);
+
+/* Select candidate `choice` (0 .. NBODY_NTUNE-1), e.g. from a cached
+ * autotuning result; nbody_get_tuning returns the current one (or a
+ * negative code).  Batch contexts only.  Errors: EINVAL, ECUDA. */
+NBODY_API int nbody_set_tuning(nbody_ctx *c, int choice);
+NBODY_API int nbody_get_tuning(nbody_ctx *c);
+
 /* ---- per-kernel timing (CUDA events on the context stream) ---- */
 #define NBODY_KCLASS_PAIR 0    /* pair-force kernel (forward and recompute)   */
 #define NBODY_KCLASS_VJP 1     /* pair VJP kernel                             */

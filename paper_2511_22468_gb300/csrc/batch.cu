@@ -1,0 +1,660 @@
+// batch.cu -- many simulations of uneven N, each with its own parameters,
+// advanced together: one persistent pair-force launch per step over a work
+// list of (simulation, i-tile, j-chunk) items, one batched update launch,
+// the whole step loop captured once as a CUDA graph and replayed.  The
+// physics per simulation is the same as the single-system path (softened
+// pair sum, paper Sec. 1; NFW + MN potential and kick-drift-kick, Sec.
+// 2.2.1).
+//
+// Work list: items are sorted by cost, largest first (LPT), and handed out
+// through an atomic counter, so the persistent blocks stay busy to the end
+// of the step; every item writes its own FP64 partial slice and the update
+// kernel sums the slices in a fixed order, so the result does not depend on
+// which block took which item.
+//
+// Autotuning: the launch shape (threads per block, i-particles per thread,
+// j-chunk length) is chosen among kNTune candidates by timing the pair
+// kernel on the batch itself (nbody_autotune).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "ext_potential.cuh"
+#include "nbody_internal.cuh"
+#include "pair_body.cuh"
+#include "staging.cuh"
+
+namespace nb {
+
+namespace {
+
+constexpr int kTJ = 128;  // j-pairs per shared-memory tile (256 particles)
+
+struct TuneCfg {
+  int nt, r, jchunk;
+};
+constexpr TuneCfg kTune[NBODY_NTUNE] = {
+    {128, 4, 4096}, {128, 4, 2048}, {128, 4, 8192}, {256, 2, 4096},
+    {256, 2, 2048}, {128, 8, 4096}, {128, 8, 8192}, {256, 4, 4096}};
+
+struct SimMeta {
+  int64_t npad, poff, part_off;
+  int64_t n;
+  int S, ntiles;
+  float eps2f;
+  int pad;
+};
+
+template <int NT, int R>
+__global__ void __launch_bounds__(NT)
+    k_pair_batch(const float4* __restrict__ st, const SimMeta* __restrict__ meta,
+                 const int4* __restrict__ items, int nitems,
+                 unsigned* __restrict__ ctr, double* __restrict__ part) {
+  __shared__ float4 sj[2 * kTJ];
+  __shared__ int s_item;
+  const int t = threadIdx.x;
+  for (;;) {
+    __syncthreads();
+    if (t == 0) s_item = (int)atomicAdd(ctr, 1u);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= nitems) break;
+    const int4 w = items[it];
+    const SimMeta M = meta[w.x];
+    const int64_t i0 = (int64_t)w.y * (NT * R) + t;  // local index
+    const int tile_b = (int)(((int64_t)w.z * M.ntiles) / M.S);
+    const int tile_e = (int)(((int64_t)(w.z + 1) * M.ntiles) / M.S);
+    const float4* sts = st + M.poff;  // one float4 per particle
+    float2 nx[R], ny[R], nz[R];
+    double dax[R], day[R], daz[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      float xi, yi, zi;
+      load_i(sts, i0 + r * NT, xi, yi, zi);
+      nx[r] = make_float2(-xi, -xi);
+      ny[r] = make_float2(-yi, -yi);
+      nz[r] = make_float2(-zi, -zi);
+      dax[r] = day[r] = daz[r] = 0.0;
+    }
+    const float2 e2 = make_float2(M.eps2f, M.eps2f);
+    for (int tile = tile_b; tile < tile_e; ++tile) {
+      __syncthreads();
+      const float4* src = sts + (int64_t)tile * (2 * kTJ);
+#pragma unroll
+      for (int q = t; q < 2 * kTJ; q += NT) sj[q] = src[q];
+      __syncthreads();
+      float2 ax[R], ay[R], az[R], ph[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) ax[r] = ay[r] = az[r] = ph[r] = make_float2(0.f, 0.f);
+#pragma unroll 2
+      for (int jj = 0; jj < kTJ; ++jj) {
+        const float4 A = sj[2 * jj];
+        const float4 B = sj[2 * jj + 1];
+        const float2 xj = make_float2(A.x, A.y), yj = make_float2(A.z, A.w);
+        const float2 zj = make_float2(B.x, B.y), mj = make_float2(B.z, B.w);
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          body<false>(xj, yj, zj, mj, nx[r], ny[r], nz[r], e2, ax[r], ay[r], az[r], ph[r]);
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        dax[r] += (double)ax[r].x + (double)ax[r].y;
+        day[r] += (double)ay[r].x + (double)ay[r].y;
+        daz[r] += (double)az[r].x + (double)az[r].y;
+      }
+    }
+    double* p = part + M.part_off + (int64_t)w.z * 3 * M.npad;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int64_t i = i0 + r * NT;
+      p[i] = dax[r];
+      p[M.npad + i] = day[r];
+      p[2 * M.npad + i] = daz[r];
+    }
+  }
+}
+
+// one thread per simulation: FP32 recentring origins of every point
+__global__ void k_guide_batch(const DevParams* __restrict__ P,
+                              const int* __restrict__ mode, double* __restrict__ g,
+                              int n_sims, int64_t n_steps, double* __restrict__ centers,
+                              int64_t cstride) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_sims) return;
+  const DevParams Q = P[s];
+  double* c = centers + (int64_t)s * cstride;
+  double x[3] = {g[6 * s], g[6 * s + 1], g[6 * s + 2]};
+  double v[3] = {g[6 * s + 3], g[6 * s + 4], g[6 * s + 5]};
+  for (int d = 0; d < 3; ++d) c[d] = x[d];
+  if (!mode[s]) {
+    for (int64_t k = 1; k <= n_steps; ++k)
+      for (int d = 0; d < 3; ++d) c[3 * k + d] = x[d];
+    return;
+  }
+  ExtUnit e;
+  ext_unit(Q, x[0], x[1], x[2], e);
+  for (int64_t k = 0; k < n_steps; ++k) {
+    for (int d = 0; d < 3; ++d) {
+      v[d] += 0.5 * Q.dt * (Q.nfw_GM * e.n[d] + Q.mn_GM * e.d[d]);
+      x[d] += Q.dt * v[d];
+    }
+    ext_unit(Q, x[0], x[1], x[2], e);
+    for (int d = 0; d < 3; ++d) {
+      v[d] += 0.5 * Q.dt * (Q.nfw_GM * e.n[d] + Q.mn_GM * e.d[d]);
+      c[3 * (k + 1) + d] = x[d];
+    }
+  }
+  for (int d = 0; d < 3; ++d) {
+    g[6 * s + d] = x[d];
+    g[6 * s + 3 + d] = v[d];
+  }
+}
+
+__global__ void __launch_bounds__(256)
+    k_stage_batch(const SimMeta* __restrict__ meta, const int* __restrict__ blk_sim,
+                  const double* __restrict__ x, const double* __restrict__ m,
+                  int64_t ptot, const double* __restrict__ centers, int64_t cstride,
+                  float4* __restrict__ st) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = blk_sim[blockIdx.x];
+  const SimMeta M = meta[s];
+  const int64_t i = g - M.poff;
+  if (i < M.n) {
+    const double* c = centers + (int64_t)s * cstride;
+    put_stage(st, g, (float)(x[g] - c[0]), (float)(x[ptot + g] - c[1]),
+              (float)(x[2 * ptot + g] - c[2]), (float)m[g]);
+  } else {
+    put_stage(st, g, 0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+__global__ void __launch_bounds__(256)
+    k_update_batch(const DevParams* __restrict__ P, const SimMeta* __restrict__ meta,
+                   const int* __restrict__ blk_sim, double* __restrict__ x,
+                   double* __restrict__ v, const double* __restrict__ part,
+                   int64_t ptot, double kick, int drift,
+                   const double* __restrict__ centers, int64_t cstride,
+                   int64_t k_next, float4* __restrict__ st, int* __restrict__ status,
+                   unsigned* __restrict__ ctr) {
+  // the pair launch of this step has finished: re-arm its work counter
+  if (blockIdx.x == 0 && threadIdx.x == 0) *ctr = 0u;
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = blk_sim[blockIdx.x];
+  const SimMeta M = meta[s];
+  const int64_t i = g - M.poff;
+  if (i >= M.n) return;
+  const DevParams Q = P[s];
+  double ap[3];
+  for (int d = 0; d < 3; ++d) {
+    double acc = 0.0;
+    for (int q = 0; q < M.S; ++q)
+      acc += part[M.part_off + ((int64_t)q * 3 + d) * M.npad + i];
+    ap[d] = Q.G * acc;
+  }
+  double xx[3], vv[3];
+  for (int d = 0; d < 3; ++d) {
+    xx[d] = x[d * ptot + g];
+    vv[d] = v[d * ptot + g];
+  }
+  ExtUnit e;
+  ext_unit(Q, xx[0], xx[1], xx[2], e);
+  bool bad = false;
+  for (int d = 0; d < 3; ++d) {
+    vv[d] += kick * Q.dt * (ap[d] + Q.nfw_GM * e.n[d] + Q.mn_GM * e.d[d]);
+    if (drift) xx[d] += Q.dt * vv[d];
+    x[d * ptot + g] = xx[d];
+    v[d * ptot + g] = vv[d];
+    bad |= !isfinite(xx[d]) || !isfinite(vv[d]);
+  }
+  if (drift) {
+    const double* c = centers + (int64_t)s * cstride + 3 * k_next;
+    put_stage_xyz(st, g, (float)(xx[0] - c[0]), (float)(xx[1] - c[1]),
+                  (float)(xx[2] - c[2]));
+  }
+  if (bad) atomicOr(status, kStatusNaN);
+}
+
+#define BCK(call)                              \
+  do {                                         \
+    cudaError_t e_ = (call);                   \
+    if (e_ != cudaSuccess) return NBODY_ECUDA; \
+  } while (0)
+
+}  // namespace
+
+struct Batch {
+  int n_sims = 0;
+  int sm_count = 0;
+  int64_t ntot = 0, ptot = 0;
+  cudaStream_t user = nullptr, gs = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::vector<int64_t> n, npad, off, poff;
+  std::vector<nbody_params> prm;
+  DevParams* dp = nullptr;
+  int* mode = nullptr;      // guide (1) or fixed (0) origin per simulation
+  double* guide = nullptr;  // [n_sims][6]
+  double *x = nullptr, *v = nullptr, *m = nullptr;
+  float4* st = nullptr;
+  double* part = nullptr;
+  size_t part_cap = 0;
+  SimMeta* meta = nullptr;
+  int* blk_sim = nullptr;
+  int4* items = nullptr;
+  size_t items_cap = 0;
+  int nitems = 0;
+  unsigned* ctr = nullptr;
+  int* status = nullptr;
+  double* centers = nullptr;
+  int64_t centers_cap = -1;
+  int tune = 0;
+  int grid_pair = 0;
+  cudaGraphExec_t exec = nullptr;
+  int64_t exec_steps = -1;
+  int exec_tune = -1;
+  int graph_nodes = 0;
+};
+
+namespace {
+
+template <class T>
+int balloc(T** p, size_t count) {
+  if (cudaMalloc((void**)p, (count ? count : 1) * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return NBODY_ENOMEM;
+  }
+  return NBODY_OK;
+}
+
+template <class T>
+void bfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+DevParams dev_params(const nbody_params& p) {
+  DevParams d{};
+  d.G = p.G;
+  d.eps2 = p.eps * p.eps;
+  d.dt = p.dt;
+  d.ext = p.ext_flags;
+  d.nfw_GM = (p.ext_flags & NBODY_EXT_NFW) ? p.G * p.nfw_M : 0.0;
+  d.nfw_rs = (p.ext_flags & NBODY_EXT_NFW) ? p.nfw_rs : 1.0;
+  d.mn_GM = (p.ext_flags & NBODY_EXT_MN) ? p.G * p.mn_M : 0.0;
+  d.mn_a = p.mn_a;
+  d.mn_b = p.mn_b;
+  d.eps2f = (float)(p.eps * p.eps);
+  return d;
+}
+
+// metadata, partial-slice layout and LPT work list for tuning candidate k
+int build_plan(Batch* b, int k) {
+  const TuneCfg c = kTune[k];
+  const int per_block = c.nt * c.r;
+  std::vector<SimMeta> meta(b->n_sims);
+  struct Item {
+    int64_t cost;
+    int4 w;
+  };
+  std::vector<Item> list;
+  int64_t part_off = 0;
+  for (int s = 0; s < b->n_sims; ++s) {
+    SimMeta M{};
+    M.npad = b->npad[s];
+    M.poff = b->poff[s];
+    M.n = b->n[s];
+    M.ntiles = (int)(M.npad / (2 * kTJ));
+    int S = (int)std::max<int64_t>(1, (M.npad + c.jchunk / 2) / c.jchunk);
+    S = std::min(S, M.ntiles);
+    M.S = S;
+    M.part_off = part_off;
+    M.eps2f = (float)(b->prm[s].eps * b->prm[s].eps);
+    part_off += (int64_t)S * 3 * M.npad;
+    meta[s] = M;
+    const int64_t itiles = M.npad / per_block;
+    for (int64_t it = 0; it < itiles; ++it)
+      for (int q = 0; q < S; ++q) {
+        const int64_t tb = ((int64_t)q * M.ntiles) / S, te = ((int64_t)(q + 1) * M.ntiles) / S;
+        list.push_back({(te - tb) * per_block, make_int4(s, (int)it, q, 0)});
+      }
+  }
+  std::stable_sort(list.begin(), list.end(),
+                   [](const Item& a, const Item& o) { return a.cost > o.cost; });
+  if (((size_t)part_off > b->part_cap || list.size() > b->items_cap) && b->exec) {
+    // a captured run refers to the buffers about to be replaced
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  if ((size_t)part_off > b->part_cap) {
+    bfree(b->part);
+    b->part_cap = 0;
+    int rc = balloc(&b->part, (size_t)part_off);
+    if (rc) return rc;
+    b->part_cap = (size_t)part_off;
+  }
+  if (list.size() > b->items_cap) {
+    bfree(b->items);
+    b->items_cap = 0;
+    int rc = balloc(&b->items, list.size());
+    if (rc) return rc;
+    b->items_cap = list.size();
+  }
+  std::vector<int4> w(list.size());
+  for (size_t i = 0; i < list.size(); ++i) w[i] = list[i].w;
+  BCK(cudaMemcpy(b->items, w.data(), w.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  BCK(cudaMemcpy(b->meta, meta.data(), meta.size() * sizeof(SimMeta),
+                 cudaMemcpyHostToDevice));
+  b->nitems = (int)list.size();
+  int occ = 1;
+  cudaError_t e = cudaSuccess;
+  if (c.nt == 128 && c.r == 4)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair_batch<128, 4>, 128, 0);
+  else if (c.nt == 256 && c.r == 2)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair_batch<256, 2>, 256, 0);
+  else if (c.nt == 128 && c.r == 8)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair_batch<128, 8>, 128, 0);
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair_batch<256, 4>, 256, 0);
+  if (e != cudaSuccess || occ < 1) occ = 1;
+  b->grid_pair = std::min(b->nitems, occ * b->sm_count);
+  b->tune = k;
+  return NBODY_OK;
+}
+
+cudaError_t launch_pair_batch(Batch* b, cudaStream_t s) {
+  const TuneCfg c = kTune[b->tune];
+  const unsigned g = (unsigned)std::max(1, b->grid_pair);
+  if (c.nt == 128 && c.r == 4)
+    k_pair_batch<128, 4><<<g, 128, 0, s>>>(b->st, b->meta, b->items, b->nitems, b->ctr, b->part);
+  else if (c.nt == 256 && c.r == 2)
+    k_pair_batch<256, 2><<<g, 256, 0, s>>>(b->st, b->meta, b->items, b->nitems, b->ctr, b->part);
+  else if (c.nt == 128 && c.r == 8)
+    k_pair_batch<128, 8><<<g, 128, 0, s>>>(b->st, b->meta, b->items, b->nitems, b->ctr, b->part);
+  else
+    k_pair_batch<256, 4><<<g, 256, 0, s>>>(b->st, b->meta, b->items, b->nitems, b->ctr, b->part);
+  return cudaGetLastError();
+}
+
+int ensure_centers(Batch* b, int64_t n_steps) {
+  if (b->centers && b->centers_cap >= n_steps) return NBODY_OK;
+  bfree(b->centers);
+  b->centers_cap = -1;
+  int rc = balloc(&b->centers, (size_t)b->n_sims * 3 * (n_steps + 1));
+  if (rc) return rc;
+  b->centers_cap = n_steps;
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  return NBODY_OK;
+}
+
+// the kernels of one n_steps run, in stream order
+int record_run(Batch* b, int64_t n_steps, cudaStream_t s, int* nodes) {
+  const int64_t cs = 3 * (b->centers_cap + 1);
+  const unsigned nblk = (unsigned)(b->ptot / 256);
+  int cnt = 0;
+  BCK(cudaMemsetAsync(b->ctr, 0, sizeof(unsigned), s));
+  k_guide_batch<<<(b->n_sims + 63) / 64, 64, 0, s>>>(b->dp, b->mode, b->guide, b->n_sims,
+                                                     n_steps, b->centers, cs);
+  BCK(cudaGetLastError());
+  k_stage_batch<<<nblk, 256, 0, s>>>(b->meta, b->blk_sim, b->x, b->m, b->ptot,
+                                     b->centers, cs, b->st);
+  BCK(cudaGetLastError());
+  cnt += 2;
+  for (int64_t k = 0; k <= n_steps; ++k) {
+    BCK(launch_pair_batch(b, s));
+    const double kick = (k == 0 || k == n_steps) ? 0.5 : 1.0;
+    k_update_batch<<<nblk, 256, 0, s>>>(b->dp, b->meta, b->blk_sim, b->x, b->v, b->part,
+                                        b->ptot, kick, k < n_steps ? 1 : 0, b->centers,
+                                        cs, k + 1, b->st, b->status, b->ctr);
+    BCK(cudaGetLastError());
+    cnt += 2;
+  }
+  *nodes = cnt;
+  return NBODY_OK;
+}
+
+int upload(Batch* b) {
+  std::vector<DevParams> d(b->n_sims);
+  std::vector<int> mode(b->n_sims);
+  std::vector<double> g(6 * (size_t)b->n_sims);
+  for (int s = 0; s < b->n_sims; ++s) {
+    d[s] = dev_params(b->prm[s]);
+    mode[s] = b->prm[s].center_mode == NBODY_CENTER_GUIDE ? 1 : 0;
+    for (int k = 0; k < 3; ++k) {
+      g[6 * s + k] = b->prm[s].center[k];
+      g[6 * s + 3 + k] = b->prm[s].center_vel[k];
+    }
+  }
+  BCK(cudaMemcpy(b->dp, d.data(), d.size() * sizeof(DevParams), cudaMemcpyHostToDevice));
+  BCK(cudaMemcpy(b->mode, mode.data(), mode.size() * sizeof(int), cudaMemcpyHostToDevice));
+  BCK(cudaMemcpy(b->guide, g.data(), g.size() * sizeof(double), cudaMemcpyHostToDevice));
+  // eps is part of the work-list metadata
+  return build_plan(b, b->tune);
+}
+
+}  // namespace
+
+int batch_create(Batch** out, int n_sims, const int64_t* offsets,
+                 const nbody_params* p, cudaStream_t user, int sm_count) {
+  Batch* b = new (std::nothrow) Batch();
+  if (!b) return NBODY_ENOMEM;
+  b->n_sims = n_sims;
+  b->sm_count = sm_count;
+  b->user = user;
+  b->prm.assign(p, p + n_sims);
+  b->ntot = offsets[n_sims];
+  int64_t poff = 0;
+  for (int s = 0; s < n_sims; ++s) {
+    const int64_t ns = offsets[s + 1] - offsets[s];
+    b->n.push_back(ns);
+    b->off.push_back(offsets[s]);
+    const int64_t np = ((ns + kPad - 1) / kPad) * kPad;
+    b->npad.push_back(np);
+    b->poff.push_back(poff);
+    poff += np;
+  }
+  b->ptot = poff;
+  const size_t pt = (size_t)b->ptot;
+  std::vector<int> bs(pt / 256);
+  for (int s = 0; s < n_sims; ++s)
+    for (int64_t k = b->poff[s] / 256; k < (b->poff[s] + b->npad[s]) / 256; ++k) bs[k] = s;
+  int rc;
+  if ((rc = balloc(&b->dp, n_sims)) || (rc = balloc(&b->mode, n_sims)) ||
+      (rc = balloc(&b->guide, 6 * (size_t)n_sims)) || (rc = balloc(&b->x, 3 * pt)) ||
+      (rc = balloc(&b->v, 3 * pt)) || (rc = balloc(&b->m, pt)) ||
+      (rc = balloc(&b->st, pt)) || (rc = balloc(&b->meta, n_sims)) ||
+      (rc = balloc(&b->blk_sim, bs.size())) || (rc = balloc(&b->ctr, 1)) ||
+      (rc = balloc(&b->status, 1))) {
+    batch_destroy(b);
+    return rc;
+  }
+  if (cudaStreamCreateWithFlags(&b->gs, cudaStreamNonBlocking) ||
+      cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) ||
+      cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) ||
+      cudaMemset(b->x, 0, 3 * pt * sizeof(double)) ||
+      cudaMemset(b->v, 0, 3 * pt * sizeof(double)) ||
+      cudaMemset(b->m, 0, pt * sizeof(double)) || cudaMemset(b->status, 0, sizeof(int)) ||
+      cudaMemcpy(b->blk_sim, bs.data(), bs.size() * sizeof(int), cudaMemcpyHostToDevice)) {
+    cudaGetLastError();
+    batch_destroy(b);
+    return NBODY_ECUDA;
+  }
+  rc = upload(b);
+  if (rc) {
+    batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return NBODY_OK;
+}
+
+void batch_destroy(Batch* b) {
+  if (!b) return;
+  if (b->gs) cudaStreamSynchronize(b->gs);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->gs) cudaStreamDestroy(b->gs);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  bfree(b->dp); bfree(b->mode); bfree(b->guide); bfree(b->x); bfree(b->v);
+  bfree(b->m); bfree(b->st); bfree(b->part); bfree(b->meta); bfree(b->blk_sim);
+  bfree(b->items); bfree(b->ctr); bfree(b->status); bfree(b->centers);
+  delete b;
+}
+
+int batch_set_params(Batch* b, const nbody_params* p) {
+  BCK(cudaStreamSynchronize(b->user));
+  BCK(cudaStreamSynchronize(b->gs));
+  b->prm.assign(p, p + b->n_sims);
+  return upload(b);
+}
+
+int batch_set_state(Batch* b, const double* x, const double* v, const double* m) {
+  for (int s = 0; s < b->n_sims; ++s) {
+    const size_t bytes = (size_t)b->n[s] * sizeof(double);
+    for (int d = 0; d < 3; ++d) {
+      BCK(cudaMemcpyAsync(b->x + d * b->ptot + b->poff[s], x + d * b->ntot + b->off[s],
+                          bytes, cudaMemcpyDefault, b->user));
+      BCK(cudaMemcpyAsync(b->v + d * b->ptot + b->poff[s], v + d * b->ntot + b->off[s],
+                          bytes, cudaMemcpyDefault, b->user));
+    }
+    BCK(cudaMemcpyAsync(b->m + b->poff[s], m + b->off[s], bytes, cudaMemcpyDefault, b->user));
+  }
+  // restart every guide from its parameters
+  std::vector<double> g(6 * (size_t)b->n_sims);
+  for (int s = 0; s < b->n_sims; ++s)
+    for (int k = 0; k < 3; ++k) {
+      g[6 * s + k] = b->prm[s].center[k];
+      g[6 * s + 3 + k] = b->prm[s].center_vel[k];
+    }
+  BCK(cudaMemcpyAsync(b->guide, g.data(), g.size() * sizeof(double), cudaMemcpyHostToDevice,
+                      b->user));
+  BCK(cudaStreamSynchronize(b->user));
+  return NBODY_OK;
+}
+
+int batch_get_state(Batch* b, double* x, double* v) {
+  for (int s = 0; s < b->n_sims; ++s) {
+    const size_t bytes = (size_t)b->n[s] * sizeof(double);
+    for (int d = 0; d < 3; ++d) {
+      if (x)
+        BCK(cudaMemcpyAsync(x + d * b->ntot + b->off[s], b->x + d * b->ptot + b->poff[s],
+                            bytes, cudaMemcpyDefault, b->user));
+      if (v)
+        BCK(cudaMemcpyAsync(v + d * b->ntot + b->off[s], b->v + d * b->ptot + b->poff[s],
+                            bytes, cudaMemcpyDefault, b->user));
+    }
+  }
+  BCK(cudaStreamSynchronize(b->user));
+  return NBODY_OK;
+}
+
+int batch_integrate(Batch* b, int64_t n_steps) {
+  int rc = ensure_centers(b, n_steps);
+  if (rc) return rc;
+  if (!b->exec || b->exec_steps != n_steps || b->exec_tune != b->tune) {
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    BCK(cudaStreamBeginCapture(b->gs, cudaStreamCaptureModeThreadLocal));
+    int nodes = 0;
+    rc = record_run(b, n_steps, b->gs, &nodes);
+    cudaError_t e = cudaStreamEndCapture(b->gs, &graph);
+    if (rc || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return rc ? rc : NBODY_ECUDA;
+    }
+    e = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      b->exec = nullptr;
+      return NBODY_ECUDA;
+    }
+    b->exec_steps = n_steps;
+    b->exec_tune = b->tune;
+    b->graph_nodes = nodes;
+  }
+  BCK(cudaEventRecord(b->ev_in, b->user));
+  BCK(cudaStreamWaitEvent(b->gs, b->ev_in, 0));
+  BCK(cudaGraphLaunch(b->exec, b->gs));
+  BCK(cudaEventRecord(b->ev_out, b->gs));
+  BCK(cudaStreamWaitEvent(b->user, b->ev_out, 0));
+  count_launch(b->graph_nodes);
+  return NBODY_OK;
+}
+
+int batch_status(Batch* b) {
+  int st = 0;
+  BCK(cudaStreamSynchronize(b->gs));
+  BCK(cudaMemcpy(&st, b->status, sizeof(int), cudaMemcpyDeviceToHost));
+  return (st & kStatusNaN) ? NBODY_ENAN : NBODY_OK;
+}
+
+int batch_set_tuning(Batch* b, int k) {
+  if (k < 0 || k >= NBODY_NTUNE) return NBODY_EINVAL;
+  BCK(cudaStreamSynchronize(b->user));
+  BCK(cudaStreamSynchronize(b->gs));
+  return build_plan(b, k);
+}
+
+int batch_autotune(Batch* b, int64_t probe_steps, int* best, double* ms_out) {
+  if (probe_steps < 1) probe_steps = 1;
+  BCK(cudaStreamSynchronize(b->user));
+  BCK(cudaStreamSynchronize(b->gs));
+  int rc = ensure_centers(b, 0);
+  if (rc) return rc;
+  // stage the current positions once (pair forces only: the state is not
+  // advanced)
+  const int64_t cs = 3 * (b->centers_cap + 1);
+  k_guide_batch<<<(b->n_sims + 63) / 64, 64, 0, b->gs>>>(b->dp, b->mode, b->guide, b->n_sims,
+                                                         0, b->centers, cs);
+  BCK(cudaGetLastError());
+  k_stage_batch<<<(unsigned)(b->ptot / 256), 256, 0, b->gs>>>(b->meta, b->blk_sim, b->x, b->m,
+                                                              b->ptot, b->centers, cs, b->st);
+  BCK(cudaGetLastError());
+  cudaEvent_t e0, e1;
+  BCK(cudaEventCreate(&e0));
+  BCK(cudaEventCreate(&e1));
+  double best_ms = 1e300;
+  int best_k = b->tune;
+  for (int k = 0; k < NBODY_NTUNE; ++k) {
+    rc = build_plan(b, k);
+    if (rc) break;
+    BCK(cudaMemsetAsync(b->ctr, 0, sizeof(unsigned), b->gs));
+    BCK(launch_pair_batch(b, b->gs));  // warm-up
+    BCK(cudaEventRecord(e0, b->gs));
+    for (int64_t q = 0; q < probe_steps; ++q) {
+      BCK(cudaMemsetAsync(b->ctr, 0, sizeof(unsigned), b->gs));
+      BCK(launch_pair_batch(b, b->gs));
+    }
+    BCK(cudaEventRecord(e1, b->gs));
+    BCK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    BCK(cudaEventElapsedTime(&ms, e0, e1));
+    const double per = (double)ms / (double)probe_steps;
+    if (ms_out) ms_out[k] = per;
+    if (per < best_ms) {
+      best_ms = per;
+      best_k = k;
+    }
+  }
+  count_launch(2 + NBODY_NTUNE * (int)(probe_steps + 1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  rc = build_plan(b, best_k);
+  if (rc) return rc;
+  if (best) *best = best_k;
+  return NBODY_OK;
+}
+
+int batch_tuning(Batch* b) { return b->tune; }
+
+}  // namespace nb

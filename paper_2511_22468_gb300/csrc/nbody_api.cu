@@ -84,6 +84,10 @@ struct nbody_ctx {
   int nblk = 0;
   int* status = nullptr;
 
+  // batched ensemble (all other buffers unused when set)
+  nb::Batch* batch = nullptr;
+  int n_sims = 0;
+
   // per-kernel event timing
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[NBODY_NKCLASS];
@@ -503,12 +507,23 @@ int nbody_create(nbody_ctx** out, int64_t n, const nbody_params* p,
 void nbody_destroy(nbody_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  if (c->batch) nb::batch_destroy(c->batch);
+  c->batch = nullptr;
   free_all(c);
   delete c;
 }
 
 int nbody_set_params(nbody_ctx* c, const nbody_params* p) {
   if (!c) return NBODY_EINVAL;
+  if (c->batch) {
+    if (!p) return NBODY_EINVAL;
+    for (int s = 0; s < c->n_sims; ++s) {
+      int rc = check_params(&p[s]);
+      if (rc) return rc;
+      if (p[s].checkpoint_every != 0 || p[s].tape_mode != 0) return NBODY_EINVAL;
+    }
+    return nb::batch_set_params(c->batch, p);
+  }
   int rc = check_params(p);
   if (rc) return rc;
   c->p = *p;
@@ -521,6 +536,7 @@ int nbody_set_params(nbody_ctx* c, const nbody_params* p) {
 int nbody_set_state(nbody_ctx* c, const double* x, const double* v,
                     const double* m) {
   if (!c || !x || !v || !m) return NBODY_EINVAL;
+  if (c->batch) return nb::batch_set_state(c->batch, x, v, m);
   int rc;
   if ((rc = copy_in3(c, c->x, x)) || (rc = copy_in3(c, c->v, v)) ||
       (rc = copy_in(c->m, m, (size_t)c->n, c->stream)))
@@ -539,6 +555,7 @@ int nbody_set_state(nbody_ctx* c, const double* x, const double* v,
 
 int nbody_get_state(nbody_ctx* c, double* x, double* v) {
   if (!c) return NBODY_EINVAL;
+  if (c->batch) return nb::batch_get_state(c->batch, x, v);
   int rc;
   if (x && (rc = copy_out3(c, x, c->x))) return rc;
   if (v && (rc = copy_out3(c, v, c->v))) return rc;
@@ -549,12 +566,19 @@ int nbody_get_state(nbody_ctx* c, double* x, double* v) {
 int nbody_step(nbody_ctx* c, int64_t k) {
   if (!c || k < 0) return NBODY_EINVAL;
   if (k == 0) return NBODY_OK;
+  if (c->batch) return nb::batch_integrate(c->batch, k);
   return run_forward(c, k, false);
 }
 
 int nbody_integrate(nbody_ctx* c, int64_t n_steps, double* x_out,
                     double* v_out) {
   if (!c || n_steps < 1) return NBODY_EINVAL;
+  if (c->batch) {
+    int rc = nb::batch_integrate(c->batch, n_steps);
+    if (rc) return rc;
+    if (x_out || v_out) return nb::batch_get_state(c->batch, x_out, v_out);
+    return NBODY_OK;
+  }
   int rc = run_forward(c, n_steps, c->p.checkpoint_every > 0);
   if (rc) return rc;
   if (x_out || v_out) return nbody_get_state(c, x_out, v_out);
@@ -564,7 +588,7 @@ int nbody_integrate(nbody_ctx* c, int64_t n_steps, double* x_out,
 int nbody_vjp(nbody_ctx* c, const double* xbar, const double* vbar,
               double* x0bar, double* v0bar, double* mbar_or_null,
               double theta_bar[4]) {
-  if (!c || !theta_bar) return NBODY_EINVAL;
+  if (!c || !theta_bar || c->batch) return NBODY_EINVAL;
   if (mbar_or_null) return NBODY_EINVAL;
   if (c->tape_steps < 1) return NBODY_ESTATE;
   cudaStream_t s = c->stream;
@@ -648,7 +672,7 @@ int nbody_vjp(nbody_ctx* c, const double* xbar, const double* vbar,
 }
 
 int nbody_energy(nbody_ctx* c, double out[4]) {
-  if (!c || !out) return NBODY_EINVAL;
+  if (!c || !out || c->batch) return NBODY_EINVAL;
   cudaStream_t s = c->stream;
   const double* cen = (c->p.center_mode == NBODY_CENTER_GUIDE) ? c->guide
                                                                : c->fixed_center;
@@ -671,7 +695,7 @@ int nbody_energy(nbody_ctx* c, double out[4]) {
 }
 
 int nbody_momentum(nbody_ctx* c, double out[3]) {
-  if (!c || !out) return NBODY_EINVAL;
+  if (!c || !out || c->batch) return NBODY_EINVAL;
   double e[4];
   int rc = nbody_energy(c, e);
   if (rc) return rc;
@@ -685,6 +709,7 @@ int nbody_momentum(nbody_ctx* c, double out[3]) {
 
 int nbody_get_status(nbody_ctx* c) {
   if (!c) return NBODY_EINVAL;
+  if (c->batch) return nb::batch_status(c->batch);
   int st = 0;
   CK(cudaStreamSynchronize(c->stream));
   CK(cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost));
@@ -693,8 +718,55 @@ int nbody_get_status(nbody_ctx* c) {
   return NBODY_OK;
 }
 
+int nbody_create_batch(nbody_ctx** out, int n_sims, const int64_t* offsets,
+                       const nbody_params* p, void* cuda_stream) {
+  if (!out) return NBODY_EINVAL;
+  *out = nullptr;
+  if (n_sims < 1 || !offsets || !p || offsets[0] != 0) return NBODY_EINVAL;
+  for (int s = 0; s < n_sims; ++s) {
+    if (offsets[s + 1] <= offsets[s]) return NBODY_EINVAL;
+    int rc = check_params(&p[s]);
+    if (rc) return rc;
+    if (p[s].checkpoint_every != 0 || p[s].tape_mode != 0) return NBODY_EINVAL;
+  }
+  int dev = 0, sms = 0;
+  int rc = check_device(&dev, &sms);
+  if (rc) return rc;
+  nbody_ctx* c = new (std::nothrow) nbody_ctx();
+  if (!c) return NBODY_ENOMEM;
+  c->dev = dev;
+  c->sm_count = sms;
+  c->n = offsets[n_sims];
+  c->n_sims = n_sims;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->p = p[0];
+  rc = nb::batch_create(&c->batch, n_sims, offsets, p, c->stream, sms);
+  if (rc) {
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return NBODY_OK;
+}
+
+int nbody_autotune(nbody_ctx* c, int64_t probe_steps, int* best,
+                   double ms[NBODY_NTUNE]) {
+  if (!c || !c->batch) return NBODY_EINVAL;
+  return nb::batch_autotune(c->batch, probe_steps, best, ms);
+}
+
+int nbody_set_tuning(nbody_ctx* c, int choice) {
+  if (!c || !c->batch) return NBODY_EINVAL;
+  return nb::batch_set_tuning(c->batch, choice);
+}
+
+int nbody_get_tuning(nbody_ctx* c) {
+  if (!c || !c->batch) return NBODY_EINVAL;
+  return nb::batch_tuning(c->batch);
+}
+
 int nbody_set_timing(nbody_ctx* c, int enable) {
-  if (!c) return NBODY_EINVAL;
+  if (!c || c->batch) return NBODY_EINVAL;
   c->timing = enable != 0;
   for (auto& u : c->ev_used) u = 0;
   return NBODY_OK;
@@ -702,7 +774,7 @@ int nbody_set_timing(nbody_ctx* c, int enable) {
 
 int nbody_kernel_times(nbody_ctx* c, double ms[NBODY_NKCLASS],
                        int64_t launches[NBODY_NKCLASS]) {
-  if (!c || !ms) return NBODY_EINVAL;
+  if (!c || !ms || c->batch) return NBODY_EINVAL;
   CK(cudaStreamSynchronize(c->stream));
   for (int k = 0; k < NBODY_NKCLASS; ++k) {
     double t = 0.0;

@@ -158,4 +158,18 @@ cudaError_t launch_reduce_partials(const double* part, int S, int64_t npad,
                                    int64_t n, double G, double* acc,
                                    cudaStream_t s);
 
+// ---- batched ensemble (batch.cu) ----
+struct Batch;
+int batch_create(Batch** out, int n_sims, const int64_t* offsets,
+                 const nbody_params* p, cudaStream_t user, int sm_count);
+void batch_destroy(Batch* b);
+int batch_set_params(Batch* b, const nbody_params* p);
+int batch_set_state(Batch* b, const double* x, const double* v, const double* m);
+int batch_get_state(Batch* b, double* x, double* v);
+int batch_integrate(Batch* b, int64_t n_steps);
+int batch_status(Batch* b);
+int batch_autotune(Batch* b, int64_t probe_steps, int* best, double* ms);
+int batch_set_tuning(Batch* b, int k);
+int batch_tuning(Batch* b);
+
 }  // namespace nb

@@ -19,56 +19,13 @@
 // Warp variant (small N): a warp owns R i-particles and its 32 lanes split
 // the j-range; lane sums are combined by a fixed xor-shuffle butterfly.
 #include "nbody_internal.cuh"
+#include "pair_body.cuh"
 
 namespace nb {
 
 namespace {
 
 constexpr int kTJ = 128;  // j-pairs per shared-memory tile (256 particles)
-
-__device__ __forceinline__ float rsqrt_ftz(float v) {
-  float y;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(v));
-  return y;
-}
-
-__device__ __forceinline__ float2 rsqrt2(float2 v) {
-  return make_float2(rsqrt_ftz(v.x), rsqrt_ftz(v.y));
-}
-
-// one j-pair against one i: accumulates m_j (x_j - x_i) s^-3 into (ax, ay,
-// az) and optionally m_j / s into ph.
-template <bool POT>
-__device__ __forceinline__ void body(float2 xj, float2 yj, float2 zj,
-                                     float2 mj, float2 nx, float2 ny,
-                                     float2 nz, float2 e2, float2& ax,
-                                     float2& ay, float2& az, float2& ph) {
-  const float2 dx = __fadd2_rn(xj, nx);
-  const float2 dy = __fadd2_rn(yj, ny);
-  const float2 dz = __fadd2_rn(zj, nz);
-  float2 s2 = __ffma2_rn(dx, dx, e2);
-  s2 = __ffma2_rn(dy, dy, s2);
-  s2 = __ffma2_rn(dz, dz, s2);
-  const float2 inv = rsqrt2(s2);
-  const float2 inv2 = __fmul2_rn(inv, inv);
-  float2 w = __fmul2_rn(mj, inv);
-  if (POT) ph = __fadd2_rn(ph, w);
-  w = __fmul2_rn(w, inv2);
-  ax = __ffma2_rn(dx, w, ax);
-  ay = __ffma2_rn(dy, w, ay);
-  az = __ffma2_rn(dz, w, az);
-}
-
-__device__ __forceinline__ void load_i(const float4* __restrict__ st,
-                                       int64_t i, float& x, float& y,
-                                       float& z) {
-  const float4 A = st[2 * (i >> 1)];
-  const float4 B = st[2 * (i >> 1) + 1];
-  const bool odd = (i & 1) != 0;
-  x = odd ? A.y : A.x;
-  y = odd ? A.w : A.z;
-  z = odd ? B.y : B.x;
-}
 
 template <int NT, int R, bool POT>
 __global__ void __launch_bounds__(NT)

@@ -21,42 +21,11 @@
 #include "block_reduce.cuh"
 #include "ext_potential.cuh"
 #include "nbody_internal.cuh"
+#include "staging.cuh"
 
 namespace nb {
 
 namespace {
-
-// ------------------------------------------------------------------ staging
-__device__ __forceinline__ void put_stage(float4* st, int64_t i, float x,
-                                          float y, float z, float m) {
-  float* f = reinterpret_cast<float*>(st) + 8 * (i >> 1) + (i & 1);
-  f[0] = x;
-  f[2] = y;
-  f[4] = z;
-  f[6] = m;
-}
-
-__device__ __forceinline__ void put_stage_xyz(float4* st, int64_t i, float x,
-                                              float y, float z) {
-  float* f = reinterpret_cast<float*>(st) + 8 * (i >> 1) + (i & 1);
-  f[0] = x;
-  f[2] = y;
-  f[4] = z;
-}
-
-__device__ __forceinline__ void put_vstage(float4* vst, int64_t i, float x,
-                                           float y, float z, float m, float lx,
-                                           float ly, float lz) {
-  float* f = reinterpret_cast<float*>(vst) + 16 * (i >> 1) + (i & 1);
-  f[0] = x;
-  f[2] = y;
-  f[4] = z;
-  f[6] = m;
-  f[8] = lx;
-  f[10] = ly;
-  f[12] = lz;
-  f[14] = 0.f;
-}
 
 __global__ void k_stage(const double* __restrict__ x,
                         const double* __restrict__ m,

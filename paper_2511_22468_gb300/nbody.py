@@ -40,7 +40,10 @@ EXPORTED = ("nbody_create", "nbody_destroy", "nbody_set_params",
             "nbody_pair_accel", "nbody_set_timing", "nbody_kernel_times",
             "nbody_pair_accel_noalloc", "nbody_stream_create",
             "nbody_stream_set_target", "nbody_stream_forward", "nbody_stream_grad",
-            "nbody_stream_destroy")
+            "nbody_stream_destroy", "nbody_create_batch", "nbody_autotune",
+            "nbody_set_tuning", "nbody_get_tuning")
+
+NBODY_NTUNE = 8
 
 NBODY_KCLASS = ("pair", "vjp", "update", "adjoint")
 
@@ -126,6 +129,10 @@ def lib():
         L.nbody_stream_grad.argtypes = [vp, dp]
         L.nbody_stream_destroy.argtypes = [vp]
         L.nbody_stream_destroy.restype = None
+        L.nbody_create_batch.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(i64), P, vp]
+        L.nbody_autotune.argtypes = [vp, i64, C.POINTER(C.c_int), dp]
+        L.nbody_set_tuning.argtypes = [vp, C.c_int]
+        L.nbody_get_tuning.argtypes = [vp]
         L.nbody_set_timing.argtypes = [vp, C.c_int]
         L.nbody_kernel_times.argtypes = [vp, dp, C.POINTER(i64)]
         _lib = L
@@ -265,6 +272,42 @@ def nbody_kernel_times(h):
     cnt = (C.c_int64 * 4)()
     _check(lib().nbody_kernel_times(h, ms, cnt), "nbody_kernel_times")
     return {k: (ms[i], cnt[i]) for i, k in enumerate(NBODY_KCLASS)}
+
+
+def nbody_create_batch(offsets, params_list, stream=None):
+    """Batch context for len(params_list) simulations; offsets has one more
+    entry (particle ranges of the concatenated state)."""
+    ns = len(params_list)
+    offs = (C.c_int64 * (ns + 1))(*[int(o) for o in offsets])
+    arr = (nbody_params * ns)(*params_list)
+    h = C.c_void_p()
+    _check(lib().nbody_create_batch(C.byref(h), ns, offs, arr, _stream(stream)),
+           "nbody_create_batch")
+    return h
+
+
+def nbody_set_params_batch(h, params_list):
+    arr = (nbody_params * len(params_list))(*params_list)
+    _check(lib().nbody_set_params(h, arr), "nbody_set_params")
+
+
+def nbody_autotune(h, probe_steps=3):
+    """(best candidate, [ms per launch of each candidate])."""
+    best = C.c_int()
+    ms = (C.c_double * NBODY_NTUNE)()
+    _check(lib().nbody_autotune(h, probe_steps, C.byref(best), ms), "nbody_autotune")
+    return best.value, list(ms)
+
+
+def nbody_set_tuning(h, choice):
+    _check(lib().nbody_set_tuning(h, int(choice)), "nbody_set_tuning")
+
+
+def nbody_get_tuning(h):
+    rc = lib().nbody_get_tuning(h)
+    if rc < 0:
+        raise NBodyError(rc, "nbody_get_tuning")
+    return rc
 
 
 def nbody_stream_create(cfg: nbody_stream_cfg, xhat, vhat, stream=None):

@@ -1,0 +1,124 @@
+"""Batched ensemble (uneven N, per-simulation parameters, one persistent
+pair launch per step, graph-captured step loop) against the oracle and the
+single-system path (needs a GB300)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import core as orc  # noqa: E402
+from paper_2511_22468_gb300 import nbody as nb  # noqa: E402
+from paper_2511_22468_gb300.configs import C1  # noqa: E402
+from paper_2511_22468_gb300.inputs import plummer_sphere  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_22468_gb300 import build
+    build.build()
+    nb.lib()
+
+
+def _members():
+    """Three simulations of uneven size: an isolated Plummer sphere in N-body
+    units and two stream progenitors on their orbit with different masses,
+    potentials and steps."""
+    pot = C1.pot
+    sims = []
+    x, v, m = plummer_sphere(300, 31, 1.0, 1.0, 1.0)
+    sims.append((x, v, m, nb.make_params(1.0, 0.02, 2e-3),
+                 orc.Physics(G=1.0, eps=0.02)))
+    for k, (n, f) in enumerate(((1500, 0.8), (2600, 1.25))):
+        x, v, m = plummer_sphere(n, 40 + k, C1.G, C1.M_prog * f, C1.a_prog,
+                                 center=C1.X0, velocity=C1.V0)
+        dt = 0.5 * f
+        p = nb.make_params(C1.G, C1.eps, dt, ext_flags=3, nfw_M=pot.nfw_M * f,
+                           nfw_rs=pot.nfw_rs, mn_M=pot.mn_M / f, mn_a=pot.mn_a,
+                           mn_b=pot.mn_b, center=C1.X0, center_vel=C1.V0,
+                           center_mode=nb.NBODY_CENTER_GUIDE)
+        ph = orc.Physics(G=C1.G, eps=C1.eps, ext=orc.NFW | orc.MN, nfw_M=pot.nfw_M * f,
+                         nfw_rs=pot.nfw_rs, mn_M=pot.mn_M / f, mn_a=pot.mn_a, mn_b=pot.mn_b)
+        sims.append((x, v, m, p, ph))
+    return sims
+
+
+def _pack(sims):
+    offs = np.cumsum([0] + [s[0].shape[0] for s in sims])
+    X = np.concatenate([s[0] for s in sims]).T.copy()
+    V = np.concatenate([s[1] for s in sims]).T.copy()
+    M = np.concatenate([s[2] for s in sims]).copy()
+    return offs, torch.tensor(X, device=DEV), torch.tensor(V, device=DEV), torch.tensor(M, device=DEV)
+
+
+def _run_batch(sims, steps, tuning=None, calls=1):
+    offs, X, V, M = _pack(sims)
+    h = nb.nbody_create_batch(offs, [s[3] for s in sims])
+    try:
+        if tuning is not None:
+            nb.nbody_set_tuning(h, tuning)
+        nb.nbody_set_state(h, X, V, M)
+        for _ in range(calls):
+            nb.nbody_integrate(h, steps // calls)
+        xo = torch.empty_like(X)
+        nb.nbody_get_state(h, xo, None)
+        assert nb.nbody_get_status(h) == 0
+    finally:
+        nb.nbody_destroy(h)
+    out = xo.cpu().numpy().T
+    return [out[offs[k]:offs[k + 1]] for k in range(len(sims))]
+
+
+@pytest.mark.parametrize("tuning", range(nb.NBODY_NTUNE))
+def test_batch_members_match_oracle(tuning):
+    sims = _members()
+    steps = 40
+    got = _run_batch(sims, steps, tuning=tuning)
+    for (x, v, m, p, ph), xb in zip(sims, got):
+        xr, _ = orc.integrate(ph, x, v, m, p.dt, steps)
+        scale = 1.0 if ph.ext == 0 else C1.a_prog
+        assert np.abs(xb - xr).max() / scale <= 1e-6
+
+
+def test_batch_equals_single_runs_and_is_reproducible():
+    sims = _members()
+    a = _run_batch(sims, 30)
+    b = _run_batch(sims, 30)
+    for xa, xb in zip(a, b):
+        assert np.array_equal(xa, xb)
+    for (x, v, m, p, ph), xa in zip(sims, a):
+        sim = nb.Simulation(x.shape[0], p)
+        sim.set_state(torch.tensor(x.T.copy(), device=DEV), torch.tensor(v.T.copy(), device=DEV),
+                      torch.tensor(m, device=DEV))
+        xo = torch.empty((3, x.shape[0]), dtype=torch.float64, device=DEV)
+        sim.integrate(30, xo)
+        scale = 1.0 if ph.ext == 0 else C1.a_prog
+        assert np.abs(xo.cpu().numpy().T - xa).max() / scale <= 1e-6
+        sim.close()
+
+
+def test_batch_graph_replay_continues_the_run():
+    sims = _members()
+    one = _run_batch(sims, 40, calls=1)
+    two = _run_batch(sims, 40, calls=2)   # the captured graph is replayed
+    for xa, xb, s in zip(one, two, sims):
+        scale = 1.0 if s[4].ext == 0 else C1.a_prog
+        assert np.abs(xa - xb).max() / scale <= 1e-9
+
+
+def test_autotune_selects_a_candidate():
+    sims = _members()
+    offs, X, V, M = _pack(sims)
+    h = nb.nbody_create_batch(offs, [s[3] for s in sims])
+    nb.nbody_set_state(h, X, V, M)
+    best, ms = nb.nbody_autotune(h, 2)
+    assert 0 <= best < nb.NBODY_NTUNE and nb.nbody_get_tuning(h) == best
+    assert all(t > 0 for t in ms) and ms[best] == min(ms)
+    xo = torch.empty_like(X)
+    nb.nbody_get_state(h, xo, None)
+    assert torch.equal(xo, X)   # tuning does not advance the state
+    nb.nbody_destroy(h)
