@@ -303,8 +303,81 @@ NBODY_API int nbody_stream_forward(nbody_stream *s, const double theta[4],
  * Errors: ESTATE (no forward), ECUDA, ENAN. */
 NBODY_API int nbody_stream_grad(nbody_stream *s, double theta_bar[4]);
 
+/* Steps 1-2 alone: the initial state at theta (host, 4 doubles) -- x0, v0
+ * (3 x n) and m (n), device pointers -- and the recovered centre of mass
+ * (host, 6 doubles: X, V; may be NULL).  Synchronises.
+ * Errors: EINVAL, ECUDA. */
+NBODY_API int nbody_stream_initial_state(nbody_stream *s, const double theta[4],
+                                         double *x0, double *v0, double *m,
+                                         double com[6]);
+
+/* Steps 4-5 alone: the histogram (nb1 * nb2, host or device) of positions x
+ * (3 x n, device) and, when loss is not NULL, their loss against the target.
+ * Does not change what nbody_stream_grad uses.  Synchronises.
+ * Errors: EINVAL, ECUDA. */
+NBODY_API int nbody_stream_head(nbody_stream *s, const double *x,
+                                double *density, double *loss);
+
 /* Release the pipeline; NULL is a no-op. */
 NBODY_API void nbody_stream_destroy(nbody_stream *s);
+
+/* ---- density surrogate (the paper's outlook, Sec. 3: a neural network
+ *      coupled to the solver) ---- */
+
+/* y = W3 GELU(W2 GELU(W1 u + b1) + b2) + b3, GELU(z) = z Phi(z) with the
+ * exact normal CDF, FP32.  Parameters are one flat FP32 array in the order
+ * W1 (h x in), b1 (h), W2 (h x h), b2 (h), W3 (out x h), b3 (out), weight
+ * matrices row-major (one row per output unit).  Inputs u are (batch x in)
+ * and outputs y, targets t (batch x out), row-major, in device memory.
+ * Used to map the four stream parameters to a binned density and to
+ * warm-start the simulator's gradient descent. */
+typedef struct nbody_mlp nbody_mlp; /* opaque, owned by the library */
+
+/* Create a network with the given widths for batches of at most max_batch
+ * rows; parameters start at zero (set them with nbody_mlp_set_params).
+ * Errors: EINVAL, ENODEV, ENOMEM. */
+NBODY_API int nbody_mlp_create(nbody_mlp **out, int n_in, int n_hidden,
+                               int n_out, int max_batch, void *cuda_stream);
+
+/* Number of FP32 parameters (the length of the flat array). */
+NBODY_API int64_t nbody_mlp_num_params(const nbody_mlp *m);
+
+/* Copy the flat parameter array in or out (host or device pointers);
+ * set_params also resets the Adam moments and step count.
+ * Errors: EINVAL, ECUDA. */
+NBODY_API int nbody_mlp_set_params(nbody_mlp *m, const float *params);
+NBODY_API int nbody_mlp_get_params(nbody_mlp *m, float *params);
+
+/* y = MLP(u) for `batch` rows (1 .. max_batch).  Errors: EINVAL, ECUDA. */
+NBODY_API int nbody_mlp_forward(nbody_mlp *m, const float *u, int batch,
+                                float *y);
+
+/* Mean squared error L = mean (MLP(u) - t)^2 over batch x out, and its
+ * gradients: with respect to the parameters (kept inside the network for
+ * nbody_mlp_adam_step and copied to grads, device, when not NULL) and to
+ * the inputs (du, device, batch x in, when not NULL).  loss (host) may be
+ * NULL.  Synchronises when loss is requested.  Errors: EINVAL, ECUDA. */
+NBODY_API int nbody_mlp_loss_grad(nbody_mlp *m, const float *u, const float *t,
+                                  int batch, float *loss, float *grads,
+                                  float *du);
+
+/* One Adam update (Kingma & Ba, bias-corrected) of every parameter with the
+ * gradient of the last nbody_mlp_loss_grad.  Errors: EINVAL, ESTATE, ECUDA. */
+NBODY_API int nbody_mlp_adam_step(nbody_mlp *m, float lr, float beta1,
+                                  float beta2, float eps);
+
+/* Invert the network: from `starts` initial inputs u (starts x n_in,
+ * device; overwritten with the results) run `iters` Adam steps (learning
+ * rate lr, inputs clamped to [lo, hi]) on each row's squared error
+ * mean_o (MLP(u)_o - target_o)^2 against target (n_out, device).  loss
+ * (device, starts floats, may be NULL) receives each row's final error.
+ * Requires starts <= max_batch.  Errors: EINVAL, ECUDA. */
+NBODY_API int nbody_mlp_invert(nbody_mlp *m, const float *target, int starts,
+                               float *u, int iters, float lr, float lo, float hi,
+                               float *loss);
+
+/* Release the network; NULL is a no-op. */
+NBODY_API void nbody_mlp_destroy(nbody_mlp *m);
 
 /* ---- allocation-free variant (no counterpart in the paper) ---- */
 

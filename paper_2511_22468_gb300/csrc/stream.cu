@@ -455,6 +455,104 @@ int nbody_stream_create(nbody_stream** out, const nbody_stream_cfg* cfg,
   return NBODY_OK;
 }
 
+int nbody_stream_initial_state(nbody_stream* s, const double theta[4], double* x0,
+                               double* v0, double* m, double com[6]) {
+  if (!s || !theta || !x0 || !v0 || !m) return NBODY_EINVAL;
+  for (int k = 0; k < 4; ++k)
+    if (!(theta[k] > 0.0) || !std::isfinite(theta[k])) return NBODY_EINVAL;
+  // the orbit helpers read s->theta; keep the recorded forward unchanged
+  double keep[4];
+  for (int k = 0; k < 4; ++k) {
+    keep[k] = s->theta[k];
+    s->theta[k] = theta[k];
+  }
+  const nbody_stream_cfg& c = s->cfg;
+  const DevParams P = orbit_params(s);
+  for (int k = 0; k < 4; ++k) s->theta[k] = keep[k];
+  const int64_t n = s->n;
+  // private orbit buffers would be wasteful: the orbit of this call goes to
+  // the pipeline's own buffers only when no forward is recorded
+  double* ox = s->ox;
+  double* ovh = s->ovh;
+  double* g6 = s->g6;
+  double* tmp = nullptr;
+  if (s->have_forward) {
+    const size_t need = 3 * (size_t)(2 * c.n_steps + 1) + 6;
+    if (cudaMalloc((void**)&tmp, need * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return NBODY_ENOMEM;
+    }
+    ox = tmp;
+    ovh = tmp + 3 * (c.n_steps + 1);
+    g6 = ovh + 3 * c.n_steps;
+  }
+  k_orbit<<<1, 32, 0, s->s>>>(P, c.X0[0], c.X0[1], c.X0[2], c.V0[0], c.V0[1], c.V0[2],
+                              c.n_steps, ox, ovh, g6);
+  nb::count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    k_ic<<<blocks_for(n, 256), 256, 0, s->s>>>(s->xhat, s->vhat, g6, c.a_prog,
+                                               std::sqrt(c.G * theta[1] / c.a_prog),
+                                               theta[1] / (double)n, n, x0, v0, m);
+    nb::count_launch();
+    e = cudaGetLastError();
+  }
+  double h6[6];
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h6, g6, sizeof(h6), cudaMemcpyDeviceToHost, s->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->s);
+  if (tmp) cudaFree(tmp);
+  if (e != cudaSuccess) return NBODY_ECUDA;
+  if (com)
+    for (int k = 0; k < 6; ++k) com[k] = h6[k];
+  return NBODY_OK;
+}
+
+int nbody_stream_head(nbody_stream* s, const double* x, double* density, double* loss) {
+  if (!s || !x || !density) return NBODY_EINVAL;
+  const nbody_stream_cfg& c = s->cfg;
+  const int64_t n = s->n;
+  // scratch of the head: its own weight / angle / histogram buffers would
+  // duplicate the pipeline's; reuse them only when no forward is recorded
+  double *phi = s->phi, *w = s->w, *rho = s->rho, *rb = s->rbar, *ls = s->loss;
+  double* tmp = nullptr;
+  if (s->have_forward) {
+    const size_t need = (size_t)n * (2 + c.nb1 + c.nb2) + 2 * (size_t)s->nb + 1;
+    if (cudaMalloc((void**)&tmp, need * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return NBODY_ENOMEM;
+    }
+    phi = tmp;
+    w = phi + 2 * n;
+    rho = w + (size_t)n * (c.nb1 + c.nb2);
+    rb = rho + s->nb;
+    ls = rb + s->nb;
+  }
+  k_head_weights<<<blocks_for(n, 128), 128, 0, s->s>>>(s->geom, x, n, phi, w);
+  nb::count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    k_hist<<<c.nb1, 256, 0, s->s>>>(w, n, c.nb1, c.nb2, rho);
+    nb::count_launch();
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    k_loss<<<1, 256, 0, s->s>>>(rho, s->target, (int)s->nb, ls, rb);
+    nb::count_launch();
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(density, rho, (size_t)s->nb * sizeof(double), cudaMemcpyDefault, s->s);
+  double L = 0.0;
+  if (e == cudaSuccess && loss)
+    e = cudaMemcpyAsync(&L, ls, sizeof(double), cudaMemcpyDeviceToHost, s->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->s);
+  if (tmp) cudaFree(tmp);
+  if (e != cudaSuccess) return NBODY_ECUDA;
+  if (loss) *loss = L;
+  return NBODY_OK;
+}
+
 void nbody_stream_destroy(nbody_stream* s) {
   if (!s) return;
   cudaStreamSynchronize(s->s);

@@ -40,8 +40,11 @@ EXPORTED = ("nbody_create", "nbody_destroy", "nbody_set_params",
             "nbody_pair_accel", "nbody_set_timing", "nbody_kernel_times",
             "nbody_pair_accel_noalloc", "nbody_stream_create",
             "nbody_stream_set_target", "nbody_stream_forward", "nbody_stream_grad",
-            "nbody_stream_destroy", "nbody_create_batch", "nbody_autotune",
-            "nbody_set_tuning", "nbody_get_tuning")
+            "nbody_stream_destroy", "nbody_stream_initial_state", "nbody_stream_head", "nbody_create_batch", "nbody_autotune",
+            "nbody_set_tuning", "nbody_get_tuning", "nbody_mlp_create",
+            "nbody_mlp_num_params", "nbody_mlp_set_params", "nbody_mlp_get_params",
+            "nbody_mlp_forward", "nbody_mlp_loss_grad", "nbody_mlp_adam_step",
+            "nbody_mlp_destroy", "nbody_mlp_invert")
 
 NBODY_NTUNE = 8
 
@@ -127,12 +130,27 @@ def lib():
         L.nbody_stream_set_target.argtypes = [vp, vp]
         L.nbody_stream_forward.argtypes = [vp, dp, dp, vp]
         L.nbody_stream_grad.argtypes = [vp, dp]
+        L.nbody_stream_initial_state.argtypes = [vp, dp, vp, vp, vp, dp]
+        L.nbody_stream_head.argtypes = [vp, vp, vp, dp]
         L.nbody_stream_destroy.argtypes = [vp]
         L.nbody_stream_destroy.restype = None
         L.nbody_create_batch.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(i64), P, vp]
         L.nbody_autotune.argtypes = [vp, i64, C.POINTER(C.c_int), dp]
         L.nbody_set_tuning.argtypes = [vp, C.c_int]
         L.nbody_get_tuning.argtypes = [vp]
+        fp = C.POINTER(C.c_float)
+        L.nbody_mlp_create.argtypes = [C.POINTER(vp), C.c_int, C.c_int, C.c_int, C.c_int, vp]
+        L.nbody_mlp_num_params.argtypes = [vp]
+        L.nbody_mlp_num_params.restype = i64
+        L.nbody_mlp_set_params.argtypes = [vp, vp]
+        L.nbody_mlp_get_params.argtypes = [vp, vp]
+        L.nbody_mlp_forward.argtypes = [vp, vp, C.c_int, vp]
+        L.nbody_mlp_loss_grad.argtypes = [vp, vp, vp, C.c_int, fp, vp, vp]
+        L.nbody_mlp_adam_step.argtypes = [vp, C.c_float, C.c_float, C.c_float, C.c_float]
+        L.nbody_mlp_invert.argtypes = [vp, vp, C.c_int, vp, C.c_int, C.c_float,
+                                        C.c_float, C.c_float, vp]
+        L.nbody_mlp_destroy.argtypes = [vp]
+        L.nbody_mlp_destroy.restype = None
         L.nbody_set_timing.argtypes = [vp, C.c_int]
         L.nbody_kernel_times.argtypes = [vp, dp, C.POINTER(i64)]
         _lib = L
@@ -155,6 +173,23 @@ def _ptr(a, shape=None):
         raise TypeError("expected a C-contiguous float64 array")
     if shape is not None and tuple(a.shape) != tuple(shape):
         raise ValueError("expected shape %s, got %s" % (shape, tuple(a.shape)))
+    return C.c_void_p(a.ctypes.data)
+
+
+def _fptr(a, shape=None):
+    """Raw address of a float32 contiguous torch tensor or numpy array."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.dtype != torch.float32 or not a.is_contiguous():
+            raise TypeError("expected a contiguous float32 tensor")
+        if shape is not None and tuple(a.shape) != tuple(shape):
+            raise ValueError("expected shape %s, got %s" % (shape, tuple(a.shape)))
+        return C.c_void_p(a.data_ptr())
+    import numpy as np
+    if a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError("expected a C-contiguous float32 array")
     return C.c_void_p(a.ctypes.data)
 
 
@@ -310,6 +345,51 @@ def nbody_get_tuning(h):
     return rc
 
 
+def nbody_mlp_create(n_in, n_hidden, n_out, max_batch, stream=None):
+    h = C.c_void_p()
+    _check(lib().nbody_mlp_create(C.byref(h), n_in, n_hidden, n_out, max_batch,
+                                  _stream(stream)), "nbody_mlp_create")
+    return h
+
+
+def nbody_mlp_num_params(h):
+    return lib().nbody_mlp_num_params(h)
+
+
+def nbody_mlp_set_params(h, params):
+    _check(lib().nbody_mlp_set_params(h, _fptr(params)), "nbody_mlp_set_params")
+
+
+def nbody_mlp_get_params(h, params):
+    _check(lib().nbody_mlp_get_params(h, _fptr(params)), "nbody_mlp_get_params")
+
+
+def nbody_mlp_forward(h, u, y):
+    _check(lib().nbody_mlp_forward(h, _fptr(u), u.shape[0], _fptr(y)), "nbody_mlp_forward")
+
+
+def nbody_mlp_loss_grad(h, u, t, grads=None, du=None, want_loss=True):
+    loss = C.c_float()
+    _check(lib().nbody_mlp_loss_grad(h, _fptr(u), _fptr(t), u.shape[0],
+                                     C.byref(loss) if want_loss else None,
+                                     _fptr(grads), _fptr(du)), "nbody_mlp_loss_grad")
+    return loss.value if want_loss else None
+
+
+def nbody_mlp_adam_step(h, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    _check(lib().nbody_mlp_adam_step(h, lr, beta1, beta2, eps), "nbody_mlp_adam_step")
+
+
+def nbody_mlp_invert(h, target, u, iters, lr, lo=-1.5, hi=1.5, loss=None):
+    """Adam on the inputs u (starts, n_in) toward target (n_out,); in place."""
+    _check(lib().nbody_mlp_invert(h, _fptr(target), u.shape[0], _fptr(u), iters, lr, lo,
+                                  hi, _fptr(loss)), "nbody_mlp_invert")
+
+
+def nbody_mlp_destroy(h):
+    lib().nbody_mlp_destroy(h)
+
+
 def nbody_stream_create(cfg: nbody_stream_cfg, xhat, vhat, stream=None):
     h = C.c_void_p()
     n = cfg.n
@@ -336,6 +416,24 @@ def nbody_stream_grad(h):
     tb = (C.c_double * 4)()
     _check(lib().nbody_stream_grad(h, tb), "nbody_stream_grad")
     return list(tb)
+
+
+def nbody_stream_initial_state(h, theta, x0, v0, m):
+    """Fills x0, v0 (3, n) and m (n,) on the device; returns the recovered
+    centre of mass (X, V) as 6 floats."""
+    th = (C.c_double * 4)(*[float(t) for t in theta])
+    com = (C.c_double * 6)()
+    _check(lib().nbody_stream_initial_state(h, th, _ptr(x0), _ptr(v0), _ptr(m), com),
+           "nbody_stream_initial_state")
+    return list(com)
+
+
+def nbody_stream_head(h, x, density, want_loss=False):
+    loss = C.c_double()
+    _check(lib().nbody_stream_head(h, _ptr(x), _ptr(density),
+                                   C.byref(loss) if want_loss else None),
+           "nbody_stream_head")
+    return loss.value if want_loss else None
 
 
 def nbody_stream_destroy(h):
