@@ -210,6 +210,22 @@ NBODY_API int nbody_autotune(nbody_ctx *c, int64_t probe_steps, int *best,
 NBODY_API int nbody_set_tuning(nbody_ctx *c, int choice);
 NBODY_API int nbody_get_tuning(nbody_ctx *c);
 
+/* ---- launch shape of the pair kernels (single-system contexts) ---- */
+
+/* Override the launch shape of the pair-force (vjp = 0) or pair-VJP
+ * (vjp = 1) kernel: variant 0 = i-particles in registers and j-tiles in
+ * shared memory (threads, per_thread in {128 x 4, 128 x 8, 256 x 4,
+ * 256 x 2} forward, {256 x 2, 128 x 4, 128 x 2} VJP), variant 1 = j split
+ * over the lanes of a warp (threads 256, per_thread 4 or 8 forward, 2 or 4
+ * VJP); chunks = number of j-chunks (1..32), 0 = chosen to fill the GPU.
+ * Results change only by the summation order.  Invalidates the tape and
+ * the cached acceleration.  Errors: EINVAL. */
+NBODY_API int nbody_set_pair_shape(nbody_ctx *c, int vjp, int variant,
+                                   int threads, int per_thread, int chunks);
+
+/* Current shape {variant, threads, per_thread, chunks} (host, 4 ints). */
+NBODY_API int nbody_get_pair_shape(nbody_ctx *c, int vjp, int out[4]);
+
 /* ---- per-kernel timing (CUDA events on the context stream) ---- */
 #define NBODY_KCLASS_PAIR 0    /* pair-force kernel (forward and recompute)   */
 #define NBODY_KCLASS_VJP 1     /* pair VJP kernel                             */

@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(256)
     put_stage(st, g, (float)(x[g] - c[0]), (float)(x[ptot + g] - c[1]),
               (float)(x[2 * ptot + g] - c[2]), (float)m[g]);
   } else {
-    put_stage(st, g, 0.f, 0.f, 0.f, 0.f);
+    put_stage(st, g, kPadPos, kPadPos, kPadPos, 0.f);
   }
 }
 

@@ -58,6 +58,8 @@ struct nbody_ctx {
   double* pot = nullptr;  // [Sf][npad]
   int Smax = 0;
   nb::PairCfg fcfg{}, vcfg{};
+  double m_eq = 1.0;  // the common mass when fcfg.eqm / vcfg.eqm
+  bool shape_fixed[2] = {false, false};  // launch shape set by the caller
 
   double* guide = nullptr;       // [6] current guide (x, v)
   double* fixed_center = nullptr;  // [3]
@@ -256,6 +258,7 @@ nb::UpdateArgs base_update(nbody_ctx* c, double* x, double* v) {
   a.part = c->part;
   a.S = c->fcfg.S;
   a.part_is_final = 0;
+  a.mscale = c->fcfg.eqm ? c->m_eq : 1.0;
   a.st = c->st;
   a.status = c->status;
   return a;
@@ -468,9 +471,9 @@ int nbody_create(nbody_ctx** out, int64_t n, const nbody_params* p,
   c->npad = ((n + nb::kPad - 1) / nb::kPad) * nb::kPad;
   c->stream = (cudaStream_t)cuda_stream;
   c->p = *p;
-  c->fcfg = nb::choose_pair_cfg(c->npad, sms, false);
-  c->vcfg = nb::choose_pair_cfg(c->npad, sms, true);
-  c->Smax = c->fcfg.S > c->vcfg.S ? c->fcfg.S : c->vcfg.S;
+  c->fcfg = nb::choose_pair_cfg(c->npad, sms, false, false);
+  c->vcfg = nb::choose_pair_cfg(c->npad, sms, true, false);
+  c->Smax = 32;  // the largest chunk count choose_chunks picks
   const size_t np = (size_t)c->npad;
   c->nblk = nb::adjoint_blocks(n);
   if ((rc = dalloc(&c->dp, 1)) || (rc = dalloc(&c->x, 3 * np)) ||
@@ -478,7 +481,7 @@ int nbody_create(nbody_ctx** out, int64_t n, const nbody_params* p,
       (rc = dalloc(&c->acc, 3 * np)) || (rc = dalloc(&c->st, np)) ||
       (rc = dalloc(&c->vst, 2 * np)) ||
       (rc = dalloc(&c->part, (size_t)c->Smax * 3 * np)) ||
-      (rc = dalloc(&c->pot, (size_t)c->fcfg.S * np)) ||
+      (rc = dalloc(&c->pot, (size_t)c->Smax * np)) ||
       (rc = dalloc(&c->guide, 6)) || (rc = dalloc(&c->fixed_center, 3)) ||
       (rc = dalloc(&c->xbar, 3 * np)) || (rc = dalloc(&c->vbar, 3 * np)) ||
       (rc = dalloc(&c->blk, (size_t)c->nblk * 6)) || (rc = dalloc(&c->red, 8)) || (rc = dalloc(&c->lsc, nb::kLscDoubles)) ||
@@ -546,6 +549,16 @@ int nbody_set_state(nbody_ctx* c, const double* x, const double* v,
   c->last_seg_valid = false;
   rc = upload_params(c);  // resets the guide; synchronises (pageable inputs)
   if (rc) return rc;
+  // equal masses select the pair kernels that leave the mass out of the sum
+  double mm[2];
+  CK(nb::launch_minmax(c->m, c->n, c->red, c->stream));
+  CK(cudaMemcpyAsync(mm, c->red, sizeof(mm), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  const bool eqm = mm[0] == mm[1] && mm[0] > 0.0;
+  if (!c->shape_fixed[0]) c->fcfg = nb::choose_pair_cfg(c->npad, c->sm_count, false, eqm);
+  if (!c->shape_fixed[1]) c->vcfg = nb::choose_pair_cfg(c->npad, c->sm_count, true, eqm);
+  c->fcfg.eqm = c->vcfg.eqm = eqm;
+  c->m_eq = eqm ? mm[0] : 1.0;
   // stage masses (and positions) once; the update kernel rewrites positions
   CK(nb::launch_stage(c->x, c->m, c->fixed_center, c->n, c->npad, c->st,
                       c->stream));
@@ -614,6 +627,7 @@ int nbody_vjp(nbody_ctx* c, const double* xbar, const double* vbar,
   a.vbar = c->vbar;
   a.gpart = c->part;
   a.S = c->vcfg.S;
+  a.mscale = c->vcfg.eqm ? c->m_eq : 1.0;
   a.m = c->m;
   a.vst = c->vst;
   a.blk = c->blk;
@@ -765,6 +779,41 @@ int nbody_get_tuning(nbody_ctx* c) {
   return nb::batch_tuning(c->batch);
 }
 
+int nbody_set_pair_shape(nbody_ctx* c, int vjp, int variant, int threads,
+                         int per_thread, int chunks) {
+  if (!c || c->batch || (variant != 0 && variant != 1) || chunks < 0 || chunks > c->Smax)
+    return NBODY_EINVAL;
+  if (!nb::pair_shape_supported(variant, threads, per_thread, vjp != 0)) return NBODY_EINVAL;
+  nb::PairCfg& cfg = vjp ? c->vcfg : c->fcfg;
+  nb::PairCfg t = cfg;
+  t.variant = variant;
+  t.nt = threads;
+  t.r = per_thread;
+  if (t.variant == nb::kTile && c->npad % (t.nt * t.r) != 0) return NBODY_EINVAL;
+  if (chunks == 0) {
+    const int occ = vjp ? nb::vjp_blocks_per_sm(t) : nb::pair_blocks_per_sm(t);
+    t.S = nb::choose_chunks(t, c->npad, c->sm_count, occ);
+  } else {
+    t.S = chunks;
+  }
+  cfg = t;
+  c->shape_fixed[vjp ? 1 : 0] = true;
+  c->acc_valid = false;
+  c->tape_steps = 0;
+  c->last_seg_valid = false;
+  return NBODY_OK;
+}
+
+int nbody_get_pair_shape(nbody_ctx* c, int vjp, int out[4]) {
+  if (!c || c->batch || !out) return NBODY_EINVAL;
+  const nb::PairCfg& cfg = vjp ? c->vcfg : c->fcfg;
+  out[0] = cfg.variant;
+  out[1] = cfg.nt;
+  out[2] = cfg.r;
+  out[3] = cfg.S;
+  return NBODY_OK;
+}
+
 int nbody_set_timing(nbody_ctx* c, int enable) {
   if (!c || c->batch) return NBODY_EINVAL;
   c->timing = enable != 0;
@@ -799,7 +848,7 @@ int nbody_pair_accel(int64_t n, const double* x, const double* m, double G,
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const int64_t npad = ((n + nb::kPad - 1) / nb::kPad) * nb::kPad;
-  const nb::PairCfg cfg = nb::choose_pair_cfg(npad, sms, false);
+  const nb::PairCfg cfg = nb::choose_pair_cfg(npad, sms, false, false);
   // scratch: padded SoA copy of x and m, centre, staging, partials
   const size_t bytes_x = (size_t)4 * npad * sizeof(double);
   const size_t bytes_st = (size_t)npad * sizeof(float4);

@@ -8,13 +8,16 @@
 //                   st[2p+1] = (z_{2p}, z_{2p+1}, m_{2p}, m_{2p+1})
 //                 coordinates are FP32 (x - c), c the FP64 recentring origin
 //   vst           float4 [2*npad]             adjoint staging, pair layout:
-//                   vst[4p]..vst[4p+1] as st, vst[4p+2] = (lx, lx', ly, ly'),
-//                   vst[4p+3] = (lz, lz', 0, 0), lambda the FP32 cotangent
+//                   vst[4p]..vst[4p+1] as st, vst[4p+2] = -(lx, lx', ly, ly'),
+//                   vst[4p+3] = (-lz, -lz', 0, 0), lambda the FP32 cotangent
+//                   (stored negated)
 //   part          FP64 [S][3][npad]           pair-kernel partial sums, one
 //                                             slice per j-chunk, reduced in
 //                                             fixed order by the consumer
-// npad is n rounded up to a multiple of kPad; pad particles sit at the
-// origin with zero mass and zero cotangent, so they add exactly nothing.
+// npad is n rounded up to a multiple of kPad; pad particles are staged at
+// 1e18 with zero mass and zero cotangent, so their contribution is nil
+// (exactly zero in the kernels that multiply by m_j, below 1e-33 relative
+// in the equal-mass ones).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -54,11 +57,18 @@ struct PairCfg {
   int nt;       // threads per block
   int r;        // i-particles per thread (kTile) or per warp (kWarp)
   int S;        // number of j-chunks (grid.y); partial-sum slices
+  bool eqm;     // equal masses: sums omit the mass, the consumer applies it
+  int vjp_tile_pairs;  // j-pairs per shared-memory tile of the kernel
 };
 
-PairCfg choose_pair_cfg(int64_t npad, int sm_count, bool vjp);
+PairCfg choose_pair_cfg(int64_t npad, int sm_count, bool vjp, bool eqm);
+int pair_blocks_per_sm(const PairCfg& c);
+int vjp_blocks_per_sm(const PairCfg& c);
+bool pair_shape_supported(int variant, int nt, int r, bool vjp);
+int choose_chunks(const PairCfg& c, int64_t npad, int sm_count, int blocks_per_sm);
 
-// Raw sums R_i = sum_j m_j (x_j - x_i) s_ij^-3 (no G) into part[S][3][npad];
+// Raw sums R_i = sum_j m_j (x_j - x_i) s_ij^-3 (no G; with cfg.eqm the
+// common mass is left out too) into part[S][3][npad];
 // with pot != NULL also P_i = sum_j m_j / s_ij (self term included) into
 // pot[S][npad].
 cudaError_t launch_pair_accel(const PairCfg& cfg, const float4* st,
@@ -66,7 +76,8 @@ cudaError_t launch_pair_accel(const PairCfg& cfg, const float4* st,
                               double* pot, cudaStream_t s);
 
 // Raw sums Q_k = sum_j [s^-3 u - 3 s^-5 d (d.u)], u = m_j l_k - m_k l_j,
-// d = x_j - x_k, into part[S][3][npad].  (J_pair^T l)_k = -G Q_k.
+// d = x_j - x_k, into part[S][3][npad].  (J_pair^T l)_k = -G Q_k.  With
+// cfg.eqm, u = l_k - l_j (the common mass is left out).
 cudaError_t launch_pair_vjp(const PairCfg& cfg, const float4* vst,
                             int64_t npad, float eps2, double* part,
                             cudaStream_t s);
@@ -83,6 +94,7 @@ struct UpdateArgs {
   const double* part;   // pair partial sums (raw) or a final a_pair
   int S;                // slices in part
   int part_is_final;    // part holds G-scaled a_pair (one slice)
+  double mscale;        // multiplies raw sums (the common mass, or 1)
   double* acc_out;      // receives a_pair (FSAL cache), may be NULL
   double kick;          // v += kick * a
   int drift;            // 1: x += dt * v after the kick, then restage
@@ -125,6 +137,7 @@ struct AdjointArgs {
   double* vbar;
   const double* gpart;   // pair-VJP partial sums (raw)
   int S;
+  double mscale;         // multiplies raw sums (the common mass, or 1)
   const double* xk;      // positions at this point
   const double* ak;      // a_pair at this point
   double ck;             // kick coefficient (dt/2 at the ends, dt inside)
@@ -141,6 +154,9 @@ struct AdjointArgs {
 };
 cudaError_t launch_adjoint(const AdjointArgs& a, cudaStream_t s);
 int adjoint_blocks(int64_t n);
+
+// out[0..1] = min and max of m[0..n)
+cudaError_t launch_minmax(const double* m, int64_t n, double* out, cudaStream_t s);
 
 cudaError_t launch_reduce_rows(const double* blk, int nblk, int ncol,
                                double* out, cudaStream_t s);

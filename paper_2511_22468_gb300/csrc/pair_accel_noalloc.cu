@@ -72,7 +72,7 @@ extern "C" int nbody_pair_accel_noalloc(int64_t n, const double* x,
   if (rc) return rc;
 
   const int64_t npad = ((n + nb::kPad - 1) / nb::kPad) * nb::kPad;
-  const nb::PairCfg cfg = nb::choose_pair_cfg(npad, sms, false);
+  const nb::PairCfg cfg = nb::choose_pair_cfg(npad, sms, false, false);
   const size_t bytes_x = align256((size_t)4 * npad * sizeof(double));
   const size_t bytes_c = 256;
   const size_t bytes_st = align256((size_t)npad * sizeof(float4));

@@ -41,6 +41,25 @@ static __device__ __forceinline__ void body(float2 xj, float2 yj, float2 zj,
   az = __ffma2_rn(dz, w, az);
 }
 
+// equal masses: accumulates (x_j - x_i) s^-3 (the common mass is applied by
+// the consumer) -- one multiply fewer per interaction
+static __device__ __forceinline__ void body_eqm(float2 xj, float2 yj, float2 zj,
+                                                float2 nx, float2 ny, float2 nz,
+                                                float2 e2, float2& ax, float2& ay,
+                                                float2& az) {
+  const float2 dx = __fadd2_rn(xj, nx);
+  const float2 dy = __fadd2_rn(yj, ny);
+  const float2 dz = __fadd2_rn(zj, nz);
+  float2 s2 = __ffma2_rn(dx, dx, e2);
+  s2 = __ffma2_rn(dy, dy, s2);
+  s2 = __ffma2_rn(dz, dz, s2);
+  const float2 inv = rsqrt2(s2);
+  const float2 w = __fmul2_rn(__fmul2_rn(inv, inv), inv);
+  ax = __ffma2_rn(dx, w, ax);
+  ay = __ffma2_rn(dy, w, ay);
+  az = __ffma2_rn(dz, w, az);
+}
+
 static __device__ __forceinline__ void load_i(const float4* __restrict__ st,
                                        int64_t i, float& x, float& y,
                                        float& z) {

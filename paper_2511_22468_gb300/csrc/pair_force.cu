@@ -27,7 +27,7 @@ namespace {
 
 constexpr int kTJ = 128;  // j-pairs per shared-memory tile (256 particles)
 
-template <int NT, int R, bool POT>
+template <int NT, int R, bool POT, bool EQM>
 __global__ void __launch_bounds__(NT)
     k_pair_tile(const float4* __restrict__ st, int ntiles, float eps2,
                 int64_t npad, double* __restrict__ part,
@@ -70,9 +70,13 @@ __global__ void __launch_bounds__(NT)
       const float2 xj = make_float2(A.x, A.y), yj = make_float2(A.z, A.w);
       const float2 zj = make_float2(B.x, B.y), mj = make_float2(B.z, B.w);
 #pragma unroll
-      for (int r = 0; r < R; ++r)
-        body<POT>(xj, yj, zj, mj, nx[r], ny[r], nz[r], e2, ax[r], ay[r],
-                  az[r], ph[r]);
+      for (int r = 0; r < R; ++r) {
+        if (EQM)
+          body_eqm(xj, yj, zj, nx[r], ny[r], nz[r], e2, ax[r], ay[r], az[r]);
+        else
+          body<POT>(xj, yj, zj, mj, nx[r], ny[r], nz[r], e2, ax[r], ay[r],
+                    az[r], ph[r]);
+      }
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -95,7 +99,7 @@ __global__ void __launch_bounds__(NT)
 }
 
 // Warp variant: block of 8 warps; warp w owns i = (blockIdx.x*8 + w)*R + r.
-template <int R, bool POT>
+template <int R, bool POT, bool EQM>
 __global__ void __launch_bounds__(256)
     k_pair_warp(const float4* __restrict__ st, int64_t npairs, float eps2,
                 int64_t npad, double* __restrict__ part,
@@ -123,9 +127,13 @@ __global__ void __launch_bounds__(256)
     const float2 xj = make_float2(A.x, A.y), yj = make_float2(A.z, A.w);
     const float2 zj = make_float2(B.x, B.y), mj = make_float2(B.z, B.w);
 #pragma unroll
-    for (int r = 0; r < R; ++r)
-      body<POT>(xj, yj, zj, mj, nx[r], ny[r], nz[r], e2, ax[r], ay[r], az[r],
-                ph[r]);
+    for (int r = 0; r < R; ++r) {
+      if (EQM)
+        body_eqm(xj, yj, zj, nx[r], ny[r], nz[r], e2, ax[r], ay[r], az[r]);
+      else
+        body<POT>(xj, yj, zj, mj, nx[r], ny[r], nz[r], e2, ax[r], ay[r], az[r],
+                  ph[r]);
+    }
   }
   double* out = part + (int64_t)blockIdx.y * 3 * npad;
 #pragma unroll
@@ -151,7 +159,7 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-template <bool POT>
+template <bool POT, bool EQM>
 cudaError_t launch_impl(const PairCfg& c, const float4* st, int64_t npad,
                         float eps2, double* part, double* pot,
                         cudaStream_t s) {
@@ -160,21 +168,21 @@ cudaError_t launch_impl(const PairCfg& c, const float4* st, int64_t npad,
     const int per_block = c.nt * c.r;
     dim3 grid((unsigned)(npad / per_block), (unsigned)c.S);
     if (c.nt == 128 && c.r == 4)
-      k_pair_tile<128, 4, POT><<<grid, 128, 0, s>>>(st, ntiles, eps2, npad, part, pot);
+      k_pair_tile<128, 4, POT, EQM><<<grid, 128, 0, s>>>(st, ntiles, eps2, npad, part, pot);
     else if (c.nt == 128 && c.r == 8)
-      k_pair_tile<128, 8, POT><<<grid, 128, 0, s>>>(st, ntiles, eps2, npad, part, pot);
+      k_pair_tile<128, 8, POT, EQM><<<grid, 128, 0, s>>>(st, ntiles, eps2, npad, part, pot);
     else if (c.nt == 256 && c.r == 4)
-      k_pair_tile<256, 4, POT><<<grid, 256, 0, s>>>(st, ntiles, eps2, npad, part, pot);
+      k_pair_tile<256, 4, POT, EQM><<<grid, 256, 0, s>>>(st, ntiles, eps2, npad, part, pot);
     else if (c.nt == 256 && c.r == 2)
-      k_pair_tile<256, 2, POT><<<grid, 256, 0, s>>>(st, ntiles, eps2, npad, part, pot);
+      k_pair_tile<256, 2, POT, EQM><<<grid, 256, 0, s>>>(st, ntiles, eps2, npad, part, pot);
     else
       return cudaErrorInvalidValue;
   } else {
     dim3 grid((unsigned)(npad / (8 * c.r)), (unsigned)c.S);
     if (c.r == 4)
-      k_pair_warp<4, POT><<<grid, 256, 0, s>>>(st, npad / 2, eps2, npad, part, pot);
+      k_pair_warp<4, POT, EQM><<<grid, 256, 0, s>>>(st, npad / 2, eps2, npad, part, pot);
     else if (c.r == 8)
-      k_pair_warp<8, POT><<<grid, 256, 0, s>>>(st, npad / 2, eps2, npad, part, pot);
+      k_pair_warp<8, POT, EQM><<<grid, 256, 0, s>>>(st, npad / 2, eps2, npad, part, pot);
     else
       return cudaErrorInvalidValue;
   }
@@ -187,51 +195,89 @@ cudaError_t launch_impl(const PairCfg& c, const float4* st, int64_t npad,
 cudaError_t launch_pair_accel(const PairCfg& cfg, const float4* st,
                               int64_t npad, float eps2, double* part,
                               double* pot, cudaStream_t s) {
-  if (pot) return launch_impl<true>(cfg, st, npad, eps2, part, pot, s);
-  return launch_impl<false>(cfg, st, npad, eps2, part, nullptr, s);
+  if (pot) return launch_impl<true, false>(cfg, st, npad, eps2, part, pot, s);
+  if (cfg.eqm) return launch_impl<false, true>(cfg, st, npad, eps2, part, nullptr, s);
+  return launch_impl<false, false>(cfg, st, npad, eps2, part, nullptr, s);
 }
 
-// Launch shape: the tile variant when there are enough i-tiles to keep every
-// SM busy, otherwise the warp variant; S (j-chunks) is chosen so that the
-// number of blocks covers the resident-block slots of the GPU in whole
-// waves as nearly as possible.
-PairCfg choose_pair_cfg(int64_t npad, int sm_count, bool vjp) {
-  PairCfg c;
-  const int64_t slots_tile = (int64_t)sm_count * (vjp ? 3 : 4);
-  if (npad >= 65536) {
-    c.variant = kTile;
-    c.nt = 128;
-    c.r = vjp ? 2 : 4;
-    if (vjp) c.nt = 256;
+int pair_blocks_per_sm(const PairCfg& c) {
+  int occ = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+#define NB_OCC(NT, R)                                                               \
+  if (c.nt == NT && c.r == R)                                                       \
+    e = c.eqm ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(                      \
+                    &occ, k_pair_tile<NT, R, false, true>, NT, 0)                   \
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(                      \
+                    &occ, k_pair_tile<NT, R, false, false>, NT, 0);
+  if (c.variant == kTile) {
+    NB_OCC(128, 4) NB_OCC(128, 8) NB_OCC(256, 4) NB_OCC(256, 2)
+  } else {
+    e = c.eqm ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair_warp<4, false, true>, 256, 0)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair_warp<4, false, false>, 256, 0);
+  }
+#undef NB_OCC
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return occ > 0 ? occ : 1;
+}
+
+bool pair_shape_supported(int variant, int nt, int r, bool vjp) {
+  if (variant == kWarp) return vjp ? (nt == 256 && (r == 4 || r == 2)) : (nt == 256 && (r == 4 || r == 8));
+  if (vjp) return (nt == 256 && r == 2) || (nt == 128 && (r == 4 || r == 2));
+  return (nt == 128 && (r == 4 || r == 8)) || (nt == 256 && (r == 4 || r == 2));
+}
+
+// j-chunk count S for a given shape: the number of blocks covers the
+// resident-block slots of the GPU in whole waves as nearly as possible, with
+// a mild preference for fewer chunks (less partial-sum traffic)
+int choose_chunks(const PairCfg& c, int64_t npad, int sm_count, int blocks_per_sm) {
+  if (c.variant == kTile) {
+    const int kTJp = c.vjp_tile_pairs;
     const int64_t itiles = npad / (c.nt * c.r);
-    const int64_t ntiles = npad / (2 * kTJ);
-    // pick S in [1, 32] minimising idle slots of the last wave, with a mild
-    // preference for fewer chunks (less partial-sum traffic)
+    const int64_t ntiles = npad / (2 * kTJp);
+    const int64_t slots = (int64_t)sm_count * blocks_per_sm;
     double best = 1e30;
     int bestS = 1;
     for (int S = 1; S <= 32 && S <= ntiles; ++S) {
       const int64_t blocks = itiles * S;
-      const int64_t waves = (blocks + slots_tile - 1) / slots_tile;
-      const double eff = (double)blocks / (double)(waves * slots_tile);
+      const int64_t waves = (blocks + slots - 1) / slots;
+      const double eff = (double)blocks / (double)(waves * slots);
       const double cost = (1.0 / eff) * (1.0 + 0.002 * S);
       if (cost < best - 1e-12) {
         best = cost;
         bestS = S;
       }
     }
-    c.S = bestS;
+    return bestS;
+  }
+  const int64_t blocks_x = npad / (8 * c.r);
+  const int64_t want = (int64_t)sm_count * 8;  // 8 blocks of 8 warps per SM
+  int64_t S = (want + blocks_x - 1) / blocks_x;
+  const int64_t max_s = (npad / 2) / 64;  // at least 64 pairs per chunk
+  if (S > max_s) S = max_s;
+  if (S < 1) S = 1;
+  return (int)S;
+}
+
+// Launch shape: the tile variant when there are enough i-tiles to keep every
+// SM busy, otherwise the warp variant.
+PairCfg choose_pair_cfg(int64_t npad, int sm_count, bool vjp, bool eqm) {
+  PairCfg c;
+  c.eqm = eqm;
+  c.vjp_tile_pairs = vjp ? 64 : kTJ;
+  if (npad >= 65536) {
+    c.variant = kTile;
+    c.nt = vjp ? (eqm ? 128 : 256) : 128;
+    c.r = vjp ? 2 : 4;
   } else {
     c.variant = kWarp;
     c.nt = 256;
     c.r = 4;
-    const int64_t blocks_x = npad / (8 * c.r);
-    const int64_t want = (int64_t)sm_count * 8;  // 8 blocks of 8 warps per SM
-    int64_t S = (want + blocks_x - 1) / blocks_x;
-    const int64_t max_s = (npad / 2) / 64;  // at least 64 pairs per chunk
-    if (S > max_s) S = max_s;
-    if (S < 1) S = 1;
-    c.S = (int)S;
   }
+  const int occ = vjp ? vjp_blocks_per_sm(c) : pair_blocks_per_sm(c);
+  c.S = choose_chunks(c, npad, sm_count, occ);
   return c;
 }
 

@@ -11,7 +11,9 @@
 // u = m_j l_k - m_k l_j, d = x_j - x_k, so that g_k = -G Q_k; the j = k term
 // vanishes (u = 0).  Same tiling, packed FP32x2 arithmetic and FP32/FP64
 // two-level summation as the forward kernel; 26 FP32 operations and one
-// rsqrt per interaction.
+// rsqrt per interaction.  With equal masses u = m (l_k - l_j), the mass is
+// applied by the consumer, and the s^-3 and s^-5 sums are kept apart
+// (Q = A - 3 B): 22 FP32 operations per interaction.
 #include "nbody_internal.cuh"
 
 namespace nb {
@@ -29,9 +31,10 @@ __device__ __forceinline__ float rsqrt_ftz(float v) {
 struct IState {
   float2 nx, ny, nz;  // (-x_k, -x_k) ...
   float2 lx, ly, lz;  // (l_k, l_k)
-  float2 nm;          // (-m_k, -m_k)
+  float2 mk;          // (m_k, m_k)
 };
 
+// general masses: j-side record A = (x), B = (z, m), L1 = -(lx, ly), L2 = (-lz)
 __device__ __forceinline__ void vjp_body(const float4& A, const float4& B,
                                          const float4& L1, const float4& L2,
                                          const IState& s, float2 e2,
@@ -46,10 +49,10 @@ __device__ __forceinline__ void vjp_body(const float4& A, const float4& B,
   const float2 inv = make_float2(rsqrt_ftz(s2.x), rsqrt_ftz(s2.y));
   const float2 inv2 = __fmul2_rn(inv, inv);
   const float2 inv3 = __fmul2_rn(inv2, inv);
-  // u = m_j l_k - m_k l_j
-  const float2 ux = __ffma2_rn(mj, s.lx, __fmul2_rn(make_float2(L1.x, L1.y), s.nm));
-  const float2 uy = __ffma2_rn(mj, s.ly, __fmul2_rn(make_float2(L1.z, L1.w), s.nm));
-  const float2 uz = __ffma2_rn(mj, s.lz, __fmul2_rn(make_float2(L2.x, L2.y), s.nm));
+  // u = m_j l_k - m_k l_j  (the record holds -l_j)
+  const float2 ux = __ffma2_rn(mj, s.lx, __fmul2_rn(make_float2(L1.x, L1.y), s.mk));
+  const float2 uy = __ffma2_rn(mj, s.ly, __fmul2_rn(make_float2(L1.z, L1.w), s.mk));
+  const float2 uz = __ffma2_rn(mj, s.lz, __fmul2_rn(make_float2(L2.x, L2.y), s.mk));
   float2 du = __fmul2_rn(dx, ux);
   du = __ffma2_rn(dy, uy, du);
   du = __ffma2_rn(dz, uz, du);
@@ -60,6 +63,35 @@ __device__ __forceinline__ void vjp_body(const float4& A, const float4& B,
   qz = __ffma2_rn(c, dz, __ffma2_rn(inv3, uz, qz));
 }
 
+// equal masses: u = l_k - l_j; A += s^-3 u, B += s^-5 (d.u) d
+__device__ __forceinline__ void vjp_body_eqm(const float4& A, const float4& B,
+                                             const float4& L1, const float4& L2,
+                                             const IState& s, float2 e2, float2* a,
+                                             float2* b) {
+  const float2 dx = __fadd2_rn(make_float2(A.x, A.y), s.nx);
+  const float2 dy = __fadd2_rn(make_float2(A.z, A.w), s.ny);
+  const float2 dz = __fadd2_rn(make_float2(B.x, B.y), s.nz);
+  float2 s2 = __ffma2_rn(dx, dx, e2);
+  s2 = __ffma2_rn(dy, dy, s2);
+  s2 = __ffma2_rn(dz, dz, s2);
+  const float2 inv = make_float2(rsqrt_ftz(s2.x), rsqrt_ftz(s2.y));
+  const float2 inv2 = __fmul2_rn(inv, inv);
+  const float2 inv3 = __fmul2_rn(inv2, inv);
+  const float2 ux = __fadd2_rn(s.lx, make_float2(L1.x, L1.y));
+  const float2 uy = __fadd2_rn(s.ly, make_float2(L1.z, L1.w));
+  const float2 uz = __fadd2_rn(s.lz, make_float2(L2.x, L2.y));
+  float2 du = __fmul2_rn(dx, ux);
+  du = __ffma2_rn(dy, uy, du);
+  du = __ffma2_rn(dz, uz, du);
+  const float2 c = __fmul2_rn(__fmul2_rn(inv3, inv2), du);
+  a[0] = __ffma2_rn(inv3, ux, a[0]);
+  a[1] = __ffma2_rn(inv3, uy, a[1]);
+  a[2] = __ffma2_rn(inv3, uz, a[2]);
+  b[0] = __ffma2_rn(c, dx, b[0]);
+  b[1] = __ffma2_rn(c, dy, b[1]);
+  b[2] = __ffma2_rn(c, dz, b[2]);
+}
+
 __device__ __forceinline__ IState load_k(const float4* __restrict__ vst,
                                          int64_t k) {
   const int64_t p = k >> 1;
@@ -68,8 +100,8 @@ __device__ __forceinline__ IState load_k(const float4* __restrict__ vst,
   const float4 L1 = vst[4 * p + 2], L2 = vst[4 * p + 3];
   const float x = odd ? A.y : A.x, y = odd ? A.w : A.z, z = odd ? B.y : B.x;
   const float m = odd ? B.w : B.z;
-  const float lx = odd ? L1.y : L1.x, ly = odd ? L1.w : L1.z;
-  const float lz = odd ? L2.y : L2.x;
+  const float lx = -(odd ? L1.y : L1.x), ly = -(odd ? L1.w : L1.z);
+  const float lz = -(odd ? L2.y : L2.x);
   IState s;
   s.nx = make_float2(-x, -x);
   s.ny = make_float2(-y, -y);
@@ -77,11 +109,11 @@ __device__ __forceinline__ IState load_k(const float4* __restrict__ vst,
   s.lx = make_float2(lx, lx);
   s.ly = make_float2(ly, ly);
   s.lz = make_float2(lz, lz);
-  s.nm = make_float2(-m, -m);
+  s.mk = make_float2(m, m);
   return s;
 }
 
-template <int NT, int R>
+template <int NT, int R, bool EQM>
 __global__ void __launch_bounds__(NT)
     k_vjp_tile(const float4* __restrict__ vst, int ntiles, float eps2,
                int64_t npad, double* __restrict__ part) {
@@ -106,21 +138,33 @@ __global__ void __launch_bounds__(NT)
 #pragma unroll
     for (int q = t; q < 4 * kTJ; q += NT) sj[q] = src[q];
     __syncthreads();
-    float2 qx[R], qy[R], qz[R];
+    float2 qa[R][3], qb[R][3];
 #pragma unroll
-    for (int r = 0; r < R; ++r) qx[r] = qy[r] = qz[r] = make_float2(0.f, 0.f);
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) qa[r][d] = qb[r][d] = make_float2(0.f, 0.f);
 #pragma unroll 2
     for (int jj = 0; jj < kTJ; ++jj) {
       const float4 A = sj[4 * jj], B = sj[4 * jj + 1];
       const float4 L1 = sj[4 * jj + 2], L2 = sj[4 * jj + 3];
 #pragma unroll
-      for (int r = 0; r < R; ++r) vjp_body(A, B, L1, L2, st[r], e2, qx[r], qy[r], qz[r]);
+      for (int r = 0; r < R; ++r) {
+        if (EQM)
+          vjp_body_eqm(A, B, L1, L2, st[r], e2, qa[r], qb[r]);
+        else
+          vjp_body(A, B, L1, L2, st[r], e2, qa[r][0], qa[r][1], qa[r][2]);
+      }
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      gx[r] += (double)qx[r].x + (double)qx[r].y;
-      gy[r] += (double)qy[r].x + (double)qy[r].y;
-      gz[r] += (double)qz[r].x + (double)qz[r].y;
+      gx[r] += (double)qa[r][0].x + (double)qa[r][0].y;
+      gy[r] += (double)qa[r][1].x + (double)qa[r][1].y;
+      gz[r] += (double)qa[r][2].x + (double)qa[r][2].y;
+      if (EQM) {
+        gx[r] -= 3.0 * ((double)qb[r][0].x + (double)qb[r][0].y);
+        gy[r] -= 3.0 * ((double)qb[r][1].x + (double)qb[r][1].y);
+        gz[r] -= 3.0 * ((double)qb[r][2].x + (double)qb[r][2].y);
+      }
     }
   }
   double* p = part + (int64_t)blockIdx.y * 3 * npad;
@@ -133,7 +177,7 @@ __global__ void __launch_bounds__(NT)
   }
 }
 
-template <int R>
+template <int R, bool EQM>
 __global__ void __launch_bounds__(256)
     k_vjp_warp(const float4* __restrict__ vst, int64_t npairs, float eps2,
                int64_t npad, double* __restrict__ part) {
@@ -143,25 +187,36 @@ __global__ void __launch_bounds__(256)
   const int64_t pb = ((int64_t)blockIdx.y * npairs) / S;
   const int64_t pe = ((int64_t)(blockIdx.y + 1) * npairs) / S;
   IState st[R];
-  float2 qx[R], qy[R], qz[R];
+  float2 qa[R][3], qb[R][3];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     st[r] = load_k(vst, kb + r);
-    qx[r] = qy[r] = qz[r] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) qa[r][d] = qb[r][d] = make_float2(0.f, 0.f);
   }
   const float2 e2 = make_float2(eps2, eps2);
   for (int64_t p = pb + lane; p < pe; p += 32) {
     const float4 A = vst[4 * p], B = vst[4 * p + 1];
     const float4 L1 = vst[4 * p + 2], L2 = vst[4 * p + 3];
 #pragma unroll
-    for (int r = 0; r < R; ++r) vjp_body(A, B, L1, L2, st[r], e2, qx[r], qy[r], qz[r]);
+    for (int r = 0; r < R; ++r) {
+      if (EQM)
+        vjp_body_eqm(A, B, L1, L2, st[r], e2, qa[r], qb[r]);
+      else
+        vjp_body(A, B, L1, L2, st[r], e2, qa[r][0], qa[r][1], qa[r][2]);
+    }
   }
   double* out = part + (int64_t)blockIdx.y * 3 * npad;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    double sx = (double)qx[r].x + (double)qx[r].y;
-    double sy = (double)qy[r].x + (double)qy[r].y;
-    double sz = (double)qz[r].x + (double)qz[r].y;
+    double sx = (double)qa[r][0].x + (double)qa[r][0].y;
+    double sy = (double)qa[r][1].x + (double)qa[r][1].y;
+    double sz = (double)qa[r][2].x + (double)qa[r][2].y;
+    if (EQM) {
+      sx -= 3.0 * ((double)qb[r][0].x + (double)qb[r][0].y);
+      sy -= 3.0 * ((double)qb[r][1].x + (double)qb[r][1].y);
+      sz -= 3.0 * ((double)qb[r][2].x + (double)qb[r][2].y);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       sx += __shfl_xor_sync(0xffffffffu, sx, o);
@@ -179,30 +234,60 @@ __global__ void __launch_bounds__(256)
 
 }  // namespace
 
-cudaError_t launch_pair_vjp(const PairCfg& c, const float4* vst, int64_t npad,
+template <bool EQM>
+cudaError_t launch_vjp_impl(const PairCfg& c, const float4* vst, int64_t npad,
                             float eps2, double* part, cudaStream_t s) {
   if (c.variant == kTile) {
     const int ntiles = (int)(npad / (2 * kTJ));
     dim3 grid((unsigned)(npad / (c.nt * c.r)), (unsigned)c.S);
     if (c.nt == 256 && c.r == 2)
-      k_vjp_tile<256, 2><<<grid, 256, 0, s>>>(vst, ntiles, eps2, npad, part);
+      k_vjp_tile<256, 2, EQM><<<grid, 256, 0, s>>>(vst, ntiles, eps2, npad, part);
     else if (c.nt == 128 && c.r == 4)
-      k_vjp_tile<128, 4><<<grid, 128, 0, s>>>(vst, ntiles, eps2, npad, part);
+      k_vjp_tile<128, 4, EQM><<<grid, 128, 0, s>>>(vst, ntiles, eps2, npad, part);
     else if (c.nt == 128 && c.r == 2)
-      k_vjp_tile<128, 2><<<grid, 128, 0, s>>>(vst, ntiles, eps2, npad, part);
+      k_vjp_tile<128, 2, EQM><<<grid, 128, 0, s>>>(vst, ntiles, eps2, npad, part);
     else
       return cudaErrorInvalidValue;
   } else {
     dim3 grid((unsigned)(npad / (8 * c.r)), (unsigned)c.S);
     if (c.r == 4)
-      k_vjp_warp<4><<<grid, 256, 0, s>>>(vst, npad / 2, eps2, npad, part);
+      k_vjp_warp<4, EQM><<<grid, 256, 0, s>>>(vst, npad / 2, eps2, npad, part);
     else if (c.r == 2)
-      k_vjp_warp<2><<<grid, 256, 0, s>>>(vst, npad / 2, eps2, npad, part);
+      k_vjp_warp<2, EQM><<<grid, 256, 0, s>>>(vst, npad / 2, eps2, npad, part);
     else
       return cudaErrorInvalidValue;
   }
   count_launch();
   return cudaGetLastError();
+}
+
+int vjp_blocks_per_sm(const PairCfg& c) {
+  int occ = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+#define NB_OCC(NT, R)                                                             \
+  if (c.nt == NT && c.r == R)                                                     \
+    e = c.eqm ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(                    \
+                    &occ, k_vjp_tile<NT, R, true>, NT, 0)                         \
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(                    \
+                    &occ, k_vjp_tile<NT, R, false>, NT, 0);
+  if (c.variant == kTile) {
+    NB_OCC(256, 2) NB_OCC(128, 4) NB_OCC(128, 2)
+  } else {
+    e = c.eqm ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_vjp_warp<4, true>, 256, 0)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_vjp_warp<4, false>, 256, 0);
+  }
+#undef NB_OCC
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return occ > 0 ? occ : 1;
+}
+
+cudaError_t launch_pair_vjp(const PairCfg& c, const float4* vst, int64_t npad,
+                            float eps2, double* part, cudaStream_t s) {
+  if (c.eqm) return launch_vjp_impl<true>(c, vst, npad, eps2, part, s);
+  return launch_vjp_impl<false>(c, vst, npad, eps2, part, s);
 }
 
 }  // namespace nb

@@ -37,7 +37,7 @@ __global__ void k_stage(const double* __restrict__ x,
     put_stage(st, i, (float)(x[i] - c[0]), (float)(x[npad + i] - c[1]),
               (float)(x[2 * npad + i] - c[2]), (float)m[i]);
   else
-    put_stage(st, i, 0.f, 0.f, 0.f, 0.f);
+    put_stage(st, i, kPadPos, kPadPos, kPadPos, 0.f);
 }
 
 // power-of-two scale 2^-e bringing the largest |lambda| (bit pattern) near 1
@@ -89,7 +89,7 @@ __global__ void k_stage_vjp(const double* __restrict__ x,
                (float)(sc * lam[i]), (float)(sc * lam[npad + i]),
                (float)(sc * lam[2 * npad + i]));
   else
-    put_vstage(vst, i, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
+    put_vstage(vst, i, kPadPos, kPadPos, kPadPos, 0.f, 0.f, 0.f, 0.f);
 }
 
 // ------------------------------------------------------------------- update
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(256) k_update(UpdateArgs a) {
     } else {
       double s = 0.0;
       for (int q = 0; q < a.S; ++q) s += a.part[((int64_t)q * 3 + d) * np + i];
-      ap[d] = P.G * s;
+      ap[d] = P.G * a.mscale * s;
     }
   }
   double x[3], v[3];
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
       ap[d] = a.ak[d * np + i];
       double s = 0.0;
       for (int q = 0; q < a.S; ++q) s += a.gpart[((int64_t)q * 3 + d) * np + i];
-      g[d] = -P.G * (s / s_here);
+      g[d] = -P.G * a.mscale * (s / s_here);
     }
     ExtUnit e;
     ext_unit(P, x[0], x[1], x[2], e);
@@ -311,6 +311,36 @@ __global__ void k_reduce_partials(const double* __restrict__ part, int S,
   }
 }
 
+// out = {min, max} of m[0..n) (one block; order-independent, deterministic)
+__global__ void __launch_bounds__(1024)
+    k_minmax(const double* __restrict__ m, int64_t n, double* __restrict__ out) {
+  __shared__ double smin[32], smax[32];
+  double lo = INFINITY, hi = -INFINITY;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    lo = fmin(lo, m[i]);
+    hi = fmax(hi, m[i]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_down_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_down_sync(0xffffffffu, hi, o));
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    smin[w] = lo;
+    smax[w] = hi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+      lo = fmin(lo, smin[k]);
+      hi = fmax(hi, smax[k]);
+    }
+    out[0] = lo;
+    out[1] = hi;
+  }
+}
+
 inline unsigned blocks_for(int64_t n, int t) {
   return (unsigned)((n + t - 1) / t);
 }
@@ -348,6 +378,12 @@ cudaError_t launch_stage_vjp(const double* x, const double* m,
 }
 
 int adjoint_blocks(int64_t n) { return (int)blocks_for(n, 256); }
+
+cudaError_t launch_minmax(const double* m, int64_t n, double* out, cudaStream_t s) {
+  k_minmax<<<1, 1024, 0, s>>>(m, n, out);
+  count_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t launch_adjoint(const AdjointArgs& a, cudaStream_t s) {
   k_adjoint<<<adjoint_blocks(a.n), 256, 0, s>>>(a);

@@ -44,7 +44,8 @@ EXPORTED = ("nbody_create", "nbody_destroy", "nbody_set_params",
             "nbody_set_tuning", "nbody_get_tuning", "nbody_mlp_create",
             "nbody_mlp_num_params", "nbody_mlp_set_params", "nbody_mlp_get_params",
             "nbody_mlp_forward", "nbody_mlp_loss_grad", "nbody_mlp_adam_step",
-            "nbody_mlp_destroy", "nbody_mlp_invert")
+            "nbody_mlp_destroy", "nbody_mlp_invert", "nbody_set_pair_shape",
+            "nbody_get_pair_shape")
 
 NBODY_NTUNE = 8
 
@@ -151,6 +152,8 @@ def lib():
                                         C.c_float, C.c_float, vp]
         L.nbody_mlp_destroy.argtypes = [vp]
         L.nbody_mlp_destroy.restype = None
+        L.nbody_set_pair_shape.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]
+        L.nbody_get_pair_shape.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
         L.nbody_set_timing.argtypes = [vp, C.c_int]
         L.nbody_kernel_times.argtypes = [vp, dp, C.POINTER(i64)]
         _lib = L
@@ -295,6 +298,18 @@ def nbody_pair_accel_noalloc(x, m, G, eps, center, acc, stream=None):
     _check(lib().nbody_pair_accel_noalloc(n, _ptr(x, (3, n)), _ptr(m, (n,)), G, eps,
                                           cen, _ptr(acc, (3, n)), _stream(stream)),
            "nbody_pair_accel_noalloc")
+
+
+def nbody_set_pair_shape(h, vjp, variant, threads, per_thread, chunks=0):
+    _check(lib().nbody_set_pair_shape(h, int(vjp), variant, threads, per_thread, chunks),
+           "nbody_set_pair_shape")
+
+
+def nbody_get_pair_shape(h, vjp):
+    """(variant, threads, per_thread, chunks)."""
+    out = (C.c_int * 4)()
+    _check(lib().nbody_get_pair_shape(h, int(vjp), out), "nbody_get_pair_shape")
+    return tuple(out)
 
 
 def nbody_set_timing(h, enable: bool):

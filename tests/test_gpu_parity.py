@@ -98,11 +98,15 @@ def _sim(n, G, eps, dt, K=0, ext=0, pot=None, center=(0, 0, 0), center_vel=(0, 0
     return nb.Simulation(n, p)
 
 
-def test_plummer_trajectory_energy_momentum():
+@pytest.mark.parametrize("uneq", [False, True])
+def test_plummer_trajectory_energy_momentum(uneq):
     """Isolated Plummer sphere (N = 1024, eps = 0.01, dt = 1e-3): positions
-    after 100 steps, energy and momentum drift against the oracle."""
+    after 100 steps, energy and momentum drift against the oracle (equal
+    masses, and masses spread over [0.5, 1.5] of the mean)."""
     n, eps, dt, steps = 1024, 0.01, 1e-3, 100
     x, v, m = plummer_sphere(n, 0, 1.0, 1.0, 1.0)
+    if uneq:
+        m = m * np.linspace(0.5, 1.5, n)
     sim = _sim(n, 1.0, eps, dt)
     sim.set_state(to_gpu(x), to_gpu(v), to_gpu(m))
     e0 = sim.energy()
@@ -183,10 +187,13 @@ def test_bitwise_reproducible():
 
 
 # ------------------------------------------------------------------ adjoint --
-@pytest.mark.parametrize("K,lean,ext", [(7, False, 0), (10, True, 0), (50, False, 3), (4, True, 3)])
-def test_adjoint_matches_oracle(K, lean, ext):
+@pytest.mark.parametrize("K,lean,ext,uneq", [(7, False, 0, False), (10, True, 0, False),
+                                             (50, False, 3, False), (4, True, 3, False),
+                                             (7, False, 0, True), (9, True, 3, True)])
+def test_adjoint_matches_oracle(K, lean, ext, uneq):
     """Discrete adjoint against the oracle's: dL/dx0, dL/dv0, dL/ddt, the mass
-    scale, dL/dM_NFW, dL/dM_MN; ragged last segments (50 = 7*7 + 1)."""
+    scale, dL/dM_NFW, dL/dM_MN; ragged last segments (50 = 7*7 + 1); equal
+    masses (the kernels that leave the mass out) and unequal ones."""
     n, steps = 256, 50
     if ext:
         x, v, m = plummer_sphere(n, 12, C1.G, C1.M_prog, C1.a_prog, center=C1.X0,
@@ -195,6 +202,8 @@ def test_adjoint_matches_oracle(K, lean, ext):
     else:
         x, v, m = plummer_sphere(n, 12, 1.0, 1.0, 1.0)
         G, eps, dt, pot = 1.0, 0.05, 2e-3, None
+    if uneq:
+        m = m * np.linspace(0.5, 1.5, n)
     sim = _sim(n, G, eps, dt, K=K, ext=ext, pot=pot, center=x.mean(axis=0),
                center_vel=v.mean(axis=0), guide=bool(ext), lean=lean)
     sim.set_state(to_gpu(x), to_gpu(v), to_gpu(m))
