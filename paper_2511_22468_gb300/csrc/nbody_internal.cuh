@@ -64,6 +64,7 @@ struct PairCfg {
 PairCfg choose_pair_cfg(int64_t npad, int sm_count, bool vjp, bool eqm);
 int pair_blocks_per_sm(const PairCfg& c);
 int vjp_blocks_per_sm(const PairCfg& c);
+int vjp_tile_pairs();
 bool pair_shape_supported(int variant, int nt, int r, bool vjp);
 int choose_chunks(const PairCfg& c, int64_t npad, int sm_count, int blocks_per_sm);
 

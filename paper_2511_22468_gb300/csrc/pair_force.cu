@@ -25,10 +25,23 @@ namespace nb {
 
 namespace {
 
-constexpr int kTJ = 128;  // j-pairs per shared-memory tile (256 particles)
+// Build-time tunables (the defaults are the measured best on GB300):
+// j-pairs per shared-memory tile, unroll of the j-loop, and the minimum
+// resident blocks per SM the register allocation must allow.
+#ifndef NB_PAIR_TJ
+#define NB_PAIR_TJ 512
+#endif
+#ifndef NB_PAIR_UNROLL
+#define NB_PAIR_UNROLL 2
+#endif
+#ifndef NB_PAIR_MINB
+#define NB_PAIR_MINB 1
+#endif
+constexpr int kTJ = NB_PAIR_TJ;  // j-pairs per shared-memory tile
+constexpr int kUnrollJ = NB_PAIR_UNROLL;
 
 template <int NT, int R, bool POT, bool EQM>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, NB_PAIR_MINB)
     k_pair_tile(const float4* __restrict__ st, int ntiles, float eps2,
                 int64_t npad, double* __restrict__ part,
                 double* __restrict__ pot) {
@@ -63,7 +76,7 @@ __global__ void __launch_bounds__(NT)
 #pragma unroll
     for (int r = 0; r < R; ++r)
       ax[r] = ay[r] = az[r] = ph[r] = make_float2(0.f, 0.f);
-#pragma unroll 2
+#pragma unroll (kUnrollJ)
     for (int jj = 0; jj < kTJ; ++jj) {
       const float4 A = sj[2 * jj];
       const float4 B = sj[2 * jj + 1];
@@ -266,7 +279,7 @@ int choose_chunks(const PairCfg& c, int64_t npad, int sm_count, int blocks_per_s
 PairCfg choose_pair_cfg(int64_t npad, int sm_count, bool vjp, bool eqm) {
   PairCfg c;
   c.eqm = eqm;
-  c.vjp_tile_pairs = vjp ? 64 : kTJ;
+  c.vjp_tile_pairs = vjp ? vjp_tile_pairs() : kTJ;
   if (npad >= 65536) {
     c.variant = kTile;
     c.nt = vjp ? (eqm ? 128 : 256) : 128;

@@ -20,7 +20,18 @@ namespace nb {
 
 namespace {
 
-constexpr int kTJ = 64;  // j-pairs per shared-memory tile (4 float4 each)
+// Build-time tunables (defaults: the measured best on GB300).
+#ifndef NB_VJP_TJ
+#define NB_VJP_TJ 256
+#endif
+#ifndef NB_VJP_UNROLL
+#define NB_VJP_UNROLL 2
+#endif
+#ifndef NB_VJP_MINB
+#define NB_VJP_MINB 1
+#endif
+constexpr int kTJ = NB_VJP_TJ;  // j-pairs per shared-memory tile (4 float4 each)
+constexpr int kUnrollJ = NB_VJP_UNROLL;
 
 __device__ __forceinline__ float rsqrt_ftz(float v) {
   float y;
@@ -114,7 +125,7 @@ __device__ __forceinline__ IState load_k(const float4* __restrict__ vst,
 }
 
 template <int NT, int R, bool EQM>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, NB_VJP_MINB)
     k_vjp_tile(const float4* __restrict__ vst, int ntiles, float eps2,
                int64_t npad, double* __restrict__ part) {
   __shared__ float4 sj[4 * kTJ];
@@ -143,7 +154,7 @@ __global__ void __launch_bounds__(NT)
     for (int r = 0; r < R; ++r)
 #pragma unroll
       for (int d = 0; d < 3; ++d) qa[r][d] = qb[r][d] = make_float2(0.f, 0.f);
-#pragma unroll 2
+#pragma unroll (kUnrollJ)
     for (int jj = 0; jj < kTJ; ++jj) {
       const float4 A = sj[4 * jj], B = sj[4 * jj + 1];
       const float4 L1 = sj[4 * jj + 2], L2 = sj[4 * jj + 3];
@@ -260,6 +271,8 @@ cudaError_t launch_vjp_impl(const PairCfg& c, const float4* vst, int64_t npad,
   count_launch();
   return cudaGetLastError();
 }
+
+int vjp_tile_pairs() { return kTJ; }
 
 int vjp_blocks_per_sm(const PairCfg& c) {
   int occ = 0;

@@ -13,7 +13,9 @@ import ctypes as C
 import os
 
 PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(PKG, "_build", "libnbody.so")
+# NBODY_LIBRARY selects another build of the same library (e.g. one built
+# with different tile sizes); the default is the in-tree build.
+LIB_PATH = os.environ.get("NBODY_LIBRARY", os.path.join(PKG, "_build", "libnbody.so"))
 
 NBODY_OK = 0
 NBODY_EINVAL = -1
