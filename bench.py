@@ -299,6 +299,15 @@ def measure_ensemble(dev, gpu_name, plain_subset=8, plain_steps=200):
 
 
 # ------------------------------------------------------------------- ours --
+def hbm_peak():
+    """Measured copy bandwidth of the GB300s (GB/s), else the
+    profiling recipe's fallback."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0
+
+
 def traffic_record(kernel):
     """Per-launch DRAM traffic of a kernel from the committed ncu summary,
     valid only while the kernel source is unchanged."""
@@ -389,6 +398,7 @@ def run_ours(args):
     units = 2.0 * n * n * SEG * args.steps * world
     value = units / (total_ms / 1e3)
 
+    peaks = nb.nbody_peaks(stream)
     # roofline of the dominant kernel (FP32 CUDA-core bound, "alu")
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
@@ -403,10 +413,22 @@ def run_ours(args):
                              "flops_per_interaction": flops,
                              "interactions_per_s": n * n / avg_s,
                              "achieved_tflops": ach, "frac_of_peak_at_2070MHz": ach / peak_max}
+    # O(N) FP64 kernels: algorithmic bytes per particle of an interior launch
+    # (update: x, v read and written, S partial slices read, FP32 restage;
+    # adjoint: cotangents, tape x, a_pair, v_half, x_prev, m read, cotangents
+    # written, S partial slices read, adjoint restage)
+    s_f = nb.nbody_get_pair_shape(sim.h, 0)[3]
+    s_v = nb.nbody_get_pair_shape(sim.h, 1)[3]
+    bpp = {"update": 48 + 24 * s_f + 48 + 12, "adjoint": 48 + 72 + 24 * s_v + 56 + 48 + 32}
+    hbm = hbm_peak()
     for name in ("update", "adjoint"):
         ms, cnt = kt[name]
-        kernels[name] = {"launches": cnt, "total_ms": ms,
-                         "avg_ms": ms / cnt if cnt else None}
+        k = {"launches": cnt, "total_ms": ms, "avg_ms": ms / cnt if cnt else None,
+             "algorithmic_bytes_per_particle": bpp[name], "bound": "fp64 alu / hbm"}
+        if cnt:
+            gbs = bpp[name] * n / (ms / cnt / 1e3) / 1e9
+            k.update({"achieved_gbs": gbs, "frac_of_hbm": gbs / hbm, "hbm_peak_gbs": hbm})
+        kernels[name] = k
     dom = max(("pair", "vjp"), key=lambda k: kt[k][0])
     d = kernels[dom]
     sm_mhz = clk["sm_mhz"] if clk else None
@@ -417,7 +439,8 @@ def run_ours(args):
                 "peak_basis": "%d SMs x %d FP32 lanes x 2 flop x 2070 MHz (max SM clock)"
                               % (sms, FP32_LANES),
                 "frac_at_measured_clock": (d["achieved_tflops"] / (peak_max * sm_mhz / 2070.0))
-                if sm_mhz else None}
+                if sm_mhz else None,
+                "measured_unit_peaks": peaks}
 
     # end to end through the C ABI with pinned host buffers
     xh = torch.tensor(x.T.copy()).pin_memory()

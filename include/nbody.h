@@ -226,6 +226,16 @@ NBODY_API int nbody_set_pair_shape(nbody_ctx *c, int vjp, int variant,
 /* Current shape {variant, threads, per_thread, chunks} (host, 4 ints). */
 NBODY_API int nbody_get_pair_shape(nbody_ctx *c, int vjp, int out[4]);
 
+/* Tune the pair-force and pair-VJP launch shapes of a single-system context
+ * on its current state: every supported shape (with the chunk count chosen
+ * to fill the GPU) is timed over probe_launches launches and the fastest is
+ * kept.  fwd_best / vjp_best (host, 4 ints each, may be NULL) receive the
+ * chosen {variant, threads, per_thread, chunks}.  The state is not advanced;
+ * the tape and the cached acceleration are invalidated.  Synchronises.
+ * Errors: EINVAL, ECUDA. */
+NBODY_API int nbody_autotune_pair(nbody_ctx *c, int probe_launches,
+                                  int fwd_best[4], int vjp_best[4]);
+
 /* ---- per-kernel timing (CUDA events on the context stream) ---- */
 #define NBODY_KCLASS_PAIR 0    /* pair-force kernel (forward and recompute)   */
 #define NBODY_KCLASS_VJP 1     /* pair VJP kernel                             */
@@ -244,6 +254,13 @@ NBODY_API int nbody_set_timing(nbody_ctx *c, int enable);
  * Synchronises the context stream.  Errors: EINVAL, ECUDA. */
 NBODY_API int nbody_kernel_times(nbody_ctx *c, double ms[NBODY_NKCLASS],
                                  int64_t launches[NBODY_NKCLASS]);
+
+/* Throughput probes of the units the kernels use, on the current device:
+ * out = { scalar FP32 FMA TFLOP/s, packed f32x2 FMA TFLOP/s, FP64 FMA
+ * TFLOP/s, MUFU rsqrt Gop/s, SM count } (host).  Each probe runs 8
+ * independent FMA (or rsqrt) chains per thread on 8 blocks of 256 threads
+ * per SM.  Synchronises.  Errors: ENODEV, ENOMEM, ECUDA. */
+NBODY_API int nbody_peaks(double out[5], void *cuda_stream);
 
 /* ---- stateless kernels (device pointers only, stream = cuda_stream) ---- */
 

@@ -86,6 +86,18 @@ struct nbody_ctx {
   int nblk = 0;
   int* status = nullptr;
 
+  // captured step loops: forward and reverse sweeps replayed as CUDA graphs
+  struct GraphEntry {
+    uint64_t key[12];
+    cudaGraphExec_t exec;
+    int nodes;
+    uint64_t stamp;
+  };
+  std::vector<GraphEntry> graphs;
+  uint64_t graph_stamp = 0;
+  cudaStream_t gs = nullptr;
+  cudaEvent_t gev_in = nullptr, gev_out = nullptr;
+
   // batched ensemble (all other buffers unused when set)
   nb::Batch* batch = nullptr;
   int n_sims = 0;
@@ -194,6 +206,90 @@ cudaError_t timed(nbody_ctx* c, int cls, F&& f) {
   return e;
 }
 
+void drop_graphs(nbody_ctx* c) {
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
+}
+
+// Step loops of small systems are launch-bound: they are captured once per
+// configuration (key) on an internal stream and replayed.  Every kernel reads
+// its parameters from device memory, so a replay stays valid when the
+// parameters change; anything else the launches bake in is part of the key,
+// and buffer reallocation drops the cache.
+bool graph_eligible(const nbody_ctx* c, int64_t n_steps) {
+  return !c->timing && c->npad <= 262144 && n_steps >= 4;
+}
+
+template <class F>
+int run_graph(nbody_ctx* c, const uint64_t (&key)[12], F record) {
+  if (!c->gs) {
+    if (cudaStreamCreateWithFlags(&c->gs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->gev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->gev_out, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return NBODY_ECUDA;
+    }
+  }
+  nbody_ctx::GraphEntry* hit = nullptr;
+  for (auto& g : c->graphs)
+    if (std::memcmp(g.key, key, sizeof(key)) == 0) hit = &g;
+  if (!hit) {
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamSynchronize(c->gs));
+    CK(cudaStreamBeginCapture(c->gs, cudaStreamCaptureModeThreadLocal));
+    const long long before = nb::g_launches.load();
+    const int rc = record(c->gs);
+    const int nodes = (int)(nb::g_launches.load() - before);
+    nb::count_launch(-nodes);  // recorded, not launched
+    const cudaError_t e = cudaStreamEndCapture(c->gs, &graph);
+    if (rc || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return rc ? rc : NBODY_ECUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      cudaGetLastError();
+      return NBODY_ECUDA;
+    }
+    if (c->graphs.size() >= 4) {  // evict the least recently used
+      size_t old = 0;
+      for (size_t i = 1; i < c->graphs.size(); ++i)
+        if (c->graphs[i].stamp < c->graphs[old].stamp) old = i;
+      cudaGraphExecDestroy(c->graphs[old].exec);
+      c->graphs.erase(c->graphs.begin() + old);
+    }
+    nbody_ctx::GraphEntry g;
+    std::memcpy(g.key, key, sizeof(key));
+    g.exec = exec;
+    g.nodes = nodes;
+    g.stamp = 0;
+    c->graphs.push_back(g);
+    hit = &c->graphs.back();
+  }
+  hit->stamp = ++c->graph_stamp;
+  CK(cudaEventRecord(c->gev_in, c->stream));
+  CK(cudaStreamWaitEvent(c->gs, c->gev_in, 0));
+  CK(cudaGraphLaunch(hit->exec, c->gs));
+  CK(cudaEventRecord(c->gev_out, c->gs));
+  CK(cudaStreamWaitEvent(c->stream, c->gev_out, 0));
+  nb::count_launch(hit->nodes);
+  return NBODY_OK;
+}
+
+uint64_t bits(double v) {
+  uint64_t u;
+  std::memcpy(&u, &v, sizeof(u));
+  return u;
+}
+
+uint64_t cfg_word(const nb::PairCfg& f) {
+  return (uint64_t)f.variant | ((uint64_t)f.nt << 4) | ((uint64_t)f.r << 16) |
+         ((uint64_t)f.S << 24) | ((uint64_t)f.eqm << 40);
+}
+
 // centre of point k of the current call
 const double* center_at(nbody_ctx* c, int64_t k) {
   if (c->p.center_mode == NBODY_CENTER_GUIDE) return c->centers + 3 * k;
@@ -202,6 +298,7 @@ const double* center_at(nbody_ctx* c, int64_t k) {
 
 int ensure_centers(nbody_ctx* c, int64_t n_steps) {
   if (c->centers_cap >= n_steps && c->centers) return NBODY_OK;
+  drop_graphs(c);
   dfree(c->centers);
   c->centers_cap = 0;
   int rc = dalloc(&c->centers, (size_t)(n_steps + 1) * 3);
@@ -213,6 +310,7 @@ int ensure_centers(nbody_ctx* c, int64_t n_steps) {
 int ensure_tape(nbody_ctx* c, int64_t nseg, int64_t K) {
   const size_t slot = (size_t)3 * c->npad;
   if (c->cp_cap < nseg + 1 || !c->cp) {
+    drop_graphs(c);
     dfree(c->cp);
     c->cp_cap = 0;
     int rc = dalloc(&c->cp, (size_t)(nseg + 1) * 3 * slot);
@@ -220,6 +318,7 @@ int ensure_tape(nbody_ctx* c, int64_t nseg, int64_t K) {
     c->cp_cap = nseg + 1;
   }
   if (c->seg_cap < K || !c->seg) {
+    drop_graphs(c);
     dfree(c->seg);
     c->seg_cap = 0;
     int rc = dalloc(&c->seg, (size_t)3 * K * slot);
@@ -227,6 +326,7 @@ int ensure_tape(nbody_ctx* c, int64_t nseg, int64_t K) {
     c->seg_cap = K;
   }
   if (!c->xw) {
+    drop_graphs(c);
     int rc = dalloc(&c->xw, slot);
     if (rc) return rc;
     rc = dalloc(&c->vw, slot);
@@ -264,24 +364,13 @@ nb::UpdateArgs base_update(nbody_ctx* c, double* x, double* v) {
   return a;
 }
 
-// Forward over points 0..n_steps from the live state; with_tape records
-// checkpoints (and the last segment unless the tape is lean).
-int run_forward(nbody_ctx* c, int64_t n_steps, bool with_tape) {
-  cudaStream_t s = c->stream;
-  int rc = ensure_centers(c, n_steps);
-  if (rc) return rc;
+// The launches of a forward run over points 0..n_steps (on stream s).
+int record_forward(nbody_ctx* c, int64_t n_steps, bool with_tape, cudaStream_t s) {
   if (c->p.center_mode == NBODY_CENTER_GUIDE)
     CK(nb::launch_guide(c->dp, c->guide, n_steps, c->centers, c->guide, s));
-  const int64_t K = with_tape ? c->p.checkpoint_every : 0;
-  int64_t nseg = 0, ls = 0;
-  if (with_tape) {
-    nseg = (n_steps + K - 1) / K;
-    ls = nseg - 1;
-    rc = ensure_tape(c, nseg, K);
-    if (rc) return rc;
-    c->K = K;
-    c->nseg = nseg;
-  }
+  const int64_t K = with_tape ? c->K : 0;
+  const int64_t nseg = with_tape ? c->nseg : 0;
+  const int64_t ls = nseg - 1;
   Tape T{c, (size_t)3 * c->npad};
   const bool keep_last = with_tape && c->p.tape_mode == NBODY_TAPE_KEEP_LAST;
   for (int64_t k = 0; k <= n_steps; ++k) {
@@ -318,6 +407,33 @@ int run_forward(nbody_ctx* c, int64_t n_steps, bool with_tape) {
     }
     CK(timed(c, NBODY_KCLASS_UPDATE, [&] { return nb::launch_update(a, s); }));
   }
+  return NBODY_OK;
+}
+
+// Forward over points 0..n_steps from the live state; with_tape records
+// checkpoints (and the last segment unless the tape is lean).
+int run_forward(nbody_ctx* c, int64_t n_steps, bool with_tape) {
+  int rc = ensure_centers(c, n_steps);
+  if (rc) return rc;
+  const int64_t K = with_tape ? c->p.checkpoint_every : 0;
+  if (with_tape) {
+    const int64_t nseg = (n_steps + K - 1) / K;
+    rc = ensure_tape(c, nseg, K);
+    if (rc) return rc;
+    c->K = K;
+    c->nseg = nseg;
+  }
+  const bool keep_last = with_tape && c->p.tape_mode == NBODY_TAPE_KEEP_LAST;
+  if (graph_eligible(c, n_steps)) {
+    const uint64_t key[12] = {1, (uint64_t)n_steps, (uint64_t)with_tape, (uint64_t)K,
+                              (uint64_t)c->p.tape_mode, (uint64_t)c->acc_valid,
+                              (uint64_t)c->p.center_mode, cfg_word(c->fcfg), bits(c->m_eq),
+                              0, 0, 0};
+    rc = run_graph(c, key, [&](cudaStream_t gs) { return record_forward(c, n_steps, with_tape, gs); });
+  } else {
+    rc = record_forward(c, n_steps, with_tape, c->stream);
+  }
+  if (rc) return rc;
   c->acc_valid = true;
   if (with_tape) {
     c->tape_steps = n_steps;
@@ -330,8 +446,7 @@ int run_forward(nbody_ctx* c, int64_t n_steps, bool with_tape) {
 }
 
 // Recompute segment sg from its checkpoint into the segment buffer.
-int recompute_segment(nbody_ctx* c, int64_t sg) {
-  cudaStream_t s = c->stream;
+int recompute_segment(nbody_ctx* c, int64_t sg, cudaStream_t s) {
   Tape T{c, (size_t)3 * c->npad};
   const int64_t K = c->K, n = c->tape_steps;
   const int64_t k0 = sg * K;
@@ -510,6 +625,11 @@ int nbody_create(nbody_ctx** out, int64_t n, const nbody_params* p,
 void nbody_destroy(nbody_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  if (c->gs) cudaStreamSynchronize(c->gs);
+  drop_graphs(c);
+  if (c->gs) cudaStreamDestroy(c->gs);
+  if (c->gev_in) cudaEventDestroy(c->gev_in);
+  if (c->gev_out) cudaEventDestroy(c->gev_out);
   if (c->batch) nb::batch_destroy(c->batch);
   c->batch = nullptr;
   free_all(c);
@@ -598,23 +718,18 @@ int nbody_integrate(nbody_ctx* c, int64_t n_steps, double* x_out,
   return NBODY_OK;
 }
 
-int nbody_vjp(nbody_ctx* c, const double* xbar, const double* vbar,
-              double* x0bar, double* v0bar, double* mbar_or_null,
-              double theta_bar[4]) {
-  if (!c || !theta_bar || c->batch) return NBODY_EINVAL;
-  if (mbar_or_null) return NBODY_EINVAL;
-  if (c->tape_steps < 1) return NBODY_ESTATE;
-  cudaStream_t s = c->stream;
-  const size_t np = (size_t)c->npad;
-  int rc;
-  CK(cudaMemsetAsync(c->xbar, 0, 3 * np * sizeof(double), s));
-  CK(cudaMemsetAsync(c->vbar, 0, 3 * np * sizeof(double), s));
-  if (xbar && (rc = copy_in3(c, c->xbar, xbar))) return rc;
-  if (vbar && (rc = copy_in3(c, c->vbar, vbar))) return rc;
-  CK(cudaMemsetAsync(c->blk, 0, (size_t)c->nblk * 4 * sizeof(double), s));
+}  // extern "C"
 
+namespace {
+
+// The launches of one reverse sweep over the recorded tape (on stream s):
+// cotangent scaling, segment recomputation, pair VJP and adjoint update at
+// every point, and the reduction of the parameter-gradient sums into red.
+int record_sweep(nbody_ctx* c, cudaStream_t s) {
+  const size_t np = (size_t)c->npad;
   Tape T{c, 3 * np};
   const int64_t n = c->tape_steps, K = c->K, nseg = c->nseg;
+  const bool last_valid = c->last_seg_valid;
   CK(cudaMemsetAsync(c->lsc, 0, nb::kLscDoubles * sizeof(double), s));
   CK(nb::launch_lam_absmax(c->vbar, c->n, c->npad, c->lsc, (int)(n & 1), s));
   CK(nb::launch_stage_vjp(T.cpx(nseg), c->m, c->vbar, center_at(c, n), c->n,
@@ -636,8 +751,8 @@ int nbody_vjp(nbody_ctx* c, const double* xbar, const double* vbar,
   for (int64_t sg = nseg - 1; sg >= 0; --sg) {
     const int64_t k0 = sg * K;
     const int64_t Ks = (k0 + K <= n) ? K : n - k0;
-    if (!(sg == nseg - 1 && c->last_seg_valid)) {
-      rc = recompute_segment(c, sg);
+    if (!(sg == nseg - 1 && last_valid)) {
+      const int rc = recompute_segment(c, sg, s);
       if (rc) return rc;
     }
     for (int64_t j = Ks; j >= 1; --j) {
@@ -659,8 +774,8 @@ int nbody_vjp(nbody_ctx* c, const double* xbar, const double* vbar,
   }
   // point 0: opening half kick of the first step
   CK(timed(c, NBODY_KCLASS_VJP, [&] {
-        return nb::launch_pair_vjp(c->vcfg, c->vst, c->npad, c->hp.eps2f, c->part, s);
-      }));
+    return nb::launch_pair_vjp(c->vcfg, c->vst, c->npad, c->hp.eps2f, c->part, s);
+  }));
   a.xk = T.cpx(0);
   a.ak = T.cpa(0);
   a.ck = 0.5;
@@ -670,9 +785,38 @@ int nbody_vjp(nbody_ctx* c, const double* xbar, const double* vbar,
   a.c_prev = nullptr;
   a.slot = 0;
   CK(timed(c, NBODY_KCLASS_ADJOINT, [&] { return nb::launch_adjoint(a, s); }));
-  c->last_seg_valid = false;  // the segment buffer now holds segment 0
-
   CK(nb::launch_reduce_rows(c->blk, c->nblk, 4, c->red, s));
+  return NBODY_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nbody_vjp(nbody_ctx* c, const double* xbar, const double* vbar,
+              double* x0bar, double* v0bar, double* mbar_or_null,
+              double theta_bar[4]) {
+  if (!c || !theta_bar || c->batch) return NBODY_EINVAL;
+  if (mbar_or_null) return NBODY_EINVAL;
+  if (c->tape_steps < 1) return NBODY_ESTATE;
+  cudaStream_t s = c->stream;
+  const size_t np = (size_t)c->npad;
+  int rc;
+  CK(cudaMemsetAsync(c->xbar, 0, 3 * np * sizeof(double), s));
+  CK(cudaMemsetAsync(c->vbar, 0, 3 * np * sizeof(double), s));
+  if (xbar && (rc = copy_in3(c, c->xbar, xbar))) return rc;
+  if (vbar && (rc = copy_in3(c, c->vbar, vbar))) return rc;
+  CK(cudaMemsetAsync(c->blk, 0, (size_t)c->nblk * 4 * sizeof(double), s));
+  if (graph_eligible(c, c->tape_steps)) {
+    const uint64_t key[12] = {2, (uint64_t)c->tape_steps, (uint64_t)c->K, (uint64_t)c->nseg,
+                              (uint64_t)c->last_seg_valid, (uint64_t)c->p.center_mode,
+                              cfg_word(c->fcfg), cfg_word(c->vcfg), bits(c->m_eq), 0, 0, 0};
+    rc = run_graph(c, key, [&](cudaStream_t gs) { return record_sweep(c, gs); });
+  } else {
+    rc = record_sweep(c, s);
+  }
+  if (rc) return rc;
+  c->last_seg_valid = false;  // the segment buffer now holds segment 0
   if (x0bar && (rc = copy_out3(c, x0bar, c->xbar))) return rc;
   if (v0bar && (rc = copy_out3(c, v0bar, c->vbar))) return rc;
   double h[4];
@@ -797,6 +941,7 @@ int nbody_set_pair_shape(nbody_ctx* c, int vjp, int variant, int threads,
     t.S = chunks;
   }
   cfg = t;
+  drop_graphs(c);
   c->shape_fixed[vjp ? 1 : 0] = true;
   c->acc_valid = false;
   c->tape_steps = 0;
@@ -812,6 +957,86 @@ int nbody_get_pair_shape(nbody_ctx* c, int vjp, int out[4]) {
   out[2] = cfg.r;
   out[3] = cfg.S;
   return NBODY_OK;
+}
+
+int nbody_autotune_pair(nbody_ctx* c, int probe_launches, int fwd_best[4],
+                        int vjp_best[4]) {
+  if (!c || c->batch || probe_launches < 1) return NBODY_EINVAL;
+  cudaStream_t s = c->stream;
+  const bool eqm = c->fcfg.eqm;
+  // stage the current positions (and zero cotangents) for both kernels
+  const double* cen = (c->p.center_mode == NBODY_CENTER_GUIDE) ? c->guide : c->fixed_center;
+  CK(nb::launch_stage(c->x, c->m, cen, c->n, c->npad, c->st, s));
+  CK(cudaMemsetAsync(c->vbar, 0, 3 * (size_t)c->npad * sizeof(double), s));
+  CK(cudaMemsetAsync(c->lsc, 0, nb::kLscDoubles * sizeof(double), s));
+  CK(nb::launch_stage_vjp(c->x, c->m, c->vbar, cen, c->n, c->npad, c->vst, c->lsc, 0, s));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  struct Shape {
+    int variant, nt, r;
+  };
+  const Shape fwd[] = {{0, 128, 4}, {0, 128, 8}, {0, 256, 4}, {0, 256, 2},
+                       {0, 128, 2}, {0, 128, 1}, {1, 256, 4}, {1, 256, 8}};
+  const Shape vjp[] = {{0, 256, 2}, {0, 128, 4}, {0, 128, 2}, {0, 128, 1},
+                       {1, 256, 4}, {1, 256, 2}};
+  int rc = NBODY_OK;
+  for (int which = 0; which < 2 && rc == NBODY_OK; ++which) {
+    const Shape* list = which ? vjp : fwd;
+    const int cnt = which ? (int)(sizeof(vjp) / sizeof(vjp[0])) : (int)(sizeof(fwd) / sizeof(fwd[0]));
+    nb::PairCfg best = which ? c->vcfg : c->fcfg;
+    double best_ms = 1e300;
+    for (int k = 0; k < cnt && rc == NBODY_OK; ++k) {
+      nb::PairCfg t = best;
+      t.variant = list[k].variant;
+      t.nt = list[k].nt;
+      t.r = list[k].r;
+      t.eqm = eqm;
+      if (t.variant == nb::kTile && (c->npad < 2048 || c->npad % (t.nt * t.r) != 0)) continue;
+      if (t.variant == nb::kWarp && c->npad % (8 * t.r) != 0) continue;
+      const int occ = which ? nb::vjp_blocks_per_sm(t) : nb::pair_blocks_per_sm(t);
+      t.S = nb::choose_chunks(t, c->npad, c->sm_count, occ);
+      auto launch = [&]() {
+        return which ? nb::launch_pair_vjp(t, c->vst, c->npad, c->hp.eps2f, c->part, s)
+                     : nb::launch_pair_accel(t, c->st, c->npad, c->hp.eps2f, c->part, nullptr, s);
+      };
+      if (launch() != cudaSuccess) {
+        rc = NBODY_ECUDA;
+        break;
+      }
+      if (cudaEventRecord(e0, s) != cudaSuccess) rc = NBODY_ECUDA;
+      for (int q = 0; q < probe_launches && rc == NBODY_OK; ++q)
+        if (launch() != cudaSuccess) rc = NBODY_ECUDA;
+      if (rc || cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+        rc = NBODY_ECUDA;
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = t;
+      }
+    }
+    if (which) {
+      c->vcfg = best;
+      if (vjp_best) {
+        vjp_best[0] = best.variant; vjp_best[1] = best.nt; vjp_best[2] = best.r; vjp_best[3] = best.S;
+      }
+    } else {
+      c->fcfg = best;
+      if (fwd_best) {
+        fwd_best[0] = best.variant; fwd_best[1] = best.nt; fwd_best[2] = best.r; fwd_best[3] = best.S;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->shape_fixed[0] = c->shape_fixed[1] = true;
+  c->acc_valid = false;
+  c->tape_steps = 0;
+  c->last_seg_valid = false;
+  return rc;
 }
 
 int nbody_set_timing(nbody_ctx* c, int enable) {

@@ -188,6 +188,10 @@ cudaError_t launch_impl(const PairCfg& c, const float4* st, int64_t npad,
       k_pair_tile<256, 4, POT, EQM><<<grid, 256, 0, s>>>(st, ntiles, eps2, npad, part, pot);
     else if (c.nt == 256 && c.r == 2)
       k_pair_tile<256, 2, POT, EQM><<<grid, 256, 0, s>>>(st, ntiles, eps2, npad, part, pot);
+    else if (c.nt == 128 && c.r == 2)
+      k_pair_tile<128, 2, POT, EQM><<<grid, 128, 0, s>>>(st, ntiles, eps2, npad, part, pot);
+    else if (c.nt == 128 && c.r == 1)
+      k_pair_tile<128, 1, POT, EQM><<<grid, 128, 0, s>>>(st, ntiles, eps2, npad, part, pot);
     else
       return cudaErrorInvalidValue;
   } else {
@@ -223,7 +227,7 @@ int pair_blocks_per_sm(const PairCfg& c) {
               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(                      \
                     &occ, k_pair_tile<NT, R, false, false>, NT, 0);
   if (c.variant == kTile) {
-    NB_OCC(128, 4) NB_OCC(128, 8) NB_OCC(256, 4) NB_OCC(256, 2)
+    NB_OCC(128, 4) NB_OCC(128, 8) NB_OCC(256, 4) NB_OCC(256, 2) NB_OCC(128, 2) NB_OCC(128, 1)
   } else {
     e = c.eqm ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair_warp<4, false, true>, 256, 0)
               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair_warp<4, false, false>, 256, 0);
@@ -238,8 +242,8 @@ int pair_blocks_per_sm(const PairCfg& c) {
 
 bool pair_shape_supported(int variant, int nt, int r, bool vjp) {
   if (variant == kWarp) return vjp ? (nt == 256 && (r == 4 || r == 2)) : (nt == 256 && (r == 4 || r == 8));
-  if (vjp) return (nt == 256 && r == 2) || (nt == 128 && (r == 4 || r == 2));
-  return (nt == 128 && (r == 4 || r == 8)) || (nt == 256 && (r == 4 || r == 2));
+  if (vjp) return (nt == 256 && r == 2) || (nt == 128 && (r == 4 || r == 2 || r == 1));
+  return (nt == 128 && (r == 4 || r == 8 || r == 2 || r == 1)) || (nt == 256 && (r == 4 || r == 2));
 }
 
 // j-chunk count S for a given shape: the number of blocks covers the

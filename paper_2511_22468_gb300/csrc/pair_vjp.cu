@@ -257,6 +257,8 @@ cudaError_t launch_vjp_impl(const PairCfg& c, const float4* vst, int64_t npad,
       k_vjp_tile<128, 4, EQM><<<grid, 128, 0, s>>>(vst, ntiles, eps2, npad, part);
     else if (c.nt == 128 && c.r == 2)
       k_vjp_tile<128, 2, EQM><<<grid, 128, 0, s>>>(vst, ntiles, eps2, npad, part);
+    else if (c.nt == 128 && c.r == 1)
+      k_vjp_tile<128, 1, EQM><<<grid, 128, 0, s>>>(vst, ntiles, eps2, npad, part);
     else
       return cudaErrorInvalidValue;
   } else {
@@ -284,7 +286,7 @@ int vjp_blocks_per_sm(const PairCfg& c) {
               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(                    \
                     &occ, k_vjp_tile<NT, R, false>, NT, 0);
   if (c.variant == kTile) {
-    NB_OCC(256, 2) NB_OCC(128, 4) NB_OCC(128, 2)
+    NB_OCC(256, 2) NB_OCC(128, 4) NB_OCC(128, 2) NB_OCC(128, 1)
   } else {
     e = c.eqm ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_vjp_warp<4, true>, 256, 0)
               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_vjp_warp<4, false>, 256, 0);

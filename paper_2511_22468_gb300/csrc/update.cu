@@ -345,6 +345,11 @@ inline unsigned blocks_for(int64_t n, int t) {
   return (unsigned)((n + t - 1) / t);
 }
 
+// threads per block of the per-particle FP64 kernels: 256 when that still
+// gives several blocks per SM, 64 for small systems so that the (slow) FP64
+// work spreads over every SM
+inline int particle_threads(int64_t n) { return n >= 262144 ? 256 : 64; }
+
 }  // namespace
 
 cudaError_t launch_stage(const double* x, const double* m, const double* c,
@@ -355,7 +360,8 @@ cudaError_t launch_stage(const double* x, const double* m, const double* c,
 }
 
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s) {
-  k_update<<<blocks_for(a.n, 256), 256, 0, s>>>(a);
+  const int t = particle_threads(a.n);
+  k_update<<<blocks_for(a.n, t), t, 0, s>>>(a);
   count_launch();
   return cudaGetLastError();
 }
@@ -377,7 +383,7 @@ cudaError_t launch_stage_vjp(const double* x, const double* m,
   return cudaGetLastError();
 }
 
-int adjoint_blocks(int64_t n) { return (int)blocks_for(n, 256); }
+int adjoint_blocks(int64_t n) { return (int)blocks_for(n, particle_threads(n)); }
 
 cudaError_t launch_minmax(const double* m, int64_t n, double* out, cudaStream_t s) {
   k_minmax<<<1, 1024, 0, s>>>(m, n, out);
@@ -386,7 +392,7 @@ cudaError_t launch_minmax(const double* m, int64_t n, double* out, cudaStream_t 
 }
 
 cudaError_t launch_adjoint(const AdjointArgs& a, cudaStream_t s) {
-  k_adjoint<<<adjoint_blocks(a.n), 256, 0, s>>>(a);
+  k_adjoint<<<adjoint_blocks(a.n), particle_threads(a.n), 0, s>>>(a);
   count_launch();
   return cudaGetLastError();
 }

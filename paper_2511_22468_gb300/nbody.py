@@ -47,7 +47,7 @@ EXPORTED = ("nbody_create", "nbody_destroy", "nbody_set_params",
             "nbody_mlp_num_params", "nbody_mlp_set_params", "nbody_mlp_get_params",
             "nbody_mlp_forward", "nbody_mlp_loss_grad", "nbody_mlp_adam_step",
             "nbody_mlp_destroy", "nbody_mlp_invert", "nbody_set_pair_shape",
-            "nbody_get_pair_shape")
+            "nbody_get_pair_shape", "nbody_peaks", "nbody_autotune_pair")
 
 NBODY_NTUNE = 8
 
@@ -156,6 +156,8 @@ def lib():
         L.nbody_mlp_destroy.restype = None
         L.nbody_set_pair_shape.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]
         L.nbody_get_pair_shape.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
+        L.nbody_peaks.argtypes = [dp, vp]
+        L.nbody_autotune_pair.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.nbody_set_timing.argtypes = [vp, C.c_int]
         L.nbody_kernel_times.argtypes = [vp, dp, C.POINTER(i64)]
         _lib = L
@@ -312,6 +314,22 @@ def nbody_get_pair_shape(h, vjp):
     out = (C.c_int * 4)()
     _check(lib().nbody_get_pair_shape(h, int(vjp), out), "nbody_get_pair_shape")
     return tuple(out)
+
+
+def nbody_autotune_pair(h, probe_launches=3):
+    """Tune the single-system pair kernels; returns (forward shape, VJP shape)."""
+    f = (C.c_int * 4)()
+    v = (C.c_int * 4)()
+    _check(lib().nbody_autotune_pair(h, probe_launches, f, v), "nbody_autotune_pair")
+    return tuple(f), tuple(v)
+
+
+def nbody_peaks(stream=None):
+    """dict of measured unit throughputs of the current device."""
+    out = (C.c_double * 5)()
+    _check(lib().nbody_peaks(out, _stream(stream)), "nbody_peaks")
+    return {"fp32_fma_tflops": out[0], "fp32x2_fma_tflops": out[1],
+            "fp64_fma_tflops": out[2], "rsqrt_gops": out[3], "sms": int(out[4])}
 
 
 def nbody_set_timing(h, enable: bool):
