@@ -56,6 +56,25 @@ def parse_args():
     return ap.parse_args()
 
 
+def aggregate(local_ms, local_units, world):
+    """Whole-job throughput of independent replicas: the units every rank
+    processed over the slowest rank's time.  Returns (max ms, units/s)."""
+    import torch
+    t = torch.tensor([float(local_ms), float(local_units)], dtype=torch.float64)
+    if world > 1:
+        import torch.distributed as dist
+        if dist.get_backend() == "nccl":
+            t = t.cuda()
+        tmax = t[:1].clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t[1:].clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        ms, units = float(tmax.item()), float(tsum.item())
+    else:
+        ms, units = float(local_ms), float(local_units)
+    return ms, units / (ms / 1e3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -390,13 +409,8 @@ def run_ours(args):
     fwd_ms = sum(ev[3 * k].elapsed_time(ev[3 * k + 1]) for k in range(args.steps))
     bwd_ms = sum(ev[3 * k + 1].elapsed_time(ev[3 * k + 2]) for k in range(args.steps))
     kt = nb.nbody_kernel_times(sim.h)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms, value = aggregate(total_ms, 2.0 * n * n * SEG * args.steps, world)
     ms_per_step = total_ms / args.steps
-    units = 2.0 * n * n * SEG * args.steps * world
-    value = units / (total_ms / 1e3)
 
     peaks = nb.nbody_peaks(stream)
     # roofline of the dominant kernel (FP32 CUDA-core bound, "alu")
@@ -457,12 +471,10 @@ def run_ours(args):
         sim.integrate(SEG)
         sim.vjp(xbh, None, x0h, v0h)
     barrier()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": 2.0 * n * n * SEG * world / e2e_s, "unit": UNIT,
+    e2e_ms, e2e_value = aggregate((time.perf_counter() - t0) / e2e_steps * 1e3,
+                                  2.0 * n * n * SEG, world)
+    e2e_s = e2e_ms / 1e3
+    e2e = {"value": e2e_value, "unit": UNIT,
            "h2d_bytes_per_step": int((3 + 3 + 1 + 3) * n * 8),
            "d2h_bytes_per_step": int((3 + 3) * n * 8 + 4 * 8),
            "steps": e2e_steps, "ms_per_step": e2e_s * 1e3}
