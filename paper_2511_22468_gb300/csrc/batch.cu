@@ -31,14 +31,14 @@ namespace nb {
 
 namespace {
 
-constexpr int kTJ = 128;  // j-pairs per shared-memory tile (256 particles)
-
+// launch shape candidates: threads, i-particles per thread, j-chunk length
+// (particles), j-pairs per shared-memory tile
 struct TuneCfg {
-  int nt, r, jchunk;
+  int nt, r, jchunk, tj;
 };
 constexpr TuneCfg kTune[NBODY_NTUNE] = {
-    {128, 4, 4096}, {128, 4, 2048}, {128, 4, 8192}, {256, 2, 4096},
-    {256, 2, 2048}, {128, 8, 4096}, {128, 8, 8192}, {256, 4, 4096}};
+    {128, 4, 4096, 512}, {128, 4, 2048, 512}, {128, 4, 8192, 512}, {128, 2, 2048, 512},
+    {256, 2, 4096, 512}, {128, 4, 4096, 128}, {128, 8, 8192, 512}, {128, 2, 4096, 128}};
 
 struct SimMeta {
   int64_t npad, poff, part_off;
@@ -46,9 +46,11 @@ struct SimMeta {
   int S, ntiles;
   float eps2f;
   int pad;
+  double mscale;  // multiplies the raw sums (the common mass with EQM, else 1)
 };
 
-template <int NT, int R>
+// EQM: every simulation has equal masses; the sums leave the mass out
+template <int NT, int R, int kTJ, bool EQM>
 __global__ void __launch_bounds__(NT)
     k_pair_batch(const float4* __restrict__ st, const SimMeta* __restrict__ meta,
                  const int4* __restrict__ items, int nitems,
@@ -96,8 +98,12 @@ __global__ void __launch_bounds__(NT)
         const float2 xj = make_float2(A.x, A.y), yj = make_float2(A.z, A.w);
         const float2 zj = make_float2(B.x, B.y), mj = make_float2(B.z, B.w);
 #pragma unroll
-        for (int r = 0; r < R; ++r)
-          body<false>(xj, yj, zj, mj, nx[r], ny[r], nz[r], e2, ax[r], ay[r], az[r], ph[r]);
+        for (int r = 0; r < R; ++r) {
+          if (EQM)
+            body_eqm(xj, yj, zj, nx[r], ny[r], nz[r], e2, ax[r], ay[r], az[r]);
+          else
+            body<false>(xj, yj, zj, mj, nx[r], ny[r], nz[r], e2, ax[r], ay[r], az[r], ph[r]);
+        }
       }
 #pragma unroll
       for (int r = 0; r < R; ++r) {
@@ -192,7 +198,7 @@ __global__ void __launch_bounds__(256)
     double acc = 0.0;
     for (int q = 0; q < M.S; ++q)
       acc += part[M.part_off + ((int64_t)q * 3 + d) * M.npad + i];
-    ap[d] = Q.G * acc;
+    ap[d] = Q.G * M.mscale * acc;
   }
   double xx[3], vv[3];
   for (int d = 0; d < 3; ++d) {
@@ -251,6 +257,8 @@ struct Batch {
   int64_t centers_cap = -1;
   int tune = 0;
   int grid_pair = 0;
+  bool eqm = false;            // every simulation has equal masses
+  std::vector<double> m_eq;    // their common masses
   cudaGraphExec_t exec = nullptr;
   int64_t exec_steps = -1;
   int exec_tune = -1;
@@ -290,6 +298,19 @@ DevParams dev_params(const nbody_params& p) {
   return d;
 }
 
+// calls f(kernel, threads) with the pair kernel of candidate k
+template <class F>
+cudaError_t with_kernel(const Batch* b, int k, F f) {
+  const TuneCfg c = kTune[k];
+#define NB_K(NT, R, TJ)                                                         \
+  if (c.nt == NT && c.r == R && c.tj == TJ)                                     \
+    return b->eqm ? f(k_pair_batch<NT, R, TJ, true>, NT) : f(k_pair_batch<NT, R, TJ, false>, NT);
+  NB_K(128, 4, 512) NB_K(128, 2, 512) NB_K(256, 2, 512) NB_K(128, 8, 512)
+  NB_K(128, 4, 128) NB_K(128, 2, 128)
+#undef NB_K
+  return cudaErrorInvalidValue;
+}
+
 // metadata, partial-slice layout and LPT work list for tuning candidate k
 int build_plan(Batch* b, int k) {
   const TuneCfg c = kTune[k];
@@ -306,7 +327,8 @@ int build_plan(Batch* b, int k) {
     M.npad = b->npad[s];
     M.poff = b->poff[s];
     M.n = b->n[s];
-    M.ntiles = (int)(M.npad / (2 * kTJ));
+    M.ntiles = (int)(M.npad / (2 * c.tj));
+    M.mscale = b->eqm ? b->m_eq[s] : 1.0;
     int S = (int)std::max<int64_t>(1, (M.npad + c.jchunk / 2) / c.jchunk);
     S = std::min(S, M.ntiles);
     M.S = S;
@@ -349,33 +371,25 @@ int build_plan(Batch* b, int k) {
                  cudaMemcpyHostToDevice));
   b->nitems = (int)list.size();
   int occ = 1;
-  cudaError_t e = cudaSuccess;
-  if (c.nt == 128 && c.r == 4)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair_batch<128, 4>, 128, 0);
-  else if (c.nt == 256 && c.r == 2)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair_batch<256, 2>, 256, 0);
-  else if (c.nt == 128 && c.r == 8)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair_batch<128, 8>, 128, 0);
-  else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair_batch<256, 4>, 256, 0);
-  if (e != cudaSuccess || occ < 1) occ = 1;
+  const cudaError_t e = with_kernel(b, k, [&](auto kern, int nt) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, nt, 0);
+  });
+  if (e != cudaSuccess || occ < 1) {
+    cudaGetLastError();
+    occ = 1;
+  }
   b->grid_pair = std::min(b->nitems, occ * b->sm_count);
   b->tune = k;
   return NBODY_OK;
 }
 
 cudaError_t launch_pair_batch(Batch* b, cudaStream_t s) {
-  const TuneCfg c = kTune[b->tune];
   const unsigned g = (unsigned)std::max(1, b->grid_pair);
-  if (c.nt == 128 && c.r == 4)
-    k_pair_batch<128, 4><<<g, 128, 0, s>>>(b->st, b->meta, b->items, b->nitems, b->ctr, b->part);
-  else if (c.nt == 256 && c.r == 2)
-    k_pair_batch<256, 2><<<g, 256, 0, s>>>(b->st, b->meta, b->items, b->nitems, b->ctr, b->part);
-  else if (c.nt == 128 && c.r == 8)
-    k_pair_batch<128, 8><<<g, 128, 0, s>>>(b->st, b->meta, b->items, b->nitems, b->ctr, b->part);
-  else
-    k_pair_batch<256, 4><<<g, 256, 0, s>>>(b->st, b->meta, b->items, b->nitems, b->ctr, b->part);
-  return cudaGetLastError();
+  const cudaError_t e = with_kernel(b, b->tune, [&](auto kern, int nt) {
+    kern<<<g, nt, 0, s>>>(b->st, b->meta, b->items, b->nitems, b->ctr, b->part);
+    return cudaGetLastError();
+  });
+  return e;
 }
 
 int ensure_centers(Batch* b, int64_t n_steps) {
@@ -524,6 +538,36 @@ int batch_set_state(Batch* b, const double* x, const double* v, const double* m)
     }
     BCK(cudaMemcpyAsync(b->m + b->poff[s], m + b->off[s], bytes, cudaMemcpyDefault, b->user));
   }
+  // equal masses within every simulation select the kernels that leave the
+  // mass out of the pair sums
+  double* mm = nullptr;
+  BCK(cudaMalloc((void**)&mm, 2 * (size_t)b->n_sims * sizeof(double)));
+  for (int s = 0; s < b->n_sims; ++s) {
+    const cudaError_t e = launch_minmax(b->m + b->poff[s], b->n[s], mm + 2 * s, b->user);
+    if (e != cudaSuccess) {
+      cudaFree(mm);
+      return NBODY_ECUDA;
+    }
+  }
+  std::vector<double> hmm(2 * (size_t)b->n_sims);
+  const cudaError_t em = cudaMemcpyAsync(hmm.data(), mm, hmm.size() * sizeof(double),
+                                         cudaMemcpyDeviceToHost, b->user);
+  const cudaError_t es = cudaStreamSynchronize(b->user);
+  cudaFree(mm);
+  if (em != cudaSuccess || es != cudaSuccess) return NBODY_ECUDA;
+  bool eqm = true;
+  b->m_eq.assign(b->n_sims, 1.0);
+  for (int s = 0; s < b->n_sims; ++s) {
+    eqm = eqm && hmm[2 * s] == hmm[2 * s + 1] && hmm[2 * s] > 0.0;
+    b->m_eq[s] = hmm[2 * s];
+  }
+  if (eqm != b->eqm && b->exec) {  // the captured run bakes the kernel in
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  b->eqm = eqm;
+  const int rc = build_plan(b, b->tune);  // per-simulation mass scales
+  if (rc) return rc;
   // restart every guide from its parameters
   std::vector<double> g(6 * (size_t)b->n_sims);
   for (int s = 0; s < b->n_sims; ++s)
