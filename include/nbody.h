@@ -140,7 +140,8 @@ NBODY_API int nbody_integrate(nbody_ctx *c, int64_t n_steps, double *x_out,
  * recomputation of tape segments.  Inputs: xbar, vbar = dL/dx_T, dL/dv_T
  * (3 x n, host or device; NULL means zero).  Outputs (host or device):
  * x0bar, v0bar = dL/dx_0, dL/dv_0 (3 x n each, may be NULL); mbar_or_null
- * must be NULL (per-particle mass gradients are not provided);
+ * (n doubles, may be NULL) = dL/dm_j, the per-particle mass gradient
+ * (costs four more FP32 operations per pair in the VJP kernel);
  * theta_bar (host, 4 doubles) = { dL/d dt,
  *                                 sum_j m_j dL/dm_j (common mass scale),
  *                                 dL/d nfw_M, dL/d mn_M }.

@@ -83,6 +83,9 @@ struct nbody_ctx {
   double* blk = nullptr;  // [nblk][6]
   double* red = nullptr;  // [8]
   double* lsc = nullptr;  // cotangent scales [kLscDoubles]
+  double* mpart = nullptr;  // mass-gradient partial sums [Smax][npad], lazily
+  double* mbar = nullptr;   // dL/dm [npad], lazily
+  bool want_mbar = false;   // the sweep being recorded accumulates dL/dm
   int nblk = 0;
   int* status = nullptr;
 
@@ -528,6 +531,8 @@ void free_all(nbody_ctx* c) {
   dfree(c->blk);
   dfree(c->red);
   dfree(c->lsc);
+  dfree(c->mpart);
+  dfree(c->mbar);
   dfree(c->status);
 }
 
@@ -747,7 +752,10 @@ int record_sweep(nbody_ctx* c, cudaStream_t s) {
   a.vst = c->vst;
   a.blk = c->blk;
   a.lsc = c->lsc;
+  a.mpart = c->want_mbar ? c->mpart : nullptr;
+  a.mbar = c->want_mbar ? c->mbar : nullptr;
   a.status = c->status;
+  double* mp = c->want_mbar ? c->mpart : nullptr;
   for (int64_t sg = nseg - 1; sg >= 0; --sg) {
     const int64_t k0 = sg * K;
     const int64_t Ks = (k0 + K <= n) ? K : n - k0;
@@ -758,7 +766,7 @@ int record_sweep(nbody_ctx* c, cudaStream_t s) {
     for (int64_t j = Ks; j >= 1; --j) {
       const int64_t k = k0 + j;
       CK(timed(c, NBODY_KCLASS_VJP, [&] {
-        return nb::launch_pair_vjp(c->vcfg, c->vst, c->npad, c->hp.eps2f, c->part, s);
+        return nb::launch_pair_vjp(c->vcfg, c->vst, c->npad, c->hp.eps2f, c->part, mp, s);
       }));
       a.xk = (j == Ks) ? T.cpx(sg + 1) : T.sx(j);
       a.ak = (j == Ks) ? T.cpa(sg + 1) : T.sa(j);
@@ -774,7 +782,7 @@ int record_sweep(nbody_ctx* c, cudaStream_t s) {
   }
   // point 0: opening half kick of the first step
   CK(timed(c, NBODY_KCLASS_VJP, [&] {
-    return nb::launch_pair_vjp(c->vcfg, c->vst, c->npad, c->hp.eps2f, c->part, s);
+    return nb::launch_pair_vjp(c->vcfg, c->vst, c->npad, c->hp.eps2f, c->part, mp, s);
   }));
   a.xk = T.cpx(0);
   a.ak = T.cpa(0);
@@ -797,11 +805,19 @@ int nbody_vjp(nbody_ctx* c, const double* xbar, const double* vbar,
               double* x0bar, double* v0bar, double* mbar_or_null,
               double theta_bar[4]) {
   if (!c || !theta_bar || c->batch) return NBODY_EINVAL;
-  if (mbar_or_null) return NBODY_EINVAL;
   if (c->tape_steps < 1) return NBODY_ESTATE;
   cudaStream_t s = c->stream;
   const size_t np = (size_t)c->npad;
   int rc;
+  c->want_mbar = mbar_or_null != nullptr;
+  if (c->want_mbar) {
+    if (!c->mpart) {
+      drop_graphs(c);
+      if ((rc = dalloc(&c->mpart, (size_t)c->Smax * np)) || (rc = dalloc(&c->mbar, np)))
+        return rc;
+    }
+    CK(cudaMemsetAsync(c->mbar, 0, np * sizeof(double), s));
+  }
   CK(cudaMemsetAsync(c->xbar, 0, 3 * np * sizeof(double), s));
   CK(cudaMemsetAsync(c->vbar, 0, 3 * np * sizeof(double), s));
   if (xbar && (rc = copy_in3(c, c->xbar, xbar))) return rc;
@@ -810,7 +826,8 @@ int nbody_vjp(nbody_ctx* c, const double* xbar, const double* vbar,
   if (graph_eligible(c, c->tape_steps)) {
     const uint64_t key[12] = {2, (uint64_t)c->tape_steps, (uint64_t)c->K, (uint64_t)c->nseg,
                               (uint64_t)c->last_seg_valid, (uint64_t)c->p.center_mode,
-                              cfg_word(c->fcfg), cfg_word(c->vcfg), bits(c->m_eq), 0, 0, 0};
+                              cfg_word(c->fcfg), cfg_word(c->vcfg), bits(c->m_eq),
+                              (uint64_t)c->want_mbar, 0, 0};
     rc = run_graph(c, key, [&](cudaStream_t gs) { return record_sweep(c, gs); });
   } else {
     rc = record_sweep(c, s);
@@ -819,6 +836,8 @@ int nbody_vjp(nbody_ctx* c, const double* xbar, const double* vbar,
   c->last_seg_valid = false;  // the segment buffer now holds segment 0
   if (x0bar && (rc = copy_out3(c, x0bar, c->xbar))) return rc;
   if (v0bar && (rc = copy_out3(c, v0bar, c->vbar))) return rc;
+  if (mbar_or_null)
+    CK(cudaMemcpyAsync(mbar_or_null, c->mbar, (size_t)c->n * sizeof(double), cudaMemcpyDefault, s));
   double h[4];
   CK(cudaMemcpyAsync(h, c->red, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -997,7 +1016,7 @@ int nbody_autotune_pair(nbody_ctx* c, int probe_launches, int fwd_best[4],
       const int occ = which ? nb::vjp_blocks_per_sm(t) : nb::pair_blocks_per_sm(t);
       t.S = nb::choose_chunks(t, c->npad, c->sm_count, occ);
       auto launch = [&]() {
-        return which ? nb::launch_pair_vjp(t, c->vst, c->npad, c->hp.eps2f, c->part, s)
+        return which ? nb::launch_pair_vjp(t, c->vst, c->npad, c->hp.eps2f, c->part, nullptr, s)
                      : nb::launch_pair_accel(t, c->st, c->npad, c->hp.eps2f, c->part, nullptr, s);
       };
       if (launch() != cudaSuccess) {

@@ -79,9 +79,11 @@ cudaError_t launch_pair_accel(const PairCfg& cfg, const float4* st,
 // Raw sums Q_k = sum_j [s^-3 u - 3 s^-5 d (d.u)], u = m_j l_k - m_k l_j,
 // d = x_j - x_k, into part[S][3][npad].  (J_pair^T l)_k = -G Q_k.  With
 // cfg.eqm, u = l_k - l_j (the common mass is left out).
+// With mpart != NULL also M_k = sum_j ((-l_j) . d) s^-3 into mpart[S][npad]
+// (dL/dm_k = G sum over kicks of c M_k).
 cudaError_t launch_pair_vjp(const PairCfg& cfg, const float4* vst,
                             int64_t npad, float eps2, double* part,
-                            cudaStream_t s);
+                            double* mpart, cudaStream_t s);
 
 // ---- per-particle kernels (update.cu) ----
 cudaError_t launch_stage(const double* x, const double* m, const double* c,
@@ -149,6 +151,8 @@ struct AdjointArgs {
   const double* m;
   float4* vst;           // restaged positions + new cotangent
   double* blk;           // [nblocks][4] accumulators
+  const double* mpart;   // mass-gradient partial sums [S][npad] or NULL
+  double* mbar;          // running dL/dm [npad] (when mpart)
   double* lsc;           // cotangent scales (see kLscDoubles)
   int slot;              // parity of this point's index
   int* status;

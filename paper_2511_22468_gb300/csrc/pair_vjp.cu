@@ -124,10 +124,29 @@ __device__ __forceinline__ IState load_k(const float4* __restrict__ vst,
   return s;
 }
 
-template <int NT, int R, bool EQM>
+// mass-gradient sum of one j-pair: M_k += ((-l_j) . d) s^-3 (the record
+// holds -l_j), so that dL/dm_k = G sum_kicks c M_k
+__device__ __forceinline__ void mass_body(const float4& A, const float4& B,
+                                          const float4& L1, const float4& L2,
+                                          const IState& s, float2 e2, float2& mk) {
+  const float2 dx = __fadd2_rn(make_float2(A.x, A.y), s.nx);
+  const float2 dy = __fadd2_rn(make_float2(A.z, A.w), s.ny);
+  const float2 dz = __fadd2_rn(make_float2(B.x, B.y), s.nz);
+  float2 s2 = __ffma2_rn(dx, dx, e2);
+  s2 = __ffma2_rn(dy, dy, s2);
+  s2 = __ffma2_rn(dz, dz, s2);
+  const float2 inv = make_float2(rsqrt_ftz(s2.x), rsqrt_ftz(s2.y));
+  const float2 inv3 = __fmul2_rn(__fmul2_rn(inv, inv), inv);
+  float2 dl = __fmul2_rn(dx, make_float2(L1.x, L1.y));
+  dl = __ffma2_rn(dy, make_float2(L1.z, L1.w), dl);
+  dl = __ffma2_rn(dz, make_float2(L2.x, L2.y), dl);
+  mk = __ffma2_rn(dl, inv3, mk);
+}
+
+template <int NT, int R, bool EQM, bool MB>
 __global__ void __launch_bounds__(NT, NB_VJP_MINB)
     k_vjp_tile(const float4* __restrict__ vst, int ntiles, float eps2,
-               int64_t npad, double* __restrict__ part) {
+               int64_t npad, double* __restrict__ part, double* __restrict__ mpart) {
   __shared__ float4 sj[4 * kTJ];
   const int t = threadIdx.x;
   const int64_t k0 = (int64_t)blockIdx.x * (NT * R) + t;
@@ -136,11 +155,11 @@ __global__ void __launch_bounds__(NT, NB_VJP_MINB)
   const int tile_e = (int)(((int64_t)(blockIdx.y + 1) * ntiles) / S);
 
   IState st[R];
-  double gx[R], gy[R], gz[R];
+  double gx[R], gy[R], gz[R], gm[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     st[r] = load_k(vst, k0 + r * NT);
-    gx[r] = gy[r] = gz[r] = 0.0;
+    gx[r] = gy[r] = gz[r] = gm[r] = 0.0;
   }
   const float2 e2 = make_float2(eps2, eps2);
   for (int tile = tile_b; tile < tile_e; ++tile) {
@@ -149,11 +168,13 @@ __global__ void __launch_bounds__(NT, NB_VJP_MINB)
 #pragma unroll
     for (int q = t; q < 4 * kTJ; q += NT) sj[q] = src[q];
     __syncthreads();
-    float2 qa[R][3], qb[R][3];
+    float2 qa[R][3], qb[R][3], qm[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r)
+    for (int r = 0; r < R; ++r) {
+      qm[r] = make_float2(0.f, 0.f);
 #pragma unroll
       for (int d = 0; d < 3; ++d) qa[r][d] = qb[r][d] = make_float2(0.f, 0.f);
+    }
 #pragma unroll (kUnrollJ)
     for (int jj = 0; jj < kTJ; ++jj) {
       const float4 A = sj[4 * jj], B = sj[4 * jj + 1];
@@ -164,10 +185,12 @@ __global__ void __launch_bounds__(NT, NB_VJP_MINB)
           vjp_body_eqm(A, B, L1, L2, st[r], e2, qa[r], qb[r]);
         else
           vjp_body(A, B, L1, L2, st[r], e2, qa[r][0], qa[r][1], qa[r][2]);
+        if (MB) mass_body(A, B, L1, L2, st[r], e2, qm[r]);
       }
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
+      if (MB) gm[r] += (double)qm[r].x + (double)qm[r].y;
       gx[r] += (double)qa[r][0].x + (double)qa[r][0].y;
       gy[r] += (double)qa[r][1].x + (double)qa[r][1].y;
       gz[r] += (double)qa[r][2].x + (double)qa[r][2].y;
@@ -185,23 +208,25 @@ __global__ void __launch_bounds__(NT, NB_VJP_MINB)
     p[k] = gx[r];
     p[npad + k] = gy[r];
     p[2 * npad + k] = gz[r];
+    if (MB) mpart[(int64_t)blockIdx.y * npad + k] = gm[r];
   }
 }
 
-template <int R, bool EQM>
+template <int R, bool EQM, bool MB>
 __global__ void __launch_bounds__(256)
     k_vjp_warp(const float4* __restrict__ vst, int64_t npairs, float eps2,
-               int64_t npad, double* __restrict__ part) {
+               int64_t npad, double* __restrict__ part, double* __restrict__ mpart) {
   const int lane = threadIdx.x & 31;
   const int64_t kb = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * R;
   const int S = gridDim.y;
   const int64_t pb = ((int64_t)blockIdx.y * npairs) / S;
   const int64_t pe = ((int64_t)(blockIdx.y + 1) * npairs) / S;
   IState st[R];
-  float2 qa[R][3], qb[R][3];
+  float2 qa[R][3], qb[R][3], qm[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     st[r] = load_k(vst, kb + r);
+    qm[r] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int d = 0; d < 3; ++d) qa[r][d] = qb[r][d] = make_float2(0.f, 0.f);
   }
@@ -215,6 +240,7 @@ __global__ void __launch_bounds__(256)
         vjp_body_eqm(A, B, L1, L2, st[r], e2, qa[r], qb[r]);
       else
         vjp_body(A, B, L1, L2, st[r], e2, qa[r][0], qa[r][1], qa[r][2]);
+      if (MB) mass_body(A, B, L1, L2, st[r], e2, qm[r]);
     }
   }
   double* out = part + (int64_t)blockIdx.y * 3 * npad;
@@ -228,51 +254,54 @@ __global__ void __launch_bounds__(256)
       sy -= 3.0 * ((double)qb[r][1].x + (double)qb[r][1].y);
       sz -= 3.0 * ((double)qb[r][2].x + (double)qb[r][2].y);
     }
+    double sm = MB ? (double)qm[r].x + (double)qm[r].y : 0.0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       sx += __shfl_xor_sync(0xffffffffu, sx, o);
       sy += __shfl_xor_sync(0xffffffffu, sy, o);
       sz += __shfl_xor_sync(0xffffffffu, sz, o);
+      if (MB) sm += __shfl_xor_sync(0xffffffffu, sm, o);
     }
     if (lane == 0) {
       const int64_t k = kb + r;
       out[k] = sx;
       out[npad + k] = sy;
       out[2 * npad + k] = sz;
+      if (MB) mpart[(int64_t)blockIdx.y * npad + k] = sm;
     }
   }
 }
 
-}  // namespace
-
-template <bool EQM>
+template <bool EQM, bool MB>
 cudaError_t launch_vjp_impl(const PairCfg& c, const float4* vst, int64_t npad,
-                            float eps2, double* part, cudaStream_t s) {
+                            float eps2, double* part, double* mpart, cudaStream_t s) {
   if (c.variant == kTile) {
     const int ntiles = (int)(npad / (2 * kTJ));
     dim3 grid((unsigned)(npad / (c.nt * c.r)), (unsigned)c.S);
     if (c.nt == 256 && c.r == 2)
-      k_vjp_tile<256, 2, EQM><<<grid, 256, 0, s>>>(vst, ntiles, eps2, npad, part);
+      k_vjp_tile<256, 2, EQM, MB><<<grid, 256, 0, s>>>(vst, ntiles, eps2, npad, part, mpart);
     else if (c.nt == 128 && c.r == 4)
-      k_vjp_tile<128, 4, EQM><<<grid, 128, 0, s>>>(vst, ntiles, eps2, npad, part);
+      k_vjp_tile<128, 4, EQM, MB><<<grid, 128, 0, s>>>(vst, ntiles, eps2, npad, part, mpart);
     else if (c.nt == 128 && c.r == 2)
-      k_vjp_tile<128, 2, EQM><<<grid, 128, 0, s>>>(vst, ntiles, eps2, npad, part);
+      k_vjp_tile<128, 2, EQM, MB><<<grid, 128, 0, s>>>(vst, ntiles, eps2, npad, part, mpart);
     else if (c.nt == 128 && c.r == 1)
-      k_vjp_tile<128, 1, EQM><<<grid, 128, 0, s>>>(vst, ntiles, eps2, npad, part);
+      k_vjp_tile<128, 1, EQM, MB><<<grid, 128, 0, s>>>(vst, ntiles, eps2, npad, part, mpart);
     else
       return cudaErrorInvalidValue;
   } else {
     dim3 grid((unsigned)(npad / (8 * c.r)), (unsigned)c.S);
     if (c.r == 4)
-      k_vjp_warp<4, EQM><<<grid, 256, 0, s>>>(vst, npad / 2, eps2, npad, part);
+      k_vjp_warp<4, EQM, MB><<<grid, 256, 0, s>>>(vst, npad / 2, eps2, npad, part, mpart);
     else if (c.r == 2)
-      k_vjp_warp<2, EQM><<<grid, 256, 0, s>>>(vst, npad / 2, eps2, npad, part);
+      k_vjp_warp<2, EQM, MB><<<grid, 256, 0, s>>>(vst, npad / 2, eps2, npad, part, mpart);
     else
       return cudaErrorInvalidValue;
   }
   count_launch();
   return cudaGetLastError();
 }
+
+}  // namespace
 
 int vjp_tile_pairs() { return kTJ; }
 
@@ -282,14 +311,14 @@ int vjp_blocks_per_sm(const PairCfg& c) {
 #define NB_OCC(NT, R)                                                             \
   if (c.nt == NT && c.r == R)                                                     \
     e = c.eqm ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(                    \
-                    &occ, k_vjp_tile<NT, R, true>, NT, 0)                         \
+                    &occ, k_vjp_tile<NT, R, true, false>, NT, 0)                  \
               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(                    \
-                    &occ, k_vjp_tile<NT, R, false>, NT, 0);
+                    &occ, k_vjp_tile<NT, R, false, false>, NT, 0);
   if (c.variant == kTile) {
     NB_OCC(256, 2) NB_OCC(128, 4) NB_OCC(128, 2) NB_OCC(128, 1)
   } else {
-    e = c.eqm ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_vjp_warp<4, true>, 256, 0)
-              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_vjp_warp<4, false>, 256, 0);
+    e = c.eqm ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_vjp_warp<4, true, false>, 256, 0)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_vjp_warp<4, false, false>, 256, 0);
   }
 #undef NB_OCC
   if (e != cudaSuccess) {
@@ -300,9 +329,13 @@ int vjp_blocks_per_sm(const PairCfg& c) {
 }
 
 cudaError_t launch_pair_vjp(const PairCfg& c, const float4* vst, int64_t npad,
-                            float eps2, double* part, cudaStream_t s) {
-  if (c.eqm) return launch_vjp_impl<true>(c, vst, npad, eps2, part, s);
-  return launch_vjp_impl<false>(c, vst, npad, eps2, part, s);
+                            float eps2, double* part, double* mpart, cudaStream_t s) {
+  if (mpart) {
+    if (c.eqm) return launch_vjp_impl<true, true>(c, vst, npad, eps2, part, mpart, s);
+    return launch_vjp_impl<false, true>(c, vst, npad, eps2, part, mpart, s);
+  }
+  if (c.eqm) return launch_vjp_impl<true, false>(c, vst, npad, eps2, part, nullptr, s);
+  return launch_vjp_impl<false, false>(c, vst, npad, eps2, part, nullptr, s);
 }
 
 }  // namespace nb

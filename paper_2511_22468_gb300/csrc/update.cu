@@ -191,6 +191,11 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
       lm += lam[d] * e.d[d];
     }
     la = lp + P.nfw_GM * ln + P.mn_GM * lm;
+    if (a.mpart) {  // per-particle mass gradient of this kick
+      double sm = 0.0;
+      for (int q = 0; q < a.S; ++q) sm += a.mpart[(int64_t)q * np + i];
+      a.mbar[i] += ck * P.G * (sm / s_here);
+    }
     contrib[0] = a.ck * la;          // dL/d dt from the kick(s)
     contrib[1] = ck * lp;            // sum_j m_j dL/dm_j
     contrib[2] = ck * P.G * ln;      // dL/d M_NFW

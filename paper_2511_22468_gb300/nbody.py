@@ -256,11 +256,12 @@ def nbody_integrate(h, n_steps: int, x_out=None, v_out=None):
            "nbody_integrate")
 
 
-def nbody_vjp(h, xbar, vbar, x0bar=None, v0bar=None):
-    """Returns theta_bar = (dL/d dt, sum_j m_j dL/dm_j, dL/dM_NFW, dL/dM_MN)."""
+def nbody_vjp(h, xbar, vbar, x0bar=None, v0bar=None, mbar=None):
+    """Returns theta_bar = (dL/d dt, sum_j m_j dL/dm_j, dL/dM_NFW, dL/dM_MN);
+    fills x0bar, v0bar (3, n) and mbar (n,) when given."""
     tb = (C.c_double * 4)()
     _check(lib().nbody_vjp(h, _ptr(xbar), _ptr(vbar), _ptr(x0bar), _ptr(v0bar),
-                           None, tb), "nbody_vjp")
+                           _ptr(mbar), tb), "nbody_vjp")
     return list(tb)
 
 
@@ -510,8 +511,8 @@ class Simulation:
     def integrate(self, n_steps, x_out=None, v_out=None):
         nbody_integrate(self.h, n_steps, x_out, v_out)
 
-    def vjp(self, xbar, vbar, x0bar=None, v0bar=None):
-        return nbody_vjp(self.h, xbar, vbar, x0bar, v0bar)
+    def vjp(self, xbar, vbar, x0bar=None, v0bar=None, mbar=None):
+        return nbody_vjp(self.h, xbar, vbar, x0bar, v0bar, mbar)
 
     def energy(self):
         return nbody_energy(self.h)
@@ -521,3 +522,60 @@ class Simulation:
 
     def status(self):
         return nbody_get_status(self.h)
+
+
+_RUN_FN = None
+
+
+def _run_fn():
+    global _RUN_FN
+    if _RUN_FN is None:
+        import torch
+
+        class _Run(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, x0, v0, m, theta, sim, n_steps):
+                if theta is not None:
+                    t = [float(a) for a in theta.detach().cpu().tolist()]
+                    p = sim.params
+                    p.dt, p.nfw_M, p.mn_M = t
+                    sim.set_params(p)
+                sim.set_state(x0.detach().contiguous(), v0.detach().contiguous(),
+                              m.detach().contiguous())
+                xT = torch.empty_like(x0)
+                vT = torch.empty_like(v0)
+                sim.integrate(n_steps, xT, vT)
+                ctx.sim = sim
+                ctx.theta_like = theta
+                return xT, vT
+
+            @staticmethod
+            def backward(ctx, xbar, vbar):
+                sim = ctx.sim
+                like = xbar if xbar is not None else vbar
+                xbar = torch.zeros_like(like) if xbar is None else xbar.contiguous()
+                vbar = torch.zeros_like(like) if vbar is None else vbar.contiguous()
+                want = ctx.needs_input_grad
+                x0b = torch.empty_like(xbar) if want[0] else None
+                v0b = torch.empty_like(xbar) if want[1] else None
+                mb = (torch.empty(xbar.shape[1], dtype=xbar.dtype, device=xbar.device)
+                      if want[2] else None)
+                tb = sim.vjp(xbar, vbar, x0b, v0b, mb)
+                thb = None
+                if want[3]:
+                    th = ctx.theta_like
+                    thb = torch.tensor([tb[0], tb[2], tb[3]], dtype=th.dtype, device=th.device)
+                return x0b, v0b, mb, thb, None, None
+
+        _RUN_FN = _Run
+    return _RUN_FN
+
+
+def simulate(sim: Simulation, x0, v0, m, n_steps: int, theta=None):
+    """Differentiable run of one context: (x_T, v_T), each (3, n) FP64 on the
+    device of x0, with a torch autograd backward through nbody_vjp that gives
+    dL/dx0, dL/dv0, dL/dm and, when theta = (dt, M_NFW, M_MN) is passed as
+    a tensor (its values then replace the context's), dL/dtheta.  The tape
+    lives in the context: run the backward before the context's next
+    integration."""
+    return _run_fn().apply(x0, v0, m, theta, sim, int(n_steps))

@@ -230,6 +230,19 @@ def test_adjoint_matches_oracle(K, lean, ext, uneq):
     # a second reverse sweep over the same tape gives the same result
     tb2 = sim.vjp(to_gpu(wx), to_gpu(wv), x0b2 := torch.empty_like(x0b), None)
     assert torch.equal(x0b, x0b2) and tb2 == tb
+    # per-particle mass gradients: against the oracle, the identity
+    # sum_j m_j dL/dm_j = theta_bar[1], no change to the other outputs, and
+    # reproducible from sweep to sweep
+    mb = torch.empty(n, dtype=torch.float64, device=DEV)
+    tb3 = sim.vjp(to_gpu(wx), to_gpu(wv), x0b3 := torch.empty_like(x0b), None, mb)
+    got = to_np(mb)
+    assert np.linalg.norm(got - r["mbar"]) <= 1e-4 * np.linalg.norm(r["mbar"])
+    assert float(np.dot(m, got)) == pytest.approx(tb3[1], rel=1e-5)
+    assert torch.allclose(x0b3, x0b, rtol=1e-12, atol=0.0)
+    assert tb3 == pytest.approx(tb, rel=1e-12)
+    mb2 = torch.empty_like(mb)
+    sim.vjp(to_gpu(wx), to_gpu(wv), None, None, mb2)
+    assert torch.equal(mb, mb2)
 
 
 # ------------------------------------------------------------ error paths --
@@ -315,3 +328,32 @@ def test_autotuned_shapes_match_oracle():
     r = orc.vjp(orc.Physics(G=1.0, eps=0.01), x, v, m, 1e-3, 5, lam, np.zeros_like(lam),
                 want_mbar=False)
     assert np.linalg.norm(to_np(g) - r["x0bar"]) <= 1e-4 * np.linalg.norm(r["x0bar"])
+
+
+def test_autograd_simulate_matches_oracle():
+    """nb.simulate as a torch autograd function: gradients for x0, v0, the
+    per-particle masses and (dt, M_NFW, M_MN) against the oracle adjoint."""
+    n, steps = 200, 40
+    x, v, m = plummer_sphere(n, 21, C1.G, C1.M_prog, C1.a_prog, center=C1.X0, velocity=C1.V0)
+    m = m * np.linspace(0.8, 1.2, n)
+    pot = C1.pot
+    sim = _sim(n, C1.G, C1.eps, 0.5, K=8, ext=3, pot=pot, center=x.mean(axis=0),
+               center_vel=v.mean(axis=0), guide=True, lean=False)
+    X0 = to_gpu(x).requires_grad_()
+    V0 = to_gpu(v).requires_grad_()
+    M = to_gpu(m).requires_grad_()
+    th = torch.tensor([0.5, pot.nfw_M, pot.mn_M], dtype=torch.float64, requires_grad=True)
+    rng = np.random.default_rng(3)
+    wx, wv = rng.normal(size=(n, 3)), rng.normal(size=(n, 3))
+    xT, vT = nb.simulate(sim, X0, V0, M, steps, th)
+    loss = (xT * to_gpu(wx)).sum() + (vT * to_gpu(wv)).sum()
+    loss.backward()
+    ph = orc.Physics(G=C1.G, eps=C1.eps, ext=orc.NFW | orc.MN, nfw_M=pot.nfw_M,
+                     nfw_rs=pot.nfw_rs, mn_M=pot.mn_M, mn_a=pot.mn_a, mn_b=pot.mn_b)
+    r = orc.vjp(ph, x, v, m, 0.5, steps, wx, wv)
+    for got, ref in ((to_np(X0.grad), r["x0bar"]), (to_np(V0.grad), r["v0bar"]),
+                     (to_np(M.grad), r["mbar"])):
+        assert np.linalg.norm(got - ref) <= 1e-4 * np.linalg.norm(ref)
+    ref_th = [r["dt_bar"], r["nfw_M_bar"], r["mn_M_bar"]]
+    assert th.grad.tolist() == pytest.approx(ref_th, rel=1e-4)
+    sim.close()
