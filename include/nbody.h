@@ -152,6 +152,14 @@ NBODY_API int nbody_vjp(nbody_ctx *c, const double *xbar, const double *vbar,
               double *x0bar, double *v0bar, double *mbar_or_null,
               double theta_bar[4]);
 
+/* Gradient of the same loss with respect to the five parameters of the
+ * external potential (Sec. 2.2.1; the parameter set of the Fisher analysis,
+ * Sec. 3.2), from the last successful nbody_vjp of this context:
+ * out (host, 5 doubles) = { dL/d nfw_M, dL/d nfw_rs, dL/d mn_M, dL/d mn_a,
+ * dL/d mn_b }; zero for a component that is switched off.  Does not touch
+ * the GPU.  Errors: EINVAL (batch context), ESTATE (no gradient yet). */
+NBODY_API int nbody_potential_grad(nbody_ctx *c, double out[5]);
+
 /* Diagnostics of the current state: out = { K = sum m v^2 / 2,
  * W_pair = -G sum_{i<j} m_i m_j / sqrt(r_ij^2 + eps^2),
  * W_ext = sum m Phi_ext(x), |P| = |sum m v| } (host).  The pair term uses

@@ -213,7 +213,8 @@ def energy(ph: Physics, x, v, m):
 def vjp(ph: Physics, x0, v0, m, dt, nsteps, xbar, vbar, want_mbar=True):
     """Reverse-mode gradient of L(x_T, v_T) through integrate().
 
-    Returns dict(x0bar, v0bar, mbar, dt_bar, nfw_M_bar, mn_M_bar)."""
+    Returns dict(x0bar, v0bar, mbar, dt_bar, nfw_M_bar, mn_M_bar, nfw_rs_bar,
+    mn_a_bar, mn_b_bar)."""
     x0 = _f64(x0, (-1, 3))
     v0 = _f64(v0, (-1, 3))
     m = _f64(m, (-1,))
@@ -223,11 +224,11 @@ def vjp(ph: Physics, x0, v0, m, dt, nsteps, xbar, vbar, want_mbar=True):
     x0b = np.zeros_like(x0)
     v0b = np.zeros_like(v0)
     mb = np.zeros(n) if want_mbar else None
-    pb = np.zeros(3)
+    pb = np.zeros(6)
     p = ph.c()
     rc = lib().orc_vjp(C.byref(p), n, _d(x0), _d(v0), _d(m), dt, nsteps,
                        _d(xbar), _d(vbar), _d(x0b), _d(v0b), _d(mb), _d(pb))
     if rc:
         raise MemoryError("oracle vjp failed (%d)" % rc)
     return dict(x0bar=x0b, v0bar=v0b, mbar=mb, dt_bar=pb[0], nfw_M_bar=pb[1],
-                mn_M_bar=pb[2])
+                mn_M_bar=pb[2], nfw_rs_bar=pb[3], mn_a_bar=pb[4], mn_b_bar=pb[5])

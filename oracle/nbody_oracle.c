@@ -230,6 +230,20 @@ static void nfw_unit_jac(double rs, const double *p, double J[9]) {
       J[3 * a + b] = -((a == b ? f : 0.0) + fp * p[a] * p[b] / r);
 }
 
+/* d(unit NFW acceleration)/d r_s.  From f above,
+ * df/dr_s = -(1/r^3) (r/r_s^2)/(1 + r/r_s) + 1/(r^2 (r+r_s)^2)
+ *         = -1/(r_s r (r + r_s)^2),
+ * so d a/d r_s = x / (r_s r (r + r_s)^2) (zero at r = 0). */
+static void nfw_unit_drs(double rs, const double *p, double *g) {
+  const double r = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+  if (r == 0.0) {
+    g[0] = g[1] = g[2] = 0.0;
+    return;
+  }
+  const double c = 1.0 / (rs * r * (r + rs) * (r + rs));
+  for (int d = 0; d < 3; ++d) g[d] = c * p[d];
+}
+
 /* Miyamoto-Nagai, per unit G*M:  Phi = -1/S, S^2 = R^2 + (a + B)^2,
  * B = sqrt(z^2 + b^2), R^2 = x^2 + y^2.
  * a_x = -x/S^3, a_y = -y/S^3, a_z = -z (a + B) / (B S^3). */
@@ -266,6 +280,27 @@ static void mn_unit_jac(double ma, double mb, const double *p, double J[9]) {
   J[6] = J[2];
   J[7] = J[5];
   J[8] = -((1.0 + ma * mb * mb / (B * B * B)) / S3 - 3.0 * q * q / S5);
+}
+
+/* Derivatives of the unit MN acceleration with respect to its shape
+ * parameters.  With dS^2/da = 2 (a+B), dB/db = b/B, dS^2/db = 2 (a+B) b/B:
+ *   d a_x/da = 3 x (a+B)/S^5,            (y alike)
+ *   d a_z/da = -(z/B) [1/S^3 - 3 (a+B)^2/S^5],
+ *   d a_x/db = 3 x (a+B) (b/B)/S^5,      (y alike)
+ *   d a_z/db = z b [a/(B^3 S^3) + 3 (a+B)^2/(B^2 S^5)]. */
+static void mn_unit_dab(double ma, double mb, const double *p, double *ga,
+                        double *gb) {
+  const double x = p[0], y = p[1], z = p[2];
+  const double B = sqrt(z * z + mb * mb);
+  const double aB = ma + B;
+  const double S2 = x * x + y * y + aB * aB;
+  const double S = sqrt(S2), S3 = S2 * S, S5 = S3 * S2;
+  ga[0] = 3.0 * x * aB / S5;
+  ga[1] = 3.0 * y * aB / S5;
+  ga[2] = -(z / B) * (1.0 / S3 - 3.0 * aB * aB / S5);
+  gb[0] = ga[0] * mb / B;
+  gb[1] = ga[1] * mb / B;
+  gb[2] = z * mb * (ma / (B * B * B * S3) + 3.0 * aB * aB / (B * B * S5));
 }
 
 /* Components of the external acceleration at one point.  parts[0..2] = NFW,
@@ -390,7 +425,9 @@ void orc_energy(const orc_params *p, int64_t n, const double *x,
 /* Adjoint of one half kick v' = v + c a(X), c = dt/2, given lam = vbar':
  *   xbar += c (da/dx)^T lam,  mbar += c (da/dm)^T lam,
  *   dt_bar += (dc/ddt) lam . a(X) = lam . a(X) / 2,
- *   Mbar_NFW += c lam . da/dM_NFW, Mbar_MN += c lam . da/dM_MN. */
+ *   Mbar_NFW += c lam . da/dM_NFW, Mbar_MN += c lam . da/dM_MN,
+ *   and for the shape parameters r_s, a_MN, b_MN likewise
+ *   (pbar[3..5] += c lam . da/dtheta). */
 static void kick_adjoint(const orc_params *p, int64_t n, const double *X,
                          const double *m, double c, const double *lam,
                          double *xbar, double *mbar, double *pbar,
@@ -409,7 +446,7 @@ static void kick_adjoint(const orc_params *p, int64_t n, const double *X,
     }
   }
   if (p->ext) {
-    double sn = 0.0, sm = 0.0;
+    double sn = 0.0, sm = 0.0, srs = 0.0, sa = 0.0, sb = 0.0;
     for (int64_t i = 0; i < n; ++i) {
       double J[9], u[3];
       orc_ext_jac(p, &X[3 * i], J);
@@ -418,25 +455,34 @@ static void kick_adjoint(const orc_params *p, int64_t n, const double *X,
         for (int a = 0; a < 3; ++a) s += J[3 * a + b] * lam[3 * i + a];
         xbar[3 * i + b] += c * s;
       }
+      const double *l = &lam[3 * i];
       if (p->ext & ORC_NFW) {
         nfw_unit_accel(p->nfw_rs, &X[3 * i], u);
-        sn += p->G * (lam[3 * i] * u[0] + lam[3 * i + 1] * u[1] +
-                      lam[3 * i + 2] * u[2]);
+        sn += p->G * (l[0] * u[0] + l[1] * u[1] + l[2] * u[2]);
+        nfw_unit_drs(p->nfw_rs, &X[3 * i], u);
+        srs += p->G * p->nfw_M * (l[0] * u[0] + l[1] * u[1] + l[2] * u[2]);
       }
       if (p->ext & ORC_MN) {
+        double ga[3], gb[3];
         mn_unit_accel(p->mn_a, p->mn_b, &X[3 * i], u);
-        sm += p->G * (lam[3 * i] * u[0] + lam[3 * i + 1] * u[1] +
-                      lam[3 * i + 2] * u[2]);
+        sm += p->G * (l[0] * u[0] + l[1] * u[1] + l[2] * u[2]);
+        mn_unit_dab(p->mn_a, p->mn_b, &X[3 * i], ga, gb);
+        sa += p->G * p->mn_M * (l[0] * ga[0] + l[1] * ga[1] + l[2] * ga[2]);
+        sb += p->G * p->mn_M * (l[0] * gb[0] + l[1] * gb[1] + l[2] * gb[2]);
       }
     }
     pbar[1] += c * sn;
     pbar[2] += c * sm;
+    pbar[3] += c * srs;
+    pbar[4] += c * sa;
+    pbar[5] += c * sb;
   }
 }
 
 /* Reverse-mode gradient of L(x_T, v_T) through orc_integrate from (x0, v0):
  * inputs xbar = dL/dx_T, vbar = dL/dv_T; outputs dL/dx0, dL/dv0, dL/dm
- * (mbar, optional) and pbar = {dL/ddt, dL/dM_NFW, dL/dM_MN}.
+ * (mbar, optional) and pbar = {dL/ddt, dL/dM_NFW, dL/dM_MN, dL/dr_s,
+ * dL/da_MN, dL/db_MN}.
  * The forward trajectory is recomputed and kept in full.
  * Returns 0, or -2 on allocation failure. */
 int orc_vjp(const orc_params *p, int64_t n, const double *x0, const double *v0,
@@ -464,7 +510,7 @@ int orc_vjp(const orc_params *p, int64_t n, const double *x0, const double *v0,
   memcpy(x0bar, xbar_T, n3 * sizeof(double)); /* running xbar */
   memcpy(v0bar, vbar_T, n3 * sizeof(double)); /* running vbar */
   if (mbar) memset(mbar, 0, (size_t)n * sizeof(double));
-  pbar[0] = pbar[1] = pbar[2] = 0.0;
+  for (int k = 0; k < 6; ++k) pbar[k] = 0.0;
   for (int64_t s = nsteps - 1; s >= 0; --s) {
     const double *Xs1 = &X[(size_t)(s + 1) * n3];
     const double *Xs = &X[(size_t)s * n3];

@@ -105,6 +105,43 @@ static __device__ __forceinline__ void ext_jvp(const DevParams& P, double x, dou
   }
 }
 
+// l . d a_ext / d theta for the shape parameters theta = (r_s, a_MN, b_MN),
+// full accelerations (G M included):
+//   NFW: d a / d r_s = G M x / (r_s r (r + r_s)^2);
+//   MN, with S^2 = R^2 + (a+B)^2, B = sqrt(z^2 + b^2):
+//     d a_{x,y} / d a = 3 G M {x,y} (a+B) / S^5,
+//     d a_z / d a     = -G M (z/B) [1/S^3 - 3 (a+B)^2/S^5],
+//     d a_{x,y} / d b = (b/B) d a_{x,y} / d a,
+//     d a_z / d b     = G M z b [a/(B^3 S^3) + 3 (a+B)^2/(B^2 S^5)].
+static __device__ __forceinline__ void ext_shape_vjp(const DevParams& P, double x,
+                                              double y, double z, const double l[3],
+                                              double out[3]) {
+  out[0] = out[1] = out[2] = 0.0;
+  if (P.ext & NBODY_EXT_NFW) {
+    const double r = sqrt(x * x + y * y + z * z);
+    if (r > 0.0) {
+      const double rp = r + P.nfw_rs;
+      out[0] = P.nfw_GM * (x * l[0] + y * l[1] + z * l[2]) / (P.nfw_rs * r * rp * rp);
+    }
+  }
+  if (P.ext & NBODY_EXT_MN) {
+    const double b = P.mn_b;
+    const double B = sqrt(z * z + b * b);
+    const double aB = P.mn_a + B;
+    const double S2 = x * x + y * y + aB * aB;
+    const double iS = 1.0 / sqrt(S2);
+    const double iS3 = iS * iS * iS;
+    const double iS5 = iS3 * iS * iS;
+    const double xy = x * l[0] + y * l[1];
+    const double iB = 1.0 / B;
+    const double da_z = -(z * iB) * (iS3 - 3.0 * aB * aB * iS5);
+    const double db_z = z * b * (P.mn_a * iB * iB * iB * iS3 + 3.0 * aB * aB * iB * iB * iS5);
+    const double da_xy = 3.0 * aB * iS5 * xy;
+    out[1] = P.mn_GM * (da_xy + da_z * l[2]);
+    out[2] = P.mn_GM * (da_xy * b * iB + db_z * l[2]);
+  }
+}
+
 static __device__ __forceinline__ double ext_potential(const DevParams& P, double x,
                                                 double y, double z) {
   double phi = 0.0;

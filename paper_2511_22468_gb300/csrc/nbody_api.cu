@@ -21,6 +21,8 @@
 // fixed order, so the recomputation reproduces the forward pass bit for bit.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <atomic>
 #include <cmath>
 #include <cstdlib>
@@ -80,12 +82,14 @@ struct nbody_ctx {
   // adjoint
   double* xbar = nullptr;
   double* vbar = nullptr;
-  double* blk = nullptr;  // [nblk][6]
+  double* blk = nullptr;  // [nblk][max(kAdjCols, 6)]
   double* red = nullptr;  // [8]
   double* lsc = nullptr;  // cotangent scales [kLscDoubles]
   double* mpart = nullptr;  // mass-gradient partial sums [Smax][npad], lazily
   double* mbar = nullptr;   // dL/dm [npad], lazily
   bool want_mbar = false;   // the sweep being recorded accumulates dL/dm
+  double pot_bar[5] = {0, 0, 0, 0, 0};  // last sweep's potential-parameter gradient
+  bool have_grad = false;
   int nblk = 0;
   int* status = nullptr;
 
@@ -604,7 +608,7 @@ int nbody_create(nbody_ctx** out, int64_t n, const nbody_params* p,
       (rc = dalloc(&c->pot, (size_t)c->Smax * np)) ||
       (rc = dalloc(&c->guide, 6)) || (rc = dalloc(&c->fixed_center, 3)) ||
       (rc = dalloc(&c->xbar, 3 * np)) || (rc = dalloc(&c->vbar, 3 * np)) ||
-      (rc = dalloc(&c->blk, (size_t)c->nblk * 6)) || (rc = dalloc(&c->red, 8)) || (rc = dalloc(&c->lsc, nb::kLscDoubles)) ||
+      (rc = dalloc(&c->blk, (size_t)c->nblk * std::max(nb::kAdjCols, 6))) || (rc = dalloc(&c->red, 8)) || (rc = dalloc(&c->lsc, nb::kLscDoubles)) ||
       (rc = dalloc(&c->status, 1))) {
     free_all(c);
     delete c;
@@ -793,7 +797,7 @@ int record_sweep(nbody_ctx* c, cudaStream_t s) {
   a.c_prev = nullptr;
   a.slot = 0;
   CK(timed(c, NBODY_KCLASS_ADJOINT, [&] { return nb::launch_adjoint(a, s); }));
-  CK(nb::launch_reduce_rows(c->blk, c->nblk, 4, c->red, s));
+  CK(nb::launch_reduce_rows(c->blk, c->nblk, nb::kAdjCols, c->red, s));
   return NBODY_OK;
 }
 
@@ -822,7 +826,8 @@ int nbody_vjp(nbody_ctx* c, const double* xbar, const double* vbar,
   CK(cudaMemsetAsync(c->vbar, 0, 3 * np * sizeof(double), s));
   if (xbar && (rc = copy_in3(c, c->xbar, xbar))) return rc;
   if (vbar && (rc = copy_in3(c, c->vbar, vbar))) return rc;
-  CK(cudaMemsetAsync(c->blk, 0, (size_t)c->nblk * 4 * sizeof(double), s));
+  CK(cudaMemsetAsync(c->blk, 0, (size_t)c->nblk * nb::kAdjCols * sizeof(double), s));
+  c->have_grad = false;
   if (graph_eligible(c, c->tape_steps)) {
     const uint64_t key[12] = {2, (uint64_t)c->tape_steps, (uint64_t)c->K, (uint64_t)c->nseg,
                               (uint64_t)c->last_seg_valid, (uint64_t)c->p.center_mode,
@@ -838,13 +843,27 @@ int nbody_vjp(nbody_ctx* c, const double* xbar, const double* vbar,
   if (v0bar && (rc = copy_out3(c, v0bar, c->vbar))) return rc;
   if (mbar_or_null)
     CK(cudaMemcpyAsync(mbar_or_null, c->mbar, (size_t)c->n * sizeof(double), cudaMemcpyDefault, s));
-  double h[4];
-  CK(cudaMemcpyAsync(h, c->red, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  double h[nb::kAdjCols];
+  CK(cudaMemcpyAsync(h, c->red, sizeof(h), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   for (int q = 0; q < 4; ++q) theta_bar[q] = h[q];
+  // potential parameters in the order (M_NFW, r_s, M_MN, a_MN, b_MN)
+  c->pot_bar[0] = h[2];
+  c->pot_bar[1] = h[4];
+  c->pot_bar[2] = h[3];
+  c->pot_bar[3] = h[5];
+  c->pot_bar[4] = h[6];
+  c->have_grad = true;
   int st = 0;
   CK(cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost));
   if (st & nb::kStatusNaN) return NBODY_ENAN;
+  return NBODY_OK;
+}
+
+int nbody_potential_grad(nbody_ctx* c, double out[5]) {
+  if (!c || !out || c->batch) return NBODY_EINVAL;
+  if (!c->have_grad) return NBODY_ESTATE;
+  for (int q = 0; q < 5; ++q) out[q] = c->pot_bar[q];
   return NBODY_OK;
 }
 

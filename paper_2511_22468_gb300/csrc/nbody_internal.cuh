@@ -45,6 +45,10 @@ struct DevParams {
 
 enum : int { kStatusNaN = 1, kStatusTimeout = 2 };
 
+// columns of the adjoint's block accumulators: dL/d dt, sum_j m_j dL/dm_j,
+// dL/dM_NFW, dL/dM_MN, dL/dr_s, dL/da_MN, dL/db_MN
+constexpr int kAdjCols = 7;
+
 // ---- launch accounting ----
 void count_launch(int k = 1);
 
@@ -150,7 +154,7 @@ struct AdjointArgs {
   const double* c_prev;  // their recentring origin
   const double* m;
   float4* vst;           // restaged positions + new cotangent
-  double* blk;           // [nblocks][4] accumulators
+  double* blk;           // [nblocks][kAdjCols] accumulators
   const double* mpart;   // mass-gradient partial sums [S][npad] or NULL
   double* mbar;          // running dL/dm [npad] (when mpart)
   double* lsc;           // cotangent scales (see kLscDoubles)

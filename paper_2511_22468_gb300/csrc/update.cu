@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const DevParams& P = *a.P;
   const int64_t np = a.npad;
-  double contrib[4] = {0.0, 0.0, 0.0, 0.0};
+  double contrib[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   // scale of the cotangents this point's VJP was computed with, and the one
   // for the cotangents staged now (from the largest |lambda| at this point)
   const double s_here = a.lsc[a.slot];
@@ -200,6 +200,13 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
     contrib[1] = ck * lp;            // sum_j m_j dL/dm_j
     contrib[2] = ck * P.G * ln;      // dL/d M_NFW
     contrib[3] = ck * P.G * lm;      // dL/d M_MN
+    if (P.ext) {                     // dL/d (r_s, a_MN, b_MN)
+      double sh[3];
+      ext_shape_vjp(P, x[0], x[1], x[2], lam, sh);
+      contrib[4] = ck * sh[0];
+      contrib[5] = ck * sh[1];
+      contrib[6] = ck * sh[2];
+    }
     double vb[3] = {lam[0], lam[1], lam[2]};
     if (a.drift) {
       double xv = 0.0;
@@ -225,7 +232,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
     }
     if (bad) atomicOr(a.status, kStatusNaN);
   }
-  block_accumulate<4>(contrib, a.blk);
+  block_accumulate<kAdjCols>(contrib, a.blk);
   if (a.drift) {
     if (i == 0) a.lsc[1 - a.slot] = s_next;
     block_absmax(vmax, reinterpret_cast<unsigned long long*>(a.lsc + 2) + (1 - a.slot));

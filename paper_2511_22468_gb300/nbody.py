@@ -47,7 +47,8 @@ EXPORTED = ("nbody_create", "nbody_destroy", "nbody_set_params",
             "nbody_mlp_num_params", "nbody_mlp_set_params", "nbody_mlp_get_params",
             "nbody_mlp_forward", "nbody_mlp_loss_grad", "nbody_mlp_adam_step",
             "nbody_mlp_destroy", "nbody_mlp_invert", "nbody_set_pair_shape",
-            "nbody_get_pair_shape", "nbody_peaks", "nbody_autotune_pair")
+            "nbody_get_pair_shape", "nbody_peaks", "nbody_autotune_pair",
+            "nbody_potential_grad")
 
 NBODY_NTUNE = 8
 
@@ -160,6 +161,7 @@ def lib():
         L.nbody_autotune_pair.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.nbody_set_timing.argtypes = [vp, C.c_int]
         L.nbody_kernel_times.argtypes = [vp, dp, C.POINTER(i64)]
+        L.nbody_potential_grad.argtypes = [vp, dp]
         _lib = L
     return _lib
 
@@ -263,6 +265,13 @@ def nbody_vjp(h, xbar, vbar, x0bar=None, v0bar=None, mbar=None):
     _check(lib().nbody_vjp(h, _ptr(xbar), _ptr(vbar), _ptr(x0bar), _ptr(v0bar),
                            _ptr(mbar), tb), "nbody_vjp")
     return list(tb)
+
+
+def nbody_potential_grad(h):
+    """(dL/dM_NFW, dL/dr_s, dL/dM_MN, dL/da_MN, dL/db_MN) of the last vjp."""
+    out = (C.c_double * 5)()
+    _check(lib().nbody_potential_grad(h, out), "nbody_potential_grad")
+    return list(out)
 
 
 def nbody_energy(h):
@@ -514,6 +523,9 @@ class Simulation:
     def vjp(self, xbar, vbar, x0bar=None, v0bar=None, mbar=None):
         return nbody_vjp(self.h, xbar, vbar, x0bar, v0bar, mbar)
 
+    def potential_grad(self):
+        return nbody_potential_grad(self.h)
+
     def energy(self):
         return nbody_energy(self.h)
 
@@ -538,7 +550,7 @@ def _run_fn():
                 if theta is not None:
                     t = [float(a) for a in theta.detach().cpu().tolist()]
                     p = sim.params
-                    p.dt, p.nfw_M, p.mn_M = t
+                    p.dt, p.nfw_M, p.nfw_rs, p.mn_M, p.mn_a, p.mn_b = t
                     sim.set_params(p)
                 sim.set_state(x0.detach().contiguous(), v0.detach().contiguous(),
                               m.detach().contiguous())
@@ -564,7 +576,8 @@ def _run_fn():
                 thb = None
                 if want[3]:
                     th = ctx.theta_like
-                    thb = torch.tensor([tb[0], tb[2], tb[3]], dtype=th.dtype, device=th.device)
+                    thb = torch.tensor([tb[0]] + sim.potential_grad(), dtype=th.dtype,
+                                       device=th.device)
                 return x0b, v0b, mb, thb, None, None
 
         _RUN_FN = _Run
@@ -574,8 +587,9 @@ def _run_fn():
 def simulate(sim: Simulation, x0, v0, m, n_steps: int, theta=None):
     """Differentiable run of one context: (x_T, v_T), each (3, n) FP64 on the
     device of x0, with a torch autograd backward through nbody_vjp that gives
-    dL/dx0, dL/dv0, dL/dm and, when theta = (dt, M_NFW, M_MN) is passed as
-    a tensor (its values then replace the context's), dL/dtheta.  The tape
+    dL/dx0, dL/dv0, dL/dm and, when theta = (dt, M_NFW, r_s, M_MN, a_MN,
+    b_MN) is passed as a tensor (its values then replace the context's),
+    dL/dtheta.  The tape
     lives in the context: run the backward before the context's next
     integration."""
     return _run_fn().apply(x0, v0, m, theta, sim, int(n_steps))

@@ -227,6 +227,9 @@ def test_adjoint_matches_oracle(K, lean, ext, uneq):
     if ext:
         assert tb[2] == pytest.approx(r["nfw_M_bar"], rel=1e-4)
         assert tb[3] == pytest.approx(r["mn_M_bar"], rel=1e-4)
+        pg = sim.potential_grad()
+        assert pg == pytest.approx([r["nfw_M_bar"], r["nfw_rs_bar"], r["mn_M_bar"],
+                                    r["mn_a_bar"], r["mn_b_bar"]], rel=1e-4)
     # a second reverse sweep over the same tape gives the same result
     tb2 = sim.vjp(to_gpu(wx), to_gpu(wv), x0b2 := torch.empty_like(x0b), None)
     assert torch.equal(x0b, x0b2) and tb2 == tb
@@ -257,6 +260,9 @@ def test_errors_are_reported():
     sim.integrate(3)
     with pytest.raises(nb.NBodyError) as e:  # no tape (checkpoint_every = 0)
         sim.vjp(to_gpu(x), None)
+    assert e.value.code == nb.NBODY_ESTATE
+    with pytest.raises(nb.NBodyError) as e:  # no gradient computed yet
+        sim.potential_grad()
     assert e.value.code == nb.NBODY_ESTATE
     with pytest.raises(nb.NBodyError):
         sim.integrate(0)
@@ -342,7 +348,8 @@ def test_autograd_simulate_matches_oracle():
     X0 = to_gpu(x).requires_grad_()
     V0 = to_gpu(v).requires_grad_()
     M = to_gpu(m).requires_grad_()
-    th = torch.tensor([0.5, pot.nfw_M, pot.mn_M], dtype=torch.float64, requires_grad=True)
+    th = torch.tensor([0.5, pot.nfw_M, pot.nfw_rs, pot.mn_M, pot.mn_a, pot.mn_b],
+                      dtype=torch.float64, requires_grad=True)
     rng = np.random.default_rng(3)
     wx, wv = rng.normal(size=(n, 3)), rng.normal(size=(n, 3))
     xT, vT = nb.simulate(sim, X0, V0, M, steps, th)
@@ -354,6 +361,7 @@ def test_autograd_simulate_matches_oracle():
     for got, ref in ((to_np(X0.grad), r["x0bar"]), (to_np(V0.grad), r["v0bar"]),
                      (to_np(M.grad), r["mbar"])):
         assert np.linalg.norm(got - ref) <= 1e-4 * np.linalg.norm(ref)
-    ref_th = [r["dt_bar"], r["nfw_M_bar"], r["mn_M_bar"]]
+    ref_th = [r["dt_bar"], r["nfw_M_bar"], r["nfw_rs_bar"], r["mn_M_bar"], r["mn_a_bar"],
+              r["mn_b_bar"]]
     assert th.grad.tolist() == pytest.approx(ref_th, rel=1e-4)
     sim.close()

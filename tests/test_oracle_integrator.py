@@ -191,6 +191,11 @@ def test_adjoint_vs_central_fd(orc, ext):
         fm_ = lambda h: L(ph=dataclasses.replace(ph, mn_M=ph.mn_M + h))
         assert fd(fn, 1e-4) == pytest.approx(r["nfw_M_bar"], rel=1e-6)
         assert fd(fm_, 1e-4) == pytest.approx(r["mn_M_bar"], rel=1e-6)
+        # shape parameters of the halo and the disk
+        for key, name in (("nfw_rs", "nfw_rs_bar"), ("mn_a", "mn_a_bar"),
+                          ("mn_b", "mn_b_bar")):
+            f = lambda h, key=key: L(ph=dataclasses.replace(ph, **{key: getattr(ph, key) + h}))
+            assert fd(f, 1e-4) == pytest.approx(r[name], rel=1e-6)
 
 
 def test_adjoint_dot_product(orc):
