@@ -363,6 +363,54 @@ NBODY_API int nbody_stream_head(nbody_stream *s, const double *x,
 /* Release the pipeline; NULL is a no-op. */
 NBODY_API void nbody_stream_destroy(nbody_stream *s);
 
+/* ---- maximum mean discrepancy between phase-space point clouds ----
+ *
+ * The paper's first inference method (Sec. 3.1; Fig. 2, step 4) compares
+ * the simulated and the observed stream as point clouds with the MMD and
+ * ranks the 10^4 points of its grid search by it.  A point is
+ * q = (x, y, z, vx, vy, vz); coordinates are standardised per dimension,
+ * u = (q - mu) / s, mu and s the target's mean and standard deviation (or
+ * the caller's scale), and the kernel is
+ *   k(a, b) = sum_l exp(-|u_a - u_b|^2 / (2 sigma_l^2)),  1 <= l <= 4.
+ * The estimator is the biased V-statistic
+ *   MMD^2 = 1/n^2 sum k(x, x') + 1/m^2 sum k(y, y') - 2/(n m) sum k(x, y).
+ * Pair sums run in FP32 within 512-point tiles and in FP64 across tiles,
+ * in fixed order (bitwise reproducible).  All arrays are FP64 SoA: a cloud
+ * of c points is x (3 x c) and v (3 x c). */
+typedef struct nbody_mmd nbody_mmd; /* opaque, owned by the library */
+
+/* Evaluator for clouds of n points against the target (tx, tv: 3 x m each,
+ * host or device; copied and staged).  max_sets bounds the sets of one
+ * batched call.  scale_or_null (host, 6) replaces the target's standard
+ * deviations; sigma (host, n_sigma in 1..4, all > 0) are the bandwidths in
+ * standardised units.  The target's own term is computed here, once.
+ * Errors: EINVAL, ENODEV, ENOMEM, ECUDA. */
+NBODY_API int nbody_mmd_create(nbody_mmd **out, int64_t n, int64_t max_sets,
+                               int64_t m, const double *tx, const double *tv,
+                               const double *scale_or_null, int n_sigma,
+                               const double *sigma, void *cuda_stream);
+
+/* MMD^2 of one cloud (x, v: 3 x n, host or device) into *loss (host), and
+ * when xbar / vbar are not NULL its gradient dMMD^2/dx, dMMD^2/dv (3 x n
+ * each, host or device).  Synchronises.  Errors: EINVAL, ENOMEM, ECUDA,
+ * ENAN. */
+NBODY_API int nbody_mmd_eval(nbody_mmd *h, const double *x, const double *v,
+                             double *loss, double *xbar, double *vbar);
+
+/* MMD^2 of `sets` clouds at once (1 <= sets <= max_sets): x, v are 3 x
+ * (sets * n) SoA, cloud b in columns b*n .. b*n+n-1 (the layout of a batch
+ * context whose simulations all hold n particles); losses (host or device,
+ * `sets` doubles).  One launch for all clouds.  Synchronises.
+ * Errors: EINVAL, ENOMEM, ECUDA, ENAN. */
+NBODY_API int nbody_mmd_eval_batch(nbody_mmd *h, int64_t sets, const double *x,
+                                   const double *v, double *losses);
+
+/* The standardisation in use: mu and s (host, 6 each; either may be NULL). */
+NBODY_API int nbody_mmd_target_stats(nbody_mmd *h, double mu[6], double scale[6]);
+
+/* Release the evaluator; NULL is a no-op. */
+NBODY_API void nbody_mmd_destroy(nbody_mmd *h);
+
 /* ---- density surrogate (the paper's outlook, Sec. 3: a neural network
  *      coupled to the solver) ---- */
 

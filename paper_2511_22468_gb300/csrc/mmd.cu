@@ -1,0 +1,628 @@
+// mmd.cu -- maximum mean discrepancy between phase-space point clouds
+// (paper Sec. 3.1, Fig. 2 step 4: the simulated and the observed stream
+// compared as point clouds; the grid search ranks parameter vectors by it).
+//
+// A point is q = (x, y, z, vx, vy, vz).  Coordinates are standardised by
+// the target cloud's per-dimension mean mu and standard deviation s (or a
+// caller's scale) and the kernel is a sum of Gaussians,
+//   k(a, b) = sum_l exp(-|u_a - u_b|^2 / (2 sigma_l^2)),  u = (q - mu) / s.
+// The biased estimator over the union Z = X u Y with weights w = 1/n on X
+// and -1/m on Y is MMD^2 = sum_{a,b in Z} w_a w_b k(a, b), and
+//   dMMD^2/du_i = 2 w_i sum_b w_b dk(u_i, u_b)/du_i.
+//
+// GPU form.  The staged coordinates are u' = u sqrt(c0) with
+// c0 = log2(e) / (2 sigma_0^2), sigma_0 the smallest bandwidth, so that
+// k = sum_l exp2(-rho_l |u'_a - u'_b|^2) with rho_l = sigma_0^2/sigma_l^2 <= 1:
+// one MUFU ex2 per bandwidth and pair.  A row kernel holds R points of X in
+// registers and sweeps column tiles of X (weight 1/n) and of Y (weight -1/m)
+// through shared memory, accumulating in FP32 within a tile (packed f32x2:
+// two columns per instruction) and in FP64 across tiles:
+//   S0A_i = sum_{j in X} w_j k_ij, S0B_i = sum_{j in Y} w_j k_ij,
+//   S1_i  = sum_j w_j (sum_l rho_l k_l,ij) (u'_j - u'_i).
+// Then MMD^2 = Kyy + sum_i (1/n) (S0A_i + 2 S0B_i) (the Y-Y term Kyy once at
+// creation) and dMMD^2/du'_i = 4 ln2 (1/n) S1_i.  Column pads sit at 1e18,
+// where every kernel value is exactly zero.  Sums are in fixed order, so
+// results are bitwise reproducible.  Per pair: 19 FP32-pipe operations and
+// one MUFU for one bandwidth, 4 operations and one MUFU more per extra one.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "nbody_internal.cuh"
+#include "staging.cuh"
+
+namespace nb {
+namespace {
+
+constexpr int kMT = 256;          // column pairs per shared-memory tile
+constexpr int kMPts = 2 * kMT;    // points per tile (padding unit)
+constexpr int kMaxSigma = 4;
+
+struct Standardise {
+  double mu[6];
+  double f[6];  // sqrt(c0) / s_d
+};
+
+static __device__ __forceinline__ float ex2_ftz(float v) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(v));
+  return y;
+}
+
+// pair p of a staged cloud: 3 float4 = (u0,u0',u1,u1'), (u2,..), (u4,..)
+static __device__ __forceinline__ float load_u(const float4* st, int64_t i, int d) {
+  const float* f = reinterpret_cast<const float*>(st) + 12 * (i >> 1) + (i & 1);
+  return f[2 * d];
+}
+
+// Stage sets of n points into pair-interleaved FP32 records, npad per set.
+// x, v: 3 x ld SoA; set b's point i is column b * n + i.
+__global__ void k_mmd_stage(const double* __restrict__ x, const double* __restrict__ v,
+                            int64_t ld, int64_t n, int64_t npad, Standardise S,
+                            float4* __restrict__ st) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // pair
+  const int64_t b = blockIdx.y;
+  if (2 * p >= npad) return;
+  float u[2][6];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int64_t i = 2 * p + h;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      if (i < n) {
+        const double q = d < 3 ? x[d * ld + b * n + i] : v[(d - 3) * ld + b * n + i];
+        u[h][d] = (float)((q - S.mu[d]) * S.f[d]);
+      } else {
+        u[h][d] = kPadPos;
+      }
+    }
+  }
+  float4* o = st + b * (3 * (npad / 2)) + 3 * p;
+  o[0] = make_float4(u[0][0], u[1][0], u[0][1], u[1][1]);
+  o[1] = make_float4(u[0][2], u[1][2], u[0][3], u[1][3]);
+  o[2] = make_float4(u[0][4], u[1][4], u[0][5], u[1][5]);
+}
+
+// Row sums.  Grid: x = row blocks of NT*R points, y = set, z = column chunk.
+// Rows of set b: rows + b * rstride; columns: ntA tiles of colA + b * astride
+// then ntB tiles of colB.  part: [set][chunk][8][npad_r] FP64 (S0A, S0B, S1).
+template <int R, int NS>
+__global__ void __launch_bounds__(128)
+    k_mmd_rows(const float4* __restrict__ rows, int64_t rstride, int64_t npad_r,
+               const float4* __restrict__ colA, int64_t astride, int ntA,
+               const float4* __restrict__ colB, int ntB, double wA, double wB,
+               float4 rho, double* __restrict__ part) {
+  constexpr int NT = 128;
+  __shared__ float4 sj[3 * kMT];
+  const int t = threadIdx.x;
+  const int64_t b = blockIdx.y;
+  const int S = gridDim.z;
+  const int nt = ntA + ntB;
+  const int tile_b = (int)(((int64_t)blockIdx.z * nt) / S);
+  const int tile_e = (int)(((int64_t)(blockIdx.z + 1) * nt) / S);
+  const float4* rs = rows + b * rstride;
+  const float4* ca = colA + b * astride;
+  const int64_t i0 = (int64_t)blockIdx.x * (NT * R) + t;
+
+  float2 nu[R][6];
+  double s0a[R], s0b[R], s1[R][6];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      const float u = load_u(rs, i0 + r * NT, d);
+      nu[r][d] = make_float2(-u, -u);
+      s1[r][d] = 0.0;
+    }
+    s0a[r] = s0b[r] = 0.0;
+  }
+  const float rl[4] = {1.f, rho.y, rho.z, rho.w};
+
+  for (int tile = tile_b; tile < tile_e; ++tile) {
+    const bool inA = tile < ntA;
+    const float4* src = inA ? ca + (int64_t)tile * (3 * kMT)
+                            : colB + (int64_t)(tile - ntA) * (3 * kMT);
+    __syncthreads();
+    for (int q = t; q < 3 * kMT; q += NT) sj[q] = src[q];
+    __syncthreads();
+
+    float2 a0[R], a1[R][6];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      a0[r] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int d = 0; d < 6; ++d) a1[r][d] = make_float2(0.f, 0.f);
+    }
+#pragma unroll 2
+    for (int jj = 0; jj < kMT; ++jj) {
+      const float4 P0 = sj[3 * jj], P1 = sj[3 * jj + 1], P2 = sj[3 * jj + 2];
+      const float2 c[6] = {make_float2(P0.x, P0.y), make_float2(P0.z, P0.w),
+                           make_float2(P1.x, P1.y), make_float2(P1.z, P1.w),
+                           make_float2(P2.x, P2.y), make_float2(P2.z, P2.w)};
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        float2 dd[6];
+#pragma unroll
+        for (int d = 0; d < 6; ++d) dd[d] = __fadd2_rn(c[d], nu[r][d]);
+        float2 r2 = __fmul2_rn(dd[0], dd[0]);
+#pragma unroll
+        for (int d = 1; d < 6; ++d) r2 = __ffma2_rn(dd[d], dd[d], r2);
+        float2 sk = make_float2(ex2_ftz(-r2.x), ex2_ftz(-r2.y));
+        float2 sg = sk;
+#pragma unroll
+        for (int l = 1; l < NS; ++l) {
+          const float2 rr = make_float2(rl[l], rl[l]);
+          const float2 e = __fmul2_rn(r2, rr);
+          const float2 kl = make_float2(ex2_ftz(-e.x), ex2_ftz(-e.y));
+          sk = __fadd2_rn(sk, kl);
+          sg = __ffma2_rn(kl, rr, sg);
+        }
+        a0[r] = __fadd2_rn(a0[r], sk);
+#pragma unroll
+        for (int d = 0; d < 6; ++d) a1[r][d] = __ffma2_rn(sg, dd[d], a1[r][d]);
+      }
+    }
+    const double w = inA ? wA : wB;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const double k0 = (double)(a0[r].x + a0[r].y);
+      if (inA)
+        s0a[r] = fma(w, k0, s0a[r]);
+      else
+        s0b[r] = fma(w, k0, s0b[r]);
+#pragma unroll
+      for (int d = 0; d < 6; ++d) s1[r][d] = fma(w, (double)(a1[r][d].x + a1[r][d].y), s1[r][d]);
+    }
+  }
+
+  double* p = part + ((int64_t)b * S + blockIdx.z) * 8 * npad_r;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int64_t i = i0 + r * NT;
+    p[i] = s0a[r];
+    p[npad_r + i] = s0b[r];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) p[(2 + d) * npad_r + i] = s1[r][d];
+  }
+}
+
+// loss_b = base + wrow sum_{i<n} sum_chunks (S0A + cB S0B), one block per set
+__global__ void __launch_bounds__(256)
+    k_mmd_finish(const double* __restrict__ part, int S, int64_t npad_r, int64_t n,
+                 double wrow, double cB, const double* __restrict__ base,
+                 double* __restrict__ loss) {
+  __shared__ double sh[256];
+  const int64_t b = blockIdx.x;
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += 256) {
+    double r = 0.0;
+    for (int q = 0; q < S; ++q) {
+      const double* p = part + ((int64_t)b * S + q) * 8 * npad_r;
+      r += p[i] + cB * p[npad_r + i];
+    }
+    acc += r;
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) loss[b] = (base ? *base : 0.0) + wrow * sh[0];
+}
+
+// dMMD^2/dq for set 0: gscale_d = 4 ln2 (1/n) f_d; out 3 x n each
+__global__ void k_mmd_grad(const double* __restrict__ part, int S, int64_t npad_r,
+                           int64_t n, Standardise Sd, double g0,
+                           double* __restrict__ xbar, double* __restrict__ vbar) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+#pragma unroll
+  for (int d = 0; d < 6; ++d) {
+    double s = 0.0;
+    for (int q = 0; q < S; ++q) s += part[((int64_t)q * 8 + 2 + d) * npad_r + i];
+    const double g = g0 * Sd.f[d] * s;
+    if (d < 3)
+      xbar[d * n + i] = g;
+    else
+      vbar[(d - 3) * n + i] = g;
+  }
+}
+
+// mean and standard deviation per dimension of a cloud (3 x m x, 3 x m v),
+// one block, two passes, fixed order
+__global__ void __launch_bounds__(256)
+    k_cloud_stats(const double* __restrict__ x, const double* __restrict__ v, int64_t m,
+                  double* __restrict__ out) {
+  __shared__ double sh[256];
+  for (int d = 0; d < 6; ++d) {
+    const double* q = d < 3 ? x + d * m : v + (d - 3) * m;
+    double a = 0.0;
+    for (int64_t i = threadIdx.x; i < m; i += 256) a += q[i];
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+      __syncthreads();
+    }
+    const double mu = sh[0] / (double)m;
+    __syncthreads();
+    a = 0.0;
+    for (int64_t i = threadIdx.x; i < m; i += 256) a += (q[i] - mu) * (q[i] - mu);
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      out[d] = mu;
+      out[6 + d] = sqrt(sh[0] / (double)m);
+    }
+    __syncthreads();
+  }
+}
+
+int64_t pad_points(int64_t n) { return ((n + kMPts - 1) / kMPts) * kMPts; }
+
+}  // namespace
+}  // namespace nb
+
+struct nbody_mmd {
+  cudaStream_t s = nullptr;
+  int64_t n = 0, m = 0, max_sets = 0, npad = 0, mpad = 0;
+  int ns = 1;
+  float4 rho{1.f, 1.f, 1.f, 1.f};
+  double c0 = 0.0;
+  nb::Standardise st{};
+  int sms = 0;
+  float4* xs = nullptr;   // staged clouds [max_sets][3 npad/2]
+  float4* ys = nullptr;   // staged target [3 mpad/2]
+  double* part = nullptr; // [max(max_sets * S1, Smax)][8][npad] (and target rows)
+  int64_t part_cap = 0;   // doubles
+  double* kyy = nullptr;  // [1]
+  double* loss = nullptr; // [max_sets]
+  double* stats = nullptr;  // [12]
+  double* gx = nullptr;     // gradient scratch [3][n]
+  double* gv = nullptr;
+};
+
+namespace {
+
+using nb::kMT;
+
+template <class T>
+int malloc_dev(T** p, size_t count) {
+  if (cudaMalloc((void**)p, (count ? count : 1) * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return NBODY_ENOMEM;
+  }
+  return NBODY_OK;
+}
+
+void free_mmd(nbody_mmd* h) {
+  if (h->xs) cudaFree(h->xs);
+  if (h->ys) cudaFree(h->ys);
+  if (h->part) cudaFree(h->part);
+  if (h->kyy) cudaFree(h->kyy);
+  if (h->loss) cudaFree(h->loss);
+  if (h->stats) cudaFree(h->stats);
+  if (h->gx) cudaFree(h->gx);
+  if (h->gv) cudaFree(h->gv);
+}
+
+#define MCK(call)                              \
+  do {                                         \
+    cudaError_t e_ = (call);                   \
+    if (e_ != cudaSuccess) return NBODY_ECUDA; \
+  } while (0)
+
+template <int NS>
+cudaError_t rows_ns(int R, dim3 grid, const float4* rows, int64_t rstride, int64_t npad_r,
+                    const float4* colA, int64_t astride, int ntA, const float4* colB,
+                    int ntB, double wA, double wB, float4 rho, double* part, cudaStream_t s) {
+  if (R == 2)
+    nb::k_mmd_rows<2, NS><<<grid, 128, 0, s>>>(rows, rstride, npad_r, colA, astride, ntA,
+                                               colB, ntB, wA, wB, rho, part);
+  else
+    nb::k_mmd_rows<1, NS><<<grid, 128, 0, s>>>(rows, rstride, npad_r, colA, astride, ntA,
+                                               colB, ntB, wA, wB, rho, part);
+  nb::count_launch();
+  return cudaGetLastError();
+}
+
+// Row sums of `sets` sets of npad_r rows against ntA + ntB column tiles.
+cudaError_t launch_rows(const nbody_mmd* h, int64_t sets, const float4* rows,
+                        int64_t rstride, int64_t npad_r, const float4* colA,
+                        int64_t astride, int ntA, const float4* colB, int ntB, double wA,
+                        double wB, int S, double* part) {
+  const int R = npad_r >= 256 ? 2 : 1;
+  dim3 grid((unsigned)(npad_r / (128 * R)), (unsigned)sets, (unsigned)S);
+  switch (h->ns) {
+    case 1: return rows_ns<1>(R, grid, rows, rstride, npad_r, colA, astride, ntA, colB, ntB, wA, wB, h->rho, part, h->s);
+    case 2: return rows_ns<2>(R, grid, rows, rstride, npad_r, colA, astride, ntA, colB, ntB, wA, wB, h->rho, part, h->s);
+    case 3: return rows_ns<3>(R, grid, rows, rstride, npad_r, colA, astride, ntA, colB, ntB, wA, wB, h->rho, part, h->s);
+    default: return rows_ns<4>(R, grid, rows, rstride, npad_r, colA, astride, ntA, colB, ntB, wA, wB, h->rho, part, h->s);
+  }
+}
+
+// column chunks so that a single set fills the GPU (4 blocks per SM)
+int chunks_for(const nbody_mmd* h, int64_t sets, int64_t npad_r, int ntiles) {
+  const int R = npad_r >= 256 ? 2 : 1;
+  const int64_t blocks = sets * (npad_r / (128 * R));
+  int64_t S = (4 * (int64_t)h->sms + blocks - 1) / blocks;
+  if (S < 1) S = 1;
+  if (S > ntiles) S = ntiles;
+  if (S > 64) S = 64;
+  return (int)S;
+}
+
+int ensure_part(nbody_mmd* h, int64_t doubles) {
+  if (doubles <= h->part_cap) return NBODY_OK;
+  if (h->part) cudaFree(h->part);
+  h->part = nullptr;
+  h->part_cap = 0;
+  int rc = malloc_dev(&h->part, (size_t)doubles);
+  if (!rc) h->part_cap = doubles;
+  return rc;
+}
+
+int stage(nbody_mmd* h, const double* x, const double* v, int64_t ld, int64_t n,
+          int64_t npad, int64_t sets, float4* out) {
+  dim3 grid((unsigned)((npad / 2 + 127) / 128), (unsigned)sets);
+  nb::k_mmd_stage<<<grid, 128, 0, h->s>>>(x, v, ld, n, npad, h->st, out);
+  nb::count_launch();
+  MCK(cudaGetLastError());
+  return NBODY_OK;
+}
+
+// device copy of a 3 x count host-or-device array (the kernels read device
+// memory; unified addressing lets a device pointer pass straight through)
+int device_view(const double* p, size_t count, double** tmp, const double** out,
+                cudaStream_t s) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) == cudaSuccess && at.type == cudaMemoryTypeDevice) {
+    *out = p;
+    return NBODY_OK;
+  }
+  cudaGetLastError();
+  int rc = malloc_dev(tmp, count);
+  if (rc) return rc;
+  MCK(cudaMemcpyAsync(*tmp, p, count * sizeof(double), cudaMemcpyDefault, s));
+  *out = *tmp;
+  return NBODY_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nbody_mmd_create(nbody_mmd** out, int64_t n, int64_t max_sets, int64_t m,
+                     const double* tx, const double* tv, const double* scale_or_null,
+                     int n_sigma, const double* sigma, void* cuda_stream) {
+  if (!out) return NBODY_EINVAL;
+  *out = nullptr;
+  if (n < 1 || max_sets < 1 || m < 1 || !tx || !tv || !sigma || n_sigma < 1 ||
+      n_sigma > nb::kMaxSigma)
+    return NBODY_EINVAL;
+  double smin = sigma[0];
+  for (int l = 0; l < n_sigma; ++l) {
+    if (!(sigma[l] > 0.0) || !std::isfinite(sigma[l])) return NBODY_EINVAL;
+    smin = std::fmin(smin, sigma[l]);
+  }
+  if (scale_or_null)
+    for (int d = 0; d < 6; ++d)
+      if (!(scale_or_null[d] > 0.0) || !std::isfinite(scale_or_null[d])) return NBODY_EINVAL;
+  int dev = 0, maj = 0, min = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&maj, cudaDevAttrComputeCapabilityMajor, dev) ||
+      cudaDeviceGetAttribute(&min, cudaDevAttrComputeCapabilityMinor, dev)) {
+    cudaGetLastError();
+    return NBODY_ENODEV;
+  }
+  if (maj != 10 || min != 3) return NBODY_ENODEV;
+  nbody_mmd* h = new (std::nothrow) nbody_mmd();
+  if (!h) return NBODY_ENOMEM;
+  h->s = (cudaStream_t)cuda_stream;
+  cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
+  h->n = n;
+  h->m = m;
+  h->max_sets = max_sets;
+  h->npad = nb::pad_points(n);
+  h->mpad = nb::pad_points(m);
+  h->ns = n_sigma;
+  // sigma_0 is the smallest bandwidth (first), the others follow in the
+  // caller's order; rho_l = sigma_0^2 / sigma_l^2 <= 1
+  {
+    double sg[4];
+    int k = 0, idx0 = 0;
+    for (int l = 0; l < n_sigma; ++l)
+      if (sigma[l] == smin) { idx0 = l; break; }
+    sg[k++] = sigma[idx0];
+    for (int l = 0; l < n_sigma; ++l)
+      if (l != idx0) sg[k++] = sigma[l];
+    float r[4] = {1.f, 1.f, 1.f, 1.f};
+    for (int l = 1; l < n_sigma; ++l) r[l] = (float)((sg[0] * sg[0]) / (sg[l] * sg[l]));
+    h->rho = make_float4(r[0], r[1], r[2], r[3]);
+    h->c0 = 1.4426950408889634 / (2.0 * sg[0] * sg[0]);  // log2(e) / (2 sigma_0^2)
+  }
+  int rc = NBODY_OK;
+  double* tmpx = nullptr;
+  double* tmpv = nullptr;
+  const double* dx = nullptr;
+  const double* dv = nullptr;
+  if ((rc = malloc_dev(&h->xs, (size_t)max_sets * 3 * (h->npad / 2))) ||
+      (rc = malloc_dev(&h->ys, (size_t)3 * (h->mpad / 2))) ||
+      (rc = malloc_dev(&h->kyy, 1)) || (rc = malloc_dev(&h->loss, (size_t)max_sets)) ||
+      (rc = malloc_dev(&h->stats, 12)) || (rc = malloc_dev(&h->gx, (size_t)3 * n)) ||
+      (rc = malloc_dev(&h->gv, (size_t)3 * n)) ||
+      (rc = device_view(tx, (size_t)3 * m, &tmpx, &dx, h->s)) ||
+      (rc = device_view(tv, (size_t)3 * m, &tmpv, &dv, h->s))) {
+    if (tmpx) cudaFree(tmpx);
+    if (tmpv) cudaFree(tmpv);
+    free_mmd(h);
+    delete h;
+    return rc;
+  }
+  auto fail = [&](int code) {
+    cudaStreamSynchronize(h->s);
+    if (tmpx) cudaFree(tmpx);
+    if (tmpv) cudaFree(tmpv);
+    free_mmd(h);
+    delete h;
+    return code;
+  };
+  // standardisation: the target's mean and standard deviation (or scale)
+  nb::k_cloud_stats<<<1, 256, 0, h->s>>>(dx, dv, m, h->stats);
+  nb::count_launch();
+  if (cudaGetLastError() != cudaSuccess) return fail(NBODY_ECUDA);
+  double stt[12];
+  if (cudaMemcpyAsync(stt, h->stats, sizeof(stt), cudaMemcpyDeviceToHost, h->s) != cudaSuccess ||
+      cudaStreamSynchronize(h->s) != cudaSuccess)
+    return fail(NBODY_ECUDA);
+  const double sc0 = std::sqrt(h->c0);
+  for (int d = 0; d < 6; ++d) {
+    const double sd = scale_or_null ? scale_or_null[d] : stt[6 + d];
+    if (!(sd > 0.0) || !std::isfinite(sd)) return fail(NBODY_EINVAL);
+    h->st.mu[d] = stt[d];
+    h->st.f[d] = sc0 / sd;
+  }
+  // the target's own term Kyy = (1/m^2) sum k(y, y')
+  if ((rc = stage(h, dx, dv, m, m, h->mpad, 1, h->ys))) return fail(rc);
+  const int nty = (int)(h->mpad / nb::kMPts);
+  const int Sy = chunks_for(h, 1, h->mpad, nty);
+  if ((rc = ensure_part(h, (int64_t)Sy * 8 * h->mpad))) return fail(rc);
+  if (launch_rows(h, 1, h->ys, 0, h->mpad, h->ys, 0, nty, nullptr, 0, 1.0 / (double)m, 0.0,
+                  Sy, h->part) != cudaSuccess)
+    return fail(NBODY_ECUDA);
+  nb::k_mmd_finish<<<1, 256, 0, h->s>>>(h->part, Sy, h->mpad, m, 1.0 / (double)m, 0.0,
+                                        nullptr, h->kyy);
+  nb::count_launch();
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->s) != cudaSuccess)
+    return fail(NBODY_ECUDA);
+  if (tmpx) cudaFree(tmpx);
+  if (tmpv) cudaFree(tmpv);
+  tmpx = tmpv = nullptr;
+  *out = h;
+  return NBODY_OK;
+}
+
+int nbody_mmd_eval_batch(nbody_mmd* h, int64_t sets, const double* x, const double* v,
+                         double* losses) {
+  if (!h || !x || !v || !losses || sets < 1 || sets > h->max_sets) return NBODY_EINVAL;
+  int rc;
+  double* tmpx = nullptr;
+  double* tmpv = nullptr;
+  const double* dx = nullptr;
+  const double* dv = nullptr;
+  const size_t cnt = (size_t)3 * sets * h->n;
+  if ((rc = device_view(x, cnt, &tmpx, &dx, h->s)) ||
+      (rc = device_view(v, cnt, &tmpv, &dv, h->s))) {
+    if (tmpx) cudaFree(tmpx);
+    return rc;
+  }
+  const int ntx = (int)(h->npad / nb::kMPts), nty = (int)(h->mpad / nb::kMPts);
+  const int S = chunks_for(h, sets, h->npad, ntx + nty);
+  rc = ensure_part(h, sets * S * 8 * h->npad);
+  if (!rc) rc = stage(h, dx, dv, sets * h->n, h->n, h->npad, sets, h->xs);
+  const int64_t xstride = 3 * (h->npad / 2);
+  if (!rc && launch_rows(h, sets, h->xs, xstride, h->npad, h->xs, xstride, ntx, h->ys, nty,
+                         1.0 / (double)h->n, -1.0 / (double)h->m, S, h->part) != cudaSuccess)
+    rc = NBODY_ECUDA;
+  if (!rc) {
+    nb::k_mmd_finish<<<(unsigned)sets, 256, 0, h->s>>>(h->part, S, h->npad, h->n,
+                                                       1.0 / (double)h->n, 2.0, h->kyy, h->loss);
+    nb::count_launch();
+    if (cudaGetLastError() != cudaSuccess) rc = NBODY_ECUDA;
+  }
+  std::vector<double> hl((size_t)sets);
+  if (!rc && cudaMemcpyAsync(hl.data(), h->loss, (size_t)sets * sizeof(double),
+                             cudaMemcpyDeviceToHost, h->s) != cudaSuccess)
+    rc = NBODY_ECUDA;
+  if (cudaStreamSynchronize(h->s) != cudaSuccess) rc = NBODY_ECUDA;
+  if (tmpx) cudaFree(tmpx);
+  if (tmpv) cudaFree(tmpv);
+  if (rc) return rc;
+  if (cudaMemcpy(losses, hl.data(), (size_t)sets * sizeof(double), cudaMemcpyDefault) !=
+      cudaSuccess)
+    return NBODY_ECUDA;
+  for (double L : hl)
+    if (!std::isfinite(L)) return NBODY_ENAN;
+  return NBODY_OK;
+}
+
+int nbody_mmd_eval(nbody_mmd* h, const double* x, const double* v, double* loss,
+                   double* xbar, double* vbar) {
+  if (!h || !x || !v || !loss) return NBODY_EINVAL;
+  int rc;
+  double* tmpx = nullptr;
+  double* tmpv = nullptr;
+  const double* dx = nullptr;
+  const double* dv = nullptr;
+  const size_t cnt = (size_t)3 * h->n;
+  if ((rc = device_view(x, cnt, &tmpx, &dx, h->s)) ||
+      (rc = device_view(v, cnt, &tmpv, &dv, h->s))) {
+    if (tmpx) cudaFree(tmpx);
+    return rc;
+  }
+  const int ntx = (int)(h->npad / nb::kMPts), nty = (int)(h->mpad / nb::kMPts);
+  const int S = chunks_for(h, 1, h->npad, ntx + nty);
+  rc = ensure_part(h, (int64_t)S * 8 * h->npad);
+  if (!rc) rc = stage(h, dx, dv, h->n, h->n, h->npad, 1, h->xs);
+  if (!rc && launch_rows(h, 1, h->xs, 0, h->npad, h->xs, 0, ntx, h->ys, nty,
+                         1.0 / (double)h->n, -1.0 / (double)h->m, S, h->part) != cudaSuccess)
+    rc = NBODY_ECUDA;
+  if (!rc) {
+    nb::k_mmd_finish<<<1, 256, 0, h->s>>>(h->part, S, h->npad, h->n, 1.0 / (double)h->n, 2.0,
+                                          h->kyy, h->loss);
+    nb::count_launch();
+    if (cudaGetLastError() != cudaSuccess) rc = NBODY_ECUDA;
+  }
+  if (!rc && (xbar || vbar)) {
+    // gradients into the context's buffers, then out to the caller's
+    const double g0 = 4.0 * 0.6931471805599453 / (double)h->n;  // 4 ln2 / n
+    nb::k_mmd_grad<<<(unsigned)((h->n + 255) / 256), 256, 0, h->s>>>(
+        h->part, S, h->npad, h->n, h->st, g0, h->gx, h->gv);
+    nb::count_launch();
+    if (cudaGetLastError() != cudaSuccess) rc = NBODY_ECUDA;
+    if (!rc && xbar &&
+        cudaMemcpyAsync(xbar, h->gx, cnt * sizeof(double), cudaMemcpyDefault, h->s) != cudaSuccess)
+      rc = NBODY_ECUDA;
+    if (!rc && vbar &&
+        cudaMemcpyAsync(vbar, h->gv, cnt * sizeof(double), cudaMemcpyDefault, h->s) != cudaSuccess)
+      rc = NBODY_ECUDA;
+  }
+  double L = 0.0;
+  if (!rc && cudaMemcpyAsync(&L, h->loss, sizeof(double), cudaMemcpyDeviceToHost, h->s) !=
+                 cudaSuccess)
+    rc = NBODY_ECUDA;
+  if (cudaStreamSynchronize(h->s) != cudaSuccess) rc = NBODY_ECUDA;
+  if (tmpx) cudaFree(tmpx);
+  if (tmpv) cudaFree(tmpv);
+  if (rc) return rc;
+  if (!std::isfinite(L)) return NBODY_ENAN;
+  *loss = L;
+  return NBODY_OK;
+}
+
+int nbody_mmd_target_stats(nbody_mmd* h, double mu[6], double scale[6]) {
+  if (!h) return NBODY_EINVAL;
+  const double sc0 = std::sqrt(h->c0);
+  for (int d = 0; d < 6; ++d) {
+    if (mu) mu[d] = h->st.mu[d];
+    if (scale) scale[d] = sc0 / h->st.f[d];
+  }
+  return NBODY_OK;
+}
+
+void nbody_mmd_destroy(nbody_mmd* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->s);
+  free_mmd(h);
+  delete h;
+}
+
+}  // extern "C"

@@ -48,7 +48,8 @@ EXPORTED = ("nbody_create", "nbody_destroy", "nbody_set_params",
             "nbody_mlp_forward", "nbody_mlp_loss_grad", "nbody_mlp_adam_step",
             "nbody_mlp_destroy", "nbody_mlp_invert", "nbody_set_pair_shape",
             "nbody_get_pair_shape", "nbody_peaks", "nbody_autotune_pair",
-            "nbody_potential_grad")
+            "nbody_potential_grad", "nbody_mmd_create", "nbody_mmd_eval",
+            "nbody_mmd_eval_batch", "nbody_mmd_target_stats", "nbody_mmd_destroy")
 
 NBODY_NTUNE = 8
 
@@ -162,6 +163,13 @@ def lib():
         L.nbody_set_timing.argtypes = [vp, C.c_int]
         L.nbody_kernel_times.argtypes = [vp, dp, C.POINTER(i64)]
         L.nbody_potential_grad.argtypes = [vp, dp]
+        L.nbody_mmd_create.argtypes = [C.POINTER(vp), i64, i64, i64, vp, vp, dp, C.c_int,
+                                       dp, vp]
+        L.nbody_mmd_eval.argtypes = [vp, vp, vp, dp, vp, vp]
+        L.nbody_mmd_eval_batch.argtypes = [vp, i64, vp, vp, vp]
+        L.nbody_mmd_target_stats.argtypes = [vp, dp, dp]
+        L.nbody_mmd_destroy.argtypes = [vp]
+        L.nbody_mmd_destroy.restype = None
         _lib = L
     return _lib
 
@@ -272,6 +280,42 @@ def nbody_potential_grad(h):
     out = (C.c_double * 5)()
     _check(lib().nbody_potential_grad(h, out), "nbody_potential_grad")
     return list(out)
+
+
+def nbody_mmd_create(n, max_sets, tx, tv, sigmas, scale=None, stream=None):
+    """MMD evaluator for clouds of n points against the target (tx, tv:
+    (3, m) each)."""
+    m = tx.shape[1]
+    h = C.c_void_p()
+    sg = (C.c_double * len(sigmas))(*[float(s) for s in sigmas])
+    sc = None if scale is None else (C.c_double * 6)(*[float(s) for s in scale])
+    _check(lib().nbody_mmd_create(C.byref(h), n, max_sets, m, _ptr(tx, (3, m)),
+                                  _ptr(tv, (3, m)), sc, len(sigmas), sg, _stream(stream)),
+           "nbody_mmd_create")
+    return h
+
+
+def nbody_mmd_eval(h, x, v, xbar=None, vbar=None):
+    loss = C.c_double()
+    _check(lib().nbody_mmd_eval(h, _ptr(x), _ptr(v), C.byref(loss), _ptr(xbar), _ptr(vbar)),
+           "nbody_mmd_eval")
+    return loss.value
+
+
+def nbody_mmd_eval_batch(h, sets, x, v, losses):
+    _check(lib().nbody_mmd_eval_batch(h, sets, _ptr(x), _ptr(v), _ptr(losses)),
+           "nbody_mmd_eval_batch")
+
+
+def nbody_mmd_target_stats(h):
+    mu = (C.c_double * 6)()
+    sc = (C.c_double * 6)()
+    _check(lib().nbody_mmd_target_stats(h, mu, sc), "nbody_mmd_target_stats")
+    return list(mu), list(sc)
+
+
+def nbody_mmd_destroy(h):
+    lib().nbody_mmd_destroy(h)
 
 
 def nbody_energy(h):

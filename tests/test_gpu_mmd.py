@@ -1,0 +1,126 @@
+"""MMD kernels vs the FP64 oracle, through the C ABI (needs a GB300).
+
+Tolerances: the kernel values are summed in FP32 within 512-point tiles
+(ex2.approx, relative error ~2^-22) and in FP64 across tiles; each of the
+three terms of MMD^2 is at most n_sigma, so the loss is compared with an
+absolute bound of 1e-5 * n_sigma and the gradient norm-wise at 1e-4.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import mmd as om  # noqa: E402
+from paper_2511_22468_gb300 import nbody as nb  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_22468_gb300 import build
+    build.build()
+    nb.lib()
+
+
+def stream_like(n, seed, shift=0.0):
+    """A seeded elongated cloud in kpc and kpc/Myr (a stream-like shape:
+    long along one axis, thin across, a velocity gradient along it)."""
+    rng = np.random.default_rng(seed)
+    t = rng.uniform(-1, 1, n)
+    x = np.stack([8.0 * t + rng.normal(0, 0.2, n), 3.0 * t ** 2 + rng.normal(0, 0.1, n),
+                  rng.normal(0, 0.15, n)], axis=1) + np.array([-5.0, 2.0, 9.0]) + shift
+    v = np.stack([0.2 + 0.02 * t, -0.05 * t + rng.normal(0, 0.003, n),
+                  rng.normal(0, 0.004, n)], axis=1) + 0.01 * shift
+    return x, v
+
+
+def soa(a):
+    return torch.tensor(np.ascontiguousarray(np.asarray(a, np.float64).T), device=DEV)
+
+
+@pytest.mark.parametrize("n,m,sig", [(600, 700, [1.0]), (1000, 1000, [0.5, 1.0, 2.0]),
+                                     (2500, 1800, [0.3, 0.6, 1.2, 2.4]),
+                                     (5, 3, [1.0, 2.0]), (513, 511, [0.7])])
+def test_mmd_matches_oracle(n, m, sig):
+    xs, vs = stream_like(n, 1, shift=0.3)
+    xt, vt = stream_like(m, 2)
+    X, Y = om.cloud(xs, vs), om.cloud(xt, vt)
+    L_ref, g_ref = om.mmd2_grad(X, Y, sig)
+    h = nb.nbody_mmd_create(n, 1, soa(xt), soa(vt), sig)
+    try:
+        xb = torch.empty((3, n), dtype=torch.float64, device=DEV)
+        vb = torch.empty_like(xb)
+        L = nb.nbody_mmd_eval(h, soa(xs), soa(vs), xb, vb)
+        assert abs(L - L_ref) <= 1e-5 * len(sig)
+        g = np.concatenate([xb.cpu().numpy().T, vb.cpu().numpy().T], axis=1)
+        assert np.linalg.norm(g - g_ref) <= 1e-4 * np.linalg.norm(g_ref)
+        mu, sc = nb.nbody_mmd_target_stats(h)
+        mu_ref, sc_ref = om.target_stats(Y)
+        np.testing.assert_allclose(mu, mu_ref, rtol=1e-12, atol=1e-14)
+        np.testing.assert_allclose(sc, sc_ref, rtol=1e-10)
+        # bitwise reproducible, and host arrays give the same result
+        L2 = nb.nbody_mmd_eval(h, np.ascontiguousarray(xs.T), np.ascontiguousarray(vs.T))
+        assert L2 == L
+    finally:
+        nb.nbody_mmd_destroy(h)
+
+
+def test_batched_sets_match_oracle():
+    n, m, sets, sig = 1000, 1200, 7, [0.5, 1.0, 2.0]
+    xt, vt = stream_like(m, 3)
+    Y = om.cloud(xt, vt)
+    clouds = [stream_like(n, 10 + b, shift=0.1 * b) for b in range(sets)]
+    X = torch.cat([soa(c[0]) for c in clouds], dim=1).contiguous()
+    V = torch.cat([soa(c[1]) for c in clouds], dim=1).contiguous()
+    h = nb.nbody_mmd_create(n, 16, soa(xt), soa(vt), sig)
+    try:
+        out = torch.empty(sets, dtype=torch.float64, device=DEV)
+        nb.nbody_mmd_eval_batch(h, sets, X, V, out)
+        got = out.cpu().numpy()
+        for b, (xs, vs) in enumerate(clouds):
+            ref = om.mmd2(om.cloud(xs, vs), Y, sig)
+            assert abs(got[b] - ref) <= 1e-5 * len(sig)
+            single = nb.nbody_mmd_eval(h, soa(xs), soa(vs))
+            assert got[b] == pytest.approx(single, rel=1e-12, abs=1e-15)
+        with pytest.raises(nb.NBodyError) as e:
+            nb.nbody_mmd_eval_batch(h, 17, X, V, out)
+        assert e.value.code == nb.NBODY_EINVAL
+    finally:
+        nb.nbody_mmd_destroy(h)
+
+
+def test_identical_cloud_and_single_points():
+    xt, vt = stream_like(1500, 4)
+    h = nb.nbody_mmd_create(1500, 1, soa(xt), soa(vt), [1.0, 2.0])
+    try:
+        assert abs(nb.nbody_mmd_eval(h, soa(xt), soa(vt))) < 1e-12
+    finally:
+        nb.nbody_mmd_destroy(h)
+    # one point each, explicit scale: MMD^2 = 2 - 2/e for d^2 = 2, sigma = 1
+    a = np.array([[1.0, 2.0, 3.0, 0.0, 0.0, 0.0]])
+    b = a + np.array([[2.0, 1.0, 0.0, 0.0, 0.0, 0.0]])
+    sc = [2.0, 1.0, 1.0, 3.0, 1.0, 1.0]
+    h = nb.nbody_mmd_create(1, 1, soa(b[:, :3]), soa(b[:, 3:]), [1.0], scale=sc)
+    try:
+        L = nb.nbody_mmd_eval(h, soa(a[:, :3]), soa(a[:, 3:]))
+        assert L == pytest.approx(1.2642411176571153, abs=2e-6)
+    finally:
+        nb.nbody_mmd_destroy(h)
+
+
+def test_mmd_errors():
+    xt, vt = stream_like(10, 5)
+    for kw in (dict(sigmas=[]), dict(sigmas=[1.0, -1.0]), dict(sigmas=[1.0] * 5)):
+        with pytest.raises(nb.NBodyError) as e:
+            nb.nbody_mmd_create(10, 1, soa(xt), soa(vt), **kw)
+        assert e.value.code == nb.NBODY_EINVAL
+    # a target without spread needs an explicit scale
+    one = soa(xt[:1])
+    with pytest.raises(nb.NBodyError) as e:
+        nb.nbody_mmd_create(10, 1, one, soa(vt[:1]), [1.0])
+    assert e.value.code == nb.NBODY_EINVAL
