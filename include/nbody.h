@@ -300,8 +300,9 @@ NBODY_API int nbody_pair_accel(int64_t n, const double *x, const double *m, doub
  *  5. a Gaussian-smoothed nb1 x nb2 histogram (sigma = half a bin, each bin
  *     receiving the normal-CDF mass between its edges, weights 1/n) is
  *     compared with a target: L = mean_b (rho_b - target_b)^2.
- * The paper compares point clouds with an MMD (Fig. 2 step 4); the binned
- * density is this library's smooth stand-in. */
+ * The paper compares point clouds with an MMD (Fig. 2 step 4); that loss is
+ * selected with nbody_stream_set_target_cloud, the binned density with
+ * nbody_stream_set_target. */
 typedef struct nbody_stream_cfg {
   int64_t n;                /* progenitor particles, >= 1                    */
   int64_t n_steps;          /* steps of the orbit and of the n-body run      */
@@ -319,6 +320,7 @@ typedef struct nbody_stream_cfg {
 } nbody_stream_cfg;
 
 typedef struct nbody_stream nbody_stream; /* opaque, owned by the library */
+typedef struct nbody_mmd nbody_mmd;       /* opaque, owned by the library */
 
 /* Create the pipeline for a unit Plummer sample xhat, vhat (3 x n each,
  * host or device; copied).  The target starts at zero.
@@ -329,8 +331,18 @@ NBODY_API int nbody_stream_create(nbody_stream **out,
                                   void *cuda_stream);
 
 /* Replace the target density (nb1 * nb2 doubles, row-major [b1][b2], host
- * or device).  Errors: EINVAL, ECUDA. */
+ * or device) and use the density loss of step 5.  Errors: EINVAL, ECUDA. */
 NBODY_API int nbody_stream_set_target(nbody_stream *s, const double *target);
+
+/* Use the point-cloud loss instead (the paper's comparison, Fig. 2 step 4):
+ * L = MMD^2 between the final phase-space cloud (x_T, v_T) and a target
+ * cloud tx, tv (3 x m each, host or device), with the standardisation and
+ * bandwidths of nbody_mmd_create (declared below).  The gradient then flows
+ * through both x_T and v_T.  Errors: as nbody_mmd_create. */
+NBODY_API int nbody_stream_set_target_cloud(nbody_stream *s, int64_t m,
+                                            const double *tx, const double *tv,
+                                            const double *scale_or_null,
+                                            int n_sigma, const double *sigma);
 
 /* Run steps 1-5 at theta (host, 4 doubles, all > 0).  loss (host, may be
  * NULL) receives L; density (host or device, nb1 * nb2, may be NULL) the
@@ -352,6 +364,17 @@ NBODY_API int nbody_stream_grad(nbody_stream *s, double theta_bar[4]);
 NBODY_API int nbody_stream_initial_state(nbody_stream *s, const double theta[4],
                                          double *x0, double *v0, double *m,
                                          double com[6]);
+
+/* Steps 1-2 for `count` parameter vectors at once (host or device, count x 4
+ * doubles, all > 0), one backward orbit per GPU thread: x0, v0 (device,
+ * 3 x (count n) SoA, member b in columns b n .. b n + n - 1: the layout of
+ * a batch context of count simulations of n particles), m (device,
+ * count n) and com (host or device, count x 6, may be NULL).  The same
+ * arithmetic as nbody_stream_initial_state.  Synchronises.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+NBODY_API int nbody_stream_initial_states(nbody_stream *s, int64_t count,
+                                          const double *thetas, double *x0,
+                                          double *v0, double *m, double *com);
 
 /* Steps 4-5 alone: the histogram (nb1 * nb2, host or device) of positions x
  * (3 x n, device) and, when loss is not NULL, their loss against the target.
@@ -377,7 +400,6 @@ NBODY_API void nbody_stream_destroy(nbody_stream *s);
  * Pair sums run in FP32 within 512-point tiles and in FP64 across tiles,
  * in fixed order (bitwise reproducible).  All arrays are FP64 SoA: a cloud
  * of c points is x (3 x c) and v (3 x c). */
-typedef struct nbody_mmd nbody_mmd; /* opaque, owned by the library */
 
 /* Evaluator for clouds of n points against the target (tx, tv: 3 x m each,
  * host or device; copied and staged).  max_sets bounds the sets of one

@@ -29,7 +29,7 @@ import math
 import numpy as np
 from scipy.special import ndtr
 
-from . import core
+from . import core, mmd
 
 
 def frame(X0, V0, observer):
@@ -136,10 +136,7 @@ class StreamModel:
         return x0, v0, m
 
     def final_positions(self, theta):
-        x0, v0, m = self.initial_state(theta)
-        xT, _ = core.integrate(self.physics(theta, True), x0, v0, m,
-                               theta[0] / self.n_steps, self.n_steps)
-        return xT
+        return self.final_state(theta)[0]
 
     def density(self, theta):
         xT = self.final_positions(theta)
@@ -153,12 +150,9 @@ class StreamModel:
     def loss_and_grad(self, theta, target):
         """Loss and dL/dTheta, Theta = (t_end, M_prog, M_NFW, M_MN)."""
         theta = [float(t) for t in theta]
-        t_acc, M_prog = theta[0], theta[1]
         n = self.n_steps
-        a = self.cfg.a_prog
-        G = self.cfg.G
         x0, v0, m = self.initial_state(theta)
-        dt = t_acc / n
+        dt = theta[0] / n
         xT, _ = core.integrate(self.physics(theta, True), x0, v0, m, dt, n)
         p1, p2 = project(xT, self.cfg.observer, self.fr)
         rho = soft_hist(p1, p2, self.e1, self.e2)
@@ -166,8 +160,36 @@ class StreamModel:
         rho_bar = 2.0 * (rho - target) / rho.size
         g1, g2 = soft_hist_vjp(p1, p2, self.e1, self.e2, rho_bar)
         xbar = project_vjp(xT, self.cfg.observer, self.fr, g1, g2)
-        r = core.vjp(self.physics(theta, True), x0, v0, m, dt, n, xbar,
-                     np.zeros_like(xbar))
+        return L, self.theta_grad(theta, x0, v0, m, xbar, np.zeros_like(xbar))
+
+    def final_state(self, theta):
+        x0, v0, m = self.initial_state(theta)
+        return core.integrate(self.physics(theta, True), x0, v0, m,
+                              theta[0] / self.n_steps, self.n_steps)
+
+    def mmd_loss(self, theta, Y, sigmas, mu=None, s=None):
+        """MMD^2 between the simulated stream's phase-space cloud and the
+        target cloud Y (m, 6) (the paper's point-cloud comparison)."""
+        xT, vT = self.final_state([float(t) for t in theta])
+        return float(mmd.mmd2(mmd.cloud(xT, vT), Y, sigmas, mu, s))
+
+    def mmd_loss_and_grad(self, theta, Y, sigmas, mu=None, s=None):
+        theta = [float(t) for t in theta]
+        x0, v0, m = self.initial_state(theta)
+        xT, vT = core.integrate(self.physics(theta, True), x0, v0, m,
+                                theta[0] / self.n_steps, self.n_steps)
+        L, g = mmd.mmd2_grad(mmd.cloud(xT, vT), Y, sigmas, mu, s)
+        return float(L), self.theta_grad(theta, x0, v0, m, g[:, :3].copy(), g[:, 3:].copy())
+
+    def theta_grad(self, theta, x0, v0, m, xbar, vbar):
+        """dL/dTheta from dL/dx_T, dL/dv_T through the n-body run, the
+        Plummer shift and the backward orbit."""
+        t_acc, M_prog = theta[0], theta[1]
+        n = self.n_steps
+        a = self.cfg.a_prog
+        G = self.cfg.G
+        dt = t_acc / n
+        r = core.vjp(self.physics(theta, True), x0, v0, m, dt, n, xbar, vbar)
         # initial-state adjoint: x0 = a xhat + X, v0 = sqrt(G M/a) vhat + V,
         # m_j = M / N
         Xb = r["x0bar"].sum(axis=0)
@@ -188,4 +210,4 @@ class StreamModel:
             r["nfw_M_bar"] + ro["nfw_M_bar"],
             r["mn_M_bar"] + ro["mn_M_bar"],
         ])
-        return L, grad
+        return grad

@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "block_reduce.cuh"
 #include "ext_potential.cuh"
@@ -64,6 +65,56 @@ __global__ void k_orbit(DevParams P, double X0, double X1, double X2,
     g6[d] = x[d];
     g6[3 + d] = v[d];
   }
+}
+
+// Backward orbits of many parameter vectors at once, one thread each (the
+// arithmetic of k_orbit without the stored trajectory): theta_b = (t_end,
+// M_prog, M_NFW, M_MN) -> g6[b] = (X, V) after ns steps of -t_end/ns.
+__global__ void k_orbit_batch(DevParams P0, double X0, double X1, double X2, double V0,
+                              double V1, double V2, int64_t ns,
+                              const double* __restrict__ theta, int64_t count,
+                              double* __restrict__ g6) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count) return;
+  DevParams P = P0;
+  P.dt = -theta[4 * b] / (double)ns;
+  P.nfw_GM = P0.G * theta[4 * b + 2];
+  P.mn_GM = P0.G * theta[4 * b + 3];
+  double x[3] = {X0, X1, X2}, v[3] = {V0, V1, V2};
+  ExtUnit e;
+  nb::ext_unit(P, x[0], x[1], x[2], e);
+  for (int64_t k = 0; k < ns; ++k) {
+    for (int d = 0; d < 3; ++d) {
+      v[d] += 0.5 * P.dt * (P.nfw_GM * e.n[d] + P.mn_GM * e.d[d]);
+      x[d] += P.dt * v[d];
+    }
+    nb::ext_unit(P, x[0], x[1], x[2], e);
+    for (int d = 0; d < 3; ++d)
+      v[d] += 0.5 * P.dt * (P.nfw_GM * e.n[d] + P.mn_GM * e.d[d]);
+  }
+  for (int d = 0; d < 3; ++d) {
+    g6[6 * b + d] = x[d];
+    g6[6 * b + 3 + d] = v[d];
+  }
+}
+
+// Plummer spheres of many parameter vectors: member b's particle i is
+// column b n + i of x0, v0 (3 x count n) and element b n + i of m.
+__global__ void k_ic_batch(const double* __restrict__ xh, const double* __restrict__ vh,
+                           const double* __restrict__ g6, const double* __restrict__ theta,
+                           double a, double G, int64_t n, int64_t count,
+                           double* __restrict__ x0, double* __restrict__ v0,
+                           double* __restrict__ m) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n * count) return;
+  const int64_t b = k / n, i = k - b * n, ld = n * count;
+  const double M = theta[4 * b + 1];
+  const double vscale = sqrt(G * M / a);
+  for (int d = 0; d < 3; ++d) {
+    x0[d * ld + k] = a * xh[d * n + i] + g6[6 * b + d];
+    v0[d * ld + k] = vscale * vh[d * n + i] + g6[6 * b + 3 + d];
+  }
+  m[k] = M / (double)n;
 }
 
 // adjoint of one half kick v' = v + (dt/2) a(x) with cotangent vb = vbar'
@@ -309,6 +360,8 @@ struct nbody_stream {
   double *phi = nullptr, *w = nullptr;
   double *rho = nullptr, *target = nullptr, *rbar = nullptr, *loss = nullptr;
   double *xbar = nullptr, *x0bar = nullptr, *v0bar = nullptr;
+  double *vT = nullptr, *vbar = nullptr;  // the point-cloud (MMD) head
+  nbody_mmd* mmd = nullptr;               // set: the loss is MMD^2 to a cloud
   double *blk = nullptr, *red = nullptr, *orb = nullptr, *tbar = nullptr;
   int nblk = 0;
   double theta[4] = {0, 0, 0, 0};
@@ -342,6 +395,9 @@ void sfree(T*& p) {
 void free_stream(nbody_stream* s) {
   if (s->ctx) nbody_destroy(s->ctx);
   s->ctx = nullptr;
+  if (s->mmd) nbody_mmd_destroy(s->mmd);
+  s->mmd = nullptr;
+  sfree(s->vT); sfree(s->vbar);
   sfree(s->xhat); sfree(s->vhat); sfree(s->x0); sfree(s->v0); sfree(s->m);
   sfree(s->xT); sfree(s->ox); sfree(s->ovh); sfree(s->g6); sfree(s->phi);
   sfree(s->w); sfree(s->rho); sfree(s->target); sfree(s->rbar); sfree(s->loss);
@@ -430,6 +486,7 @@ int nbody_stream_create(nbody_stream** out, const nbody_stream_cfg* cfg,
   if (rc || (rc = salloc(&s->xhat, n3)) || (rc = salloc(&s->vhat, n3)) ||
       (rc = salloc(&s->x0, n3)) || (rc = salloc(&s->v0, n3)) ||
       (rc = salloc(&s->m, (size_t)c.n)) || (rc = salloc(&s->xT, n3)) ||
+      (rc = salloc(&s->vT, n3)) || (rc = salloc(&s->vbar, n3)) ||
       (rc = salloc(&s->ox, 3 * (ns + 1))) || (rc = salloc(&s->ovh, 3 * ns)) ||
       (rc = salloc(&s->g6, 6)) || (rc = salloc(&s->phi, 2 * (size_t)c.n)) ||
       (rc = salloc(&s->w, (size_t)c.n * (c.nb1 + c.nb2))) ||
@@ -508,6 +565,55 @@ int nbody_stream_initial_state(nbody_stream* s, const double theta[4], double* x
   return NBODY_OK;
 }
 
+int nbody_stream_initial_states(nbody_stream* s, int64_t count, const double* thetas,
+                                double* x0, double* v0, double* m, double* com) {
+  if (!s || count < 1 || !thetas || !x0 || !v0 || !m) return NBODY_EINVAL;
+  const nbody_stream_cfg& c = s->cfg;
+  const int64_t n = s->n;
+  std::vector<double> th((size_t)count * 4);
+  if (cudaMemcpy(th.data(), thetas, th.size() * sizeof(double), cudaMemcpyDefault) !=
+      cudaSuccess)
+    return NBODY_ECUDA;
+  for (double t : th)
+    if (!(t > 0.0) || !std::isfinite(t)) return NBODY_EINVAL;
+  double* dth = nullptr;
+  double* g6 = nullptr;
+  int rc = salloc(&dth, th.size());
+  if (!rc) rc = salloc(&g6, (size_t)count * 6);
+  cudaError_t e = cudaSuccess;
+  if (!rc) {
+    e = cudaMemcpyAsync(dth, th.data(), th.size() * sizeof(double), cudaMemcpyHostToDevice,
+                        s->s);
+    DevParams P{};
+    P.G = c.G;
+    P.ext = NBODY_EXT_NFW | NBODY_EXT_MN;
+    P.nfw_rs = c.nfw_rs;
+    P.mn_a = c.mn_a;
+    P.mn_b = c.mn_b;
+    if (e == cudaSuccess) {
+      k_orbit_batch<<<blocks_for(count, 64), 64, 0, s->s>>>(P, c.X0[0], c.X0[1], c.X0[2],
+                                                             c.V0[0], c.V0[1], c.V0[2],
+                                                             c.n_steps, dth, count, g6);
+      nb::count_launch();
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+      k_ic_batch<<<blocks_for(n * count, 256), 256, 0, s->s>>>(s->xhat, s->vhat, g6, dth,
+                                                               c.a_prog, c.G, n, count, x0,
+                                                               v0, m);
+      nb::count_launch();
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && com)
+      e = cudaMemcpyAsync(com, g6, (size_t)count * 6 * sizeof(double), cudaMemcpyDefault, s->s);
+    if (cudaStreamSynchronize(s->s) != cudaSuccess) e = cudaErrorUnknown;
+  }
+  sfree(dth);
+  sfree(g6);
+  if (rc) return rc;
+  return e == cudaSuccess ? NBODY_OK : NBODY_ECUDA;
+}
+
 int nbody_stream_head(nbody_stream* s, const double* x, double* density, double* loss) {
   if (!s || !x || !density) return NBODY_EINVAL;
   const nbody_stream_cfg& c = s->cfg;
@@ -560,8 +666,24 @@ void nbody_stream_destroy(nbody_stream* s) {
   delete s;
 }
 
+int nbody_stream_set_target_cloud(nbody_stream* s, int64_t m, const double* tx,
+                                  const double* tv, const double* scale_or_null,
+                                  int n_sigma, const double* sigma) {
+  if (!s || !tx || !tv || !sigma) return NBODY_EINVAL;
+  nbody_mmd* h = nullptr;
+  const int rc = nbody_mmd_create(&h, s->n, 1, m, tx, tv, scale_or_null, n_sigma, sigma, s->s);
+  if (rc) return rc;
+  if (s->mmd) nbody_mmd_destroy(s->mmd);
+  s->mmd = h;
+  s->have_forward = false;
+  return NBODY_OK;
+}
+
 int nbody_stream_set_target(nbody_stream* s, const double* target) {
   if (!s || !target) return NBODY_EINVAL;
+  if (s->mmd) nbody_mmd_destroy(s->mmd);
+  s->mmd = nullptr;
+  s->have_forward = false;
   SCK(cudaMemcpyAsync(s->target, target, (size_t)s->nb * sizeof(double),
                       cudaMemcpyDefault, s->s));
   SCK(cudaStreamSynchronize(s->s));
@@ -612,8 +734,27 @@ int nbody_stream_forward(nbody_stream* s, const double theta[4], double* loss,
   }
   int rc = nbody_set_params(s->ctx, &p);
   if (!rc) rc = nbody_set_state(s->ctx, s->x0, s->v0, s->m);
-  if (!rc) rc = nbody_integrate(s->ctx, ns, s->xT, nullptr);
+  if (!rc) rc = nbody_integrate(s->ctx, ns, s->xT, s->mmd ? s->vT : nullptr);
   if (rc) return rc;
+  if (s->mmd) {
+    // 4-5. point-cloud head: MMD^2 of the final phase-space cloud
+    double L = 0.0;
+    if ((rc = nbody_mmd_eval(s->mmd, s->xT, s->vT, &L, nullptr, nullptr))) return rc;
+    if (density) {
+      k_head_weights<<<blocks_for(n, 128), 128, 0, s->s>>>(s->geom, s->xT, n, s->phi, s->w);
+      nb::count_launch();
+      SCK(cudaGetLastError());
+      k_hist<<<c.nb1, 256, 0, s->s>>>(s->w, n, c.nb1, c.nb2, s->rho);
+      nb::count_launch();
+      SCK(cudaGetLastError());
+      SCK(cudaMemcpyAsync(density, s->rho, (size_t)s->nb * sizeof(double),
+                          cudaMemcpyDefault, s->s));
+      SCK(cudaStreamSynchronize(s->s));
+    }
+    if (loss) *loss = L;
+    s->have_forward = true;
+    return NBODY_OK;
+  }
   // 4-5. head
   k_head_weights<<<blocks_for(n, 128), 128, 0, s->s>>>(s->geom, s->xT, n, s->phi, s->w);
   nb::count_launch();
@@ -641,12 +782,19 @@ int nbody_stream_grad(nbody_stream* s, double theta_bar[4]) {
   if (!s->have_forward) return NBODY_ESTATE;
   const nbody_stream_cfg& c = s->cfg;
   const int64_t n = s->n, ns = c.n_steps;
-  k_head_vjp<<<blocks_for(n, 128), 128, 0, s->s>>>(s->geom, s->xT, s->phi, s->w,
-                                                   s->rbar, n, s->xbar);
-  nb::count_launch();
-  SCK(cudaGetLastError());
   double tb[4];
-  int rc = nbody_vjp(s->ctx, s->xbar, nullptr, s->x0bar, s->v0bar, nullptr, tb);
+  int rc;
+  if (s->mmd) {
+    double L = 0.0;
+    if ((rc = nbody_mmd_eval(s->mmd, s->xT, s->vT, &L, s->xbar, s->vbar))) return rc;
+    rc = nbody_vjp(s->ctx, s->xbar, s->vbar, s->x0bar, s->v0bar, nullptr, tb);
+  } else {
+    k_head_vjp<<<blocks_for(n, 128), 128, 0, s->s>>>(s->geom, s->xT, s->phi, s->w,
+                                                     s->rbar, n, s->xbar);
+    nb::count_launch();
+    SCK(cudaGetLastError());
+    rc = nbody_vjp(s->ctx, s->xbar, nullptr, s->x0bar, s->v0bar, nullptr, tb);
+  }
   if (rc) return rc;
   SCK(cudaMemsetAsync(s->blk, 0, (size_t)s->nblk * 7 * sizeof(double), s->s));
   k_ic_vjp<<<s->nblk, 256, 0, s->s>>>(s->x0bar, s->v0bar, s->vhat, n, s->blk);

@@ -49,7 +49,8 @@ EXPORTED = ("nbody_create", "nbody_destroy", "nbody_set_params",
             "nbody_mlp_destroy", "nbody_mlp_invert", "nbody_set_pair_shape",
             "nbody_get_pair_shape", "nbody_peaks", "nbody_autotune_pair",
             "nbody_potential_grad", "nbody_mmd_create", "nbody_mmd_eval",
-            "nbody_mmd_eval_batch", "nbody_mmd_target_stats", "nbody_mmd_destroy")
+            "nbody_mmd_eval_batch", "nbody_mmd_target_stats", "nbody_mmd_destroy",
+            "nbody_stream_set_target_cloud", "nbody_stream_initial_states")
 
 NBODY_NTUNE = 8
 
@@ -133,6 +134,8 @@ def lib():
         SC = C.POINTER(nbody_stream_cfg)
         L.nbody_stream_create.argtypes = [C.POINTER(vp), SC, vp, vp, vp]
         L.nbody_stream_set_target.argtypes = [vp, vp]
+        L.nbody_stream_set_target_cloud.argtypes = [vp, i64, vp, vp, dp, C.c_int, dp]
+        L.nbody_stream_initial_states.argtypes = [vp, i64, vp, vp, vp, vp, vp]
         L.nbody_stream_forward.argtypes = [vp, dp, dp, vp]
         L.nbody_stream_grad.argtypes = [vp, dp]
         L.nbody_stream_initial_state.argtypes = [vp, dp, vp, vp, vp, dp]
@@ -492,6 +495,16 @@ def nbody_stream_set_target(h, target):
     _check(lib().nbody_stream_set_target(h, _ptr(target)), "nbody_stream_set_target")
 
 
+def nbody_stream_set_target_cloud(h, tx, tv, sigmas, scale=None):
+    """Point-cloud (MMD) loss against the cloud tx, tv ((3, m) each)."""
+    m = tx.shape[1]
+    sg = (C.c_double * len(sigmas))(*[float(s) for s in sigmas])
+    sc = None if scale is None else (C.c_double * 6)(*[float(s) for s in scale])
+    _check(lib().nbody_stream_set_target_cloud(h, m, _ptr(tx, (3, m)), _ptr(tv, (3, m)), sc,
+                                               len(sigmas), sg),
+           "nbody_stream_set_target_cloud")
+
+
 def nbody_stream_forward(h, theta, density=None):
     """Loss at theta = (t_end, M_Plummer, M_NFW, M_MN); fills density if given."""
     th = (C.c_double * 4)(*[float(t) for t in theta])
@@ -515,6 +528,16 @@ def nbody_stream_initial_state(h, theta, x0, v0, m):
     _check(lib().nbody_stream_initial_state(h, th, _ptr(x0), _ptr(v0), _ptr(m), com),
            "nbody_stream_initial_state")
     return list(com)
+
+
+def nbody_stream_initial_states(h, thetas, x0, v0, m, com=None):
+    """Initial states of count = len(thetas) parameter vectors: x0, v0
+    (3, count n) and m (count n,) on the device; com (count, 6) if given."""
+    import numpy as np
+    th = np.ascontiguousarray(np.asarray(thetas, np.float64).reshape(-1, 4))
+    _check(lib().nbody_stream_initial_states(h, th.shape[0], _ptr(th), _ptr(x0), _ptr(v0),
+                                             _ptr(m), _ptr(com)),
+           "nbody_stream_initial_states")
 
 
 def nbody_stream_head(h, x, density, want_loss=False):

@@ -1,5 +1,6 @@
 """Mock-stream inference on the GPU: the pipeline of the paper's Fig. 2 with
-a binned-density loss, and its gradient as a torch.autograd.Function.
+a binned-density loss or the paper's point-cloud (MMD) loss, and its
+gradient as a torch.autograd.Function.
 
 StreamModel owns one nbody_stream (C ABI); StreamLoss.apply(theta, model)
 returns the loss as a tensor whose backward runs the discrete adjoint
@@ -67,6 +68,31 @@ class StreamModel:
     def set_target(self, target):
         t = torch.as_tensor(target, dtype=torch.float64).to(self.device).contiguous()
         nb.nbody_stream_set_target(self.h, t)
+
+    def set_target_cloud(self, x, v, sigmas=(0.5, 1.0, 2.0), scale=None):
+        """MMD^2 loss against the phase-space cloud x, v ((3, m) FP64
+        tensors or arrays)."""
+        tx = torch.as_tensor(x, dtype=torch.float64).to(self.device).contiguous()
+        tv = torch.as_tensor(v, dtype=torch.float64).to(self.device).contiguous()
+        nb.nbody_stream_set_target_cloud(self.h, tx, tv, list(sigmas), scale)
+
+    def final_state(self, theta):
+        """(x_T, v_T), (3, n) each, of the simulated stream at theta."""
+        x0 = torch.empty((3, self.n), dtype=torch.float64, device=self.device)
+        v0 = torch.empty_like(x0)
+        m = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        com = nb.nbody_stream_initial_state(self.h, theta, x0, v0, m)
+        p = self.cfg
+        params = nb.make_params(p.G, p.eps, theta[0] / p.n_steps, ext_flags=3, nfw_M=theta[2],
+                                nfw_rs=p.nfw_rs, mn_M=theta[3], mn_a=p.mn_a, mn_b=p.mn_b,
+                                center=com[:3], center_vel=com[3:6],
+                                center_mode=nb.NBODY_CENTER_GUIDE)
+        sim = nb.Simulation(self.n, params)
+        sim.set_state(x0, v0, m)
+        xT, vT = torch.empty_like(x0), torch.empty_like(v0)
+        sim.integrate(p.n_steps, xT, vT)
+        sim.close()
+        return xT, vT
 
     def loss(self, theta):
         return nb.nbody_stream_forward(self.h, theta)

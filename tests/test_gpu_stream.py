@@ -96,3 +96,31 @@ def test_stream_autograd_function():
     assert gpu.loss(truth) <= 1e-6 * L_ref
     assert np.all(np.abs(gpu.grad()) <= 1e-3 * np.abs(g_ref))
     gpu.close()
+
+
+def test_stream_mmd_loss_and_gradient_match_oracle():
+    """The point-cloud form (MMD^2 of the final phase-space cloud against a
+    target cloud) through the pipeline's adjoint, against the oracle."""
+    from oracle import mmd
+    from paper_2511_22468_gb300.stream import StreamModel
+    cfg, xh, vh = _case()
+    orc = ostream.StreamModel(cfg, xh, vh)
+    truth = np.array(cfg.theta_true, float)
+    xt, vt = orc.final_state(truth)
+    Y = mmd.cloud(xt, vt)
+    sig = [0.5, 1.0, 2.0]
+    th = truth * np.array([1.05, 0.9, 1.1, 0.95])
+    L_ref, g_ref = orc.mmd_loss_and_grad(th, Y, sig)
+    gpu = StreamModel(cfg, xh, vh, checkpoint_every=8)
+    gpu.set_target_cloud(xt.T.copy(), vt.T.copy(), sig)
+    L, g = gpu.loss_and_grad(th)
+    assert abs(L - L_ref) <= 1e-5 * len(sig) and L == pytest.approx(L_ref, rel=1e-3)
+    assert_grad_close(g, g_ref, orc.t_end_parts)
+    # the GPU's own final state at the truth reproduces the target cloud
+    xg, vg = gpu.final_state(list(truth))
+    assert np.max(np.abs(xg.cpu().numpy().T - xt)) <= 1e-6 * np.max(np.abs(xt))
+    assert gpu.loss(list(truth)) < 1e-9
+    # switching back to the density loss
+    gpu.set_target(orc.density(truth))
+    assert gpu.loss(list(th)) == pytest.approx(orc.loss(th, orc.density(truth)), rel=1e-4)
+    gpu.close()
