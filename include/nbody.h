@@ -283,6 +283,14 @@ NBODY_API int nbody_pair_accel(int64_t n, const double *x, const double *m, doub
                      double eps, const double center[3], double *acc,
                      void *cuda_stream);
 
+/* External acceleration (NFW halo + Miyamoto-Nagai disk per p->ext_flags,
+ * Sec. 2.2.1; G M included) at n >= 1 points x (3 x n SoA, host or device)
+ * into acc (3 x n, host or device): the FP64 field the integrator kicks
+ * with.  Only the potential fields of p are used (p->eps and p->dt must
+ * still be valid).  Synchronises.  Errors: EINVAL, ENODEV, ENOMEM, ECUDA. */
+NBODY_API int nbody_ext_accel(const nbody_params *p, int64_t n, const double *x,
+                              double *acc, void *cuda_stream);
+
 /* ---- the mock-stream pipeline (Fig. 2, Sec. 2.2.1) ---- */
 
 /* Loss L(Theta), Theta = { t_end, M_Plummer, M_NFW, M_MN } (Sec. 2.2.1):

@@ -42,7 +42,7 @@ constexpr TuneCfg kTune[NBODY_NTUNE] = {
 
 struct SimMeta {
   int64_t npad, poff, part_off;
-  int64_t n;
+  int64_t n, off;  // particles and offset in the caller's unpadded layout
   int S, ntiles;
   float eps2f;
   int pad;
@@ -223,6 +223,61 @@ __global__ void __launch_bounds__(256)
   if (bad) atomicOr(status, kStatusNaN);
 }
 
+// caller layout (3 x ntot SoA, simulation s at columns off .. off+n-1) ->
+// padded state (3 x ptot, simulation s at poff); one grid row per simulation
+__global__ void k_gather_batch(const SimMeta* __restrict__ meta, int n_sims,
+                               const double* __restrict__ x, const double* __restrict__ v,
+                               const double* __restrict__ m, int64_t ntot, int64_t ptot,
+                               double* __restrict__ X, double* __restrict__ V,
+                               double* __restrict__ Mo) {
+  for (int s = blockIdx.y; s < n_sims; s += gridDim.y) {
+    const SimMeta M = meta[s];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M.n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        X[d * ptot + M.poff + i] = x[d * ntot + M.off + i];
+        V[d * ptot + M.poff + i] = v[d * ntot + M.off + i];
+      }
+      Mo[M.poff + i] = m[M.off + i];
+    }
+  }
+}
+
+// per-simulation minimum and maximum mass (out[2 s], out[2 s + 1])
+__global__ void __launch_bounds__(256)
+    k_minmax_batch(const SimMeta* __restrict__ meta, int n_sims, const double* __restrict__ m,
+                   double* __restrict__ out) {
+  __shared__ double smin[8], smax[8];
+  for (int s = blockIdx.x; s < n_sims; s += gridDim.x) {
+    const SimMeta M = meta[s];
+    double lo = INFINITY, hi = -INFINITY;
+    for (int64_t i = threadIdx.x; i < M.n; i += 256) {
+      lo = fmin(lo, m[M.poff + i]);
+      hi = fmax(hi, m[M.poff + i]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fmin(lo, __shfl_down_sync(0xffffffffu, lo, o));
+      hi = fmax(hi, __shfl_down_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      smin[threadIdx.x >> 5] = lo;
+      smax[threadIdx.x >> 5] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int k = 1; k < 8; ++k) {
+        lo = fmin(lo, smin[k]);
+        hi = fmax(hi, smax[k]);
+      }
+      out[2 * s] = lo;
+      out[2 * s + 1] = hi;
+    }
+    __syncthreads();
+  }
+}
+
 #define BCK(call)                              \
   do {                                         \
     cudaError_t e_ = (call);                   \
@@ -327,6 +382,7 @@ int build_plan(Batch* b, int k) {
     M.npad = b->npad[s];
     M.poff = b->poff[s];
     M.n = b->n[s];
+    M.off = b->off[s];
     M.ntiles = (int)(M.npad / (2 * c.tj));
     M.mscale = b->eqm ? b->m_eq[s] : 1.0;
     int S = (int)std::max<int64_t>(1, (M.npad + c.jchunk / 2) / c.jchunk);
@@ -527,34 +583,66 @@ int batch_set_params(Batch* b, const nbody_params* p) {
   return upload(b);
 }
 
-int batch_set_state(Batch* b, const double* x, const double* v, const double* m) {
-  for (int s = 0; s < b->n_sims; ++s) {
-    const size_t bytes = (size_t)b->n[s] * sizeof(double);
-    for (int d = 0; d < 3; ++d) {
-      BCK(cudaMemcpyAsync(b->x + d * b->ptot + b->poff[s], x + d * b->ntot + b->off[s],
-                          bytes, cudaMemcpyDefault, b->user));
-      BCK(cudaMemcpyAsync(b->v + d * b->ptot + b->poff[s], v + d * b->ntot + b->off[s],
-                          bytes, cudaMemcpyDefault, b->user));
-    }
-    BCK(cudaMemcpyAsync(b->m + b->poff[s], m + b->off[s], bytes, cudaMemcpyDefault, b->user));
+bool on_device(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
   }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int batch_set_state(Batch* b, const double* x, const double* v, const double* m) {
+  // host inputs are first copied whole (three copies), then every
+  // simulation is gathered into its padded place by one kernel
+  double* tmp = nullptr;
+  const bool dev = on_device(x) && on_device(v) && on_device(m);
+  if (!dev) {
+    BCK(cudaMalloc((void**)&tmp, 7 * (size_t)b->ntot * sizeof(double)));
+    const size_t n3 = 3 * (size_t)b->ntot;
+    if (cudaMemcpyAsync(tmp, x, n3 * sizeof(double), cudaMemcpyDefault, b->user) ||
+        cudaMemcpyAsync(tmp + n3, v, n3 * sizeof(double), cudaMemcpyDefault, b->user) ||
+        cudaMemcpyAsync(tmp + 2 * n3, m, (size_t)b->ntot * sizeof(double), cudaMemcpyDefault,
+                        b->user)) {
+      cudaStreamSynchronize(b->user);
+      cudaFree(tmp);
+      return NBODY_ECUDA;
+    }
+    x = tmp;
+    v = tmp + n3;
+    m = tmp + 2 * n3;
+  }
+  int64_t nmax = 1;
+  for (int s = 0; s < b->n_sims; ++s) nmax = std::max(nmax, b->n[s]);
+  dim3 grid((unsigned)std::min<int64_t>((nmax + 255) / 256, 64),
+            (unsigned)std::min(b->n_sims, 65535));
+  k_gather_batch<<<grid, 256, 0, b->user>>>(b->meta, b->n_sims, x, v, m, b->ntot, b->ptot,
+                                            b->x, b->v, b->m);
+  count_launch();
+  cudaError_t eg = cudaGetLastError();
   // equal masses within every simulation select the kernels that leave the
   // mass out of the pair sums
   double* mm = nullptr;
-  BCK(cudaMalloc((void**)&mm, 2 * (size_t)b->n_sims * sizeof(double)));
-  for (int s = 0; s < b->n_sims; ++s) {
-    const cudaError_t e = launch_minmax(b->m + b->poff[s], b->n[s], mm + 2 * s, b->user);
-    if (e != cudaSuccess) {
-      cudaFree(mm);
-      return NBODY_ECUDA;
-    }
+  if (eg == cudaSuccess &&
+      cudaMalloc((void**)&mm, 2 * (size_t)b->n_sims * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    eg = cudaErrorMemoryAllocation;
+  }
+  if (eg == cudaSuccess) {
+    k_minmax_batch<<<(unsigned)std::min(b->n_sims, 65535), 256, 0, b->user>>>(
+        b->meta, b->n_sims, b->m, mm);
+    count_launch();
+    eg = cudaGetLastError();
   }
   std::vector<double> hmm(2 * (size_t)b->n_sims);
-  const cudaError_t em = cudaMemcpyAsync(hmm.data(), mm, hmm.size() * sizeof(double),
-                                         cudaMemcpyDeviceToHost, b->user);
+  cudaError_t em = cudaSuccess;
+  if (eg == cudaSuccess)
+    em = cudaMemcpyAsync(hmm.data(), mm, hmm.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                         b->user);
   const cudaError_t es = cudaStreamSynchronize(b->user);
-  cudaFree(mm);
-  if (em != cudaSuccess || es != cudaSuccess) return NBODY_ECUDA;
+  if (mm) cudaFree(mm);
+  if (tmp) cudaFree(tmp);
+  if (eg != cudaSuccess || em != cudaSuccess || es != cudaSuccess) return NBODY_ECUDA;
   bool eqm = true;
   b->m_eq.assign(b->n_sims, 1.0);
   for (int s = 0; s < b->n_sims; ++s) {

@@ -1148,4 +1148,27 @@ int nbody_pair_accel(int64_t n, const double* x, const double* m, double G,
   return rc;
 }
 
+int nbody_ext_accel(const nbody_params* p, int64_t n, const double* x, double* acc,
+                    void* cuda_stream) {
+  if (!p || n < 1 || !x || !acc) return NBODY_EINVAL;
+  int rc = check_params(p);
+  if (rc) return rc;
+  int dev = 0, sms = 0;
+  if ((rc = check_device(&dev, &sms))) return rc;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const size_t bytes = (size_t)3 * n * sizeof(double);
+  double* buf = nullptr;
+  if (cudaMallocAsync((void**)&buf, 2 * bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    return NBODY_ENOMEM;
+  }
+  cudaError_t e = cudaMemcpyAsync(buf, x, bytes, cudaMemcpyDefault, s);
+  if (e == cudaSuccess) e = nb::launch_ext_accel(to_dev(*p), buf, n, buf + 3 * n, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(acc, buf + 3 * n, bytes, cudaMemcpyDefault, s);
+  rc = e == cudaSuccess ? NBODY_OK : NBODY_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) rc = NBODY_ECUDA;
+  cudaFreeAsync(buf, s);
+  return rc;
+}
+
 }  // extern "C"

@@ -166,6 +166,8 @@ int adjoint_blocks(int64_t n);
 
 // out[0..1] = min and max of m[0..n)
 cudaError_t launch_minmax(const double* m, int64_t n, double* out, cudaStream_t s);
+cudaError_t launch_ext_accel(const DevParams& P, const double* x, int64_t n, double* acc,
+                             cudaStream_t s);
 
 cudaError_t launch_reduce_rows(const double* blk, int nblk, int ncol,
                                double* out, cudaStream_t s);

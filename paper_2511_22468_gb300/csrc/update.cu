@@ -239,6 +239,17 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
   }
 }
 
+// external acceleration at caller points (3 x n SoA in and out)
+__global__ void k_ext_accel(DevParams P, const double* __restrict__ x, int64_t n,
+                            double* __restrict__ acc) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double a[3];
+  ext_accel(P, x[i], x[n + i], x[2 * n + i], a);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) acc[d * n + i] = a[d];
+}
+
 // ------------------------------------------------------------ reductions etc
 __global__ void __launch_bounds__(256)
     k_reduce_rows(const double* __restrict__ blk, int nblk, int ncol,
@@ -396,6 +407,13 @@ cudaError_t launch_stage_vjp(const double* x, const double* m,
 }
 
 int adjoint_blocks(int64_t n) { return (int)blocks_for(n, particle_threads(n)); }
+
+cudaError_t launch_ext_accel(const DevParams& P, const double* x, int64_t n, double* acc,
+                             cudaStream_t s) {
+  k_ext_accel<<<blocks_for(n, 256), 256, 0, s>>>(P, x, n, acc);
+  count_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t launch_minmax(const double* m, int64_t n, double* out, cudaStream_t s) {
   k_minmax<<<1, 1024, 0, s>>>(m, n, out);

@@ -89,8 +89,12 @@ class GridSearch:
             nb.nbody_set_params_batch(self.h, [self._params(th, cm)
                                                for th, cm in zip(full, self.com)])
             nb.nbody_set_state(self.h, self.X, self.V, self.M)
-            if self.tuning is not None:
-                nb.nbody_set_tuning(self.h, self.tuning)
+            if self.tuning is None:
+                from . import autotune
+                self.tuning, _, _ = autotune.tune(self.h, [self.n] * B,
+                                                  torch.cuda.get_device_name(self.dev),
+                                                  probe_steps=2)
+            nb.nbody_set_tuning(self.h, self.tuning)
             sync()
             t1 = time.perf_counter()
             nb.nbody_integrate(self.h, self.steps)

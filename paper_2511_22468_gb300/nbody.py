@@ -50,7 +50,8 @@ EXPORTED = ("nbody_create", "nbody_destroy", "nbody_set_params",
             "nbody_get_pair_shape", "nbody_peaks", "nbody_autotune_pair",
             "nbody_potential_grad", "nbody_mmd_create", "nbody_mmd_eval",
             "nbody_mmd_eval_batch", "nbody_mmd_target_stats", "nbody_mmd_destroy",
-            "nbody_stream_set_target_cloud", "nbody_stream_initial_states")
+            "nbody_stream_set_target_cloud", "nbody_stream_initial_states",
+            "nbody_ext_accel")
 
 NBODY_NTUNE = 8
 
@@ -166,6 +167,7 @@ def lib():
         L.nbody_set_timing.argtypes = [vp, C.c_int]
         L.nbody_kernel_times.argtypes = [vp, dp, C.POINTER(i64)]
         L.nbody_potential_grad.argtypes = [vp, dp]
+        L.nbody_ext_accel.argtypes = [P, i64, vp, vp, vp]
         L.nbody_mmd_create.argtypes = [C.POINTER(vp), i64, i64, i64, vp, vp, dp, C.c_int,
                                        dp, vp]
         L.nbody_mmd_eval.argtypes = [vp, vp, vp, dp, vp, vp]
@@ -346,6 +348,13 @@ def nbody_pair_accel(x, m, G, eps, center, acc, stream=None):
     _check(lib().nbody_pair_accel(n, _ptr(x, (3, n)), _ptr(m, (n,)), G, eps,
                                   cen, _ptr(acc, (3, n)), _stream(stream)),
            "nbody_pair_accel")
+
+
+def nbody_ext_accel(params, x, acc, stream=None):
+    """External acceleration at the points x (3, n) into acc (3, n)."""
+    n = x.shape[1]
+    _check(lib().nbody_ext_accel(C.byref(params), n, _ptr(x, (3, n)), _ptr(acc, (3, n)),
+                                 _stream(stream)), "nbody_ext_accel")
 
 
 def nbody_pair_accel_noalloc(x, m, G, eps, center, acc, stream=None):
