@@ -205,10 +205,12 @@ NBODY_API int nbody_create_batch(nbody_ctx **out, int n_sims,
  * i-particles per thread, j-chunk length). */
 #define NBODY_NTUNE 8
 
-/* Time every candidate on the batch's current positions (probe_steps pair
- * launches each; the state is not advanced), select the fastest and return
- * its index in *best (may be NULL); ms (host, NBODY_NTUNE entries, may be
- * NULL) receives the time per launch of each.  Batch contexts only.
+/* Time every candidate on the batch's current positions (probe_steps whole
+ * steps each: the pair pass and the update, fused into one launch when every
+ * simulation takes one j-chunk, run with zero kick and no drift so that the
+ * state is not advanced), select the fastest and return its index in *best
+ * (may be NULL); ms (host, NBODY_NTUNE entries, may be NULL) receives the
+ * time per step of each.  Batch contexts only.
  * Synchronises.  Errors: EINVAL, ENOMEM, ECUDA. */
 NBODY_API int nbody_autotune(nbody_ctx *c, int64_t probe_steps, int *best,
                              double ms[NBODY_NTUNE]);

@@ -49,7 +49,62 @@ struct SimMeta {
   double mscale;  // multiplies the raw sums (the common mass with EQM, else 1)
 };
 
-// EQM: every simulation has equal masses; the sums leave the mass out
+// Pair sums of one work item w = (simulation, i-tile, j-chunk): FP32 within
+// a shared-memory tile of kTJ j-pairs, FP64 across tiles, into dax/day/daz.
+// EQM: every simulation has equal masses; the sums leave the mass out.
+template <int NT, int R, int kTJ, bool EQM>
+__device__ __forceinline__ void pair_item(const float4* __restrict__ st, const SimMeta& M,
+                                          int4 w, float4* sj, int64_t i0, double (&dax)[R],
+                                          double (&day)[R], double (&daz)[R]) {
+  const int t = threadIdx.x;
+  const int tile_b = (int)(((int64_t)w.z * M.ntiles) / M.S);
+  const int tile_e = (int)(((int64_t)(w.z + 1) * M.ntiles) / M.S);
+  const float4* sts = st + M.poff;  // one float4 per particle
+  float2 nx[R], ny[R], nz[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    float xi, yi, zi;
+    load_i(sts, i0 + r * NT, xi, yi, zi);
+    nx[r] = make_float2(-xi, -xi);
+    ny[r] = make_float2(-yi, -yi);
+    nz[r] = make_float2(-zi, -zi);
+    dax[r] = day[r] = daz[r] = 0.0;
+  }
+  const float2 e2 = make_float2(M.eps2f, M.eps2f);
+  for (int tile = tile_b; tile < tile_e; ++tile) {
+    __syncthreads();
+    const float4* src = sts + (int64_t)tile * (2 * kTJ);
+#pragma unroll
+    for (int q = t; q < 2 * kTJ; q += NT) sj[q] = src[q];
+    __syncthreads();
+    float2 ax[R], ay[R], az[R], ph[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) ax[r] = ay[r] = az[r] = ph[r] = make_float2(0.f, 0.f);
+#pragma unroll 2
+    for (int jj = 0; jj < kTJ; ++jj) {
+      const float4 A = sj[2 * jj];
+      const float4 B = sj[2 * jj + 1];
+      const float2 xj = make_float2(A.x, A.y), yj = make_float2(A.z, A.w);
+      const float2 zj = make_float2(B.x, B.y), mj = make_float2(B.z, B.w);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (EQM)
+          body_eqm(xj, yj, zj, nx[r], ny[r], nz[r], e2, ax[r], ay[r], az[r]);
+        else
+          body<false>(xj, yj, zj, mj, nx[r], ny[r], nz[r], e2, ax[r], ay[r], az[r], ph[r]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      dax[r] += (double)ax[r].x + (double)ax[r].y;
+      day[r] += (double)ay[r].x + (double)ay[r].y;
+      daz[r] += (double)az[r].x + (double)az[r].y;
+    }
+  }
+}
+
+// one pair pass for every simulation: persistent blocks take work items
+// (largest first) from an atomic counter; per-chunk partial sums to part
 template <int NT, int R, int kTJ, bool EQM>
 __global__ void __launch_bounds__(NT)
     k_pair_batch(const float4* __restrict__ st, const SimMeta* __restrict__ meta,
@@ -67,51 +122,8 @@ __global__ void __launch_bounds__(NT)
     const int4 w = items[it];
     const SimMeta M = meta[w.x];
     const int64_t i0 = (int64_t)w.y * (NT * R) + t;  // local index
-    const int tile_b = (int)(((int64_t)w.z * M.ntiles) / M.S);
-    const int tile_e = (int)(((int64_t)(w.z + 1) * M.ntiles) / M.S);
-    const float4* sts = st + M.poff;  // one float4 per particle
-    float2 nx[R], ny[R], nz[R];
     double dax[R], day[R], daz[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      float xi, yi, zi;
-      load_i(sts, i0 + r * NT, xi, yi, zi);
-      nx[r] = make_float2(-xi, -xi);
-      ny[r] = make_float2(-yi, -yi);
-      nz[r] = make_float2(-zi, -zi);
-      dax[r] = day[r] = daz[r] = 0.0;
-    }
-    const float2 e2 = make_float2(M.eps2f, M.eps2f);
-    for (int tile = tile_b; tile < tile_e; ++tile) {
-      __syncthreads();
-      const float4* src = sts + (int64_t)tile * (2 * kTJ);
-#pragma unroll
-      for (int q = t; q < 2 * kTJ; q += NT) sj[q] = src[q];
-      __syncthreads();
-      float2 ax[R], ay[R], az[R], ph[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) ax[r] = ay[r] = az[r] = ph[r] = make_float2(0.f, 0.f);
-#pragma unroll 2
-      for (int jj = 0; jj < kTJ; ++jj) {
-        const float4 A = sj[2 * jj];
-        const float4 B = sj[2 * jj + 1];
-        const float2 xj = make_float2(A.x, A.y), yj = make_float2(A.z, A.w);
-        const float2 zj = make_float2(B.x, B.y), mj = make_float2(B.z, B.w);
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          if (EQM)
-            body_eqm(xj, yj, zj, nx[r], ny[r], nz[r], e2, ax[r], ay[r], az[r]);
-          else
-            body<false>(xj, yj, zj, mj, nx[r], ny[r], nz[r], e2, ax[r], ay[r], az[r], ph[r]);
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        dax[r] += (double)ax[r].x + (double)ax[r].y;
-        day[r] += (double)ay[r].x + (double)ay[r].y;
-        daz[r] += (double)az[r].x + (double)az[r].y;
-      }
-    }
+    pair_item<NT, R, kTJ, EQM>(st, M, w, sj, i0, dax, day, daz);
     double* p = part + M.part_off + (int64_t)w.z * 3 * M.npad;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -121,6 +133,83 @@ __global__ void __launch_bounds__(NT)
       p[2 * M.npad + i] = daz[r];
     }
   }
+}
+
+// KDK update of one particle (global index g of simulation s) from its
+// complete pair sums (the arithmetic of the separate update kernel)
+__device__ __forceinline__ bool update_one(const DevParams& Q, const SimMeta& M, int s,
+                                           int64_t g, const double sum[3], double* x,
+                                           double* v, int64_t ptot, double kick, int drift,
+                                           const double* centers, int64_t cstride,
+                                           int64_t k_next, float4* st_next) {
+  double ap[3];
+  for (int d = 0; d < 3; ++d) ap[d] = Q.G * M.mscale * (0.0 + sum[d]);
+  double xx[3], vv[3];
+  for (int d = 0; d < 3; ++d) {
+    xx[d] = x[d * ptot + g];
+    vv[d] = v[d * ptot + g];
+  }
+  ExtUnit e;
+  ext_unit(Q, xx[0], xx[1], xx[2], e);
+  bool bad = false;
+  for (int d = 0; d < 3; ++d) {
+    vv[d] += kick * Q.dt * (ap[d] + Q.nfw_GM * e.n[d] + Q.mn_GM * e.d[d]);
+    if (drift) xx[d] += Q.dt * vv[d];
+    x[d * ptot + g] = xx[d];
+    v[d * ptot + g] = vv[d];
+    bad |= !isfinite(xx[d]) || !isfinite(vv[d]);
+  }
+  if (drift) {
+    const double* c = centers + (int64_t)s * cstride + 3 * k_next;
+    put_stage_xyz(st_next, g, (float)(xx[0] - c[0]), (float)(xx[1] - c[1]),
+                  (float)(xx[2] - c[2]));
+  }
+  return bad;
+}
+
+// Fused step for batches whose simulations each take one j-chunk: a work
+// item holds the complete pair sums of its i-tile, so the block applies the
+// kick (and drift) to those particles itself and stages them into the other
+// staging buffer.  FP64 update work of some blocks then overlaps the FP32
+// pair loops of others on the same SM (separate pipes).  The work counter
+// of the next step is re-armed here (ctr_next), this step's by the last.
+template <int NT, int R, int kTJ, bool EQM>
+__global__ void __launch_bounds__(NT)
+    k_step_batch(const float4* __restrict__ st, float4* __restrict__ st_next,
+                 const SimMeta* __restrict__ meta, const int4* __restrict__ items, int nitems,
+                 unsigned* __restrict__ ctr, unsigned* __restrict__ ctr_next,
+                 const DevParams* __restrict__ P, double* __restrict__ x,
+                 double* __restrict__ v, int64_t ptot, double kick, int drift,
+                 const double* __restrict__ centers, int64_t cstride, int64_t k_next,
+                 int* __restrict__ status) {
+  __shared__ float4 sj[2 * kTJ];
+  __shared__ int s_item;
+  const int t = threadIdx.x;
+  if (blockIdx.x == 0 && t == 0) *ctr_next = 0u;
+  bool bad = false;
+  for (;;) {
+    __syncthreads();
+    if (t == 0) s_item = (int)atomicAdd(ctr, 1u);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= nitems) break;
+    const int4 w = items[it];
+    const SimMeta M = meta[w.x];
+    const int64_t i0 = (int64_t)w.y * (NT * R) + t;
+    double dax[R], day[R], daz[R];
+    pair_item<NT, R, kTJ, EQM>(st, M, w, sj, i0, dax, day, daz);
+    const DevParams Q = P[w.x];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int64_t i = i0 + r * NT;
+      if (i < M.n) {
+        const double sum[3] = {dax[r], day[r], daz[r]};
+        bad |= update_one(Q, M, w.x, M.poff + i, sum, x, v, ptot, kick, drift, centers,
+                          cstride, k_next, st_next);
+      }
+    }
+  }
+  if (bad) atomicOr(status, kStatusNaN);
 }
 
 // one thread per simulation: FP32 recentring origins of every point
@@ -163,18 +252,21 @@ __global__ void __launch_bounds__(256)
     k_stage_batch(const SimMeta* __restrict__ meta, const int* __restrict__ blk_sim,
                   const double* __restrict__ x, const double* __restrict__ m,
                   int64_t ptot, const double* __restrict__ centers, int64_t cstride,
-                  float4* __restrict__ st) {
+                  float4* __restrict__ st, float4* __restrict__ st2) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int s = blk_sim[blockIdx.x];
   const SimMeta M = meta[s];
   const int64_t i = g - M.poff;
+  float px = kPadPos, py = kPadPos, pz = kPadPos, pm = 0.f;
   if (i < M.n) {
     const double* c = centers + (int64_t)s * cstride;
-    put_stage(st, g, (float)(x[g] - c[0]), (float)(x[ptot + g] - c[1]),
-              (float)(x[2 * ptot + g] - c[2]), (float)m[g]);
-  } else {
-    put_stage(st, g, kPadPos, kPadPos, kPadPos, 0.f);
+    px = (float)(x[g] - c[0]);
+    py = (float)(x[ptot + g] - c[1]);
+    pz = (float)(x[2 * ptot + g] - c[2]);
+    pm = (float)m[g];
   }
+  put_stage(st, g, px, py, pz, pm);
+  if (st2) put_stage(st2, g, px, py, pz, pm);
 }
 
 __global__ void __launch_bounds__(256)
@@ -299,6 +391,7 @@ struct Batch {
   double* guide = nullptr;  // [n_sims][6]
   double *x = nullptr, *v = nullptr, *m = nullptr;
   float4* st = nullptr;
+  float4* st2 = nullptr;    // second staging buffer of the fused step
   double* part = nullptr;
   size_t part_cap = 0;
   SimMeta* meta = nullptr;
@@ -312,6 +405,8 @@ struct Batch {
   int64_t centers_cap = -1;
   int tune = 0;
   int grid_pair = 0;
+  int grid_step = 0;
+  bool fused = false;          // every simulation takes one j-chunk: fused steps
   bool eqm = false;            // every simulation has equal masses
   std::vector<double> m_eq;    // their common masses
   cudaGraphExec_t exec = nullptr;
@@ -360,6 +455,19 @@ cudaError_t with_kernel(const Batch* b, int k, F f) {
 #define NB_K(NT, R, TJ)                                                         \
   if (c.nt == NT && c.r == R && c.tj == TJ)                                     \
     return b->eqm ? f(k_pair_batch<NT, R, TJ, true>, NT) : f(k_pair_batch<NT, R, TJ, false>, NT);
+  NB_K(128, 4, 512) NB_K(128, 2, 512) NB_K(256, 2, 512) NB_K(128, 8, 512)
+  NB_K(128, 4, 128) NB_K(128, 2, 128)
+#undef NB_K
+  return cudaErrorInvalidValue;
+}
+
+// calls f(kernel, threads) with the fused step kernel of candidate k
+template <class F>
+cudaError_t with_step_kernel(const Batch* b, int k, F f) {
+  const TuneCfg c = kTune[k];
+#define NB_K(NT, R, TJ)                                                         \
+  if (c.nt == NT && c.r == R && c.tj == TJ)                                     \
+    return b->eqm ? f(k_step_batch<NT, R, TJ, true>, NT) : f(k_step_batch<NT, R, TJ, false>, NT);
   NB_K(128, 4, 512) NB_K(128, 2, 512) NB_K(256, 2, 512) NB_K(128, 8, 512)
   NB_K(128, 4, 128) NB_K(128, 2, 128)
 #undef NB_K
@@ -435,6 +543,24 @@ int build_plan(Batch* b, int k) {
     occ = 1;
   }
   b->grid_pair = std::min(b->nitems, occ * b->sm_count);
+  bool fused = true;
+  for (const SimMeta& M : meta) fused = fused && M.S == 1;
+  if (fused != b->fused && b->exec) {  // the captured run bakes the kernels in
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  b->fused = fused;
+  if (fused) {
+    int occ2 = 1;
+    const cudaError_t e2 = with_step_kernel(b, k, [&](auto kern, int nt) {
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, kern, nt, 0);
+    });
+    if (e2 != cudaSuccess || occ2 < 1) {
+      cudaGetLastError();
+      occ2 = 1;
+    }
+    b->grid_step = std::min(b->nitems, occ2 * b->sm_count);
+  }
   b->tune = k;
   return NBODY_OK;
 }
@@ -467,14 +593,32 @@ int record_run(Batch* b, int64_t n_steps, cudaStream_t s, int* nodes) {
   const int64_t cs = 3 * (b->centers_cap + 1);
   const unsigned nblk = (unsigned)(b->ptot / 256);
   int cnt = 0;
-  BCK(cudaMemsetAsync(b->ctr, 0, sizeof(unsigned), s));
+  BCK(cudaMemsetAsync(b->ctr, 0, 2 * sizeof(unsigned), s));
   k_guide_batch<<<(b->n_sims + 63) / 64, 64, 0, s>>>(b->dp, b->mode, b->guide, b->n_sims,
                                                      n_steps, b->centers, cs);
   BCK(cudaGetLastError());
   k_stage_batch<<<nblk, 256, 0, s>>>(b->meta, b->blk_sim, b->x, b->m, b->ptot,
-                                     b->centers, cs, b->st);
+                                     b->centers, cs, b->st, b->fused ? b->st2 : nullptr);
   BCK(cudaGetLastError());
   cnt += 2;
+  if (b->fused) {
+    // one launch per step: pair sums and update of the same rows
+    float4* sbuf[2] = {b->st, b->st2};
+    const unsigned g = (unsigned)std::max(1, b->grid_step);
+    for (int64_t k = 0; k <= n_steps; ++k) {
+      const double kick = (k == 0 || k == n_steps) ? 0.5 : 1.0;
+      const int cur = (int)(k & 1);
+      BCK(with_step_kernel(b, b->tune, [&](auto kern, int nt) {
+        kern<<<g, nt, 0, s>>>(sbuf[cur], sbuf[1 - cur], b->meta, b->items, b->nitems,
+                              b->ctr + cur, b->ctr + (1 - cur), b->dp, b->x, b->v, b->ptot,
+                              kick, k < n_steps ? 1 : 0, b->centers, cs, k + 1, b->status);
+        return cudaGetLastError();
+      }));
+      cnt += 1;
+    }
+    *nodes = cnt;
+    return NBODY_OK;
+  }
   for (int64_t k = 0; k <= n_steps; ++k) {
     BCK(launch_pair_batch(b, s));
     const double kick = (k == 0 || k == n_steps) ? 0.5 : 1.0;
@@ -537,8 +681,9 @@ int batch_create(Batch** out, int n_sims, const int64_t* offsets,
   if ((rc = balloc(&b->dp, n_sims)) || (rc = balloc(&b->mode, n_sims)) ||
       (rc = balloc(&b->guide, 6 * (size_t)n_sims)) || (rc = balloc(&b->x, 3 * pt)) ||
       (rc = balloc(&b->v, 3 * pt)) || (rc = balloc(&b->m, pt)) ||
-      (rc = balloc(&b->st, pt)) || (rc = balloc(&b->meta, n_sims)) ||
-      (rc = balloc(&b->blk_sim, bs.size())) || (rc = balloc(&b->ctr, 1)) ||
+      (rc = balloc(&b->st, pt)) || (rc = balloc(&b->st2, pt)) ||
+      (rc = balloc(&b->meta, n_sims)) ||
+      (rc = balloc(&b->blk_sim, bs.size())) || (rc = balloc(&b->ctr, 2)) ||
       (rc = balloc(&b->status, 1))) {
     batch_destroy(b);
     return rc;
@@ -571,7 +716,7 @@ void batch_destroy(Batch* b) {
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
   bfree(b->dp); bfree(b->mode); bfree(b->guide); bfree(b->x); bfree(b->v);
-  bfree(b->m); bfree(b->st); bfree(b->part); bfree(b->meta); bfree(b->blk_sim);
+  bfree(b->m); bfree(b->st); bfree(b->st2); bfree(b->part); bfree(b->meta); bfree(b->blk_sim);
   bfree(b->items); bfree(b->ctr); bfree(b->status); bfree(b->centers);
   delete b;
 }
@@ -749,23 +894,41 @@ int batch_autotune(Batch* b, int64_t probe_steps, int* best, double* ms_out) {
                                                          0, b->centers, cs);
   BCK(cudaGetLastError());
   k_stage_batch<<<(unsigned)(b->ptot / 256), 256, 0, b->gs>>>(b->meta, b->blk_sim, b->x, b->m,
-                                                              b->ptot, b->centers, cs, b->st);
+                                                              b->ptot, b->centers, cs, b->st, nullptr);
   BCK(cudaGetLastError());
   cudaEvent_t e0, e1;
   BCK(cudaEventCreate(&e0));
   BCK(cudaEventCreate(&e1));
   double best_ms = 1e300;
   int best_k = b->tune;
+  // one probe = a whole step of the candidate (fused, or pair + update) with
+  // zero kick and no drift, which leaves positions and velocities as they are
+  const unsigned nblk = (unsigned)(b->ptot / 256);
+  auto probe = [&]() -> cudaError_t {
+    cudaError_t e = cudaMemsetAsync(b->ctr, 0, 2 * sizeof(unsigned), b->gs);
+    if (e != cudaSuccess) return e;
+    if (b->fused) {
+      const unsigned g = (unsigned)std::max(1, b->grid_step);
+      return with_step_kernel(b, b->tune, [&](auto kern, int nt) {
+        kern<<<g, nt, 0, b->gs>>>(b->st, b->st2, b->meta, b->items, b->nitems, b->ctr,
+                                  b->ctr + 1, b->dp, b->x, b->v, b->ptot, 0.0, 0, b->centers,
+                                  cs, 0, b->status);
+        return cudaGetLastError();
+      });
+    }
+    e = launch_pair_batch(b, b->gs);
+    if (e != cudaSuccess) return e;
+    k_update_batch<<<nblk, 256, 0, b->gs>>>(b->dp, b->meta, b->blk_sim, b->x, b->v, b->part,
+                                            b->ptot, 0.0, 0, b->centers, cs, 0, b->st,
+                                            b->status, b->ctr);
+    return cudaGetLastError();
+  };
   for (int k = 0; k < NBODY_NTUNE; ++k) {
     rc = build_plan(b, k);
     if (rc) break;
-    BCK(cudaMemsetAsync(b->ctr, 0, sizeof(unsigned), b->gs));
-    BCK(launch_pair_batch(b, b->gs));  // warm-up
+    BCK(probe());  // warm-up
     BCK(cudaEventRecord(e0, b->gs));
-    for (int64_t q = 0; q < probe_steps; ++q) {
-      BCK(cudaMemsetAsync(b->ctr, 0, sizeof(unsigned), b->gs));
-      BCK(launch_pair_batch(b, b->gs));
-    }
+    for (int64_t q = 0; q < probe_steps; ++q) BCK(probe());
     BCK(cudaEventRecord(e1, b->gs));
     BCK(cudaEventSynchronize(e1));
     float ms = 0.f;
@@ -777,7 +940,7 @@ int batch_autotune(Batch* b, int64_t probe_steps, int* best, double* ms_out) {
       best_k = k;
     }
   }
-  count_launch(2 + NBODY_NTUNE * (int)(probe_steps + 1));
+  count_launch(2 + 2 * NBODY_NTUNE * (int)(probe_steps + 1));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;

@@ -151,7 +151,8 @@ def run(n=1000, steps=1000, t_end=500.0, per_dim=10, batch=1024, refine_iters=10
                         "theta_obs": theta_obs.tolist(), "prior_width": width},
            "grid": {"time_s": t_grid, "sims_per_s": len(grid) / t_grid,
                     "pair_interactions_per_s": inter / gs.times["simulate_s"],
-                    "breakdown_s": dict(gs.times), "best_theta": best.tolist(),
+                    "breakdown_s": dict(gs.times), "launch_shape": gs.tuning,
+                    "best_theta": best.tolist(),
                     "best_loss": float(L[k]),
                     "best_err": float(np.max(np.abs(best / theta_obs - 1)))}}
     gs.close()

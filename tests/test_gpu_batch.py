@@ -133,3 +133,16 @@ def test_autotune_selects_a_candidate():
     nb.nbody_get_state(h, xo, None)
     assert torch.equal(xo, X)   # tuning does not advance the state
     nb.nbody_destroy(h)
+
+
+def test_fused_step_matches_separate_kernels():
+    """Launch shape 0 (j-chunks of 4096: every member here takes one chunk)
+    runs the fused pair + update step; shape 1 (chunks of 2048: the 2600
+    member takes two) runs separate pair and update kernels.  Same
+    arithmetic up to the order of the FP64 chunk sums."""
+    sims = _members()
+    fused = _run_batch(sims, 30, tuning=0)
+    split = _run_batch(sims, 30, tuning=1)
+    for xa, xb, s in zip(fused, split, sims):
+        scale = 1.0 if s[4].ext == 0 else C1.a_prog
+        assert np.abs(xa - xb).max() / scale <= 1e-10
