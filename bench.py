@@ -53,6 +53,7 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-grid", action="store_true")
     return ap.parse_args()
 
 
@@ -483,6 +484,15 @@ def run_ours(args):
     if not args.no_ensemble:
         ens = measure_ensemble(dev, props.name)
 
+    grid = None
+    if not args.no_grid:
+        # the point-cloud grid search at the paper's stage-1 size: 10^4
+        # simulations of 1000 particles, 1000 steps, ranked by batched MMD
+        from paper_2511_22468_gb300 import gridsearch
+        g = gridsearch.run(refine_iters=0, device=str(dev))
+        grid = {"workload": "grid_1e4_n1000_steps1000", **g["grid"],
+                "grid_points": g["workload"]["grid_points"]}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ra, rv = 8192, 1024
@@ -507,6 +517,7 @@ def run_ours(args):
                                   for k in ("pair", "vjp") if k in kernels},
                 "batched_sims_per_s": ens["sims_per_s"] * world if ens else None,
                 "ensemble": ens,
+                "grid_search": grid,
                 "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu,
                 "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
                 "parallelism": "replicas" if world > 1 else "single"}

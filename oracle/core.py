@@ -17,6 +17,7 @@ from .build import build_oracle
 NFW = 1
 MN = 2
 HARM = 4
+BULGE = 8
 
 
 class OrcParams(C.Structure):
@@ -24,7 +25,8 @@ class OrcParams(C.Structure):
                 ("ext", C.c_uint32), ("nfw_M", C.c_double),
                 ("nfw_rs", C.c_double), ("mn_M", C.c_double),
                 ("mn_a", C.c_double), ("mn_b", C.c_double),
-                ("omega2", C.c_double)]
+                ("omega2", C.c_double), ("bulge_M", C.c_double),
+                ("bulge_alpha", C.c_double), ("bulge_rc", C.c_double)]
 
 
 @dataclass
@@ -40,11 +42,15 @@ class Physics:
     mn_a: float = 0.0
     mn_b: float = 0.0
     omega2: float = 0.0
+    bulge_M: float = 0.0
+    bulge_alpha: float = 1.8
+    bulge_rc: float = 1.9
 
     def c(self) -> OrcParams:
         return OrcParams(self.G, self.eps, int(self.pair), self.ext,
                          self.nfw_M, self.nfw_rs, self.mn_M, self.mn_a,
-                         self.mn_b, self.omega2)
+                         self.mn_b, self.omega2, self.bulge_M, self.bulge_alpha,
+                         self.bulge_rc)
 
 
 _lib = None
@@ -78,6 +84,8 @@ def lib():
         L.orc_vjp.argtypes = [P, C.c_int64, _D, _D, _D, C.c_double, C.c_int64,
                               _D, _D, _D, _D, _D, _D]
         L.orc_vjp.restype = C.c_int
+        L.orc_bulge_mass.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double]
+        L.orc_bulge_mass.restype = C.c_double
         _lib = L
     return _lib
 
@@ -139,12 +147,12 @@ def pair_mass_vjp(x, G, eps, lam):
 
 
 def ext_accel_parts(ph: Physics, x3):
-    """(NFW, MN, harmonic) accelerations at one point, each shape (3,)."""
+    """(NFW, MN, harmonic, bulge) accelerations at one point, each shape (3,)."""
     x3 = _f64(x3, (3,))
-    out = np.zeros(9)
+    out = np.zeros(12)
     p = ph.c()
     lib().orc_ext_accel_parts(C.byref(p), _d(x3), _d(out))
-    return out.reshape(3, 3)
+    return out.reshape(4, 3)
 
 
 def ext_accel(ph: Physics, x3):
@@ -214,7 +222,7 @@ def vjp(ph: Physics, x0, v0, m, dt, nsteps, xbar, vbar, want_mbar=True):
     """Reverse-mode gradient of L(x_T, v_T) through integrate().
 
     Returns dict(x0bar, v0bar, mbar, dt_bar, nfw_M_bar, mn_M_bar, nfw_rs_bar,
-    mn_a_bar, mn_b_bar)."""
+    mn_a_bar, mn_b_bar, bulge_M_bar)."""
     x0 = _f64(x0, (-1, 3))
     v0 = _f64(v0, (-1, 3))
     m = _f64(m, (-1,))
@@ -224,11 +232,17 @@ def vjp(ph: Physics, x0, v0, m, dt, nsteps, xbar, vbar, want_mbar=True):
     x0b = np.zeros_like(x0)
     v0b = np.zeros_like(v0)
     mb = np.zeros(n) if want_mbar else None
-    pb = np.zeros(6)
+    pb = np.zeros(7)
     p = ph.c()
     rc = lib().orc_vjp(C.byref(p), n, _d(x0), _d(v0), _d(m), dt, nsteps,
                        _d(xbar), _d(vbar), _d(x0b), _d(v0b), _d(mb), _d(pb))
     if rc:
         raise MemoryError("oracle vjp failed (%d)" % rc)
     return dict(x0bar=x0b, v0bar=v0b, mbar=mb, dt_bar=pb[0], nfw_M_bar=pb[1],
-                mn_M_bar=pb[2], nfw_rs_bar=pb[3], mn_a_bar=pb[4], mn_b_bar=pb[5])
+                mn_M_bar=pb[2], nfw_rs_bar=pb[3], mn_a_bar=pb[4], mn_b_bar=pb[5],
+                bulge_M_bar=pb[6])
+
+
+def bulge_mass(M_b, alpha, r_c, r):
+    """Enclosed mass of the power-law bulge (quadrature of its density)."""
+    return lib().orc_bulge_mass(M_b, alpha, r_c, r)

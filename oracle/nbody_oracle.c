@@ -13,7 +13,8 @@
  *   - softened direct pairwise gravity (paper Sec. 1, "N-body codes": exact
  *     pairwise forces with softening, no tree or multipole), Plummer
  *     softening a_i = -G sum_{j!=i} m_j (x_i-x_j) (|x_i-x_j|^2+eps^2)^-3/2;
- *   - the NFW halo and Miyamoto-Nagai disk of MWPotential2014 (Sec. 2.2.1):
+ *   - the NFW halo, Miyamoto-Nagai disk and power-law bulge of
+ *     MWPotential2014 (Sec. 2.2.1, Sec. 3.1):
  *     potential, acceleration and the Jacobian of the acceleration;
  *   - the second-order Velocity-Verlet (kick-drift-kick) integrator with a
  *     fixed number of steps (Sec. 2.2.1);
@@ -38,6 +39,7 @@
 #define ORC_NFW 1u
 #define ORC_MN 2u
 #define ORC_HARM 4u
+#define ORC_BULGE 8u
 
 typedef struct orc_params {
   double G;      /* gravitational constant */
@@ -50,6 +52,9 @@ typedef struct orc_params {
   double mn_a;   /* MN scale length */
   double mn_b;   /* MN scale height */
   double omega2; /* harmonic test force */
+  double bulge_M;     /* bulge total mass */
+  double bulge_alpha; /* bulge inner power-law slope, 0 <= alpha < 3 */
+  double bulge_rc;    /* bulge cut-off radius */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -282,6 +287,103 @@ static void mn_unit_jac(double ma, double mb, const double *p, double J[9]) {
   J[8] = -((1.0 + ma * mb * mb / (B * B * B)) / S3 - 3.0 * q * q / S5);
 }
 
+/* Power-law bulge with an exponential cut-off, the bulge of MWPotential2014
+ * (Sec. 3.1): rho(r) = rho_0 (r/r_1)^-alpha exp(-(r/r_c)^2), normalised by
+ * its total mass M_b = 2 pi rho_0 r_1^alpha r_c^(3-alpha) Gamma(s),
+ * s = (3 - alpha)/2, so 4 pi rho_0 r_1^alpha = 2 M_b / (r_c^(3-alpha) Gamma(s)).
+ * Everything follows from the density by its definitions:
+ *   M(<r) = int_0^r 4 pi r'^2 rho dr'; with r' = r t^(1/(3-alpha))
+ *         = 4 pi rho_0 r_1^alpha r^(3-alpha)/(3-alpha)
+ *           int_0^1 exp(-(r/r_c)^2 t^(2/(3-alpha))) dt,
+ *   a = -G M(<r) x / r^3,  M'(r) = 4 pi r^2 rho(r),
+ *   Phi = -G M(<r)/r - G int_r^inf 4 pi r' rho(r') dr'; with
+ *         r' = r + r_c w/(1-w) the tail becomes an integral over [0, 1).
+ * Integrals by adaptive Simpson quadrature (relative tolerance 1e-15). */
+static double simpson_rec(double (*f)(double, const double *), const double *c,
+                          double a, double b, double fa, double fm, double fb,
+                          double whole, double tol, int depth) {
+  const double m = 0.5 * (a + b);
+  const double lm = 0.5 * (a + m), rm = 0.5 * (m + b);
+  const double flm = f(lm, c), frm = f(rm, c);
+  const double left = (m - a) / 6.0 * (fa + 4.0 * flm + fm);
+  const double right = (b - m) / 6.0 * (fm + 4.0 * frm + fb);
+  const double delta = left + right - whole;
+  if (depth <= 0 || fabs(delta) <= 15.0 * tol) return left + right + delta / 15.0;
+  return simpson_rec(f, c, a, m, fa, flm, fm, left, 0.5 * tol, depth - 1) +
+         simpson_rec(f, c, m, b, fm, frm, fb, right, 0.5 * tol, depth - 1);
+}
+
+static double simpson(double (*f)(double, const double *), const double *c, double a,
+                      double b, double rtol) {
+  const double fa = f(a, c), fb = f(b, c), fm = f(0.5 * (a + b), c);
+  const double whole = (b - a) / 6.0 * (fa + 4.0 * fm + fb);
+  /* a first pass fixes the scale of the absolute tolerance */
+  const double rough = simpson_rec(f, c, a, b, fa, fm, fb, whole, 1e-6 * fabs(whole) + 1e-300, 30);
+  return simpson_rec(f, c, a, b, fa, fm, fb, whole, rtol * fabs(rough) + 1e-300, 50);
+}
+
+/* c = {u = (r/r_c)^2, 2/(3-alpha)} */
+static double bulge_inner(double t, const double *c) {
+  return exp(-c[0] * pow(t, c[1]));
+}
+
+/* c = {r, r_c, alpha} ; integrand of int_r^inf r'^(1-alpha) exp(-(r'/r_c)^2) dr' */
+static double bulge_tail(double w, const double *c) {
+  if (w >= 1.0) return 0.0;
+  const double rp = c[0] + c[1] * w / (1.0 - w);
+  const double x = rp / c[1];
+  return pow(rp, 1.0 - c[2]) * exp(-x * x) * c[1] / ((1.0 - w) * (1.0 - w));
+}
+
+static double bulge_4pi_rho0r1a(double Mb, double alpha, double rc) {
+  const double s = 0.5 * (3.0 - alpha);
+  return 2.0 * Mb / (pow(rc, 3.0 - alpha) * tgamma(s));
+}
+
+/* enclosed mass M(<r) */
+static double bulge_mass(double Mb, double alpha, double rc, double r) {
+  if (r <= 0.0) return 0.0;
+  const double c[2] = {(r / rc) * (r / rc), 2.0 / (3.0 - alpha)};
+  return bulge_4pi_rho0r1a(Mb, alpha, rc) * pow(r, 3.0 - alpha) / (3.0 - alpha) *
+         simpson(bulge_inner, c, 0.0, 1.0, 1e-15);
+}
+
+/* unit-G acceleration of the bulge */
+static void bulge_accel(double Mb, double alpha, double rc, const double *p, double *a) {
+  const double r = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+  if (r == 0.0) {
+    a[0] = a[1] = a[2] = 0.0;
+    return;
+  }
+  const double f = bulge_mass(Mb, alpha, rc, r) / (r * r * r);
+  for (int d = 0; d < 3; ++d) a[d] = -f * p[d];
+}
+
+static double bulge_potential(double Mb, double alpha, double rc, const double *p) {
+  const double r = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+  const double c[3] = {r, rc, alpha};
+  const double tail = bulge_4pi_rho0r1a(Mb, alpha, rc) * simpson(bulge_tail, c, 0.0, 1.0, 1e-15);
+  return (r > 0.0 ? -bulge_mass(Mb, alpha, rc, r) / r : 0.0) - tail;
+}
+
+/* d a / d x per unit G: -[ f I + (f'/r) x x^T ], f = M/r^3,
+ * f' = M'(r)/r^3 - 3 M/r^4, M'(r) = 4 pi rho_0 r_1^alpha r^(2-alpha) exp(-(r/r_c)^2) */
+static void bulge_jac(double Mb, double alpha, double rc, const double *p, double J[9]) {
+  const double r = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+  const double M = bulge_mass(Mb, alpha, rc, r);
+  const double Mp = bulge_4pi_rho0r1a(Mb, alpha, rc) * pow(r, 2.0 - alpha) *
+                    exp(-(r / rc) * (r / rc));
+  const double f = M / (r * r * r);
+  const double fp = Mp / (r * r * r) - 3.0 * M / (r * r * r * r);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) J[3 * a + b] = -((a == b ? f : 0.0) + fp * p[a] * p[b] / r);
+}
+
+/* enclosed mass, exported for the quadrature's pins */
+double orc_bulge_mass(double Mb, double alpha, double rc, double r) {
+  return bulge_mass(Mb, alpha, rc, r);
+}
+
 /* Derivatives of the unit MN acceleration with respect to its shape
  * parameters.  With dS^2/da = 2 (a+B), dB/db = b/B, dS^2/db = 2 (a+B) b/B:
  *   d a_x/da = 3 x (a+B)/S^5,            (y alike)
@@ -307,7 +409,7 @@ static void mn_unit_dab(double ma, double mb, const double *p, double *ga,
  * parts[3..5] = MN, parts[6..8] = harmonic; each is the full acceleration
  * (G*M included) of that component, zero when the component is off. */
 void orc_ext_accel_parts(const orc_params *p, const double *x3, double *parts) {
-  memset(parts, 0, 9 * sizeof(double));
+  memset(parts, 0, 12 * sizeof(double));
   double u[3];
   if (p->ext & ORC_NFW) {
     nfw_unit_accel(p->nfw_rs, x3, u);
@@ -319,12 +421,16 @@ void orc_ext_accel_parts(const orc_params *p, const double *x3, double *parts) {
   }
   if (p->ext & ORC_HARM)
     for (int d = 0; d < 3; ++d) parts[6 + d] = -p->omega2 * x3[d];
+  if (p->ext & ORC_BULGE) {
+    bulge_accel(p->bulge_M, p->bulge_alpha, p->bulge_rc, x3, u);
+    for (int d = 0; d < 3; ++d) parts[9 + d] = p->G * u[d];
+  }
 }
 
 void orc_ext_accel(const orc_params *p, const double *x3, double *a3) {
-  double parts[9];
+  double parts[12];
   orc_ext_accel_parts(p, x3, parts);
-  for (int d = 0; d < 3; ++d) a3[d] = parts[d] + parts[3 + d] + parts[6 + d];
+  for (int d = 0; d < 3; ++d) a3[d] = parts[d] + parts[3 + d] + parts[6 + d] + parts[9 + d];
 }
 
 double orc_ext_potential(const orc_params *p, const double *x3) {
@@ -333,6 +439,8 @@ double orc_ext_potential(const orc_params *p, const double *x3) {
   if (p->ext & ORC_MN) phi += p->G * p->mn_M * mn_unit_potential(p->mn_a, p->mn_b, x3);
   if (p->ext & ORC_HARM)
     phi += 0.5 * p->omega2 * (x3[0] * x3[0] + x3[1] * x3[1] + x3[2] * x3[2]);
+  if (p->ext & ORC_BULGE)
+    phi += p->G * bulge_potential(p->bulge_M, p->bulge_alpha, p->bulge_rc, x3);
   return phi;
 }
 
@@ -350,6 +458,10 @@ void orc_ext_jac(const orc_params *p, const double *x3, double *J) {
   }
   if (p->ext & ORC_HARM)
     for (int d = 0; d < 3; ++d) J[4 * d] -= p->omega2;
+  if (p->ext & ORC_BULGE) {
+    bulge_jac(p->bulge_M, p->bulge_alpha, p->bulge_rc, x3, Ju);
+    for (int k = 0; k < 9; ++k) J[k] += p->G * Ju[k];
+  }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -446,7 +558,7 @@ static void kick_adjoint(const orc_params *p, int64_t n, const double *X,
     }
   }
   if (p->ext) {
-    double sn = 0.0, sm = 0.0, srs = 0.0, sa = 0.0, sb = 0.0;
+    double sn = 0.0, sm = 0.0, srs = 0.0, sa = 0.0, sb = 0.0, sbm = 0.0;
     for (int64_t i = 0; i < n; ++i) {
       double J[9], u[3];
       orc_ext_jac(p, &X[3 * i], J);
@@ -462,6 +574,10 @@ static void kick_adjoint(const orc_params *p, int64_t n, const double *X,
         nfw_unit_drs(p->nfw_rs, &X[3 * i], u);
         srs += p->G * p->nfw_M * (l[0] * u[0] + l[1] * u[1] + l[2] * u[2]);
       }
+      if (p->ext & ORC_BULGE) {
+        bulge_accel(1.0, p->bulge_alpha, p->bulge_rc, &X[3 * i], u);
+        sbm += p->G * (l[0] * u[0] + l[1] * u[1] + l[2] * u[2]);
+      }
       if (p->ext & ORC_MN) {
         double ga[3], gb[3];
         mn_unit_accel(p->mn_a, p->mn_b, &X[3 * i], u);
@@ -476,13 +592,14 @@ static void kick_adjoint(const orc_params *p, int64_t n, const double *X,
     pbar[3] += c * srs;
     pbar[4] += c * sa;
     pbar[5] += c * sb;
+    pbar[6] += c * sbm;
   }
 }
 
 /* Reverse-mode gradient of L(x_T, v_T) through orc_integrate from (x0, v0):
  * inputs xbar = dL/dx_T, vbar = dL/dv_T; outputs dL/dx0, dL/dv0, dL/dm
  * (mbar, optional) and pbar = {dL/ddt, dL/dM_NFW, dL/dM_MN, dL/dr_s,
- * dL/da_MN, dL/db_MN}.
+ * dL/da_MN, dL/db_MN, dL/dM_bulge}.
  * The forward trajectory is recomputed and kept in full.
  * Returns 0, or -2 on allocation failure. */
 int orc_vjp(const orc_params *p, int64_t n, const double *x0, const double *v0,
@@ -510,7 +627,7 @@ int orc_vjp(const orc_params *p, int64_t n, const double *x0, const double *v0,
   memcpy(x0bar, xbar_T, n3 * sizeof(double)); /* running xbar */
   memcpy(v0bar, vbar_T, n3 * sizeof(double)); /* running vbar */
   if (mbar) memset(mbar, 0, (size_t)n * sizeof(double));
-  for (int k = 0; k < 6; ++k) pbar[k] = 0.0;
+  for (int k = 0; k < 7; ++k) pbar[k] = 0.0;
   for (int64_t s = nsteps - 1; s >= 0; --s) {
     const double *Xs1 = &X[(size_t)(s + 1) * n3];
     const double *Xs = &X[(size_t)s * n3];
