@@ -63,6 +63,11 @@ extern "C" {
 /* ---- external potential components (Sec. 2.2.1) ---- */
 #define NBODY_EXT_NFW 1u /* NFW halo: Phi = -G M ln(1 + r/r_s) / r          */
 #define NBODY_EXT_MN 2u  /* Miyamoto-Nagai: Phi = -G M / sqrt(R^2 + (a + sqrt(z^2 + b^2))^2) */
+#define NBODY_EXT_BULGE 4u /* MWPotential2014's bulge (Sec. 3.1): density
+                              rho_0 (r/r_1)^-alpha exp(-(r/r_c)^2) of total
+                              mass M_b, a = -G M_b P(s, r^2/r_c^2) x / r^3,
+                              P the regularised incomplete gamma function,
+                              s = (3 - alpha)/2; 0 <= alpha < 2             */
 
 /* ---- FP32 recentring origin of the pair sum ---- */
 #define NBODY_CENTER_FIXED 0u /* origin = params.center for every step       */
@@ -83,7 +88,7 @@ typedef struct nbody_params {
   double dt;                /* time step; may be negative (backward orbit)   */
   int64_t checkpoint_every; /* K >= 1: integrate() records an adjoint tape
                                with a checkpoint every K steps; 0: no tape   */
-  uint32_t ext_flags;       /* NBODY_EXT_NFW | NBODY_EXT_MN                   */
+  uint32_t ext_flags;       /* NBODY_EXT_NFW | NBODY_EXT_MN | NBODY_EXT_BULGE */
   uint32_t center_mode;     /* NBODY_CENTER_FIXED or NBODY_CENTER_GUIDE      */
   uint32_t tape_mode;       /* NBODY_TAPE_KEEP_LAST or NBODY_TAPE_LEAN       */
   uint32_t reserved;        /* must be 0                                     */
@@ -95,6 +100,9 @@ typedef struct nbody_params {
   double center[3];         /* FP64 origin subtracted before the FP32 pair
                                sum (fixed) or the guide's start position     */
   double center_vel[3];     /* guide start velocity (CENTER_GUIDE)           */
+  double bulge_M;           /* bulge total mass M_b                          */
+  double bulge_alpha;       /* bulge inner slope, 0 <= alpha < 2             */
+  double bulge_rc;          /* bulge cut-off radius, > 0                     */
 } nbody_params;
 
 typedef struct nbody_ctx nbody_ctx; /* opaque, owned by the library */
@@ -152,13 +160,14 @@ NBODY_API int nbody_vjp(nbody_ctx *c, const double *xbar, const double *vbar,
               double *x0bar, double *v0bar, double *mbar_or_null,
               double theta_bar[4]);
 
-/* Gradient of the same loss with respect to the five parameters of the
- * external potential (Sec. 2.2.1; the parameter set of the Fisher analysis,
- * Sec. 3.2), from the last successful nbody_vjp of this context:
- * out (host, 5 doubles) = { dL/d nfw_M, dL/d nfw_rs, dL/d mn_M, dL/d mn_a,
- * dL/d mn_b }; zero for a component that is switched off.  Does not touch
- * the GPU.  Errors: EINVAL (batch context), ESTATE (no gradient yet). */
-NBODY_API int nbody_potential_grad(nbody_ctx *c, double out[5]);
+/* Gradient of the same loss with respect to the parameters of the external
+ * potential (Sec. 2.2.1; the first five are the parameter set of the Fisher
+ * analysis, Sec. 3.2), from the last successful nbody_vjp of this context:
+ * out (host, 6 doubles) = { dL/d nfw_M, dL/d nfw_rs, dL/d mn_M, dL/d mn_a,
+ * dL/d mn_b, dL/d bulge_M }; zero for a component that is switched off.
+ * Does not touch the GPU.  Errors: EINVAL (batch context), ESTATE (no
+ * gradient yet). */
+NBODY_API int nbody_potential_grad(nbody_ctx *c, double out[6]);
 
 /* Diagnostics of the current state: out = { K = sum m v^2 / 2,
  * W_pair = -G sum_{i<j} m_i m_j / sqrt(r_ij^2 + eps^2),

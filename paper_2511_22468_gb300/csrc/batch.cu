@@ -153,7 +153,7 @@ __device__ __forceinline__ bool update_one(const DevParams& Q, const SimMeta& M,
   ext_unit(Q, xx[0], xx[1], xx[2], e);
   bool bad = false;
   for (int d = 0; d < 3; ++d) {
-    vv[d] += kick * Q.dt * (ap[d] + Q.nfw_GM * e.n[d] + Q.mn_GM * e.d[d]);
+    vv[d] += kick * Q.dt * (ap[d] + Q.nfw_GM * e.n[d] + Q.mn_GM * e.d[d] + Q.bulge_GM * e.b[d]);
     if (drift) xx[d] += Q.dt * vv[d];
     x[d * ptot + g] = xx[d];
     v[d * ptot + g] = vv[d];
@@ -233,12 +233,12 @@ __global__ void k_guide_batch(const DevParams* __restrict__ P,
   ext_unit(Q, x[0], x[1], x[2], e);
   for (int64_t k = 0; k < n_steps; ++k) {
     for (int d = 0; d < 3; ++d) {
-      v[d] += 0.5 * Q.dt * (Q.nfw_GM * e.n[d] + Q.mn_GM * e.d[d]);
+      v[d] += 0.5 * Q.dt * (Q.nfw_GM * e.n[d] + Q.mn_GM * e.d[d] + Q.bulge_GM * e.b[d]);
       x[d] += Q.dt * v[d];
     }
     ext_unit(Q, x[0], x[1], x[2], e);
     for (int d = 0; d < 3; ++d) {
-      v[d] += 0.5 * Q.dt * (Q.nfw_GM * e.n[d] + Q.mn_GM * e.d[d]);
+      v[d] += 0.5 * Q.dt * (Q.nfw_GM * e.n[d] + Q.mn_GM * e.d[d] + Q.bulge_GM * e.b[d]);
       c[3 * (k + 1) + d] = x[d];
     }
   }
@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(256)
   ext_unit(Q, xx[0], xx[1], xx[2], e);
   bool bad = false;
   for (int d = 0; d < 3; ++d) {
-    vv[d] += kick * Q.dt * (ap[d] + Q.nfw_GM * e.n[d] + Q.mn_GM * e.d[d]);
+    vv[d] += kick * Q.dt * (ap[d] + Q.nfw_GM * e.n[d] + Q.mn_GM * e.d[d] + Q.bulge_GM * e.b[d]);
     if (drift) xx[d] += Q.dt * vv[d];
     x[d * ptot + g] = xx[d];
     v[d * ptot + g] = vv[d];
@@ -445,6 +445,7 @@ DevParams dev_params(const nbody_params& p) {
   d.mn_a = p.mn_a;
   d.mn_b = p.mn_b;
   d.eps2f = (float)(p.eps * p.eps);
+  if (p.ext_flags & NBODY_EXT_BULGE) set_bulge(d, p.G, p.bulge_M, p.bulge_alpha, p.bulge_rc);
   return d;
 }
 

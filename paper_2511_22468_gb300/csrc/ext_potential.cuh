@@ -1,7 +1,11 @@
 // ext_potential.cuh -- FP64 device functions of the external potential:
-// MWPotential2014's NFW halo and Miyamoto-Nagai disk (paper Sec. 2.2.1),
+// MWPotential2014's NFW halo, Miyamoto-Nagai disk and bulge (paper
+// Sec. 2.2.1, Sec. 3.1),
 //   NFW  Phi = -G M ln(1 + r/r_s) / r,
 //   MN   Phi = -G M / sqrt(R^2 + (a + sqrt(z^2 + b^2))^2),
+//   bulge rho = rho_0 (r/r_1)^-alpha exp(-(r/r_c)^2) with total mass M_b:
+//        M(<r) = M_b P(s, r^2/r_c^2), s = (3 - alpha)/2, a = -G M(<r) x / r^3,
+//        Phi = -G M_b [P(s, u)/r + Gamma(s - 1/2, u) / (r_c Gamma(s))],
 // their accelerations (per unit G M and full) and the Jacobian-vector
 // product of the acceleration.  Shared by the integrator, the adjoint and
 // the single-orbit kernels.
@@ -15,7 +19,64 @@ namespace nb {
 struct ExtUnit {
   double n[3];
   double d[3];
+  double b[3];
 };
+
+// Incomplete gamma functions by the series and the continued fraction of
+// Numerical Recipes (Press et al., Sec. 6.2; the fraction evaluated with
+// the modified Lentz method), each with a bounded number of terms:
+//   gamma(s, u) = e^-u u^s sum_{n>=0} u^n / (s (s+1) ... (s+n))   (u < s+1),
+//   Gamma(s, u) = e^-u u^s / (u + 1 - s - 1 (1-s) / (u + 3 - s - 2 (2-s) / ...)).
+// lnpre = s ln u - u.
+static __device__ __forceinline__ double igamma_lower_series(double s, double u,
+                                                             double lnpre) {
+  double ap = s, term = 1.0 / s, sum = term;
+  for (int k = 0; k < 400; ++k) {
+    ap += 1.0;
+    term *= u / ap;
+    sum += term;
+    if (fabs(term) < fabs(sum) * 1e-17) break;
+  }
+  return sum * exp(lnpre);
+}
+
+static __device__ __forceinline__ double igamma_upper_cf(double s, double u, double lnpre) {
+  const double tiny = 1e-300;
+  double b = u + 1.0 - s, c = 1.0 / tiny, d = 1.0 / b, h = d;
+  for (int i = 1; i < 400; ++i) {
+    const double an = -i * (i - s);
+    b += 2.0;
+    d = an * d + b;
+    if (fabs(d) < tiny) d = tiny;
+    c = b + an / c;
+    if (fabs(c) < tiny) c = tiny;
+    d = 1.0 / d;
+    const double del = d * c;
+    h *= del;
+    if (fabs(del - 1.0) < 1e-16) break;
+  }
+  return exp(lnpre) * h;
+}
+
+// regularised lower incomplete gamma P(s, u); 1 beyond u = 60, where
+// 1 - P < 1e-26
+static __device__ __forceinline__ double bulge_P(const DevParams& P, double u) {
+  if (u <= 0.0) return 0.0;
+  if (u > 60.0) return 1.0;
+  const double s = P.bulge_s;
+  const double lnpre = s * log(u) - u;
+  return u < s + 1.0 ? igamma_lower_series(s, u, lnpre) * P.bulge_igs
+                     : 1.0 - igamma_upper_cf(s, u, lnpre) * P.bulge_igs;
+}
+
+// upper incomplete gamma Gamma(s - 1/2, u) (not regularised), 0 < s - 1/2 <= 1
+static __device__ __forceinline__ double bulge_upper(const DevParams& P, double u) {
+  const double sh = P.bulge_s - 0.5;
+  if (u <= 0.0) return P.bulge_gsh;
+  const double lnpre = sh * log(u) - u;
+  return u < sh + 1.0 ? P.bulge_gsh - igamma_lower_series(sh, u, lnpre)
+                      : igamma_upper_cf(sh, u, lnpre);
+}
 
 static __device__ __forceinline__ double nfw_f(double r, double rs) {
   // a_NFW = -G M f(r) x, f(r) = ln(1 + r/r_s)/r^3 - 1/(r^2 (r + r_s));
@@ -91,6 +152,17 @@ static __device__ __forceinline__ void ext_unit(const DevParams& P, double x,
     e.d[1] = -y * iS3;
     e.d[2] = -z * aB * iB * iS3;
   }
+  e.b[0] = e.b[1] = e.b[2] = 0.0;
+  if (P.ext & NBODY_EXT_BULGE) {
+    const double r2 = x * x + y * y + z * z;
+    if (r2 > 0.0) {
+      const double ir = rsqrt_nr(r2);
+      const double f = bulge_P(P, r2 * P.bulge_irc2) * (ir * ir * ir);
+      e.b[0] = -f * x;
+      e.b[1] = -f * y;
+      e.b[2] = -f * z;
+    }
+  }
 }
 
 // full external acceleration (G M included) at one point
@@ -99,7 +171,7 @@ static __device__ __forceinline__ void ext_accel(const DevParams& P, double x, d
   ExtUnit e;
   ext_unit(P, x, y, z, e);
 #pragma unroll
-  for (int d = 0; d < 3; ++d) a[d] = P.nfw_GM * e.n[d] + P.mn_GM * e.d[d];
+  for (int d = 0; d < 3; ++d) a[d] = P.nfw_GM * e.n[d] + P.mn_GM * e.d[d] + P.bulge_GM * e.b[d];
 }
 
 // (d a_ext / d x) l, full accelerations (G M included); the Jacobian is
@@ -137,6 +209,24 @@ static __device__ __forceinline__ void ext_jvp(const DevParams& P, double x, dou
     out[0] -= P.mn_GM * (l[0] * iS3 - 3.0 * x * ql * iS5);
     out[1] -= P.mn_GM * (l[1] * iS3 - 3.0 * y * ql * iS5);
     out[2] -= P.mn_GM * (dz * l[2] * iS3 - 3.0 * q2 * ql * iS5);
+  }
+  if (P.ext & NBODY_EXT_BULGE) {
+    // J = -G M_b [ f I + (f'/r) x x^T ], f = P(s,u)/r^3, u = r^2/r_c^2,
+    // f'/r = (2/r_c^2) P'(u)/r^3 - 3 P/r^5, P'(u) = u^(s-1) e^-u / Gamma(s)
+    const double r2 = x * x + y * y + z * z;
+    if (r2 > 0.0) {
+      const double u = r2 * P.bulge_irc2;
+      const double ir = 1.0 / sqrt(r2);
+      const double ir3 = ir * ir * ir;
+      const double Pu = bulge_P(P, u);
+      const double dP = u > 700.0 ? 0.0 : exp((P.bulge_s - 1.0) * log(u) - u) * P.bulge_igs;
+      const double f = Pu * ir3;
+      const double g = 2.0 * P.bulge_irc2 * dP * ir3 - 3.0 * Pu * ir3 * ir * ir;
+      const double xl = x * l[0] + y * l[1] + z * l[2];
+      out[0] -= P.bulge_GM * (f * l[0] + g * xl * x);
+      out[1] -= P.bulge_GM * (f * l[1] + g * xl * y);
+      out[2] -= P.bulge_GM * (f * l[2] + g * xl * z);
+    }
   }
 }
 
@@ -188,6 +278,12 @@ static __device__ __forceinline__ double ext_potential(const DevParams& P, doubl
     const double B = sqrt(z * z + P.mn_b * P.mn_b);
     const double aB = P.mn_a + B;
     phi -= P.mn_GM / sqrt(x * x + y * y + aB * aB);
+  }
+  if (P.ext & NBODY_EXT_BULGE) {
+    const double r2 = x * x + y * y + z * z;
+    const double u = r2 * P.bulge_irc2;
+    const double inner = r2 > 0.0 ? bulge_P(P, u) / sqrt(r2) : 0.0;
+    phi -= P.bulge_GM * (inner + bulge_upper(P, u) * P.bulge_irc * P.bulge_igs);
   }
   return phi;
 }

@@ -88,7 +88,7 @@ struct nbody_ctx {
   double* mpart = nullptr;  // mass-gradient partial sums [Smax][npad], lazily
   double* mbar = nullptr;   // dL/dm [npad], lazily
   bool want_mbar = false;   // the sweep being recorded accumulates dL/dm
-  double pot_bar[5] = {0, 0, 0, 0, 0};  // last sweep's potential-parameter gradient
+  double pot_bar[6] = {0, 0, 0, 0, 0, 0};  // last sweep's potential-parameter gradient
   bool have_grad = false;
   int nblk = 0;
   int* status = nullptr;
@@ -128,12 +128,16 @@ int check_params(const nbody_params* p) {
   if (!(p->eps > 0.0) || !std::isfinite(p->eps)) return NBODY_EINVAL;
   if (!std::isfinite(p->G) || !std::isfinite(p->dt)) return NBODY_EINVAL;
   if (p->checkpoint_every < 0) return NBODY_EINVAL;
-  if (p->ext_flags & ~(NBODY_EXT_NFW | NBODY_EXT_MN)) return NBODY_EINVAL;
+  if (p->ext_flags & ~(NBODY_EXT_NFW | NBODY_EXT_MN | NBODY_EXT_BULGE)) return NBODY_EINVAL;
   if (p->center_mode > NBODY_CENTER_GUIDE) return NBODY_EINVAL;
   if (p->tape_mode > NBODY_TAPE_LEAN) return NBODY_EINVAL;
   if (p->reserved != 0) return NBODY_EINVAL;
   if ((p->ext_flags & NBODY_EXT_NFW) && !(p->nfw_rs > 0.0)) return NBODY_EINVAL;
   if ((p->ext_flags & NBODY_EXT_MN) && !(p->mn_b >= 0.0 && p->mn_a >= 0.0))
+    return NBODY_EINVAL;
+  if ((p->ext_flags & NBODY_EXT_BULGE) &&
+      !(std::isfinite(p->bulge_M) && p->bulge_alpha >= 0.0 && p->bulge_alpha < 2.0 &&
+        p->bulge_rc > 0.0 && std::isfinite(p->bulge_rc)))
     return NBODY_EINVAL;
   return NBODY_OK;
 }
@@ -150,6 +154,7 @@ DevParams to_dev(const nbody_params& p) {
   d.mn_a = p.mn_a;
   d.mn_b = p.mn_b;
   d.eps2f = (float)(p.eps * p.eps);
+  if (p.ext_flags & NBODY_EXT_BULGE) nb::set_bulge(d, p.G, p.bulge_M, p.bulge_alpha, p.bulge_rc);
   return d;
 }
 
@@ -847,12 +852,13 @@ int nbody_vjp(nbody_ctx* c, const double* xbar, const double* vbar,
   CK(cudaMemcpyAsync(h, c->red, sizeof(h), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   for (int q = 0; q < 4; ++q) theta_bar[q] = h[q];
-  // potential parameters in the order (M_NFW, r_s, M_MN, a_MN, b_MN)
+  // potential parameters in the order (M_NFW, r_s, M_MN, a_MN, b_MN, M_b)
   c->pot_bar[0] = h[2];
   c->pot_bar[1] = h[4];
   c->pot_bar[2] = h[3];
   c->pot_bar[3] = h[5];
   c->pot_bar[4] = h[6];
+  c->pot_bar[5] = h[7];
   c->have_grad = true;
   int st = 0;
   CK(cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost));
@@ -860,10 +866,10 @@ int nbody_vjp(nbody_ctx* c, const double* xbar, const double* vbar,
   return NBODY_OK;
 }
 
-int nbody_potential_grad(nbody_ctx* c, double out[5]) {
+int nbody_potential_grad(nbody_ctx* c, double out[6]) {
   if (!c || !out || c->batch) return NBODY_EINVAL;
   if (!c->have_grad) return NBODY_ESTATE;
-  for (int q = 0; q < 5; ++q) out[q] = c->pot_bar[q];
+  for (int q = 0; q < 6; ++q) out[q] = c->pot_bar[q];
   return NBODY_OK;
 }
 

@@ -37,6 +37,8 @@ struct DevParams {
   double dt;
   double nfw_GM, nfw_rs;
   double mn_GM, mn_a, mn_b;
+  // bulge: G M_b, s = (3 - alpha)/2, 1/r_c^2, 1/r_c, 1/Gamma(s), Gamma(s - 1/2)
+  double bulge_GM, bulge_s, bulge_irc2, bulge_irc, bulge_igs, bulge_gsh;
   uint32_t ext;
   uint32_t pad0;
   float eps2f;
@@ -46,8 +48,11 @@ struct DevParams {
 enum : int { kStatusNaN = 1, kStatusTimeout = 2 };
 
 // columns of the adjoint's block accumulators: dL/d dt, sum_j m_j dL/dm_j,
-// dL/dM_NFW, dL/dM_MN, dL/dr_s, dL/da_MN, dL/db_MN
-constexpr int kAdjCols = 7;
+// dL/dM_NFW, dL/dM_MN, dL/dr_s, dL/da_MN, dL/db_MN, dL/dM_bulge
+constexpr int kAdjCols = 8;
+
+// host: the bulge fields of DevParams from (M_b, alpha, r_c) and G
+void set_bulge(DevParams& d, double G, double M, double alpha, double rc);
 
 // ---- launch accounting ----
 void count_launch(int k = 1);

@@ -52,14 +52,14 @@ __global__ void k_orbit(DevParams P, double X0, double X1, double X2,
   for (int d = 0; d < 3; ++d) ox[d] = x[d];
   for (int64_t k = 0; k < ns; ++k) {
     for (int d = 0; d < 3; ++d) {
-      v[d] += 0.5 * P.dt * (P.nfw_GM * e.n[d] + P.mn_GM * e.d[d]);
+      v[d] += 0.5 * P.dt * (P.nfw_GM * e.n[d] + P.mn_GM * e.d[d] + P.bulge_GM * e.b[d]);
       ovh[3 * k + d] = v[d];
       x[d] += P.dt * v[d];
       ox[3 * (k + 1) + d] = x[d];
     }
     nb::ext_unit(P, x[0], x[1], x[2], e);
     for (int d = 0; d < 3; ++d)
-      v[d] += 0.5 * P.dt * (P.nfw_GM * e.n[d] + P.mn_GM * e.d[d]);
+      v[d] += 0.5 * P.dt * (P.nfw_GM * e.n[d] + P.mn_GM * e.d[d] + P.bulge_GM * e.b[d]);
   }
   for (int d = 0; d < 3; ++d) {
     g6[d] = x[d];
@@ -85,12 +85,12 @@ __global__ void k_orbit_batch(DevParams P0, double X0, double X1, double X2, dou
   nb::ext_unit(P, x[0], x[1], x[2], e);
   for (int64_t k = 0; k < ns; ++k) {
     for (int d = 0; d < 3; ++d) {
-      v[d] += 0.5 * P.dt * (P.nfw_GM * e.n[d] + P.mn_GM * e.d[d]);
+      v[d] += 0.5 * P.dt * (P.nfw_GM * e.n[d] + P.mn_GM * e.d[d] + P.bulge_GM * e.b[d]);
       x[d] += P.dt * v[d];
     }
     nb::ext_unit(P, x[0], x[1], x[2], e);
     for (int d = 0; d < 3; ++d)
-      v[d] += 0.5 * P.dt * (P.nfw_GM * e.n[d] + P.mn_GM * e.d[d]);
+      v[d] += 0.5 * P.dt * (P.nfw_GM * e.n[d] + P.mn_GM * e.d[d] + P.bulge_GM * e.b[d]);
   }
   for (int d = 0; d < 3; ++d) {
     g6[6 * b + d] = x[d];

@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(256) k_update(UpdateArgs a) {
   bool bad = false;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const double acc = ap[d] + P.nfw_GM * e.n[d] + P.mn_GM * e.d[d];
+    const double acc = ap[d] + P.nfw_GM * e.n[d] + P.mn_GM * e.d[d] + P.bulge_GM * e.b[d];
     v[d] += kick * acc;
   }
   if (a.drift) {
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const DevParams& P = *a.P;
   const int64_t np = a.npad;
-  double contrib[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  double contrib[kAdjCols] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   // scale of the cotangents this point's VJP was computed with, and the one
   // for the cotangents staged now (from the largest |lambda| at this point)
   const double s_here = a.lsc[a.slot];
@@ -182,15 +182,16 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
     ext_jvp(P, x[0], x[1], x[2], lam, jl);
     const double ck = a.ck * P.dt;
     double xb[3];
-    double la = 0.0, lp = 0.0, ln = 0.0, lm = 0.0;
+    double la = 0.0, lp = 0.0, ln = 0.0, lm = 0.0, lb = 0.0;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       xb[d] = a.xbar[d * np + i] + ck * (g[d] + jl[d]);
       lp += lam[d] * ap[d];
       ln += lam[d] * e.n[d];
       lm += lam[d] * e.d[d];
+      lb += lam[d] * e.b[d];
     }
-    la = lp + P.nfw_GM * ln + P.mn_GM * lm;
+    la = lp + P.nfw_GM * ln + P.mn_GM * lm + P.bulge_GM * lb;
     if (a.mpart) {  // per-particle mass gradient of this kick
       double sm = 0.0;
       for (int q = 0; q < a.S; ++q) sm += a.mpart[(int64_t)q * np + i];
@@ -206,6 +207,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
       contrib[4] = ck * sh[0];
       contrib[5] = ck * sh[1];
       contrib[6] = ck * sh[2];
+      contrib[7] = ck * P.G * lb;    // dL/d M_bulge
     }
     double vb[3] = {lam[0], lam[1], lam[2]};
     if (a.drift) {
@@ -281,12 +283,12 @@ __global__ void k_guide(const DevParams* __restrict__ Pp,
   for (int d = 0; d < 3; ++d) centers[d] = x[d];
   for (int64_t s = 0; s < n_steps; ++s) {
     for (int d = 0; d < 3; ++d) {
-      v[d] += 0.5 * P.dt * (P.nfw_GM * e.n[d] + P.mn_GM * e.d[d]);
+      v[d] += 0.5 * P.dt * (P.nfw_GM * e.n[d] + P.mn_GM * e.d[d] + P.bulge_GM * e.b[d]);
       x[d] += P.dt * v[d];
     }
     ext_unit(P, x[0], x[1], x[2], e);
     for (int d = 0; d < 3; ++d) {
-      v[d] += 0.5 * P.dt * (P.nfw_GM * e.n[d] + P.mn_GM * e.d[d]);
+      v[d] += 0.5 * P.dt * (P.nfw_GM * e.n[d] + P.mn_GM * e.d[d] + P.bulge_GM * e.b[d]);
       centers[3 * (s + 1) + d] = x[d];
     }
   }
@@ -407,6 +409,16 @@ cudaError_t launch_stage_vjp(const double* x, const double* m,
 }
 
 int adjoint_blocks(int64_t n) { return (int)blocks_for(n, particle_threads(n)); }
+
+void set_bulge(DevParams& d, double G, double M, double alpha, double rc) {
+  const double s = 0.5 * (3.0 - alpha);
+  d.bulge_GM = G * M;
+  d.bulge_s = s;
+  d.bulge_irc2 = 1.0 / (rc * rc);
+  d.bulge_irc = 1.0 / rc;
+  d.bulge_igs = 1.0 / std::tgamma(s);
+  d.bulge_gsh = std::tgamma(s - 0.5);
+}
 
 cudaError_t launch_ext_accel(const DevParams& P, const double* x, int64_t n, double* acc,
                              cudaStream_t s) {

@@ -30,6 +30,7 @@ NBODY_NOALLOC_MAX_N = 32768
 
 NBODY_EXT_NFW = 1
 NBODY_EXT_MN = 2
+NBODY_EXT_BULGE = 4
 NBODY_CENTER_FIXED = 0
 NBODY_CENTER_GUIDE = 1
 NBODY_TAPE_KEEP_LAST = 0
@@ -65,7 +66,9 @@ class nbody_params(C.Structure):
                 ("reserved", C.c_uint32), ("nfw_M", C.c_double),
                 ("nfw_rs", C.c_double), ("mn_M", C.c_double),
                 ("mn_a", C.c_double), ("mn_b", C.c_double),
-                ("center", C.c_double * 3), ("center_vel", C.c_double * 3)]
+                ("center", C.c_double * 3), ("center_vel", C.c_double * 3),
+                ("bulge_M", C.c_double), ("bulge_alpha", C.c_double),
+                ("bulge_rc", C.c_double)]
 
 
 class nbody_stream_cfg(C.Structure):
@@ -82,7 +85,8 @@ class nbody_stream_cfg(C.Structure):
 def make_params(G, eps, dt, checkpoint_every=0, ext_flags=0, nfw_M=0.0,
                 nfw_rs=1.0, mn_M=0.0, mn_a=0.0, mn_b=0.0, center=(0, 0, 0),
                 center_vel=(0, 0, 0), center_mode=NBODY_CENTER_FIXED,
-                tape_mode=NBODY_TAPE_KEEP_LAST) -> nbody_params:
+                tape_mode=NBODY_TAPE_KEEP_LAST, bulge_M=0.0, bulge_alpha=1.8,
+                bulge_rc=1.9) -> nbody_params:
     p = nbody_params()
     p.G, p.eps, p.dt = G, eps, dt
     p.checkpoint_every = int(checkpoint_every)
@@ -90,6 +94,7 @@ def make_params(G, eps, dt, checkpoint_every=0, ext_flags=0, nfw_M=0.0,
     p.nfw_M, p.nfw_rs, p.mn_M, p.mn_a, p.mn_b = nfw_M, nfw_rs, mn_M, mn_a, mn_b
     p.center[:] = [float(c) for c in center]
     p.center_vel[:] = [float(c) for c in center_vel]
+    p.bulge_M, p.bulge_alpha, p.bulge_rc = bulge_M, bulge_alpha, bulge_rc
     return p
 
 
@@ -281,8 +286,9 @@ def nbody_vjp(h, xbar, vbar, x0bar=None, v0bar=None, mbar=None):
 
 
 def nbody_potential_grad(h):
-    """(dL/dM_NFW, dL/dr_s, dL/dM_MN, dL/da_MN, dL/db_MN) of the last vjp."""
-    out = (C.c_double * 5)()
+    """(dL/dM_NFW, dL/dr_s, dL/dM_MN, dL/da_MN, dL/db_MN, dL/dM_bulge) of the
+    last vjp."""
+    out = (C.c_double * 6)()
     _check(lib().nbody_potential_grad(h, out), "nbody_potential_grad")
     return list(out)
 
@@ -652,7 +658,7 @@ def _run_fn():
                 thb = None
                 if want[3]:
                     th = ctx.theta_like
-                    thb = torch.tensor([tb[0]] + sim.potential_grad(), dtype=th.dtype,
+                    thb = torch.tensor([tb[0]] + sim.potential_grad()[:5], dtype=th.dtype,
                                        device=th.device)
                 return x0b, v0b, mb, thb, None, None
 
