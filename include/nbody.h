@@ -452,6 +452,76 @@ NBODY_API int nbody_mmd_target_stats(nbody_mmd *h, double mu[6], double scale[6]
 /* Release the evaluator; NULL is a no-op. */
 NBODY_API void nbody_mmd_destroy(nbody_mmd *h);
 
+/* ---- orbit fitting and the Fisher matrix (Sec. 3.2) ----
+ *
+ * The progenitor, a single particle, is integrated from its present-day
+ * point (X0, V0) forward and backward with kick-drift-kick steps of dt in
+ * the NFW + Miyamoto-Nagai field of theta = (M_NFW, r_s, M_MN, a_MN, b_MN),
+ * projected onto the stream frame (e1 towards X0 from the observer, pole
+ * along (X0 - observer) x V0): phi1, phi2 (rad), mu_phi1 cos phi2, mu_phi2
+ * (mas/yr, relative to the observer's velocity), v_h (km/s); interpolated
+ * linearly along phi1 at the observed phi1 values (an observation beyond
+ * the arc's end takes the end point) and compared by
+ *   chi^2 = sum_obs sum_q (model_q - obs_q)^2 / sigma_q^2,
+ * q = (phi2, mu_phi1 cos phi2, mu_phi2, v_h).  The arc runs forward while
+ * phi1 stays in [phi1_lo, phi1_hi] and increases, backward while it stays
+ * in the window and decreases, at most t_max each way.  Derivatives are
+ * exact (forward-mode dual numbers through orbit, projection and
+ * interpolation) with respect to xi = ln theta.  One GPU thread per
+ * parameter vector; all arithmetic FP64. */
+typedef struct nbody_orbitfit_cfg {
+  double G;                  /* gravitational constant                        */
+  double X0[3], V0[3];       /* present-day progenitor position, velocity     */
+  double observer[3];        /* observer position                             */
+  double observer_vel[3];    /* observer velocity                             */
+  double phi1_lo, phi1_hi;   /* window (rad), phi1_lo < 0 < phi1_hi           */
+  double dt;                 /* step, > 0                                     */
+  double t_max;              /* longest integration each way, >= dt           */
+  double sigma[4];           /* errors of phi2 (rad), mu1, mu2 (mas/yr), v_h (km/s) */
+} nbody_orbitfit_cfg;
+
+typedef struct nbody_orbitfit nbody_orbitfit; /* opaque, owned by the library */
+
+/* obs: n_obs rows (phi1, phi2, mu_phi1 cos phi2, mu_phi2, v_h), host, any
+ * order (copied, sorted by phi1).  Errors: EINVAL, ENODEV, ENOMEM, ECUDA. */
+NBODY_API int nbody_orbitfit_create(nbody_orbitfit **out, const nbody_orbitfit_cfg *cfg,
+                                    int64_t n_obs, const double *obs, void *cuda_stream);
+
+/* chi^2 at count parameter vectors theta (host, count x 5, all > 0) into
+ * chi2 (host, count); grad (count x 5, may be NULL) = d chi^2 / d ln theta;
+ * gn (count x 25, may be NULL) = the Gauss-Newton matrix
+ * sum (dr/d ln theta)(dr/d ln theta)^T of the scaled residuals r (half the
+ * Gauss-Newton Hessian of chi^2: the Fisher matrix of a Gaussian
+ * likelihood).  Synchronises.  Errors: EINVAL, ENOMEM, ECUDA. */
+NBODY_API int nbody_orbitfit_eval(nbody_orbitfit *h, int64_t count, const double *theta,
+                                  double *chi2, double *grad, double *gn);
+
+/* Levenberg-Marquardt on ln theta from count starts at once (one GPU thread
+ * each; max_iter in 1..10000): step (A + lambda diag A) delta = -grad/2,
+ * lambda divided by 10 on success and multiplied by 10 on failure; stops
+ * when chi^2 falls by less than 1e-12 of itself.  theta_out (count x 5),
+ * chi2_out (count), iters_out (count, may be NULL), host.  Synchronises.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+NBODY_API int nbody_orbitfit_lm(nbody_orbitfit *h, int64_t count, const double *theta0,
+                                int max_iter, double *theta_out, double *chi2_out,
+                                int *iters_out);
+
+/* Fisher matrix at theta: F = (1/2) d^2 chi^2 / d ln theta^2 by central
+ * differences (step in ln theta, 0 < step < 0.1) of the exact gradient,
+ * symmetrised; F_gn (may be NULL) the Gauss-Newton matrix at theta.  Both
+ * host, 5 x 5 row-major.  Errors: EINVAL, ENOMEM, ECUDA. */
+NBODY_API int nbody_orbitfit_fisher(nbody_orbitfit *h, const double *theta, double step,
+                                    double F[25], double F_gn[25]);
+
+/* The model arc at theta: *n_pts rows (phi1, phi2, mu1, mu2, v_h) by
+ * increasing phi1 into arc (host, max_pts x 5).  Errors: EINVAL, ESIZE
+ * (*n_pts > max_pts; *n_pts is set), ENOMEM, ECUDA. */
+NBODY_API int nbody_orbitfit_arc(nbody_orbitfit *h, const double *theta, int64_t max_pts,
+                                 double *arc, int64_t *n_pts);
+
+/* Release; NULL is a no-op. */
+NBODY_API void nbody_orbitfit_destroy(nbody_orbitfit *h);
+
 /* ---- density surrogate (the paper's outlook, Sec. 3: a neural network
  *      coupled to the solver) ---- */
 

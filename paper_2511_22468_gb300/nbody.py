@@ -52,7 +52,9 @@ EXPORTED = ("nbody_create", "nbody_destroy", "nbody_set_params",
             "nbody_potential_grad", "nbody_mmd_create", "nbody_mmd_eval",
             "nbody_mmd_eval_batch", "nbody_mmd_target_stats", "nbody_mmd_destroy",
             "nbody_stream_set_target_cloud", "nbody_stream_initial_states",
-            "nbody_ext_accel")
+            "nbody_ext_accel", "nbody_orbitfit_create", "nbody_orbitfit_eval",
+            "nbody_orbitfit_lm", "nbody_orbitfit_fisher", "nbody_orbitfit_arc",
+            "nbody_orbitfit_destroy")
 
 NBODY_NTUNE = 8
 
@@ -69,6 +71,13 @@ class nbody_params(C.Structure):
                 ("center", C.c_double * 3), ("center_vel", C.c_double * 3),
                 ("bulge_M", C.c_double), ("bulge_alpha", C.c_double),
                 ("bulge_rc", C.c_double)]
+
+
+class nbody_orbitfit_cfg(C.Structure):
+    _fields_ = [("G", C.c_double), ("X0", C.c_double * 3), ("V0", C.c_double * 3),
+                ("observer", C.c_double * 3), ("observer_vel", C.c_double * 3),
+                ("phi1_lo", C.c_double), ("phi1_hi", C.c_double), ("dt", C.c_double),
+                ("t_max", C.c_double), ("sigma", C.c_double * 4)]
 
 
 class nbody_stream_cfg(C.Structure):
@@ -173,6 +182,14 @@ def lib():
         L.nbody_kernel_times.argtypes = [vp, dp, C.POINTER(i64)]
         L.nbody_potential_grad.argtypes = [vp, dp]
         L.nbody_ext_accel.argtypes = [P, i64, vp, vp, vp]
+        OC = C.POINTER(nbody_orbitfit_cfg)
+        L.nbody_orbitfit_create.argtypes = [C.POINTER(vp), OC, i64, dp, vp]
+        L.nbody_orbitfit_eval.argtypes = [vp, i64, dp, dp, dp, dp]
+        L.nbody_orbitfit_lm.argtypes = [vp, i64, dp, C.c_int, dp, dp, C.POINTER(C.c_int)]
+        L.nbody_orbitfit_fisher.argtypes = [vp, dp, C.c_double, dp, dp]
+        L.nbody_orbitfit_arc.argtypes = [vp, dp, i64, dp, C.POINTER(i64)]
+        L.nbody_orbitfit_destroy.argtypes = [vp]
+        L.nbody_orbitfit_destroy.restype = None
         L.nbody_mmd_create.argtypes = [C.POINTER(vp), i64, i64, i64, vp, vp, dp, C.c_int,
                                        dp, vp]
         L.nbody_mmd_eval.argtypes = [vp, vp, vp, dp, vp, vp]
@@ -675,3 +692,66 @@ def simulate(sim: Simulation, x0, v0, m, n_steps: int, theta=None):
     lives in the context: run the backward before the context's next
     integration."""
     return _run_fn().apply(x0, v0, m, theta, sim, int(n_steps))
+
+
+# ---- orbit fitting (host numpy arrays in and out) ----
+def _dp(a):
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def nbody_orbitfit_create(cfg: nbody_orbitfit_cfg, obs, stream=None):
+    import numpy as np
+    obs, po = _dp(np.asarray(obs, float).reshape(-1, 5))
+    h = C.c_void_p()
+    _check(lib().nbody_orbitfit_create(C.byref(h), C.byref(cfg), obs.shape[0], po,
+                                       _stream(stream)), "nbody_orbitfit_create")
+    return h
+
+
+def nbody_orbitfit_eval(h, thetas, want_grad=True, want_gn=True):
+    """(chi2 (k,), grad (k, 5) or None, gn (k, 5, 5) or None)."""
+    import numpy as np
+    th, pt = _dp(np.asarray(thetas, float).reshape(-1, 5))
+    k = th.shape[0]
+    chi2, pc = _dp(np.zeros(k))
+    g, pg = _dp(np.zeros((k, 5))) if want_grad else (None, None)
+    a, pa = _dp(np.zeros((k, 5, 5))) if want_gn else (None, None)
+    _check(lib().nbody_orbitfit_eval(h, k, pt, pc, pg, pa), "nbody_orbitfit_eval")
+    return chi2, g, a
+
+
+def nbody_orbitfit_lm(h, theta0, max_iter=100):
+    """(theta (k, 5), chi2 (k,), iterations (k,))."""
+    import numpy as np
+    th, pt = _dp(np.asarray(theta0, float).reshape(-1, 5))
+    k = th.shape[0]
+    out, po = _dp(np.zeros((k, 5)))
+    chi2, pc = _dp(np.zeros(k))
+    its = (C.c_int * k)()
+    _check(lib().nbody_orbitfit_lm(h, k, pt, int(max_iter), po, pc, its), "nbody_orbitfit_lm")
+    return out, chi2, np.array(its[:], dtype=int)
+
+
+def nbody_orbitfit_fisher(h, theta, step=1e-4):
+    """(F, F_gn), 5 x 5 each, in ln theta."""
+    import numpy as np
+    th, pt = _dp(np.asarray(theta, float).reshape(5))
+    F, pf = _dp(np.zeros((5, 5)))
+    Fg, pg = _dp(np.zeros((5, 5)))
+    _check(lib().nbody_orbitfit_fisher(h, pt, float(step), pf, pg), "nbody_orbitfit_fisher")
+    return F, Fg
+
+
+def nbody_orbitfit_arc(h, theta, max_pts=20000):
+    import numpy as np
+    th, pt = _dp(np.asarray(theta, float).reshape(5))
+    arc, pa = _dp(np.zeros((max_pts, 5)))
+    n = C.c_int64()
+    _check(lib().nbody_orbitfit_arc(h, pt, max_pts, pa, C.byref(n)), "nbody_orbitfit_arc")
+    return arc[:n.value].copy()
+
+
+def nbody_orbitfit_destroy(h):
+    lib().nbody_orbitfit_destroy(h)
