@@ -499,19 +499,23 @@ NBODY_API int nbody_orbitfit_eval(nbody_orbitfit *h, int64_t count, const double
 /* Levenberg-Marquardt on ln theta from count starts at once (one GPU thread
  * each; max_iter in 1..10000): step (A + lambda diag A) delta = -grad/2,
  * lambda divided by 10 on success and multiplied by 10 on failure; stops
- * when chi^2 falls by less than 1e-12 of itself.  theta_out (count x 5),
- * chi2_out (count), iters_out (count, may be NULL), host.  Synchronises.
- * Errors: EINVAL, ENOMEM, ECUDA. */
+ * when an accepted step lowers chi^2 by less than 1e-10 of itself or when,
+ * at lambda <= 1e-3, the step's predicted decrease -grad.delta/2 is below
+ * 1e-6.  theta_lo, theta_hi (host,
+ * 5 each, both or neither) bound the trial points (projection onto the box
+ * in ln theta).  theta_out (count x 5), chi2_out (count), iters_out (count,
+ * may be NULL), host.  Synchronises.  Errors: EINVAL, ENOMEM, ECUDA. */
 NBODY_API int nbody_orbitfit_lm(nbody_orbitfit *h, int64_t count, const double *theta0,
-                                int max_iter, double *theta_out, double *chi2_out,
-                                int *iters_out);
+                                int max_iter, const double *theta_lo,
+                                const double *theta_hi, double *theta_out,
+                                double *chi2_out, int *iters_out);
 
-/* Fisher matrix at theta: F = (1/2) d^2 chi^2 / d ln theta^2 by central
- * differences (step in ln theta, 0 < step < 0.1) of the exact gradient,
- * symmetrised; F_gn (may be NULL) the Gauss-Newton matrix at theta.  Both
+/* Fisher matrix at theta: F = (1/2) d^2 chi^2 / d ln theta^2, exact
+ * (second-order forward-mode dual numbers through orbit, projection and
+ * interpolation); F_gn (may be NULL) the Gauss-Newton matrix at theta.  Both
  * host, 5 x 5 row-major.  Errors: EINVAL, ENOMEM, ECUDA. */
-NBODY_API int nbody_orbitfit_fisher(nbody_orbitfit *h, const double *theta, double step,
-                                    double F[25], double F_gn[25]);
+NBODY_API int nbody_orbitfit_fisher(nbody_orbitfit *h, const double *theta, double F[25],
+                                    double F_gn[25]);
 
 /* The model arc at theta: *n_pts rows (phi1, phi2, mu1, mu2, v_h) by
  * increasing phi1 into arc (host, max_pts x 5).  Errors: EINVAL, ESIZE

@@ -34,6 +34,18 @@ namespace {
 
 constexpr int kP = 5;  // parameters
 using D5 = Dual<kP>;
+using H5 = HDual<kP>;  // second order, for the exact Hessian
+
+template <class T>
+__device__ __forceinline__ T cst(double c);
+template <>
+__device__ __forceinline__ D5 cst<D5>(double c) {
+  return dconst<kP>(c);
+}
+template <>
+__device__ __forceinline__ H5 cst<H5>(double c) {
+  return hconst<kP>(c);
+}
 
 constexpr double kMasYr = 206.26480624709636;        // 1 rad/Myr in mas/yr
 constexpr double kKms = 1.0227121650537077e-3;       // 1 km/s in kpc/Myr
@@ -55,51 +67,57 @@ struct Acc {  // running chi^2, gradient (d chi^2 / d xi), Gauss-Newton matrix
   double A[kP][kP];
 };
 
+struct AccH : Acc {  // and the exact Hessian d^2 chi^2 / d xi^2
+  double H[kP][kP];
+};
+
 // NFW + MN acceleration in duals; th = (M_NFW, r_s, M_MN, a, b)
-__device__ void field(const FitCfg& c, const D5 x[3], const D5 th[kP], D5 a[3]) {
-  const D5 r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
-  const D5 r = dsqrt(r2);
-  const D5 u = r / th[1];
-  D5 f;
+template <class T>
+__device__ void field(const FitCfg& c, const T x[3], const T th[kP], T a[3]) {
+  const T r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+  const T r = dsqrt(r2);
+  const T u = r / th[1];
+  T f;
   if (u.v < 1e-4) {
     // Taylor series of the NFW f(r) below r = 1e-4 r_s
-    const D5 rs = th[1];
-    const D5 rs2 = rs * rs, rs3 = rs2 * rs;
-    f = dconst<kP>(0.5) / (rs2 * r) - dconst<kP>(2.0 / 3.0) / rs3 +
-        dconst<kP>(0.75) * r / (rs3 * rs) - dconst<kP>(0.8) * r2 / (rs3 * rs2);
+    const T rs = th[1];
+    const T rs2 = rs * rs, rs3 = rs2 * rs;
+    f = cst<T>(0.5) / (rs2 * r) - cst<T>(2.0 / 3.0) / rs3 + cst<T>(0.75) * r / (rs3 * rs) -
+        cst<T>(0.8) * r2 / (rs3 * rs2);
   } else {
-    f = (dlog1p(u) / r - dconst<kP>(1.0) / (r + th[1])) / r2;
+    f = (dlog1p(u) / r - cst<T>(1.0) / (r + th[1])) / r2;
   }
-  const D5 gmn = c.G * th[0];
-  const D5 B = dsqrt(x[2] * x[2] + th[4] * th[4]);
-  const D5 aB = th[3] + B;
-  const D5 S2 = x[0] * x[0] + x[1] * x[1] + aB * aB;
-  const D5 iS3 = dconst<kP>(1.0) / (S2 * dsqrt(S2));
-  const D5 gmd = c.G * th[2];
-  const D5 kn = gmn * f, kd = gmd * iS3;
+  const T gmn = c.G * th[0];
+  const T B = dsqrt(x[2] * x[2] + th[4] * th[4]);
+  const T aB = th[3] + B;
+  const T S2 = x[0] * x[0] + x[1] * x[1] + aB * aB;
+  const T iS3 = cst<T>(1.0) / (S2 * dsqrt(S2));
+  const T gmd = c.G * th[2];
+  const T kn = gmn * f, kd = gmd * iS3;
   a[0] = -(kn * x[0]) - kd * x[0];
   a[1] = -(kn * x[1]) - kd * x[1];
   a[2] = -(kn * x[2]) - kd * x[2] * aB / B;
 }
 
 // (phi1, phi2, mu1 [mas/yr], mu2 [mas/yr], v_h [km/s])
-__device__ void observe(const FitCfg& c, const D5 x[3], const D5 v[3], D5 q[5]) {
-  D5 d[3], w[3];
+template <class T>
+__device__ void observe(const FitCfg& c, const T x[3], const T v[3], T q[5]) {
+  T d[3], w[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     d[k] = x[k] - c.xo[k];
     w[k] = v[k] - c.vo[k];
   }
-  const D5 d1 = c.e1[0] * d[0] + c.e1[1] * d[1] + c.e1[2] * d[2];
-  const D5 d2 = c.e2[0] * d[0] + c.e2[1] * d[1] + c.e2[2] * d[2];
-  const D5 d3 = c.nv[0] * d[0] + c.nv[1] * d[1] + c.nv[2] * d[2];
-  const D5 w1 = c.e1[0] * w[0] + c.e1[1] * w[1] + c.e1[2] * w[2];
-  const D5 w2 = c.e2[0] * w[0] + c.e2[1] * w[1] + c.e2[2] * w[2];
-  const D5 w3 = c.nv[0] * w[0] + c.nv[1] * w[1] + c.nv[2] * w[2];
-  const D5 rho2 = d1 * d1 + d2 * d2;
-  const D5 D2 = rho2 + d3 * d3;
-  const D5 D = dsqrt(D2);
-  const D5 rho = dsqrt(rho2);
+  const T d1 = c.e1[0] * d[0] + c.e1[1] * d[1] + c.e1[2] * d[2];
+  const T d2 = c.e2[0] * d[0] + c.e2[1] * d[1] + c.e2[2] * d[2];
+  const T d3 = c.nv[0] * d[0] + c.nv[1] * d[1] + c.nv[2] * d[2];
+  const T w1 = c.e1[0] * w[0] + c.e1[1] * w[1] + c.e1[2] * w[2];
+  const T w2 = c.e2[0] * w[0] + c.e2[1] * w[1] + c.e2[2] * w[2];
+  const T w3 = c.nv[0] * w[0] + c.nv[1] * w[1] + c.nv[2] * w[2];
+  const T rho2 = d1 * d1 + d2 * d2;
+  const T D2 = rho2 + d3 * d3;
+  const T D = dsqrt(D2);
+  const T rho = dsqrt(rho2);
   q[0] = datan2(d2, d1);
   q[1] = dasin(d3 / D);
   q[2] = kMasYr * ((d1 * w2 - d2 * w1) / (rho * D));
@@ -124,10 +142,35 @@ __device__ void add_obs(const FitCfg& c, const double* ob, const D5 q[4], Acc& s
   }
 }
 
+// the same with second derivatives: d^2 chi^2 = 2 sum (r_a r_b + r r_ab)
+__device__ void add_obs(const FitCfg& c, const double* ob, const H5 q[4], AccH& s) {
+  H5 r[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) r[k] = c.isig[k] * (q[k] - ob[1 + k]);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    s.chi2 += r[k].v * r[k].v;
+    int p = 0;
+#pragma unroll
+    for (int a = 0; a < kP; ++a) {
+      s.g[a] += 2.0 * r[k].v * r[k].d[a];
+#pragma unroll
+      for (int b = 0; b < kP; ++b) s.A[a][b] += r[k].d[a] * r[k].d[b];
+#pragma unroll
+      for (int b = a; b < kP; ++b, ++p) {
+        const double hab = 2.0 * (r[k].d[a] * r[k].d[b] + r[k].v * r[k].h[p]);
+        s.H[a][b] += hab;
+        if (b != a) s.H[b][a] += hab;
+      }
+    }
+  }
+}
+
 // linear interpolation of (phi2, mu1, mu2, v_h) at phi1 = p between two
 // arc points
-__device__ void interp(const D5 qa[5], const D5 qb[5], double p, D5 out[4]) {
-  const D5 w = (p - qa[0]) / (qb[0] - qa[0]);
+template <class T>
+__device__ void interp(const T qa[5], const T qb[5], double p, T out[4]) {
+  const T w = (p - qa[0]) / (qb[0] - qa[0]);
 #pragma unroll
   for (int k = 0; k < 4; ++k) out[k] = qa[1 + k] + w * (qb[1 + k] - qa[1 + k]);
 }
@@ -136,13 +179,14 @@ __device__ void interp(const D5 qa[5], const D5 qb[5], double p, D5 out[4]) {
 // of that side: obs sorted by phi1; forward side j = jb, jb+1, .. n-1;
 // backward side j = jb, jb-1, .. 0.  arc_out (values, may be NULL) receives
 // the points, the count returned.
-__device__ int64_t half_arc(const FitCfg& c, const D5 th[kP], double sign, const double* obs,
-                            int n_obs, int jb, Acc& s, double* arc_out) {
-  D5 x[3], v[3], a[3], q[5], qp[5];
+template <class T, class S>
+__device__ int64_t half_arc(const FitCfg& c, const T th[kP], double sign, const double* obs,
+                            int n_obs, int jb, S& s, double* arc_out) {
+  T x[3], v[3], a[3], q[5], qp[5];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    x[k] = dconst<kP>(c.X0[k]);
-    v[k] = dconst<kP>(c.V0[k]);
+    x[k] = cst<T>(c.X0[k]);
+    v[k] = cst<T>(c.V0[k]);
   }
   observe(c, x, v, q);
   int64_t npts = 1;
@@ -171,7 +215,7 @@ __device__ int64_t half_arc(const FitCfg& c, const D5 th[kP], double sign, const
     }
     // observations between the previous and this point
     while (j >= 0 && j < n_obs && sign * (obs[5 * j] - q[0].v) < 0.0) {
-      D5 m[4];
+      T m[4];
       interp(qp, q, obs[5 * j], m);
       add_obs(c, obs + 5 * j, m, s);
       j += dj;
@@ -182,7 +226,7 @@ __device__ int64_t half_arc(const FitCfg& c, const D5 th[kP], double sign, const
   }
   // observations beyond the arc's end take the end point
   while (j >= 0 && j < n_obs) {
-    D5 m[4] = {q[1], q[2], q[3], q[4]};
+    T m[4] = {q[1], q[2], q[3], q[4]};
     add_obs(c, obs + 5 * j, m, s);
     j += dj;
   }
@@ -226,6 +270,38 @@ __global__ void k_fit_eval(FitCfg c, const double* __restrict__ obs, int n_obs, 
       for (int b = 0; b < kP; ++b) gn[kP * kP * t + kP * a + b] = s.A[a][b];
 }
 
+// chi^2, gradient, Gauss-Newton matrix and exact Hessian (second-order
+// duals; d theta / d xi = d^2 theta / d xi^2 = theta)
+__global__ void k_fit_hess(FitCfg c, const double* __restrict__ obs, int n_obs, int split,
+                           const double* __restrict__ xi, double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  H5 th[kP];
+  for (int k = 0; k < kP; ++k) {
+    const double t = exp(xi[k]);
+    th[k] = hconst<kP>(t);
+    th[k].d[k] = t;
+    int p = 0;  // index of (k, k) in the upper triangle
+    for (int i = 0; i < k; ++i) p += kP - i;
+    th[k].h[p] = t;
+  }
+  AccH s;
+  s.chi2 = 0.0;
+  for (int a = 0; a < kP; ++a) {
+    s.g[a] = 0.0;
+    for (int b = 0; b < kP; ++b) s.A[a][b] = s.H[a][b] = 0.0;
+  }
+  half_arc(c, th, 1.0, obs, n_obs, split, s, nullptr);
+  half_arc(c, th, -1.0, obs, n_obs, split - 1, s, nullptr);
+  out[0] = s.chi2;
+  for (int a = 0; a < kP; ++a) {
+    out[1 + a] = s.g[a];
+    for (int b = 0; b < kP; ++b) {
+      out[1 + kP + kP * a + b] = s.A[a][b];
+      out[1 + kP + kP * kP + kP * a + b] = s.H[a][b];
+    }
+  }
+}
+
 // solve (A + lam diag(A)) x = b by Cholesky; false if not positive definite
 __device__ bool damped_solve(const double A[kP][kP], double lam, const double b[kP],
                              double x[kP]) {
@@ -262,8 +338,8 @@ __device__ bool damped_solve(const double A[kP][kP], double lam, const double b[
 // (A + lam diag A) delta = -g/2 (A the Gauss-Newton matrix, g = d chi^2/d xi)
 __global__ void k_fit_lm(FitCfg c, const double* __restrict__ obs, int n_obs, int split,
                          const double* __restrict__ xi0, int count, int max_iter,
-                         double* __restrict__ xi_out, double* __restrict__ chi2_out,
-                         int* __restrict__ iters_out) {
+                         const double* __restrict__ bounds, double* __restrict__ xi_out,
+                         double* __restrict__ chi2_out, int* __restrict__ iters_out) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= count) return;
   double xi[kP], xn[kP], delta[kP], rhs[kP];
@@ -279,14 +355,22 @@ __global__ void k_fit_lm(FitCfg c, const double* __restrict__ obs, int n_obs, in
       if (lam > 1e12) break;
       continue;
     }
-    for (int k = 0; k < kP; ++k) xn[k] = xi[k] + delta[k];
+    // predicted decrease of the damped Gauss-Newton step: converged when it
+    // is below 1e-6 in chi^2 (a millionth of one standard deviation)
+    double pred = 0.0;
+    for (int k = 0; k < kP; ++k) pred -= 0.5 * cur.g[k] * delta[k];
+    if (lam <= 1e-3 && pred < 1e-6) break;
+    for (int k = 0; k < kP; ++k) {
+      xn[k] = xi[k] + delta[k];
+      if (bounds) xn[k] = fmin(fmax(xn[k], bounds[k]), bounds[kP + k]);  // box in ln theta
+    }
     evaluate(c, obs, n_obs, split, xn, trial);
     if (isfinite(trial.chi2) && trial.chi2 < cur.chi2) {
       const double drop = cur.chi2 - trial.chi2;
       for (int k = 0; k < kP; ++k) xi[k] = xn[k];
       cur = trial;
       lam = fmax(lam * 0.1, 1e-12);
-      if (drop <= 1e-12 * cur.chi2 + 1e-300) break;
+      if (drop <= 1e-10 * cur.chi2 + 1e-300) break;
     } else {
       lam *= 10.0;
       if (lam > 1e12) break;
@@ -470,14 +554,31 @@ int nbody_orbitfit_eval(nbody_orbitfit* h, int64_t count, const double* theta, d
 }
 
 int nbody_orbitfit_lm(nbody_orbitfit* h, int64_t count, const double* theta0, int max_iter,
-                      double* theta_out, double* chi2_out, int* iters_out) {
+                      const double* theta_lo, const double* theta_hi, double* theta_out,
+                      double* chi2_out, int* iters_out) {
   if (!h || count < 1 || count > (1 << 24) || !theta0 || !theta_out || !chi2_out ||
       max_iter < 1 || max_iter > 10000)
     return NBODY_EINVAL;
   if (!valid_theta(theta0, count)) return NBODY_EINVAL;
-  double *dxi = nullptr, *dxo = nullptr, *dc = nullptr;
+  if ((theta_lo == nullptr) != (theta_hi == nullptr)) return NBODY_EINVAL;
+  double box[2 * nb::kP];
+  if (theta_lo) {
+    if (!valid_theta(theta_lo, 1) || !valid_theta(theta_hi, 1)) return NBODY_EINVAL;
+    for (int k = 0; k < nb::kP; ++k) {
+      if (!(theta_hi[k] >= theta_lo[k])) return NBODY_EINVAL;
+      box[k] = std::log(theta_lo[k]);
+      box[nb::kP + k] = std::log(theta_hi[k]);
+    }
+  }
+  double *dxi = nullptr, *dxo = nullptr, *dc = nullptr, *dbox = nullptr;
   int* dit = nullptr;
   int rc = upload_xi(h, theta0, count, &dxi);
+  if (!rc && theta_lo) {
+    rc = fit_alloc((void**)&dbox, sizeof(box));
+    if (!rc && (cudaMemcpyAsync(dbox, box, sizeof(box), cudaMemcpyHostToDevice, h->s) ||
+                cudaStreamSynchronize(h->s)))
+      rc = NBODY_ECUDA;
+  }
   if (!rc) rc = fit_alloc((void**)&dxo, (size_t)count * nb::kP * sizeof(double));
   if (!rc) rc = fit_alloc((void**)&dc, (size_t)count * sizeof(double));
   if (!rc) rc = fit_alloc((void**)&dit, (size_t)count * sizeof(int));
@@ -485,7 +586,7 @@ int nbody_orbitfit_lm(nbody_orbitfit* h, int64_t count, const double* theta0, in
   std::vector<int> its((size_t)count);
   if (!rc) {
     nb::k_fit_lm<<<(unsigned)((count + 31) / 32), 32, 0, h->s>>>(
-        h->c, h->obs, h->n_obs, h->split, dxi, (int)count, max_iter, dxo, dc, dit);
+        h->c, h->obs, h->n_obs, h->split, dxi, (int)count, max_iter, dbox, dxo, dc, dit);
     nb::count_launch();
     if (cudaGetLastError() != cudaSuccess) rc = NBODY_ECUDA;
   }
@@ -501,6 +602,7 @@ int nbody_orbitfit_lm(nbody_orbitfit* h, int64_t count, const double* theta0, in
   if (dxo) cudaFree(dxo);
   if (dc) cudaFree(dc);
   if (dit) cudaFree(dit);
+  if (dbox) cudaFree(dbox);
   if (rc) return rc;
   for (size_t i = 0; i < xo.size(); ++i) theta_out[i] = std::exp(xo[i]);
   if (iters_out)
@@ -508,30 +610,31 @@ int nbody_orbitfit_lm(nbody_orbitfit* h, int64_t count, const double* theta0, in
   return NBODY_OK;
 }
 
-int nbody_orbitfit_fisher(nbody_orbitfit* h, const double* theta, double step,
-                          double F[25], double F_gn[25]) {
-  if (!h || !theta || !F || !(step > 0.0) || !(step < 0.1)) return NBODY_EINVAL;
+int nbody_orbitfit_fisher(nbody_orbitfit* h, const double* theta, double F[25],
+                          double F_gn[25]) {
+  if (!h || !theta || !F) return NBODY_EINVAL;
   if (!valid_theta(theta, 1)) return NBODY_EINVAL;
-  // gradients at xi +- step e_b (10 evaluations in one launch) and the
-  // Gauss-Newton matrix at xi
-  std::vector<double> th(11 * nb::kP);
-  for (int k = 0; k < nb::kP; ++k) th[k] = theta[k];
-  for (int b = 0; b < nb::kP; ++b)
-    for (int sgn = 0; sgn < 2; ++sgn) {
-      double* t = th.data() + nb::kP * (1 + 2 * b + sgn);
-      for (int k = 0; k < nb::kP; ++k) t[k] = theta[k];
-      t[b] = theta[b] * std::exp(sgn ? -step : step);
-    }
-  std::vector<double> chi2(11), g(11 * nb::kP), A(11 * 25);
-  int rc = nbody_orbitfit_eval(h, 11, th.data(), chi2.data(), g.data(), A.data());
+  const int nout = 1 + nb::kP + 2 * nb::kP * nb::kP;
+  double *dxi = nullptr, *dout = nullptr;
+  int rc = upload_xi(h, theta, 1, &dxi);
+  if (!rc) rc = fit_alloc((void**)&dout, nout * sizeof(double));
+  std::vector<double> o(nout);
+  if (!rc) {
+    nb::k_fit_hess<<<1, 32, 0, h->s>>>(h->c, h->obs, h->n_obs, h->split, dxi, dout);
+    nb::count_launch();
+    if (cudaGetLastError() != cudaSuccess) rc = NBODY_ECUDA;
+  }
+  if (!rc && cudaMemcpyAsync(o.data(), dout, nout * sizeof(double), cudaMemcpyDeviceToHost,
+                             h->s) != cudaSuccess)
+    rc = NBODY_ECUDA;
+  if (cudaStreamSynchronize(h->s) != cudaSuccess) rc = NBODY_ECUDA;
+  if (dxi) cudaFree(dxi);
+  if (dout) cudaFree(dout);
   if (rc) return rc;
-  for (int a = 0; a < nb::kP; ++a)
-    for (int b = 0; b < nb::kP; ++b) {
-      const double hab = (g[nb::kP * (1 + 2 * b) + a] - g[nb::kP * (2 + 2 * b) + a]) / (2 * step);
-      const double hba = (g[nb::kP * (1 + 2 * a) + b] - g[nb::kP * (2 + 2 * a) + b]) / (2 * step);
-      F[5 * a + b] = 0.25 * (hab + hba);  // (1/2) d^2 chi^2, symmetrised
-      if (F_gn) F_gn[5 * a + b] = A[5 * a + b];
-    }
+  for (int q = 0; q < 25; ++q) {
+    F[q] = 0.5 * o[1 + nb::kP + 25 + q];  // (1/2) d^2 chi^2 / d xi^2
+    if (F_gn) F_gn[q] = o[1 + nb::kP + q];
+  }
   return NBODY_OK;
 }
 

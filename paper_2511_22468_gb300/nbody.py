@@ -185,8 +185,9 @@ def lib():
         OC = C.POINTER(nbody_orbitfit_cfg)
         L.nbody_orbitfit_create.argtypes = [C.POINTER(vp), OC, i64, dp, vp]
         L.nbody_orbitfit_eval.argtypes = [vp, i64, dp, dp, dp, dp]
-        L.nbody_orbitfit_lm.argtypes = [vp, i64, dp, C.c_int, dp, dp, C.POINTER(C.c_int)]
-        L.nbody_orbitfit_fisher.argtypes = [vp, dp, C.c_double, dp, dp]
+        L.nbody_orbitfit_lm.argtypes = [vp, i64, dp, C.c_int, dp, dp, dp, dp,
+                                        C.POINTER(C.c_int)]
+        L.nbody_orbitfit_fisher.argtypes = [vp, dp, dp, dp]
         L.nbody_orbitfit_arc.argtypes = [vp, dp, i64, dp, C.POINTER(i64)]
         L.nbody_orbitfit_destroy.argtypes = [vp]
         L.nbody_orbitfit_destroy.restype = None
@@ -722,25 +723,28 @@ def nbody_orbitfit_eval(h, thetas, want_grad=True, want_gn=True):
     return chi2, g, a
 
 
-def nbody_orbitfit_lm(h, theta0, max_iter=100):
-    """(theta (k, 5), chi2 (k,), iterations (k,))."""
+def nbody_orbitfit_lm(h, theta0, max_iter=100, lo=None, hi=None):
+    """(theta (k, 5), chi2 (k,), iterations (k,)); lo, hi: optional box."""
     import numpy as np
     th, pt = _dp(np.asarray(theta0, float).reshape(-1, 5))
     k = th.shape[0]
     out, po = _dp(np.zeros((k, 5)))
     chi2, pc = _dp(np.zeros(k))
     its = (C.c_int * k)()
-    _check(lib().nbody_orbitfit_lm(h, k, pt, int(max_iter), po, pc, its), "nbody_orbitfit_lm")
+    lo_a, plo = _dp(np.asarray(lo, float).reshape(5)) if lo is not None else (None, None)
+    hi_a, phi = _dp(np.asarray(hi, float).reshape(5)) if hi is not None else (None, None)
+    _check(lib().nbody_orbitfit_lm(h, k, pt, int(max_iter), plo, phi, po, pc, its),
+           "nbody_orbitfit_lm")
     return out, chi2, np.array(its[:], dtype=int)
 
 
-def nbody_orbitfit_fisher(h, theta, step=1e-4):
+def nbody_orbitfit_fisher(h, theta):
     """(F, F_gn), 5 x 5 each, in ln theta."""
     import numpy as np
     th, pt = _dp(np.asarray(theta, float).reshape(5))
     F, pf = _dp(np.zeros((5, 5)))
     Fg, pg = _dp(np.zeros((5, 5)))
-    _check(lib().nbody_orbitfit_fisher(h, pt, float(step), pf, pg), "nbody_orbitfit_fisher")
+    _check(lib().nbody_orbitfit_fisher(h, pt, pf, pg), "nbody_orbitfit_fisher")
     return F, Fg
 
 
