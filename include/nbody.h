@@ -247,9 +247,10 @@ NBODY_API int nbody_set_pair_shape(nbody_ctx *c, int vjp, int variant,
 NBODY_API int nbody_get_pair_shape(nbody_ctx *c, int vjp, int out[4]);
 
 /* Tune the pair-force and pair-VJP launch shapes of a single-system context
- * on its current state: every supported shape (with the chunk count chosen
- * to fill the GPU) is timed over probe_launches launches and the fastest is
- * kept.  fwd_best / vjp_best (host, 4 ints each, may be NULL) receive the
+ * on its current state: every supported shape and tile size, each with the
+ * chunk count chosen to fill the GPU and the nearest counts that split the
+ * j-tiles evenly, is timed over at least probe_launches launches (about 2 ms
+ * of them) and the fastest is kept.  fwd_best / vjp_best (host, 4 ints each, may be NULL) receive the
  * chosen {variant, threads, per_thread, chunks}.  The state is not advanced;
  * the tape and the cached acceleration are invalidated.  Synchronises.
  * Errors: EINVAL, ECUDA. */

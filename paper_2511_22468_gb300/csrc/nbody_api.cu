@@ -977,6 +977,7 @@ int nbody_set_pair_shape(nbody_ctx* c, int vjp, int variant, int threads,
   t.variant = variant;
   t.nt = threads;
   t.r = per_thread;
+  t.vjp_tile_pairs = nb::choose_pair_cfg(c->npad, c->sm_count, vjp != 0, t.eqm).vjp_tile_pairs;
   if (t.variant == nb::kTile && c->npad % (t.nt * t.r) != 0) return NBODY_EINVAL;
   if (chunks == 0) {
     const int occ = vjp ? nb::vjp_blocks_per_sm(t) : nb::pair_blocks_per_sm(t);
@@ -1018,12 +1019,13 @@ int nbody_autotune_pair(nbody_ctx* c, int probe_launches, int fwd_best[4],
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   struct Shape {
-    int variant, nt, r;
+    int variant, nt, r, tj;  // tj = 0: the kernel's default tile
   };
-  const Shape fwd[] = {{0, 128, 4}, {0, 128, 8}, {0, 256, 4}, {0, 256, 2},
-                       {0, 128, 2}, {0, 128, 1}, {1, 256, 4}, {1, 256, 8}};
-  const Shape vjp[] = {{0, 256, 2}, {0, 128, 4}, {0, 128, 2}, {0, 128, 1},
-                       {1, 256, 4}, {1, 256, 2}};
+  const Shape fwd[] = {{0, 128, 4, 0},   {0, 128, 8, 0},   {0, 256, 4, 0}, {0, 256, 2, 0},
+                       {0, 128, 2, 0},   {0, 128, 1, 0},   {1, 256, 4, 0}, {1, 256, 8, 0},
+                       {0, 128, 4, 128}, {0, 128, 2, 128}, {0, 128, 1, 128}};
+  const Shape vjp[] = {{0, 256, 2, 0}, {0, 128, 4, 0}, {0, 128, 2, 0}, {0, 128, 1, 0},
+                       {1, 256, 4, 0}, {1, 256, 2, 0}};
   int rc = NBODY_OK;
   for (int which = 0; which < 2 && rc == NBODY_OK; ++which) {
     const Shape* list = which ? vjp : fwd;
@@ -1036,30 +1038,62 @@ int nbody_autotune_pair(nbody_ctx* c, int probe_launches, int fwd_best[4],
       t.nt = list[k].nt;
       t.r = list[k].r;
       t.eqm = eqm;
+      t.vjp_tile_pairs = list[k].tj ? list[k].tj
+                                    : nb::choose_pair_cfg(c->npad, c->sm_count, which == 1, eqm)
+                                          .vjp_tile_pairs;
+      if (t.variant == nb::kTile && c->npad % (2 * t.vjp_tile_pairs) != 0) continue;
       if (t.variant == nb::kTile && (c->npad < 2048 || c->npad % (t.nt * t.r) != 0)) continue;
       if (t.variant == nb::kWarp && c->npad % (8 * t.r) != 0) continue;
       const int occ = which ? nb::vjp_blocks_per_sm(t) : nb::pair_blocks_per_sm(t);
-      t.S = nb::choose_chunks(t, c->npad, c->sm_count, occ);
-      auto launch = [&]() {
-        return which ? nb::launch_pair_vjp(t, c->vst, c->npad, c->hp.eps2f, c->part, nullptr, s)
-                     : nb::launch_pair_accel(t, c->st, c->npad, c->hp.eps2f, c->part, nullptr, s);
-      };
-      if (launch() != cudaSuccess) {
-        rc = NBODY_ECUDA;
-        break;
+      const int S0 = nb::choose_chunks(t, c->npad, c->sm_count, occ);
+      // besides the occupancy-based chunk count, the nearest counts that
+      // split the j-tiles evenly (equal work per block)
+      int cand[3] = {S0, 0, 0};
+      if (t.variant == nb::kTile) {
+        const int64_t ntiles = c->npad / (2 * t.vjp_tile_pairs);
+        for (int d = S0; d >= 1; --d)
+          if (ntiles % d == 0) { cand[1] = d; break; }
+        for (int d = S0 + 1; d <= std::min<int64_t>(ntiles, c->Smax); ++d)
+          if (ntiles % d == 0) { cand[2] = d; break; }
       }
-      if (cudaEventRecord(e0, s) != cudaSuccess) rc = NBODY_ECUDA;
-      for (int q = 0; q < probe_launches && rc == NBODY_OK; ++q)
-        if (launch() != cudaSuccess) rc = NBODY_ECUDA;
-      if (rc || cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
-        rc = NBODY_ECUDA;
-        break;
-      }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = t;
+      for (int ci = 0; ci < 3 && rc == NBODY_OK; ++ci) {
+        if (cand[ci] < 1 || cand[ci] > c->Smax || (ci > 0 && (cand[ci] == S0 ||
+                                                           (ci == 2 && cand[2] == cand[1]))))
+          continue;
+        t.S = cand[ci];
+        auto launch = [&]() {
+          return which ? nb::launch_pair_vjp(t, c->vst, c->npad, c->hp.eps2f, c->part, nullptr, s)
+                       : nb::launch_pair_accel(t, c->st, c->npad, c->hp.eps2f, c->part, nullptr, s);
+        };
+        if (launch() != cudaSuccess) {
+          rc = NBODY_ECUDA;
+          break;
+        }
+        // one timed launch sets the repetition count: at least probe_launches
+        // and about 2 ms of launches, so that short kernels are timed well
+        float ms1 = 0.f;
+        if (cudaEventRecord(e0, s) != cudaSuccess || launch() != cudaSuccess ||
+            cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+          rc = NBODY_ECUDA;
+          break;
+        }
+        cudaEventElapsedTime(&ms1, e0, e1);
+        int reps = probe_launches;
+        if (ms1 > 0.f && 2.0f / ms1 > (float)reps) reps = (int)std::min(2.0f / ms1, 400.0f);
+        if (cudaEventRecord(e0, s) != cudaSuccess) rc = NBODY_ECUDA;
+        for (int q = 0; q < reps && rc == NBODY_OK; ++q)
+          if (launch() != cudaSuccess) rc = NBODY_ECUDA;
+        if (rc || cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+          rc = NBODY_ECUDA;
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= (float)reps;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = t;
+        }
       }
     }
     if (which) {

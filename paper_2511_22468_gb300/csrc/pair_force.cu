@@ -38,14 +38,15 @@ namespace {
 #define NB_PAIR_MINB 1
 #endif
 constexpr int kTJ = NB_PAIR_TJ;  // j-pairs per shared-memory tile
+constexpr int kTJSmall = 128;    // small tiles: more j-chunks for small N
 constexpr int kUnrollJ = NB_PAIR_UNROLL;
 
-template <int NT, int R, bool POT, bool EQM>
+template <int NT, int R, bool POT, bool EQM, int TJ = kTJ>
 __global__ void __launch_bounds__(NT, NB_PAIR_MINB)
     k_pair_tile(const float4* __restrict__ st, int ntiles, float eps2,
                 int64_t npad, double* __restrict__ part,
                 double* __restrict__ pot) {
-  __shared__ float4 sj[2 * kTJ];
+  __shared__ float4 sj[2 * TJ];
   const int t = threadIdx.x;
   const int64_t i0 = (int64_t)blockIdx.x * (NT * R) + t;
   const int S = gridDim.y;
@@ -67,9 +68,9 @@ __global__ void __launch_bounds__(NT, NB_PAIR_MINB)
 
   for (int tile = tile_b; tile < tile_e; ++tile) {
     __syncthreads();
-    const float4* src = st + (int64_t)tile * (2 * kTJ);
+    const float4* src = st + (int64_t)tile * (2 * TJ);
 #pragma unroll
-    for (int q = t; q < 2 * kTJ; q += NT) sj[q] = src[q];
+    for (int q = t; q < 2 * TJ; q += NT) sj[q] = src[q];
     __syncthreads();
 
     float2 ax[R], ay[R], az[R], ph[R];
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(NT, NB_PAIR_MINB)
     for (int r = 0; r < R; ++r)
       ax[r] = ay[r] = az[r] = ph[r] = make_float2(0.f, 0.f);
 #pragma unroll (kUnrollJ)
-    for (int jj = 0; jj < kTJ; ++jj) {
+    for (int jj = 0; jj < TJ; ++jj) {
       const float4 A = sj[2 * jj];
       const float4 B = sj[2 * jj + 1];
       const float2 xj = make_float2(A.x, A.y), yj = make_float2(A.z, A.w);
@@ -176,7 +177,19 @@ template <bool POT, bool EQM>
 cudaError_t launch_impl(const PairCfg& c, const float4* st, int64_t npad,
                         float eps2, double* part, double* pot,
                         cudaStream_t s) {
-  if (c.variant == kTile) {
+  if (c.variant == kTile && c.vjp_tile_pairs == kTJSmall) {
+    const int ntiles = (int)(npad / (2 * kTJSmall));
+    dim3 grid((unsigned)(npad / (c.nt * c.r)), (unsigned)c.S);
+    if (c.nt == 128 && c.r == 4)
+      k_pair_tile<128, 4, POT, EQM, kTJSmall><<<grid, 128, 0, s>>>(st, ntiles, eps2, npad, part, pot);
+    else if (c.nt == 128 && c.r == 2)
+      k_pair_tile<128, 2, POT, EQM, kTJSmall><<<grid, 128, 0, s>>>(st, ntiles, eps2, npad, part, pot);
+    else if (c.nt == 128 && c.r == 1)
+      k_pair_tile<128, 1, POT, EQM, kTJSmall><<<grid, 128, 0, s>>>(st, ntiles, eps2, npad, part, pot);
+    else
+      return cudaErrorInvalidValue;
+  } else if (c.variant == kTile) {
+    if (c.vjp_tile_pairs != kTJ) return cudaErrorInvalidValue;
     const int ntiles = (int)(npad / (2 * kTJ));
     const int per_block = c.nt * c.r;
     dim3 grid((unsigned)(npad / per_block), (unsigned)c.S);
@@ -226,13 +239,22 @@ int pair_blocks_per_sm(const PairCfg& c) {
                     &occ, k_pair_tile<NT, R, false, true>, NT, 0)                   \
               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(                      \
                     &occ, k_pair_tile<NT, R, false, false>, NT, 0);
-  if (c.variant == kTile) {
+#define NB_OCC_S(NT, R)                                                             \
+  if (c.nt == NT && c.r == R)                                                       \
+    e = c.eqm ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(                      \
+                    &occ, k_pair_tile<NT, R, false, true, kTJSmall>, NT, 0)         \
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(                      \
+                    &occ, k_pair_tile<NT, R, false, false, kTJSmall>, NT, 0);
+  if (c.variant == kTile && c.vjp_tile_pairs == kTJSmall) {
+    NB_OCC_S(128, 4) NB_OCC_S(128, 2) NB_OCC_S(128, 1)
+  } else if (c.variant == kTile) {
     NB_OCC(128, 4) NB_OCC(128, 8) NB_OCC(256, 4) NB_OCC(256, 2) NB_OCC(128, 2) NB_OCC(128, 1)
   } else {
     e = c.eqm ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair_warp<4, false, true>, 256, 0)
               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair_warp<4, false, false>, 256, 0);
   }
 #undef NB_OCC
+#undef NB_OCC_S
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 1;
