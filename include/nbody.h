@@ -385,6 +385,13 @@ NBODY_API int nbody_stream_initial_state(nbody_stream *s, const double theta[4],
                                          double *x0, double *v0, double *m,
                                          double com[6]);
 
+/* Tune the launch shapes of the pipeline's n-body kernels (as
+ * nbody_autotune_pair) on the initial state at theta (host, 4 doubles).
+ * The next nbody_stream_forward keeps the chosen shapes; a recorded forward
+ * is dropped.  Synchronises.  Errors: EINVAL, ECUDA. */
+NBODY_API int nbody_stream_autotune(nbody_stream *s, const double theta[4],
+                                    int probe_launches);
+
 /* Steps 1-2 for `count` parameter vectors at once (host or device, count x 4
  * doubles, all > 0), one backward orbit per GPU thread: x0, v0 (device,
  * 3 x (count n) SoA, member b in columns b n .. b n + n - 1: the layout of

@@ -36,9 +36,11 @@ namespace {
 struct TuneCfg {
   int nt, r, jchunk, tj;
 };
+// (the last takes every simulation's j-range whole: one chunk each, so the
+// step always runs fused)
 constexpr TuneCfg kTune[NBODY_NTUNE] = {
     {128, 4, 4096, 512}, {128, 4, 2048, 512}, {128, 4, 8192, 512}, {128, 2, 2048, 512},
-    {256, 2, 4096, 512}, {128, 4, 4096, 128}, {128, 8, 8192, 512}, {128, 2, 4096, 128}};
+    {256, 2, 4096, 512}, {128, 4, 4096, 128}, {128, 8, 8192, 512}, {128, 4, 1 << 30, 512}};
 
 struct SimMeta {
   int64_t npad, poff, part_off;

@@ -614,6 +614,30 @@ int nbody_stream_initial_states(nbody_stream* s, int64_t count, const double* th
   return e == cudaSuccess ? NBODY_OK : NBODY_ECUDA;
 }
 
+int nbody_stream_autotune(nbody_stream* s, const double theta[4], int probe_launches) {
+  if (!s || !theta || probe_launches < 1) return NBODY_EINVAL;
+  double com[6];
+  int rc = nbody_stream_initial_state(s, theta, s->x0, s->v0, s->m, com);
+  if (rc) return rc;
+  const nbody_stream_cfg& c = s->cfg;
+  nbody_params p{};
+  p.G = c.G;
+  p.eps = c.eps;
+  p.dt = theta[0] / (double)c.n_steps;
+  p.ext_flags = NBODY_EXT_NFW | NBODY_EXT_MN;
+  p.center_mode = NBODY_CENTER_FIXED;
+  p.nfw_M = theta[2];
+  p.nfw_rs = c.nfw_rs;
+  p.mn_M = theta[3];
+  p.mn_a = c.mn_a;
+  p.mn_b = c.mn_b;
+  for (int k = 0; k < 3; ++k) p.center[k] = com[k];
+  s->have_forward = false;
+  if ((rc = nbody_set_params(s->ctx, &p))) return rc;
+  if ((rc = nbody_set_state(s->ctx, s->x0, s->v0, s->m))) return rc;
+  return nbody_autotune_pair(s->ctx, probe_launches, nullptr, nullptr);
+}
+
 int nbody_stream_head(nbody_stream* s, const double* x, double* density, double* loss) {
   if (!s || !x || !density) return NBODY_EINVAL;
   const nbody_stream_cfg& c = s->cfg;

@@ -52,7 +52,7 @@ EXPORTED = ("nbody_create", "nbody_destroy", "nbody_set_params",
             "nbody_potential_grad", "nbody_mmd_create", "nbody_mmd_eval",
             "nbody_mmd_eval_batch", "nbody_mmd_target_stats", "nbody_mmd_destroy",
             "nbody_stream_set_target_cloud", "nbody_stream_initial_states",
-            "nbody_ext_accel", "nbody_orbitfit_create", "nbody_orbitfit_eval",
+            "nbody_ext_accel", "nbody_stream_autotune", "nbody_orbitfit_create", "nbody_orbitfit_eval",
             "nbody_orbitfit_lm", "nbody_orbitfit_fisher", "nbody_orbitfit_arc",
             "nbody_orbitfit_destroy")
 
@@ -151,6 +151,7 @@ def lib():
         L.nbody_stream_set_target.argtypes = [vp, vp]
         L.nbody_stream_set_target_cloud.argtypes = [vp, i64, vp, vp, dp, C.c_int, dp]
         L.nbody_stream_initial_states.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+        L.nbody_stream_autotune.argtypes = [vp, dp, C.c_int]
         L.nbody_stream_forward.argtypes = [vp, dp, dp, vp]
         L.nbody_stream_grad.argtypes = [vp, dp]
         L.nbody_stream_initial_state.argtypes = [vp, dp, vp, vp, vp, dp]
@@ -571,6 +572,11 @@ def nbody_stream_initial_states(h, thetas, x0, v0, m, com=None):
     _check(lib().nbody_stream_initial_states(h, th.shape[0], _ptr(th), _ptr(x0), _ptr(v0),
                                              _ptr(m), _ptr(com)),
            "nbody_stream_initial_states")
+
+
+def nbody_stream_autotune(h, theta, probe_launches=3):
+    th = (C.c_double * 4)(*[float(t) for t in theta])
+    _check(lib().nbody_stream_autotune(h, th, int(probe_launches)), "nbody_stream_autotune")
 
 
 def nbody_stream_head(h, x, density, want_loss=False):

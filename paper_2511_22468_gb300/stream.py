@@ -100,6 +100,10 @@ class StreamModel:
     def grad(self):
         return nb.nbody_stream_grad(self.h)
 
+    def autotune(self, theta, probe_launches=3):
+        """Tune the n-body kernels' launch shapes on the state at theta."""
+        nb.nbody_stream_autotune(self.h, theta, probe_launches)
+
     def loss_and_grad(self, theta):
         L = self.loss(theta)
         return L, np.array(self.grad())
@@ -148,9 +152,44 @@ def horizon_sweep(horizons_myr=(50, 100, 200, 400, 800, 1600, 3000), rel=0.02,
     return rows
 
 
+def time_pipeline(reps=3, autotune=True):
+    """Seconds per loss (forward) and per gradient (reverse sweep, Plummer
+    shift and orbit adjoints) of the stream workload (N = 1e4, 6000 steps of
+    0.5 Myr), at theta_true * 1.02 with the target at theta_true."""
+    import time
+
+    from .configs import C1
+    from .inputs import plummer_unit
+    xh, vh = plummer_unit(C1.n, C1.seed)
+    m = StreamModel(C1, xh, vh)
+    truth = np.array(C1.theta_true, float)
+    m.set_target(m.density(truth))
+    th = list(truth * 1.02)
+    if autotune:
+        nb.nbody_stream_autotune(m.h, th)
+    m.loss(th)
+    m.grad()
+    fw, gr = [], []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L = m.loss(th)
+        t1 = time.perf_counter()
+        m.grad()
+        t2 = time.perf_counter()
+        fw.append(t1 - t0)
+        gr.append(t2 - t1)
+    m.close()
+    return {"workload": "stream_n1e4_6000_steps", "forward_s": min(fw), "gradient_s": min(gr),
+            "forward_us_per_step": 1e6 * min(fw) / C1.n_steps,
+            "gradient_us_per_step": 1e6 * min(gr) / C1.n_steps, "loss": L}
+
+
 if __name__ == "__main__":
     import json
     import sys
+    if "--time" in sys.argv:
+        print(json.dumps(time_pipeline()), flush=True)
     if "--horizon-sweep" in sys.argv:
         for row in horizon_sweep():
             print(json.dumps({"t_end_myr": row[0], "steps": row[1], "loss": row[2],

@@ -124,3 +124,22 @@ def test_stream_mmd_loss_and_gradient_match_oracle():
     gpu.set_target(orc.density(truth))
     assert gpu.loss(list(th)) == pytest.approx(orc.loss(th, orc.density(truth)), rel=1e-4)
     gpu.close()
+
+
+def test_stream_autotune_keeps_parity():
+    """Tuned launch shapes of the pipeline's n-body kernels give the same
+    loss and gradient as the oracle."""
+    from paper_2511_22468_gb300.stream import StreamModel
+    cfg, xh, vh = _case()
+    orc = ostream.StreamModel(cfg, xh, vh)
+    truth = np.array(cfg.theta_true, float)
+    target = orc.density(truth)
+    th = truth * np.array([1.05, 0.9, 1.1, 0.95])
+    L_ref, g_ref = orc.loss_and_grad(th, target)
+    gpu = StreamModel(cfg, xh, vh, checkpoint_every=8)
+    gpu.set_target(target)
+    gpu.autotune(list(th))
+    L, g = gpu.loss_and_grad(th)
+    assert L == pytest.approx(L_ref, rel=1e-4)
+    assert_grad_close(g, g_ref, orc.t_end_parts)
+    gpu.close()
