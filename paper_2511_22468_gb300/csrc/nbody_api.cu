@@ -86,6 +86,11 @@ struct nbody_ctx {
   double* red = nullptr;  // [8]
   double* lsc = nullptr;  // cotangent scales [kLscDoubles]
   double* mpart = nullptr;  // mass-gradient partial sums [Smax][npad], lazily
+  // the FP64 external field of a point runs on a side stream beside that
+  // point's pair kernel (different pipes), joined before the update
+  double* aext = nullptr;   // [3][npad]
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   double* mbar = nullptr;   // dL/dm [npad], lazily
   bool want_mbar = false;   // the sweep being recorded accumulates dL/dm
   double pot_bar[6] = {0, 0, 0, 0, 0, 0};  // last sweep's potential-parameter gradient
@@ -376,6 +381,24 @@ nb::UpdateArgs base_update(nbody_ctx* c, double* x, double* v) {
   return a;
 }
 
+// The external field of the point x is computed on the side stream while
+// stream s runs that point's pair kernel; the update waits for both.
+int fork_field(nbody_ctx* c, const double* x, cudaStream_t s) {
+  if (!c->p.ext_flags || !c->side) return NBODY_OK;
+  CK(cudaEventRecord(c->ev_fork, s));
+  CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+  CK(nb::launch_field(c->dp, x, c->n, c->npad, c->aext, c->side));
+  CK(cudaEventRecord(c->ev_join, c->side));
+  return NBODY_OK;
+}
+
+int join_field(nbody_ctx* c, cudaStream_t s, nb::UpdateArgs& a) {
+  if (!c->p.ext_flags || !c->side) return NBODY_OK;
+  CK(cudaStreamWaitEvent(s, c->ev_join, 0));
+  a.aext = c->aext;
+  return NBODY_OK;
+}
+
 // The launches of a forward run over points 0..n_steps (on stream s).
 int record_forward(nbody_ctx* c, int64_t n_steps, bool with_tape, cudaStream_t s) {
   if (c->p.center_mode == NBODY_CENTER_GUIDE)
@@ -394,10 +417,12 @@ int record_forward(nbody_ctx* c, int64_t n_steps, bool with_tape, cudaStream_t s
     } else {
       if (k == 0)
         CK(nb::launch_stage(c->x, c->m, center_at(c, 0), c->n, c->npad, c->st, s));
+      if (int r_ = fork_field(c, c->x, s)) return r_;
       CK(timed(c, NBODY_KCLASS_PAIR, [&] {
         return nb::launch_pair_accel(c->fcfg, c->st, c->npad, c->hp.eps2f,
                                      c->part, nullptr, s);
       }));
+      if (int r_ = join_field(c, s, a)) return r_;
     }
     a.acc_out = (k == n_steps) ? c->acc : nullptr;
     a.kick = (k == 0 || k == n_steps) ? 0.5 : 1.0;
@@ -474,10 +499,12 @@ int recompute_segment(nbody_ctx* c, int64_t sg, cudaStream_t s) {
       a.S = 1;
       a.part_is_final = 1;
     } else {
+      if (int r_ = fork_field(c, c->xw, s)) return r_;
       CK(timed(c, NBODY_KCLASS_PAIR, [&] {
         return nb::launch_pair_accel(c->fcfg, c->st, c->npad, c->hp.eps2f,
                                      c->part, nullptr, s);
       }));
+      if (int r_ = join_field(c, s, a)) return r_;
     }
     a.kick = (k == 0) ? 0.5 : 1.0;
     a.drift = 1;
@@ -514,6 +541,12 @@ int copy_out3(nbody_ctx* c, double* dst, const double* src) {
 }
 
 void free_all(nbody_ctx* c) {
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  c->side = nullptr;
+  c->ev_fork = c->ev_join = nullptr;
+  dfree(c->aext);
   for (auto& pool : c->ev)
     for (auto& pr : pool) {
       cudaEventDestroy(pr.first);
@@ -614,10 +647,18 @@ int nbody_create(nbody_ctx** out, int64_t n, const nbody_params* p,
       (rc = dalloc(&c->guide, 6)) || (rc = dalloc(&c->fixed_center, 3)) ||
       (rc = dalloc(&c->xbar, 3 * np)) || (rc = dalloc(&c->vbar, 3 * np)) ||
       (rc = dalloc(&c->blk, (size_t)c->nblk * std::max(nb::kAdjCols, 6))) || (rc = dalloc(&c->red, 8)) || (rc = dalloc(&c->lsc, nb::kLscDoubles)) ||
-      (rc = dalloc(&c->status, 1))) {
+      (rc = dalloc(&c->status, 1)) || (rc = dalloc(&c->aext, 3 * np))) {
     free_all(c);
     delete c;
     return rc;
+  }
+  if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    free_all(c);
+    delete c;
+    return NBODY_ECUDA;
   }
   cudaStream_t s = c->stream;
   if (cudaMemsetAsync(c->x, 0, 3 * np * sizeof(double), s) ||

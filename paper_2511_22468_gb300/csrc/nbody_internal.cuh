@@ -118,9 +118,15 @@ struct UpdateArgs {
   double* tape_x;       // segment tape slot for this point (x, a_pair) or NULL
   double* tape_a;
   double* tape_vh;      // segment tape slot of the half-step velocity or NULL
+  const double* aext;   // external acceleration at x [3][npad] (launch_field) or
+                        // NULL: computed in the update
   int* status;
 };
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
+// FP64 external acceleration (G M included) of n particles into aext
+// [3][npad]; runs beside the pair kernel of the same point
+cudaError_t launch_field(const DevParams* P, const double* x, int64_t n, int64_t npad,
+                         double* aext, cudaStream_t s);
 
 // FP32 cotangent scaling of the reverse sweep: the cotangents staged for the
 // pair VJP are multiplied by an exact power of two s = 2^-e chosen from the

@@ -125,15 +125,17 @@ __global__ void __launch_bounds__(256) k_update(UpdateArgs a) {
       a.tape_a[d * np + i] = ap[d];
     }
   }
-  ExtUnit e;
-  ext_unit(P, x[0], x[1], x[2], e);
+  double ae[3];
+  if (a.aext) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) ae[d] = a.aext[d * np + i];
+  } else {
+    ext_accel(P, x[0], x[1], x[2], ae);
+  }
   const double kick = a.kick * P.dt;
   bool bad = false;
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const double acc = ap[d] + P.nfw_GM * e.n[d] + P.mn_GM * e.d[d] + P.bulge_GM * e.b[d];
-    v[d] += kick * acc;
-  }
+  for (int d = 0; d < 3; ++d) v[d] += kick * (ap[d] + ae[d]);
   if (a.drift) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -239,6 +241,19 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
     if (i == 0) a.lsc[1 - a.slot] = s_next;
     block_absmax(vmax, reinterpret_cast<unsigned long long*>(a.lsc + 2) + (1 - a.slot));
   }
+}
+
+// external acceleration of the state (x [3][npad]) into aext [3][npad]: the
+// same ext_accel the update applies when it computes the field itself
+__global__ void __launch_bounds__(256)
+    k_field(const DevParams* __restrict__ P, const double* __restrict__ x, int64_t n,
+            int64_t npad, double* __restrict__ aext) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double a[3];
+  ext_accel(*P, x[i], x[npad + i], x[2 * npad + i], a);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) aext[d * npad + i] = a[d];
 }
 
 // external acceleration at caller points (3 x n SoA in and out)
@@ -418,6 +433,13 @@ void set_bulge(DevParams& d, double G, double M, double alpha, double rc) {
   d.bulge_irc = 1.0 / rc;
   d.bulge_igs = 1.0 / std::tgamma(s);
   d.bulge_gsh = std::tgamma(s - 0.5);
+}
+
+cudaError_t launch_field(const DevParams* P, const double* x, int64_t n, int64_t npad,
+                         double* aext, cudaStream_t s) {
+  k_field<<<blocks_for(n, 64), 64, 0, s>>>(P, x, n, npad, aext);
+  count_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_ext_accel(const DevParams& P, const double* x, int64_t n, double* acc,
