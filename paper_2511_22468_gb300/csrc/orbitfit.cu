@@ -12,8 +12,9 @@
 // every evaluation returns chi^2, its exact gradient and the Gauss-Newton
 // matrix sum_r (dr/dxi)(dr/dxi)^T (one half of the Gauss-Newton Hessian of
 // chi^2), accumulated while the orbit streams past the sorted observations.
-// Levenberg-Marquardt runs whole inside a thread (1000 random starts are
-// 1000 threads); every loop has a fixed bound.
+// Levenberg-Marquardt runs whole inside a group of 16 lanes, 8 per half of
+// the arc, each lane carrying one derivative direction (1000 random starts
+// are 16000 threads); every loop has a fixed bound.
 //
 // The arc: from t = 0 forward while phi1 stays in the window and keeps
 // increasing, and backward (step -dt) while it stays in the window and keeps
@@ -35,6 +36,7 @@ namespace {
 constexpr int kP = 5;  // parameters
 using D5 = Dual<kP>;
 using H5 = HDual<kP>;  // second order, for the exact Hessian
+using D1 = Dual<1>;    // one derivative direction per lane (lane-parallel fits)
 
 template <class T>
 __device__ __forceinline__ T cst(double c);
@@ -45,6 +47,10 @@ __device__ __forceinline__ D5 cst<D5>(double c) {
 template <>
 __device__ __forceinline__ H5 cst<H5>(double c) {
   return hconst<kP>(c);
+}
+template <>
+__device__ __forceinline__ D1 cst<D1>(double c) {
+  return dconst<1>(c);
 }
 
 constexpr double kMasYr = 206.26480624709636;        // 1 rad/Myr in mas/yr
@@ -69,6 +75,19 @@ struct Acc {  // running chi^2, gradient (d chi^2 / d xi), Gauss-Newton matrix
 
 struct AccH : Acc {  // and the exact Hessian d^2 chi^2 / d xi^2
   double H[kP][kP];
+};
+
+// Lane-parallel accumulation: 8 lanes per half-arc, lane `dir` carries the
+// derivative along xi_dir (lanes 5..7 repeat direction 4); the lanes of a
+// half see the same values, so they take the same branches.  Row `dir` of
+// the Gauss-Newton matrix gathers the other directions by shuffles.
+struct AccL {
+  double chi2;
+  double g;         // d chi^2 / d xi_dir
+  double A[kP];     // row dir of sum (dr/dxi)(dr/dxi)^T
+  unsigned mask;    // the 8 lanes of this half
+  int base;         // lane of direction 0 of this half
+  int dir;
 };
 
 // NFW + MN acceleration in duals; th = (M_NFW, r_s, M_MN, a, b)
@@ -162,6 +181,20 @@ __device__ void add_obs(const FitCfg& c, const double* ob, const H5 q[4], AccH& 
         s.H[a][b] += hab;
         if (b != a) s.H[b][a] += hab;
       }
+    }
+  }
+}
+
+__device__ void add_obs(const FitCfg& c, const double* ob, const D1 q[4], AccL& s) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const D1 r = c.isig[k] * (q[k] - ob[1 + k]);
+    s.chi2 += r.v * r.v;
+    s.g += 2.0 * r.v * r.d[0];
+#pragma unroll
+    for (int b = 0; b < kP; ++b) {
+      const double rb = __shfl_sync(s.mask, r.d[0], s.base + b);
+      s.A[b] += r.d[0] * rb;
     }
   }
 }
@@ -334,18 +367,67 @@ __device__ bool damped_solve(const double A[kP][kP], double lam, const double b[
   return true;
 }
 
-// Levenberg-Marquardt from each start: minimise chi^2(xi) with the step
-// (A + lam diag A) delta = -g/2 (A the Gauss-Newton matrix, g = d chi^2/d xi)
-__global__ void k_fit_lm(FitCfg c, const double* __restrict__ obs, int n_obs, int split,
-                         const double* __restrict__ xi0, int count, int max_iter,
-                         const double* __restrict__ bounds, double* __restrict__ xi_out,
-                         double* __restrict__ chi2_out, int* __restrict__ iters_out) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= count) return;
+// One lane group (16 lanes: 8 per half-arc) evaluates chi^2, its gradient
+// and the Gauss-Newton matrix at xi; every lane of the group ends with the
+// same full results (sums combined in the same order everywhere).
+__device__ void evaluate_lanes(const FitCfg& c, const double* obs, int n_obs, int split,
+                               const double xi[kP], int glane, unsigned gmask, Acc& out) {
+  const int half = glane >> 3;
+  const int dir = min(glane & 7, kP - 1);
+  const int lane = threadIdx.x & 31;
+  const int gbase = lane - glane;  // first lane of the group
+  AccL s;
+  s.chi2 = 0.0;
+  s.g = 0.0;
+  for (int b = 0; b < kP; ++b) s.A[b] = 0.0;
+  s.base = gbase + 8 * half;
+  s.mask = 0xFFu << s.base;
+  s.dir = dir;
+  D1 th[kP];
+  for (int k = 0; k < kP; ++k) {
+    const double t = exp(xi[k]);
+    th[k] = dconst<1>(t);
+    if (k == dir) th[k].d[0] = t;
+  }
+  if (half == 0)
+    half_arc(c, th, 1.0, obs, n_obs, split, s, nullptr);
+  else
+    half_arc(c, th, -1.0, obs, n_obs, split - 1, s, nullptr);
+  // both halves: partner lane glane ^ 8 holds the other half's sums
+  double chi2 = s.chi2, g = s.g, A[kP];
+  const double co = __shfl_xor_sync(gmask, chi2, 8);
+  const double go = __shfl_xor_sync(gmask, g, 8);
+  out.chi2 = half == 0 ? chi2 + co : co + chi2;
+  g = half == 0 ? g + go : go + g;
+  for (int b = 0; b < kP; ++b) {
+    const double ao = __shfl_xor_sync(gmask, s.A[b], 8);
+    A[b] = half == 0 ? s.A[b] + ao : ao + s.A[b];
+  }
+  // every lane gathers all rows from the group's first five lanes
+  for (int a = 0; a < kP; ++a) {
+    out.g[a] = __shfl_sync(gmask, g, gbase + a);
+    for (int b = 0; b < kP; ++b) out.A[a][b] = __shfl_sync(gmask, A[b], gbase + a);
+  }
+}
+
+// Levenberg-Marquardt from each start, one start per 16-lane group (the
+// lanes share the work of every evaluation and take identical decisions):
+// minimise chi^2(xi) with the step (A + lam diag A) delta = -g/2, A the
+// Gauss-Newton matrix and g = d chi^2 / d xi
+__global__ void __launch_bounds__(128)
+    k_fit_lm_lanes(FitCfg c, const double* __restrict__ obs, int n_obs, int split,
+                   const double* __restrict__ xi0, int count, int max_iter,
+                   const double* __restrict__ bounds, double* __restrict__ xi_out,
+                   double* __restrict__ chi2_out, int* __restrict__ iters_out) {
+  const int lane = threadIdx.x & 31;
+  const int glane = lane & 15;
+  const unsigned gmask = 0xFFFFu << (lane & 16);
+  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 4;  // start
+  if (t >= count) return;  // whole groups leave together (count is per group)
   double xi[kP], xn[kP], delta[kP], rhs[kP];
   for (int k = 0; k < kP; ++k) xi[k] = xi0[kP * t + k];
   Acc cur, trial;
-  evaluate(c, obs, n_obs, split, xi, cur);
+  evaluate_lanes(c, obs, n_obs, split, xi, glane, gmask, cur);
   double lam = 1e-3;
   int it = 0;
   for (; it < max_iter; ++it) {
@@ -355,16 +437,14 @@ __global__ void k_fit_lm(FitCfg c, const double* __restrict__ obs, int n_obs, in
       if (lam > 1e12) break;
       continue;
     }
-    // predicted decrease of the damped Gauss-Newton step: converged when it
-    // is below 1e-6 in chi^2 (a millionth of one standard deviation)
     double pred = 0.0;
     for (int k = 0; k < kP; ++k) pred -= 0.5 * cur.g[k] * delta[k];
     if (lam <= 1e-3 && pred < 1e-6) break;
     for (int k = 0; k < kP; ++k) {
       xn[k] = xi[k] + delta[k];
-      if (bounds) xn[k] = fmin(fmax(xn[k], bounds[k]), bounds[kP + k]);  // box in ln theta
+      if (bounds) xn[k] = fmin(fmax(xn[k], bounds[k]), bounds[kP + k]);
     }
-    evaluate(c, obs, n_obs, split, xn, trial);
+    evaluate_lanes(c, obs, n_obs, split, xn, glane, gmask, trial);
     if (isfinite(trial.chi2) && trial.chi2 < cur.chi2) {
       const double drop = cur.chi2 - trial.chi2;
       for (int k = 0; k < kP; ++k) xi[k] = xn[k];
@@ -376,9 +456,11 @@ __global__ void k_fit_lm(FitCfg c, const double* __restrict__ obs, int n_obs, in
       if (lam > 1e12) break;
     }
   }
-  for (int k = 0; k < kP; ++k) xi_out[kP * t + k] = xi[k];
-  chi2_out[t] = cur.chi2;
-  iters_out[t] = it;
+  if (glane == 0) {
+    for (int k = 0; k < kP; ++k) xi_out[kP * t + k] = xi[k];
+    chi2_out[t] = cur.chi2;
+    iters_out[t] = it;
+  }
 }
 
 // the model arc at one parameter vector (values only): forward and backward
@@ -585,7 +667,8 @@ int nbody_orbitfit_lm(nbody_orbitfit* h, int64_t count, const double* theta0, in
   std::vector<double> xo((size_t)count * nb::kP);
   std::vector<int> its((size_t)count);
   if (!rc) {
-    nb::k_fit_lm<<<(unsigned)((count + 31) / 32), 32, 0, h->s>>>(
+    // 16 lanes per start, 8 starts per block of 128 threads
+    nb::k_fit_lm_lanes<<<(unsigned)((count + 7) / 8), 128, 0, h->s>>>(
         h->c, h->obs, h->n_obs, h->split, dxi, (int)count, max_iter, dbox, dxo, dc, dit);
     nb::count_launch();
     if (cudaGetLastError() != cudaSuccess) rc = NBODY_ECUDA;
