@@ -84,6 +84,39 @@ def test_pair_accel_full_size_sampled():
     assert acc_err(to_np(acc)[rows], ref) <= 1e-5
 
 
+def test_full_size_step_and_adjoint_sampled():
+    """The benchmark's context at full size (N = 1e6, equal masses: the
+    equal-mass force and VJP kernels in their tuned launch shapes, NFW + MN,
+    guide origin): one kick-drift-kick step and its reverse sweep with
+    xbar = W, vbar = 0, whose closed forms for sampled rows are
+      x1 - x0 - dt v0 = (dt^2 / 2) a(x0),
+      x0bar - W = (dt^2 / 2) (J_pair + J_ext)(x0)^T W,
+    against the oracle on 256 rows (acceleration 1e-5 per particle,
+    gradient 1e-4 norm-wise)."""
+    n, dt, pot = C3.n, C3.dt, C3.pot
+    x, v, m = plummer_sphere(n, C3.seed, C3.G, C3.M, C3.a, center=C3.X0, velocity=C3.V0)
+    sim = _sim(n, C3.G, C3.eps, dt, K=1, ext=3, pot=pot, center=C3.X0, center_vel=C3.V0,
+               guide=True)
+    sim.set_state(to_gpu(x), to_gpu(v), to_gpu(m))
+    xo = torch.empty((3, n), dtype=torch.float64, device=DEV)
+    sim.integrate(1, xo)
+    W = np.random.default_rng(9).normal(size=(n, 3))
+    x0b = torch.empty_like(xo)
+    sim.vjp(to_gpu(W), None, x0b, None)
+    rows = np.random.default_rng(10).choice(n, 256, replace=False)
+    ph = orc.Physics(G=C3.G, eps=C3.eps, ext=orc.NFW | orc.MN, nfw_M=pot.nfw_M,
+                     nfw_rs=pot.nfw_rs, mn_M=pot.mn_M, mn_a=pot.mn_a, mn_b=pot.mn_b)
+    a_ext = np.array([orc.ext_accel(ph, x[k]) for k in rows])
+    a_ref = orc.pair_accel(x, m, C3.G, C3.eps, rows=rows) + a_ext
+    got = (to_np(xo)[rows] - x[rows] - dt * v[rows]) / (0.5 * dt * dt)
+    assert acc_err(got, a_ref) <= 1e-5
+    Jt = orc.pair_vjp(x, m, C3.G, C3.eps, W, rows=rows)
+    Jt += np.array([orc.ext_jac(ph, x[k]).T @ W[k] for k in rows])
+    gb = (to_np(x0b)[rows] - W[rows]) / (0.5 * dt * dt)
+    assert np.linalg.norm(gb - Jt) <= 1e-4 * np.linalg.norm(Jt)
+    sim.close()
+
+
 # --------------------------------------------------------------- trajectory --
 def _sim(n, G, eps, dt, K=0, ext=0, pot=None, center=(0, 0, 0), center_vel=(0, 0, 0),
          guide=False, lean=False):
