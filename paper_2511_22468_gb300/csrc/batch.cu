@@ -22,6 +22,7 @@
 #include <new>
 #include <vector>
 
+#include "block_reduce.cuh"
 #include "ext_potential.cuh"
 #include "nbody_internal.cuh"
 #include "pair_body.cuh"
@@ -287,13 +288,9 @@ __global__ void __launch_bounds__(256)
   const int64_t i = g - M.poff;
   if (i >= M.n) return;
   const DevParams Q = P[s];
-  double ap[3];
-  for (int d = 0; d < 3; ++d) {
-    double acc = 0.0;
-    for (int q = 0; q < M.S; ++q)
-      acc += part[M.part_off + ((int64_t)q * 3 + d) * M.npad + i];
-    ap[d] = Q.G * M.mscale * acc;
-  }
+  double ap[3], acc[3];
+  slice_sums<3>(part + M.part_off + i, M.S, 3 * M.npad, M.npad, acc);
+  for (int d = 0; d < 3; ++d) ap[d] = Q.G * M.mscale * acc[d];
   double xx[3], vv[3];
   for (int d = 0; d < 3; ++d) {
     xx[d] = x[d * ptot + g];

@@ -33,4 +33,28 @@ static __device__ __forceinline__ void block_accumulate(double (&val)[NV],
   }
 }
 
+// sum over q = 0..S-1 of p[q * qstride + d * dstride] for d < NV, in
+// ascending q (the order fixes the rounding), with the loads of eight
+// slices issued before their adds so that their latencies overlap
+template <int NV>
+static __device__ __forceinline__ void slice_sums(const double* __restrict__ p, int S,
+                                                  int64_t qstride, int64_t dstride,
+                                                  double (&out)[NV]) {
+#pragma unroll
+  for (int d = 0; d < NV; ++d) out[d] = 0.0;
+  for (int q0 = 0; q0 < S; q0 += 8) {
+    double v[8][NV];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int d = 0; d < NV; ++d)
+        v[u][d] = (q0 + u < S) ? p[(int64_t)(q0 + u) * qstride + d * dstride] : 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int d = 0; d < NV; ++d)
+        if (q0 + u < S) out[d] += v[u][d];
+  }
+}
+
 }  // namespace nb

@@ -652,7 +652,11 @@ int nbody_create(nbody_ctx** out, int64_t n, const nbody_params* p,
     delete c;
     return rc;
   }
-  if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+  // the side stream takes the highest priority, so that the small field
+  // kernel's blocks are placed before the pair kernel fills the SMs
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();

@@ -99,15 +99,14 @@ __global__ void __launch_bounds__(256) k_update(UpdateArgs a) {
   const DevParams& P = *a.P;
   const int64_t np = a.npad;
   double ap[3];
+  if (a.part_is_final) {
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    if (a.part_is_final) {
-      ap[d] = a.part[d * np + i];
-    } else {
-      double s = 0.0;
-      for (int q = 0; q < a.S; ++q) s += a.part[((int64_t)q * 3 + d) * np + i];
-      ap[d] = P.G * a.mscale * s;
-    }
+    for (int d = 0; d < 3; ++d) ap[d] = a.part[d * np + i];
+  } else {
+    double s[3];
+    slice_sums<3>(a.part + i, a.S, 3 * np, np, s);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) ap[d] = P.G * a.mscale * s[d];
   }
   double x[3], v[3];
 #pragma unroll
@@ -168,15 +167,14 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
   const double s_next = a.drift ? lam_scale_from(maxbits[a.slot]) : 1.0;
   double vmax = 0.0;
   if (i < a.n) {
-    double lam[3], x[3], ap[3], g[3];
+    double lam[3], x[3], ap[3], g[3], gs[3];
+    slice_sums<3>(a.gpart + i, a.S, 3 * np, np, gs);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       lam[d] = a.vbar[d * np + i];
       x[d] = a.xk[d * np + i];
       ap[d] = a.ak[d * np + i];
-      double s = 0.0;
-      for (int q = 0; q < a.S; ++q) s += a.gpart[((int64_t)q * 3 + d) * np + i];
-      g[d] = -P.G * a.mscale * (s / s_here);
+      g[d] = -P.G * a.mscale * (gs[d] / s_here);
     }
     ExtUnit e;
     ext_unit(P, x[0], x[1], x[2], e);
@@ -195,9 +193,9 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
     }
     la = lp + P.nfw_GM * ln + P.mn_GM * lm + P.bulge_GM * lb;
     if (a.mpart) {  // per-particle mass gradient of this kick
-      double sm = 0.0;
-      for (int q = 0; q < a.S; ++q) sm += a.mpart[(int64_t)q * np + i];
-      a.mbar[i] += ck * P.G * (sm / s_here);
+      double sm[1];
+      slice_sums<1>(a.mpart + i, a.S, np, 0, sm);
+      a.mbar[i] += ck * P.G * (sm[0] / s_here);
     }
     contrib[0] = a.ck * la;          // dL/d dt from the kick(s)
     contrib[1] = ck * lp;            // sum_j m_j dL/dm_j
