@@ -6,14 +6,18 @@
  * Odisseo" (arXiv 2511.22468):
  *   - softened direct pairwise gravity, no tree or multipole (Sec. 1,
  *     "N-body codes"):  a_i = -G sum_j m_j (x_i - x_j) (|x_i - x_j|^2 + eps^2)^(-3/2)
- *   - external potential of MWPotential2014's NFW halo and Miyamoto-Nagai
- *     disk (Sec. 2.2.1)
+ *   - external potential of MWPotential2014's NFW halo, Miyamoto-Nagai
+ *     disk and power-law bulge (Sec. 2.2.1)
  *   - second-order Velocity-Verlet (kick-drift-kick) with a fixed number of
  *     steps (Sec. 2.2.1)
  *   - reverse-mode gradients of the final state with respect to the initial
  *     conditions, the time step (integration time), the particle masses and
- *     the potential masses (Sec. 2; the parameter vector of Sec. 2.2.1 and
- *     Fig. 2).
+ *     the potential's parameters (Sec. 2; the parameter vector of Sec. 2.2.1
+ *     and Fig. 2)
+ *   - the inference stages built on them: the mock-stream pipeline with a
+ *     binned-density or point-cloud (MMD) loss, batched ensembles and grid
+ *     searches (Sec. 2.2.1, Fig. 2), orbit fitting with its Fisher matrix
+ *     (Sec. 2.2.2), and a neural surrogate (Sec. 3 outlook).
  *
  * Conventions for every call:
  *   - Return value: NBODY_OK (0) or a negative NBODY_E* code; no call exits,
@@ -63,7 +67,7 @@ extern "C" {
 /* ---- external potential components (Sec. 2.2.1) ---- */
 #define NBODY_EXT_NFW 1u /* NFW halo: Phi = -G M ln(1 + r/r_s) / r          */
 #define NBODY_EXT_MN 2u  /* Miyamoto-Nagai: Phi = -G M / sqrt(R^2 + (a + sqrt(z^2 + b^2))^2) */
-#define NBODY_EXT_BULGE 4u /* MWPotential2014's bulge (Sec. 3.1): density
+#define NBODY_EXT_BULGE 4u /* MWPotential2014's bulge (Sec. 2.2.1): density
                               rho_0 (r/r_1)^-alpha exp(-(r/r_c)^2) of total
                               mass M_b, a = -G M_b P(s, r^2/r_c^2) x / r^3,
                               P the regularised incomplete gamma function,
@@ -162,7 +166,7 @@ NBODY_API int nbody_vjp(nbody_ctx *c, const double *xbar, const double *vbar,
 
 /* Gradient of the same loss with respect to the parameters of the external
  * potential (Sec. 2.2.1; the first five are the parameter set of the Fisher
- * analysis, Sec. 3.2), from the last successful nbody_vjp of this context:
+ * analysis, Sec. 2.2.2), from the last successful nbody_vjp of this context:
  * out (host, 6 doubles) = { dL/d nfw_M, dL/d nfw_rs, dL/d mn_M, dL/d mn_a,
  * dL/d mn_b, dL/d bulge_M }; zero for a component that is switched off.
  * Does not touch the GPU.  Errors: EINVAL (batch context), ESTATE (no
@@ -415,7 +419,7 @@ NBODY_API void nbody_stream_destroy(nbody_stream *s);
 
 /* ---- maximum mean discrepancy between phase-space point clouds ----
  *
- * The paper's first inference method (Sec. 3.1; Fig. 2, step 4) compares
+ * The paper's first inference method (Sec. 2.2.1; Fig. 2, step 4) compares
  * the simulated and the observed stream as point clouds with the MMD and
  * ranks the 10^4 points of its grid search by it.  A point is
  * q = (x, y, z, vx, vy, vz); coordinates are standardised per dimension,
@@ -460,7 +464,7 @@ NBODY_API int nbody_mmd_target_stats(nbody_mmd *h, double mu[6], double scale[6]
 /* Release the evaluator; NULL is a no-op. */
 NBODY_API void nbody_mmd_destroy(nbody_mmd *h);
 
-/* ---- orbit fitting and the Fisher matrix (Sec. 3.2) ----
+/* ---- orbit fitting and the Fisher matrix (Sec. 2.2.2) ----
  *
  * The progenitor, a single particle, is integrated from its present-day
  * point (X0, V0) forward and backward with kick-drift-kick steps of dt in

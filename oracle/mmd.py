@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY.
 
-The paper's first inference method (Sec. 3.1; Fig. 2, step 4) treats the
+The paper's first inference method (Sec. 2.2.1; Fig. 2, step 4) treats the
 simulated and the observed stream as point clouds and compares them with the
 maximum mean discrepancy; the grid search of that method ranks 10^4
 parameter vectors by it.  The paper names neither the kernel nor its

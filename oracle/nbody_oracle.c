@@ -14,7 +14,7 @@
  *     pairwise forces with softening, no tree or multipole), Plummer
  *     softening a_i = -G sum_{j!=i} m_j (x_i-x_j) (|x_i-x_j|^2+eps^2)^-3/2;
  *   - the NFW halo, Miyamoto-Nagai disk and power-law bulge of
- *     MWPotential2014 (Sec. 2.2.1, Sec. 3.1):
+ *     MWPotential2014 (Sec. 2.2.1):
  *     potential, acceleration and the Jacobian of the acceleration;
  *   - the second-order Velocity-Verlet (kick-drift-kick) integrator with a
  *     fixed number of steps (Sec. 2.2.1);
@@ -288,7 +288,7 @@ static void mn_unit_jac(double ma, double mb, const double *p, double J[9]) {
 }
 
 /* Power-law bulge with an exponential cut-off, the bulge of MWPotential2014
- * (Sec. 3.1): rho(r) = rho_0 (r/r_1)^-alpha exp(-(r/r_c)^2), normalised by
+ * (Sec. 2.2.1): rho(r) = rho_0 (r/r_1)^-alpha exp(-(r/r_c)^2), normalised by
  * its total mass M_b = 2 pi rho_0 r_1^alpha r_c^(3-alpha) Gamma(s),
  * s = (3 - alpha)/2, so 4 pi rho_0 r_1^alpha = 2 M_b / (r_c^(3-alpha) Gamma(s)).
  * Everything follows from the density by its definitions:

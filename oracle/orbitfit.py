@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY.
 
-The paper's second inference method (Sec. 3.2): a single particle, the
+The paper's second inference method (Sec. 2.2.2): a single particle, the
 progenitor, is integrated forward and backward for up to 2 Gyr from its
 present-day phase-space point in the external potential; its orbit is
 projected onto the stream's frame (phi1, phi2, mu_phi1 cos phi2, mu_phi2,
@@ -37,8 +37,6 @@ differences (Richardson) of chi^2, written in the tests.
 """
 from __future__ import annotations
 
-import math
-
 import numpy as np
 
 from . import core
@@ -71,7 +69,7 @@ def observables(x, v, x_obs, v_obs, fr):
 class OrbitFit:
     """chi^2 of the progenitor's orbit against an observed track."""
 
-    def __init__(self, G, X0, V0, x_obs, v_obs, window, dt, t_max, pot_fixed=None):
+    def __init__(self, G, X0, V0, x_obs, v_obs, window, dt, t_max):
         self.G = G
         self.X0 = np.asarray(X0, float)
         self.V0 = np.asarray(V0, float)
@@ -172,7 +170,3 @@ def fd_hessian(f, xi, h=1e-3):
             H[a, b] = H[b, a] = (f(xi + ea + eb) - f(xi + ea - eb) - f(xi - ea + eb)
                                  + f(xi - ea - eb)) / (4 * h * h)
     return H
-
-
-def deg(x):
-    return math.radians(x)

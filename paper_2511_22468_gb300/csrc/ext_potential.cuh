@@ -1,6 +1,6 @@
 // ext_potential.cuh -- FP64 device functions of the external potential:
 // MWPotential2014's NFW halo, Miyamoto-Nagai disk and bulge (paper
-// Sec. 2.2.1, Sec. 3.1),
+// Sec. 2.2.1),
 //   NFW  Phi = -G M ln(1 + r/r_s) / r,
 //   MN   Phi = -G M / sqrt(R^2 + (a + sqrt(z^2 + b^2))^2),
 //   bulge rho = rho_0 (r/r_1)^-alpha exp(-(r/r_c)^2) with total mass M_b:

@@ -1,5 +1,5 @@
 // mmd.cu -- maximum mean discrepancy between phase-space point clouds
-// (paper Sec. 3.1, Fig. 2 step 4: the simulated and the observed stream
+// (paper Sec. 2.2.1, Fig. 2 step 4: the simulated and the observed stream
 // compared as point clouds; the grid search ranks parameter vectors by it).
 //
 // A point is q = (x, y, z, vx, vy, vz).  Coordinates are standardised by

@@ -1,5 +1,5 @@
 // orbitfit.cu -- orbit fitting of the progenitor and the Fisher matrix
-// (paper Sec. 3.2).  A single particle is integrated from its present-day
+// (paper Sec. 2.2.2).  A single particle is integrated from its present-day
 // phase-space point forward and backward in the NFW + Miyamoto-Nagai field
 // with kick-drift-kick steps, projected onto the stream frame (phi1, phi2,
 // mu_phi1 cos phi2, mu_phi2, v_h), interpolated along phi1 at the observed

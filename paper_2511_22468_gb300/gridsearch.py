@@ -1,5 +1,5 @@
 """Grid search and gradient refinement with the point-cloud loss (the
-paper's first inference method, Sec. 3.1 and Fig. 2).
+paper's first inference method, Sec. 2.2.1 and Fig. 2).
 
   * observation: the simulated stream (final phase-space cloud) at theta_obs;
   * grid: a regular grid of per_dim^4 parameter vectors theta = (t_end,

@@ -1,5 +1,5 @@
 """Orbit fitting and Fisher contours (the paper's second inference method,
-Sec. 3.2) on a synthetic stream track.
+Sec. 2.2.2) on a synthetic stream track.
 
   * observation: the progenitor's arc at theta_true = (M_NFW, r_s, M_MN,
     a_MN, b_MN) projected to (phi1, phi2, mu_phi1 cos phi2, mu_phi2, v_h),

@@ -1,4 +1,4 @@
-"""Orbit fitting and the Fisher matrix (Sec. 3.2) against the oracle (needs
+"""Orbit fitting and the Fisher matrix (Sec. 2.2.2) against the oracle (needs
 a GB300).  Observations come from the oracle's orbit at the true
 parameters.  Tolerances: arc points and chi^2 1e-10 relative (FP64 on both
 sides, different operation order); the dual-number gradient and
