@@ -250,13 +250,26 @@ NBODY_API int nbody_set_pair_shape(nbody_ctx *c, int vjp, int variant,
 /* Current shape {variant, threads, per_thread, chunks} (host, 4 ints). */
 NBODY_API int nbody_get_pair_shape(nbody_ctx *c, int vjp, int out[4]);
 
+/* Where the chunk sums of a tile-variant pair kernel split into chunks >= 2
+ * are added up: mode 1 = by the block of each row tile that finishes last,
+ * inside the pair kernel (the consumer then reads one slice); 0 = by the
+ * consumer (the update or adjoint kernel reads every chunk's slice); -1 =
+ * automatic (1 when chunks >= 8, the default).  Both add the slices in
+ * ascending chunk order, so results are bitwise the same; only the time
+ * differs.  vjp selects the pair-VJP kernel (1) or the pair-force kernel (0).
+ * Errors: EINVAL. */
+NBODY_API int nbody_set_pair_finish(nbody_ctx *c, int vjp, int mode);
+
 /* Tune the pair-force and pair-VJP launch shapes of a single-system context
  * on its current state: every supported shape and tile size, each with the
  * chunk count chosen to fill the GPU and the nearest counts that split the
- * j-tiles evenly, is timed over at least probe_launches launches (about 2 ms
- * of them) and the fastest is kept.  fwd_best / vjp_best (host, 4 ints each, may be NULL) receive the
- * chosen {variant, threads, per_thread, chunks}.  The state is not advanced;
- * the tape and the cached acceleration are invalidated.  Synchronises.
+ * j-tiles evenly, and each with its chunk sums added in the pair kernel and
+ * by the consumer (nbody_set_pair_finish), is timed together with a consumer
+ * of its sums (the update kernel with a zero kick) over at least
+ * probe_launches launches (about 2 ms of them); the fastest is kept.
+ * fwd_best / vjp_best (host, 4 ints each, may be NULL) receive the chosen
+ * {variant, threads, per_thread, chunks}.  The state is not advanced; the
+ * tape and the cached acceleration are invalidated.  Synchronises.
  * Errors: EINVAL, ECUDA. */
 NBODY_API int nbody_autotune_pair(nbody_ctx *c, int probe_launches,
                                   int fwd_best[4], int vjp_best[4]);

@@ -58,6 +58,11 @@ struct nbody_ctx {
   float4* vst = nullptr;  // [2*npad]
   double* part = nullptr; // [Smax][3][npad]
   double* pot = nullptr;  // [Sf][npad]
+  double* fin = nullptr;  // pair (or VJP) sums with the slices summed [4][npad]
+  unsigned* pctr = nullptr;  // finished-chunk counters per row tile [npad/128]
+  int fin_mode = -1;  // forward slices summed in the pair kernel: 1 yes, 0 no,
+                      // -1 by chunk count (S >= 8)
+  int vfin_mode = -1;  // the same for the VJP kernel
   int Smax = 0;
   nb::PairCfg fcfg{}, vcfg{};
   double m_eq = 1.0;  // the common mass when fcfg.eqm / vcfg.eqm
@@ -399,6 +404,29 @@ int join_field(nbody_ctx* c, cudaStream_t s, nb::UpdateArgs& a) {
   return NBODY_OK;
 }
 
+// The pair kernel of one forward point; with the tile kernel split into
+// S >= 2 j-chunks its last block per row tile sums the slices, and the
+// update reads that one slice (same sums, same order).
+bool use_fin(const nb::PairCfg& f, int mode) {
+  if (f.variant != nb::kTile || f.S < 2) return false;
+  return mode < 0 ? f.S >= 8 : mode == 1;
+}
+
+int pair_forward(nbody_ctx* c, nb::UpdateArgs& a, cudaStream_t s) {
+  const bool fin = use_fin(c->fcfg, c->fin_mode);
+  CK(timed(c, NBODY_KCLASS_PAIR, [&] {
+    return fin ? nb::launch_pair_accel_fin(c->fcfg, c->st, c->npad, c->hp.eps2f, c->part,
+                                           c->fin, c->pctr, s)
+               : nb::launch_pair_accel(c->fcfg, c->st, c->npad, c->hp.eps2f, c->part,
+                                       nullptr, s);
+  }));
+  if (fin) {
+    a.part = c->fin;
+    a.S = 1;
+  }
+  return NBODY_OK;
+}
+
 // The launches of a forward run over points 0..n_steps (on stream s).
 int record_forward(nbody_ctx* c, int64_t n_steps, bool with_tape, cudaStream_t s) {
   if (c->p.center_mode == NBODY_CENTER_GUIDE)
@@ -418,10 +446,7 @@ int record_forward(nbody_ctx* c, int64_t n_steps, bool with_tape, cudaStream_t s
       if (k == 0)
         CK(nb::launch_stage(c->x, c->m, center_at(c, 0), c->n, c->npad, c->st, s));
       if (int r_ = fork_field(c, c->x, s)) return r_;
-      CK(timed(c, NBODY_KCLASS_PAIR, [&] {
-        return nb::launch_pair_accel(c->fcfg, c->st, c->npad, c->hp.eps2f,
-                                     c->part, nullptr, s);
-      }));
+      if (int r_ = pair_forward(c, a, s)) return r_;
       if (int r_ = join_field(c, s, a)) return r_;
     }
     a.acc_out = (k == n_steps) ? c->acc : nullptr;
@@ -465,7 +490,7 @@ int run_forward(nbody_ctx* c, int64_t n_steps, bool with_tape) {
     const uint64_t key[12] = {1, (uint64_t)n_steps, (uint64_t)with_tape, (uint64_t)K,
                               (uint64_t)c->p.tape_mode, (uint64_t)c->acc_valid,
                               (uint64_t)c->p.center_mode, cfg_word(c->fcfg), bits(c->m_eq),
-                              0, 0, 0};
+                              (uint64_t)use_fin(c->fcfg, c->fin_mode), 0, 0};
     rc = run_graph(c, key, [&](cudaStream_t gs) { return record_forward(c, n_steps, with_tape, gs); });
   } else {
     rc = record_forward(c, n_steps, with_tape, c->stream);
@@ -500,10 +525,7 @@ int recompute_segment(nbody_ctx* c, int64_t sg, cudaStream_t s) {
       a.part_is_final = 1;
     } else {
       if (int r_ = fork_field(c, c->xw, s)) return r_;
-      CK(timed(c, NBODY_KCLASS_PAIR, [&] {
-        return nb::launch_pair_accel(c->fcfg, c->st, c->npad, c->hp.eps2f,
-                                     c->part, nullptr, s);
-      }));
+      if (int r_ = pair_forward(c, a, s)) return r_;
       if (int r_ = join_field(c, s, a)) return r_;
     }
     a.kick = (k == 0) ? 0.5 : 1.0;
@@ -561,6 +583,8 @@ void free_all(nbody_ctx* c) {
   dfree(c->vst);
   dfree(c->part);
   dfree(c->pot);
+  dfree(c->fin);
+  dfree(c->pctr);
   dfree(c->guide);
   dfree(c->fixed_center);
   dfree(c->centers);
@@ -647,7 +671,8 @@ int nbody_create(nbody_ctx** out, int64_t n, const nbody_params* p,
       (rc = dalloc(&c->guide, 6)) || (rc = dalloc(&c->fixed_center, 3)) ||
       (rc = dalloc(&c->xbar, 3 * np)) || (rc = dalloc(&c->vbar, 3 * np)) ||
       (rc = dalloc(&c->blk, (size_t)c->nblk * std::max(nb::kAdjCols, 6))) || (rc = dalloc(&c->red, 8)) || (rc = dalloc(&c->lsc, nb::kLscDoubles)) ||
-      (rc = dalloc(&c->status, 1)) || (rc = dalloc(&c->aext, 3 * np))) {
+      (rc = dalloc(&c->status, 1)) || (rc = dalloc(&c->aext, 3 * np)) ||
+      (rc = dalloc(&c->fin, 4 * np)) || (rc = dalloc(&c->pctr, np / 128))) {
     free_all(c);
     delete c;
     return rc;
@@ -672,7 +697,8 @@ int nbody_create(nbody_ctx** out, int64_t n, const nbody_params* p,
       cudaMemsetAsync(c->vbar, 0, 3 * np * sizeof(double), s) ||
       cudaMemsetAsync(c->st, 0, np * sizeof(float4), s) ||
       cudaMemsetAsync(c->vst, 0, 2 * np * sizeof(float4), s) ||
-      cudaMemsetAsync(c->status, 0, sizeof(int), s) || upload_params(c)) {
+      cudaMemsetAsync(c->status, 0, sizeof(int), s) ||
+      cudaMemsetAsync(c->pctr, 0, (np / 128) * sizeof(unsigned), s) || upload_params(c)) {
     free_all(c);
     delete c;
     return NBODY_ECUDA;
@@ -810,6 +836,14 @@ int record_sweep(nbody_ctx* c, cudaStream_t s) {
   a.mbar = c->want_mbar ? c->mbar : nullptr;
   a.status = c->status;
   double* mp = c->want_mbar ? c->mpart : nullptr;
+  // with the VJP's slices summed in its kernel the adjoint reads one slice
+  const bool vfin = use_fin(c->vcfg, c->vfin_mode);
+  double* vfin_p = vfin ? c->fin : nullptr;
+  if (vfin) {
+    a.gpart = c->fin;
+    a.S = 1;
+    if (a.mpart) a.mpart = c->fin + 3 * np;
+  }
   for (int64_t sg = nseg - 1; sg >= 0; --sg) {
     const int64_t k0 = sg * K;
     const int64_t Ks = (k0 + K <= n) ? K : n - k0;
@@ -820,7 +854,8 @@ int record_sweep(nbody_ctx* c, cudaStream_t s) {
     for (int64_t j = Ks; j >= 1; --j) {
       const int64_t k = k0 + j;
       CK(timed(c, NBODY_KCLASS_VJP, [&] {
-        return nb::launch_pair_vjp(c->vcfg, c->vst, c->npad, c->hp.eps2f, c->part, mp, s);
+        return nb::launch_pair_vjp_fin(c->vcfg, c->vst, c->npad, c->hp.eps2f, c->part, mp,
+                                       vfin_p, c->pctr, s);
       }));
       a.xk = (j == Ks) ? T.cpx(sg + 1) : T.sx(j);
       a.ak = (j == Ks) ? T.cpa(sg + 1) : T.sa(j);
@@ -836,7 +871,8 @@ int record_sweep(nbody_ctx* c, cudaStream_t s) {
   }
   // point 0: opening half kick of the first step
   CK(timed(c, NBODY_KCLASS_VJP, [&] {
-    return nb::launch_pair_vjp(c->vcfg, c->vst, c->npad, c->hp.eps2f, c->part, mp, s);
+    return nb::launch_pair_vjp_fin(c->vcfg, c->vst, c->npad, c->hp.eps2f, c->part, mp, vfin_p,
+                                   c->pctr, s);
   }));
   a.xk = T.cpx(0);
   a.ak = T.cpa(0);
@@ -882,7 +918,8 @@ int nbody_vjp(nbody_ctx* c, const double* xbar, const double* vbar,
     const uint64_t key[12] = {2, (uint64_t)c->tape_steps, (uint64_t)c->K, (uint64_t)c->nseg,
                               (uint64_t)c->last_seg_valid, (uint64_t)c->p.center_mode,
                               cfg_word(c->fcfg), cfg_word(c->vcfg), bits(c->m_eq),
-                              (uint64_t)c->want_mbar, 0, 0};
+                              (uint64_t)c->want_mbar, (uint64_t)use_fin(c->fcfg, c->fin_mode),
+                              (uint64_t)use_fin(c->vcfg, c->vfin_mode)};
     rc = run_graph(c, key, [&](cudaStream_t gs) { return record_sweep(c, gs); });
   } else {
     rc = record_sweep(c, s);
@@ -1039,6 +1076,12 @@ int nbody_set_pair_shape(nbody_ctx* c, int vjp, int variant, int threads,
   return NBODY_OK;
 }
 
+int nbody_set_pair_finish(nbody_ctx* c, int vjp, int mode) {
+  if (!c || c->batch || mode < -1 || mode > 1) return NBODY_EINVAL;
+  (vjp ? c->vfin_mode : c->fin_mode) = mode;
+  return NBODY_OK;
+}
+
 int nbody_get_pair_shape(nbody_ctx* c, int vjp, int out[4]) {
   if (!c || c->batch || !out) return NBODY_EINVAL;
   const nb::PairCfg& cfg = vjp ? c->vcfg : c->fcfg;
@@ -1072,6 +1115,7 @@ int nbody_autotune_pair(nbody_ctx* c, int probe_launches, int fwd_best[4],
   const Shape vjp[] = {{0, 256, 2, 0}, {0, 128, 4, 0}, {0, 128, 2, 0}, {0, 128, 1, 0},
                        {1, 256, 4, 0}, {1, 256, 2, 0}};
   int rc = NBODY_OK;
+  int best_fin[2] = {0, 0};
   for (int which = 0; which < 2 && rc == NBODY_OK; ++which) {
     const Shape* list = which ? vjp : fwd;
     const int cnt = which ? (int)(sizeof(vjp) / sizeof(vjp[0])) : (int)(sizeof(fwd) / sizeof(fwd[0]));
@@ -1101,14 +1145,29 @@ int nbody_autotune_pair(nbody_ctx* c, int probe_launches, int fwd_best[4],
         for (int d = S0 + 1; d <= std::min<int64_t>(ntiles, c->Smax); ++d)
           if (ntiles % d == 0) { cand[2] = d; break; }
       }
-      for (int ci = 0; ci < 3 && rc == NBODY_OK; ++ci) {
-        if (cand[ci] < 1 || cand[ci] > c->Smax || (ci > 0 && (cand[ci] == S0 ||
-                                                           (ci == 2 && cand[2] == cand[1]))))
+      // every candidate is timed with a consumer of its sums, the update
+      // (kick 0, no drift: the state is left as it is; for the VJP it stands
+      // in for the adjoint, which reads the same slices), once with the
+      // slices summed by the consumer and once in the pair kernel
+      for (int ci = 0; ci < 6 && rc == NBODY_OK; ++ci) {
+        const int cs = ci % 3, fin = ci / 3;
+        if (cand[cs] < 1 || cand[cs] > c->Smax || (cs > 0 && (cand[cs] == S0 ||
+                                                           (cs == 2 && cand[2] == cand[1]))))
           continue;
-        t.S = cand[ci];
+        if (fin && (t.variant != nb::kTile || cand[cs] < 2)) continue;
+        t.S = cand[cs];
+        nb::UpdateArgs u = base_update(c, c->x, c->v);
+        u.S = fin ? 1 : t.S;
+        u.part = fin ? c->fin : c->part;
+        u.mscale = 0.0;
         auto launch = [&]() {
-          return which ? nb::launch_pair_vjp(t, c->vst, c->npad, c->hp.eps2f, c->part, nullptr, s)
-                       : nb::launch_pair_accel(t, c->st, c->npad, c->hp.eps2f, c->part, nullptr, s);
+          double* f = fin ? c->fin : nullptr;
+          const cudaError_t e =
+              which ? nb::launch_pair_vjp_fin(t, c->vst, c->npad, c->hp.eps2f, c->part, nullptr,
+                                              f, c->pctr, s)
+                    : nb::launch_pair_accel_fin(t, c->st, c->npad, c->hp.eps2f, c->part, f,
+                                                c->pctr, s);
+          return e == cudaSuccess ? nb::launch_update(u, s) : e;
         };
         if (launch() != cudaSuccess) {
           rc = NBODY_ECUDA;
@@ -1138,16 +1197,19 @@ int nbody_autotune_pair(nbody_ctx* c, int probe_launches, int fwd_best[4],
         if (ms < best_ms) {
           best_ms = ms;
           best = t;
+          best_fin[which] = fin;
         }
       }
     }
     if (which) {
       c->vcfg = best;
+      c->vfin_mode = best_fin[1];
       if (vjp_best) {
         vjp_best[0] = best.variant; vjp_best[1] = best.nt; vjp_best[2] = best.r; vjp_best[3] = best.S;
       }
     } else {
       c->fcfg = best;
+      c->fin_mode = best_fin[0];
       if (fwd_best) {
         fwd_best[0] = best.variant; fwd_best[1] = best.nt; fwd_best[2] = best.r; fwd_best[3] = best.S;
       }

@@ -81,6 +81,13 @@ int choose_chunks(const PairCfg& c, int64_t npad, int sm_count, int blocks_per_s
 // common mass is left out too) into part[S][3][npad];
 // with pot != NULL also P_i = sum_j m_j / s_ij (self term included) into
 // pot[S][npad].
+// The same (tile variant, S >= 2) with the S partial slices of every row
+// tile summed by the tile's last-finishing block into fin [3][npad] (raw
+// sums, ascending chunk order); ctr: one counter per row tile, zero between
+// launches.  Other shapes fall back to launch_pair_accel (partials only).
+cudaError_t launch_pair_accel_fin(const PairCfg& cfg, const float4* st, int64_t npad,
+                                  float eps2, double* part, double* fin, unsigned* ctr,
+                                  cudaStream_t s);
 cudaError_t launch_pair_accel(const PairCfg& cfg, const float4* st,
                               int64_t npad, float eps2, double* part,
                               double* pot, cudaStream_t s);
@@ -93,6 +100,12 @@ cudaError_t launch_pair_accel(const PairCfg& cfg, const float4* st,
 cudaError_t launch_pair_vjp(const PairCfg& cfg, const float4* vst,
                             int64_t npad, float eps2, double* part,
                             double* mpart, cudaStream_t s);
+// The same with the slices of every row tile summed by its last-finishing
+// block (tile variant, S >= 2; otherwise fin is ignored): Q into fin[0..2]
+// [npad], M into fin[3][npad]; ctr as for launch_pair_accel_fin.
+cudaError_t launch_pair_vjp_fin(const PairCfg& cfg, const float4* vst, int64_t npad,
+                                float eps2, double* part, double* mpart, double* fin,
+                                unsigned* ctr, cudaStream_t s);
 
 // ---- per-particle kernels (update.cu) ----
 cudaError_t launch_stage(const double* x, const double* m, const double* c,

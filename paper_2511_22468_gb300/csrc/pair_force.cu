@@ -18,6 +18,7 @@
 //
 // Warp variant (small N): a warp owns R i-particles and its 32 lanes split
 // the j-range; lane sums are combined by a fixed xor-shuffle butterfly.
+#include "block_reduce.cuh"
 #include "nbody_internal.cuh"
 #include "pair_body.cuh"
 
@@ -45,7 +46,8 @@ template <int NT, int R, bool POT, bool EQM, int TJ = kTJ>
 __global__ void __launch_bounds__(NT, NB_PAIR_MINB)
     k_pair_tile(const float4* __restrict__ st, int ntiles, float eps2,
                 int64_t npad, double* __restrict__ part,
-                double* __restrict__ pot) {
+                double* __restrict__ pot, double* __restrict__ fin,
+                unsigned* __restrict__ ctr) {
   __shared__ float4 sj[2 * TJ];
   const int t = threadIdx.x;
   const int64_t i0 = (int64_t)blockIdx.x * (NT * R) + t;
@@ -110,6 +112,7 @@ __global__ void __launch_bounds__(NT, NB_PAIR_MINB)
     p[2 * npad + i] = daz[r];
     if (POT) pot[(int64_t)blockIdx.y * npad + i] = dph[r];
   }
+  if (fin) finish_row_tile<NT, R>(part, nullptr, S, npad, i0, fin, ctr);
 }
 
 // Warp variant: block of 8 warps; warp w owns i = (blockIdx.x*8 + w)*R + r.
@@ -175,17 +178,17 @@ __global__ void __launch_bounds__(256)
 
 template <bool POT, bool EQM>
 cudaError_t launch_impl(const PairCfg& c, const float4* st, int64_t npad,
-                        float eps2, double* part, double* pot,
-                        cudaStream_t s) {
+                        float eps2, double* part, double* pot, double* fin,
+                        unsigned* ctr, cudaStream_t s) {
   if (c.variant == kTile && c.vjp_tile_pairs == kTJSmall) {
     const int ntiles = (int)(npad / (2 * kTJSmall));
     dim3 grid((unsigned)(npad / (c.nt * c.r)), (unsigned)c.S);
     if (c.nt == 128 && c.r == 4)
-      k_pair_tile<128, 4, POT, EQM, kTJSmall><<<grid, 128, 0, s>>>(st, ntiles, eps2, npad, part, pot);
+      k_pair_tile<128, 4, POT, EQM, kTJSmall><<<grid, 128, 0, s>>>(st, ntiles, eps2, npad, part, pot, fin, ctr);
     else if (c.nt == 128 && c.r == 2)
-      k_pair_tile<128, 2, POT, EQM, kTJSmall><<<grid, 128, 0, s>>>(st, ntiles, eps2, npad, part, pot);
+      k_pair_tile<128, 2, POT, EQM, kTJSmall><<<grid, 128, 0, s>>>(st, ntiles, eps2, npad, part, pot, fin, ctr);
     else if (c.nt == 128 && c.r == 1)
-      k_pair_tile<128, 1, POT, EQM, kTJSmall><<<grid, 128, 0, s>>>(st, ntiles, eps2, npad, part, pot);
+      k_pair_tile<128, 1, POT, EQM, kTJSmall><<<grid, 128, 0, s>>>(st, ntiles, eps2, npad, part, pot, fin, ctr);
     else
       return cudaErrorInvalidValue;
   } else if (c.variant == kTile) {
@@ -194,17 +197,17 @@ cudaError_t launch_impl(const PairCfg& c, const float4* st, int64_t npad,
     const int per_block = c.nt * c.r;
     dim3 grid((unsigned)(npad / per_block), (unsigned)c.S);
     if (c.nt == 128 && c.r == 4)
-      k_pair_tile<128, 4, POT, EQM><<<grid, 128, 0, s>>>(st, ntiles, eps2, npad, part, pot);
+      k_pair_tile<128, 4, POT, EQM><<<grid, 128, 0, s>>>(st, ntiles, eps2, npad, part, pot, fin, ctr);
     else if (c.nt == 128 && c.r == 8)
-      k_pair_tile<128, 8, POT, EQM><<<grid, 128, 0, s>>>(st, ntiles, eps2, npad, part, pot);
+      k_pair_tile<128, 8, POT, EQM><<<grid, 128, 0, s>>>(st, ntiles, eps2, npad, part, pot, fin, ctr);
     else if (c.nt == 256 && c.r == 4)
-      k_pair_tile<256, 4, POT, EQM><<<grid, 256, 0, s>>>(st, ntiles, eps2, npad, part, pot);
+      k_pair_tile<256, 4, POT, EQM><<<grid, 256, 0, s>>>(st, ntiles, eps2, npad, part, pot, fin, ctr);
     else if (c.nt == 256 && c.r == 2)
-      k_pair_tile<256, 2, POT, EQM><<<grid, 256, 0, s>>>(st, ntiles, eps2, npad, part, pot);
+      k_pair_tile<256, 2, POT, EQM><<<grid, 256, 0, s>>>(st, ntiles, eps2, npad, part, pot, fin, ctr);
     else if (c.nt == 128 && c.r == 2)
-      k_pair_tile<128, 2, POT, EQM><<<grid, 128, 0, s>>>(st, ntiles, eps2, npad, part, pot);
+      k_pair_tile<128, 2, POT, EQM><<<grid, 128, 0, s>>>(st, ntiles, eps2, npad, part, pot, fin, ctr);
     else if (c.nt == 128 && c.r == 1)
-      k_pair_tile<128, 1, POT, EQM><<<grid, 128, 0, s>>>(st, ntiles, eps2, npad, part, pot);
+      k_pair_tile<128, 1, POT, EQM><<<grid, 128, 0, s>>>(st, ntiles, eps2, npad, part, pot, fin, ctr);
     else
       return cudaErrorInvalidValue;
   } else {
@@ -225,9 +228,19 @@ cudaError_t launch_impl(const PairCfg& c, const float4* st, int64_t npad,
 cudaError_t launch_pair_accel(const PairCfg& cfg, const float4* st,
                               int64_t npad, float eps2, double* part,
                               double* pot, cudaStream_t s) {
-  if (pot) return launch_impl<true, false>(cfg, st, npad, eps2, part, pot, s);
-  if (cfg.eqm) return launch_impl<false, true>(cfg, st, npad, eps2, part, nullptr, s);
-  return launch_impl<false, false>(cfg, st, npad, eps2, part, nullptr, s);
+  if (pot) return launch_impl<true, false>(cfg, st, npad, eps2, part, pot, nullptr, nullptr, s);
+  if (cfg.eqm)
+    return launch_impl<false, true>(cfg, st, npad, eps2, part, nullptr, nullptr, nullptr, s);
+  return launch_impl<false, false>(cfg, st, npad, eps2, part, nullptr, nullptr, nullptr, s);
+}
+
+cudaError_t launch_pair_accel_fin(const PairCfg& cfg, const float4* st, int64_t npad,
+                                  float eps2, double* part, double* fin, unsigned* ctr,
+                                  cudaStream_t s) {
+  if (!fin || cfg.variant != kTile || cfg.S < 2)
+    return launch_pair_accel(cfg, st, npad, eps2, part, nullptr, s);
+  if (cfg.eqm) return launch_impl<false, true>(cfg, st, npad, eps2, part, nullptr, fin, ctr, s);
+  return launch_impl<false, false>(cfg, st, npad, eps2, part, nullptr, fin, ctr, s);
 }
 
 int pair_blocks_per_sm(const PairCfg& c) {

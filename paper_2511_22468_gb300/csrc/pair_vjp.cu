@@ -14,6 +14,7 @@
 // rsqrt per interaction.  With equal masses u = m (l_k - l_j), the mass is
 // applied by the consumer, and the s^-3 and s^-5 sums are kept apart
 // (Q = A - 3 B): 22 FP32 operations per interaction.
+#include "block_reduce.cuh"
 #include "nbody_internal.cuh"
 
 namespace nb {
@@ -146,7 +147,8 @@ __device__ __forceinline__ void mass_body(const float4& A, const float4& B,
 template <int NT, int R, bool EQM, bool MB>
 __global__ void __launch_bounds__(NT, NB_VJP_MINB)
     k_vjp_tile(const float4* __restrict__ vst, int ntiles, float eps2,
-               int64_t npad, double* __restrict__ part, double* __restrict__ mpart) {
+               int64_t npad, double* __restrict__ part, double* __restrict__ mpart,
+               double* __restrict__ fin, unsigned* __restrict__ ctr) {
   __shared__ float4 sj[4 * kTJ];
   const int t = threadIdx.x;
   const int64_t k0 = (int64_t)blockIdx.x * (NT * R) + t;
@@ -210,6 +212,7 @@ __global__ void __launch_bounds__(NT, NB_VJP_MINB)
     p[2 * npad + k] = gz[r];
     if (MB) mpart[(int64_t)blockIdx.y * npad + k] = gm[r];
   }
+  if (fin) finish_row_tile<NT, R>(part, MB ? mpart : nullptr, S, npad, k0, fin, ctr);
 }
 
 template <int R, bool EQM, bool MB>
@@ -274,18 +277,19 @@ __global__ void __launch_bounds__(256)
 
 template <bool EQM, bool MB>
 cudaError_t launch_vjp_impl(const PairCfg& c, const float4* vst, int64_t npad,
-                            float eps2, double* part, double* mpart, cudaStream_t s) {
+                            float eps2, double* part, double* mpart, double* fin,
+                            unsigned* ctr, cudaStream_t s) {
   if (c.variant == kTile) {
     const int ntiles = (int)(npad / (2 * kTJ));
     dim3 grid((unsigned)(npad / (c.nt * c.r)), (unsigned)c.S);
     if (c.nt == 256 && c.r == 2)
-      k_vjp_tile<256, 2, EQM, MB><<<grid, 256, 0, s>>>(vst, ntiles, eps2, npad, part, mpart);
+      k_vjp_tile<256, 2, EQM, MB><<<grid, 256, 0, s>>>(vst, ntiles, eps2, npad, part, mpart, fin, ctr);
     else if (c.nt == 128 && c.r == 4)
-      k_vjp_tile<128, 4, EQM, MB><<<grid, 128, 0, s>>>(vst, ntiles, eps2, npad, part, mpart);
+      k_vjp_tile<128, 4, EQM, MB><<<grid, 128, 0, s>>>(vst, ntiles, eps2, npad, part, mpart, fin, ctr);
     else if (c.nt == 128 && c.r == 2)
-      k_vjp_tile<128, 2, EQM, MB><<<grid, 128, 0, s>>>(vst, ntiles, eps2, npad, part, mpart);
+      k_vjp_tile<128, 2, EQM, MB><<<grid, 128, 0, s>>>(vst, ntiles, eps2, npad, part, mpart, fin, ctr);
     else if (c.nt == 128 && c.r == 1)
-      k_vjp_tile<128, 1, EQM, MB><<<grid, 128, 0, s>>>(vst, ntiles, eps2, npad, part, mpart);
+      k_vjp_tile<128, 1, EQM, MB><<<grid, 128, 0, s>>>(vst, ntiles, eps2, npad, part, mpart, fin, ctr);
     else
       return cudaErrorInvalidValue;
   } else {
@@ -328,14 +332,21 @@ int vjp_blocks_per_sm(const PairCfg& c) {
   return occ > 0 ? occ : 1;
 }
 
+cudaError_t launch_pair_vjp_fin(const PairCfg& c, const float4* vst, int64_t npad,
+                                float eps2, double* part, double* mpart, double* fin,
+                                unsigned* ctr, cudaStream_t s) {
+  if (c.variant != kTile || c.S < 2) fin = nullptr;
+  if (mpart) {
+    if (c.eqm) return launch_vjp_impl<true, true>(c, vst, npad, eps2, part, mpart, fin, ctr, s);
+    return launch_vjp_impl<false, true>(c, vst, npad, eps2, part, mpart, fin, ctr, s);
+  }
+  if (c.eqm) return launch_vjp_impl<true, false>(c, vst, npad, eps2, part, nullptr, fin, ctr, s);
+  return launch_vjp_impl<false, false>(c, vst, npad, eps2, part, nullptr, fin, ctr, s);
+}
+
 cudaError_t launch_pair_vjp(const PairCfg& c, const float4* vst, int64_t npad,
                             float eps2, double* part, double* mpart, cudaStream_t s) {
-  if (mpart) {
-    if (c.eqm) return launch_vjp_impl<true, true>(c, vst, npad, eps2, part, mpart, s);
-    return launch_vjp_impl<false, true>(c, vst, npad, eps2, part, mpart, s);
-  }
-  if (c.eqm) return launch_vjp_impl<true, false>(c, vst, npad, eps2, part, nullptr, s);
-  return launch_vjp_impl<false, false>(c, vst, npad, eps2, part, nullptr, s);
+  return launch_pair_vjp_fin(c, vst, npad, eps2, part, mpart, nullptr, nullptr, s);
 }
 
 }  // namespace nb

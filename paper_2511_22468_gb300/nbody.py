@@ -48,7 +48,7 @@ EXPORTED = ("nbody_create", "nbody_destroy", "nbody_set_params",
             "nbody_mlp_num_params", "nbody_mlp_set_params", "nbody_mlp_get_params",
             "nbody_mlp_forward", "nbody_mlp_loss_grad", "nbody_mlp_adam_step",
             "nbody_mlp_destroy", "nbody_mlp_invert", "nbody_set_pair_shape",
-            "nbody_get_pair_shape", "nbody_peaks", "nbody_autotune_pair",
+            "nbody_set_pair_finish", "nbody_get_pair_shape", "nbody_peaks", "nbody_autotune_pair",
             "nbody_potential_grad", "nbody_mmd_create", "nbody_mmd_eval",
             "nbody_mmd_eval_batch", "nbody_mmd_target_stats", "nbody_mmd_destroy",
             "nbody_stream_set_target_cloud", "nbody_stream_initial_states",
@@ -177,6 +177,7 @@ def lib():
         L.nbody_mlp_destroy.restype = None
         L.nbody_set_pair_shape.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]
         L.nbody_get_pair_shape.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
+        L.nbody_set_pair_finish.argtypes = [vp, C.c_int, C.c_int]
         L.nbody_peaks.argtypes = [dp, vp]
         L.nbody_autotune_pair.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.nbody_set_timing.argtypes = [vp, C.c_int]
@@ -398,6 +399,12 @@ def nbody_pair_accel_noalloc(x, m, G, eps, center, acc, stream=None):
 def nbody_set_pair_shape(h, vjp, variant, threads, per_thread, chunks=0):
     _check(lib().nbody_set_pair_shape(h, int(vjp), variant, threads, per_thread, chunks),
            "nbody_set_pair_shape")
+
+
+def nbody_set_pair_finish(h, vjp, mode):
+    """Chunk sums added in the pair kernel (1), by the consumer (0) or by
+    chunk count (-1); results are bitwise the same."""
+    _check(lib().nbody_set_pair_finish(h, int(vjp), int(mode)), "nbody_set_pair_finish")
 
 
 def nbody_get_pair_shape(h, vjp):

@@ -48,7 +48,7 @@ def measure(n, steps, adjoint=False, device="cuda:0", seed=5):
     M = torch.tensor(m, device=dev)
     sim = nb.Simulation(n, p)
     sim.set_state(X, V, M)
-    nb.nbody_autotune_pair(sim.h)
+    fwd_shape, vjp_shape = nb.nbody_autotune_pair(sim.h)
     stream = torch.cuda.current_stream(dev)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -75,6 +75,7 @@ def measure(n, steps, adjoint=False, device="cuda:0", seed=5):
         t_bwd = e0.elapsed_time(e1) / 1e3
         row["adjoint_ms_per_step"] = 1e3 * t_bwd / steps
         row["fwd_adjoint_interactions_per_s"] = 2.0 * n * n * steps / (t_fwd + t_bwd)
+    row["shapes"] = {"pair": list(fwd_shape), "vjp": list(vjp_shape)}
     row["status_ok"] = sim.status() == 0
     sim.close()
     return row

@@ -352,6 +352,50 @@ def test_graph_replay_equals_eager_launches():
     assert outs[0][2] == outs[1][2]
 
 
+@pytest.mark.parametrize("ext,uneq", [(0, False), (3, True)])
+def test_chunk_sums_in_kernel_equal_sums_by_consumer(ext, uneq):
+    """The chunk sums of a split pair kernel added by its last-finishing
+    block or by the update / adjoint kernel give the same bits (same slices,
+    same ascending order): trajectory, dL/dx0, dL/dv0, dL/dm and the
+    potential-parameter gradient."""
+    n = 5000
+    if ext:
+        x, v, m = plummer_sphere(n, 24, C1.G, C1.M_prog, C1.a_prog, center=C1.X0,
+                                 velocity=C1.V0)
+        G, eps, dt, pot = C1.G, C1.eps, 0.5, C1.pot
+    else:
+        x, v, m = plummer_sphere(n, 24, 1.0, 1.0, 1.0)
+        G, eps, dt, pot = 1.0, 0.01, 1e-3, None
+    if uneq:
+        m = m * np.random.default_rng(3).uniform(0.5, 1.5, n)
+    xb = torch.tensor(np.random.default_rng(4).normal(size=(3, n)), device=DEV)
+    vb = torch.tensor(np.random.default_rng(5).normal(size=(3, n)), device=DEV)
+    outs = []
+    for mode in (0, 1):
+        s = _sim(n, G, eps, dt, K=4, ext=ext, pot=pot, center=x.mean(axis=0),
+                 center_vel=v.mean(axis=0), guide=bool(ext))
+        for vjp in (0, 1):
+            nb.nbody_set_pair_shape(s.h, vjp, 0, 128, 1, 9)
+            nb.nbody_set_pair_finish(s.h, vjp, mode)
+        s.set_state(to_gpu(x), to_gpu(v), to_gpu(m))
+        xo = torch.empty((3, n), dtype=torch.float64, device=DEV)
+        vo = torch.empty_like(xo)
+        s.integrate(13, xo, vo)
+        g, gv = torch.empty_like(xo), torch.empty_like(xo)
+        gm = torch.empty(n, dtype=torch.float64, device=DEV)
+        tb = s.vjp(xb, vb, g, gv, gm)
+        pg = s.potential_grad() if ext else None
+        assert s.status() == 0
+        outs.append((xo, vo, g, gv, gm, tb, pg))
+        s.close()
+    a, b = outs
+    for k in range(5):
+        assert torch.equal(a[k], b[k]), k
+    assert a[5] == b[5]
+    if ext:
+        assert np.array_equal(np.asarray(a[6]), np.asarray(b[6]))
+
+
 def test_autotuned_shapes_match_oracle():
     n = 5000
     x, v, m = plummer_sphere(n, 23, 1.0, 1.0, 1.0)
