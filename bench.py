@@ -328,6 +328,23 @@ def hbm_peak():
         return 6800.0
 
 
+def kernel_source_hash(src):
+    """First 16 hex digits of the SHA-256 of a kernel's source file followed
+    by the device-code headers it includes (in include order; the shared
+    declarations header nbody_internal.cuh holds no device code and is left
+    out), so that a change to the kernel's code voids the recorded counters."""
+    csrc = os.path.join(ROOT, "paper_2511_22468_gb300", "csrc")
+    text = open(os.path.join(csrc, src), "rb").read()
+    h = hashlib.sha256(text)
+    for line in text.decode().splitlines():
+        line = line.strip()
+        if line.startswith('#include "'):
+            inc = os.path.join(csrc, line.split('"')[1])
+            if os.path.exists(inc) and not inc.endswith("nbody_internal.cuh"):
+                h.update(open(inc, "rb").read())
+    return h.hexdigest()[:16]
+
+
 def traffic_record(kernel):
     """Per-launch DRAM traffic of a kernel from the committed ncu summary,
     valid only while the kernel source is unchanged."""
@@ -337,8 +354,7 @@ def traffic_record(kernel):
     src = {"pair": "pair_force.cu", "vjp": "pair_vjp.cu"}.get(kernel)
     if src is None:
         return None
-    h = hashlib.sha256(open(os.path.join(ROOT, "paper_2511_22468_gb300", "csrc", src),
-                            "rb").read()).hexdigest()[:16]
+    h = kernel_source_hash(src)
     for line in open(path):
         kv = dict(t.split("=", 1) for t in line.split() if "=" in t)
         if kv.get("kernel") == kernel and kv.get("source_sha256_16") == h:
