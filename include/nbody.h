@@ -471,6 +471,23 @@ NBODY_API int nbody_mmd_eval(nbody_mmd *h, const double *x, const double *v,
 NBODY_API int nbody_mmd_eval_batch(nbody_mmd *h, int64_t sets, const double *x,
                                    const double *v, double *losses);
 
+/* MMD^2 of each of `sets` clouds against each of `targets` other clouds of
+ * m2 points (the bootstrap realisations of an observation, Sec. 2.2.1),
+ * with this evaluator's standardisation and bandwidths (those of its own
+ * target: MMD^2 depends on differences only, so every realisation is
+ * compared in the same units).  x, v: 3 x (sets n) as in
+ * nbody_mmd_eval_batch; ty, tv: 3 x (targets m2), target t in columns
+ * t m2 .. t m2 + m2 - 1 (host or device); losses[t * sets + b] (host or
+ * device, sets * targets doubles).  Every cloud's own term and every
+ * target's own term is computed once; the cross terms take one launch per
+ * group of targets.  1 <= sets, targets <= 65535.  Device scratch: 24 B
+ * per point of the clouds and targets, and up to 256 MB of block sums;
+ * allocated and freed by the call.  Synchronises.
+ * Errors: EINVAL, ENOMEM, ECUDA, ENAN. */
+NBODY_API int nbody_mmd_eval_cross(nbody_mmd *h, int64_t sets, const double *x,
+                                   const double *v, int64_t targets, int64_t m2,
+                                   const double *ty, const double *tv, double *losses);
+
 /* The standardisation in use: mu and s (host, 6 each; either may be NULL). */
 NBODY_API int nbody_mmd_target_stats(nbody_mmd *h, double mu[6], double scale[6]);
 

@@ -869,8 +869,8 @@ int batch_integrate(Batch* b, int64_t n_steps) {
 
 int batch_status(Batch* b) {
   int st = 0;
+  BCK(cudaMemcpyAsync(&st, b->status, sizeof(int), cudaMemcpyDeviceToHost, b->gs));
   BCK(cudaStreamSynchronize(b->gs));
-  BCK(cudaMemcpy(&st, b->status, sizeof(int), cudaMemcpyDeviceToHost));
   return (st & kStatusNaN) ? NBODY_ENAN : NBODY_OK;
 }
 

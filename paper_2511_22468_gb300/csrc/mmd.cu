@@ -26,6 +26,7 @@
 // one MUFU for one bandwidth, 4 operations and one MUFU more per extra one.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <new>
 #include <vector>
@@ -188,6 +189,114 @@ __global__ void __launch_bounds__(128)
   }
 }
 
+// Loss-only kernel sums between clouds: block (x, a, c) sums k(u_i, u_j)
+// over its rows i of row set a (NT*R rows from x * NT*R; rows >= n_r are
+// pads and left out) and every column j of column set (a, c) (nct tiles;
+// pad columns add exactly 0), FP32 within a tile, FP64 across tiles, then a
+// fixed-order block reduction into out[(c * gridDim.y + a) * gridDim.x + x].
+// Rows of set a: rows + a * rstride; columns: cols + a * cas + c * ccs (a
+// cloud against itself: cas = rstride, ccs = 0; clouds against other
+// clouds: cas = 0, ccs = their stride).  Per pair: 13 FP32-pipe operations
+// (two pairs per packed instruction) and one MUFU ex2 per bandwidth.
+template <int R, int NS>
+__global__ void __launch_bounds__(128)
+    k_mmd_sum(const float4* __restrict__ rows, int64_t rstride, int64_t n_r,
+              const float4* __restrict__ cols, int64_t cas, int64_t ccs, int nct, float4 rho,
+              double* __restrict__ out) {
+  constexpr int NT = 128;
+  __shared__ float4 sj[3 * kMT];
+  __shared__ double sw[NT / 32];
+  const int t = threadIdx.x;
+  const int64_t a = blockIdx.y, c = blockIdx.z;
+  const float4* rs = rows + a * rstride;
+  const float4* cs = cols + a * cas + c * ccs;
+  const int64_t i0 = (int64_t)blockIdx.x * (NT * R) + t;
+  float2 nu[R][6];
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      const float u = load_u(rs, i0 + r * NT, d);
+      nu[r][d] = make_float2(-u, -u);
+    }
+  const float rl[4] = {1.f, rho.y, rho.z, rho.w};
+  double s0[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) s0[r] = 0.0;
+  for (int tile = 0; tile < nct; ++tile) {
+    const float4* src = cs + (int64_t)tile * (3 * kMT);
+    __syncthreads();
+    for (int q = t; q < 3 * kMT; q += NT) sj[q] = src[q];
+    __syncthreads();
+    float2 a0[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) a0[r] = make_float2(0.f, 0.f);
+#pragma unroll 2
+    for (int jj = 0; jj < kMT; ++jj) {
+      const float4 P0 = sj[3 * jj], P1 = sj[3 * jj + 1], P2 = sj[3 * jj + 2];
+      const float2 cc[6] = {make_float2(P0.x, P0.y), make_float2(P0.z, P0.w),
+                            make_float2(P1.x, P1.y), make_float2(P1.z, P1.w),
+                            make_float2(P2.x, P2.y), make_float2(P2.z, P2.w)};
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        float2 dd = __fadd2_rn(cc[0], nu[r][0]);
+        float2 r2 = __fmul2_rn(dd, dd);
+#pragma unroll
+        for (int d = 1; d < 6; ++d) {
+          dd = __fadd2_rn(cc[d], nu[r][d]);
+          r2 = __ffma2_rn(dd, dd, r2);
+        }
+        float2 sk = make_float2(ex2_ftz(-r2.x), ex2_ftz(-r2.y));
+#pragma unroll
+        for (int l = 1; l < NS; ++l) {
+          const float2 e = __fmul2_rn(r2, make_float2(rl[l], rl[l]));
+          sk = __fadd2_rn(sk, make_float2(ex2_ftz(-e.x), ex2_ftz(-e.y)));
+        }
+        a0[r] = __fadd2_rn(a0[r], sk);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) s0[r] += (double)(a0[r].x + a0[r].y);
+  }
+  double acc = 0.0;
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (i0 + r * NT < n_r) acc += s0[r];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((t & 31) == 0) sw[t >> 5] = acc;
+  __syncthreads();
+  if (t == 0) {
+    double tot = 0.0;
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) tot += sw[w];
+    out[(c * gridDim.y + a) * gridDim.x + blockIdx.x] = tot;
+  }
+}
+
+// per-set sums of k_mmd_sum's block sums: res[q] = w * sum_x bs[q * nrb + x]
+__global__ void k_mmd_block_total(const double* __restrict__ bs, int64_t count, int nrb,
+                                  double w, double* __restrict__ res) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= count) return;
+  double s = 0.0;
+  for (int x = 0; x < nrb; ++x) s += bs[q * nrb + x];
+  res[q] = w * s;
+}
+
+// loss[t * sets + b] = kxx[b] + kyy[t] - 2/(n m) sum_x cross[(t sets + b) nrb + x]
+__global__ void k_mmd_cross_finish(const double* __restrict__ cross, int64_t sets,
+                                   int64_t targets, int nrb, double wxy,
+                                   const double* __restrict__ kxx,
+                                   const double* __restrict__ kyy, double* __restrict__ loss) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= sets * targets) return;
+  const int64_t b = q % sets, t = q / sets;
+  double s = 0.0;
+  for (int x = 0; x < nrb; ++x) s += cross[q * nrb + x];
+  loss[q] = kxx[b] + kyy[t] - wxy * s;
+}
+
 // loss_b = base + wrow sum_{i<n} sum_chunks (S0A + cB S0B), one block per set
 __global__ void __launch_bounds__(256)
     k_mmd_finish(const double* __restrict__ part, int S, int64_t npad_r, int64_t n,
@@ -274,6 +383,7 @@ struct nbody_mmd {
   cudaStream_t s = nullptr;
   int64_t n = 0, m = 0, max_sets = 0, npad = 0, mpad = 0;
   int ns = 1;
+  double sigma[4] = {0, 0, 0, 0};  // the caller's bandwidths, in its order
   float4 rho{1.f, 1.f, 1.f, 1.f};
   double c0 = 0.0;
   nb::Standardise st{};
@@ -349,6 +459,35 @@ cudaError_t launch_rows(const nbody_mmd* h, int64_t sets, const float4* rows,
   }
 }
 
+template <int NS>
+cudaError_t sum_ns(int R, dim3 grid, const float4* rows, int64_t rstride, int64_t n_r,
+                   const float4* cols, int64_t cas, int64_t ccs, int nct, float4 rho,
+                   double* out, cudaStream_t s) {
+  if (R == 2)
+    nb::k_mmd_sum<2, NS><<<grid, 128, 0, s>>>(rows, rstride, n_r, cols, cas, ccs, nct, rho, out);
+  else
+    nb::k_mmd_sum<1, NS><<<grid, 128, 0, s>>>(rows, rstride, n_r, cols, cas, ccs, nct, rho, out);
+  nb::count_launch();
+  return cudaGetLastError();
+}
+
+int rows_per_thread(int64_t npad_r) { return npad_r >= 256 ? 2 : 1; }
+
+// k_mmd_sum over `csets` column sets for every one of `rsets` row sets of
+// npad_r rows (n_r real); block sums to out
+cudaError_t launch_sum(const nbody_mmd* h, int64_t rsets, int64_t csets, const float4* rows,
+                       int64_t rstride, int64_t npad_r, int64_t n_r, const float4* cols,
+                       int64_t cas, int64_t ccs, int nct, double* out) {
+  const int R = rows_per_thread(npad_r);
+  dim3 grid((unsigned)(npad_r / (128 * R)), (unsigned)rsets, (unsigned)csets);
+  switch (h->ns) {
+    case 1: return sum_ns<1>(R, grid, rows, rstride, n_r, cols, cas, ccs, nct, h->rho, out, h->s);
+    case 2: return sum_ns<2>(R, grid, rows, rstride, n_r, cols, cas, ccs, nct, h->rho, out, h->s);
+    case 3: return sum_ns<3>(R, grid, rows, rstride, n_r, cols, cas, ccs, nct, h->rho, out, h->s);
+    default: return sum_ns<4>(R, grid, rows, rstride, n_r, cols, cas, ccs, nct, h->rho, out, h->s);
+  }
+}
+
 // column chunks so that a single set fills the GPU (4 blocks per SM)
 int chunks_for(const nbody_mmd* h, int64_t sets, int64_t npad_r, int ntiles) {
   const int R = npad_r >= 256 ? 2 : 1;
@@ -396,7 +535,68 @@ int device_view(const double* p, size_t count, double** tmp, const double** out,
   return NBODY_OK;
 }
 
+// The target (h->m points, device arrays): its standardisation (mean and
+// standard deviation, or the caller's scale), its staged points and its own
+// term Kyy = (1/m^2) sum k(y, y').  No allocation beyond the evaluator's
+// own buffers (the row-sum scratch grows once).  Synchronises.
+int set_target(nbody_mmd* h, const double* dx, const double* dv, const double* scale_or_null) {
+  const int64_t m = h->m;
+  nb::k_cloud_stats<<<1, 256, 0, h->s>>>(dx, dv, m, h->stats);
+  nb::count_launch();
+  MCK(cudaGetLastError());
+  double stt[12];
+  MCK(cudaMemcpyAsync(stt, h->stats, sizeof(stt), cudaMemcpyDeviceToHost, h->s));
+  MCK(cudaStreamSynchronize(h->s));
+  const double sc0 = std::sqrt(h->c0);
+  nb::Standardise st{};
+  for (int d = 0; d < 6; ++d) {
+    const double sd = scale_or_null ? scale_or_null[d] : stt[6 + d];
+    if (!(sd > 0.0) || !std::isfinite(sd)) return NBODY_EINVAL;
+    st.mu[d] = stt[d];
+    st.f[d] = sc0 / sd;
+  }
+  h->st = st;
+  int rc = stage(h, dx, dv, m, m, h->mpad, 1, h->ys);
+  if (rc) return rc;
+  const int nty = (int)(h->mpad / nb::kMPts);
+  const int Sy = chunks_for(h, 1, h->mpad, nty);
+  if ((rc = ensure_part(h, (int64_t)Sy * 8 * h->mpad))) return rc;
+  MCK(launch_rows(h, 1, h->ys, 0, h->mpad, h->ys, 0, nty, nullptr, 0, 1.0 / (double)m, 0.0,
+                  Sy, h->part));
+  nb::k_mmd_finish<<<1, 256, 0, h->s>>>(h->part, Sy, h->mpad, m, 1.0 / (double)m, 0.0,
+                                        nullptr, h->kyy);
+  nb::count_launch();
+  MCK(cudaGetLastError());
+  MCK(cudaStreamSynchronize(h->s));
+  return NBODY_OK;
+}
+
 }  // namespace
+
+namespace nb {
+
+// A new target for an evaluator of clouds of n points when the target keeps
+// its size m and the bandwidths are the same: restaged in place (no
+// allocation, so no device-wide synchronisation); NBODY_ESTATE otherwise.
+int mmd_retarget(nbody_mmd* h, int64_t n, int64_t m, const double* tx, const double* tv,
+                 const double* scale_or_null, int n_sigma, const double* sigma) {
+  if (!h || h->n != n || h->m != m || h->ns != n_sigma || !tx || !tv || !sigma)
+    return NBODY_ESTATE;
+  for (int l = 0; l < n_sigma; ++l)
+    if (h->sigma[l] != sigma[l]) return NBODY_ESTATE;
+  cudaPointerAttributes ax{}, av{};
+  if (cudaPointerGetAttributes(&ax, tx) != cudaSuccess || ax.type != cudaMemoryTypeDevice ||
+      cudaPointerGetAttributes(&av, tv) != cudaSuccess || av.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    return NBODY_ESTATE;
+  }
+  if (scale_or_null)
+    for (int d = 0; d < 6; ++d)
+      if (!(scale_or_null[d] > 0.0) || !std::isfinite(scale_or_null[d])) return NBODY_EINVAL;
+  return set_target(h, tx, tv, scale_or_null);
+}
+
+}  // namespace nb
 
 extern "C" {
 
@@ -434,6 +634,7 @@ int nbody_mmd_create(nbody_mmd** out, int64_t n, int64_t max_sets, int64_t m,
   h->npad = nb::pad_points(n);
   h->mpad = nb::pad_points(m);
   h->ns = n_sigma;
+  for (int l = 0; l < n_sigma; ++l) h->sigma[l] = sigma[l];
   // sigma_0 is the smallest bandwidth (first), the others follow in the
   // caller's order; rho_l = sigma_0^2 / sigma_l^2 <= 1
   {
@@ -467,45 +668,15 @@ int nbody_mmd_create(nbody_mmd** out, int64_t n, int64_t max_sets, int64_t m,
     delete h;
     return rc;
   }
-  auto fail = [&](int code) {
-    cudaStreamSynchronize(h->s);
-    if (tmpx) cudaFree(tmpx);
-    if (tmpv) cudaFree(tmpv);
-    free_mmd(h);
-    delete h;
-    return code;
-  };
-  // standardisation: the target's mean and standard deviation (or scale)
-  nb::k_cloud_stats<<<1, 256, 0, h->s>>>(dx, dv, m, h->stats);
-  nb::count_launch();
-  if (cudaGetLastError() != cudaSuccess) return fail(NBODY_ECUDA);
-  double stt[12];
-  if (cudaMemcpyAsync(stt, h->stats, sizeof(stt), cudaMemcpyDeviceToHost, h->s) != cudaSuccess ||
-      cudaStreamSynchronize(h->s) != cudaSuccess)
-    return fail(NBODY_ECUDA);
-  const double sc0 = std::sqrt(h->c0);
-  for (int d = 0; d < 6; ++d) {
-    const double sd = scale_or_null ? scale_or_null[d] : stt[6 + d];
-    if (!(sd > 0.0) || !std::isfinite(sd)) return fail(NBODY_EINVAL);
-    h->st.mu[d] = stt[d];
-    h->st.f[d] = sc0 / sd;
-  }
-  // the target's own term Kyy = (1/m^2) sum k(y, y')
-  if ((rc = stage(h, dx, dv, m, m, h->mpad, 1, h->ys))) return fail(rc);
-  const int nty = (int)(h->mpad / nb::kMPts);
-  const int Sy = chunks_for(h, 1, h->mpad, nty);
-  if ((rc = ensure_part(h, (int64_t)Sy * 8 * h->mpad))) return fail(rc);
-  if (launch_rows(h, 1, h->ys, 0, h->mpad, h->ys, 0, nty, nullptr, 0, 1.0 / (double)m, 0.0,
-                  Sy, h->part) != cudaSuccess)
-    return fail(NBODY_ECUDA);
-  nb::k_mmd_finish<<<1, 256, 0, h->s>>>(h->part, Sy, h->mpad, m, 1.0 / (double)m, 0.0,
-                                        nullptr, h->kyy);
-  nb::count_launch();
-  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->s) != cudaSuccess)
-    return fail(NBODY_ECUDA);
+  rc = set_target(h, dx, dv, scale_or_null);
+  if (rc) cudaStreamSynchronize(h->s);
   if (tmpx) cudaFree(tmpx);
   if (tmpv) cudaFree(tmpv);
-  tmpx = tmpv = nullptr;
+  if (rc) {
+    free_mmd(h);
+    delete h;
+    return rc;
+  }
   *out = h;
   return NBODY_OK;
 }
@@ -605,6 +776,93 @@ int nbody_mmd_eval(nbody_mmd* h, const double* x, const double* v, double* loss,
   if (rc) return rc;
   if (!std::isfinite(L)) return NBODY_ENAN;
   *loss = L;
+  return NBODY_OK;
+}
+
+int nbody_mmd_eval_cross(nbody_mmd* h, int64_t sets, const double* x, const double* v,
+                         int64_t targets, int64_t m2, const double* ty, const double* tv,
+                         double* losses) {
+  constexpr int64_t kMaxGridYZ = 65535;
+  if (!h || !x || !v || !ty || !tv || !losses || sets < 1 || targets < 1 || m2 < 1 ||
+      sets > kMaxGridYZ || targets > kMaxGridYZ)
+    return NBODY_EINVAL;
+  const int64_t n = h->n, npad = h->npad, m2pad = nb::pad_points(m2);
+  const int64_t xstr = 3 * (npad / 2), tstr = 3 * (m2pad / 2);
+  const int nrx = (int)(npad / (128 * rows_per_thread(npad)));
+  const int nrt = (int)(m2pad / (128 * rows_per_thread(m2pad)));
+  // targets per cross launch: the block sums of one launch stay below 2^25
+  // doubles (256 MB)
+  int64_t tc = std::max<int64_t>(1, ((int64_t)1 << 25) / (sets * nrx));
+  tc = std::min(std::min(tc, targets), kMaxGridYZ);
+  const int64_t nbs = std::max(std::max(sets * nrx, targets * nrt), tc * sets * nrx);
+  double *tmpx = nullptr, *tmpv = nullptr, *tmpy = nullptr, *tmpw = nullptr;
+  const double *dx = nullptr, *dv = nullptr, *dy = nullptr, *dw = nullptr;
+  float4 *xs = nullptr, *ts = nullptr;
+  double *bs = nullptr, *kxx = nullptr, *kyy = nullptr, *dl = nullptr;
+  int rc = device_view(x, (size_t)(3 * sets * n), &tmpx, &dx, h->s);
+  if (!rc) rc = device_view(v, (size_t)(3 * sets * n), &tmpv, &dv, h->s);
+  if (!rc) rc = device_view(ty, (size_t)(3 * targets * m2), &tmpy, &dy, h->s);
+  if (!rc) rc = device_view(tv, (size_t)(3 * targets * m2), &tmpw, &dw, h->s);
+  if (!rc) rc = malloc_dev(&xs, (size_t)(sets * xstr));
+  if (!rc) rc = malloc_dev(&ts, (size_t)(targets * tstr));
+  if (!rc) rc = malloc_dev(&bs, (size_t)nbs);
+  if (!rc) rc = malloc_dev(&kxx, (size_t)sets);
+  if (!rc) rc = malloc_dev(&kyy, (size_t)targets);
+  if (!rc) rc = malloc_dev(&dl, (size_t)(sets * targets));
+  // the clouds and the targets in the evaluator's standardisation, staged once
+  if (!rc) rc = stage(h, dx, dv, sets * n, n, npad, sets, xs);
+  if (!rc) rc = stage(h, dy, dw, targets * m2, m2, m2pad, targets, ts);
+  const unsigned tpb = 256;
+  // own terms: (1/n^2) sum k(x, x') per cloud, (1/m^2) sum k(y, y') per target
+  if (!rc && launch_sum(h, sets, 1, xs, xstr, npad, n, xs, xstr, 0, (int)(npad / nb::kMPts),
+                        bs) != cudaSuccess)
+    rc = NBODY_ECUDA;
+  if (!rc) {
+    nb::k_mmd_block_total<<<(unsigned)((sets + tpb - 1) / tpb), tpb, 0, h->s>>>(
+        bs, sets, nrx, 1.0 / ((double)n * (double)n), kxx);
+    nb::count_launch();
+    if (cudaGetLastError() != cudaSuccess) rc = NBODY_ECUDA;
+  }
+  if (!rc && launch_sum(h, targets, 1, ts, tstr, m2pad, m2, ts, tstr, 0,
+                        (int)(m2pad / nb::kMPts), bs) != cudaSuccess)
+    rc = NBODY_ECUDA;
+  if (!rc) {
+    nb::k_mmd_block_total<<<(unsigned)((targets + tpb - 1) / tpb), tpb, 0, h->s>>>(
+        bs, targets, nrt, 1.0 / ((double)m2 * (double)m2), kyy);
+    nb::count_launch();
+    if (cudaGetLastError() != cudaSuccess) rc = NBODY_ECUDA;
+  }
+  // cross terms, tc targets per launch
+  for (int64_t t0 = 0; !rc && t0 < targets; t0 += tc) {
+    const int64_t cnt = std::min(tc, targets - t0);
+    if (launch_sum(h, sets, cnt, xs, xstr, npad, n, ts + t0 * tstr, 0, tstr,
+                   (int)(m2pad / nb::kMPts), bs) != cudaSuccess) {
+      rc = NBODY_ECUDA;
+      break;
+    }
+    const int64_t q = cnt * sets;
+    nb::k_mmd_cross_finish<<<(unsigned)((q + tpb - 1) / tpb), tpb, 0, h->s>>>(
+        bs, sets, cnt, nrx, 2.0 / ((double)n * (double)m2), kxx, kyy + t0, dl + t0 * sets);
+    nb::count_launch();
+    if (cudaGetLastError() != cudaSuccess) rc = NBODY_ECUDA;
+  }
+  std::vector<double> hl;
+  if (!rc) {
+    hl.resize((size_t)(sets * targets));
+    if (cudaMemcpyAsync(hl.data(), dl, hl.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                        h->s) != cudaSuccess)
+      rc = NBODY_ECUDA;
+  }
+  if (cudaStreamSynchronize(h->s) != cudaSuccess && !rc) rc = NBODY_ECUDA;
+  for (void* p : {(void*)tmpx, (void*)tmpv, (void*)tmpy, (void*)tmpw, (void*)xs, (void*)ts,
+                  (void*)bs, (void*)kxx, (void*)kyy, (void*)dl})
+    if (p) cudaFree(p);
+  if (rc) return rc;
+  if (cudaMemcpy(losses, hl.data(), hl.size() * sizeof(double), cudaMemcpyDefault) !=
+      cudaSuccess)
+    return NBODY_ECUDA;
+  for (double L : hl)
+    if (!std::isfinite(L)) return NBODY_ENAN;
   return NBODY_OK;
 }
 

@@ -35,7 +35,14 @@
 
 namespace nb {
 static std::atomic<long long> g_launches{0};
-void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+// this thread's launches: a graph capture counts its nodes from it, so that
+// other threads' launches in the meantime are not taken for recorded ones
+static thread_local long long t_launches = 0;
+void count_launch(int k) {
+  g_launches.fetch_add(k, std::memory_order_relaxed);
+  t_launches += k;
+}
+long long thread_launches() { return t_launches; }
 }  // namespace nb
 
 using nb::DevParams;
@@ -259,9 +266,9 @@ int run_graph(nbody_ctx* c, const uint64_t (&key)[12], F record) {
     cudaGraph_t graph = nullptr;
     CK(cudaStreamSynchronize(c->gs));
     CK(cudaStreamBeginCapture(c->gs, cudaStreamCaptureModeThreadLocal));
-    const long long before = nb::g_launches.load();
+    const long long before = nb::thread_launches();
     const int rc = record(c->gs);
-    const int nodes = (int)(nb::g_launches.load() - before);
+    const int nodes = (int)(nb::thread_launches() - before);
     nb::count_launch(-nodes);  // recorded, not launched
     const cudaError_t e = cudaStreamEndCapture(c->gs, &graph);
     if (rc || e != cudaSuccess) {
@@ -943,7 +950,8 @@ int nbody_vjp(nbody_ctx* c, const double* xbar, const double* vbar,
   c->pot_bar[5] = h[7];
   c->have_grad = true;
   int st = 0;
-  CK(cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
   if (st & nb::kStatusNaN) return NBODY_ENAN;
   return NBODY_OK;
 }
@@ -984,7 +992,8 @@ int nbody_momentum(nbody_ctx* c, double out[3]) {
   int rc = nbody_energy(c, e);
   if (rc) return rc;
   double h[8];
-  CK(cudaMemcpy(h, c->red, 6 * sizeof(double), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpyAsync(h, c->red, 6 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
   out[0] = h[3];
   out[1] = h[4];
   out[2] = h[5];
@@ -995,8 +1004,8 @@ int nbody_get_status(nbody_ctx* c) {
   if (!c) return NBODY_EINVAL;
   if (c->batch) return nb::batch_status(c->batch);
   int st = 0;
+  CK(cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
-  CK(cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost));
   if (st & nb::kStatusNaN) return NBODY_ENAN;
   if (st & nb::kStatusTimeout) return NBODY_ETIMEOUT;
   return NBODY_OK;

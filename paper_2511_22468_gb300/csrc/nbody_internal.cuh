@@ -56,6 +56,14 @@ void set_bulge(DevParams& d, double G, double M, double alpha, double rc);
 
 // ---- launch accounting ----
 void count_launch(int k = 1);
+long long thread_launches();  // launches counted by the calling thread
+}  // namespace nb
+struct nbody_mmd;
+namespace nb {
+// New target of the same size and bandwidths for an MMD evaluator, in place
+// (device arrays); NBODY_ESTATE when it does not fit (mmd.cu).
+int mmd_retarget(nbody_mmd* h, int64_t n, int64_t m, const double* tx, const double* tv,
+                 const double* scale_or_null, int n_sigma, const double* sigma);
 
 // ---- pair kernels (pair_force.cu, pair_vjp.cu) ----
 enum PairVariant : int { kTile = 0, kWarp = 1 };

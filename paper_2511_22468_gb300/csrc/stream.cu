@@ -694,6 +694,12 @@ int nbody_stream_set_target_cloud(nbody_stream* s, int64_t m, const double* tx,
                                   const double* tv, const double* scale_or_null,
                                   int n_sigma, const double* sigma) {
   if (!s || !tx || !tv || !sigma) return NBODY_EINVAL;
+  // same size and bandwidths: the evaluator takes the new target in place
+  if (s->mmd && nb::mmd_retarget(s->mmd, s->n, m, tx, tv, scale_or_null, n_sigma, sigma) ==
+                    NBODY_OK) {
+    s->have_forward = false;
+    return NBODY_OK;
+  }
   nbody_mmd* h = nullptr;
   const int rc = nbody_mmd_create(&h, s->n, 1, m, tx, tv, scale_or_null, n_sigma, sigma, s->s);
   if (rc) return rc;

@@ -10,14 +10,26 @@ paper's first inference method, Sec. 2.2.1 and Fig. 2).
     and scored by MMD^2 against the observation (one batched MMD launch);
   * refinement: gradient descent from the best grid point with the
     pipeline's discrete-adjoint gradient of the same MMD^2 (the paper runs
-    10 such steps); the estimate is the minimum-loss iterate.
+    10 such steps); the estimate is the minimum-loss iterate;
+  * bootstrap (--bootstrap R): the observation is redrawn R times from its
+    observational errors (Gaussian per coordinate: --sigma-x kpc and
+    --sigma-v km/s, or by default 5 % of the observed cloud's spread in
+    that coordinate) and the grid stage is repeated for every
+    realisation.  The grid's simulated clouds do not depend on the
+    observation, so they are simulated once and kept in device memory
+    (48 B per particle, 480 MB for 10^4 clouds of 1000); one call then
+    scores every cloud against every realisation (nbody_mmd_eval_cross),
+    and the spread of the per-realisation best grid points is the
+    bootstrap distribution.  --bootstrap-refine K adds the gradient
+    refinement for the first K realisations.
 
 The paper's workload is 10^4 grid points of 1000 particles and 1000 steps;
 the default here keeps the stream workload's step (0.5 Myr), so 1000 steps
 cover t_end = 500 Myr.
 
     python -m paper_2511_22468_gb300.gridsearch [--n 1000] [--steps 1000]
-        [--per-dim 10] [--batch 1024] [--refine 10]
+        [--per-dim 10] [--batch 1024] [--refine 10] [--bootstrap R]
+        [--bootstrap-refine K]
 """
 from __future__ import annotations
 
@@ -31,7 +43,7 @@ import torch
 
 from . import nbody as nb
 from .configs import C1
-from .inputs import plummer_unit
+from .inputs import perturbed_clouds, plummer_unit
 from .stream import StreamModel
 
 
@@ -46,7 +58,7 @@ class GridSearch:
     """MMD^2 of many parameter vectors against one observed cloud."""
 
     def __init__(self, cfg, xhat, vhat, tx, tv, sigmas=(0.5, 1.0, 2.0), batch=1024,
-                 device="cuda:0", tuning=None):
+                 device="cuda:0", tuning=None, keep_clouds=0):
         self.dev = torch.device(device)
         self.cfg = cfg
         self.model = StreamModel(cfg, xhat, vhat, device=device)
@@ -67,6 +79,11 @@ class GridSearch:
         self.com = np.zeros((B, 6))
         self.L = torch.empty(B, dtype=torch.float64, device=self.dev)
         self.times = {"initial_states_s": 0.0, "simulate_s": 0.0, "mmd_s": 0.0}
+        # every simulated cloud, kept for scoring against other observations
+        self.CX = self.CV = None
+        if keep_clouds:
+            self.CX = torch.empty((3, keep_clouds * n), dtype=torch.float64, device=self.dev)
+            self.CV = torch.empty_like(self.CX)
 
     def _params(self, th, com):
         c, p = self.cfg, self.cfg.pot
@@ -103,11 +120,27 @@ class GridSearch:
             t2 = time.perf_counter()
             nb.nbody_mmd_eval_batch(self.mmd, B, self.XO, self.VO, self.L)
             out[c0:c0 + len(chunk)] = self.L.cpu().numpy()[:len(chunk)]
+            if self.CX is not None:
+                k = len(chunk) * self.n
+                self.CX[:, c0 * self.n:c0 * self.n + k] = self.XO[:, :k]
+                self.CV[:, c0 * self.n:c0 * self.n + k] = self.VO[:, :k]
             t3 = time.perf_counter()
             self.times["initial_states_s"] += t1 - t0
             self.times["simulate_s"] += t2 - t1
             self.times["mmd_s"] += t3 - t2
         return out
+
+    def cross_losses(self, count, tx, tv):
+        """MMD^2 of the first `count` kept clouds against each of the target
+        clouds tx, tv (R, m, 3): an (R, count) array."""
+        R, m = tx.shape[0], tx.shape[1]
+        TY = torch.as_tensor(np.ascontiguousarray(tx.transpose(2, 0, 1).reshape(3, R * m)),
+                             device=self.dev)
+        TV = torch.as_tensor(np.ascontiguousarray(tv.transpose(2, 0, 1).reshape(3, R * m)),
+                             device=self.dev)
+        out = torch.empty(R * count, dtype=torch.float64, device=self.dev)
+        nb.nbody_mmd_eval_cross(self.mmd, count, self.CX, self.CV, R, m, TY, TV, out)
+        return out.cpu().numpy().reshape(R, count)
 
     def close(self):
         if self.h is not None:
@@ -126,9 +159,13 @@ def refine(model, theta0, centre, width, iters=10, lr=0.05):
     return descend(model, theta0, centre, width, lr=lr, max_iters=iters)
 
 
+KMS = 1.0227121650537077e-3   # 1 km/s in kpc/Myr
+
+
 def run(n=1000, steps=1000, t_end=500.0, per_dim=10, batch=1024, refine_iters=10,
         sigmas=(0.5, 1.0, 2.0), f_obs=(1.1, 0.9, 1.15, 0.85), width=0.3, seed=1,
-        device="cuda:0", tuning=None):
+        device="cuda:0", tuning=None, bootstrap=0, bootstrap_refine=0, sigma_frac=0.05,
+        sigma_x=None, sigma_v_kms=None):
     cfg = dataclasses.replace(C1, n=n, n_steps=steps, t_acc=float(t_end))
     centre = np.array(cfg.theta_true, float)
     theta_obs = centre * np.array(f_obs)
@@ -136,9 +173,9 @@ def run(n=1000, steps=1000, t_end=500.0, per_dim=10, batch=1024, refine_iters=10
     obs = StreamModel(cfg, xh, vh, device=device)
     tx, tv = obs.final_state(list(theta_obs))
     obs.close()
-    gs = GridSearch(cfg, xh, vh, tx, tv, sigmas=sigmas, batch=batch, device=device,
-                    tuning=tuning)
     grid = regular_grid(centre, width, per_dim)
+    gs = GridSearch(cfg, xh, vh, tx, tv, sigmas=sigmas, batch=batch, device=device,
+                    tuning=tuning, keep_clouds=len(grid) if bootstrap else 0)
     torch.cuda.synchronize(device)
     t0 = time.perf_counter()
     L = gs.losses(grid)
@@ -155,6 +192,38 @@ def run(n=1000, steps=1000, t_end=500.0, per_dim=10, batch=1024, refine_iters=10
                     "best_theta": best.tolist(),
                     "best_loss": float(L[k]),
                     "best_err": float(np.max(np.abs(best / theta_obs - 1)))}}
+    reals = None
+    if bootstrap:
+        # the observation redrawn from its errors, every kept cloud scored
+        # against every realisation in one call
+        ox = tx.cpu().numpy().T if hasattr(tx, "cpu") else np.asarray(tx).T
+        ov = tv.cpu().numpy().T if hasattr(tv, "cpu") else np.asarray(tv).T
+        # errors: given in kpc and km/s, else a fraction of the observed
+        # cloud's spread in each coordinate
+        ex = sigma_x if sigma_x is not None else sigma_frac * ox.std(axis=0)
+        ev = sigma_v_kms * KMS if sigma_v_kms is not None else sigma_frac * ov.std(axis=0)
+        rx, rv = perturbed_clouds(ox, ov, ex, ev, bootstrap, seed + 1000)
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        LB = gs.cross_losses(len(grid), rx, rv)
+        t_b = time.perf_counter() - t0
+        kb = np.argmin(LB, axis=1)
+        bt = grid[kb]
+        rel = bt / theta_obs[None, :] - 1.0
+        pairs = float(len(grid)) * bootstrap * n * n
+        res["bootstrap"] = {
+            "realisations": bootstrap,
+            "sigma_x_kpc": np.broadcast_to(ex, (3,)).tolist(),
+            "sigma_v_kms": (np.broadcast_to(ev, (3,)) / KMS).tolist(),
+            "time_s": t_b, "cloud_pairs_per_s": len(grid) * bootstrap / t_b,
+            "kernel_pairs_per_s": pairs / t_b,
+            "best_theta_mean": bt.mean(axis=0).tolist(),
+            "best_theta_std": bt.std(axis=0).tolist(),
+            "best_rel_err_mean": rel.mean(axis=0).tolist(),
+            "distinct_best_points": int(len(np.unique(kb))),
+            "fraction_at_noise_free_best": float(np.mean(kb == k))}
+        reals = (rx, rv, bt)
+    obs_scale = nb.nbody_mmd_target_stats(gs.mmd)[1]   # the observation's units
     gs.close()
     if refine_iters > 0:
         model = StreamModel(cfg, xh, vh, device=device)
@@ -168,6 +237,27 @@ def run(n=1000, steps=1000, t_end=500.0, per_dim=10, batch=1024, refine_iters=10
                                                           theta_obs - 1))),
                          "loss_trace": [r["loss"] for r in tr]}
         model.close()
+    if reals is not None and bootstrap_refine > 0:
+        # gradient refinement of the first realisations, one after another
+        # (the pipeline takes each new target in place)
+        rx, rv, bt = reals
+        K = min(bootstrap_refine, bootstrap)
+        model = StreamModel(cfg, xh, vh, device=device)
+        out = []
+        t0 = time.perf_counter()
+        for r in range(K):
+            model.set_target_cloud(np.ascontiguousarray(rx[r].T), np.ascontiguousarray(rv[r].T),
+                                   sigmas, scale=obs_scale)
+            tr = refine(model, bt[r], centre, width, iters=refine_iters)
+            out.append(tr[int(np.argmin([q["loss"] for q in tr]))]["theta"])
+        t_r = time.perf_counter() - t0
+        model.close()
+        est = np.array(out)
+        res["bootstrap"]["refine"] = {
+            "realisations": K, "iters": refine_iters, "time_s": t_r,
+            "s_per_realisation": t_r / K, "theta_mean": est.mean(axis=0).tolist(),
+            "theta_std": est.std(axis=0).tolist(),
+            "rel_err_mean": (est / theta_obs[None, :] - 1.0).mean(axis=0).tolist()}
     return res
 
 
@@ -179,11 +269,20 @@ def main():
     ap.add_argument("--per-dim", type=int, default=10)
     ap.add_argument("--batch", type=int, default=1024)
     ap.add_argument("--refine", type=int, default=10)
+    ap.add_argument("--bootstrap", type=int, default=0)
+    ap.add_argument("--bootstrap-refine", type=int, default=0)
+    ap.add_argument("--sigma-frac", type=float, default=0.05,
+                    help="errors as a fraction of the observed spread per coordinate")
+    ap.add_argument("--sigma-x", type=float, default=None, help="position error, kpc")
+    ap.add_argument("--sigma-v", type=float, default=None, help="velocity error, km/s")
     a = ap.parse_args()
     from . import build
     build.build()
     print(json.dumps(run(n=a.n, steps=a.steps, t_end=a.t_end, per_dim=a.per_dim,
-                         batch=a.batch, refine_iters=a.refine)))
+                         batch=a.batch, refine_iters=a.refine, bootstrap=a.bootstrap,
+                         bootstrap_refine=a.bootstrap_refine, sigma_frac=a.sigma_frac,
+                         sigma_x=a.sigma_x,
+                         sigma_v_kms=a.sigma_v)))
 
 
 if __name__ == "__main__":

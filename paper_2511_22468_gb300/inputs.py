@@ -85,3 +85,20 @@ def uniform_factors(count: int, width: float, dims: int, seed: int) -> np.ndarra
     """Multiplicative parameter factors drawn uniformly in [1-width, 1+width]."""
     rng = np.random.default_rng(seed)
     return rng.uniform(1.0 - width, 1.0 + width, (count, dims))
+
+
+def perturbed_clouds(x: np.ndarray, v: np.ndarray, sigma_x: float, sigma_v: float,
+                     count: int, seed: int):
+    """`count` realisations of an observed cloud (x, v: (n, 3) each) with
+    every coordinate drawn from a Gaussian around its observed value:
+    standard deviation sigma_x for positions, sigma_v for velocities (the
+    bootstrap of the paper's first inference method, Sec. 2.2.1, which
+    resamples the observation by its observational errors); sigma_x and
+    sigma_v are scalars or per-coordinate (3,) arrays.  Returns (count, n, 3)
+    positions and velocities."""
+    rng = np.random.default_rng(seed)
+    x = np.asarray(x, float)
+    v = np.asarray(v, float)
+    ex = rng.normal(size=(count,) + x.shape) * sigma_x
+    ev = rng.normal(size=(count,) + v.shape) * sigma_v
+    return x[None] + ex, v[None] + ev

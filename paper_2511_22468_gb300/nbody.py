@@ -50,7 +50,8 @@ EXPORTED = ("nbody_create", "nbody_destroy", "nbody_set_params",
             "nbody_mlp_destroy", "nbody_mlp_invert", "nbody_set_pair_shape",
             "nbody_set_pair_finish", "nbody_get_pair_shape", "nbody_peaks", "nbody_autotune_pair",
             "nbody_potential_grad", "nbody_mmd_create", "nbody_mmd_eval",
-            "nbody_mmd_eval_batch", "nbody_mmd_target_stats", "nbody_mmd_destroy",
+            "nbody_mmd_eval_batch", "nbody_mmd_eval_cross", "nbody_mmd_target_stats",
+            "nbody_mmd_destroy",
             "nbody_stream_set_target_cloud", "nbody_stream_initial_states",
             "nbody_ext_accel", "nbody_stream_autotune", "nbody_orbitfit_create", "nbody_orbitfit_eval",
             "nbody_orbitfit_lm", "nbody_orbitfit_fisher", "nbody_orbitfit_arc",
@@ -197,6 +198,7 @@ def lib():
                                        dp, vp]
         L.nbody_mmd_eval.argtypes = [vp, vp, vp, dp, vp, vp]
         L.nbody_mmd_eval_batch.argtypes = [vp, i64, vp, vp, vp]
+        L.nbody_mmd_eval_cross.argtypes = [vp, i64, vp, vp, i64, i64, vp, vp, vp]
         L.nbody_mmd_target_stats.argtypes = [vp, dp, dp]
         L.nbody_mmd_destroy.argtypes = [vp]
         L.nbody_mmd_destroy.restype = None
@@ -336,6 +338,13 @@ def nbody_mmd_eval(h, x, v, xbar=None, vbar=None):
 def nbody_mmd_eval_batch(h, sets, x, v, losses):
     _check(lib().nbody_mmd_eval_batch(h, sets, _ptr(x), _ptr(v), _ptr(losses)),
            "nbody_mmd_eval_batch")
+
+
+def nbody_mmd_eval_cross(h, sets, x, v, targets, m2, ty, tv, losses):
+    """MMD^2 of `sets` clouds against each of `targets` clouds of m2 points;
+    losses[t * sets + b]."""
+    _check(lib().nbody_mmd_eval_cross(h, sets, _ptr(x), _ptr(v), targets, m2, _ptr(ty),
+                                      _ptr(tv), _ptr(losses)), "nbody_mmd_eval_cross")
 
 
 def nbody_mmd_target_stats(h):

@@ -37,7 +37,7 @@ def stream_cfg(cfg, n=None, n_steps=None, checkpoint_every=None) -> nb.nbody_str
 
 class StreamModel:
     def __init__(self, cfg, xhat, vhat, n_steps=None, checkpoint_every=None,
-                 device="cuda:0"):
+                 device="cuda:0", stream=None):
         xhat = np.asarray(xhat, np.float64)
         vhat = np.asarray(vhat, np.float64)
         self.n = xhat.shape[0]
@@ -46,7 +46,9 @@ class StreamModel:
         self.device = torch.device(device)
         xh = torch.tensor(xhat.T.copy(), device=self.device)
         vh = torch.tensor(vhat.T.copy(), device=self.device)
-        self.h = nb.nbody_stream_create(self.cfg, xh, vh)
+        if stream is not None:   # the copies above run on the caller's stream
+            torch.cuda.current_stream(self.device).synchronize()
+        self.h = nb.nbody_stream_create(self.cfg, xh, vh, stream)
         self.nb = (self.cfg.nb1, self.cfg.nb2)
 
     def close(self):

@@ -74,3 +74,37 @@ def test_grid_losses_match_oracle_and_rank_the_truth_first():
     ref = np.array([orc.mmd_loss(th, Y, sig) for th in grid])
     assert np.all(np.abs(L - ref) <= 1e-5 * len(sig) + 1e-3 * np.abs(ref)), (L, ref)
     assert int(np.argmin(L)) == 5 and L[5] < 1e-6
+
+
+def test_bootstrap_cross_losses_match_oracle():
+    """The kept grid clouds scored against perturbed realisations of the
+    observation (in the observation's standardisation) equal the oracle's
+    MMD^2 of the oracle's clouds; the noise-free realisation reproduces the
+    grid losses."""
+    from paper_2511_22468_gb300.gridsearch import GridSearch, regular_grid
+    from paper_2511_22468_gb300.inputs import perturbed_clouds
+    cfg = _cfg()
+    xh, vh = plummer_unit(cfg.n, 4)
+    orc = ostream.StreamModel(cfg, xh, vh)
+    centre = np.array(cfg.theta_true, float)
+    grid = regular_grid(centre, 0.3, 2)
+    xt, vt = orc.final_state(grid[5])
+    Y = om.cloud(xt, vt)
+    mu, s = om.target_stats(Y)
+    sig = [0.5, 1.0, 2.0]
+    rx, rv = perturbed_clouds(xt, vt, 0.05, 1e-3, 3, seed=11)
+    rx = np.concatenate([xt[None], rx])                    # realisation 0: no noise
+    rv = np.concatenate([vt[None], rv])
+    gs = GridSearch(cfg, xh, vh, xt.T.copy(), vt.T.copy(), sigmas=sig, batch=6,
+                    keep_clouds=len(grid))
+    L = gs.losses(grid)
+    LB = gs.cross_losses(len(grid), rx, rv)
+    gs.close()
+    assert LB.shape == (4, len(grid))
+    assert np.all(np.abs(LB[0] - L) <= 1e-6 * len(sig)), (LB[0], L)
+    clouds = [om.cloud(*orc.final_state(th)) for th in grid]
+    for r in range(4):
+        Yr = om.cloud(rx[r], rv[r])
+        ref = np.array([om.mmd2(c, Yr, sig, mu, s) for c in clouds])
+        assert np.all(np.abs(LB[r] - ref) <= 1e-5 * len(sig) + 1e-3 * np.abs(ref)), (r, LB[r], ref)
+

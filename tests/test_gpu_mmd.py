@@ -124,3 +124,49 @@ def test_mmd_errors():
     with pytest.raises(nb.NBodyError) as e:
         nb.nbody_mmd_create(10, 1, one, soa(vt[:1]), [1.0])
     assert e.value.code == nb.NBODY_EINVAL
+
+
+@pytest.mark.parametrize("n,m2,sets,targets,sig", [(1000, 1000, 6, 5, [0.5, 1.0, 2.0]),
+                                                   (700, 513, 3, 4, [1.0]),
+                                                   (5, 9, 2, 3, [0.3, 0.6, 1.2, 2.4])])
+def test_cross_targets_match_oracle(n, m2, sets, targets, sig):
+    """Many clouds against many perturbed realisations of the observation,
+    in the evaluator's units (its own target's standardisation): each loss
+    against the oracle's MMD^2 with that standardisation."""
+    from paper_2511_22468_gb300.inputs import perturbed_clouds
+    xt, vt = stream_like(m2, 6)
+    Y = om.cloud(xt, vt)
+    mu, s = om.target_stats(Y)
+    rx, rv = perturbed_clouds(xt, vt, 0.1, 2e-3, targets, seed=7)
+    clouds = [stream_like(n, 20 + b, shift=0.05 * b) for b in range(sets)]
+    X = torch.cat([soa(c[0]) for c in clouds], dim=1).contiguous()
+    V = torch.cat([soa(c[1]) for c in clouds], dim=1).contiguous()
+    TY = torch.cat([soa(rx[t]) for t in range(targets)], dim=1).contiguous()
+    TV = torch.cat([soa(rv[t]) for t in range(targets)], dim=1).contiguous()
+    h = nb.nbody_mmd_create(n, sets, soa(xt), soa(vt), sig)
+    try:
+        out = torch.empty(targets * sets, dtype=torch.float64, device=DEV)
+        nb.nbody_mmd_eval_cross(h, sets, X, V, targets, m2, TY, TV, out)
+        got = out.cpu().numpy().reshape(targets, sets)
+        for t in range(targets):
+            Yt = om.cloud(rx[t], rv[t])
+            for b, (xs, vs) in enumerate(clouds):
+                ref = om.mmd2(om.cloud(xs, vs), Yt, sig, mu, s)
+                assert abs(got[t, b] - ref) <= 1e-5 * len(sig), (t, b)
+        # against the evaluator's own target it is the batched evaluation
+        # (same terms, another summation order)
+        one = torch.empty(sets, dtype=torch.float64, device=DEV)
+        nb.nbody_mmd_eval_cross(h, sets, X, V, 1, m2, soa(xt), soa(vt), one)
+        ref1 = torch.empty(sets, dtype=torch.float64, device=DEV)
+        nb.nbody_mmd_eval_batch(h, sets, X, V, ref1)
+        assert torch.allclose(one, ref1, rtol=0, atol=1e-6 * len(sig))
+        # host arrays give the same bits; repeated calls too
+        host = np.empty(targets * sets)
+        nb.nbody_mmd_eval_cross(h, sets, X.cpu().numpy(), V.cpu().numpy(), targets, m2,
+                                TY.cpu().numpy(), TV.cpu().numpy(), host)
+        assert np.array_equal(host, out.cpu().numpy())
+        with pytest.raises(nb.NBodyError) as e:
+            nb.nbody_mmd_eval_cross(h, 0, X, V, targets, m2, TY, TV, out)
+        assert e.value.code == nb.NBODY_EINVAL
+    finally:
+        nb.nbody_mmd_destroy(h)

@@ -120,6 +120,16 @@ def test_stream_mmd_loss_and_gradient_match_oracle():
     xg, vg = gpu.final_state(list(truth))
     assert np.max(np.abs(xg.cpu().numpy().T - xt)) <= 1e-6 * np.max(np.abs(xt))
     assert gpu.loss(list(truth)) < 1e-9
+    # a new target of the same size is taken in place: the same bits as a
+    # fresh pipeline given that target
+    xt2, vt2 = orc.final_state(truth * 1.02)
+    gpu.set_target_cloud(xt2.T.copy(), vt2.T.copy(), sig)
+    L2, g2 = gpu.loss_and_grad(th)
+    fresh = StreamModel(cfg, xh, vh, checkpoint_every=8)
+    fresh.set_target_cloud(xt2.T.copy(), vt2.T.copy(), sig)
+    L2f, g2f = fresh.loss_and_grad(th)
+    fresh.close()
+    assert L2 == L2f and np.array_equal(g2, g2f)
     # switching back to the density loss
     gpu.set_target(orc.density(truth))
     assert gpu.loss(list(th)) == pytest.approx(orc.loss(th, orc.density(truth)), rel=1e-4)
