@@ -199,8 +199,9 @@ NBODY_API int64_t nbody_launch_count(void);
 /* Create a context holding n_sims >= 1 independent simulations of uneven
  * size: simulation s owns particles offsets[s] .. offsets[s+1]-1 (host
  * array of n_sims + 1 increasing values, offsets[0] = 0) and has its own
- * parameters p[s] (G, eps, dt, potential, centre; checkpoint_every and
- * tape_mode must be 0: a batch records no tape).  Every step runs one
+ * parameters p[s] (G, eps, dt, potential, centre; tape_mode must be 0;
+ * checkpoint_every > 0 for every simulation, or for none, asks the runs to
+ * record their trajectories for nbody_vjp_batch).  Every step runs one
  * persistent pair-force launch over all simulations (a work list of
  * (simulation, i-tile, j-chunk) items, largest first, taken through an
  * atomic counter) and one batched update; nbody_integrate replays the whole
@@ -213,6 +214,30 @@ NBODY_API int64_t nbody_launch_count(void);
 NBODY_API int nbody_create_batch(nbody_ctx **out, int n_sims,
                                  const int64_t *offsets, const nbody_params *p,
                                  void *cuda_stream);
+
+/* Discrete adjoint of a batch's last nbody_integrate (or nbody_step) run,
+ * for every simulation at once (Sec. 2: the reverse of the kick-drift-kick
+ * steps with the pair VJP and the external-field Hessian).  The run must
+ * have recorded its trajectory (checkpoint_every > 0 when it ran): the
+ * batch keeps positions and pair accelerations at every point and the
+ * half-step velocities of every step in device memory, 72 B per particle
+ * and step (a 1000-step run of 1024 simulations of 1000 particles: 75 GB),
+ * so nothing is recomputed.  One persistent launch per point computes the
+ * pair VJP of each work item's rows over its simulation's whole j-range
+ * (FP32 within a tile, FP64 across tiles, in fixed order) and applies the
+ * FP64 adjoint update to those rows; the sweep is captured once as a CUDA
+ * graph per step count.  Cotangents are FP32 in the pair VJP without the
+ * single-system path's power-of-two rescaling, so they must stay within
+ * the FP32 range (about 1e-30 .. 1e30; the NaN status reports an overflow).
+ * xbar, vbar (3 x offsets[n_sims], the batch's layout; host or device;
+ * either may be NULL for zero) are dL/dx_T, dL/dv_T; x0bar, v0bar (same
+ * layout, may be NULL) receive dL/dx_0, dL/dv_0; theta_bar (host or device,
+ * n_sims x 8, may be NULL) receives per simulation (dL/d dt, sum_j m_j
+ * dL/dm_j, dL/dM_NFW, dL/dM_MN, dL/dr_s, dL/da_MN, dL/db_MN, dL/dM_bulge).
+ * Synchronises.  Errors: EINVAL, ESTATE (no recorded run), ENOMEM, ECUDA,
+ * ENAN. */
+NBODY_API int nbody_vjp_batch(nbody_ctx *c, const double *xbar, const double *vbar,
+                              double *x0bar, double *v0bar, double *theta_bar);
 
 /* Launch-shape candidates of the batched pair kernel (threads per block,
  * i-particles per thread, j-chunk length). */
@@ -295,10 +320,11 @@ NBODY_API int nbody_kernel_times(nbody_ctx *c, double ms[NBODY_NKCLASS],
 
 /* Throughput probes of the units the kernels use, on the current device:
  * out = { scalar FP32 FMA TFLOP/s, packed f32x2 FMA TFLOP/s, FP64 FMA
- * TFLOP/s, MUFU rsqrt Gop/s, SM count } (host).  Each probe runs 8
- * independent FMA (or rsqrt) chains per thread on 8 blocks of 256 threads
- * per SM.  Synchronises.  Errors: ENODEV, ENOMEM, ECUDA. */
-NBODY_API int nbody_peaks(double out[5], void *cuda_stream);
+ * TFLOP/s, MUFU rsqrt Gop/s, SM count, MUFU ex2 Gop/s } (host, 6
+ * doubles).  Each probe runs 8 independent FMA (or MUFU) chains per thread
+ * on 8 blocks of 256 threads per SM.  Synchronises.
+ * Errors: ENODEV, ENOMEM, ECUDA. */
+NBODY_API int nbody_peaks(double out[6], void *cuda_stream);
 
 /* ---- stateless kernels (device pointers only, stream = cuda_stream) ---- */
 

@@ -15,6 +15,16 @@
 // Autotuning: the launch shape (threads per block, i-particles per thread,
 // j-chunk length) is chosen among kNTune candidates by timing the pair
 // kernel on the batch itself (nbody_autotune).
+//
+// Reverse sweep (nbody_vjp_batch): when every simulation asks for an
+// adjoint tape, the forward run keeps its whole trajectory in device memory
+// (positions and pair accelerations at every point, half-step velocities of
+// every step: 72 B per particle and step), so the reverse sweep recomputes
+// nothing.  One persistent launch per point computes the pair VJP of a work
+// item's rows over their simulation's whole j-range and applies the adjoint
+// update to those rows (the discrete adjoint of the kick-drift-kick step,
+// Sec. 2), staging the cotangents of the previous point into the other
+// adjoint staging buffer.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,6 +37,7 @@
 #include "nbody_internal.cuh"
 #include "pair_body.cuh"
 #include "staging.cuh"
+#include "vjp_body.cuh"
 
 namespace nb {
 
@@ -140,23 +151,37 @@ __global__ void __launch_bounds__(NT)
 
 // KDK update of one particle (global index g of simulation s) from its
 // complete pair sums (the arithmetic of the separate update kernel)
+// Tape of a recorded forward run at one point k (NULL when not recording):
+// positions x_k and pair accelerations a_k at the point, and the velocity
+// after its kick (the half-step velocity of the drift that follows).
+struct TapePoint {
+  double* x;
+  double* a;
+  double* vh;
+};
+
 __device__ __forceinline__ bool update_one(const DevParams& Q, const SimMeta& M, int s,
                                            int64_t g, const double sum[3], double* x,
                                            double* v, int64_t ptot, double kick, int drift,
                                            const double* centers, int64_t cstride,
-                                           int64_t k_next, float4* st_next) {
+                                           int64_t k_next, float4* st_next, TapePoint tp) {
   double ap[3];
   for (int d = 0; d < 3; ++d) ap[d] = Q.G * M.mscale * (0.0 + sum[d]);
   double xx[3], vv[3];
   for (int d = 0; d < 3; ++d) {
     xx[d] = x[d * ptot + g];
     vv[d] = v[d * ptot + g];
+    if (tp.x) {
+      tp.x[d * ptot + g] = xx[d];
+      tp.a[d * ptot + g] = ap[d];
+    }
   }
   ExtUnit e;
   ext_unit(Q, xx[0], xx[1], xx[2], e);
   bool bad = false;
   for (int d = 0; d < 3; ++d) {
     vv[d] += kick * Q.dt * (ap[d] + Q.nfw_GM * e.n[d] + Q.mn_GM * e.d[d] + Q.bulge_GM * e.b[d]);
+    if (drift && tp.vh) tp.vh[d * ptot + g] = vv[d];
     if (drift) xx[d] += Q.dt * vv[d];
     x[d * ptot + g] = xx[d];
     v[d * ptot + g] = vv[d];
@@ -184,7 +209,7 @@ __global__ void __launch_bounds__(NT)
                  const DevParams* __restrict__ P, double* __restrict__ x,
                  double* __restrict__ v, int64_t ptot, double kick, int drift,
                  const double* __restrict__ centers, int64_t cstride, int64_t k_next,
-                 int* __restrict__ status) {
+                 int* __restrict__ status, TapePoint tp) {
   __shared__ float4 sj[2 * kTJ];
   __shared__ int s_item;
   const int t = threadIdx.x;
@@ -208,7 +233,7 @@ __global__ void __launch_bounds__(NT)
       if (i < M.n) {
         const double sum[3] = {dax[r], day[r], daz[r]};
         bad |= update_one(Q, M, w.x, M.poff + i, sum, x, v, ptot, kick, drift, centers,
-                          cstride, k_next, st_next);
+                          cstride, k_next, st_next, tp);
       }
     }
   }
@@ -279,7 +304,7 @@ __global__ void __launch_bounds__(256)
                    int64_t ptot, double kick, int drift,
                    const double* __restrict__ centers, int64_t cstride,
                    int64_t k_next, float4* __restrict__ st, int* __restrict__ status,
-                   unsigned* __restrict__ ctr) {
+                   unsigned* __restrict__ ctr, TapePoint tp) {
   // the pair launch of this step has finished: re-arm its work counter
   if (blockIdx.x == 0 && threadIdx.x == 0) *ctr = 0u;
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -295,12 +320,17 @@ __global__ void __launch_bounds__(256)
   for (int d = 0; d < 3; ++d) {
     xx[d] = x[d * ptot + g];
     vv[d] = v[d * ptot + g];
+    if (tp.x) {
+      tp.x[d * ptot + g] = xx[d];
+      tp.a[d * ptot + g] = ap[d];
+    }
   }
   ExtUnit e;
   ext_unit(Q, xx[0], xx[1], xx[2], e);
   bool bad = false;
   for (int d = 0; d < 3; ++d) {
     vv[d] += kick * Q.dt * (ap[d] + Q.nfw_GM * e.n[d] + Q.mn_GM * e.d[d] + Q.bulge_GM * e.b[d]);
+    if (drift && tp.vh) tp.vh[d * ptot + g] = vv[d];
     if (drift) xx[d] += Q.dt * vv[d];
     x[d * ptot + g] = xx[d];
     v[d * ptot + g] = vv[d];
@@ -312,6 +342,233 @@ __global__ void __launch_bounds__(256)
                   (float)(xx[2] - c[2]));
   }
   if (bad) atomicOr(status, kStatusNaN);
+}
+
+// ------------------------------------------------------------ reverse sweep
+// VJP work items: (simulation, row tile of kVNT * kVR rows), each over its
+// simulation's whole j-range (kVTJ j-pairs per shared-memory tile)
+constexpr int kVNT = 128, kVR = 2, kVTJ = 256;
+
+// adjoint staging of point k (positions x, cotangents lam) of every
+// simulation into vst, and the pads (far away, zero mass and cotangent)
+// into vst2 as well
+__global__ void __launch_bounds__(256)
+    k_vstage_batch(const SimMeta* __restrict__ meta, const int* __restrict__ blk_sim,
+                   const double* __restrict__ x, const double* __restrict__ m,
+                   const double* __restrict__ lam, int64_t ptot,
+                   const double* __restrict__ centers, int64_t cstride, int64_t k,
+                   float4* __restrict__ vst, float4* __restrict__ vst2) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = blk_sim[blockIdx.x];
+  const SimMeta M = meta[s];
+  const int64_t i = g - M.poff;
+  if (i < M.n) {
+    const double* c = centers + (int64_t)s * cstride + 3 * k;
+    put_vstage(vst, g, (float)(x[g] - c[0]), (float)(x[ptot + g] - c[1]),
+               (float)(x[2 * ptot + g] - c[2]), (float)m[g], (float)lam[g],
+               (float)lam[ptot + g], (float)lam[2 * ptot + g]);
+  } else {
+    put_vstage(vst, g, kPadPos, kPadPos, kPadPos, 0.f, 0.f, 0.f, 0.f);
+    put_vstage(vst2, g, kPadPos, kPadPos, kPadPos, 0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// One reverse point k for every simulation: persistent blocks take VJP work
+// items (sim, row tile); per row the raw VJP sums Q over all j (FP32 within
+// a tile, FP64 across tiles, the single-system kernel's inner step), then
+// the adjoint of the point's kick(s) with coefficient ck (G Q and the
+// external Hessian product, parameter-gradient terms) and, when drift, of
+// the drift that led to it, staging (x_{k-1}, new vbar) into vst_next.
+// Per-item sums of the parameter-gradient terms accumulate in blk[item][8]
+// (fixed order: one block per item per point, points in sequence).  The
+// work counter of the next point is re-armed here.
+template <bool EQM>
+__global__ void __launch_bounds__(kVNT)
+    k_adj_step_batch(const float4* __restrict__ vst, float4* __restrict__ vst_next,
+                     const SimMeta* __restrict__ vmeta, const int4* __restrict__ items,
+                     int nitems, unsigned* __restrict__ ctr, unsigned* __restrict__ ctr_next,
+                     const DevParams* __restrict__ P, double* __restrict__ xbar,
+                     double* __restrict__ vbar, const double* __restrict__ m, int64_t ptot,
+                     const double* __restrict__ xk, const double* __restrict__ ak, double ck,
+                     int drift, const double* __restrict__ vh_prev,
+                     const double* __restrict__ x_prev, const double* __restrict__ centers,
+                     int64_t cstride, int64_t k_prev, double* __restrict__ blk,
+                     int* __restrict__ status) {
+  constexpr int NT = kVNT, R = kVR;
+  __shared__ float4 sj[4 * kVTJ];
+  __shared__ double sred[kAdjCols][NT / 32];
+  __shared__ int s_item;
+  const int t = threadIdx.x;
+  if (blockIdx.x == 0 && t == 0) *ctr_next = 0u;
+  bool bad = false;
+  for (;;) {
+    __syncthreads();
+    if (t == 0) s_item = (int)atomicAdd(ctr, 1u);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= nitems) break;
+    const int4 w = items[it];
+    const SimMeta M = vmeta[w.x];
+    const float4* vs = vst + 2 * M.poff;  // two float4 per particle
+    const int64_t k0 = (int64_t)w.y * (NT * R) + t;
+    IState st[R];
+    double gx[R], gy[R], gz[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      st[r] = load_k(vs, k0 + r * NT);
+      gx[r] = gy[r] = gz[r] = 0.0;
+    }
+    const float2 e2 = make_float2(M.eps2f, M.eps2f);
+    for (int tile = 0; tile < M.ntiles; ++tile) {
+      __syncthreads();
+      const float4* src = vs + (int64_t)tile * (4 * kVTJ);
+#pragma unroll
+      for (int q = t; q < 4 * kVTJ; q += NT) sj[q] = src[q];
+      __syncthreads();
+      float2 qa[R][3], qb[R][3];
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) qa[r][d] = qb[r][d] = make_float2(0.f, 0.f);
+#pragma unroll 2
+      for (int jj = 0; jj < kVTJ; ++jj) {
+        const float4 A = sj[4 * jj], B = sj[4 * jj + 1];
+        const float4 L1 = sj[4 * jj + 2], L2 = sj[4 * jj + 3];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          if (EQM)
+            vjp_body_eqm(A, B, L1, L2, st[r], e2, qa[r], qb[r]);
+          else
+            vjp_body(A, B, L1, L2, st[r], e2, qa[r][0], qa[r][1], qa[r][2]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        gx[r] += (double)qa[r][0].x + (double)qa[r][0].y;
+        gy[r] += (double)qa[r][1].x + (double)qa[r][1].y;
+        gz[r] += (double)qa[r][2].x + (double)qa[r][2].y;
+        if (EQM) {
+          gx[r] -= 3.0 * ((double)qb[r][0].x + (double)qb[r][0].y);
+          gy[r] -= 3.0 * ((double)qb[r][1].x + (double)qb[r][1].y);
+          gz[r] -= 3.0 * ((double)qb[r][2].x + (double)qb[r][2].y);
+        }
+      }
+    }
+    const DevParams Q = P[w.x];
+    double contrib[kAdjCols] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int64_t i = k0 + r * NT;
+      if (i >= M.n) continue;
+      const int64_t g = M.poff + i;
+      double lam[3], x[3], ap[3], gv[3];
+      const double qs[3] = {gx[r], gy[r], gz[r]};
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        lam[d] = vbar[d * ptot + g];
+        x[d] = xk[d * ptot + g];
+        ap[d] = ak[d * ptot + g];
+        gv[d] = -Q.G * M.mscale * qs[d];
+      }
+      ExtUnit e;
+      ext_unit(Q, x[0], x[1], x[2], e);
+      double jl[3];
+      ext_jvp(Q, x[0], x[1], x[2], lam, jl);
+      const double ckdt = ck * Q.dt;
+      double xb[3];
+      double lp = 0.0, ln = 0.0, lm = 0.0, lb = 0.0;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        xb[d] = xbar[d * ptot + g] + ckdt * (gv[d] + jl[d]);
+        lp += lam[d] * ap[d];
+        ln += lam[d] * e.n[d];
+        lm += lam[d] * e.d[d];
+        lb += lam[d] * e.b[d];
+      }
+      const double la = lp + Q.nfw_GM * ln + Q.mn_GM * lm + Q.bulge_GM * lb;
+      contrib[0] += ck * la;          // dL/d dt from the kick(s)
+      contrib[1] += ckdt * lp;        // sum_j m_j dL/dm_j
+      contrib[2] += ckdt * Q.G * ln;  // dL/d M_NFW
+      contrib[3] += ckdt * Q.G * lm;  // dL/d M_MN
+      if (Q.ext) {                    // dL/d (r_s, a_MN, b_MN), dL/d M_bulge
+        double sh[3];
+        ext_shape_vjp(Q, x[0], x[1], x[2], lam, sh);
+        contrib[4] += ckdt * sh[0];
+        contrib[5] += ckdt * sh[1];
+        contrib[6] += ckdt * sh[2];
+        contrib[7] += ckdt * Q.G * lb;
+      }
+      double vb[3] = {lam[0], lam[1], lam[2]};
+      if (drift) {
+        double xv = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          xv += xb[d] * vh_prev[d * ptot + g];
+          vb[d] += Q.dt * xb[d];
+          vbar[d * ptot + g] = vb[d];
+        }
+        contrib[0] += xv;             // dL/d dt from the drift
+        const double* c = centers + (int64_t)w.x * cstride + 3 * k_prev;
+        put_vstage(vst_next, g, (float)(x_prev[g] - c[0]), (float)(x_prev[ptot + g] - c[1]),
+                   (float)(x_prev[2 * ptot + g] - c[2]), (float)m[g], (float)vb[0],
+                   (float)vb[1], (float)vb[2]);
+      }
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        xbar[d * ptot + g] = xb[d];
+        bad |= !isfinite(xb[d]) || !isfinite(vb[d]);
+      }
+    }
+    // the item's parameter-gradient terms: fixed-order block sum
+    const int lane = t & 31, wp = t >> 5;
+#pragma unroll
+    for (int q = 0; q < kAdjCols; ++q) {
+      double v = contrib[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) sred[q][wp] = v;
+    }
+    __syncthreads();
+    if (t < kAdjCols) {
+      double v = 0.0;
+#pragma unroll
+      for (int k = 0; k < NT / 32; ++k) v += sred[t][k];
+      blk[(int64_t)it * kAdjCols + t] += v;
+    }
+  }
+  if (bad) atomicOr(status, kStatusNaN);
+}
+
+// per-simulation parameter gradient: the sum of its items' rows of blk in
+// item order (items of one simulation are contiguous), into out[s][8]
+__global__ void k_adj_reduce_batch(const double* __restrict__ blk,
+                                   const int* __restrict__ first_item, int n_sims,
+                                   double* __restrict__ out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_sims) return;
+  for (int q = 0; q < kAdjCols; ++q) {
+    double v = 0.0;
+    for (int it = first_item[s]; it < first_item[s + 1]; ++it) v += blk[(int64_t)it * kAdjCols + q];
+    out[(int64_t)s * kAdjCols + q] = v;
+  }
+}
+
+// caller layout -> padded (3 x ntot -> 3 x ptot), or back when to_caller
+__global__ void k_move_batch(const SimMeta* __restrict__ meta, int n_sims,
+                             const double* __restrict__ src, double* __restrict__ dst,
+                             int64_t ntot, int64_t ptot, int to_caller) {
+  for (int s = blockIdx.y; s < n_sims; s += gridDim.y) {
+    const SimMeta M = meta[s];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M.n;
+         i += (int64_t)gridDim.x * blockDim.x)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        if (to_caller)
+          dst[d * ntot + M.off + i] = src[d * ptot + M.poff + i];
+        else
+          dst[d * ptot + M.poff + i] = src[d * ntot + M.off + i];
+      }
+  }
 }
 
 // caller layout (3 x ntot SoA, simulation s at columns off .. off+n-1) ->
@@ -411,7 +668,29 @@ struct Batch {
   cudaGraphExec_t exec = nullptr;
   int64_t exec_steps = -1;
   int exec_tune = -1;
+  bool exec_record = false;
   int graph_nodes = 0;
+  // reverse sweep
+  bool record = false;          // every simulation asks for an adjoint tape
+  double* tape = nullptr;       // x, a at points 0..n; vh of steps 0..n-1
+  int64_t tape_cap = -1;        // steps the tape holds room for
+  int64_t tape_steps = -1;      // steps of the recorded run (-1: none)
+  SimMeta* vmeta = nullptr;     // VJP plan: whole j-range per item
+  int4* vitems = nullptr;
+  int nvitems = 0;
+  int grid_vjp = 0;
+  std::vector<int> first_item;  // first VJP item of every simulation (+ end)
+  int* dfirst = nullptr;
+  double *xbar = nullptr, *vbar = nullptr;
+  float4 *vst = nullptr, *vst2 = nullptr;
+  double* vblk = nullptr;       // [nvitems][kAdjCols]
+  double* tbar = nullptr;       // [n_sims][kAdjCols]
+  double* cot = nullptr;        // caller-layout scratch of host cotangents
+  cudaGraphExec_t vexec = nullptr;
+  int64_t vexec_steps = -1;
+  bool vexec_eqm = false;
+  int vgraph_nodes = 0;
+  bool vplan_valid = false;     // vmeta matches the current masses and eps
 };
 
 namespace {
@@ -588,6 +867,37 @@ int ensure_centers(Batch* b, int64_t n_steps) {
   return NBODY_OK;
 }
 
+// tape slots of point k of a recorded run of n_steps (all NULL when the
+// batch does not record)
+TapePoint tape_point(const Batch* b, int64_t n_steps, int64_t k) {
+  TapePoint tp{nullptr, nullptr, nullptr};
+  if (!b->record) return tp;
+  const size_t slot = 3 * (size_t)b->ptot;
+  tp.x = b->tape + (size_t)k * slot;
+  tp.a = b->tape + (size_t)(n_steps + 1 + k) * slot;
+  tp.vh = k < n_steps ? b->tape + (size_t)(2 * (n_steps + 1) + k) * slot : nullptr;
+  return tp;
+}
+
+int ensure_tape(Batch* b, int64_t n_steps) {
+  if (!b->record || (b->tape && b->tape_cap == n_steps)) return NBODY_OK;
+  if (b->exec) {  // a captured run refers to the buffer about to be replaced
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  if (b->vexec) {
+    cudaGraphExecDestroy(b->vexec);
+    b->vexec = nullptr;
+  }
+  bfree(b->tape);
+  b->tape_cap = -1;
+  b->tape_steps = -1;
+  int rc = balloc(&b->tape, (size_t)(3 * n_steps + 2) * 3 * (size_t)b->ptot);
+  if (rc) return rc;
+  b->tape_cap = n_steps;
+  return NBODY_OK;
+}
+
 // the kernels of one n_steps run, in stream order
 int record_run(Batch* b, int64_t n_steps, cudaStream_t s, int* nodes) {
   const int64_t cs = 3 * (b->centers_cap + 1);
@@ -611,7 +921,8 @@ int record_run(Batch* b, int64_t n_steps, cudaStream_t s, int* nodes) {
       BCK(with_step_kernel(b, b->tune, [&](auto kern, int nt) {
         kern<<<g, nt, 0, s>>>(sbuf[cur], sbuf[1 - cur], b->meta, b->items, b->nitems,
                               b->ctr + cur, b->ctr + (1 - cur), b->dp, b->x, b->v, b->ptot,
-                              kick, k < n_steps ? 1 : 0, b->centers, cs, k + 1, b->status);
+                              kick, k < n_steps ? 1 : 0, b->centers, cs, k + 1, b->status,
+                              tape_point(b, n_steps, k));
         return cudaGetLastError();
       }));
       cnt += 1;
@@ -624,7 +935,8 @@ int record_run(Batch* b, int64_t n_steps, cudaStream_t s, int* nodes) {
     const double kick = (k == 0 || k == n_steps) ? 0.5 : 1.0;
     k_update_batch<<<nblk, 256, 0, s>>>(b->dp, b->meta, b->blk_sim, b->x, b->v, b->part,
                                         b->ptot, kick, k < n_steps ? 1 : 0, b->centers,
-                                        cs, k + 1, b->st, b->status, b->ctr);
+                                        cs, k + 1, b->st, b->status, b->ctr,
+                                        tape_point(b, n_steps, k));
     BCK(cudaGetLastError());
     cnt += 2;
   }
@@ -635,6 +947,14 @@ int record_run(Batch* b, int64_t n_steps, cudaStream_t s, int* nodes) {
 int upload(Batch* b) {
   std::vector<DevParams> d(b->n_sims);
   std::vector<int> mode(b->n_sims);
+  bool record = true;
+  for (int s = 0; s < b->n_sims; ++s) record = record && b->prm[s].checkpoint_every > 0;
+  if (record != b->record && b->exec) {  // the captured run bakes the tape in
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  b->record = record;
+  b->vplan_valid = false;  // eps may have changed
   std::vector<double> g(6 * (size_t)b->n_sims);
   for (int s = 0; s < b->n_sims; ++s) {
     d[s] = dev_params(b->prm[s]);
@@ -683,7 +1003,7 @@ int batch_create(Batch** out, int n_sims, const int64_t* offsets,
       (rc = balloc(&b->v, 3 * pt)) || (rc = balloc(&b->m, pt)) ||
       (rc = balloc(&b->st, pt)) || (rc = balloc(&b->st2, pt)) ||
       (rc = balloc(&b->meta, n_sims)) ||
-      (rc = balloc(&b->blk_sim, bs.size())) || (rc = balloc(&b->ctr, 2)) ||
+      (rc = balloc(&b->blk_sim, bs.size())) || (rc = balloc(&b->ctr, 4)) ||
       (rc = balloc(&b->status, 1))) {
     batch_destroy(b);
     return rc;
@@ -718,6 +1038,9 @@ void batch_destroy(Batch* b) {
   bfree(b->dp); bfree(b->mode); bfree(b->guide); bfree(b->x); bfree(b->v);
   bfree(b->m); bfree(b->st); bfree(b->st2); bfree(b->part); bfree(b->meta); bfree(b->blk_sim);
   bfree(b->items); bfree(b->ctr); bfree(b->status); bfree(b->centers);
+  if (b->vexec) cudaGraphExecDestroy(b->vexec);
+  bfree(b->tape); bfree(b->vmeta); bfree(b->vitems); bfree(b->dfirst); bfree(b->xbar);
+  bfree(b->vbar); bfree(b->vst); bfree(b->vst2); bfree(b->vblk); bfree(b->tbar); bfree(b->cot);
   delete b;
 }
 
@@ -799,6 +1122,8 @@ int batch_set_state(Batch* b, const double* x, const double* v, const double* m)
     b->exec = nullptr;
   }
   b->eqm = eqm;
+  b->vplan_valid = false;
+  b->tape_steps = -1;
   const int rc = build_plan(b, b->tune);  // per-simulation mass scales
   if (rc) return rc;
   // restart every guide from its parameters
@@ -833,7 +1158,10 @@ int batch_get_state(Batch* b, double* x, double* v) {
 int batch_integrate(Batch* b, int64_t n_steps) {
   int rc = ensure_centers(b, n_steps);
   if (rc) return rc;
-  if (!b->exec || b->exec_steps != n_steps || b->exec_tune != b->tune) {
+  if ((rc = ensure_tape(b, n_steps))) return rc;
+  b->tape_steps = -1;
+  if (!b->exec || b->exec_steps != n_steps || b->exec_tune != b->tune ||
+      b->exec_record != b->record) {
     if (b->exec) {
       cudaGraphExecDestroy(b->exec);
       b->exec = nullptr;
@@ -856,6 +1184,7 @@ int batch_integrate(Batch* b, int64_t n_steps) {
     }
     b->exec_steps = n_steps;
     b->exec_tune = b->tune;
+    b->exec_record = b->record;
     b->graph_nodes = nodes;
   }
   BCK(cudaEventRecord(b->ev_in, b->user));
@@ -864,7 +1193,187 @@ int batch_integrate(Batch* b, int64_t n_steps) {
   BCK(cudaEventRecord(b->ev_out, b->gs));
   BCK(cudaStreamWaitEvent(b->user, b->ev_out, 0));
   count_launch(b->graph_nodes);
+  if (b->record) b->tape_steps = n_steps;
   return NBODY_OK;
+}
+
+namespace {
+
+// VJP plan and reverse-sweep buffers (once per batch)
+int ensure_vjp_plan(Batch* b) {
+  if (b->vmeta && b->vplan_valid) return NBODY_OK;
+  const int per_block = kVNT * kVR;
+  std::vector<SimMeta> vm(b->n_sims);
+  std::vector<int4> items;
+  b->first_item.assign(b->n_sims + 1, 0);
+  for (int s = 0; s < b->n_sims; ++s) {
+    SimMeta M{};
+    M.npad = b->npad[s];
+    M.poff = b->poff[s];
+    M.n = b->n[s];
+    M.off = b->off[s];
+    M.S = 1;
+    M.ntiles = (int)(M.npad / (2 * kVTJ));
+    M.eps2f = (float)(b->prm[s].eps * b->prm[s].eps);
+    M.mscale = b->eqm ? b->m_eq[s] : 1.0;
+    vm[s] = M;
+    b->first_item[s] = (int)items.size();
+    for (int64_t it = 0; it < M.npad / per_block; ++it) items.push_back(make_int4(s, (int)it, 0, 0));
+  }
+  b->first_item[b->n_sims] = (int)items.size();
+  b->nvitems = (int)items.size();
+  const size_t pt = (size_t)b->ptot;
+  int rc;
+  if (!b->vmeta &&
+      ((rc = balloc(&b->vitems, items.size())) ||
+       (rc = balloc(&b->dfirst, b->first_item.size())) || (rc = balloc(&b->xbar, 3 * pt)) ||
+       (rc = balloc(&b->vbar, 3 * pt)) || (rc = balloc(&b->vst, 2 * pt)) ||
+       (rc = balloc(&b->vst2, 2 * pt)) ||
+       (rc = balloc(&b->vblk, (size_t)b->nvitems * kAdjCols)) ||
+       (rc = balloc(&b->tbar, (size_t)b->n_sims * kAdjCols)) ||
+       (rc = balloc(&b->vmeta, (size_t)b->n_sims))))
+    return rc;
+  BCK(cudaMemcpyAsync(b->vmeta, vm.data(), vm.size() * sizeof(SimMeta), cudaMemcpyHostToDevice,
+                      b->gs));
+  BCK(cudaMemcpyAsync(b->vitems, items.data(), items.size() * sizeof(int4),
+                      cudaMemcpyHostToDevice, b->gs));
+  BCK(cudaMemcpyAsync(b->dfirst, b->first_item.data(), b->first_item.size() * sizeof(int),
+                      cudaMemcpyHostToDevice, b->gs));
+  BCK(cudaStreamSynchronize(b->gs));
+  int occ = 1;
+  const cudaError_t e = b->eqm
+      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adj_step_batch<true>, kVNT, 0)
+      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adj_step_batch<false>, kVNT, 0);
+  if (e != cudaSuccess || occ < 1) {
+    cudaGetLastError();
+    occ = 1;
+  }
+  b->grid_vjp = std::min(b->nvitems, occ * b->sm_count);
+  b->vplan_valid = true;
+  return NBODY_OK;
+}
+
+// the kernels of the reverse sweep over a recorded run of n_steps
+int record_sweep(Batch* b, int64_t n_steps, cudaStream_t s, int* nodes) {
+  const int64_t cs = 3 * (b->centers_cap + 1);
+  const unsigned nblk = (unsigned)(b->ptot / 256);
+  BCK(cudaMemsetAsync(b->ctr + 2, 0, 2 * sizeof(unsigned), s));
+  BCK(cudaMemsetAsync(b->vblk, 0, (size_t)b->nvitems * kAdjCols * sizeof(double), s));
+  const TapePoint tn = tape_point(b, n_steps, n_steps);
+  k_vstage_batch<<<nblk, 256, 0, s>>>(b->meta, b->blk_sim, tn.x, b->m, b->vbar, b->ptot,
+                                      b->centers, cs, n_steps, b->vst, b->vst2);
+  BCK(cudaGetLastError());
+  float4* vbuf[2] = {b->vst, b->vst2};
+  const unsigned g = (unsigned)std::max(1, b->grid_vjp);
+  int cnt = 1;
+  for (int64_t k = n_steps; k >= 0; --k) {
+    const int cur = (int)((n_steps - k) & 1);
+    const TapePoint tk = tape_point(b, n_steps, k);
+    const TapePoint tp = k > 0 ? tape_point(b, n_steps, k - 1) : TapePoint{nullptr, nullptr, nullptr};
+    const double ck = (k == n_steps || k == 0) ? 0.5 : 1.0;
+    const int drift = k > 0 ? 1 : 0;
+    if (b->eqm)
+      k_adj_step_batch<true><<<g, kVNT, 0, s>>>(
+          vbuf[cur], vbuf[1 - cur], b->vmeta, b->vitems, b->nvitems, b->ctr + 2 + cur,
+          b->ctr + 2 + (1 - cur), b->dp, b->xbar, b->vbar, b->m, b->ptot, tk.x, tk.a, ck, drift,
+          tp.vh, tp.x, b->centers, cs, k > 0 ? k - 1 : 0, b->vblk, b->status);
+    else
+      k_adj_step_batch<false><<<g, kVNT, 0, s>>>(
+          vbuf[cur], vbuf[1 - cur], b->vmeta, b->vitems, b->nvitems, b->ctr + 2 + cur,
+          b->ctr + 2 + (1 - cur), b->dp, b->xbar, b->vbar, b->m, b->ptot, tk.x, tk.a, ck, drift,
+          tp.vh, tp.x, b->centers, cs, k > 0 ? k - 1 : 0, b->vblk, b->status);
+    BCK(cudaGetLastError());
+    ++cnt;
+  }
+  k_adj_reduce_batch<<<(b->n_sims + 127) / 128, 128, 0, s>>>(b->vblk, b->dfirst, b->n_sims,
+                                                             b->tbar);
+  BCK(cudaGetLastError());
+  *nodes = cnt + 1;
+  return NBODY_OK;
+}
+
+}  // namespace
+
+int batch_vjp(Batch* b, const double* xbar, const double* vbar, double* x0bar, double* v0bar,
+              double* theta_bar) {
+  if (!b->record || b->tape_steps < 0) return NBODY_ESTATE;
+  const int64_t n_steps = b->tape_steps;
+  int rc = ensure_vjp_plan(b);
+  if (rc) return rc;
+  // the sweep runs on the batch's stream after the caller's work so far
+  BCK(cudaEventRecord(b->ev_in, b->user));
+  BCK(cudaStreamWaitEvent(b->gs, b->ev_in, 0));
+  const size_t n3 = 3 * (size_t)b->ntot;
+  // cotangents of the final state into the padded layout (host arrays go
+  // through one scratch copy)
+  const double* src[2] = {xbar, vbar};
+  double* dst[2] = {b->xbar, b->vbar};
+  dim3 grid((unsigned)std::min<int64_t>(64, (b->ptot / b->n_sims + 255) / 256 + 1),
+            (unsigned)std::min(b->n_sims, 65535));
+  for (int q = 0; q < 2; ++q) {
+    BCK(cudaMemsetAsync(dst[q], 0, 3 * (size_t)b->ptot * sizeof(double), b->gs));
+    if (!src[q]) continue;
+    const double* p = src[q];
+    if (!on_device(p)) {
+      if (!b->cot && (rc = balloc(&b->cot, n3))) return rc;
+      BCK(cudaMemcpyAsync(b->cot, p, n3 * sizeof(double), cudaMemcpyDefault, b->gs));
+      p = b->cot;
+    }
+    k_move_batch<<<grid, 256, 0, b->gs>>>(b->meta, b->n_sims, p, dst[q], b->ntot, b->ptot, 0);
+    BCK(cudaGetLastError());
+    if (p == b->cot) BCK(cudaStreamSynchronize(b->gs));  // the scratch is reused
+  }
+  count_launch(2);
+  if (!b->vexec || b->vexec_steps != n_steps || b->vexec_eqm != b->eqm) {
+    if (b->vexec) {
+      cudaGraphExecDestroy(b->vexec);
+      b->vexec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    BCK(cudaStreamBeginCapture(b->gs, cudaStreamCaptureModeThreadLocal));
+    int nodes = 0;
+    rc = record_sweep(b, n_steps, b->gs, &nodes);
+    cudaError_t e = cudaStreamEndCapture(b->gs, &graph);
+    if (rc || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return rc ? rc : NBODY_ECUDA;
+    }
+    e = cudaGraphInstantiate(&b->vexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      b->vexec = nullptr;
+      return NBODY_ECUDA;
+    }
+    b->vexec_steps = n_steps;
+    b->vexec_eqm = b->eqm;
+    b->vgraph_nodes = nodes;
+  }
+  BCK(cudaGraphLaunch(b->vexec, b->gs));
+  count_launch(b->vgraph_nodes);
+  double* out[2] = {x0bar, v0bar};
+  const double* res[2] = {b->xbar, b->vbar};
+  for (int q = 0; q < 2; ++q) {
+    if (!out[q]) continue;
+    double* p = out[q];
+    const bool dev = on_device(p);
+    if (!dev) {
+      if (!b->cot && (rc = balloc(&b->cot, n3))) return rc;
+      p = b->cot;
+    }
+    k_move_batch<<<grid, 256, 0, b->gs>>>(b->meta, b->n_sims, res[q], p, b->ntot, b->ptot, 1);
+    BCK(cudaGetLastError());
+    count_launch();
+    if (!dev) {
+      BCK(cudaMemcpyAsync(out[q], b->cot, n3 * sizeof(double), cudaMemcpyDefault, b->gs));
+      BCK(cudaStreamSynchronize(b->gs));
+    }
+  }
+  if (theta_bar)
+    BCK(cudaMemcpyAsync(theta_bar, b->tbar, (size_t)b->n_sims * kAdjCols * sizeof(double),
+                        cudaMemcpyDefault, b->gs));
+  BCK(cudaStreamSynchronize(b->gs));
+  return batch_status(b);
 }
 
 int batch_status(Batch* b) {
@@ -912,7 +1421,7 @@ int batch_autotune(Batch* b, int64_t probe_steps, int* best, double* ms_out) {
       return with_step_kernel(b, b->tune, [&](auto kern, int nt) {
         kern<<<g, nt, 0, b->gs>>>(b->st, b->st2, b->meta, b->items, b->nitems, b->ctr,
                                   b->ctr + 1, b->dp, b->x, b->v, b->ptot, 0.0, 0, b->centers,
-                                  cs, 0, b->status);
+                                  cs, 0, b->status, TapePoint{nullptr, nullptr, nullptr});
         return cudaGetLastError();
       });
     }
@@ -920,7 +1429,7 @@ int batch_autotune(Batch* b, int64_t probe_steps, int* best, double* ms_out) {
     if (e != cudaSuccess) return e;
     k_update_batch<<<nblk, 256, 0, b->gs>>>(b->dp, b->meta, b->blk_sim, b->x, b->v, b->part,
                                             b->ptot, 0.0, 0, b->centers, cs, 0, b->st,
-                                            b->status, b->ctr);
+                                            b->status, b->ctr, TapePoint{nullptr, nullptr, nullptr});
     return cudaGetLastError();
   };
   for (int k = 0; k < NBODY_NTUNE; ++k) {

@@ -735,7 +735,8 @@ int nbody_set_params(nbody_ctx* c, const nbody_params* p) {
     for (int s = 0; s < c->n_sims; ++s) {
       int rc = check_params(&p[s]);
       if (rc) return rc;
-      if (p[s].checkpoint_every != 0 || p[s].tape_mode != 0) return NBODY_EINVAL;
+      if ((p[s].checkpoint_every > 0) != (p[0].checkpoint_every > 0) || p[s].tape_mode != 0)
+        return NBODY_EINVAL;
     }
     return nb::batch_set_params(c->batch, p);
   }
@@ -1020,7 +1021,8 @@ int nbody_create_batch(nbody_ctx** out, int n_sims, const int64_t* offsets,
     if (offsets[s + 1] <= offsets[s]) return NBODY_EINVAL;
     int rc = check_params(&p[s]);
     if (rc) return rc;
-    if (p[s].checkpoint_every != 0 || p[s].tape_mode != 0) return NBODY_EINVAL;
+    if ((p[s].checkpoint_every > 0) != (p[0].checkpoint_every > 0) || p[s].tape_mode != 0)
+      return NBODY_EINVAL;
   }
   int dev = 0, sms = 0;
   int rc = check_device(&dev, &sms);
@@ -1040,6 +1042,12 @@ int nbody_create_batch(nbody_ctx** out, int n_sims, const int64_t* offsets,
   }
   *out = c;
   return NBODY_OK;
+}
+
+int nbody_vjp_batch(nbody_ctx* c, const double* xbar, const double* vbar, double* x0bar,
+                    double* v0bar, double* theta_bar) {
+  if (!c || !c->batch) return NBODY_EINVAL;
+  return nb::batch_vjp(c->batch, xbar, vbar, x0bar, v0bar, theta_bar);
 }
 
 int nbody_autotune(nbody_ctx* c, int64_t probe_steps, int* best,

@@ -226,6 +226,11 @@ int batch_set_params(Batch* b, const nbody_params* p);
 int batch_set_state(Batch* b, const double* x, const double* v, const double* m);
 int batch_get_state(Batch* b, double* x, double* v);
 int batch_integrate(Batch* b, int64_t n_steps);
+// reverse sweep of the last recorded run (every simulation's
+// checkpoint_every > 0); cotangents and results in the caller's layout,
+// theta_bar [n_sims][kAdjCols] or NULL
+int batch_vjp(Batch* b, const double* xbar, const double* vbar, double* x0bar, double* v0bar,
+              double* theta_bar);
 int batch_status(Batch* b);
 int batch_autotune(Batch* b, int64_t probe_steps, int* best, double* ms);
 int batch_set_tuning(Batch* b, int k);

@@ -1,6 +1,6 @@
 // peaks.cu -- throughput probes of the units the method's kernels use:
-// FP32 FMA (scalar and packed f32x2), FP64 FMA and the MUFU reciprocal
-// square root.  Each thread runs 8 independent dependency chains so that
+// FP32 FMA (scalar and packed f32x2), FP64 FMA, and the MUFU reciprocal
+// square root and base-2 exponential.  Each thread runs 8 independent dependency chains so that
 // latency is hidden and the pipe's issue rate is what is measured.
 #include <cuda_runtime.h>
 
@@ -67,9 +67,26 @@ __global__ void k_rsqrt(float* out, int iters) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+__global__ void k_ex2(float* out, int iters) {
+  float x[kChains];
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) x[k] = 0.5f + threadIdx.x * 1e-4f + 0.01f * k;
+  for (int i = 0; i < iters; ++i)
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) {
+      float y;
+      asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(-x[k]));
+      x[k] = y;
+    }
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) s += x[k];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 }  // namespace
 
-extern "C" int nbody_peaks(double out[5], void* cuda_stream) {
+extern "C" int nbody_peaks(double out[6], void* cuda_stream) {
   if (!out) return NBODY_EINVAL;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -111,7 +128,9 @@ extern "C" int nbody_peaks(double out[5], void* cuda_stream) {
   out[3] = timed([&] { k_rsqrt<<<blocks, threads, 0, s>>>((float*)buf, itr); },
                  (double)kChains * itr * (double)nt) / 1e9;
   out[4] = (double)sms;
-  nb::count_launch(8);
+  out[5] = timed([&] { k_ex2<<<blocks, threads, 0, s>>>((float*)buf, itr); },
+                 (double)kChains * itr * (double)nt) / 1e9;
+  nb::count_launch(10);
   const cudaError_t e = cudaGetLastError();
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -43,7 +43,8 @@ EXPORTED = ("nbody_create", "nbody_destroy", "nbody_set_params",
             "nbody_pair_accel", "nbody_set_timing", "nbody_kernel_times",
             "nbody_pair_accel_noalloc", "nbody_stream_create",
             "nbody_stream_set_target", "nbody_stream_forward", "nbody_stream_grad",
-            "nbody_stream_destroy", "nbody_stream_initial_state", "nbody_stream_head", "nbody_create_batch", "nbody_autotune",
+            "nbody_stream_destroy", "nbody_stream_initial_state", "nbody_stream_head", "nbody_create_batch",
+            "nbody_vjp_batch", "nbody_autotune",
             "nbody_set_tuning", "nbody_get_tuning", "nbody_mlp_create",
             "nbody_mlp_num_params", "nbody_mlp_set_params", "nbody_mlp_get_params",
             "nbody_mlp_forward", "nbody_mlp_loss_grad", "nbody_mlp_adam_step",
@@ -160,6 +161,7 @@ def lib():
         L.nbody_stream_destroy.argtypes = [vp]
         L.nbody_stream_destroy.restype = None
         L.nbody_create_batch.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(i64), P, vp]
+        L.nbody_vjp_batch.argtypes = [vp, vp, vp, vp, vp, vp]
         L.nbody_autotune.argtypes = [vp, i64, C.POINTER(C.c_int), dp]
         L.nbody_set_tuning.argtypes = [vp, C.c_int]
         L.nbody_get_tuning.argtypes = [vp]
@@ -433,10 +435,11 @@ def nbody_autotune_pair(h, probe_launches=3):
 
 def nbody_peaks(stream=None):
     """dict of measured unit throughputs of the current device."""
-    out = (C.c_double * 5)()
+    out = (C.c_double * 6)()
     _check(lib().nbody_peaks(out, _stream(stream)), "nbody_peaks")
     return {"fp32_fma_tflops": out[0], "fp32x2_fma_tflops": out[1],
-            "fp64_fma_tflops": out[2], "rsqrt_gops": out[3], "sms": int(out[4])}
+            "fp64_fma_tflops": out[2], "rsqrt_gops": out[3], "sms": int(out[4]),
+            "ex2_gops": out[5]}
 
 
 def nbody_set_timing(h, enable: bool):
@@ -461,6 +464,18 @@ def nbody_create_batch(offsets, params_list, stream=None):
     _check(lib().nbody_create_batch(C.byref(h), ns, offs, arr, _stream(stream)),
            "nbody_create_batch")
     return h
+
+
+def nbody_vjp_batch(h, n_sims, xbar, vbar, x0bar=None, v0bar=None):
+    """Adjoint of a batch's last recorded run: fills x0bar, v0bar (3, ntot)
+    when given and returns theta_bar (n_sims, 8) = per simulation (dL/d dt,
+    sum_j m_j dL/dm_j, dL/dM_NFW, dL/dM_MN, dL/dr_s, dL/da_MN, dL/db_MN,
+    dL/dM_bulge)."""
+    import numpy as np
+    tb = np.zeros((n_sims, 8))
+    _check(lib().nbody_vjp_batch(h, _ptr(xbar), _ptr(vbar), _ptr(x0bar), _ptr(v0bar),
+                                 _ptr(tb)), "nbody_vjp_batch")
+    return tb
 
 
 def nbody_set_params_batch(h, params_list):
