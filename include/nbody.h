@@ -456,6 +456,44 @@ NBODY_API int nbody_stream_head(nbody_stream *s, const double *x,
 /* Release the pipeline; NULL is a no-op. */
 NBODY_API void nbody_stream_destroy(nbody_stream *s);
 
+/* ---- the pipeline for many parameter vectors at once ----
+ *
+ * The point-cloud form of the pipeline above for `count` parameter vectors
+ * theta_b = (t_end, M_Plummer, M_NFW, M_MN) together, member b scored by
+ * MMD^2 against its own target cloud: the gradient refinement of many grid
+ * points or of many bootstrap realisations of the observation (Sec. 2.2.1).
+ * Steps 1-2 run one thread per member; step 3 is one batch context of
+ * count simulations of n particles (nbody_create_batch) recording its
+ * trajectories, its reverse sweep nbody_vjp_batch; the MMD terms of all
+ * members take one launch each way. */
+typedef struct nbody_stream_batch nbody_stream_batch; /* opaque */
+
+/* cfg as for nbody_stream_create (checkpoint_every and the histogram
+ * fields are not used: the batch keeps whole trajectories); xhat, vhat the
+ * unit Plummer sample (3 x n, host or device); the targets tx, tv (3 x
+ * count m, target b in columns b m .. b m + m - 1, host or device), all
+ * compared in the units `scale` (host, 6 standard deviations) with the
+ * bandwidths sigma (host, n_sigma in 1..4).  1 <= count <= 65535.  Device
+ * memory: about 72 B per particle and step for the recorded trajectories
+ * (count n (3 n_steps + 2) x 24 B).  Errors: EINVAL, ENODEV, ENOMEM, ECUDA. */
+NBODY_API int nbody_stream_batch_create(nbody_stream_batch **out,
+                                        const nbody_stream_cfg *cfg, int64_t count,
+                                        const double *xhat, const double *vhat, int64_t m,
+                                        const double *tx, const double *tv,
+                                        const double *scale, int n_sigma,
+                                        const double *sigma, void *cuda_stream);
+
+/* losses[b] = MMD^2 of member b's final cloud at thetas[b] (host or device,
+ * count x 4) against target b, and when theta_bars is not NULL (host or
+ * device, count x 4) its gradient dL_b/dtheta_b.  The first call tunes the
+ * batch's pair-kernel launch shape.  Synchronises.
+ * Errors: EINVAL, ENOMEM, ECUDA, ENAN. */
+NBODY_API int nbody_stream_batch_loss_grad(nbody_stream_batch *s, const double *thetas,
+                                           double *losses, double *theta_bars);
+
+/* Release; NULL is a no-op. */
+NBODY_API void nbody_stream_batch_destroy(nbody_stream_batch *s);
+
 /* ---- maximum mean discrepancy between phase-space point clouds ----
  *
  * The paper's first inference method (Sec. 2.2.1; Fig. 2, step 4) compares

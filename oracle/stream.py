@@ -194,8 +194,9 @@ class StreamModel:
         # m_j = M / N
         Xb = r["x0bar"].sum(axis=0)
         Vb = r["v0bar"].sum(axis=0)
-        Mb = (0.5 * math.sqrt(G / (a * M_prog)) * np.sum(r["v0bar"] * self.vhat)
-              + np.sum(r["mbar"]) / self.N)
+        Mb_v = 0.5 * math.sqrt(G / (a * M_prog)) * np.sum(r["v0bar"] * self.vhat)
+        Mb_m = np.sum(r["mbar"]) / self.N
+        Mb = Mb_v + Mb_m
         # backward orbit adjoint (single particle, external potential only)
         ro = core.vjp(self.physics(theta, False),
                       np.asarray(self.cfg.X0, float)[None, :],
@@ -204,6 +205,12 @@ class StreamModel:
         # t_end enters twice, through the forward run's dt and the backward
         # orbit's -dt; the two parts are kept for error bounds
         self.t_end_parts = (r["dt_bar"] / n, -ro["dt_bar"] / n)
+        # every component is a sum of two separately computed parts (the
+        # n-body run's and the orbit's; for M_Plummer the velocity scaling's
+        # and the masses'); kept for error bounds as well
+        self.grad_parts = (np.array([r["dt_bar"] / n, Mb_v, r["nfw_M_bar"], r["mn_M_bar"]]),
+                           np.array([-ro["dt_bar"] / n, Mb_m, ro["nfw_M_bar"],
+                                     ro["mn_M_bar"]]))
         grad = np.array([
             r["dt_bar"] / n - ro["dt_bar"] / n,
             Mb,

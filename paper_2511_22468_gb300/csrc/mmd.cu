@@ -88,13 +88,13 @@ __global__ void k_mmd_stage(const double* __restrict__ x, const double* __restri
 
 // Row sums.  Grid: x = row blocks of NT*R points, y = set, z = column chunk.
 // Rows of set b: rows + b * rstride; columns: ntA tiles of colA + b * astride
-// then ntB tiles of colB.  part: [set][chunk][8][npad_r] FP64 (S0A, S0B, S1).
+// then ntB tiles of colB + b * bstride.  part: [set][chunk][8][npad_r] FP64 (S0A, S0B, S1).
 template <int R, int NS>
 __global__ void __launch_bounds__(128)
     k_mmd_rows(const float4* __restrict__ rows, int64_t rstride, int64_t npad_r,
                const float4* __restrict__ colA, int64_t astride, int ntA,
-               const float4* __restrict__ colB, int ntB, double wA, double wB,
-               float4 rho, double* __restrict__ part) {
+               const float4* __restrict__ colB, int64_t bstride, int ntB, double wA,
+               double wB, float4 rho, double* __restrict__ part) {
   constexpr int NT = 128;
   __shared__ float4 sj[3 * kMT];
   const int t = threadIdx.x;
@@ -105,6 +105,7 @@ __global__ void __launch_bounds__(128)
   const int tile_e = (int)(((int64_t)(blockIdx.z + 1) * nt) / S);
   const float4* rs = rows + b * rstride;
   const float4* ca = colA + b * astride;
+  const float4* cb = colB + b * bstride;
   const int64_t i0 = (int64_t)blockIdx.x * (NT * R) + t;
 
   float2 nu[R][6];
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(128)
   for (int tile = tile_b; tile < tile_e; ++tile) {
     const bool inA = tile < ntA;
     const float4* src = inA ? ca + (int64_t)tile * (3 * kMT)
-                            : colB + (int64_t)(tile - ntA) * (3 * kMT);
+                            : cb + (int64_t)(tile - ntA) * (3 * kMT);
     __syncthreads();
     for (int q = t; q < 3 * kMT; q += NT) sj[q] = src[q];
     __syncthreads();
@@ -297,10 +298,11 @@ __global__ void k_mmd_cross_finish(const double* __restrict__ cross, int64_t set
   loss[q] = kxx[b] + kyy[t] - wxy * s;
 }
 
-// loss_b = base + wrow sum_{i<n} sum_chunks (S0A + cB S0B), one block per set
+// loss_b = base[b * base_stride] + wrow sum_{i<n} sum_chunks (S0A + cB S0B),
+// one block per set
 __global__ void __launch_bounds__(256)
     k_mmd_finish(const double* __restrict__ part, int S, int64_t npad_r, int64_t n,
-                 double wrow, double cB, const double* __restrict__ base,
+                 double wrow, double cB, const double* __restrict__ base, int base_stride,
                  double* __restrict__ loss) {
   __shared__ double sh[256];
   const int64_t b = blockIdx.x;
@@ -319,24 +321,27 @@ __global__ void __launch_bounds__(256)
     if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) loss[b] = (base ? *base : 0.0) + wrow * sh[0];
+  if (threadIdx.x == 0) loss[b] = (base ? base[b * base_stride] : 0.0) + wrow * sh[0];
 }
 
-// dMMD^2/dq for set 0: gscale_d = 4 ln2 (1/n) f_d; out 3 x n each
+// dMMD^2/dq of set b = blockIdx.y: gscale_d = 4 ln2 (1/n) f_d; out 3 x ld
+// each, set b in columns b n .. b n + n - 1
 __global__ void k_mmd_grad(const double* __restrict__ part, int S, int64_t npad_r,
-                           int64_t n, Standardise Sd, double g0,
+                           int64_t n, int64_t ld, Standardise Sd, double g0,
                            double* __restrict__ xbar, double* __restrict__ vbar) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t b = blockIdx.y;
   if (i >= n) return;
+  const double* pb = part + b * S * 8 * npad_r;
 #pragma unroll
   for (int d = 0; d < 6; ++d) {
     double s = 0.0;
-    for (int q = 0; q < S; ++q) s += part[((int64_t)q * 8 + 2 + d) * npad_r + i];
+    for (int q = 0; q < S; ++q) s += pb[((int64_t)q * 8 + 2 + d) * npad_r + i];
     const double g = g0 * Sd.f[d] * s;
     if (d < 3)
-      xbar[d * n + i] = g;
+      xbar[d * ld + b * n + i] = g;
     else
-      vbar[(d - 3) * n + i] = g;
+      vbar[(d - 3) * ld + b * n + i] = g;
   }
 }
 
@@ -397,6 +402,7 @@ struct nbody_mmd {
   double* stats = nullptr;  // [12]
   double* gx = nullptr;     // gradient scratch [3][n]
   double* gv = nullptr;
+  int64_t tsets = 1;        // targets: 1, or one per set (mmd_create_multi)
 };
 
 namespace {
@@ -433,29 +439,31 @@ void free_mmd(nbody_mmd* h) {
 template <int NS>
 cudaError_t rows_ns(int R, dim3 grid, const float4* rows, int64_t rstride, int64_t npad_r,
                     const float4* colA, int64_t astride, int ntA, const float4* colB,
-                    int ntB, double wA, double wB, float4 rho, double* part, cudaStream_t s) {
+                    int64_t bstride, int ntB, double wA, double wB, float4 rho, double* part,
+                    cudaStream_t s) {
   if (R == 2)
     nb::k_mmd_rows<2, NS><<<grid, 128, 0, s>>>(rows, rstride, npad_r, colA, astride, ntA,
-                                               colB, ntB, wA, wB, rho, part);
+                                               colB, bstride, ntB, wA, wB, rho, part);
   else
     nb::k_mmd_rows<1, NS><<<grid, 128, 0, s>>>(rows, rstride, npad_r, colA, astride, ntA,
-                                               colB, ntB, wA, wB, rho, part);
+                                               colB, bstride, ntB, wA, wB, rho, part);
   nb::count_launch();
   return cudaGetLastError();
 }
 
-// Row sums of `sets` sets of npad_r rows against ntA + ntB column tiles.
+// Row sums of `sets` sets of npad_r rows against ntA + ntB column tiles
+// (column set B of set b at colB + b * bstride).
 cudaError_t launch_rows(const nbody_mmd* h, int64_t sets, const float4* rows,
                         int64_t rstride, int64_t npad_r, const float4* colA,
                         int64_t astride, int ntA, const float4* colB, int ntB, double wA,
-                        double wB, int S, double* part) {
+                        double wB, int S, double* part, int64_t bstride = 0) {
   const int R = npad_r >= 256 ? 2 : 1;
   dim3 grid((unsigned)(npad_r / (128 * R)), (unsigned)sets, (unsigned)S);
   switch (h->ns) {
-    case 1: return rows_ns<1>(R, grid, rows, rstride, npad_r, colA, astride, ntA, colB, ntB, wA, wB, h->rho, part, h->s);
-    case 2: return rows_ns<2>(R, grid, rows, rstride, npad_r, colA, astride, ntA, colB, ntB, wA, wB, h->rho, part, h->s);
-    case 3: return rows_ns<3>(R, grid, rows, rstride, npad_r, colA, astride, ntA, colB, ntB, wA, wB, h->rho, part, h->s);
-    default: return rows_ns<4>(R, grid, rows, rstride, npad_r, colA, astride, ntA, colB, ntB, wA, wB, h->rho, part, h->s);
+    case 1: return rows_ns<1>(R, grid, rows, rstride, npad_r, colA, astride, ntA, colB, bstride, ntB, wA, wB, h->rho, part, h->s);
+    case 2: return rows_ns<2>(R, grid, rows, rstride, npad_r, colA, astride, ntA, colB, bstride, ntB, wA, wB, h->rho, part, h->s);
+    case 3: return rows_ns<3>(R, grid, rows, rstride, npad_r, colA, astride, ntA, colB, bstride, ntB, wA, wB, h->rho, part, h->s);
+    default: return rows_ns<4>(R, grid, rows, rstride, npad_r, colA, astride, ntA, colB, bstride, ntB, wA, wB, h->rho, part, h->s);
   }
 }
 
@@ -535,6 +543,27 @@ int device_view(const double* p, size_t count, double** tmp, const double** out,
   return NBODY_OK;
 }
 
+// sigma_0 is the smallest bandwidth (first), the others follow in the
+// caller's order; rho_l = sigma_0^2 / sigma_l^2 <= 1
+void set_bandwidths(nbody_mmd* h, int n_sigma, const double* sigma, double smin) {
+  h->ns = n_sigma;
+  for (int l = 0; l < n_sigma; ++l) h->sigma[l] = sigma[l];
+  double sg[4];
+  int k = 0, idx0 = 0;
+  for (int l = 0; l < n_sigma; ++l)
+    if (sigma[l] == smin) {
+      idx0 = l;
+      break;
+    }
+  sg[k++] = sigma[idx0];
+  for (int l = 0; l < n_sigma; ++l)
+    if (l != idx0) sg[k++] = sigma[l];
+  float r[4] = {1.f, 1.f, 1.f, 1.f};
+  for (int l = 1; l < n_sigma; ++l) r[l] = (float)((sg[0] * sg[0]) / (sg[l] * sg[l]));
+  h->rho = make_float4(r[0], r[1], r[2], r[3]);
+  h->c0 = 1.4426950408889634 / (2.0 * sg[0] * sg[0]);  // log2(e) / (2 sigma_0^2)
+}
+
 // The target (h->m points, device arrays): its standardisation (mean and
 // standard deviation, or the caller's scale), its staged points and its own
 // term Kyy = (1/m^2) sum k(y, y').  No allocation beyond the evaluator's
@@ -564,7 +593,7 @@ int set_target(nbody_mmd* h, const double* dx, const double* dv, const double* s
   MCK(launch_rows(h, 1, h->ys, 0, h->mpad, h->ys, 0, nty, nullptr, 0, 1.0 / (double)m, 0.0,
                   Sy, h->part));
   nb::k_mmd_finish<<<1, 256, 0, h->s>>>(h->part, Sy, h->mpad, m, 1.0 / (double)m, 0.0,
-                                        nullptr, h->kyy);
+                                        nullptr, 0, h->kyy);
   nb::count_launch();
   MCK(cudaGetLastError());
   MCK(cudaStreamSynchronize(h->s));
@@ -594,6 +623,101 @@ int mmd_retarget(nbody_mmd* h, int64_t n, int64_t m, const double* tx, const dou
     for (int d = 0; d < 6; ++d)
       if (!(scale_or_null[d] > 0.0) || !std::isfinite(scale_or_null[d])) return NBODY_EINVAL;
   return set_target(h, tx, tv, scale_or_null);
+}
+
+int mmd_create_multi(nbody_mmd** out, int64_t n, int64_t sets, int64_t m, const double* ty,
+                     const double* tv, const double* scale, int n_sigma, const double* sigma,
+                     cudaStream_t s) {
+  if (!out || n < 1 || sets < 1 || sets > 65535 || m < 1 || !ty || !tv || !scale || !sigma ||
+      n_sigma < 1 || n_sigma > kMaxSigma)
+    return NBODY_EINVAL;
+  *out = nullptr;
+  double smin = sigma[0];
+  for (int l = 0; l < n_sigma; ++l) {
+    if (!(sigma[l] > 0.0) || !std::isfinite(sigma[l])) return NBODY_EINVAL;
+    smin = std::fmin(smin, sigma[l]);
+  }
+  for (int d = 0; d < 6; ++d)
+    if (!(scale[d] > 0.0) || !std::isfinite(scale[d])) return NBODY_EINVAL;
+  nbody_mmd* h = new (std::nothrow) nbody_mmd();
+  if (!h) return NBODY_ENOMEM;
+  h->s = s;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
+  h->n = n;
+  h->m = m;
+  h->max_sets = sets;
+  h->tsets = sets;
+  h->npad = pad_points(n);
+  h->mpad = pad_points(m);
+  set_bandwidths(h, n_sigma, sigma, smin);
+  const int nrt = (int)(h->mpad / (128 * rows_per_thread(h->mpad)));
+  int rc = malloc_dev(&h->xs, (size_t)sets * 3 * (h->npad / 2));
+  if (!rc) rc = malloc_dev(&h->ys, (size_t)sets * 3 * (h->mpad / 2));
+  if (!rc) rc = malloc_dev(&h->kyy, (size_t)sets);
+  if (!rc) rc = malloc_dev(&h->loss, (size_t)sets);
+  if (!rc) rc = malloc_dev(&h->stats, 12);
+  if (!rc) rc = ensure_part(h, sets * nrt);
+  auto fail = [&](int code) {
+    cudaStreamSynchronize(h->s);
+    free_mmd(h);
+    delete h;
+    return code;
+  };
+  if (rc) return fail(rc);
+  // units: the caller's scale; the origin: the first target's mean
+  k_cloud_stats<<<1, 256, 0, s>>>(ty, tv, m, h->stats);
+  count_launch();
+  double stt[12];
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(stt, h->stats, sizeof(stt), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return fail(NBODY_ECUDA);
+  const double sc0 = std::sqrt(h->c0);
+  for (int d = 0; d < 6; ++d) {
+    h->st.mu[d] = stt[d];
+    h->st.f[d] = sc0 / scale[d];
+  }
+  // every target's own term (1/m^2) sum k(y, y')
+  const int64_t ystr = 3 * (h->mpad / 2);
+  if ((rc = stage(h, ty, tv, sets * m, m, h->mpad, sets, h->ys))) return fail(rc);
+  if (launch_sum(h, sets, 1, h->ys, ystr, h->mpad, m, h->ys, ystr, 0,
+                 (int)(h->mpad / kMPts), h->part) != cudaSuccess)
+    return fail(NBODY_ECUDA);
+  k_mmd_block_total<<<(unsigned)((sets + 255) / 256), 256, 0, s>>>(
+      h->part, sets, nrt, 1.0 / ((double)m * (double)m), h->kyy);
+  count_launch();
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+    return fail(NBODY_ECUDA);
+  *out = h;
+  return NBODY_OK;
+}
+
+int mmd_eval_multi(nbody_mmd* h, const double* x, const double* v, double* loss, double* xbar,
+                   double* vbar) {
+  if (!h || h->tsets != h->max_sets || !x || !v || !loss) return NBODY_EINVAL;
+  const int64_t sets = h->tsets, n = h->n;
+  const int ntx = (int)(h->npad / kMPts), nty = (int)(h->mpad / kMPts);
+  const int S = chunks_for(h, sets, h->npad, ntx + nty);
+  int rc = ensure_part(h, sets * S * 8 * h->npad);
+  if (!rc) rc = stage(h, x, v, sets * n, n, h->npad, sets, h->xs);
+  if (rc) return rc;
+  const int64_t xstr = 3 * (h->npad / 2), ystr = 3 * (h->mpad / 2);
+  MCK(launch_rows(h, sets, h->xs, xstr, h->npad, h->xs, xstr, ntx, h->ys, nty,
+                  1.0 / (double)n, -1.0 / (double)h->m, S, h->part, ystr));
+  k_mmd_finish<<<(unsigned)sets, 256, 0, h->s>>>(h->part, S, h->npad, n, 1.0 / (double)n, 2.0,
+                                                 h->kyy, 1, loss);
+  count_launch();
+  MCK(cudaGetLastError());
+  if (xbar && vbar) {
+    const double g0 = 4.0 * 0.6931471805599453 / (double)n;  // 4 ln2 / n
+    dim3 grid((unsigned)((n + 255) / 256), (unsigned)sets);
+    k_mmd_grad<<<grid, 256, 0, h->s>>>(h->part, S, h->npad, n, sets * n, h->st, g0, xbar, vbar);
+    count_launch();
+    MCK(cudaGetLastError());
+  }
+  return NBODY_OK;
 }
 
 }  // namespace nb
@@ -633,23 +757,7 @@ int nbody_mmd_create(nbody_mmd** out, int64_t n, int64_t max_sets, int64_t m,
   h->max_sets = max_sets;
   h->npad = nb::pad_points(n);
   h->mpad = nb::pad_points(m);
-  h->ns = n_sigma;
-  for (int l = 0; l < n_sigma; ++l) h->sigma[l] = sigma[l];
-  // sigma_0 is the smallest bandwidth (first), the others follow in the
-  // caller's order; rho_l = sigma_0^2 / sigma_l^2 <= 1
-  {
-    double sg[4];
-    int k = 0, idx0 = 0;
-    for (int l = 0; l < n_sigma; ++l)
-      if (sigma[l] == smin) { idx0 = l; break; }
-    sg[k++] = sigma[idx0];
-    for (int l = 0; l < n_sigma; ++l)
-      if (l != idx0) sg[k++] = sigma[l];
-    float r[4] = {1.f, 1.f, 1.f, 1.f};
-    for (int l = 1; l < n_sigma; ++l) r[l] = (float)((sg[0] * sg[0]) / (sg[l] * sg[l]));
-    h->rho = make_float4(r[0], r[1], r[2], r[3]);
-    h->c0 = 1.4426950408889634 / (2.0 * sg[0] * sg[0]);  // log2(e) / (2 sigma_0^2)
-  }
+  set_bandwidths(h, n_sigma, sigma, smin);
   int rc = NBODY_OK;
   double* tmpx = nullptr;
   double* tmpv = nullptr;
@@ -705,7 +813,8 @@ int nbody_mmd_eval_batch(nbody_mmd* h, int64_t sets, const double* x, const doub
     rc = NBODY_ECUDA;
   if (!rc) {
     nb::k_mmd_finish<<<(unsigned)sets, 256, 0, h->s>>>(h->part, S, h->npad, h->n,
-                                                       1.0 / (double)h->n, 2.0, h->kyy, h->loss);
+                                                       1.0 / (double)h->n, 2.0, h->kyy, 0,
+                                                       h->loss);
     nb::count_launch();
     if (cudaGetLastError() != cudaSuccess) rc = NBODY_ECUDA;
   }
@@ -748,7 +857,7 @@ int nbody_mmd_eval(nbody_mmd* h, const double* x, const double* v, double* loss,
     rc = NBODY_ECUDA;
   if (!rc) {
     nb::k_mmd_finish<<<1, 256, 0, h->s>>>(h->part, S, h->npad, h->n, 1.0 / (double)h->n, 2.0,
-                                          h->kyy, h->loss);
+                                          h->kyy, 0, h->loss);
     nb::count_launch();
     if (cudaGetLastError() != cudaSuccess) rc = NBODY_ECUDA;
   }
@@ -756,7 +865,7 @@ int nbody_mmd_eval(nbody_mmd* h, const double* x, const double* v, double* loss,
     // gradients into the context's buffers, then out to the caller's
     const double g0 = 4.0 * 0.6931471805599453 / (double)h->n;  // 4 ln2 / n
     nb::k_mmd_grad<<<(unsigned)((h->n + 255) / 256), 256, 0, h->s>>>(
-        h->part, S, h->npad, h->n, h->st, g0, h->gx, h->gv);
+        h->part, S, h->npad, h->n, h->n, h->st, g0, h->gx, h->gv);
     nb::count_launch();
     if (cudaGetLastError() != cudaSuccess) rc = NBODY_ECUDA;
     if (!rc && xbar &&

@@ -64,6 +64,17 @@ namespace nb {
 // (device arrays); NBODY_ESTATE when it does not fit (mmd.cu).
 int mmd_retarget(nbody_mmd* h, int64_t n, int64_t m, const double* tx, const double* tv,
                  const double* scale_or_null, int n_sigma, const double* sigma);
+// Evaluator of `sets` clouds of n points, each against its own target of m
+// points (ty, tv: device, 3 x sets m, target b in columns b m ..), in the
+// caller's units (scale: 6 standard deviations); the targets' own terms are
+// computed here (mmd.cu).  Destroy with nbody_mmd_destroy.
+int mmd_create_multi(nbody_mmd** out, int64_t n, int64_t sets, int64_t m, const double* ty,
+                     const double* tv, const double* scale, int n_sigma, const double* sigma,
+                     cudaStream_t s);
+// MMD^2 of every set against its target into loss (device, sets) and, when
+// xbar and vbar (device, 3 x sets n) are given, its gradient; stream-ordered.
+int mmd_eval_multi(nbody_mmd* h, const double* x, const double* v, double* loss, double* xbar,
+                   double* vbar);
 
 // ---- pair kernels (pair_force.cu, pair_vjp.cu) ----
 enum PairVariant : int { kTile = 0, kWarp = 1 };

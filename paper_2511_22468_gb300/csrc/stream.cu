@@ -346,6 +346,110 @@ __global__ void k_theta_bar(double tb0, double tb1, double tb2, double tb3,
 
 unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// ------------------------------------------------------- batched pipeline
+// orbit parameters of member b: theta_b = (t_end, M_prog, M_NFW, M_MN)
+__device__ __forceinline__ DevParams member_orbit_params(const DevParams& P0,
+                                                         const double* theta, int64_t ns) {
+  DevParams P = P0;
+  P.dt = -theta[0] / (double)ns;
+  P.nfw_GM = P0.G * theta[2];
+  P.mn_GM = P0.G * theta[3];
+  return P;
+}
+
+// backward orbits of every member, one thread each, with the trajectory
+// stored (the arithmetic of k_orbit): member b's x_0..x_ns at
+// ox + b 3 (ns + 1), half-step velocities at ovh + b 3 ns, end point g6[b]
+__global__ void k_orbit_batch_tape(DevParams P0, double X0, double X1, double X2, double V0,
+                                   double V1, double V2, int64_t ns,
+                                   const double* __restrict__ theta, int64_t count,
+                                   double* __restrict__ ox, double* __restrict__ ovh,
+                                   double* __restrict__ g6) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count) return;
+  const DevParams P = member_orbit_params(P0, theta + 4 * b, ns);
+  double* xo = ox + b * 3 * (ns + 1);
+  double* vo = ovh + b * 3 * ns;
+  double x[3] = {X0, X1, X2}, v[3] = {V0, V1, V2};
+  ExtUnit e;
+  nb::ext_unit(P, x[0], x[1], x[2], e);
+  for (int d = 0; d < 3; ++d) xo[d] = x[d];
+  for (int64_t k = 0; k < ns; ++k) {
+    for (int d = 0; d < 3; ++d) {
+      v[d] += 0.5 * P.dt * (P.nfw_GM * e.n[d] + P.mn_GM * e.d[d] + P.bulge_GM * e.b[d]);
+      vo[3 * k + d] = v[d];
+      x[d] += P.dt * v[d];
+      xo[3 * (k + 1) + d] = x[d];
+    }
+    nb::ext_unit(P, x[0], x[1], x[2], e);
+    for (int d = 0; d < 3; ++d)
+      v[d] += 0.5 * P.dt * (P.nfw_GM * e.n[d] + P.mn_GM * e.d[d] + P.bulge_GM * e.b[d]);
+  }
+  for (int d = 0; d < 3; ++d) {
+    g6[6 * b + d] = x[d];
+    g6[6 * b + 3 + d] = v[d];
+  }
+}
+
+// per member b (one block each): sums of x0bar, v0bar and of v0bar . vhat
+// over its particles (columns b n .. of 3 x count n) into red[b][0..6]
+__global__ void __launch_bounds__(256)
+    k_ic_vjp_batch(const double* __restrict__ x0b, const double* __restrict__ v0b,
+                   const double* __restrict__ vh, int64_t n, int64_t count,
+                   double* __restrict__ red) {
+  const int64_t b = blockIdx.x, ld = n * count;
+  double val[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+    for (int d = 0; d < 3; ++d) {
+      val[d] += x0b[d * ld + b * n + i];
+      val[3 + d] += v0b[d * ld + b * n + i];
+      val[6] += v0b[d * ld + b * n + i] * vh[d * n + i];
+    }
+  nb::block_accumulate<7>(val, red);
+}
+
+// reverse of every member's backward orbit (the arithmetic of k_orbit_vjp)
+// from the cotangents red[b][0..5] of its end point: orb[b] = (dL/d dt_orbit,
+// dL/dM_NFW, dL/dM_MN), orbit part
+__global__ void k_orbit_vjp_batch(DevParams P0, const double* __restrict__ ox,
+                                  const double* __restrict__ ovh, int64_t ns,
+                                  const double* __restrict__ theta, int64_t count,
+                                  const double* __restrict__ red, double* __restrict__ orb) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count) return;
+  const DevParams P = member_orbit_params(P0, theta + 4 * b, ns);
+  const double* xo = ox + b * 3 * (ns + 1);
+  const double* vo = ovh + b * 3 * ns;
+  const double* cot = red + 7 * b;
+  double xb[3] = {cot[0], cot[1], cot[2]};
+  double vb[3] = {cot[3], cot[4], cot[5]};
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int64_t k = ns - 1; k >= 0; --k) {
+    orbit_kick_adj(P, &xo[3 * (k + 1)], vb, xb, acc);  // closing kick
+    for (int d = 0; d < 3; ++d) acc[0] += xb[d] * vo[3 * k + d];
+    for (int d = 0; d < 3; ++d) vb[d] += P.dt * xb[d];  // drift
+    orbit_kick_adj(P, &xo[3 * k], vb, xb, acc);        // opening kick
+  }
+  for (int q = 0; q < 3; ++q) orb[3 * b + q] = acc[q];
+}
+
+// dL/dtheta of every member (the arithmetic of k_theta_bar) from its n-body
+// parameter gradient tb[b][0..3] (dt, mass scale, M_NFW, M_MN), its
+// initial-state sums red[b] and its orbit part orb[b]
+__global__ void k_theta_bar_batch(const double* __restrict__ tb, int64_t ns, double G,
+                                  double a, const double* __restrict__ theta, int64_t count,
+                                  const double* __restrict__ red,
+                                  const double* __restrict__ orb, double* __restrict__ out) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count) return;
+  const double* t = tb + 8 * b;
+  const double M = theta[4 * b + 1];
+  out[4 * b] = t[0] / (double)ns - orb[3 * b] / (double)ns;
+  out[4 * b + 1] = 0.5 * sqrt(G / (a * M)) * red[7 * b + 6] + t[1] / M;
+  out[4 * b + 2] = t[2] + orb[3 * b + 1];
+  out[4 * b + 3] = t[3] + orb[3 * b + 2];
+}
+
 }  // namespace
 
 struct nbody_stream {
@@ -366,6 +470,24 @@ struct nbody_stream {
   int nblk = 0;
   double theta[4] = {0, 0, 0, 0};
   bool have_forward = false;
+};
+
+// The pipeline for `count` parameter vectors at once (the gradient
+// refinement of many grid points or bootstrap realisations, Sec. 2.2.1):
+// one batch context of count members of n particles, each member scored by
+// MMD^2 against its own target cloud.
+struct nbody_stream_batch {
+  nbody_stream_cfg cfg{};
+  cudaStream_t s = nullptr;
+  int64_t n = 0, count = 0;
+  nbody_ctx* ctx = nullptr;   // batch of count members, trajectories recorded
+  nbody_mmd* mmd = nullptr;   // one target per member
+  bool tuned = false;
+  double *xhat = nullptr, *vhat = nullptr, *theta = nullptr;
+  double *x0 = nullptr, *v0 = nullptr, *m = nullptr, *xT = nullptr, *vT = nullptr;
+  double *xbar = nullptr, *vbar = nullptr, *x0bar = nullptr, *v0bar = nullptr;
+  double *ox = nullptr, *ovh = nullptr, *g6 = nullptr;
+  double *loss = nullptr, *tb = nullptr, *red = nullptr, *orb = nullptr, *out = nullptr;
 };
 
 namespace {
@@ -403,6 +525,15 @@ void free_stream(nbody_stream* s) {
   sfree(s->w); sfree(s->rho); sfree(s->target); sfree(s->rbar); sfree(s->loss);
   sfree(s->xbar); sfree(s->x0bar); sfree(s->v0bar); sfree(s->blk); sfree(s->red);
   sfree(s->orb); sfree(s->tbar);
+}
+
+void free_stream_batch(nbody_stream_batch* s) {
+  if (s->ctx) nbody_destroy(s->ctx);
+  if (s->mmd) nbody_mmd_destroy(s->mmd);
+  for (double** p : {&s->xhat, &s->vhat, &s->theta, &s->x0, &s->v0, &s->m, &s->xT, &s->vT,
+                     &s->xbar, &s->vbar, &s->x0bar, &s->v0bar, &s->ox, &s->ovh, &s->g6,
+                     &s->loss, &s->tb, &s->red, &s->orb, &s->out})
+    sfree(*p);
 }
 
 void unit3(const double* a, double* out) {
@@ -845,6 +976,175 @@ int nbody_stream_grad(nbody_stream* s, double theta_bar[4]) {
   for (int k = 0; k < 4; ++k)
     if (!std::isfinite(theta_bar[k])) return NBODY_ENAN;
   return NBODY_OK;
+}
+
+int nbody_stream_batch_create(nbody_stream_batch** out, const nbody_stream_cfg* cfg,
+                              int64_t count, const double* xhat, const double* vhat, int64_t m,
+                              const double* tx, const double* tv, const double* scale,
+                              int n_sigma, const double* sigma, void* cuda_stream) {
+  if (!out || !cfg || !xhat || !vhat || !tx || !tv || !scale || !sigma) return NBODY_EINVAL;
+  *out = nullptr;
+  const nbody_stream_cfg& c = *cfg;
+  if (c.n < 1 || c.n_steps < 1 || !(c.eps > 0.0) || !(c.a_prog > 0.0) || !(c.nfw_rs > 0.0) ||
+      c.mn_a < 0.0 || c.mn_b < 0.0 || count < 1 || count > 65535 || m < 1)
+    return NBODY_EINVAL;
+  nbody_stream_batch* s = new (std::nothrow) nbody_stream_batch();
+  if (!s) return NBODY_ENOMEM;
+  s->cfg = c;
+  s->s = (cudaStream_t)cuda_stream;
+  s->n = c.n;
+  s->count = count;
+  const size_t n3 = 3 * (size_t)c.n, all3 = n3 * (size_t)count, ns = (size_t)c.n_steps;
+  std::vector<nbody_params> prm((size_t)count);
+  for (auto& p : prm) {
+    p = nbody_params{};
+    p.G = c.G;
+    p.eps = c.eps;
+    p.dt = 1.0;
+    p.checkpoint_every = 1;  // record the trajectories for the reverse sweep
+    p.ext_flags = NBODY_EXT_NFW | NBODY_EXT_MN;
+    p.center_mode = NBODY_CENTER_GUIDE;
+    p.nfw_M = 1.0;
+    p.nfw_rs = c.nfw_rs;
+    p.mn_M = 1.0;
+    p.mn_a = c.mn_a;
+    p.mn_b = c.mn_b;
+  }
+  std::vector<int64_t> offs((size_t)count + 1);
+  for (int64_t b = 0; b <= count; ++b) offs[(size_t)b] = b * c.n;
+  int rc = nbody_create_batch(&s->ctx, (int)count, offs.data(), prm.data(), cuda_stream);
+  double *dtx = nullptr, *dtv = nullptr;
+  const size_t tm3 = 3 * (size_t)m * (size_t)count;
+  if (!rc) rc = salloc(&s->xhat, n3);
+  if (!rc) rc = salloc(&s->vhat, n3);
+  if (!rc) rc = salloc(&s->theta, 4 * (size_t)count);
+  for (double** p : {&s->x0, &s->v0, &s->xT, &s->vT, &s->xbar, &s->vbar, &s->x0bar, &s->v0bar})
+    if (!rc) rc = salloc(p, all3);
+  if (!rc) rc = salloc(&s->m, n3 / 3 * (size_t)count);
+  if (!rc) rc = salloc(&s->ox, 3 * (ns + 1) * (size_t)count);
+  if (!rc) rc = salloc(&s->ovh, 3 * ns * (size_t)count);
+  if (!rc) rc = salloc(&s->g6, 6 * (size_t)count);
+  if (!rc) rc = salloc(&s->loss, (size_t)count);
+  if (!rc) rc = salloc(&s->tb, 8 * (size_t)count);
+  if (!rc) rc = salloc(&s->red, 7 * (size_t)count);
+  if (!rc) rc = salloc(&s->orb, 3 * (size_t)count);
+  if (!rc) rc = salloc(&s->out, 4 * (size_t)count);
+  if (!rc) rc = salloc(&dtx, tm3);
+  if (!rc) rc = salloc(&dtv, tm3);
+  if (!rc && (cudaMemcpyAsync(s->xhat, xhat, n3 * sizeof(double), cudaMemcpyDefault, s->s) ||
+              cudaMemcpyAsync(s->vhat, vhat, n3 * sizeof(double), cudaMemcpyDefault, s->s) ||
+              cudaMemcpyAsync(dtx, tx, tm3 * sizeof(double), cudaMemcpyDefault, s->s) ||
+              cudaMemcpyAsync(dtv, tv, tm3 * sizeof(double), cudaMemcpyDefault, s->s)))
+    rc = NBODY_ECUDA;
+  if (!rc) rc = nb::mmd_create_multi(&s->mmd, c.n, count, m, dtx, dtv, scale, n_sigma, sigma, s->s);
+  cudaStreamSynchronize(s->s);
+  sfree(dtx);
+  sfree(dtv);
+  if (rc) {
+    free_stream_batch(s);
+    delete s;
+    return rc;
+  }
+  *out = s;
+  return NBODY_OK;
+}
+
+int nbody_stream_batch_loss_grad(nbody_stream_batch* s, const double* thetas, double* losses,
+                                 double* theta_bars) {
+  if (!s || !thetas || !losses) return NBODY_EINVAL;
+  const nbody_stream_cfg& c = s->cfg;
+  const int64_t n = s->n, ns = c.n_steps, count = s->count;
+  std::vector<double> th(4 * (size_t)count);
+  SCK(cudaMemcpyAsync(th.data(), thetas, th.size() * sizeof(double), cudaMemcpyDefault, s->s));
+  SCK(cudaStreamSynchronize(s->s));
+  for (double t : th)
+    if (!(t > 0.0) || !std::isfinite(t)) return NBODY_EINVAL;
+  SCK(cudaMemcpyAsync(s->theta, th.data(), th.size() * sizeof(double), cudaMemcpyHostToDevice,
+                      s->s));
+  // 1-2. backward orbits (kept for their adjoint) and Plummer spheres
+  DevParams P0{};
+  P0.G = c.G;
+  P0.ext = NBODY_EXT_NFW | NBODY_EXT_MN;
+  P0.nfw_rs = c.nfw_rs;
+  P0.mn_a = c.mn_a;
+  P0.mn_b = c.mn_b;
+  k_orbit_batch_tape<<<blocks_for(count, 64), 64, 0, s->s>>>(
+      P0, c.X0[0], c.X0[1], c.X0[2], c.V0[0], c.V0[1], c.V0[2], ns, s->theta, count, s->ox,
+      s->ovh, s->g6);
+  nb::count_launch();
+  SCK(cudaGetLastError());
+  k_ic_batch<<<blocks_for(n * count, 256), 256, 0, s->s>>>(s->xhat, s->vhat, s->g6, s->theta,
+                                                           c.a_prog, c.G, n, count, s->x0,
+                                                           s->v0, s->m);
+  nb::count_launch();
+  SCK(cudaGetLastError());
+  std::vector<double> g6(6 * (size_t)count);
+  SCK(cudaMemcpyAsync(g6.data(), s->g6, g6.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                      s->s));
+  SCK(cudaStreamSynchronize(s->s));
+  // 3. the n-body runs, every member with its own step, potential and centre
+  std::vector<nbody_params> prm((size_t)count);
+  for (int64_t b = 0; b < count; ++b) {
+    nbody_params& p = prm[(size_t)b];
+    p = nbody_params{};
+    p.G = c.G;
+    p.eps = c.eps;
+    p.dt = th[4 * b] / (double)ns;
+    p.checkpoint_every = 1;
+    p.ext_flags = NBODY_EXT_NFW | NBODY_EXT_MN;
+    p.center_mode = NBODY_CENTER_GUIDE;
+    p.nfw_M = th[4 * b + 2];
+    p.nfw_rs = c.nfw_rs;
+    p.mn_M = th[4 * b + 3];
+    p.mn_a = c.mn_a;
+    p.mn_b = c.mn_b;
+    for (int k = 0; k < 3; ++k) {
+      p.center[k] = g6[6 * b + k];
+      p.center_vel[k] = g6[6 * b + 3 + k];
+    }
+  }
+  int rc;
+  if ((rc = nbody_set_params(s->ctx, prm.data()))) return rc;
+  if ((rc = nbody_set_state(s->ctx, s->x0, s->v0, s->m))) return rc;
+  if (!s->tuned) {  // launch shape of the pair kernels, once, on the first state
+    if ((rc = nbody_autotune(s->ctx, 2, nullptr, nullptr))) return rc;
+    s->tuned = true;
+  }
+  if ((rc = nbody_integrate(s->ctx, ns, s->xT, s->vT))) return rc;
+  // 4. MMD^2 of every member against its target, and its gradient
+  if ((rc = nb::mmd_eval_multi(s->mmd, s->xT, s->vT, s->loss, theta_bars ? s->xbar : nullptr,
+                               theta_bars ? s->vbar : nullptr)))
+    return rc;
+  if (theta_bars) {
+    // 5. reverse: n-body runs, Plummer shifts, backward orbits
+    if ((rc = nbody_vjp_batch(s->ctx, s->xbar, s->vbar, s->x0bar, s->v0bar, s->tb))) return rc;
+    SCK(cudaMemsetAsync(s->red, 0, 7 * (size_t)count * sizeof(double), s->s));
+    k_ic_vjp_batch<<<(unsigned)count, 256, 0, s->s>>>(s->x0bar, s->v0bar, s->vhat, n, count,
+                                                      s->red);
+    nb::count_launch();
+    SCK(cudaGetLastError());
+    k_orbit_vjp_batch<<<blocks_for(count, 64), 64, 0, s->s>>>(P0, s->ox, s->ovh, ns, s->theta,
+                                                              count, s->red, s->orb);
+    nb::count_launch();
+    SCK(cudaGetLastError());
+    k_theta_bar_batch<<<blocks_for(count, 64), 64, 0, s->s>>>(s->tb, ns, c.G, c.a_prog,
+                                                              s->theta, count, s->red, s->orb,
+                                                              s->out);
+    nb::count_launch();
+    SCK(cudaGetLastError());
+    SCK(cudaMemcpyAsync(theta_bars, s->out, 4 * (size_t)count * sizeof(double),
+                        cudaMemcpyDefault, s->s));
+  }
+  SCK(cudaMemcpyAsync(losses, s->loss, (size_t)count * sizeof(double), cudaMemcpyDefault, s->s));
+  SCK(cudaStreamSynchronize(s->s));
+  return NBODY_OK;
+}
+
+void nbody_stream_batch_destroy(nbody_stream_batch* s) {
+  if (!s) return;
+  cudaStreamSynchronize(s->s);
+  free_stream_batch(s);
+  delete s;
 }
 
 }  // extern "C"

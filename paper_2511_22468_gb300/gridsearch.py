@@ -21,7 +21,8 @@ paper's first inference method, Sec. 2.2.1 and Fig. 2).
     scores every cloud against every realisation (nbody_mmd_eval_cross),
     and the spread of the per-realisation best grid points is the
     bootstrap distribution.  --bootstrap-refine K adds the gradient
-    refinement for the first K realisations.
+    refinement for the first K realisations, many at once (one batched
+    pipeline whose members each compare with their own realisation).
 
 The paper's workload is 10^4 grid points of 1000 particles and 1000 steps;
 the default here keeps the stream workload's step (0.5 Myr), so 1000 steps
@@ -44,7 +45,8 @@ import torch
 from . import nbody as nb
 from .configs import C1
 from .inputs import perturbed_clouds, plummer_unit
-from .stream import StreamModel
+from .stream import StreamBatch, StreamModel
+from .surrogate import descend_batch
 
 
 def regular_grid(centre, width, per_dim):
@@ -165,7 +167,7 @@ KMS = 1.0227121650537077e-3   # 1 km/s in kpc/Myr
 def run(n=1000, steps=1000, t_end=500.0, per_dim=10, batch=1024, refine_iters=10,
         sigmas=(0.5, 1.0, 2.0), f_obs=(1.1, 0.9, 1.15, 0.85), width=0.3, seed=1,
         device="cuda:0", tuning=None, bootstrap=0, bootstrap_refine=0, sigma_frac=0.05,
-        sigma_x=None, sigma_v_kms=None):
+        sigma_x=None, sigma_v_kms=None, refine_batch=512):
     cfg = dataclasses.replace(C1, n=n, n_steps=steps, t_acc=float(t_end))
     centre = np.array(cfg.theta_true, float)
     theta_obs = centre * np.array(f_obs)
@@ -238,23 +240,23 @@ def run(n=1000, steps=1000, t_end=500.0, per_dim=10, batch=1024, refine_iters=10
                          "loss_trace": [r["loss"] for r in tr]}
         model.close()
     if reals is not None and bootstrap_refine > 0:
-        # gradient refinement of the first realisations, one after another
-        # (the pipeline takes each new target in place)
+        # gradient refinement of the first realisations, `refine_batch` at a
+        # time: one batched pipeline (every member against its own
+        # realisation) and one gradient call for all members per iteration
         rx, rv, bt = reals
         K = min(bootstrap_refine, bootstrap)
-        model = StreamModel(cfg, xh, vh, device=device)
-        out = []
+        est = np.empty((K, 4))
         t0 = time.perf_counter()
-        for r in range(K):
-            model.set_target_cloud(np.ascontiguousarray(rx[r].T), np.ascontiguousarray(rv[r].T),
-                                   sigmas, scale=obs_scale)
-            tr = refine(model, bt[r], centre, width, iters=refine_iters)
-            out.append(tr[int(np.argmin([q["loss"] for q in tr]))]["theta"])
+        for r0 in range(0, K, refine_batch):
+            r1 = min(K, r0 + refine_batch)
+            model = StreamBatch(cfg, xh, vh, rx[r0:r1], rv[r0:r1], sigmas, scale=obs_scale,
+                                device=device)
+            est[r0:r1], _, _ = descend_batch(model, bt[r0:r1], centre, width,
+                                             iters=refine_iters)
+            model.close()
         t_r = time.perf_counter() - t0
-        model.close()
-        est = np.array(out)
         res["bootstrap"]["refine"] = {
-            "realisations": K, "iters": refine_iters, "time_s": t_r,
+            "realisations": K, "iters": refine_iters, "batch": refine_batch, "time_s": t_r,
             "s_per_realisation": t_r / K, "theta_mean": est.mean(axis=0).tolist(),
             "theta_std": est.std(axis=0).tolist(),
             "rel_err_mean": (est / theta_obs[None, :] - 1.0).mean(axis=0).tolist()}
@@ -275,6 +277,8 @@ def main():
                     help="errors as a fraction of the observed spread per coordinate")
     ap.add_argument("--sigma-x", type=float, default=None, help="position error, kpc")
     ap.add_argument("--sigma-v", type=float, default=None, help="velocity error, km/s")
+    ap.add_argument("--refine-batch", type=int, default=512,
+                    help="realisations refined together (72 MB of trajectory each)")
     a = ap.parse_args()
     from . import build
     build.build()
@@ -282,7 +286,7 @@ def main():
                          batch=a.batch, refine_iters=a.refine, bootstrap=a.bootstrap,
                          bootstrap_refine=a.bootstrap_refine, sigma_frac=a.sigma_frac,
                          sigma_x=a.sigma_x,
-                         sigma_v_kms=a.sigma_v)))
+                         sigma_v_kms=a.sigma_v, refine_batch=a.refine_batch)))
 
 
 if __name__ == "__main__":

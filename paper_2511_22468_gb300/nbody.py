@@ -56,7 +56,8 @@ EXPORTED = ("nbody_create", "nbody_destroy", "nbody_set_params",
             "nbody_stream_set_target_cloud", "nbody_stream_initial_states",
             "nbody_ext_accel", "nbody_stream_autotune", "nbody_orbitfit_create", "nbody_orbitfit_eval",
             "nbody_orbitfit_lm", "nbody_orbitfit_fisher", "nbody_orbitfit_arc",
-            "nbody_orbitfit_destroy")
+            "nbody_orbitfit_destroy", "nbody_stream_batch_create",
+            "nbody_stream_batch_loss_grad", "nbody_stream_batch_destroy")
 
 NBODY_NTUNE = 8
 
@@ -162,6 +163,11 @@ def lib():
         L.nbody_stream_destroy.restype = None
         L.nbody_create_batch.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(i64), P, vp]
         L.nbody_vjp_batch.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.nbody_stream_batch_create.argtypes = [C.POINTER(vp), SC, i64, vp, vp, i64, vp, vp,
+                                                dp, C.c_int, dp, vp]
+        L.nbody_stream_batch_loss_grad.argtypes = [vp, vp, vp, vp]
+        L.nbody_stream_batch_destroy.argtypes = [vp]
+        L.nbody_stream_batch_destroy.restype = None
         L.nbody_autotune.argtypes = [vp, i64, C.POINTER(C.c_int), dp]
         L.nbody_set_tuning.argtypes = [vp, C.c_int]
         L.nbody_get_tuning.argtypes = [vp]
@@ -476,6 +482,35 @@ def nbody_vjp_batch(h, n_sims, xbar, vbar, x0bar=None, v0bar=None):
     _check(lib().nbody_vjp_batch(h, _ptr(xbar), _ptr(vbar), _ptr(x0bar), _ptr(v0bar),
                                  _ptr(tb)), "nbody_vjp_batch")
     return tb
+
+
+def nbody_stream_batch_create(cfg, count, xhat, vhat, m, tx, tv, scale, sigmas, stream=None):
+    """Pipeline of `count` parameter vectors, member b against target b
+    (tx, tv: (3, count m))."""
+    h = C.c_void_p()
+    n = cfg.n
+    sc = (C.c_double * 6)(*[float(v) for v in scale])
+    sg = (C.c_double * len(sigmas))(*[float(v) for v in sigmas])
+    _check(lib().nbody_stream_batch_create(C.byref(h), C.byref(cfg), count, _ptr(xhat, (3, n)),
+                                           _ptr(vhat, (3, n)), m, _ptr(tx, (3, count * m)),
+                                           _ptr(tv, (3, count * m)), sc, len(sigmas), sg,
+                                           _stream(stream)), "nbody_stream_batch_create")
+    return h
+
+
+def nbody_stream_batch_loss_grad(h, thetas, want_grad=True):
+    """(losses (count,), dL/dtheta (count, 4) or None) at thetas (count, 4)."""
+    import numpy as np
+    th = np.ascontiguousarray(np.asarray(thetas, np.float64))
+    L = np.empty(th.shape[0])
+    g = np.empty_like(th) if want_grad else None
+    _check(lib().nbody_stream_batch_loss_grad(h, _ptr(th), _ptr(L), _ptr(g)),
+           "nbody_stream_batch_loss_grad")
+    return L, g
+
+
+def nbody_stream_batch_destroy(h):
+    lib().nbody_stream_batch_destroy(h)
 
 
 def nbody_set_params_batch(h, params_list):

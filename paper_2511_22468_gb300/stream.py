@@ -111,6 +111,53 @@ class StreamModel:
         return L, np.array(self.grad())
 
 
+class StreamBatch:
+    """The point-cloud pipeline for many parameter vectors at once: member
+    b's final cloud against its own target cloud b (targets: (count, m, 3)
+    positions and velocities), all in the units `scale` (6 standard
+    deviations) with the bandwidths `sigmas`."""
+
+    def __init__(self, cfg, xhat, vhat, targets_x, targets_v, sigmas=(0.5, 1.0, 2.0),
+                 scale=None, n_steps=None, device="cuda:0"):
+        xhat = np.asarray(xhat, np.float64)
+        vhat = np.asarray(vhat, np.float64)
+        tx = np.asarray(targets_x, np.float64)
+        tv = np.asarray(targets_v, np.float64)
+        self.n = xhat.shape[0]
+        self.count, m = tx.shape[0], tx.shape[1]
+        self.cfg = stream_cfg(cfg, n=self.n, n_steps=n_steps)
+        self.device = torch.device(device)
+        if scale is None:   # the first target's spread
+            scale = np.concatenate([tx[0].std(axis=0), tv[0].std(axis=0)])
+        TX = torch.tensor(tx.transpose(2, 0, 1).reshape(3, self.count * m).copy(),
+                          device=self.device)
+        TV = torch.tensor(tv.transpose(2, 0, 1).reshape(3, self.count * m).copy(),
+                          device=self.device)
+        xh = torch.tensor(xhat.T.copy(), device=self.device)
+        vh = torch.tensor(vhat.T.copy(), device=self.device)
+        torch.cuda.current_stream(self.device).synchronize()
+        self.h = nb.nbody_stream_batch_create(self.cfg, self.count, xh, vh, m, TX, TV,
+                                              list(scale), list(sigmas))
+
+    def loss_and_grad(self, thetas):
+        """(losses (count,), dL/dtheta (count, 4)) at thetas (count, 4)."""
+        return nb.nbody_stream_batch_loss_grad(self.h, thetas)
+
+    def loss(self, thetas):
+        return nb.nbody_stream_batch_loss_grad(self.h, thetas, want_grad=False)[0]
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            nb.nbody_stream_batch_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class StreamLoss(torch.autograd.Function):
     """L(theta) with d L / d theta from the library's adjoint kernels."""
 

@@ -170,6 +170,51 @@ class Surrogate:
             self.h = None
 
 
+def descend_batch(model, thetas0, centre, width, lr=0.05, iters=10):
+    """descend() for many problems at once (a StreamBatch: one gradient call
+    for all members per iteration): per member Adam in normalised
+    parameters, a step that raises the member's loss above its best is
+    undone, its moments reset and its rate halved; returns the minimum-loss
+    iterate of every member (count, 4), its loss (count,) and the best loss
+    after every iteration (iters + 1, count)."""
+    centre = np.asarray(centre, float)
+    u = to_u(thetas0, centre, width)
+    count = u.shape[0]
+    m = np.zeros_like(u)
+    v = np.zeros_like(u)
+    k = np.zeros(count)
+    lr = np.full(count, float(lr))
+    best_L = np.full(count, np.inf)
+    best_u = u.copy()
+    best_g = np.zeros_like(u)
+    trace = []
+    for it in range(iters + 1):
+        L, g = model.loss_and_grad(from_u(u, centre, width))
+        gu = g * centre[None, :] * width
+        better = L <= best_L
+        best_L = np.where(better, L, best_L)
+        best_u[better] = u[better]
+        best_g[better] = gu[better]
+        worse = ~better
+        lr[worse] *= 0.5
+        m[worse] = 0.0
+        v[worse] = 0.0
+        k[worse] = 0
+        u[worse] = best_u[worse]
+        gu[worse] = best_g[worse]
+        trace.append(best_L.copy())
+        if it == iters:
+            break
+        ok = np.all(np.isfinite(gu), axis=1)
+        k += ok
+        m[ok] = 0.9 * m[ok] + 0.1 * gu[ok]
+        v[ok] = 0.999 * v[ok] + 0.001 * gu[ok] * gu[ok]
+        kk = np.maximum(k, 1)[:, None]
+        step = lr[:, None] * (m / (1 - 0.9 ** kk)) / (np.sqrt(v / (1 - 0.999 ** kk)) + 1e-300)
+        u[ok] = np.clip(u[ok] - step[ok], -1.5, 1.5)
+    return from_u(best_u, centre, width), best_L, np.array(trace)
+
+
 def descend(model: StreamModel, theta0, centre, width, lr=0.05, max_iters=50,
             loss_target=None, theta_true=None, err_target=None, clock=None):
     """Gradient descent on the simulator's loss in normalised parameters u,

@@ -153,3 +153,48 @@ def test_stream_autotune_keeps_parity():
     assert L == pytest.approx(L_ref, rel=1e-4)
     assert_grad_close(g, g_ref, orc.t_end_parts)
     gpu.close()
+
+
+def test_stream_batch_losses_and_gradients_match_oracle():
+    """The pipeline for several parameter vectors at once, each member
+    against its own target cloud in common units: every member's MMD^2 and
+    dL/dtheta against the oracle's pipeline for that member."""
+    from oracle import mmd
+    from paper_2511_22468_gb300.stream import StreamBatch
+    from paper_2511_22468_gb300.surrogate import descend_batch
+    cfg, xh, vh = _case()
+    orc = ostream.StreamModel(cfg, xh, vh)
+    truth = np.array(cfg.theta_true, float)
+    f_target = np.array([[1.0, 1.0, 1.0, 1.0], [1.1, 0.9, 1.0, 1.05], [0.95, 1.1, 1.05, 0.9]])
+    f_theta = np.array([[1.05, 0.9, 1.1, 0.95], [1.0, 1.0, 0.95, 1.1], [0.9, 1.05, 1.0, 1.0]])
+    targets = [orc.final_state(truth * f) for f in f_target]
+    tx = np.stack([t[0] for t in targets])
+    tv = np.stack([t[1] for t in targets])
+    Y0 = mmd.cloud(tx[0], tv[0])
+    mu, sc = mmd.target_stats(Y0)
+    sig = [0.5, 1.0, 2.0]
+    thetas = truth[None, :] * f_theta
+    gpu = StreamBatch(cfg, xh, vh, tx, tv, sig, scale=sc)
+    L, g = gpu.loss_and_grad(thetas)
+    for b in range(3):
+        Yb = mmd.cloud(tx[b], tv[b])
+        L_ref, g_ref = orc.mmd_loss_and_grad(thetas[b], Yb, sig, mu, sc)
+        assert abs(L[b] - L_ref) <= 1e-5 * len(sig) and L[b] == pytest.approx(L_ref, rel=1e-3)
+        # each component is the sum of two separately rounded parts (n-body
+        # run and orbit): 1e-4 of the parts' magnitudes bounds its error
+        p1, p2 = orc.grad_parts
+        assert np.all(np.abs(g[b] - g_ref) <= 1e-4 * (np.abs(p1) + np.abs(p2))), (b, g[b], g_ref,
+                                                                                p1, p2)
+    # the same call again gives the same bits; the loss alone agrees
+    L2, g2 = gpu.loss_and_grad(thetas)
+    assert np.array_equal(L, L2) and np.array_equal(g, g2)
+    assert np.array_equal(gpu.loss(thetas), L)
+    # a member at its own target's parameters has zero loss (to the loss
+    # tolerance: the target is the oracle's cloud, the kernel sums are FP32)
+    L0, _ = gpu.loss_and_grad(truth[None, :] * f_target)
+    assert np.all(np.abs(L0) <= 1e-5 * len(sig)) and np.all(np.abs(L0) < 1e-3 * L)
+    # batched descent: the best loss of every member never increases
+    best, Lb, trace = descend_batch(gpu, thetas, truth, 0.3, iters=3)
+    assert trace.shape == (4, 3) and np.all(np.diff(trace, axis=0) <= 0.0)
+    assert np.all(Lb <= L) and np.array_equal(Lb, trace[-1])
+    gpu.close()
