@@ -504,10 +504,20 @@ def run_ours(args):
     if not args.no_grid:
         # the point-cloud grid search at the paper's stage-1 size: 10^4
         # simulations of 1000 particles, 1000 steps, ranked by batched MMD
+        # and its bootstrap: 1000 realisations of the observation scored
+        # against every kept grid cloud, then all 1000 refined by 10 batched
+        # gradient steps
         from paper_2511_22468_gb300 import gridsearch
-        g = gridsearch.run(refine_iters=0, device=str(dev))
+        g = gridsearch.run(refine_iters=10, device=str(dev), bootstrap=1000,
+                           bootstrap_refine=1000, refine_batch=500)
         grid = {"workload": "grid_1e4_n1000_steps1000", **g["grid"],
                 "grid_points": g["workload"]["grid_points"]}
+        b = g["bootstrap"]
+        grid["bootstrap"] = {"realisations": b["realisations"], "cross_mmd_s": b["time_s"],
+                             "cross_kernel_pairs_per_s": b["kernel_pairs_per_s"],
+                             "refine_s": b["refine"]["time_s"],
+                             "refine_iters": b["refine"]["iters"],
+                             "refine_batch": b["refine"]["batch"]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
