@@ -380,10 +380,11 @@ __global__ void __launch_bounds__(256)
 // external Hessian product, parameter-gradient terms) and, when drift, of
 // the drift that led to it, staging (x_{k-1}, new vbar) into vst_next.
 // Per-item sums of the parameter-gradient terms accumulate in blk[item][8]
-// (fixed order: one block per item per point, points in sequence).  The
-// work counter of the next point is re-armed here.
-template <bool EQM>
-__global__ void __launch_bounds__(kVNT)
+// (fixed order: one block per item per point, points in sequence); SHAPE
+// adds the shape-parameter terms (r_s, a_MN, b_MN), otherwise left at 0.
+// The work counter of the next point is re-armed here.
+template <bool EQM, bool SHAPE>
+__global__ void __launch_bounds__(kVNT, 4)
     k_adj_step_batch(const float4* __restrict__ vst, float4* __restrict__ vst_next,
                      const SimMeta* __restrict__ vmeta, const int4* __restrict__ items,
                      int nitems, unsigned* __restrict__ ctr, unsigned* __restrict__ ctr_next,
@@ -470,33 +471,26 @@ __global__ void __launch_bounds__(kVNT)
         ap[d] = ak[d * ptot + g];
         gv[d] = -Q.G * M.mscale * qs[d];
       }
-      ExtUnit e;
-      ext_unit(Q, x[0], x[1], x[2], e);
-      double jl[3];
-      ext_jvp(Q, x[0], x[1], x[2], lam, jl);
+      ExtAdj ea;
+      ext_adjoint<SHAPE>(Q, x[0], x[1], x[2], lam, ea);
       const double ckdt = ck * Q.dt;
       double xb[3];
-      double lp = 0.0, ln = 0.0, lm = 0.0, lb = 0.0;
+      double lp = 0.0;
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        xb[d] = xbar[d * ptot + g] + ckdt * (gv[d] + jl[d]);
+        xb[d] = xbar[d * ptot + g] + ckdt * (gv[d] + ea.jl[d]);
         lp += lam[d] * ap[d];
-        ln += lam[d] * e.n[d];
-        lm += lam[d] * e.d[d];
-        lb += lam[d] * e.b[d];
       }
-      const double la = lp + Q.nfw_GM * ln + Q.mn_GM * lm + Q.bulge_GM * lb;
-      contrib[0] += ck * la;          // dL/d dt from the kick(s)
-      contrib[1] += ckdt * lp;        // sum_j m_j dL/dm_j
-      contrib[2] += ckdt * Q.G * ln;  // dL/d M_NFW
-      contrib[3] += ckdt * Q.G * lm;  // dL/d M_MN
-      if (Q.ext) {                    // dL/d (r_s, a_MN, b_MN), dL/d M_bulge
-        double sh[3];
-        ext_shape_vjp(Q, x[0], x[1], x[2], lam, sh);
-        contrib[4] += ckdt * sh[0];
-        contrib[5] += ckdt * sh[1];
-        contrib[6] += ckdt * sh[2];
-        contrib[7] += ckdt * Q.G * lb;
+      const double la = lp + Q.nfw_GM * ea.ln + Q.mn_GM * ea.lm + Q.bulge_GM * ea.lb;
+      contrib[0] += ck * la;             // dL/d dt from the kick(s)
+      contrib[1] += ckdt * lp;           // sum_j m_j dL/dm_j
+      contrib[2] += ckdt * Q.G * ea.ln;  // dL/d M_NFW
+      contrib[3] += ckdt * Q.G * ea.lm;  // dL/d M_MN
+      contrib[7] += ckdt * Q.G * ea.lb;  // dL/d M_bulge
+      if (SHAPE) {                       // dL/d (r_s, a_MN, b_MN)
+        contrib[4] += ckdt * ea.sh[0];
+        contrib[5] += ckdt * ea.sh[1];
+        contrib[6] += ckdt * ea.sh[2];
       }
       double vb[3] = {lam[0], lam[1], lam[2]};
       if (drift) {
@@ -689,8 +683,10 @@ struct Batch {
   cudaGraphExec_t vexec = nullptr;
   int64_t vexec_steps = -1;
   bool vexec_eqm = false;
+  bool vexec_shape = true;
   int vgraph_nodes = 0;
   bool vplan_valid = false;     // vmeta matches the current masses and eps
+  bool vjp_shape = true;        // the sweep also forms dL/d(r_s, a_MN, b_MN)
 };
 
 namespace {
@@ -1199,6 +1195,14 @@ int batch_integrate(Batch* b, int64_t n_steps) {
 
 namespace {
 
+// calls f(kernel) with the reverse-point kernel for the batch's masses and
+// gradient set
+template <class F>
+cudaError_t with_adj_kernel(const Batch* b, F f) {
+  if (b->eqm) return b->vjp_shape ? f(k_adj_step_batch<true, true>) : f(k_adj_step_batch<true, false>);
+  return b->vjp_shape ? f(k_adj_step_batch<false, true>) : f(k_adj_step_batch<false, false>);
+}
+
 // VJP plan and reverse-sweep buffers (once per batch)
 int ensure_vjp_plan(Batch* b) {
   if (b->vmeta && b->vplan_valid) return NBODY_OK;
@@ -1241,9 +1245,9 @@ int ensure_vjp_plan(Batch* b) {
                       cudaMemcpyHostToDevice, b->gs));
   BCK(cudaStreamSynchronize(b->gs));
   int occ = 1;
-  const cudaError_t e = b->eqm
-      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adj_step_batch<true>, kVNT, 0)
-      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adj_step_batch<false>, kVNT, 0);
+  const cudaError_t e = with_adj_kernel(b, [&](auto kern) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kVNT, 0);
+  });
   if (e != cudaSuccess || occ < 1) {
     cudaGetLastError();
     occ = 1;
@@ -1272,17 +1276,13 @@ int record_sweep(Batch* b, int64_t n_steps, cudaStream_t s, int* nodes) {
     const TapePoint tp = k > 0 ? tape_point(b, n_steps, k - 1) : TapePoint{nullptr, nullptr, nullptr};
     const double ck = (k == n_steps || k == 0) ? 0.5 : 1.0;
     const int drift = k > 0 ? 1 : 0;
-    if (b->eqm)
-      k_adj_step_batch<true><<<g, kVNT, 0, s>>>(
-          vbuf[cur], vbuf[1 - cur], b->vmeta, b->vitems, b->nvitems, b->ctr + 2 + cur,
-          b->ctr + 2 + (1 - cur), b->dp, b->xbar, b->vbar, b->m, b->ptot, tk.x, tk.a, ck, drift,
-          tp.vh, tp.x, b->centers, cs, k > 0 ? k - 1 : 0, b->vblk, b->status);
-    else
-      k_adj_step_batch<false><<<g, kVNT, 0, s>>>(
-          vbuf[cur], vbuf[1 - cur], b->vmeta, b->vitems, b->nvitems, b->ctr + 2 + cur,
-          b->ctr + 2 + (1 - cur), b->dp, b->xbar, b->vbar, b->m, b->ptot, tk.x, tk.a, ck, drift,
-          tp.vh, tp.x, b->centers, cs, k > 0 ? k - 1 : 0, b->vblk, b->status);
-    BCK(cudaGetLastError());
+    BCK(with_adj_kernel(b, [&](auto kern) {
+      kern<<<g, kVNT, 0, s>>>(vbuf[cur], vbuf[1 - cur], b->vmeta, b->vitems, b->nvitems,
+                              b->ctr + 2 + cur, b->ctr + 2 + (1 - cur), b->dp, b->xbar, b->vbar,
+                              b->m, b->ptot, tk.x, tk.a, ck, drift, tp.vh, tp.x, b->centers, cs,
+                              k > 0 ? k - 1 : 0, b->vblk, b->status);
+      return cudaGetLastError();
+    }));
     ++cnt;
   }
   k_adj_reduce_batch<<<(b->n_sims + 127) / 128, 128, 0, s>>>(b->vblk, b->dfirst, b->n_sims,
@@ -1293,6 +1293,11 @@ int record_sweep(Batch* b, int64_t n_steps, cudaStream_t s, int* nodes) {
 }
 
 }  // namespace
+
+void batch_set_vjp_shape(Batch* b, bool on) {
+  if (on != b->vjp_shape) b->vplan_valid = false;  // the occupancy differs
+  b->vjp_shape = on;
+}
 
 int batch_vjp(Batch* b, const double* xbar, const double* vbar, double* x0bar, double* v0bar,
               double* theta_bar) {
@@ -1324,7 +1329,8 @@ int batch_vjp(Batch* b, const double* xbar, const double* vbar, double* x0bar, d
     if (p == b->cot) BCK(cudaStreamSynchronize(b->gs));  // the scratch is reused
   }
   count_launch(2);
-  if (!b->vexec || b->vexec_steps != n_steps || b->vexec_eqm != b->eqm) {
+  if (!b->vexec || b->vexec_steps != n_steps || b->vexec_eqm != b->eqm ||
+      b->vexec_shape != b->vjp_shape) {
     if (b->vexec) {
       cudaGraphExecDestroy(b->vexec);
       b->vexec = nullptr;
@@ -1347,6 +1353,7 @@ int batch_vjp(Batch* b, const double* xbar, const double* vbar, double* x0bar, d
     }
     b->vexec_steps = n_steps;
     b->vexec_eqm = b->eqm;
+    b->vexec_shape = b->vjp_shape;
     b->vgraph_nodes = nodes;
   }
   BCK(cudaGraphLaunch(b->vexec, b->gs));

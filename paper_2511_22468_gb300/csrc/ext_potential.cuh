@@ -267,6 +267,91 @@ static __device__ __forceinline__ void ext_shape_vjp(const DevParams& P, double 
   }
 }
 
+// Everything the adjoint of a kick needs of the external field at one
+// point, with the square roots, the logarithm and the incomplete gamma
+// function taken once: for cotangents l,
+//   jl = (d a_ext / d x) l                           (as ext_jvp),
+//   ln = l . e.n, lm = l . e.d, lb = l . e.b          (unit accelerations, as ext_unit),
+//   sh = l . d a_ext / d (r_s, a_MN, b_MN)            (as ext_shape_vjp; SHAPE only).
+struct ExtAdj {
+  double jl[3];
+  double ln, lm, lb;
+  double sh[3];
+};
+
+template <bool SHAPE>
+static __device__ __forceinline__ void ext_adjoint(const DevParams& P, double x, double y,
+                                                   double z, const double l[3], ExtAdj& o) {
+  o.jl[0] = o.jl[1] = o.jl[2] = 0.0;
+  o.ln = o.lm = o.lb = 0.0;
+  o.sh[0] = o.sh[1] = o.sh[2] = 0.0;
+  const double xl = x * l[0] + y * l[1] + z * l[2];
+  const double r2 = x * x + y * y + z * z;
+  if ((P.ext & NBODY_EXT_NFW) && r2 > 0.0) {
+    // a = -G M f(r) x; J = -G M [f I + (f'/r) x x^T] (nfw_f, nfw_fprime_over_r)
+    const double rs = P.nfw_rs;
+    const double ir = rsqrt_nr(r2);
+    const double r = r2 * ir;
+    const double u = r / rs;
+    const double irp = 1.0 / (r + rs);
+    double f, g;
+    if (u < 1e-4) {
+      f = nfw_f(r, rs);
+      g = nfw_fprime_over_r(r, rs);
+    } else {
+      const double L = log1p(u);
+      const double ir2 = ir * ir, ir3 = ir2 * ir;
+      f = (L * ir - irp) * ir2;
+      g = (ir3 * irp - 3.0 * L * ir2 * ir2 + (3.0 * r + 2.0 * rs) * ir3 * irp * irp) * ir;
+    }
+    o.ln = -f * xl;
+    o.jl[0] -= P.nfw_GM * (f * l[0] + g * xl * x);
+    o.jl[1] -= P.nfw_GM * (f * l[1] + g * xl * y);
+    o.jl[2] -= P.nfw_GM * (f * l[2] + g * xl * z);
+    if (SHAPE) o.sh[0] = P.nfw_GM * xl * ir * irp * irp / rs;  // G M x.l / (r_s r (r+r_s)^2)
+  }
+  if (P.ext & NBODY_EXT_MN) {
+    // a = -G M q / S^3, q = (x, y, z (a+B)/B); J and the shape terms as in
+    // ext_jvp and ext_shape_vjp
+    const double b = P.mn_b;
+    const double B2 = z * z + b * b;
+    const double iB = B2 > 0.0 ? rsqrt_nr(B2) : 0.0;
+    const double B = B2 * iB;
+    const double aB = P.mn_a + B;
+    const double iS = rsqrt_nr(x * x + y * y + aB * aB);
+    const double iS2 = iS * iS, iS3 = iS2 * iS, iS5 = iS3 * iS2;
+    const double q2 = z * aB * iB;
+    const double xy = x * l[0] + y * l[1];
+    const double ql = xy + q2 * l[2];
+    o.lm = -ql * iS3;
+    const double dz = 1.0 + P.mn_a * b * b * iB * iB * iB;
+    o.jl[0] -= P.mn_GM * (l[0] * iS3 - 3.0 * x * ql * iS5);
+    o.jl[1] -= P.mn_GM * (l[1] * iS3 - 3.0 * y * ql * iS5);
+    o.jl[2] -= P.mn_GM * (dz * l[2] * iS3 - 3.0 * q2 * ql * iS5);
+    if (SHAPE) {
+      const double da_z = -(z * iB) * (iS3 - 3.0 * aB * aB * iS5);
+      const double db_z = z * b * (P.mn_a * iB * iB * iB * iS3 + 3.0 * aB * aB * iB * iB * iS5);
+      const double da_xy = 3.0 * aB * iS5 * xy;
+      o.sh[1] = P.mn_GM * (da_xy + da_z * l[2]);
+      o.sh[2] = P.mn_GM * (da_xy * b * iB + db_z * l[2]);
+    }
+  }
+  if ((P.ext & NBODY_EXT_BULGE) && r2 > 0.0) {
+    // a = -G M_b P(s, u) x / r^3, u = r^2 / r_c^2; J as in ext_jvp
+    const double u = r2 * P.bulge_irc2;
+    const double ir = rsqrt_nr(r2);
+    const double ir3 = ir * ir * ir;
+    const double Pu = bulge_P(P, u);
+    const double dP = u > 700.0 ? 0.0 : exp((P.bulge_s - 1.0) * log(u) - u) * P.bulge_igs;
+    const double f = Pu * ir3;
+    const double g = 2.0 * P.bulge_irc2 * dP * ir3 - 3.0 * Pu * ir3 * ir * ir;
+    o.lb = -f * xl;
+    o.jl[0] -= P.bulge_GM * (f * l[0] + g * xl * x);
+    o.jl[1] -= P.bulge_GM * (f * l[1] + g * xl * y);
+    o.jl[2] -= P.bulge_GM * (f * l[2] + g * xl * z);
+  }
+}
+
 static __device__ __forceinline__ double ext_potential(const DevParams& P, double x,
                                                 double y, double z) {
   double phi = 0.0;

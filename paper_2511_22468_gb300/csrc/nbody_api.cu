@@ -132,6 +132,10 @@ struct nbody_ctx {
   size_t ev_used[NBODY_NKCLASS] = {};
 };
 
+namespace nb {
+Batch* context_batch(nbody_ctx* c) { return c ? c->batch : nullptr; }
+}  // namespace nb
+
 namespace {
 
 #define CK(call)                              \

@@ -242,6 +242,11 @@ int batch_integrate(Batch* b, int64_t n_steps);
 // theta_bar [n_sims][kAdjCols] or NULL
 int batch_vjp(Batch* b, const double* xbar, const double* vbar, double* x0bar, double* v0bar,
               double* theta_bar);
+// whether batch_vjp forms the shape-parameter gradients (default yes; the
+// batched pipeline, which needs the masses only, turns them off)
+void batch_set_vjp_shape(Batch* b, bool on);
+// the batch behind a batch context (nbody_api.cu)
+Batch* context_batch(nbody_ctx* c);
 int batch_status(Batch* b);
 int batch_autotune(Batch* b, int64_t probe_steps, int* best, double* ms);
 int batch_set_tuning(Batch* b, int k);

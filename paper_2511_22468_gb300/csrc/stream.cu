@@ -1013,6 +1013,8 @@ int nbody_stream_batch_create(nbody_stream_batch** out, const nbody_stream_cfg* 
   std::vector<int64_t> offs((size_t)count + 1);
   for (int64_t b = 0; b <= count; ++b) offs[(size_t)b] = b * c.n;
   int rc = nbody_create_batch(&s->ctx, (int)count, offs.data(), prm.data(), cuda_stream);
+  // the pipeline needs the masses' gradients only, not the shape parameters'
+  if (!rc) nb::batch_set_vjp_shape(nb::context_batch(s->ctx), false);
   double *dtx = nullptr, *dtv = nullptr;
   const size_t tm3 = 3 * (size_t)m * (size_t)count;
   if (!rc) rc = salloc(&s->xhat, n3);

@@ -176,20 +176,16 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
       ap[d] = a.ak[d * np + i];
       g[d] = -P.G * a.mscale * (gs[d] / s_here);
     }
-    ExtUnit e;
-    ext_unit(P, x[0], x[1], x[2], e);
-    double jl[3];
-    ext_jvp(P, x[0], x[1], x[2], lam, jl);
+    ExtAdj ea;
+    ext_adjoint<true>(P, x[0], x[1], x[2], lam, ea);
     const double ck = a.ck * P.dt;
     double xb[3];
-    double la = 0.0, lp = 0.0, ln = 0.0, lm = 0.0, lb = 0.0;
+    double la = 0.0, lp = 0.0;
+    const double ln = ea.ln, lm = ea.lm, lb = ea.lb;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      xb[d] = a.xbar[d * np + i] + ck * (g[d] + jl[d]);
+      xb[d] = a.xbar[d * np + i] + ck * (g[d] + ea.jl[d]);
       lp += lam[d] * ap[d];
-      ln += lam[d] * e.n[d];
-      lm += lam[d] * e.d[d];
-      lb += lam[d] * e.b[d];
     }
     la = lp + P.nfw_GM * ln + P.mn_GM * lm + P.bulge_GM * lb;
     if (a.mpart) {  // per-particle mass gradient of this kick
@@ -202,11 +198,9 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
     contrib[2] = ck * P.G * ln;      // dL/d M_NFW
     contrib[3] = ck * P.G * lm;      // dL/d M_MN
     if (P.ext) {                     // dL/d (r_s, a_MN, b_MN)
-      double sh[3];
-      ext_shape_vjp(P, x[0], x[1], x[2], lam, sh);
-      contrib[4] = ck * sh[0];
-      contrib[5] = ck * sh[1];
-      contrib[6] = ck * sh[2];
+      contrib[4] = ck * ea.sh[0];
+      contrib[5] = ck * ea.sh[1];
+      contrib[6] = ck * ea.sh[2];
       contrib[7] = ck * P.G * lb;    // dL/d M_bulge
     }
     double vb[3] = {lam[0], lam[1], lam[2]};
