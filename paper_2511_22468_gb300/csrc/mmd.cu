@@ -197,8 +197,13 @@ __global__ void __launch_bounds__(128)
 // fixed-order block reduction into out[(c * gridDim.y + a) * gridDim.x + x].
 // Rows of set a: rows + a * rstride; columns: cols + a * cas + c * ccs (a
 // cloud against itself: cas = rstride, ccs = 0; clouds against other
-// clouds: cas = 0, ccs = their stride).  Per pair: 13 FP32-pipe operations
-// (two pairs per packed instruction) and one MUFU ex2 per bandwidth.
+// clouds: cas = 0, ccs = their stride).  The squared distance is expanded,
+// |u_i - u_j|^2 = |u_i|^2 + |u_j|^2 - 2 u_i . u_j, with the column norms
+// formed once per tile in shared memory: per two pairs one packed add and
+// six packed FMAs instead of twelve operations (the kernel's values keep a
+// relative error of about |u|^2 2^-24 near zero distance, far below the FP32
+// sums' own).  Per two pairs: 8 + 2 (NS - 1) + 1 FP32-pipe instructions and
+// 2 NS ex2 (the ex2 unit bounds it).
 template <int R, int NS>
 __global__ void __launch_bounds__(128)
     k_mmd_sum(const float4* __restrict__ rows, int64_t rstride, int64_t n_r,
@@ -206,20 +211,25 @@ __global__ void __launch_bounds__(128)
               double* __restrict__ out) {
   constexpr int NT = 128;
   __shared__ float4 sj[3 * kMT];
+  __shared__ float2 snb[kMT];  // column norms |u_j|^2 of the tile's pairs
   __shared__ double sw[NT / 32];
   const int t = threadIdx.x;
   const int64_t a = blockIdx.y, c = blockIdx.z;
   const float4* rs = rows + a * rstride;
   const float4* cs = cols + a * cas + c * ccs;
   const int64_t i0 = (int64_t)blockIdx.x * (NT * R) + t;
-  float2 nu[R][6];
+  float2 m2u[R][6], na[R];  // -2 u_i and |u_i|^2, both lanes alike
 #pragma unroll
-  for (int r = 0; r < R; ++r)
+  for (int r = 0; r < R; ++r) {
+    float n2 = 0.f;
 #pragma unroll
     for (int d = 0; d < 6; ++d) {
       const float u = load_u(rs, i0 + r * NT, d);
-      nu[r][d] = make_float2(-u, -u);
+      m2u[r][d] = make_float2(-2.f * u, -2.f * u);
+      n2 = fmaf(u, u, n2);
     }
+    na[r] = make_float2(n2, n2);
+  }
   const float rl[4] = {1.f, rho.y, rho.z, rho.w};
   double s0[R];
 #pragma unroll
@@ -229,24 +239,32 @@ __global__ void __launch_bounds__(128)
     __syncthreads();
     for (int q = t; q < 3 * kMT; q += NT) sj[q] = src[q];
     __syncthreads();
+    for (int q = t; q < kMT; q += NT) {
+      const float4 P0 = sj[3 * q], P1 = sj[3 * q + 1], P2 = sj[3 * q + 2];
+      float2 n2 = make_float2(P0.x * P0.x, P0.y * P0.y);
+      n2 = __ffma2_rn(make_float2(P0.z, P0.w), make_float2(P0.z, P0.w), n2);
+      n2 = __ffma2_rn(make_float2(P1.x, P1.y), make_float2(P1.x, P1.y), n2);
+      n2 = __ffma2_rn(make_float2(P1.z, P1.w), make_float2(P1.z, P1.w), n2);
+      n2 = __ffma2_rn(make_float2(P2.x, P2.y), make_float2(P2.x, P2.y), n2);
+      n2 = __ffma2_rn(make_float2(P2.z, P2.w), make_float2(P2.z, P2.w), n2);
+      snb[q] = n2;
+    }
+    __syncthreads();
     float2 a0[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) a0[r] = make_float2(0.f, 0.f);
 #pragma unroll 2
     for (int jj = 0; jj < kMT; ++jj) {
       const float4 P0 = sj[3 * jj], P1 = sj[3 * jj + 1], P2 = sj[3 * jj + 2];
+      const float2 nb2 = snb[jj];
       const float2 cc[6] = {make_float2(P0.x, P0.y), make_float2(P0.z, P0.w),
                             make_float2(P1.x, P1.y), make_float2(P1.z, P1.w),
                             make_float2(P2.x, P2.y), make_float2(P2.z, P2.w)};
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        float2 dd = __fadd2_rn(cc[0], nu[r][0]);
-        float2 r2 = __fmul2_rn(dd, dd);
+        float2 r2 = __fadd2_rn(na[r], nb2);
 #pragma unroll
-        for (int d = 1; d < 6; ++d) {
-          dd = __fadd2_rn(cc[d], nu[r][d]);
-          r2 = __ffma2_rn(dd, dd, r2);
-        }
+        for (int d = 0; d < 6; ++d) r2 = __ffma2_rn(cc[d], m2u[r][d], r2);
         float2 sk = make_float2(ex2_ftz(-r2.x), ex2_ftz(-r2.y));
 #pragma unroll
         for (int l = 1; l < NS; ++l) {

@@ -181,6 +181,9 @@ def test_batch_adjoint_matches_oracle(uneq):
     if uneq:   # unequal masses in one member: the general VJP kernel
         x, v, m, p, ph = sims[1]
         sims[1] = (x, v, m * np.linspace(0.5, 1.5, len(m)), p, ph)
+    # and a tiny member (7 particles in a 1024-row pad)
+    x, v, m = plummer_sphere(7, 33, 1.0, 1.0, 1.0)
+    sims.append((x, v, m, nb.make_params(1.0, 0.05, 1e-3), orc.Physics(G=1.0, eps=0.05)))
     for s in sims:
         s[3].checkpoint_every = 1
     steps = 25
