@@ -226,9 +226,10 @@ NBODY_API int nbody_create_batch(nbody_ctx **out, int n_sims,
  * pair VJP of each work item's rows over its simulation's whole j-range
  * (FP32 within a tile, FP64 across tiles, in fixed order) and applies the
  * FP64 adjoint update to those rows; the sweep is captured once as a CUDA
- * graph per step count.  Cotangents are FP32 in the pair VJP without the
- * single-system path's power-of-two rescaling, so they must stay within
- * the FP32 range (about 1e-30 .. 1e30; the NaN status reports an overflow).
+ * graph per step count.  The FP32 copies of the cotangents staged for the
+ * pair VJP are rescaled per simulation by an exact power of two (from the
+ * simulation's largest |lambda| at the point before), so cotangents of any
+ * FP64 size can be propagated.
  * xbar, vbar (3 x offsets[n_sims], the batch's layout; host or device;
  * either may be NULL for zero) are dL/dx_T, dL/dv_T; x0bar, v0bar (same
  * layout, may be NULL) receive dL/dx_0, dL/dv_0; theta_bar (host or device,

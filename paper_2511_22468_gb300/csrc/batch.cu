@@ -349,24 +349,71 @@ __global__ void __launch_bounds__(256)
 // simulation's whole j-range (kVTJ j-pairs per shared-memory tile)
 constexpr int kVNT = 128, kVR = 2, kVTJ = 256;
 
-// adjoint staging of point k (positions x, cotangents lam) of every
-// simulation into vst, and the pads (far away, zero mass and cotangent)
-// into vst2 as well
+// FP32 cotangent scaling, per simulation (the single-system sweep's scheme):
+// the cotangents staged for point k are multiplied by an exact power of two
+// s = 2^-e chosen from the largest |lambda| of the simulation at the point
+// before, so their FP32 copies neither overflow nor underflow while the
+// FP64 cotangents grow or shrink.  lsc[(k & 1) * n_sims + s] holds the
+// scale of point k's staging, lmax[...] (bit patterns of non-negative
+// doubles) the running maxima.
+__device__ __forceinline__ double lam_scale(unsigned long long bits) {
+  const double mx = __longlong_as_double((long long)bits);
+  if (!(mx > 0.0) || !isfinite(mx)) return 1.0;
+  return ldexp(1.0, -ilogb(mx));
+}
+
+// block maximum of v (>= 0) into *out by an atomic max of its bit pattern
+__device__ __forceinline__ void block_max_into(double v, unsigned long long* out) {
+  __shared__ double sm[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if (lane == 0) sm[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) mx = fmax(mx, sm[k]);
+    if (mx > 0.0 && isfinite(mx)) atomicMax(out, (unsigned long long)__double_as_longlong(mx));
+  }
+}
+
+// per-simulation max |lam| of the final cotangents into lmax[s]
+__global__ void __launch_bounds__(256)
+    k_vabsmax_batch(const SimMeta* __restrict__ meta, const int* __restrict__ blk_sim,
+                    const double* __restrict__ lam, int64_t ptot,
+                    unsigned long long* __restrict__ lmax) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = blk_sim[blockIdx.x];
+  const SimMeta M = meta[s];
+  double v = 0.0;
+  if (g - M.poff < M.n)
+    v = fmax(fabs(lam[g]), fmax(fabs(lam[ptot + g]), fabs(lam[2 * ptot + g])));
+  block_max_into(v, lmax + s);
+}
+
+// adjoint staging of point k (positions x, cotangents lam scaled by the
+// simulation's power of two from lmax) of every simulation into vst, the
+// scale into lsc[s]; the pads (far away, zero mass and cotangent) into vst2
+// as well
 __global__ void __launch_bounds__(256)
     k_vstage_batch(const SimMeta* __restrict__ meta, const int* __restrict__ blk_sim,
                    const double* __restrict__ x, const double* __restrict__ m,
                    const double* __restrict__ lam, int64_t ptot,
                    const double* __restrict__ centers, int64_t cstride, int64_t k,
+                   const unsigned long long* __restrict__ lmax, double* __restrict__ lsc,
                    float4* __restrict__ vst, float4* __restrict__ vst2) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int s = blk_sim[blockIdx.x];
   const SimMeta M = meta[s];
   const int64_t i = g - M.poff;
+  const double sc = lam_scale(lmax[s]);
+  if (i == 0) lsc[s] = sc;
   if (i < M.n) {
     const double* c = centers + (int64_t)s * cstride + 3 * k;
     put_vstage(vst, g, (float)(x[g] - c[0]), (float)(x[ptot + g] - c[1]),
-               (float)(x[2 * ptot + g] - c[2]), (float)m[g], (float)lam[g],
-               (float)lam[ptot + g], (float)lam[2 * ptot + g]);
+               (float)(x[2 * ptot + g] - c[2]), (float)m[g], (float)(sc * lam[g]),
+               (float)(sc * lam[ptot + g]), (float)(sc * lam[2 * ptot + g]));
   } else {
     put_vstage(vst, g, kPadPos, kPadPos, kPadPos, 0.f, 0.f, 0.f, 0.f);
     put_vstage(vst2, g, kPadPos, kPadPos, kPadPos, 0.f, 0.f, 0.f, 0.f);
@@ -394,7 +441,9 @@ __global__ void __launch_bounds__(kVNT, 4)
                      int drift, const double* __restrict__ vh_prev,
                      const double* __restrict__ x_prev, const double* __restrict__ centers,
                      int64_t cstride, int64_t k_prev, double* __restrict__ blk,
-                     int* __restrict__ status) {
+                     const double* __restrict__ lsc_here, double* __restrict__ lsc_next,
+                     const unsigned long long* __restrict__ lmax_here,
+                     unsigned long long* __restrict__ lmax_next, int* __restrict__ status) {
   constexpr int NT = kVNT, R = kVR;
   __shared__ float4 sj[4 * kVTJ];
   __shared__ double sred[kAdjCols][NT / 32];
@@ -456,6 +505,12 @@ __global__ void __launch_bounds__(kVNT, 4)
       }
     }
     const DevParams Q = P[w.x];
+    // the scale this point's cotangents were staged with, and the one for
+    // the staging of the previous point (from this point's largest |lambda|)
+    const double s_here = lsc_here[w.x];
+    const double s_next = drift ? lam_scale(lmax_here[w.x]) : 1.0;
+    if (drift && w.y == 0 && t == 0) lsc_next[w.x] = s_next;
+    double vmax = 0.0;
     double contrib[kAdjCols] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -469,7 +524,7 @@ __global__ void __launch_bounds__(kVNT, 4)
         lam[d] = vbar[d * ptot + g];
         x[d] = xk[d * ptot + g];
         ap[d] = ak[d * ptot + g];
-        gv[d] = -Q.G * M.mscale * qs[d];
+        gv[d] = -Q.G * M.mscale * (qs[d] / s_here);
       }
       ExtAdj ea;
       ext_adjoint<SHAPE>(Q, x[0], x[1], x[2], lam, ea);
@@ -500,12 +555,13 @@ __global__ void __launch_bounds__(kVNT, 4)
           xv += xb[d] * vh_prev[d * ptot + g];
           vb[d] += Q.dt * xb[d];
           vbar[d * ptot + g] = vb[d];
+          vmax = fmax(vmax, fabs(vb[d]));
         }
         contrib[0] += xv;             // dL/d dt from the drift
         const double* c = centers + (int64_t)w.x * cstride + 3 * k_prev;
         put_vstage(vst_next, g, (float)(x_prev[g] - c[0]), (float)(x_prev[ptot + g] - c[1]),
-                   (float)(x_prev[2 * ptot + g] - c[2]), (float)m[g], (float)vb[0],
-                   (float)vb[1], (float)vb[2]);
+                   (float)(x_prev[2 * ptot + g] - c[2]), (float)m[g], (float)(s_next * vb[0]),
+                   (float)(s_next * vb[1]), (float)(s_next * vb[2]));
       }
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
@@ -529,6 +585,7 @@ __global__ void __launch_bounds__(kVNT, 4)
       for (int k = 0; k < NT / 32; ++k) v += sred[t][k];
       blk[(int64_t)it * kAdjCols + t] += v;
     }
+    if (drift) block_max_into(vmax, lmax_next + w.x);
   }
   if (bad) atomicOr(status, kStatusNaN);
 }
@@ -678,6 +735,8 @@ struct Batch {
   double *xbar = nullptr, *vbar = nullptr;
   float4 *vst = nullptr, *vst2 = nullptr;
   double* vblk = nullptr;       // [nvitems][kAdjCols]
+  double* vlsc = nullptr;       // cotangent scales [2][n_sims] (point parity)
+  unsigned long long* vlmax = nullptr;  // their running maxima [2][n_sims]
   double* tbar = nullptr;       // [n_sims][kAdjCols]
   double* cot = nullptr;        // caller-layout scratch of host cotangents
   cudaGraphExec_t vexec = nullptr;
@@ -1037,6 +1096,7 @@ void batch_destroy(Batch* b) {
   if (b->vexec) cudaGraphExecDestroy(b->vexec);
   bfree(b->tape); bfree(b->vmeta); bfree(b->vitems); bfree(b->dfirst); bfree(b->xbar);
   bfree(b->vbar); bfree(b->vst); bfree(b->vst2); bfree(b->vblk); bfree(b->tbar); bfree(b->cot);
+  bfree(b->vlsc); bfree(b->vlmax);
   delete b;
 }
 
@@ -1235,6 +1295,8 @@ int ensure_vjp_plan(Batch* b) {
        (rc = balloc(&b->vst2, 2 * pt)) ||
        (rc = balloc(&b->vblk, (size_t)b->nvitems * kAdjCols)) ||
        (rc = balloc(&b->tbar, (size_t)b->n_sims * kAdjCols)) ||
+       (rc = balloc(&b->vlsc, 2 * (size_t)b->n_sims)) ||
+       (rc = balloc(&b->vlmax, 2 * (size_t)b->n_sims)) ||
        (rc = balloc(&b->vmeta, (size_t)b->n_sims))))
     return rc;
   BCK(cudaMemcpyAsync(b->vmeta, vm.data(), vm.size() * sizeof(SimMeta), cudaMemcpyHostToDevice,
@@ -1261,17 +1323,27 @@ int ensure_vjp_plan(Batch* b) {
 int record_sweep(Batch* b, int64_t n_steps, cudaStream_t s, int* nodes) {
   const int64_t cs = 3 * (b->centers_cap + 1);
   const unsigned nblk = (unsigned)(b->ptot / 256);
+  const int ns_ = b->n_sims;
   BCK(cudaMemsetAsync(b->ctr + 2, 0, 2 * sizeof(unsigned), s));
   BCK(cudaMemsetAsync(b->vblk, 0, (size_t)b->nvitems * kAdjCols * sizeof(double), s));
+  BCK(cudaMemsetAsync(b->vlmax, 0, 2 * (size_t)ns_ * sizeof(unsigned long long), s));
   const TapePoint tn = tape_point(b, n_steps, n_steps);
+  const int sl_n = (int)(n_steps & 1);
+  k_vabsmax_batch<<<nblk, 256, 0, s>>>(b->meta, b->blk_sim, b->vbar, b->ptot,
+                                       b->vlmax + (size_t)sl_n * ns_);
+  BCK(cudaGetLastError());
   k_vstage_batch<<<nblk, 256, 0, s>>>(b->meta, b->blk_sim, tn.x, b->m, b->vbar, b->ptot,
-                                      b->centers, cs, n_steps, b->vst, b->vst2);
+                                      b->centers, cs, n_steps, b->vlmax + (size_t)sl_n * ns_,
+                                      b->vlsc + (size_t)sl_n * ns_, b->vst, b->vst2);
   BCK(cudaGetLastError());
   float4* vbuf[2] = {b->vst, b->vst2};
   const unsigned g = (unsigned)std::max(1, b->grid_vjp);
-  int cnt = 1;
+  int cnt = 2;
   for (int64_t k = n_steps; k >= 0; --k) {
     const int cur = (int)((n_steps - k) & 1);
+    const size_t here = (size_t)(k & 1) * ns_, next = (size_t)(1 - (k & 1)) * ns_;
+    // the maxima of the cotangents staged now start from zero
+    BCK(cudaMemsetAsync(b->vlmax + next, 0, (size_t)ns_ * sizeof(unsigned long long), s));
     const TapePoint tk = tape_point(b, n_steps, k);
     const TapePoint tp = k > 0 ? tape_point(b, n_steps, k - 1) : TapePoint{nullptr, nullptr, nullptr};
     const double ck = (k == n_steps || k == 0) ? 0.5 : 1.0;
@@ -1280,7 +1352,8 @@ int record_sweep(Batch* b, int64_t n_steps, cudaStream_t s, int* nodes) {
       kern<<<g, kVNT, 0, s>>>(vbuf[cur], vbuf[1 - cur], b->vmeta, b->vitems, b->nvitems,
                               b->ctr + 2 + cur, b->ctr + 2 + (1 - cur), b->dp, b->xbar, b->vbar,
                               b->m, b->ptot, tk.x, tk.a, ck, drift, tp.vh, tp.x, b->centers, cs,
-                              k > 0 ? k - 1 : 0, b->vblk, b->status);
+                              k > 0 ? k - 1 : 0, b->vblk, b->vlsc + here, b->vlsc + next,
+                              b->vlmax + here, b->vlmax + next, b->status);
       return cudaGetLastError();
     }));
     ++cnt;

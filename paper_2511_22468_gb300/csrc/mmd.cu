@@ -198,11 +198,12 @@ __global__ void __launch_bounds__(128)
 // Rows of set a: rows + a * rstride; columns: cols + a * cas + c * ccs (a
 // cloud against itself: cas = rstride, ccs = 0; clouds against other
 // clouds: cas = 0, ccs = their stride).  The squared distance is expanded,
-// |u_i - u_j|^2 = |u_i|^2 + |u_j|^2 - 2 u_i . u_j, with the column norms
-// formed once per tile in shared memory: per two pairs one packed add and
-// six packed FMAs instead of twelve operations (the kernel's values keep a
-// relative error of about |u|^2 2^-24 near zero distance, far below the FP32
-// sums' own).  Per two pairs: 8 + 2 (NS - 1) + 1 FP32-pipe instructions and
+// |u_i - u_j|^2 = |u_i'|^2 + |u_j'|^2 - 2 u_i' . u_j' with u' = u - c, c the
+// row set's first point, and the column norms formed once per tile in
+// shared memory: per two pairs one packed add and six packed FMAs instead
+// of twelve operations.  The expansion's rounding error, about |u'|^2 2^-24,
+// matters only for near pairs, whose u' are of the size of the clouds'
+// extent.  Per two pairs: 8 + 2 (NS - 1) + 1 FP32-pipe instructions and
 // 2 NS ex2 (the ex2 unit bounds it).
 template <int R, int NS>
 __global__ void __launch_bounds__(128)
@@ -218,13 +219,23 @@ __global__ void __launch_bounds__(128)
   const float4* rs = rows + a * rstride;
   const float4* cs = cols + a * cas + c * ccs;
   const int64_t i0 = (int64_t)blockIdx.x * (NT * R) + t;
-  float2 m2u[R][6], na[R];  // -2 u_i and |u_i|^2, both lanes alike
+  // distances are formed relative to the row set's first point, so that
+  // the norms stay of the size of the clouds' extent rather than of their
+  // offset from the standardisation origin (the expansion's rounding error
+  // scales with the norms)
+  float cr[6];
+#pragma unroll
+  for (int d = 0; d < 6; ++d) cr[d] = load_u(rs, 0, d);
+  const float4 cq0 = make_float4(cr[0], cr[0], cr[1], cr[1]);
+  const float4 cq1 = make_float4(cr[2], cr[2], cr[3], cr[3]);
+  const float4 cq2 = make_float4(cr[4], cr[4], cr[5], cr[5]);
+  float2 m2u[R][6], na[R];  // -2 (u_i - c) and |u_i - c|^2, both lanes alike
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     float n2 = 0.f;
 #pragma unroll
     for (int d = 0; d < 6; ++d) {
-      const float u = load_u(rs, i0 + r * NT, d);
+      const float u = load_u(rs, i0 + r * NT, d) - cr[d];
       m2u[r][d] = make_float2(-2.f * u, -2.f * u);
       n2 = fmaf(u, u, n2);
     }
@@ -237,7 +248,11 @@ __global__ void __launch_bounds__(128)
   for (int tile = 0; tile < nct; ++tile) {
     const float4* src = cs + (int64_t)tile * (3 * kMT);
     __syncthreads();
-    for (int q = t; q < 3 * kMT; q += NT) sj[q] = src[q];
+    for (int q = t; q < 3 * kMT; q += NT) {
+      const int k3 = q % 3;
+      const float4 v = src[q], c = k3 == 0 ? cq0 : (k3 == 1 ? cq1 : cq2);
+      sj[q] = make_float4(v.x - c.x, v.y - c.y, v.z - c.z, v.w - c.w);
+    }
     __syncthreads();
     for (int q = t; q < kMT; q += NT) {
       const float4 P0 = sj[3 * q], P1 = sj[3 * q + 1], P2 = sj[3 * q + 2];

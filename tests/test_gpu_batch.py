@@ -207,6 +207,14 @@ def test_batch_adjoint_matches_oracle(uneq):
         hx = np.empty((3, int(offs[-1])))
         tb3 = nb.nbody_vjp_batch(h, len(sims), wx.T.copy(), wv.T.copy(), hx, None)
         assert np.array_equal(hx, x0b.cpu().numpy()) and np.array_equal(tb3, tb)
+        # cotangents 2^100 larger (their FP32 copies would overflow in the pair
+        # VJP unscaled): the per-simulation power-of-two scaling stages the
+        # same FP32 values, so every result is exactly 2^100 larger
+        big = 2.0 ** 100
+        x0b4, v0b4 = torch.empty_like(X), torch.empty_like(X)
+        tb4 = nb.nbody_vjp_batch(h, len(sims), WX * big, WV * big, x0b4, v0b4)
+        assert torch.equal(x0b4, x0b * big) and torch.equal(v0b4, v0b * big)
+        assert np.array_equal(tb4, tb * big)
         assert nb.nbody_get_status(h) == 0
     finally:
         nb.nbody_destroy(h)
