@@ -241,3 +241,34 @@ def test_batch_adjoint_needs_consistent_tape_requests():
     with pytest.raises(nb.NBodyError) as e:
         nb.nbody_create_batch(offs, [s[3] for s in sims])
     assert e.value.code == nb.NBODY_EINVAL
+
+
+def test_batch_adjoint_single_member_single_step():
+    """The smallest recorded run (one simulation, one step) and a run of no
+    recorded steps after a plain one: against the oracle, and ESTATE when the
+    last run did not record."""
+    x, v, m = plummer_sphere(50, 34, 1.0, 1.0, 1.0)
+    p = nb.make_params(1.0, 0.05, 1e-2, checkpoint_every=1)
+    h = nb.nbody_create_batch([0, 50], [p])
+    try:
+        X = torch.tensor(x.T.copy(), device=DEV)
+        V = torch.tensor(v.T.copy(), device=DEV)
+        nb.nbody_set_state(h, X, V, torch.tensor(m, device=DEV))
+        nb.nbody_integrate(h, 1)
+        rng = np.random.default_rng(5)
+        wx, wv = rng.normal(size=(50, 3)), rng.normal(size=(50, 3))
+        x0b, v0b = torch.empty_like(X), torch.empty_like(X)
+        tb = nb.nbody_vjp_batch(h, 1, torch.tensor(wx.T.copy(), device=DEV),
+                                torch.tensor(wv.T.copy(), device=DEV), x0b, v0b)
+        r = orc.vjp(orc.Physics(G=1.0, eps=0.05), x, v, m, 1e-2, 1, wx, wv)
+        for got, ref in ((x0b.cpu().numpy().T, r["x0bar"]), (v0b.cpu().numpy().T, r["v0bar"])):
+            assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
+        assert tb[0, 0] == pytest.approx(r["dt_bar"], rel=1e-5)
+        assert tb[0, 1] == pytest.approx(np.dot(m, r["mbar"]), rel=1e-5)
+        # a new state invalidates the recorded run
+        nb.nbody_set_state(h, X, V, torch.tensor(m, device=DEV))
+        with pytest.raises(nb.NBodyError) as e:
+            nb.nbody_vjp_batch(h, 1, None, None)
+        assert e.value.code == nb.NBODY_ESTATE
+    finally:
+        nb.nbody_destroy(h)
