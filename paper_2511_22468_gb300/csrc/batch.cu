@@ -1195,16 +1195,28 @@ int batch_set_state(Batch* b, const double* x, const double* v, const double* m)
   return NBODY_OK;
 }
 
+// padded state -> caller layout: one kernel per array into device memory,
+// or into a scratch copy and one transfer for host memory
 int batch_get_state(Batch* b, double* x, double* v) {
-  for (int s = 0; s < b->n_sims; ++s) {
-    const size_t bytes = (size_t)b->n[s] * sizeof(double);
-    for (int d = 0; d < 3; ++d) {
-      if (x)
-        BCK(cudaMemcpyAsync(x + d * b->ntot + b->off[s], b->x + d * b->ptot + b->poff[s],
-                            bytes, cudaMemcpyDefault, b->user));
-      if (v)
-        BCK(cudaMemcpyAsync(v + d * b->ntot + b->off[s], b->v + d * b->ptot + b->poff[s],
-                            bytes, cudaMemcpyDefault, b->user));
+  const size_t n3 = 3 * (size_t)b->ntot;
+  dim3 grid((unsigned)std::min<int64_t>(64, (b->ptot / b->n_sims + 255) / 256 + 1),
+            (unsigned)std::min(b->n_sims, 65535));
+  double* out[2] = {x, v};
+  const double* src[2] = {b->x, b->v};
+  for (int q = 0; q < 2; ++q) {
+    if (!out[q]) continue;
+    const bool dev = on_device(out[q]);
+    if (!dev && !b->cot) {
+      int rc = balloc(&b->cot, n3);
+      if (rc) return rc;
+    }
+    double* p = dev ? out[q] : b->cot;
+    k_move_batch<<<grid, 256, 0, b->user>>>(b->meta, b->n_sims, src[q], p, b->ntot, b->ptot, 1);
+    BCK(cudaGetLastError());
+    count_launch();
+    if (!dev) {
+      BCK(cudaMemcpyAsync(out[q], b->cot, n3 * sizeof(double), cudaMemcpyDefault, b->user));
+      BCK(cudaStreamSynchronize(b->user));  // the scratch is reused
     }
   }
   BCK(cudaStreamSynchronize(b->user));

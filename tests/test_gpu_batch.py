@@ -255,6 +255,12 @@ def test_batch_adjoint_single_member_single_step():
         V = torch.tensor(v.T.copy(), device=DEV)
         nb.nbody_set_state(h, X, V, torch.tensor(m, device=DEV))
         nb.nbody_integrate(h, 1)
+        # the state into device and into host arrays: the same bits
+        xd, xh = torch.empty_like(X), np.empty((3, 50))
+        vh = np.empty((3, 50))
+        nb.nbody_get_state(h, xd, None)
+        nb.nbody_get_state(h, xh, vh)
+        assert np.array_equal(xh, xd.cpu().numpy()) and np.all(np.isfinite(vh))
         rng = np.random.default_rng(5)
         wx, wv = rng.normal(size=(50, 3)), rng.normal(size=(50, 3))
         x0b, v0b = torch.empty_like(X), torch.empty_like(X)
