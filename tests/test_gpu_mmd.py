@@ -170,3 +170,36 @@ def test_cross_targets_match_oracle(n, m2, sets, targets, sig):
         assert e.value.code == nb.NBODY_EINVAL
     finally:
         nb.nbody_mmd_destroy(h)
+
+
+def test_cross_full_size_sampled():
+    """The bootstrap's full size (10^4 clouds of 1000 points against 1000
+    realisations of 1000 points, the launch configuration of the benchmark's
+    bootstrap): sampled (cloud, realisation) losses against the oracle."""
+    from paper_2511_22468_gb300.inputs import perturbed_clouds
+    n = m = 1000
+    sets, targets, sig = 10000, 1000, [0.5, 1.0, 2.0]
+    xb, vb = stream_like(n, 41)
+    rng = np.random.default_rng(42)
+    f = 1.0 + 0.05 * rng.normal(size=(sets, 1, 1))
+    dx = 0.3 * rng.normal(size=(sets, 1, 3))
+    cx = xb[None] * f + dx                        # (sets, n, 3)
+    cv = vb[None] * f + 0.01 * dx
+    rx, rv = perturbed_clouds(xb, vb, 0.05 * xb.std(axis=0), 0.05 * vb.std(axis=0), targets,
+                              seed=43)
+    Y = om.cloud(xb, vb)
+    mu, s = om.target_stats(Y)
+    to_dev = lambda a: torch.tensor(  # noqa: E731
+        np.ascontiguousarray(a.transpose(2, 0, 1).reshape(3, -1)), device=DEV)
+    h = nb.nbody_mmd_create(n, 1, soa(xb), soa(vb), sig)
+    try:
+        out = torch.empty(targets * sets, dtype=torch.float64, device=DEV)
+        nb.nbody_mmd_eval_cross(h, sets, to_dev(cx), to_dev(cv), targets, m, to_dev(rx),
+                                to_dev(rv), out)
+        got = out.cpu().numpy().reshape(targets, sets)
+    finally:
+        nb.nbody_mmd_destroy(h)
+    assert np.all(np.isfinite(got))
+    for t, b in [(0, 0), (999, 9999), (17, 5003), (500, 1), (3, 7777), (998, 2)]:
+        ref = om.mmd2(om.cloud(cx[b], cv[b]), om.cloud(rx[t], rv[t]), sig, mu, s)
+        assert abs(got[t, b] - ref) <= 1e-5 * len(sig), (t, b, got[t, b], ref)
