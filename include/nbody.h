@@ -208,8 +208,9 @@ NBODY_API int64_t nbody_launch_count(void);
  * step loop as one CUDA graph, captured on its first call for a given
  * step count.  On a batch context, nbody_set_params takes an array of
  * n_sims parameter sets; nbody_set_state / nbody_get_state use arrays laid
- * out 3 x offsets[n_sims] (simulations concatenated); nbody_vjp,
- * nbody_energy, nbody_momentum and the timing calls return EINVAL.
+ * out 3 x offsets[n_sims] (simulations concatenated); the adjoint is
+ * nbody_vjp_batch (nbody_vjp, nbody_energy, nbody_momentum and the timing
+ * calls return EINVAL).
  * Errors: EINVAL, ENODEV, ENOMEM, ECUDA. */
 NBODY_API int nbody_create_batch(nbody_ctx **out, int n_sims,
                                  const int64_t *offsets, const nbody_params *p,
