@@ -487,9 +487,11 @@ NBODY_API int nbody_stream_batch_create(nbody_stream_batch **out,
 
 /* losses[b] = MMD^2 of member b's final cloud at thetas[b] (host or device,
  * count x 4) against target b, and when theta_bars is not NULL (host or
- * device, count x 4) its gradient dL_b/dtheta_b.  The first call tunes the
- * batch's pair-kernel launch shape.  Synchronises.
- * Errors: EINVAL, ENOMEM, ECUDA, ENAN. */
+ * device, count x 4) its gradient dL_b/dtheta_b.  A member whose run or
+ * gradient leaves the finite range gets loss +inf and a NaN gradient; the
+ * members are independent, so the others are unaffected and the call still
+ * succeeds.  The first call tunes the batch's pair-kernel launch shape.
+ * Synchronises.  Errors: EINVAL, ENOMEM, ECUDA. */
 NBODY_API int nbody_stream_batch_loss_grad(nbody_stream_batch *s, const double *thetas,
                                            double *losses, double *theta_bars);
 

@@ -1468,6 +1468,12 @@ int batch_vjp(Batch* b, const double* xbar, const double* vbar, double* x0bar, d
   return batch_status(b);
 }
 
+int batch_clear_status(Batch* b) {
+  BCK(cudaMemsetAsync(b->status, 0, sizeof(int), b->gs));
+  BCK(cudaStreamSynchronize(b->gs));
+  return NBODY_OK;
+}
+
 int batch_status(Batch* b) {
   int st = 0;
   BCK(cudaMemcpyAsync(&st, b->status, sizeof(int), cudaMemcpyDeviceToHost, b->gs));

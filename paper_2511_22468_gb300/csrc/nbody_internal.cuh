@@ -245,6 +245,9 @@ int batch_vjp(Batch* b, const double* xbar, const double* vbar, double* x0bar, d
 // whether batch_vjp forms the shape-parameter gradients (default yes; the
 // batched pipeline, which needs the masses only, turns them off)
 void batch_set_vjp_shape(Batch* b, bool on);
+// clears the batch's sticky NaN status (the batched pipeline reports failed
+// members itself)
+int batch_clear_status(Batch* b);
 // the batch behind a batch context (nbody_api.cu)
 Batch* context_batch(nbody_ctx* c);
 int batch_status(Batch* b);

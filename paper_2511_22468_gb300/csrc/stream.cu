@@ -450,6 +450,21 @@ __global__ void k_theta_bar_batch(const double* __restrict__ tb, int64_t ns, dou
   out[4 * b + 3] = t[3] + orb[3 * b + 2];
 }
 
+// members whose loss or gradient is not finite (their run left the finite
+// range): loss +inf and gradient NaN, the other members untouched
+__global__ void k_mark_failed_batch(double* __restrict__ loss, double* __restrict__ out,
+                                    int64_t count) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count) return;
+  bool bad = !isfinite(loss[b]);
+  if (out)
+    for (int q = 0; q < 4; ++q) bad |= !isfinite(out[4 * b + q]);
+  if (!bad) return;
+  loss[b] = INFINITY;
+  if (out)
+    for (int q = 0; q < 4; ++q) out[4 * b + q] = NAN;
+}
+
 }  // namespace
 
 struct nbody_stream {
@@ -1106,6 +1121,10 @@ int nbody_stream_batch_loss_grad(nbody_stream_batch* s, const double* thetas, do
     }
   }
   int rc;
+  // every call starts from a clean status: a member that fails (its run
+  // leaves the finite range) is reported in its own loss and gradient
+  nb::Batch* bt = nb::context_batch(s->ctx);
+  if ((rc = nb::batch_clear_status(bt))) return rc;
   if ((rc = nbody_set_params(s->ctx, prm.data()))) return rc;
   if ((rc = nbody_set_state(s->ctx, s->x0, s->v0, s->m))) return rc;
   if (!s->tuned) {  // launch shape of the pair kernels, once, on the first state
@@ -1119,7 +1138,9 @@ int nbody_stream_batch_loss_grad(nbody_stream_batch* s, const double* thetas, do
     return rc;
   if (theta_bars) {
     // 5. reverse: n-body runs, Plummer shifts, backward orbits
-    if ((rc = nbody_vjp_batch(s->ctx, s->xbar, s->vbar, s->x0bar, s->v0bar, s->tb))) return rc;
+    rc = nbody_vjp_batch(s->ctx, s->xbar, s->vbar, s->x0bar, s->v0bar, s->tb);
+    if (rc == NBODY_ENAN) rc = nb::batch_clear_status(bt);  // failed members marked below
+    if (rc) return rc;
     SCK(cudaMemsetAsync(s->red, 0, 7 * (size_t)count * sizeof(double), s->s));
     k_ic_vjp_batch<<<(unsigned)count, 256, 0, s->s>>>(s->x0bar, s->v0bar, s->vhat, n, count,
                                                       s->red);
@@ -1134,9 +1155,14 @@ int nbody_stream_batch_loss_grad(nbody_stream_batch* s, const double* thetas, do
                                                               s->out);
     nb::count_launch();
     SCK(cudaGetLastError());
+  }
+  k_mark_failed_batch<<<blocks_for(count, 64), 64, 0, s->s>>>(s->loss,
+                                                              theta_bars ? s->out : nullptr, count);
+  nb::count_launch();
+  SCK(cudaGetLastError());
+  if (theta_bars)
     SCK(cudaMemcpyAsync(theta_bars, s->out, 4 * (size_t)count * sizeof(double),
                         cudaMemcpyDefault, s->s));
-  }
   SCK(cudaMemcpyAsync(losses, s->loss, (size_t)count * sizeof(double), cudaMemcpyDefault, s->s));
   SCK(cudaStreamSynchronize(s->s));
   return NBODY_OK;

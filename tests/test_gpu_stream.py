@@ -198,3 +198,29 @@ def test_stream_batch_losses_and_gradients_match_oracle():
     assert trace.shape == (4, 3) and np.all(np.diff(trace, axis=0) <= 0.0)
     assert np.all(Lb <= L) and np.array_equal(Lb, trace[-1])
     gpu.close()
+
+
+def test_stream_batch_isolates_a_failing_member():
+    """A member whose run leaves the finite range (a halo mass of 1e300)
+    gets loss +inf and a NaN gradient; the other members get the bits they
+    get without it, and the next call is clean again."""
+    from paper_2511_22468_gb300.stream import StreamBatch
+    cfg, xh, vh = _case()
+    orc = ostream.StreamModel(cfg, xh, vh)
+    truth = np.array(cfg.theta_true, float)
+    xt, vt = orc.final_state(truth)
+    tx, tv = np.stack([xt] * 3), np.stack([vt] * 3)
+    thetas = truth[None, :] * np.array([[1.05, 0.9, 1.1, 0.95], [1.0, 1.0, 1.0, 1.0],
+                                        [0.95, 1.05, 1.0, 1.02]])
+    gpu = StreamBatch(cfg, xh, vh, tx, tv)
+    L, g = gpu.loss_and_grad(thetas)
+    assert np.all(np.isfinite(L)) and np.all(np.isfinite(g))
+    bad = thetas.copy()
+    bad[1, 2] = 1e300
+    Lb, gb = gpu.loss_and_grad(bad)
+    assert Lb[1] == np.inf and np.all(np.isnan(gb[1]))
+    assert Lb[0] == L[0] and Lb[2] == L[2]
+    assert np.array_equal(gb[[0, 2]], g[[0, 2]])
+    L2, g2 = gpu.loss_and_grad(thetas)
+    assert np.array_equal(L2, L) and np.array_equal(g2, g)
+    gpu.close()
