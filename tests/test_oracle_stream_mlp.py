@@ -116,6 +116,12 @@ def test_stream_mmd_pipeline_gradient_vs_fd():
         d1 = (f(h) - f(-h)) / (2 * h)
         d2 = (f(h / 2) - f(-h / 2)) / h
         assert (4 * d2 - d1) / 3 == pytest.approx(g[k], rel=1e-5)
+    # the two parts the error bounds use add up to the gradient (recomputed
+    # at th: the FD calls above do not touch them)
+    model.mmd_loss_and_grad(th, Y, sig, mu, sd)
+    p1, p2 = model.grad_parts
+    np.testing.assert_allclose(p1 + p2, g, rtol=1e-14, atol=0.0)
+    assert p1[0] == model.t_end_parts[0] and p2[0] == model.t_end_parts[1]
 
 
 def test_stream_loss_zero_at_truth():
