@@ -709,13 +709,15 @@ NBODY_API void nbody_mlp_destroy(nbody_mlp *m);
  * cudaFree, no allocating library routine): its scratch is one 4 MiB
  * device array inside the library, which every GPU that loads the library
  * holds until the process exits.  x (3 x n), m (n) and acc (3 x n) are
- * caller-owned device memory; center is 3 host doubles.
+ * caller-owned device memory; center is 3 host doubles, read by value
+ * during the call (the caller may reuse them as soon as the call returns).
  *
  * - n must be in [1, NBODY_NOALLOC_MAX_N]; a larger n returns NBODY_ESIZE
  *   and launches nothing.
  * - The first call on a device looks up the device address of the array
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture on the device.
+ *   (cudaGetSymbolAddress) with that device current, and looks it up again
+ *   after the device's context has been re-created (cudaDeviceReset); make
+ *   that first call before any stream capture on the device.
  * - Asynchronous: acc is complete when cuda_stream reaches the end of the
  *   call.  Every call on a device shares the one array, so calls that may
  *   overlap on the GPU (issued to different streams without ordering)

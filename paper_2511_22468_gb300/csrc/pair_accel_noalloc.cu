@@ -15,6 +15,7 @@
 // position and mass copy) are cleared on every call.  Two calls that overlap
 // on the GPU (different streams, no ordering between them) race on the
 // array and give undefined results.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -28,24 +29,79 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-// device-side address of g_scratch, looked up once per device; in host code
-// the name g_scratch is only a host-side stand-in, not a device address
-void* g_addr[kMaxDevices] = {};
+// The device address of g_scratch, looked up with the device current (in
+// host code the name g_scratch is only a host-side stand-in, not a device
+// address).  A module's device address belongs to one context: after
+// cudaDeviceReset the device's primary context is re-created and the
+// library's module may be loaded at another address, so each cached address
+// is keyed by the unique id of the context it was looked up in, and looked
+// up again when the current context's id differs.
+struct Slot {
+  unsigned long long ctx_id;
+  void* addr;
+};
+Slot g_slot[kMaxDevices] = {};
 std::mutex g_mu;
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+bool g_fn_looked_up = false;
+
+// id of the calling thread's current context (unique for the life of the
+// process), 0 when there is none or the driver does not report it; the
+// driver functions are reached through the runtime, so the library does not
+// link against the driver library.  Called with g_mu held.
+unsigned long long current_context_id() {
+  if (!g_fn_looked_up) {
+    g_fn_looked_up = true;
+    cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+    void *f1 = nullptr, *f2 = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault,
+                                         &q1) != cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault,
+                                         &q2) != cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      f1 = f2 = nullptr;
+    }
+    g_ctx_current = (CtxGetCurrentFn)f1;
+    g_ctx_id = (CtxGetIdFn)f2;
+  }
+  if (!g_ctx_current || !g_ctx_id) return 0;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (g_ctx_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+  if (g_ctx_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 int scratch_address(int dev, void** out) {
   if (dev < 0 || dev >= kMaxDevices) return NBODY_ENODEV;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
+  unsigned long long id = current_context_id();
+  Slot& sl = g_slot[dev];
+  if (!sl.addr || id == 0 || id != sl.ctx_id) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
       return NBODY_ECUDA;
     }
-    g_addr[dev] = p;
+    sl.addr = p;
+    sl.ctx_id = current_context_id();  // the lookup made the context current
   }
-  *out = g_addr[dev];
+  *out = sl.addr;
   return NBODY_OK;
+}
+
+// the recentring origin, passed by value, into the scratch array: the
+// caller's host copy is read when the call is made, never later by a copy
+// waiting on the stream
+__global__ void k_put_center(double* cen, double cx, double cy, double cz) {
+  cen[0] = cx;
+  cen[1] = cy;
+  cen[2] = cz;
 }
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -95,8 +151,11 @@ extern "C" int nbody_pair_accel_noalloc(int64_t n, const double* x,
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(mp, m, (size_t)n * sizeof(double),
                         cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(cen, center, 3 * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    k_put_center<<<1, 1, 0, s>>>(cen, center[0], center[1], center[2]);
+    nb::count_launch();
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = nb::launch_stage(xp, mp, cen, n, npad, st, s);
   if (e == cudaSuccess)
     e = nb::launch_pair_accel(cfg, st, npad, (float)(eps * eps), part, nullptr, s);

@@ -12,6 +12,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+from oracle import core as orc  # noqa: E402
 from paper_2511_22468_gb300 import nbody as nb  # noqa: E402
 from paper_2511_22468_gb300.inputs import plummer_sphere  # noqa: E402
 
@@ -50,6 +51,33 @@ def test_noalloc_matches_allocating_entry_point_twice():
         nb.nbody_pair_accel_noalloc(X, M, 1.0, 0.01, (0.1, -0.2, 0.05), got)
         torch.cuda.synchronize()
         assert _rel_err(got.cpu().numpy(), ref.cpu().numpy()) <= 1e-5
+
+
+def test_noalloc_matches_oracle_direct_sum():
+    """A small, uneven n with unequal masses and a non-zero recentring origin
+    against the oracle's FP64 direct sum (not only against the allocating
+    entry point, which runs the same kernels), twice in a row.  The centre is
+    a host buffer that is overwritten right after each call returns, before
+    the stream has run: the call reads it by value."""
+    import ctypes as C
+    dev = torch.device("cuda:0")
+    n = 1001
+    x, v, m = plummer_sphere(n, 11, 1.0, 1.0, 1.0, center=(0.3, -0.1, 0.2))
+    m = m * np.random.default_rng(12).uniform(0.5, 1.5, n)
+    X = torch.tensor(x.T.copy(), device=dev)
+    M = torch.tensor(m, device=dev)
+    ref = orc.pair_accel(x, m, 1.0, 0.01)
+    stream = torch.cuda.current_stream().cuda_stream
+    for _ in range(2):
+        got = torch.full((3, n), float("nan"), dtype=torch.float64, device=dev)
+        cen = (C.c_double * 3)(0.3, -0.1, 0.2)
+        rc = nb.lib().nbody_pair_accel_noalloc(n, C.c_void_p(X.data_ptr()),
+                                               C.c_void_p(M.data_ptr()), 1.0, 0.01, cen,
+                                               C.c_void_p(got.data_ptr()), C.c_void_p(stream))
+        cen[0], cen[1], cen[2] = 5.0, 7.0, -9.0
+        assert rc == nb.NBODY_OK
+        torch.cuda.synchronize()
+        assert _rel_err(got.cpu().numpy(), ref.T) <= 1e-5
 
 
 def test_noalloc_rejects_sizes_beyond_its_buffer():
