@@ -437,6 +437,12 @@ NBODY_API int nbody_stream_initial_state(nbody_stream *s, const double theta[4],
 NBODY_API int nbody_stream_autotune(nbody_stream *s, const double theta[4],
                                     int probe_launches);
 
+/* Launch shape {variant, threads, per_thread, chunks} (host, 4 ints) of the
+ * pipeline's pair-force (vjp = 0) or pair-VJP (vjp = 1) kernel, as chosen by
+ * the default rule or by nbody_stream_autotune (see nbody_get_pair_shape).
+ * Errors: EINVAL. */
+NBODY_API int nbody_stream_get_pair_shape(nbody_stream *s, int vjp, int out[4]);
+
 /* Steps 1-2 for `count` parameter vectors at once (host or device, count x 4
  * doubles, all > 0), one backward orbit per GPU thread: x0, v0 (device,
  * 3 x (count n) SoA, member b in columns b n .. b n + n - 1: the layout of
@@ -490,8 +496,11 @@ NBODY_API int nbody_stream_batch_create(nbody_stream_batch **out,
  * device, count x 4) its gradient dL_b/dtheta_b.  A member whose run or
  * gradient leaves the finite range gets loss +inf and a NaN gradient; the
  * members are independent, so the others are unaffected and the call still
- * succeeds.  The first call tunes the batch's pair-kernel launch shape.
- * Synchronises.  Errors: EINVAL, ENOMEM, ECUDA. */
+ * succeeds.  When the reverse sweep raised the NaN flag but no member's loss
+ * or gradient shows a non-finite value (the failure cannot be attributed to
+ * a member), the call returns NBODY_ENAN.  The first call tunes the batch's
+ * pair-kernel launch shape.  Synchronises.  Errors: EINVAL, ENOMEM, ECUDA,
+ * ENAN. */
 NBODY_API int nbody_stream_batch_loss_grad(nbody_stream_batch *s, const double *thetas,
                                            double *losses, double *theta_bars);
 

@@ -453,13 +453,14 @@ __global__ void k_theta_bar_batch(const double* __restrict__ tb, int64_t ns, dou
 // members whose loss or gradient is not finite (their run left the finite
 // range): loss +inf and gradient NaN, the other members untouched
 __global__ void k_mark_failed_batch(double* __restrict__ loss, double* __restrict__ out,
-                                    int64_t count) {
+                                    int64_t count, unsigned* __restrict__ nmark) {
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= count) return;
   bool bad = !isfinite(loss[b]);
   if (out)
     for (int q = 0; q < 4; ++q) bad |= !isfinite(out[4 * b + q]);
   if (!bad) return;
+  atomicAdd(nmark, 1u);
   loss[b] = INFINITY;
   if (out)
     for (int q = 0; q < 4; ++q) out[4 * b + q] = NAN;
@@ -503,6 +504,7 @@ struct nbody_stream_batch {
   double *xbar = nullptr, *vbar = nullptr, *x0bar = nullptr, *v0bar = nullptr;
   double *ox = nullptr, *ovh = nullptr, *g6 = nullptr;
   double *loss = nullptr, *tb = nullptr, *red = nullptr, *orb = nullptr, *out = nullptr;
+  unsigned* nmark = nullptr;  // members marked failed by the last call
 };
 
 namespace {
@@ -549,6 +551,7 @@ void free_stream_batch(nbody_stream_batch* s) {
                      &s->xbar, &s->vbar, &s->x0bar, &s->v0bar, &s->ox, &s->ovh, &s->g6,
                      &s->loss, &s->tb, &s->red, &s->orb, &s->out})
     sfree(*p);
+  sfree(s->nmark);
 }
 
 void unit3(const double* a, double* out) {
@@ -782,6 +785,11 @@ int nbody_stream_autotune(nbody_stream* s, const double theta[4], int probe_laun
   if ((rc = nbody_set_params(s->ctx, &p))) return rc;
   if ((rc = nbody_set_state(s->ctx, s->x0, s->v0, s->m))) return rc;
   return nbody_autotune_pair(s->ctx, probe_launches, nullptr, nullptr);
+}
+
+int nbody_stream_get_pair_shape(nbody_stream* s, int vjp, int out[4]) {
+  if (!s || !out) return NBODY_EINVAL;
+  return nbody_get_pair_shape(s->ctx, vjp, out);
 }
 
 int nbody_stream_head(nbody_stream* s, const double* x, double* density, double* loss) {
@@ -1046,6 +1054,7 @@ int nbody_stream_batch_create(nbody_stream_batch** out, const nbody_stream_cfg* 
   if (!rc) rc = salloc(&s->red, 7 * (size_t)count);
   if (!rc) rc = salloc(&s->orb, 3 * (size_t)count);
   if (!rc) rc = salloc(&s->out, 4 * (size_t)count);
+  if (!rc) rc = salloc(&s->nmark, 1);
   if (!rc) rc = salloc(&dtx, tm3);
   if (!rc) rc = salloc(&dtv, tm3);
   if (!rc && (cudaMemcpyAsync(s->xhat, xhat, n3 * sizeof(double), cudaMemcpyDefault, s->s) ||
@@ -1121,6 +1130,7 @@ int nbody_stream_batch_loss_grad(nbody_stream_batch* s, const double* thetas, do
     }
   }
   int rc;
+  bool nan_seen = false;
   // every call starts from a clean status: a member that fails (its run
   // leaves the finite range) is reported in its own loss and gradient
   nb::Batch* bt = nb::context_batch(s->ctx);
@@ -1139,7 +1149,10 @@ int nbody_stream_batch_loss_grad(nbody_stream_batch* s, const double* thetas, do
   if (theta_bars) {
     // 5. reverse: n-body runs, Plummer shifts, backward orbits
     rc = nbody_vjp_batch(s->ctx, s->xbar, s->vbar, s->x0bar, s->v0bar, s->tb);
-    if (rc == NBODY_ENAN) rc = nb::batch_clear_status(bt);  // failed members marked below
+    if (rc == NBODY_ENAN) {  // failed members are marked below
+      nan_seen = true;
+      rc = nb::batch_clear_status(bt);
+    }
     if (rc) return rc;
     SCK(cudaMemsetAsync(s->red, 0, 7 * (size_t)count * sizeof(double), s->s));
     k_ic_vjp_batch<<<(unsigned)count, 256, 0, s->s>>>(s->x0bar, s->v0bar, s->vhat, n, count,
@@ -1156,15 +1169,21 @@ int nbody_stream_batch_loss_grad(nbody_stream_batch* s, const double* thetas, do
     nb::count_launch();
     SCK(cudaGetLastError());
   }
-  k_mark_failed_batch<<<blocks_for(count, 64), 64, 0, s->s>>>(s->loss,
-                                                              theta_bars ? s->out : nullptr, count);
+  SCK(cudaMemsetAsync(s->nmark, 0, sizeof(unsigned), s->s));
+  k_mark_failed_batch<<<blocks_for(count, 64), 64, 0, s->s>>>(
+      s->loss, theta_bars ? s->out : nullptr, count, s->nmark);
   nb::count_launch();
   SCK(cudaGetLastError());
   if (theta_bars)
     SCK(cudaMemcpyAsync(theta_bars, s->out, 4 * (size_t)count * sizeof(double),
                         cudaMemcpyDefault, s->s));
   SCK(cudaMemcpyAsync(losses, s->loss, (size_t)count * sizeof(double), cudaMemcpyDefault, s->s));
+  unsigned marked = 0;
+  SCK(cudaMemcpyAsync(&marked, s->nmark, sizeof(unsigned), cudaMemcpyDeviceToHost, s->s));
   SCK(cudaStreamSynchronize(s->s));
+  // the NaN flag came from a value that reached no member's loss or
+  // gradient: the failure cannot be attributed, so it is reported
+  if (nan_seen && marked == 0) return NBODY_ENAN;
   return NBODY_OK;
 }
 

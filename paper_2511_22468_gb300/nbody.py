@@ -54,7 +54,7 @@ EXPORTED = ("nbody_create", "nbody_destroy", "nbody_set_params",
             "nbody_mmd_eval_batch", "nbody_mmd_eval_cross", "nbody_mmd_target_stats",
             "nbody_mmd_destroy",
             "nbody_stream_set_target_cloud", "nbody_stream_initial_states",
-            "nbody_ext_accel", "nbody_stream_autotune", "nbody_orbitfit_create", "nbody_orbitfit_eval",
+            "nbody_ext_accel", "nbody_stream_autotune", "nbody_stream_get_pair_shape", "nbody_orbitfit_create", "nbody_orbitfit_eval",
             "nbody_orbitfit_lm", "nbody_orbitfit_fisher", "nbody_orbitfit_arc",
             "nbody_orbitfit_destroy", "nbody_stream_batch_create",
             "nbody_stream_batch_loss_grad", "nbody_stream_batch_destroy")
@@ -155,6 +155,7 @@ def lib():
         L.nbody_stream_set_target_cloud.argtypes = [vp, i64, vp, vp, dp, C.c_int, dp]
         L.nbody_stream_initial_states.argtypes = [vp, i64, vp, vp, vp, vp, vp]
         L.nbody_stream_autotune.argtypes = [vp, dp, C.c_int]
+        L.nbody_stream_get_pair_shape.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
         L.nbody_stream_forward.argtypes = [vp, dp, dp, vp]
         L.nbody_stream_grad.argtypes = [vp, dp]
         L.nbody_stream_initial_state.argtypes = [vp, dp, vp, vp, vp, dp]
@@ -643,6 +644,14 @@ def nbody_stream_initial_states(h, thetas, x0, v0, m, com=None):
 def nbody_stream_autotune(h, theta, probe_launches=3):
     th = (C.c_double * 4)(*[float(t) for t in theta])
     _check(lib().nbody_stream_autotune(h, th, int(probe_launches)), "nbody_stream_autotune")
+
+
+def nbody_stream_get_pair_shape(h, vjp):
+    """(variant, threads, per_thread, chunks) of the pipeline's pair-force
+    (vjp = 0) or pair-VJP (vjp = 1) kernel."""
+    out = (C.c_int * 4)()
+    _check(lib().nbody_stream_get_pair_shape(h, int(vjp), out), "nbody_stream_get_pair_shape")
+    return tuple(out)
 
 
 def nbody_stream_head(h, x, density, want_loss=False):
