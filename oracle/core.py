@@ -70,7 +70,7 @@ def lib():
         L.orc_pair_vjp.argtypes = [C.c_int64, _D, _D, C.c_double, C.c_double, _D,
                                    _I64, C.c_int64, _D]
         L.orc_pair_mass_vjp.argtypes = [C.c_int64, _D, C.c_double, C.c_double,
-                                        _D, _D]
+                                        _D, _I64, C.c_int64, _D]
         L.orc_ext_accel_parts.argtypes = [P, _D, _D]
         L.orc_ext_accel.argtypes = [P, _D, _D]
         L.orc_ext_potential.argtypes = [P, _D]
@@ -138,11 +138,18 @@ def pair_vjp(x, m, G, eps, lam, rows=None):
     return out
 
 
-def pair_mass_vjp(x, G, eps, lam):
+def pair_mass_vjp(x, G, eps, lam, rows=None):
+    """mbar_j = sum_i lam_i . d a_i / d m_j for rows j (all when None)."""
     x = _f64(x, (-1, 3))
     lam = _f64(lam, (-1, 3))
-    out = np.zeros(x.shape[0])
-    lib().orc_pair_mass_vjp(x.shape[0], _d(x), G, eps, _d(lam), _d(out))
+    n = x.shape[0]
+    if rows is None:
+        nr, rp = n, None
+    else:
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        nr, rp = rows.shape[0], rows.ctypes.data_as(_I64)
+    out = np.zeros(nr)
+    lib().orc_pair_mass_vjp(n, _d(x), G, eps, _d(lam), rp, nr, _d(out))
     return out
 
 

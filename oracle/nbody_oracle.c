@@ -161,12 +161,15 @@ void orc_pair_vjp(int64_t n, const double *x, const double *m, double G,
 }
 
 /* mbar_j = sum_{i != j} lam_i . d a_i / d m_j, d a_i / d m_j =
- * -G (x_i - x_j) s_ij^-3. */
+ * -G (x_i - x_j) s_ij^-3, for the rows j listed in rows (all j when rows is
+ * NULL; out[r] belongs to rows[r]). */
 void orc_pair_mass_vjp(int64_t n, const double *x, double G, double eps,
-                       const double *lam, double *out) {
+                       const double *lam, const int64_t *rows, int64_t nrows,
+                       double *out) {
   const double e2 = eps * eps;
 #pragma omp parallel for schedule(dynamic, 8)
-  for (int64_t j = 0; j < n; ++j) {
+  for (int64_t r = 0; r < nrows; ++r) {
+    const int64_t j = rows ? rows[r] : r;
     double acc = 0.0;
     for (int64_t i = 0; i < n; ++i) {
       if (i == j) continue;
@@ -178,7 +181,7 @@ void orc_pair_mass_vjp(int64_t n, const double *x, double G, double eps,
       acc -= G * (lam[3 * i + 0] * dx + lam[3 * i + 1] * dy +
                   lam[3 * i + 2] * dz) / s3;
     }
-    out[j] = acc;
+    out[r] = acc;
   }
 }
 
@@ -553,7 +556,7 @@ static void kick_adjoint(const orc_params *p, int64_t n, const double *X,
     orc_pair_vjp(n, X, m, p->G, p->eps, lam, NULL, n, work_g);
     for (int64_t k = 0; k < 3 * n; ++k) xbar[k] += c * work_g[k];
     if (mbar) {
-      orc_pair_mass_vjp(n, X, p->G, p->eps, lam, work_m);
+      orc_pair_mass_vjp(n, X, p->G, p->eps, lam, NULL, n, work_m);
       for (int64_t j = 0; j < n; ++j) mbar[j] += c * work_m[j];
     }
   }

@@ -86,6 +86,10 @@ def test_pair_vjp_matches_fd_jacobian(orc):
         mm[j] -= 1e-6
         fd = np.sum(lam * (o.pair_accel(x, mp, 1.0, eps) - o.pair_accel(x, mm, 1.0, eps))) / 2e-6
         assert fd == pytest.approx(mb[j], rel=1e-6)
+    # row selections give the rows of the full products
+    rows = np.array([39, 0, 17])
+    assert np.array_equal(o.pair_mass_vjp(x, 1.0, eps, lam, rows=rows), mb[rows])
+    assert np.array_equal(o.pair_vjp(x, m, 1.0, eps, lam, rows=rows), g[rows])
 
 
 def test_pair_mean_field_plummer(orc):
