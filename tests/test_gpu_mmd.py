@@ -3,7 +3,8 @@
 Tolerances: the kernel values are summed in FP32 within 512-point tiles
 (ex2.approx, relative error ~2^-22) and in FP64 across tiles; each of the
 three terms of MMD^2 is at most n_sigma, so the loss is compared with an
-absolute bound of 1e-5 * n_sigma and the gradient norm-wise at 1e-4.
+absolute bound of 1e-5 * n_sigma and the gradient point by point at 1e-4
+(relative to each point's gradient, floored at 1e-3 of the rms).
 """
 import numpy as np
 import pytest
@@ -12,6 +13,7 @@ torch = pytest.importorskip("torch")
 
 from oracle import mmd as om  # noqa: E402
 from paper_2511_22468_gb300 import nbody as nb  # noqa: E402
+from tolerances import per_particle_err  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -58,7 +60,7 @@ def test_mmd_matches_oracle(n, m, sig):
         L = nb.nbody_mmd_eval(h, soa(xs), soa(vs), xb, vb)
         assert abs(L - L_ref) <= 1e-5 * len(sig)
         g = np.concatenate([xb.cpu().numpy().T, vb.cpu().numpy().T], axis=1)
-        assert np.linalg.norm(g - g_ref) <= 1e-4 * np.linalg.norm(g_ref)
+        assert per_particle_err(g, g_ref) <= 1e-4
         mu, sc = nb.nbody_mmd_target_stats(h)
         mu_ref, sc_ref = om.target_stats(Y)
         np.testing.assert_allclose(mu, mu_ref, rtol=1e-12, atol=1e-14)

@@ -6,8 +6,9 @@ Tolerances (stated for the method's FP32 pair sum with FP64 state):
   * positions after 100 steps: max |dx| / r_scale <= 1e-6 (r_scale = the
     Plummer scale radius);
   * energy and momentum drift within 1e-6 of the oracle's;
-  * gradients: relative 1e-4 of the oracle adjoint (norm-wise per array,
-    element-wise per scalar).
+  * gradients: relative 1e-4 of the oracle adjoint, particle by particle for
+    dL/dx0, dL/dv0 and dL/dm (the acceleration's measure: |g_k - r_k| /
+    (|r_k| + 1e-3 rms|r|)), element-wise for every scalar.
 """
 import numpy as np
 import pytest
@@ -18,6 +19,7 @@ from oracle import core as orc  # noqa: E402
 from paper_2511_22468_gb300 import nbody as nb  # noqa: E402
 from paper_2511_22468_gb300.configs import C1, C3  # noqa: E402
 from paper_2511_22468_gb300.inputs import plummer_sphere  # noqa: E402
+from tolerances import per_particle_err  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -47,8 +49,7 @@ def to_np(t):
 
 
 def acc_err(a, ref):
-    scale = np.linalg.norm(ref, axis=1) + 1e-3 * np.sqrt(np.mean(np.sum(ref * ref, axis=1)))
-    return np.max(np.linalg.norm(a - ref, axis=1) / scale)
+    return per_particle_err(a, ref)
 
 
 # -------------------------------------------------------------- pair force --
@@ -92,7 +93,7 @@ def test_full_size_step_and_adjoint_sampled():
       x1 - x0 - dt v0 = (dt^2 / 2) a(x0),
       x0bar - W = (dt^2 / 2) (J_pair + J_ext)(x0)^T W,
     against the oracle on 256 rows (acceleration 1e-5 per particle,
-    gradient 1e-4 norm-wise)."""
+    gradient 1e-4 per particle)."""
     n, dt, pot = C3.n, C3.dt, C3.pot
     x, v, m = plummer_sphere(n, C3.seed, C3.G, C3.M, C3.a, center=C3.X0, velocity=C3.V0)
     sim = _sim(n, C3.G, C3.eps, dt, K=1, ext=3, pot=pot, center=C3.X0, center_vel=C3.V0,
@@ -113,8 +114,62 @@ def test_full_size_step_and_adjoint_sampled():
     Jt = orc.pair_vjp(x, m, C3.G, C3.eps, W, rows=rows)
     Jt += np.array([orc.ext_jac(ph, x[k]).T @ W[k] for k in rows])
     gb = (to_np(x0b)[rows] - W[rows]) / (0.5 * dt * dt)
-    assert np.linalg.norm(gb - Jt) <= 1e-4 * np.linalg.norm(Jt)
+    assert per_particle_err(gb, Jt) <= 1e-4
     sim.close()
+
+
+# (variant, threads, per thread, chunks (0: automatic), where the chunk sums
+# are added (-1: automatic))
+VJP_SHAPES = [(0, 256, 2, 0, -1), (0, 128, 4, 0, -1), (0, 128, 2, 0, -1), (0, 128, 1, 0, -1),
+              (0, 128, 2, 9, 1), (0, 128, 2, 9, 0)]
+
+
+@pytest.mark.parametrize("eqm", [False, True])
+def test_tile_vjp_and_mass_gradient_sampled(eqm):
+    """The tile pair-VJP kernels, general masses (spread over
+    [0.5, 1.5] of the mean) and equal masses, with and without the
+    per-particle mass gradient, in every supported tile shape (and with the
+    chunk sums added by the pair kernel and by the consumer), at N = 70001
+    (npad = 70656, a ragged last tile): one kick-drift-kick step and its
+    reverse sweep with
+    xbar = W, vbar = 0, whose closed forms for sampled rows k are
+      x0bar_k - W_k = (dt^2 / 2) ((J_pair + J_ext)(x0)^T W)_k,
+      mbar_k       = (dt^2 / 2) sum_i W_i . d a_i / d m_k,
+    against the oracle on 256 rows, 1e-4 per particle."""
+    n, dt = 70001, 0.5
+    x, v, m = plummer_sphere(n, 31, C1.G, 1e5, 0.03, center=C1.X0, velocity=C1.V0)
+    if not eqm:
+        m = m * np.random.default_rng(32).uniform(0.5, 1.5, n)
+    pot = C1.pot
+    W = np.random.default_rng(33).normal(size=(n, 3))
+    rows = np.random.default_rng(34).choice(n, 256, replace=False)
+    ph = orc.Physics(G=C1.G, eps=C1.eps, ext=orc.NFW | orc.MN, nfw_M=pot.nfw_M,
+                     nfw_rs=pot.nfw_rs, mn_M=pot.mn_M, mn_a=pot.mn_a, mn_b=pot.mn_b)
+    Jt = orc.pair_vjp(x, m, C1.G, C1.eps, W, rows=rows)
+    Jt += np.array([orc.ext_jac(ph, x[k]).T @ W[k] for k in rows])
+    mref = orc.pair_mass_vjp(x, C1.G, C1.eps, W, rows=rows)
+    X, V, M, WG = to_gpu(x), to_gpu(v), to_gpu(m), to_gpu(W)
+    for variant, nt, r, chunks, finish in VJP_SHAPES:
+        sim = _sim(n, C1.G, C1.eps, dt, K=1, ext=3, pot=pot, center=C1.X0,
+                   center_vel=C1.V0, guide=True)
+        nb.nbody_set_pair_shape(sim.h, 1, variant, nt, r, chunks)
+        if finish >= 0:
+            nb.nbody_set_pair_finish(sim.h, 1, finish)
+        sim.set_state(X, V, M)
+        sim.integrate(1)
+        x0b = torch.empty((3, n), dtype=torch.float64, device=DEV)
+        sim.vjp(WG, None, x0b, None)                       # no mass gradient
+        gb = (to_np(x0b)[rows] - W[rows]) / (0.5 * dt * dt)
+        assert per_particle_err(gb, Jt) <= 1e-4, (variant, nt, r, chunks, finish)
+        mb = torch.empty(n, dtype=torch.float64, device=DEV)
+        x0b2 = torch.empty_like(x0b)
+        sim.vjp(WG, None, x0b2, None, mb)                  # with it
+        assert torch.allclose(x0b2, x0b, rtol=1e-12, atol=0.0)
+        got = to_np(mb)[rows] / (0.5 * dt * dt)
+        assert per_particle_err(got, mref) <= 1e-4, (variant, nt, r, chunks, finish)
+        assert tuple(nb.nbody_get_pair_shape(sim.h, 1))[:3] == (variant, nt, r)
+        assert sim.status() == 0
+        sim.close()
 
 
 # --------------------------------------------------------------- trajectory --
@@ -224,14 +279,18 @@ def test_bitwise_reproducible():
                                              (50, False, 3, False), (4, True, 3, False),
                                              (7, False, 0, True), (9, True, 3, True)])
 def test_adjoint_matches_oracle(K, lean, ext, uneq):
-    """Discrete adjoint against the oracle's: dL/dx0, dL/dv0, dL/ddt, the mass
-    scale, dL/dM_NFW, dL/dM_MN; ragged last segments (50 = 7*7 + 1); equal
-    masses (the kernels that leave the mass out) and unequal ones."""
+    """Discrete adjoint against the oracle's: dL/dx0, dL/dv0, dL/dm particle
+    by particle, dL/ddt, the mass scale, dL/dM_NFW, dL/dM_MN; ragged last
+    segments (50 = 7*7 + 1); equal masses (the kernels that leave the mass
+    out) and unequal ones.  The cluster on its orbit takes steps of 0.1 Myr:
+    the 50 steps span 1.5 dynamical times (3.3 Myr), where the gradient of
+    each particle is well conditioned (longer runs: the envelope test
+    below)."""
     n, steps = 256, 50
     if ext:
         x, v, m = plummer_sphere(n, 12, C1.G, C1.M_prog, C1.a_prog, center=C1.X0,
                                  velocity=C1.V0)
-        G, eps, dt, pot = C1.G, C1.eps, 0.5, C1.pot
+        G, eps, dt, pot = C1.G, C1.eps, 0.1, C1.pot
     else:
         x, v, m = plummer_sphere(n, 12, 1.0, 1.0, 1.0)
         G, eps, dt, pot = 1.0, 0.05, 2e-3, None
@@ -254,7 +313,7 @@ def test_adjoint_matches_oracle(K, lean, ext, uneq):
         ph = orc.Physics(G=G, eps=eps)
     r = orc.vjp(ph, x, v, m, dt, steps, wx, wv)
     for got, ref in ((to_np(x0b), r["x0bar"]), (to_np(v0b), r["v0bar"])):
-        assert np.linalg.norm(got - ref) <= 1e-4 * np.linalg.norm(ref)
+        assert per_particle_err(got, ref) <= 1e-4
     assert tb[0] == pytest.approx(r["dt_bar"], rel=1e-4)
     assert tb[1] == pytest.approx(np.dot(m, r["mbar"]), rel=1e-4)
     if ext:
@@ -273,13 +332,53 @@ def test_adjoint_matches_oracle(K, lean, ext, uneq):
     mb = torch.empty(n, dtype=torch.float64, device=DEV)
     tb3 = sim.vjp(to_gpu(wx), to_gpu(wv), x0b3 := torch.empty_like(x0b), None, mb)
     got = to_np(mb)
-    assert np.linalg.norm(got - r["mbar"]) <= 1e-4 * np.linalg.norm(r["mbar"])
+    assert per_particle_err(got, r["mbar"]) <= 1e-4
     assert float(np.dot(m, got)) == pytest.approx(tb3[1], rel=1e-5)
     assert torch.allclose(x0b3, x0b, rtol=1e-12, atol=0.0)
     assert tb3 == pytest.approx(tb, rel=1e-12)
     mb2 = torch.empty_like(mb)
     sim.vjp(to_gpu(wx), to_gpu(wv), None, None, mb2)
     assert torch.equal(mb, mb2)
+
+
+def test_adjoint_chaotic_horizon_within_oracle_envelope():
+    """Over 7.5 dynamical times (50 steps of 0.5 Myr) the cluster's chaos
+    amplifies a perturbation by ~e^7.5, so no FP32 force sum can follow the
+    FP64 oracle's trajectory to 1e-4 per particle: the oracle itself, run
+    from positions perturbed by 6e-8 relative (the FP32 rounding of x - c),
+    differs from its own gradients by ~3e-4 per particle in dL/dm.  Bound:
+    per particle, the GPU stays within 4x the larger of two such envelopes
+    (and 1e-4); norm-wise and for every scalar, 1e-4 relative."""
+    n, steps, dt, pot = 256, 50, 0.5, C1.pot
+    x, v, m = plummer_sphere(n, 12, C1.G, C1.M_prog, C1.a_prog, center=C1.X0, velocity=C1.V0)
+    sim = _sim(n, C1.G, C1.eps, dt, K=9, ext=3, pot=pot, center=x.mean(axis=0),
+               center_vel=v.mean(axis=0), guide=True)
+    sim.set_state(to_gpu(x), to_gpu(v), to_gpu(m))
+    sim.integrate(steps)
+    rng = np.random.default_rng(50)
+    wx, wv = rng.normal(size=(n, 3)), rng.normal(size=(n, 3))
+    x0b = torch.empty((3, n), dtype=torch.float64, device=DEV)
+    v0b = torch.empty_like(x0b)
+    mb = torch.empty(n, dtype=torch.float64, device=DEV)
+    tb = sim.vjp(to_gpu(wx), to_gpu(wv), x0b, v0b, mb)
+    ph = orc.Physics(G=C1.G, eps=C1.eps, ext=orc.NFW | orc.MN, nfw_M=pot.nfw_M,
+                     nfw_rs=pot.nfw_rs, mn_M=pot.mn_M, mn_a=pot.mn_a, mn_b=pot.mn_b)
+    r = orc.vjp(ph, x, v, m, dt, steps, wx, wv)
+    c = x.mean(axis=0)
+    env = {"x0bar": 0.0, "v0bar": 0.0, "mbar": 0.0}
+    for seed in (1, 2):
+        xp = c + (x - c) * (1.0 + 6e-8 * np.random.default_rng(seed).standard_normal(x.shape))
+        rp = orc.vjp(ph, xp, v, m, dt, steps, wx, wv)
+        for k in env:
+            env[k] = max(env[k], per_particle_err(rp[k], r[k]))
+    for k, got in (("x0bar", to_np(x0b)), ("v0bar", to_np(v0b)), ("mbar", to_np(mb))):
+        assert per_particle_err(got, r[k]) <= max(1e-4, 4.0 * env[k]), (k, env[k])
+        assert np.linalg.norm(got - r[k]) <= 1e-4 * np.linalg.norm(r[k]), k
+    assert tb[0] == pytest.approx(r["dt_bar"], rel=1e-4)
+    assert tb[1] == pytest.approx(np.dot(m, r["mbar"]), rel=1e-4)
+    assert tb[2] == pytest.approx(r["nfw_M_bar"], rel=1e-4)
+    assert tb[3] == pytest.approx(r["mn_M_bar"], rel=1e-4)
+    sim.close()
 
 
 # ------------------------------------------------------------ error paths --
@@ -411,7 +510,7 @@ def test_autotuned_shapes_match_oracle():
     tb = s.vjp(to_gpu(lam), None, g := torch.empty_like(xo), None)
     r = orc.vjp(orc.Physics(G=1.0, eps=0.01), x, v, m, 1e-3, 5, lam, np.zeros_like(lam),
                 want_mbar=False)
-    assert np.linalg.norm(to_np(g) - r["x0bar"]) <= 1e-4 * np.linalg.norm(r["x0bar"])
+    assert per_particle_err(to_np(g), r["x0bar"]) <= 1e-4
 
 
 def test_autograd_simulate_matches_oracle():
@@ -438,7 +537,7 @@ def test_autograd_simulate_matches_oracle():
     r = orc.vjp(ph, x, v, m, 0.5, steps, wx, wv)
     for got, ref in ((to_np(X0.grad), r["x0bar"]), (to_np(V0.grad), r["v0bar"]),
                      (to_np(M.grad), r["mbar"])):
-        assert np.linalg.norm(got - ref) <= 1e-4 * np.linalg.norm(ref)
+        assert per_particle_err(got, ref) <= 1e-4
     ref_th = [r["dt_bar"], r["nfw_M_bar"], r["nfw_rs_bar"], r["mn_M_bar"], r["mn_a_bar"],
               r["mn_b_bar"]]
     assert th.grad.tolist() == pytest.approx(ref_th, rel=1e-4)
@@ -523,7 +622,7 @@ def test_bulge_field_orbit_and_adjoint_match_oracle():
     x0b = torch.empty((3, n), dtype=torch.float64, device=DEV)
     tb = sim.vjp(to_gpu(wx), to_gpu(wv), x0b, None)
     rr = orc.vjp(ph, xc, vc, m, dt, steps, wx, wv, want_mbar=False)
-    assert np.linalg.norm(to_np(x0b) - rr["x0bar"]) <= 1e-4 * np.linalg.norm(rr["x0bar"])
+    assert per_particle_err(to_np(x0b), rr["x0bar"]) <= 1e-4
     assert tb[0] == pytest.approx(rr["dt_bar"], rel=1e-4)
     pg = sim.potential_grad()
     assert pg == pytest.approx([rr["nfw_M_bar"], rr["nfw_rs_bar"], rr["mn_M_bar"],
