@@ -504,6 +504,17 @@ NBODY_API int nbody_stream_batch_create(nbody_stream_batch **out,
 NBODY_API int nbody_stream_batch_loss_grad(nbody_stream_batch *s, const double *thetas,
                                            double *losses, double *theta_bars);
 
+/* The two parts of every gradient component of the last
+ * nbody_stream_batch_loss_grad call with gradients, parts (host or device,
+ * count x 8): parts[b][0..3] the n-body run's parts of dL/d(t_end, M_NFW,
+ * M_MN) and the velocity scaling's part of dL/dM_Plummer (in the order t_end,
+ * M_Plummer, M_NFW, M_MN), parts[b][4..7] the backward orbit's parts and the
+ * masses' part; theta_bars[b][q] = parts[b][q] + parts[b][4 + q].  The parts
+ * of t_end, M_NFW and M_MN cancel to first order (the centre of mass returns
+ * to its present-day point), so each part is the well-conditioned quantity
+ * to check.  Synchronises.  Errors: EINVAL, ESTATE (no gradient yet), ECUDA. */
+NBODY_API int nbody_stream_batch_grad_parts(nbody_stream_batch *s, double *parts);
+
 /* Release; NULL is a no-op. */
 NBODY_API void nbody_stream_batch_destroy(nbody_stream_batch *s);
 

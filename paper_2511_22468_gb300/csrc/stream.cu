@@ -436,18 +436,27 @@ __global__ void k_orbit_vjp_batch(DevParams P0, const double* __restrict__ ox,
 // dL/dtheta of every member (the arithmetic of k_theta_bar) from its n-body
 // parameter gradient tb[b][0..3] (dt, mass scale, M_NFW, M_MN), its
 // initial-state sums red[b] and its orbit part orb[b]
+// (every component is the sum of two separately computed parts, kept in
+// parts[b][0..3] and parts[b][4..7]: the n-body run's and the backward
+// orbit's for t_end, M_NFW and M_MN; the velocity scaling's and the masses'
+// for M_Plummer)
 __global__ void k_theta_bar_batch(const double* __restrict__ tb, int64_t ns, double G,
                                   double a, const double* __restrict__ theta, int64_t count,
                                   const double* __restrict__ red,
-                                  const double* __restrict__ orb, double* __restrict__ out) {
+                                  const double* __restrict__ orb, double* __restrict__ out,
+                                  double* __restrict__ parts) {
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= count) return;
   const double* t = tb + 8 * b;
   const double M = theta[4 * b + 1];
-  out[4 * b] = t[0] / (double)ns - orb[3 * b] / (double)ns;
-  out[4 * b + 1] = 0.5 * sqrt(G / (a * M)) * red[7 * b + 6] + t[1] / M;
-  out[4 * b + 2] = t[2] + orb[3 * b + 1];
-  out[4 * b + 3] = t[3] + orb[3 * b + 2];
+  const double p1[4] = {t[0] / (double)ns, 0.5 * sqrt(G / (a * M)) * red[7 * b + 6], t[2],
+                        t[3]};
+  const double p2[4] = {-orb[3 * b] / (double)ns, t[1] / M, orb[3 * b + 1], orb[3 * b + 2]};
+  for (int q = 0; q < 4; ++q) {
+    out[4 * b + q] = p1[q] + p2[q];
+    parts[8 * b + q] = p1[q];
+    parts[8 * b + 4 + q] = p2[q];
+  }
 }
 
 // members whose loss or gradient is not finite (their run left the finite
@@ -505,6 +514,8 @@ struct nbody_stream_batch {
   double *ox = nullptr, *ovh = nullptr, *g6 = nullptr;
   double *loss = nullptr, *tb = nullptr, *red = nullptr, *orb = nullptr, *out = nullptr;
   unsigned* nmark = nullptr;  // members marked failed by the last call
+  double* parts = nullptr;    // [count][8] the gradient's two parts per component
+  bool have_parts = false;
 };
 
 namespace {
@@ -552,6 +563,7 @@ void free_stream_batch(nbody_stream_batch* s) {
                      &s->loss, &s->tb, &s->red, &s->orb, &s->out})
     sfree(*p);
   sfree(s->nmark);
+  sfree(s->parts);
 }
 
 void unit3(const double* a, double* out) {
@@ -1055,6 +1067,7 @@ int nbody_stream_batch_create(nbody_stream_batch** out, const nbody_stream_cfg* 
   if (!rc) rc = salloc(&s->orb, 3 * (size_t)count);
   if (!rc) rc = salloc(&s->out, 4 * (size_t)count);
   if (!rc) rc = salloc(&s->nmark, 1);
+  if (!rc) rc = salloc(&s->parts, 8 * (size_t)count);
   if (!rc) rc = salloc(&dtx, tm3);
   if (!rc) rc = salloc(&dtv, tm3);
   if (!rc && (cudaMemcpyAsync(s->xhat, xhat, n3 * sizeof(double), cudaMemcpyDefault, s->s) ||
@@ -1165,7 +1178,8 @@ int nbody_stream_batch_loss_grad(nbody_stream_batch* s, const double* thetas, do
     SCK(cudaGetLastError());
     k_theta_bar_batch<<<blocks_for(count, 64), 64, 0, s->s>>>(s->tb, ns, c.G, c.a_prog,
                                                               s->theta, count, s->red, s->orb,
-                                                              s->out);
+                                                              s->out, s->parts);
+    s->have_parts = true;
     nb::count_launch();
     SCK(cudaGetLastError());
   }
@@ -1184,6 +1198,15 @@ int nbody_stream_batch_loss_grad(nbody_stream_batch* s, const double* thetas, do
   // the NaN flag came from a value that reached no member's loss or
   // gradient: the failure cannot be attributed, so it is reported
   if (nan_seen && marked == 0) return NBODY_ENAN;
+  return NBODY_OK;
+}
+
+int nbody_stream_batch_grad_parts(nbody_stream_batch* s, double* parts) {
+  if (!s || !parts) return NBODY_EINVAL;
+  if (!s->have_parts) return NBODY_ESTATE;
+  SCK(cudaMemcpyAsync(parts, s->parts, 8 * (size_t)s->count * sizeof(double),
+                      cudaMemcpyDefault, s->s));
+  SCK(cudaStreamSynchronize(s->s));
   return NBODY_OK;
 }
 

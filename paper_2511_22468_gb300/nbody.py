@@ -57,7 +57,8 @@ EXPORTED = ("nbody_create", "nbody_destroy", "nbody_set_params",
             "nbody_ext_accel", "nbody_stream_autotune", "nbody_stream_get_pair_shape", "nbody_orbitfit_create", "nbody_orbitfit_eval",
             "nbody_orbitfit_lm", "nbody_orbitfit_fisher", "nbody_orbitfit_arc",
             "nbody_orbitfit_destroy", "nbody_stream_batch_create",
-            "nbody_stream_batch_loss_grad", "nbody_stream_batch_destroy")
+            "nbody_stream_batch_loss_grad", "nbody_stream_batch_grad_parts",
+            "nbody_stream_batch_destroy")
 
 NBODY_NTUNE = 8
 
@@ -167,6 +168,7 @@ def lib():
         L.nbody_stream_batch_create.argtypes = [C.POINTER(vp), SC, i64, vp, vp, i64, vp, vp,
                                                 dp, C.c_int, dp, vp]
         L.nbody_stream_batch_loss_grad.argtypes = [vp, vp, vp, vp]
+        L.nbody_stream_batch_grad_parts.argtypes = [vp, vp]
         L.nbody_stream_batch_destroy.argtypes = [vp]
         L.nbody_stream_batch_destroy.restype = None
         L.nbody_autotune.argtypes = [vp, i64, C.POINTER(C.c_int), dp]
@@ -497,6 +499,15 @@ def nbody_stream_batch_create(cfg, count, xhat, vhat, m, tx, tv, scale, sigmas, 
                                            _ptr(tv, (3, count * m)), sc, len(sigmas), sg,
                                            _stream(stream)), "nbody_stream_batch_create")
     return h
+
+
+def nbody_stream_batch_grad_parts(h, count):
+    """(count, 2, 4): the two parts of every component of the last gradient
+    (n-body run / velocity scaling, then orbit / masses)."""
+    import numpy as np
+    out = np.zeros((count, 8))
+    _check(lib().nbody_stream_batch_grad_parts(h, _ptr(out)), "nbody_stream_batch_grad_parts")
+    return out.reshape(count, 2, 4)
 
 
 def nbody_stream_batch_loss_grad(h, thetas, want_grad=True):

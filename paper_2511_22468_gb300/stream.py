@@ -146,6 +146,11 @@ class StreamBatch:
     def loss(self, thetas):
         return nb.nbody_stream_batch_loss_grad(self.h, thetas, want_grad=False)[0]
 
+    def grad_parts(self):
+        """(count, 2, 4): the two parts of every gradient component of the
+        last loss_and_grad (n-body run / velocity scaling, orbit / masses)."""
+        return nb.nbody_stream_batch_grad_parts(self.h, self.count)
+
     def close(self):
         if self.h is not None and self.h.value:
             nb.nbody_stream_batch_destroy(self.h)

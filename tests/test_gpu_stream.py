@@ -10,12 +10,9 @@ backward orbit's -dt, which cancel to first order (the centre of mass comes
 back to X0); its error is bounded by 1e-4 of the sum of the parts' sizes.
 """
 
-
-def assert_grad_close(g, g_ref, parts):
-    scale = np.abs(np.asarray(g_ref, float))
-    scale[0] = abs(parts[0]) + abs(parts[1])
-    assert np.all(np.abs(np.asarray(g) - g_ref) <= 1e-4 * scale), (g, g_ref, parts)
 import dataclasses
+import json
+import os
 
 import numpy as np
 import pytest
@@ -27,6 +24,15 @@ from paper_2511_22468_gb300.configs import C1  # noqa: E402
 from paper_2511_22468_gb300.inputs import plummer_unit  # noqa: E402
 
 pytestmark = pytest.mark.gpu
+
+
+def assert_grad_close(g, g_ref, parts):
+    """1e-4 relative per component; dL/dt_end (the difference of the forward
+    run's and the backward orbit's parts) to 1e-4 of the parts' sizes."""
+    scale = np.abs(np.asarray(g_ref, float))
+    scale[0] = abs(parts[0]) + abs(parts[1])
+    err = np.abs(np.asarray(g) - g_ref) / scale
+    assert np.all(err <= 1e-4), (g, g_ref, parts, err)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -176,15 +182,27 @@ def test_stream_batch_losses_and_gradients_match_oracle():
     thetas = truth[None, :] * f_theta
     gpu = StreamBatch(cfg, xh, vh, tx, tv, sig, scale=sc)
     L, g = gpu.loss_and_grad(thetas)
+    parts = gpu.grad_parts()
     for b in range(3):
         Yb = mmd.cloud(tx[b], tv[b])
         L_ref, g_ref = orc.mmd_loss_and_grad(thetas[b], Yb, sig, mu, sc)
         assert abs(L[b] - L_ref) <= 1e-5 * len(sig) and L[b] == pytest.approx(L_ref, rel=1e-3)
-        # each component is the sum of two separately rounded parts (n-body
-        # run and orbit): 1e-4 of the parts' magnitudes bounds its error
+        # each component is the sum of two parts (n-body run and backward
+        # orbit; velocity scaling and masses); dL/dt_end is held to 1e-4 of
+        # its parts (reading of the t_end bound), dL/dM_Plummer to 1e-4.
+        # dL/dM_NFW and dL/dM_MN: their parts cancel 50-540x here and both
+        # depend on the common mode of the FP32 point-cloud cotangent (a sum
+        # over the cloud that cancels to a few per cent), which shifts the
+        # two parts in opposite directions; the bound adds 2e-5 of the
+        # parts' sizes to 1e-4 of the component.  The component is the sum
+        # of the reported parts, bit for bit.
         p1, p2 = orc.grad_parts
-        assert np.all(np.abs(g[b] - g_ref) <= 1e-4 * (np.abs(p1) + np.abs(p2))), (b, g[b], g_ref,
-                                                                                p1, p2)
+        gp = parts[b]
+        np.testing.assert_array_equal(gp[0] + gp[1], g[b])
+        scale = 1e-4 * np.abs(g_ref)
+        scale[0] = 1e-4 * (abs(p1[0]) + abs(p2[0]))
+        scale[2:] += 2e-5 * (np.abs(p1[2:]) + np.abs(p2[2:]))
+        assert np.all(np.abs(g[b] - g_ref) <= scale), (b, g[b], g_ref, p1, p2)
     # the same call again gives the same bits; the loss alone agrees
     L2, g2 = gpu.loss_and_grad(thetas)
     assert np.array_equal(L, L2) and np.array_equal(g, g2)
@@ -223,4 +241,44 @@ def test_stream_batch_isolates_a_failing_member():
     assert np.array_equal(gb[[0, 2]], g[[0, 2]])
     L2, g2 = gpu.loss_and_grad(thetas)
     assert np.array_equal(L2, L) and np.array_equal(g2, g)
+    gpu.close()
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.mark.parametrize("steps", [200])
+def test_stream_pipeline_at_workload_size(steps):
+    """The GD-1-like stream workload at its own size, N = 10^4, over `steps`
+    steps of 0.5 Myr, in the launch shapes the pipeline's autotuner picks at
+    that size, against the oracle's values stored by
+    tests/golden/make_stream_n1e4.py (the oracle alone computes them):
+    density per bin 1e-8 absolute, loss 1e-4 relative, dL/dTheta per
+    component 1e-4 relative of the oracle adjoint (dL/dt_end: of its parts)
+    and of the oracle's Richardson central differences."""
+    from paper_2511_22468_gb300 import nbody as nb
+    from paper_2511_22468_gb300.stream import StreamModel
+    g = json.load(open(os.path.join(GOLDEN, "stream_n1e4_s%d.json" % steps)))
+    cfg = dataclasses.replace(C1, t_acc=g["t_end_true"], n_steps=g["n_steps"])
+    assert cfg.n == g["n"] and cfg.seed == g["seed"]
+    xh, vh = plummer_unit(cfg.n, cfg.seed)
+    fp = g["inputs"]
+    np.testing.assert_allclose([np.abs(xh).sum(), np.abs(vh).sum()],
+                               [fp["sum_abs_x"], fp["sum_abs_v"]], rtol=1e-12)
+    np.testing.assert_allclose(xh[fp["rows"]], fp["x_rows"], rtol=1e-12)
+    np.testing.assert_allclose(vh[fp["rows"]], fp["v_rows"], rtol=1e-12)
+    th = np.array(g["theta"])
+    gpu = StreamModel(cfg, xh, vh)
+    gpu.set_target(np.array(g["target_density"]).reshape(cfg.nb1, cfg.nb2))
+    gpu.autotune(list(th))
+    shapes = [nb.nbody_stream_get_pair_shape(gpu.h, k) for k in (0, 1)]
+    rho = gpu.density(th).cpu().numpy().ravel()
+    np.testing.assert_allclose(rho, g["density"], rtol=0, atol=1e-8, err_msg=str(shapes))
+    L, grad = gpu.loss_and_grad(th)
+    assert L == pytest.approx(g["loss"], rel=1e-4), shapes
+    assert_grad_close(grad, np.array(g["grad"]), g["t_end_parts"])
+    fd = np.array(g["grad_fd_richardson"])
+    scale = np.abs(fd)
+    scale[0] = sum(abs(p) for p in g["t_end_parts"])
+    assert np.all(np.abs(grad - fd) <= 1e-4 * scale), (grad, fd, shapes)
     gpu.close()

@@ -211,3 +211,31 @@ def test_plummer_sampler_seeded():
     b = plummer_unit(100, 7)
     c = plummer_unit(100, 8)
     assert np.array_equal(a[0], b[0]) and not np.array_equal(a[0], c[0])
+
+
+def test_golden_stream_n1e4_adjoint_matches_differences():
+    """The stored oracle values of the stream pipeline at N = 10^4
+    (tests/golden/stream_n1e4_s*.json, written by make_stream_n1e4.py): the
+    oracle's adjoint agrees with its own Richardson central differences
+    (1e-4 relative per component; dL/dt_end to 1e-4 of its two parts), the
+    parts add up to the gradient, the loss is the mean squared difference of
+    the stored densities, and the density is normalised (mass fraction of
+    the particles inside the window)."""
+    import glob
+    import json
+    import os
+    files = sorted(glob.glob(os.path.join(os.path.dirname(__file__), "golden",
+                                          "stream_n1e4_s*.json")))
+    assert files
+    for f in files:
+        g = json.load(open(f))
+        grad = np.array(g["grad"])
+        fd = np.array(g["grad_fd_richardson"])
+        p1, p2 = (np.array(p) for p in g["grad_parts"])
+        np.testing.assert_allclose(p1 + p2, grad, rtol=1e-12, atol=0)
+        scale = np.abs(fd)
+        scale[0] = sum(abs(p) for p in g["t_end_parts"])
+        assert np.all(np.abs(grad - fd) <= 1e-4 * scale), f
+        rho, tgt = np.array(g["density"]), np.array(g["target_density"])
+        assert g["loss"] == pytest.approx(np.mean((rho - tgt) ** 2), rel=1e-12)
+        assert 0.0 < rho.sum() <= 1.0 and 0.0 < tgt.sum() <= 1.0
