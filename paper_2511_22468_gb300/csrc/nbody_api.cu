@@ -320,7 +320,8 @@ uint64_t bits(double v) {
 
 uint64_t cfg_word(const nb::PairCfg& f) {
   return (uint64_t)f.variant | ((uint64_t)f.nt << 4) | ((uint64_t)f.r << 16) |
-         ((uint64_t)f.S << 24) | ((uint64_t)f.eqm << 40);
+         ((uint64_t)f.S << 24) | ((uint64_t)f.eqm << 40) |
+         ((uint64_t)(f.vjp_tile_pairs >> 7) << 41);
 }
 
 // centre of point k of the current call

@@ -18,6 +18,7 @@
 //
 // Warp variant (small N): a warp owns R i-particles and its 32 lanes split
 // the j-range; lane sums are combined by a fixed xor-shuffle butterfly.
+#include "async_copy.cuh"
 #include "block_reduce.cuh"
 #include "nbody_internal.cuh"
 #include "pair_body.cuh"
@@ -38,6 +39,12 @@ namespace {
 #ifndef NB_PAIR_MINB
 #define NB_PAIR_MINB 1
 #endif
+// 1: j-tiles staged with cp.async into two shared-memory buffers (the copy
+// of the next tile overlaps the current one, one barrier per tile);
+// 0: loaded through registers into one buffer, two barriers per tile
+#ifndef NB_TILE_ASYNC
+#define NB_TILE_ASYNC 0
+#endif
 constexpr int kTJ = NB_PAIR_TJ;  // j-pairs per shared-memory tile
 constexpr int kTJSmall = 128;    // small tiles: more j-chunks for small N
 constexpr int kUnrollJ = NB_PAIR_UNROLL;
@@ -48,7 +55,8 @@ __global__ void __launch_bounds__(NT, NB_PAIR_MINB)
                 int64_t npad, double* __restrict__ part,
                 double* __restrict__ pot, double* __restrict__ fin,
                 unsigned* __restrict__ ctr) {
-  __shared__ float4 sj[2 * TJ];
+  constexpr bool kAsync = NB_TILE_ASYNC != 0;
+  __shared__ __align__(16) float4 sbuf[kAsync ? 2 : 1][2 * TJ];
   const int t = threadIdx.x;
   const int64_t i0 = (int64_t)blockIdx.x * (NT * R) + t;
   const int S = gridDim.y;
@@ -68,12 +76,31 @@ __global__ void __launch_bounds__(NT, NB_PAIR_MINB)
   }
   const float2 e2 = make_float2(eps2, eps2);
 
+  if (kAsync && tile_b < tile_e) {
+    const float4* src = st + (int64_t)tile_b * (2 * TJ);
+    for (int q = t; q < 2 * TJ; q += NT) cp_async16(&sbuf[0][q], src + q);
+    cp_async_commit();
+  }
   for (int tile = tile_b; tile < tile_e; ++tile) {
-    __syncthreads();
-    const float4* src = st + (int64_t)tile * (2 * TJ);
+    const float4* sj;
+    if (kAsync) {
+      cp_async_wait_all();
+      __syncthreads();  // this tile visible; the previous one no longer read
+      if (tile + 1 < tile_e) {
+        const float4* src = st + (int64_t)(tile + 1) * (2 * TJ);
+        float4* dst = sbuf[(tile + 1 - tile_b) & 1];
+        for (int q = t; q < 2 * TJ; q += NT) cp_async16(dst + q, src + q);
+        cp_async_commit();
+      }
+      sj = sbuf[(tile - tile_b) & 1];
+    } else {
+      __syncthreads();
+      const float4* src = st + (int64_t)tile * (2 * TJ);
 #pragma unroll
-    for (int q = t; q < 2 * TJ; q += NT) sj[q] = src[q];
-    __syncthreads();
+      for (int q = t; q < 2 * TJ; q += NT) sbuf[0][q] = src[q];
+      __syncthreads();
+      sj = sbuf[0];
+    }
 
     float2 ax[R], ay[R], az[R], ph[R];
 #pragma unroll

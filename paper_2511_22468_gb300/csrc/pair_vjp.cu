@@ -14,6 +14,7 @@
 // rsqrt per interaction.  With equal masses u = m (l_k - l_j), the mass is
 // applied by the consumer, and the s^-3 and s^-5 sums are kept apart
 // (Q = A - 3 B): 22 FP32 operations per interaction.
+#include "async_copy.cuh"
 #include "block_reduce.cuh"
 #include "nbody_internal.cuh"
 #include "vjp_body.cuh"
@@ -32,6 +33,12 @@ namespace {
 #ifndef NB_VJP_MINB
 #define NB_VJP_MINB 1
 #endif
+// 1: j-tiles staged with cp.async into two shared-memory buffers (the copy
+// of the next tile overlaps the current one, one barrier per tile);
+// 0: loaded through registers into one buffer, two barriers per tile
+#ifndef NB_TILE_ASYNC
+#define NB_TILE_ASYNC 0
+#endif
 constexpr int kTJ = NB_VJP_TJ;  // j-pairs per shared-memory tile (4 float4 each)
 constexpr int kUnrollJ = NB_VJP_UNROLL;
 
@@ -40,7 +47,8 @@ __global__ void __launch_bounds__(NT, NB_VJP_MINB)
     k_vjp_tile(const float4* __restrict__ vst, int ntiles, float eps2,
                int64_t npad, double* __restrict__ part, double* __restrict__ mpart,
                double* __restrict__ fin, unsigned* __restrict__ ctr) {
-  __shared__ float4 sj[4 * kTJ];
+  constexpr bool kAsync = NB_TILE_ASYNC != 0;
+  __shared__ __align__(16) float4 sbuf[kAsync ? 2 : 1][4 * kTJ];
   const int t = threadIdx.x;
   const int64_t k0 = (int64_t)blockIdx.x * (NT * R) + t;
   const int S = gridDim.y;
@@ -55,12 +63,31 @@ __global__ void __launch_bounds__(NT, NB_VJP_MINB)
     gx[r] = gy[r] = gz[r] = gm[r] = 0.0;
   }
   const float2 e2 = make_float2(eps2, eps2);
+  if (kAsync && tile_b < tile_e) {
+    const float4* src = vst + (int64_t)tile_b * (4 * kTJ);
+    for (int q = t; q < 4 * kTJ; q += NT) cp_async16(&sbuf[0][q], src + q);
+    cp_async_commit();
+  }
   for (int tile = tile_b; tile < tile_e; ++tile) {
-    __syncthreads();
-    const float4* src = vst + (int64_t)tile * (4 * kTJ);
+    const float4* sj;
+    if (kAsync) {
+      cp_async_wait_all();
+      __syncthreads();  // this tile visible; the previous one no longer read
+      if (tile + 1 < tile_e) {
+        const float4* src = vst + (int64_t)(tile + 1) * (4 * kTJ);
+        float4* dst = sbuf[(tile + 1 - tile_b) & 1];
+        for (int q = t; q < 4 * kTJ; q += NT) cp_async16(dst + q, src + q);
+        cp_async_commit();
+      }
+      sj = sbuf[(tile - tile_b) & 1];
+    } else {
+      __syncthreads();
+      const float4* src = vst + (int64_t)tile * (4 * kTJ);
 #pragma unroll
-    for (int q = t; q < 4 * kTJ; q += NT) sj[q] = src[q];
-    __syncthreads();
+      for (int q = t; q < 4 * kTJ; q += NT) sbuf[0][q] = src[q];
+      __syncthreads();
+      sj = sbuf[0];
+    }
     float2 qa[R][3], qb[R][3], qm[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
