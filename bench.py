@@ -40,6 +40,11 @@ UNIT = "interactions/s"
 SEG = 10                  # KDK steps per benchmark step (= checkpoint spacing)
 FLOPS_PAIR = 20           # flops per interaction, forward convention
 FLOPS_VJP = 41            # flops per interaction of the pair VJP kernel
+# flops the kernels execute per interaction (FADD = FMUL = rsqrt = 1,
+# FFMA = 2).  Equal masses: force 3 FADD + 6 FFMA + 2 FMUL + rsqrt = 18,
+# VJP 6 FADD + 11 FFMA + 5 FMUL + rsqrt = 34; general masses: force 19,
+# VJP 41 (the convention's count is the general VJP's).
+EXEC_FLOPS = {("pair", True): 18, ("pair", False): 19, ("vjp", True): 34, ("vjp", False): 41}
 FP32_LANES = 128          # FP32 FMA lanes per SM
 L2_BYTES = 129 * 2 ** 20
 
@@ -50,10 +55,18 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    # end-to-end steps: by default as many as the timed device steps
+    ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-grid", action="store_true")
+    ap.add_argument("--no-stream", action="store_true")
+    # the grid search's bootstrap (1000 resampled observations) is opt-in
+    ap.add_argument("--bootstrap", action="store_true")
+    # particle number of the throughput workload; other values than the
+    # default serve profiling captures of a smaller case and name their size
+    # in config.workload
+    ap.add_argument("--n", type=int, default=None)
     return ap.parse_args()
 
 
@@ -83,9 +96,13 @@ def dist_env():
     return rank, world, local
 
 
-def workload_arrays():
+def workload_arrays(n=None):
+    import dataclasses
+
     from paper_2511_22468_gb300.configs import C3
     from paper_2511_22468_gb300.inputs import plummer_sphere
+    if n is not None and n != C3.n:
+        C3 = dataclasses.replace(C3, n=int(n), name="plummer_n%d_nfw_mn" % int(n))
     x, v, m = plummer_sphere(C3.n, C3.seed, C3.G, C3.M, C3.a, center=C3.X0,
                              velocity=C3.V0)
     rng = np.random.default_rng(C3.seed + 1)
@@ -187,7 +204,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    C3, x, v, m, _ = workload_arrays()
+    C3, x, v, m, _ = workload_arrays(args.n)
     from oracle.build import build_oracle
     build_oracle()
     ra, rv = 1024, 128
@@ -318,6 +335,54 @@ def measure_ensemble(dev, gpu_name, plain_subset=8, plain_steps=200):
                 "speedup": t_plain / t_batch_sub}}
 
 
+# ------------------------------------------------------- stream workload --
+def measure_stream_c1(dev, peak_max):
+    """The GD-1-like stream workload at its own size (N = 10^4, 6000 steps
+    of 0.5 Myr): seconds per loss and per gradient of the whole pipeline
+    (launch shapes autotuned), as microseconds per step, and the pair
+    kernels alone on the progenitor at N = 10^4 (tuned shape, CUDA-event
+    timing of each launch)."""
+    import torch
+    from paper_2511_22468_gb300 import nbody as nb
+    from paper_2511_22468_gb300.configs import C1
+    from paper_2511_22468_gb300.inputs import plummer_sphere
+    from paper_2511_22468_gb300.stream import time_pipeline
+    t = time_pipeline(reps=2, autotune=True)
+    out = {"workload": "gd1_stream_n10k_6000_steps", "forward_s": t["forward_s"],
+           "gradient_s": t["gradient_s"], "forward_us_per_step": t["forward_us_per_step"],
+           "fwd_adjoint_us_per_step": t["forward_us_per_step"] + t["gradient_us_per_step"]}
+    n, steps = C1.n, 200
+    x, v, m = plummer_sphere(n, C1.seed, C1.G, C1.M_prog, C1.a_prog, center=C1.X0,
+                             velocity=C1.V0)
+    pot = C1.pot
+    prm = nb.make_params(C1.G, C1.eps, 0.5, checkpoint_every=10, ext_flags=3,
+                         nfw_M=pot.nfw_M, nfw_rs=pot.nfw_rs, mn_M=pot.mn_M, mn_a=pot.mn_a,
+                         mn_b=pot.mn_b, center=C1.X0, center_vel=C1.V0,
+                         center_mode=nb.NBODY_CENTER_GUIDE, tape_mode=nb.NBODY_TAPE_LEAN)
+    sim = nb.Simulation(n, prm)
+    X = torch.tensor(x.T.copy(), device=dev)
+    sim.set_state(X, torch.tensor(v.T.copy(), device=dev), torch.tensor(m, device=dev))
+    fwd_shape, vjp_shape = nb.nbody_autotune_pair(sim.h)
+    nb.nbody_set_timing(sim.h, True)
+    sim.integrate(steps)
+    sim.vjp(X, None)
+    kt = nb.nbody_kernel_times(sim.h)
+    for name, flops, shape in (("pair", FLOPS_PAIR, fwd_shape), ("vjp", FLOPS_VJP, vjp_shape)):
+        ms, cnt = kt[name]
+        avg = ms / cnt / 1e3
+        ach = flops * n * n / avg / 1e12
+        out[name + "_kernel"] = {"avg_us": avg * 1e6, "launches": cnt,
+                                 "interactions_per_s": n * n / avg,
+                                 "flops_per_interaction": flops,
+                                 "frac_of_peak_at_2070MHz": ach / peak_max,
+                                 "executed_flops_per_interaction": EXEC_FLOPS[(name, True)],
+                                 "frac_executed_of_peak_at_2070MHz":
+                                     ach * EXEC_FLOPS[(name, True)] / flops / peak_max,
+                                 "shape": list(shape)}
+    sim.close()
+    return out
+
+
 # ------------------------------------------------------------------- ours --
 def hbm_peak():
     """Measured copy bandwidth of the GB300s (GB/s), else the
@@ -372,7 +437,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     from paper_2511_22468_gb300 import build, nbody as nb
     build.build()
-    C3, x, v, m, xbar = workload_arrays()
+    C3, x, v, m, xbar = workload_arrays(args.n)
     n = C3.n
     p = C3.pot
     prm = nb.make_params(C3.G, C3.eps, C3.dt, checkpoint_every=SEG, ext_flags=3,
@@ -435,15 +500,24 @@ def run_ours(args):
     sms = props.multi_processor_count
     peak_max = sms * FP32_LANES * 2 * 2070e6 / 1e12
     kernels = {}
+    eqm = bool(np.all(m == m[0]))
+    ffma_meas = peaks.get("fp32x2_fma_tflops") or None
     for name, flops in (("pair", FLOPS_PAIR), ("vjp", FLOPS_VJP)):
         ms, cnt = kt[name]
         if cnt:
             avg_s = ms / cnt / 1e3
             ach = flops * n * n / avg_s / 1e12
+            ex = EXEC_FLOPS[(name, eqm)]
+            ach_ex = ex * n * n / avg_s / 1e12
             kernels[name] = {"launches": cnt, "total_ms": ms, "avg_ms": avg_s * 1e3,
                              "flops_per_interaction": flops,
                              "interactions_per_s": n * n / avg_s,
-                             "achieved_tflops": ach, "frac_of_peak_at_2070MHz": ach / peak_max}
+                             "achieved_tflops": ach, "frac_of_peak_at_2070MHz": ach / peak_max,
+                             "executed_flops_per_interaction": ex,
+                             "executed_tflops": ach_ex,
+                             "frac_executed_of_peak_at_2070MHz": ach_ex / peak_max,
+                             "frac_executed_of_measured_ffma":
+                                 ach_ex / ffma_meas if ffma_meas else None}
     # O(N) FP64 kernels: algorithmic bytes per particle of an interior launch
     # (update: x, v read and written, S partial slices read, FP32 restage;
     # adjoint: cotangents, tape x, a_pair, v_half, x_prev, m read, cotangents
@@ -466,6 +540,11 @@ def run_ours(args):
     roofline = {"bound": "alu", "kernel": dom, "achieved": d["achieved_tflops"],
                 "peak": peak_max, "unit": "TFLOP/s",
                 "frac": d["achieved_tflops"] / peak_max,
+                "flops_per_interaction": d["flops_per_interaction"],
+                "executed_flops_per_interaction": d["executed_flops_per_interaction"],
+                "frac_executed": d["frac_executed_of_peak_at_2070MHz"],
+                "peak_measured_ffma": ffma_meas,
+                "frac_executed_of_measured_ffma": d["frac_executed_of_measured_ffma"],
                 "traffic": traffic_record(dom),
                 "peak_basis": "%d SMs x %d FP32 lanes x 2 flop x 2070 MHz (max SM clock)"
                               % (sms, FP32_LANES),
@@ -480,7 +559,7 @@ def run_ours(args):
     xbh = torch.tensor(xbar.T.copy()).pin_memory()
     x0h = torch.empty((3, n), dtype=torch.float64).pin_memory()
     v0h = torch.empty((3, n), dtype=torch.float64).pin_memory()
-    e2e_steps = max(1, args.e2e_steps)
+    e2e_steps = max(1, args.steps if args.e2e_steps is None else args.e2e_steps)
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
@@ -510,26 +589,32 @@ def run_ours(args):
 
     def grid_and_bootstrap():
         # the point-cloud grid search at the paper's stage-1 size: 10^4
-        # simulations of 1000 particles, 1000 steps, ranked by batched MMD
-        # and its bootstrap: 1000 realisations of the observation scored
+        # simulations of 1000 particles, 1000 steps, ranked by batched MMD;
+        # with --bootstrap also 1000 realisations of the observation scored
         # against every kept grid cloud, then all 1000 refined by 10 batched
         # gradient steps
         from paper_2511_22468_gb300 import gridsearch
-        g = gridsearch.run(refine_iters=10, device=str(dev), bootstrap=1000,
-                           bootstrap_refine=1000, refine_batch=500)
+        nb_boot = 1000 if args.bootstrap else 0
+        g = gridsearch.run(refine_iters=10, device=str(dev), bootstrap=nb_boot,
+                           bootstrap_refine=nb_boot, refine_batch=500)
         out = {"workload": "grid_1e4_n1000_steps1000", **g["grid"],
                "grid_points": g["workload"]["grid_points"]}
-        b = g["bootstrap"]
-        out["bootstrap"] = {"realisations": b["realisations"], "cross_mmd_s": b["time_s"],
-                            "cross_kernel_pairs_per_s": b["kernel_pairs_per_s"],
-                            "refine_s": b["refine"]["time_s"],
-                            "refine_iters": b["refine"]["iters"],
-                            "refine_batch": b["refine"]["batch"]}
+        b = g.get("bootstrap")
+        if b:
+            out["bootstrap"] = {"realisations": b["realisations"], "cross_mmd_s": b["time_s"],
+                                "cross_kernel_pairs_per_s": b["kernel_pairs_per_s"],
+                                "refine_s": b["refine"]["time_s"],
+                                "refine_iters": b["refine"]["iters"],
+                                "refine_batch": b["refine"]["batch"]}
         return out
 
     grid = None
     if not args.no_grid:
         grid = secondary(grid_and_bootstrap)
+
+    stream_c1 = None
+    if not args.no_stream:
+        stream_c1 = secondary(lambda: measure_stream_c1(dev, peak_max))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -557,6 +642,7 @@ def run_ours(args):
                 else None,
                 "ensemble": ens,
                 "grid_search": grid,
+                "stream_c1": stream_c1,
                 "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu,
                 "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
                 "parallelism": "replicas" if world > 1 else "single"}
