@@ -22,11 +22,12 @@ struct ExtUnit {
   double b[3];
 };
 
-// Incomplete gamma functions by the series and the continued fraction of
-// Numerical Recipes (Press et al., Sec. 6.2; the fraction evaluated with
-// the modified Lentz method), each with a bounded number of terms:
-//   gamma(s, u) = e^-u u^s sum_{n>=0} u^n / (s (s+1) ... (s+n))   (u < s+1),
-//   Gamma(s, u) = e^-u u^s / (u + 1 - s - 1 (1-s) / (u + 3 - s - 2 (2-s) / ...)).
+// Incomplete gamma functions, each with a bounded number of terms:
+//   gamma(s, u) = e^-u u^s sum_{n>=0} u^n / (s (s+1) ... (s+n))   (u < s+1;
+//                 the power series, Abramowitz & Stegun 6.5.29),
+//   Gamma(s, u) = e^-u u^s / K,  K = b_0 + a_1 / (b_1 + a_2 / (b_2 + ...)),
+//                 b_k = u + 2k + 1 - s, a_k = -k (k - s)   (u >= s+1; the
+//                 Legendre continued fraction, A&S 6.5.31, in its even form).
 // lnpre = s ln u - u.
 static __device__ __forceinline__ double igamma_lower_series(double s, double u,
                                                              double lnpre) {
@@ -40,22 +41,28 @@ static __device__ __forceinline__ double igamma_lower_series(double s, double u,
   return sum * exp(lnpre);
 }
 
+// K by its convergents K_k = P_k / Q_k and the three-term recurrences
+// P_k = b_k P_{k-1} + a_k P_{k-2}, Q_k = b_k Q_{k-1} + a_k Q_{k-2}
+// (P_{-1} = 1, Q_{-1} = 0, P_0 = b_0, Q_0 = 1), both pairs divided by Q_k
+// after every step so that Q_k = 1 and K_k = P_k stay in range; stops when
+// two convergents agree to 1e-16.
 static __device__ __forceinline__ double igamma_upper_cf(double s, double u, double lnpre) {
-  const double tiny = 1e-300;
-  double b = u + 1.0 - s, c = 1.0 / tiny, d = 1.0 / b, h = d;
-  for (int i = 1; i < 400; ++i) {
-    const double an = -i * (i - s);
-    b += 2.0;
-    d = an * d + b;
-    if (fabs(d) < tiny) d = tiny;
-    c = b + an / c;
-    if (fabs(c) < tiny) c = tiny;
-    d = 1.0 / d;
-    const double del = d * c;
-    h *= del;
-    if (fabs(del - 1.0) < 1e-16) break;
+  double p_prev = 1.0, q_prev = 0.0;  // P_{k-1}, Q_{k-1} (scaled)
+  double p = u + 1.0 - s, q = 1.0;    // P_k, Q_k
+  for (int k = 1; k < 400; ++k) {
+    const double a = -(double)k * ((double)k - s);
+    const double b = u + (double)(2 * k + 1) - s;
+    const double p_new = b * p + a * p_prev;
+    const double q_new = b * q + a * q_prev;
+    const double inv = 1.0 / q_new;
+    p_prev = p * inv;
+    q_prev = q * inv;
+    const double k_old = p / q;
+    p = p_new * inv;
+    q = 1.0;
+    if (fabs(p - k_old) <= 1e-16 * fabs(p)) break;
   }
-  return exp(lnpre) * h;
+  return exp(lnpre) / p;
 }
 
 // regularised lower incomplete gamma P(s, u); 1 beyond u = 60, where
