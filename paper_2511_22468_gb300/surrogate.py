@@ -216,15 +216,19 @@ def descend_batch(model, thetas0, centre, width, lr=0.05, iters=10):
 
 
 def descend(model: StreamModel, theta0, centre, width, lr=0.05, max_iters=50,
-            loss_target=None, theta_true=None, err_target=None, clock=None):
+            loss_target=None, theta_true=None, err_target=None, clock=None, grow=1.0,
+            lr_max=None):
     """Gradient descent on the simulator's loss in normalised parameters u,
     with the discrete-adjoint gradient dL/du = dL/dtheta * theta_c * width.
     Adam steps from the current point; the estimate is the minimum-loss
     iterate (as in the paper's Fig. 2, step 5); a step that raises the loss
     above the best is undone, the moments reset and the rate halved.
+    A step that lowers the loss multiplies the rate by `grow` (up to
+    lr_max), so that a rate halved by a noisy step recovers.
     Stops at loss_target, at parameter error err_target
     (max_k |theta_k / theta_true_k - 1|) or after max_iters simulator
     gradients; each trajectory row holds the best iterate so far."""
+    lr_max = lr if lr_max is None else lr_max
     clock = clock or time.perf_counter
     t0 = clock()
     u = to_u(theta0, centre, width)
@@ -238,6 +242,8 @@ def descend(model: StreamModel, theta0, centre, width, lr=0.05, max_iters=50,
         L, g = model.loss_and_grad(th)
         gu = np.asarray(g) * np.asarray(centre) * width
         if best is None or L <= best[0]:
+            if best is not None:
+                lr = min(lr * grow, lr_max)
             best = (L, u.copy(), gu)
         else:
             lr *= 0.5
