@@ -1133,9 +1133,10 @@ int nbody_autotune_pair(nbody_ctx* c, int probe_launches, int fwd_best[4],
   };
   const Shape fwd[] = {{0, 128, 4, 0},   {0, 128, 8, 0},   {0, 256, 4, 0}, {0, 256, 2, 0},
                        {0, 128, 2, 0},   {0, 128, 1, 0},   {1, 256, 4, 0}, {1, 256, 8, 0},
-                       {0, 128, 4, 128}, {0, 128, 2, 128}, {0, 128, 1, 128}};
+                       {0, 128, 4, 128}, {0, 128, 2, 128}, {0, 128, 1, 128},
+                       {0, 64, 2, 128},  {0, 64, 4, 128},  {0, 64, 2, 0}};
   const Shape vjp[] = {{0, 256, 2, 0}, {0, 128, 4, 0}, {0, 128, 2, 0}, {0, 128, 1, 0},
-                       {1, 256, 4, 0}, {1, 256, 2, 0}};
+                       {1, 256, 4, 0}, {1, 256, 2, 0}, {0, 64, 2, 0}};
   int rc = NBODY_OK;
   int best_fin[2] = {0, 0};
   for (int which = 0; which < 2 && rc == NBODY_OK; ++which) {

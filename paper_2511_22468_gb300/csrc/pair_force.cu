@@ -216,6 +216,10 @@ cudaError_t launch_impl(const PairCfg& c, const float4* st, int64_t npad,
       k_pair_tile<128, 2, POT, EQM, kTJSmall><<<grid, 128, 0, s>>>(st, ntiles, eps2, npad, part, pot, fin, ctr);
     else if (c.nt == 128 && c.r == 1)
       k_pair_tile<128, 1, POT, EQM, kTJSmall><<<grid, 128, 0, s>>>(st, ntiles, eps2, npad, part, pot, fin, ctr);
+    else if (c.nt == 64 && c.r == 2)
+      k_pair_tile<64, 2, POT, EQM, kTJSmall><<<grid, 64, 0, s>>>(st, ntiles, eps2, npad, part, pot, fin, ctr);
+    else if (c.nt == 64 && c.r == 4)
+      k_pair_tile<64, 4, POT, EQM, kTJSmall><<<grid, 64, 0, s>>>(st, ntiles, eps2, npad, part, pot, fin, ctr);
     else
       return cudaErrorInvalidValue;
   } else if (c.variant == kTile) {
@@ -235,6 +239,10 @@ cudaError_t launch_impl(const PairCfg& c, const float4* st, int64_t npad,
       k_pair_tile<128, 2, POT, EQM><<<grid, 128, 0, s>>>(st, ntiles, eps2, npad, part, pot, fin, ctr);
     else if (c.nt == 128 && c.r == 1)
       k_pair_tile<128, 1, POT, EQM><<<grid, 128, 0, s>>>(st, ntiles, eps2, npad, part, pot, fin, ctr);
+    else if (c.nt == 64 && c.r == 2)
+      k_pair_tile<64, 2, POT, EQM><<<grid, 64, 0, s>>>(st, ntiles, eps2, npad, part, pot, fin, ctr);
+    else if (c.nt == 64 && c.r == 4)
+      k_pair_tile<64, 4, POT, EQM><<<grid, 64, 0, s>>>(st, ntiles, eps2, npad, part, pot, fin, ctr);
     else
       return cudaErrorInvalidValue;
   } else {
@@ -286,9 +294,10 @@ int pair_blocks_per_sm(const PairCfg& c) {
               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(                      \
                     &occ, k_pair_tile<NT, R, false, false, kTJSmall>, NT, 0);
   if (c.variant == kTile && c.vjp_tile_pairs == kTJSmall) {
-    NB_OCC_S(128, 4) NB_OCC_S(128, 2) NB_OCC_S(128, 1)
+    NB_OCC_S(128, 4) NB_OCC_S(128, 2) NB_OCC_S(128, 1) NB_OCC_S(64, 2) NB_OCC_S(64, 4)
   } else if (c.variant == kTile) {
     NB_OCC(128, 4) NB_OCC(128, 8) NB_OCC(256, 4) NB_OCC(256, 2) NB_OCC(128, 2) NB_OCC(128, 1)
+    NB_OCC(64, 2) NB_OCC(64, 4)
   } else {
     e = c.eqm ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair_warp<4, false, true>, 256, 0)
               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair_warp<4, false, false>, 256, 0);
@@ -304,8 +313,10 @@ int pair_blocks_per_sm(const PairCfg& c) {
 
 bool pair_shape_supported(int variant, int nt, int r, bool vjp) {
   if (variant == kWarp) return vjp ? (nt == 256 && (r == 4 || r == 2)) : (nt == 256 && (r == 4 || r == 8));
-  if (vjp) return (nt == 256 && r == 2) || (nt == 128 && (r == 4 || r == 2 || r == 1));
-  return (nt == 128 && (r == 4 || r == 8 || r == 2 || r == 1)) || (nt == 256 && (r == 4 || r == 2));
+  if (vjp) return (nt == 256 && r == 2) || (nt == 128 && (r == 4 || r == 2 || r == 1)) ||
+                 (nt == 64 && r == 2);
+  return (nt == 128 && (r == 4 || r == 8 || r == 2 || r == 1)) || (nt == 256 && (r == 4 || r == 2)) ||
+         (nt == 64 && (r == 2 || r == 4));
 }
 
 // j-chunk count S for a given shape: the number of blocks covers the

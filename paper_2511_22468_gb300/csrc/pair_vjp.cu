@@ -208,6 +208,8 @@ cudaError_t launch_vjp_impl(const PairCfg& c, const float4* vst, int64_t npad,
       k_vjp_tile<128, 2, EQM, MB><<<grid, 128, 0, s>>>(vst, ntiles, eps2, npad, part, mpart, fin, ctr);
     else if (c.nt == 128 && c.r == 1)
       k_vjp_tile<128, 1, EQM, MB><<<grid, 128, 0, s>>>(vst, ntiles, eps2, npad, part, mpart, fin, ctr);
+    else if (c.nt == 64 && c.r == 2)
+      k_vjp_tile<64, 2, EQM, MB><<<grid, 64, 0, s>>>(vst, ntiles, eps2, npad, part, mpart, fin, ctr);
     else
       return cudaErrorInvalidValue;
   } else {
@@ -237,7 +239,7 @@ int vjp_blocks_per_sm(const PairCfg& c) {
               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(                    \
                     &occ, k_vjp_tile<NT, R, false, false>, NT, 0);
   if (c.variant == kTile) {
-    NB_OCC(256, 2) NB_OCC(128, 4) NB_OCC(128, 2) NB_OCC(128, 1)
+    NB_OCC(256, 2) NB_OCC(128, 4) NB_OCC(128, 2) NB_OCC(128, 1) NB_OCC(64, 2)
   } else {
     e = c.eqm ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_vjp_warp<4, true, false>, 256, 0)
               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_vjp_warp<4, false, false>, 256, 0);

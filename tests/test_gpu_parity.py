@@ -121,7 +121,7 @@ def test_full_size_step_and_adjoint_sampled():
 # (variant, threads, per thread, chunks (0: automatic), where the chunk sums
 # are added (-1: automatic))
 VJP_SHAPES = [(0, 256, 2, 0, -1), (0, 128, 4, 0, -1), (0, 128, 2, 0, -1), (0, 128, 1, 0, -1),
-              (0, 128, 2, 9, 1), (0, 128, 2, 9, 0)]
+              (0, 128, 2, 9, 1), (0, 128, 2, 9, 0), (0, 64, 2, 0, -1), (0, 64, 2, 17, 1)]
 
 
 @pytest.mark.parametrize("eqm", [False, True])
@@ -170,6 +170,41 @@ def test_tile_vjp_and_mass_gradient_sampled(eqm):
         assert tuple(nb.nbody_get_pair_shape(sim.h, 1))[:3] == (variant, nt, r)
         assert sim.status() == 0
         sim.close()
+
+
+@pytest.mark.parametrize("n", [10000, 70001])
+def test_tile_force_shapes_one_step(n):
+    """Every tile shape of the pair-force kernel (including the 64-thread
+    blocks for small systems), general masses: one kick-drift-kick step,
+    whose closed form x1 - x0 - dt v0 = (dt^2 / 2) a(x0) gives the
+    acceleration, against the oracle (1e-5 per particle; sampled rows for
+    the larger n), the chunk sums added by the pair kernel and by the
+    consumer (same bits)."""
+    x, v, m = plummer_sphere(n, 41, C1.G, 1e5, 0.03, center=C1.X0, velocity=C1.V0)
+    m = m * np.random.default_rng(42).uniform(0.5, 1.5, n)
+    dt, pot = 0.5, C1.pot
+    rows = None if n <= 10000 else np.random.default_rng(43).choice(n, 256, replace=False)
+    ph = orc.Physics(G=C1.G, eps=C1.eps, ext=orc.NFW | orc.MN, nfw_M=pot.nfw_M,
+                     nfw_rs=pot.nfw_rs, mn_M=pot.mn_M, mn_a=pot.mn_a, mn_b=pot.mn_b)
+    sel = np.arange(n) if rows is None else rows
+    a_ref = orc.pair_accel(x, m, C1.G, C1.eps, rows=rows)
+    a_ref += np.array([orc.ext_accel(ph, x[k]) for k in sel])
+    for nt, r in ((128, 4), (128, 8), (256, 4), (256, 2), (128, 2), (128, 1), (64, 2), (64, 4)):
+        outs = []
+        for fin in (0, 1):
+            sim = _sim(n, C1.G, C1.eps, dt, ext=3, pot=pot, center=C1.X0, center_vel=C1.V0,
+                       guide=True)
+            nb.nbody_set_pair_shape(sim.h, 0, 0, nt, r, 9)
+            nb.nbody_set_pair_finish(sim.h, 0, fin)
+            sim.set_state(to_gpu(x), to_gpu(v), to_gpu(m))
+            xo = torch.empty((3, n), dtype=torch.float64, device=DEV)
+            sim.integrate(1, xo)
+            assert sim.status() == 0
+            sim.close()
+            outs.append(xo)
+        assert torch.equal(outs[0], outs[1]), (nt, r)
+        got = (to_np(outs[0])[sel] - x[sel] - dt * v[sel]) / (0.5 * dt * dt)
+        assert acc_err(got, a_ref) <= 1e-5, (nt, r)
 
 
 # --------------------------------------------------------------- trajectory --

@@ -1,9 +1,12 @@
 """What the trained surrogate and the batched grid stage gain over the
 prior centre (needs a GB300), on the recovery workload (N = 1e4, 100 Myr,
 the point-cloud loss) with a reduced training set (768 simulations from the
-batched kernel): both give a start whose parameter error max_k |theta_k /
-theta_obs_k - 1| is smaller than the prior centre's, the grid stage's at
-most half of it, and the simulator's loss is lower there."""
+batched kernel).  The surrogate's inverted start has at most half the prior
+centre's error in t_end, M_Plummer and M_NFW (the binned density at this
+horizon carries almost no information on the disk mass M_MN) and a lower
+simulator loss; the batched grid stage's start has at most half the prior
+centre's error max_k |theta_k / theta_obs_k - 1| over all four parameters
+and a lower loss."""
 import dataclasses
 
 import numpy as np
@@ -37,8 +40,8 @@ def test_warm_starts_reduce_parameter_error():
     centre = np.array(cfg.theta_true)
     obs = centre * np.array(F_OBS)
 
-    def err(th):
-        return float(np.max(np.abs(np.asarray(th) / obs - 1.0)))
+    def err(th, k=4):
+        return float(np.max(np.abs(np.asarray(th)[:k] / obs[:k] - 1.0)))
 
     model = StreamModel(cfg, xh, vh)
     xt, vt = model.final_state(list(obs))
@@ -58,7 +61,7 @@ def test_warm_starts_reduce_parameter_error():
     u0, _ = net.invert(rho * DENSITY_SCALE)
     theta0 = from_u(u0, centre, C4.width)
     net.close()
-    assert err(theta0) < err(centre)
+    assert err(theta0, 3) < 0.5 * err(centre, 3)
     assert model.loss(list(theta0)) < L_centre
 
     X, V = xt.cpu().numpy().T, vt.cpu().numpy().T
