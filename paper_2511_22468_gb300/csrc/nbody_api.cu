@@ -90,6 +90,17 @@ struct nbody_ctx {
   int64_t seg_cap = 0;   // K allocated
   double* xw = nullptr;  // recompute work state [3][npad] x2
   double* vw = nullptr;
+  // small systems: the reverse sweep of a segment runs beside the
+  // recomputation of the segment before it (stream rs2, the second segment
+  // buffer, its own pair-kernel scratch), so that two kernels share the SMs
+  double* seg2 = nullptr;  // [3K][3][npad]
+  int64_t seg2_cap = 0;
+  float4* st2 = nullptr;
+  double* part2 = nullptr;
+  double* fin2 = nullptr;
+  unsigned* pctr2 = nullptr;
+  cudaStream_t rs2 = nullptr;
+  cudaEvent_t ev_rfork = nullptr, ev_rready = nullptr;
 
   // adjoint
   double* xbar = nullptr;
@@ -253,6 +264,12 @@ bool graph_eligible(const nbody_ctx* c, int64_t n_steps) {
   return !c->timing && c->npad <= 262144 && n_steps >= 4;
 }
 
+// the overlapped reverse sweep: small systems, whose kernels leave SMs idle,
+// and not under per-kernel event timing (events on one stream)
+bool use_overlap(const nbody_ctx* c) {
+  return !c->timing && c->npad < 65536 && c->rs2 != nullptr;
+}
+
 template <class F>
 int run_graph(nbody_ctx* c, const uint64_t (&key)[12], F record) {
   if (!c->gs) {
@@ -366,36 +383,89 @@ int ensure_tape(nbody_ctx* c, int64_t nseg, int64_t K) {
     rc = dalloc(&c->vw, slot);
     if (rc) return rc;
   }
+  if (c->npad < 65536) {  // the overlapped reverse sweep's second buffer and scratch
+    if (c->seg2_cap < K || !c->seg2) {
+      drop_graphs(c);
+      dfree(c->seg2);
+      c->seg2_cap = 0;
+      int rc = dalloc(&c->seg2, (size_t)3 * K * slot);
+      if (rc) return rc;
+      c->seg2_cap = K;
+    }
+    if (!c->rs2) {
+      drop_graphs(c);
+      const size_t np = (size_t)c->npad;
+      int rc = NBODY_OK;
+      if (!c->st2) rc = dalloc(&c->st2, np);
+      if (!rc && !c->part2) rc = dalloc(&c->part2, (size_t)c->Smax * 3 * np);
+      if (!rc && !c->fin2) rc = dalloc(&c->fin2, 4 * np);
+      if (!rc && !c->pctr2) {
+        rc = dalloc(&c->pctr2, np / 128);
+        if (!rc && cudaMemsetAsync(c->pctr2, 0, (np / 128) * sizeof(unsigned), c->stream) !=
+                       cudaSuccess) {
+          cudaGetLastError();
+          dfree(c->pctr2);
+          rc = NBODY_ECUDA;
+        }
+      }
+      if (rc) return rc;
+      if ((!c->ev_rfork &&
+           cudaEventCreateWithFlags(&c->ev_rfork, cudaEventDisableTiming) != cudaSuccess) ||
+          (!c->ev_rready &&
+           cudaEventCreateWithFlags(&c->ev_rready, cudaEventDisableTiming) != cudaSuccess) ||
+          cudaStreamCreateWithFlags(&c->rs2, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        c->rs2 = nullptr;
+        return NBODY_ECUDA;
+      }
+    }
+  }
   return NBODY_OK;
 }
 
 struct Tape {
   nbody_ctx* c;
   size_t slot;
+  double* seg = nullptr;  // segment buffer (the context's first when null)
+  double* base() const { return seg ? seg : c->seg; }
   double* cpx(int64_t i) const { return c->cp + (size_t)i * 3 * slot; }
   double* cpv(int64_t i) const { return cpx(i) + slot; }
   double* cpa(int64_t i) const { return cpx(i) + 2 * slot; }
-  double* sx(int64_t j) const { return c->seg + (size_t)j * slot; }
-  double* sa(int64_t j) const { return c->seg + (size_t)(c->K + j) * slot; }
+  double* sx(int64_t j) const { return base() + (size_t)j * slot; }
+  double* sa(int64_t j) const { return base() + (size_t)(c->K + j) * slot; }
   double* svh(int64_t j) const {  // j = 1..K
-    return c->seg + (size_t)(2 * c->K + j - 1) * slot;
+    return base() + (size_t)(2 * c->K + j - 1) * slot;
   }
 };
 
-nb::UpdateArgs base_update(nbody_ctx* c, double* x, double* v) {
+// the pair kernel's staging and sums used by a forward run or recomputation
+struct PairScratch {
+  float4* st;
+  double* part;
+  double* fin;
+  unsigned* pctr;
+};
+PairScratch primary_scratch(nbody_ctx* c) { return {c->st, c->part, c->fin, c->pctr}; }
+PairScratch second_scratch(nbody_ctx* c) { return {c->st2, c->part2, c->fin2, c->pctr2}; }
+
+nb::UpdateArgs base_update(nbody_ctx* c, double* x, double* v, const PairScratch& sc) {
   nb::UpdateArgs a{};
   a.P = c->dp;
   a.n = c->n;
   a.npad = c->npad;
   a.x = x;
   a.v = v;
-  a.part = c->part;
+  a.part = sc.part;
   a.S = c->fcfg.S;
   a.part_is_final = 0;
   a.mscale = c->fcfg.eqm ? c->m_eq : 1.0;
-  a.st = c->st;
+  a.st = sc.st;
   a.status = c->status;
   return a;
+}
+
+nb::UpdateArgs base_update(nbody_ctx* c, double* x, double* v) {
+  return base_update(c, x, v, primary_scratch(c));
 }
 
 // The external field of the point x is computed on the side stream while
@@ -424,19 +494,23 @@ bool use_fin(const nb::PairCfg& f, int mode) {
   return mode < 0 ? f.S >= 8 : mode == 1;
 }
 
-int pair_forward(nbody_ctx* c, nb::UpdateArgs& a, cudaStream_t s) {
+int pair_forward(nbody_ctx* c, nb::UpdateArgs& a, cudaStream_t s, const PairScratch& sc) {
   const bool fin = use_fin(c->fcfg, c->fin_mode);
   CK(timed(c, NBODY_KCLASS_PAIR, [&] {
-    return fin ? nb::launch_pair_accel_fin(c->fcfg, c->st, c->npad, c->hp.eps2f, c->part,
-                                           c->fin, c->pctr, s)
-               : nb::launch_pair_accel(c->fcfg, c->st, c->npad, c->hp.eps2f, c->part,
+    return fin ? nb::launch_pair_accel_fin(c->fcfg, sc.st, c->npad, c->hp.eps2f, sc.part,
+                                           sc.fin, sc.pctr, s)
+               : nb::launch_pair_accel(c->fcfg, sc.st, c->npad, c->hp.eps2f, sc.part,
                                        nullptr, s);
   }));
   if (fin) {
-    a.part = c->fin;
+    a.part = sc.fin;
     a.S = 1;
   }
   return NBODY_OK;
+}
+
+int pair_forward(nbody_ctx* c, nb::UpdateArgs& a, cudaStream_t s) {
+  return pair_forward(c, a, s, primary_scratch(c));
 }
 
 // The launches of a forward run over points 0..n_steps (on stream s).
@@ -519,9 +593,11 @@ int run_forward(nbody_ctx* c, int64_t n_steps, bool with_tape) {
   return NBODY_OK;
 }
 
-// Recompute segment sg from its checkpoint into the segment buffer.
-int recompute_segment(nbody_ctx* c, int64_t sg, cudaStream_t s) {
-  Tape T{c, (size_t)3 * c->npad};
+// Recompute segment sg from its checkpoint into the segment buffer seg
+// (the context's first when null), with the pair-kernel scratch sc.
+int recompute_segment(nbody_ctx* c, int64_t sg, cudaStream_t s, const PairScratch& sc,
+                      double* seg) {
+  Tape T{c, (size_t)3 * c->npad, seg};
   const int64_t K = c->K, n = c->tape_steps;
   const int64_t k0 = sg * K;
   const int64_t Ks = (k0 + K <= n) ? K : n - k0;
@@ -530,14 +606,14 @@ int recompute_segment(nbody_ctx* c, int64_t sg, cudaStream_t s) {
   CK(cudaMemcpyAsync(c->vw, T.cpv(sg), bytes, cudaMemcpyDeviceToDevice, s));
   for (int64_t j = 0; j < Ks; ++j) {
     const int64_t k = k0 + j;
-    nb::UpdateArgs a = base_update(c, c->xw, c->vw);
+    nb::UpdateArgs a = base_update(c, c->xw, c->vw, sc);
     if (j == 0) {
       a.part = T.cpa(sg);
       a.S = 1;
       a.part_is_final = 1;
     } else {
       if (int r_ = fork_field(c, c->xw, s)) return r_;
-      if (int r_ = pair_forward(c, a, s)) return r_;
+      if (int r_ = pair_forward(c, a, s, sc)) return r_;
       if (int r_ = join_field(c, s, a)) return r_;
     }
     a.kick = (k == 0) ? 0.5 : 1.0;
@@ -602,6 +678,16 @@ void free_all(nbody_ctx* c) {
   dfree(c->centers);
   dfree(c->cp);
   dfree(c->seg);
+  dfree(c->seg2);
+  dfree(c->st2);
+  dfree(c->part2);
+  dfree(c->fin2);
+  dfree(c->pctr2);
+  if (c->rs2) cudaStreamDestroy(c->rs2);
+  if (c->ev_rfork) cudaEventDestroy(c->ev_rfork);
+  if (c->ev_rready) cudaEventDestroy(c->ev_rready);
+  c->rs2 = nullptr;
+  c->ev_rfork = c->ev_rready = nullptr;
   dfree(c->xw);
   dfree(c->vw);
   dfree(c->xbar);
@@ -857,12 +943,40 @@ int record_sweep(nbody_ctx* c, cudaStream_t s) {
     a.S = 1;
     if (a.mpart) a.mpart = c->fin + 3 * np;
   }
+  // small systems: segment sg - 1 is recomputed on rs2 (second buffer,
+  // second scratch) while the reverse sweep of segment sg runs on s; the
+  // last segment uses the first buffer (where the forward run keeps it)
+  const bool overlap = use_overlap(c) && nseg >= 2;
+  auto seg_of = [&](int64_t sg) { return ((nseg - 1 - sg) & 1) ? c->seg2 : c->seg; };
+  // the update restages positions only: masses and padding come from the
+  // primary staging
+  if (overlap)
+    CK(cudaMemcpyAsync(c->st2, c->st, np * sizeof(float4), cudaMemcpyDeviceToDevice, s));
   for (int64_t sg = nseg - 1; sg >= 0; --sg) {
     const int64_t k0 = sg * K;
     const int64_t Ks = (k0 + K <= n) ? K : n - k0;
-    if (!(sg == nseg - 1 && last_valid)) {
-      const int rc = recompute_segment(c, sg, s);
-      if (rc) return rc;
+    if (!overlap) {
+      if (!(sg == nseg - 1 && last_valid)) {
+        const int rc = recompute_segment(c, sg, s, primary_scratch(c), nullptr);
+        if (rc) return rc;
+      }
+    } else {
+      T.seg = seg_of(sg);
+      if (sg == nseg - 1) {
+        if (!last_valid) {
+          const int rc = recompute_segment(c, sg, s, primary_scratch(c), T.seg);
+          if (rc) return rc;
+        }
+      } else {
+        CK(cudaStreamWaitEvent(s, c->ev_rready, 0));  // segment sg recomputed
+      }
+      if (sg >= 1) {  // segment sg - 1, beside this segment's reverse sweep
+        CK(cudaEventRecord(c->ev_rfork, s));
+        CK(cudaStreamWaitEvent(c->rs2, c->ev_rfork, 0));
+        const int rc = recompute_segment(c, sg - 1, c->rs2, second_scratch(c), seg_of(sg - 1));
+        if (rc) return rc;
+        CK(cudaEventRecord(c->ev_rready, c->rs2));
+      }
     }
     for (int64_t j = Ks; j >= 1; --j) {
       const int64_t k = k0 + j;
