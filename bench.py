@@ -620,17 +620,19 @@ def run_ours(args):
     def recovery():
         # time to a 5 % error on all four parameters (N = 1e4, 100 Myr,
         # point-cloud loss) for the plain descent, the batched grid stage
-        # then descent, and the surrogate warm start, one observation
+        # then descent, the surrogate warm start, and the surrogate's start
+        # refined by the grid stage, one observation
         from paper_2511_22468_gb300 import warmstart
         r = warmstart.run(observations=(warmstart.F_OBS,), device=str(dev))
         o = r["observations"][0]
         out = {"workload": "gd1_stream_n10k_100myr_mmd", "err_target": r["workload"]["err_target"],
                "f_obs": o["f_obs"], "surrogate_training": r["surrogate_training"]}
-        for k in ("plain", "batched", "surrogate"):
+        for k in ("plain", "batched", "surrogate", "surrogate_grid"):
             x = o[k]
             out[k] = {key: x[key] for key in ("reached", "time_to_target_s", "final_err",
                                               "start_err", "iters")}
-            for key in ("grid_calls", "grid_s", "theta0_err", "time_incl_data_and_training_s"):
+            for key in ("grid_calls", "grid_s", "theta0_err", "inversion_and_grid_s",
+                        "time_incl_data_and_training_s"):
                 if key in x:
                     out[k][key] = x[key]
         return out

@@ -12,7 +12,8 @@ step), pair evaluations per second (a run of k kick-drift-kick steps makes
 k + 1 pair passes: the kicks at both ends of a step share one force) and
 the fraction of the FP32 peak at 20 flops per evaluation.
 
-    python -m paper_2511_22468_gb300.nsweep [--sizes 1000,10000,...] [--adjoint]
+    python -m paper_2511_22468_gb300.nsweep [--sizes 1000,10000,...] [--adjoint] [--steps K]
+        [--pair-shape V,T,R,S] [--vjp-shape V,T,R,S]
 """
 from __future__ import annotations
 
@@ -34,7 +35,9 @@ def peak_tflops(dev):
     return sms * 128 * 2 * 2.07e9 / 1e12
 
 
-def measure(n, steps, adjoint=False, device="cuda:0", seed=5):
+def measure(n, steps, adjoint=False, device="cuda:0", seed=5, shapes=None):
+    """One size; shapes = (pair, vjp) launch shapes (variant, threads,
+    per_thread, chunks), either None, replaces the autotuner when given."""
     dev = torch.device(device)
     pot = C1.pot
     x, v, m = plummer_sphere(n, seed, G_KPC_MSUN_MYR, C1.M_prog, C1.a_prog, center=C1.X0,
@@ -48,7 +51,13 @@ def measure(n, steps, adjoint=False, device="cuda:0", seed=5):
     M = torch.tensor(m, device=dev)
     sim = nb.Simulation(n, p)
     sim.set_state(X, V, M)
-    fwd_shape, vjp_shape = nb.nbody_autotune_pair(sim.h)
+    if shapes is None:
+        fwd_shape, vjp_shape = nb.nbody_autotune_pair(sim.h)
+    else:
+        for vjp, sh in enumerate(shapes):
+            if sh is not None:
+                nb.nbody_set_pair_shape(sim.h, vjp, *sh)
+        fwd_shape, vjp_shape = nb.nbody_get_pair_shape(sim.h, 0), nb.nbody_get_pair_shape(sim.h, 1)
     stream = torch.cuda.current_stream(dev)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -57,6 +66,9 @@ def measure(n, steps, adjoint=False, device="cuda:0", seed=5):
         sim.vjp(X, None)
     sim.set_state(X, V, M)
     torch.cuda.synchronize(dev)
+    # the timed region is an NVTX range ("timed"), so that a profiler can be
+    # limited to it and skip the autotuner's and the warm-up's launches
+    torch.cuda.nvtx.range_push("timed")
     e0.record(stream)
     sim.integrate(steps)
     e1.record(stream)
@@ -75,6 +87,7 @@ def measure(n, steps, adjoint=False, device="cuda:0", seed=5):
         t_bwd = e0.elapsed_time(e1) / 1e3
         row["adjoint_ms_per_step"] = 1e3 * t_bwd / steps
         row["fwd_adjoint_interactions_per_s"] = 2.0 * n * n * steps / (t_fwd + t_bwd)
+    torch.cuda.nvtx.range_pop()
     row["shapes"] = {"pair": list(fwd_shape), "vjp": list(vjp_shape)}
     row["status_ok"] = sim.status() == 0
     sim.close()
@@ -90,11 +103,22 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--sizes", default="1000,3000,10000,30000,100000,300000,1000000")
     ap.add_argument("--adjoint", action="store_true")
+    ap.add_argument("--steps", type=int, default=None,
+                    help="steps per size (default: about 2e11 interactions)")
+    ap.add_argument("--pair-shape", default=None,
+                    help="variant,threads,per_thread,chunks of the pair-force kernel "
+                         "(with --vjp-shape: instead of the autotuner)")
+    ap.add_argument("--vjp-shape", default=None, help="the same for the pair-VJP kernel")
     a = ap.parse_args()
     from . import build
     build.build()
+    shapes = None
+    if a.pair_shape or a.vjp_shape:
+        shapes = tuple(tuple(int(v) for v in sh.split(",")) if sh else None
+                       for sh in (a.pair_shape, a.vjp_shape))
     for n in [int(s) for s in a.sizes.split(",")]:
-        print(json.dumps(measure(n, default_steps(n), adjoint=a.adjoint)), flush=True)
+        steps = a.steps if a.steps else default_steps(n)
+        print(json.dumps(measure(n, steps, adjoint=a.adjoint, shapes=shapes)), flush=True)
 
 
 if __name__ == "__main__":

@@ -28,11 +28,15 @@ chaotic growth of the progenitor's adjoint):
     extent at this horizon) of n_train prior samples from the batched kernel,
     the network trained on them by the library's kernels and inverted for the
     observed density, then the plain descent from there.  Its time is given
-    with and without the one-off data generation and training.
+    with and without the one-off data generation and training;
+  * surrogate + grid: the same inversion as the start of the batched grid
+    stage, whose first spacing per parameter is twice the surrogate's rms
+    inversion error on validation densities (measured once after training:
+    the spread the surrogate leaves in each parameter), then the descent.
 Every final parameter comes from the simulator-gradient descent.
 
     python -m paper_2511_22468_gb300.warmstart [--n 10000] [--t-end 100]
-        [--err-target 0.05] [--n-train 3584] [--epochs 300]
+        [--err-target 0.05] [--n-train 3584] [--epochs 300] [--n-random K]
 """
 from __future__ import annotations
 
@@ -57,17 +61,19 @@ SIGMAS = (0.5, 1.0, 2.0)
 
 
 def pattern_search(batch, centre, width, theta_true, err_target, s0=0.5, s_min=0.02,
-                   max_calls=30, clock=time.perf_counter):
+                   max_calls=30, clock=time.perf_counter, u_start=None):
     """The grid stage on the batched pipeline: each call evaluates the loss
-    at the 81 points centre + s * {-1, 0, 1}^4 (normalised parameters) as
-    members of one batch; the best point becomes the new centre, and the
-    spacing s halves when the centre itself is best.  Returns the trajectory
-    of estimates (the best point so far after every call)."""
+    at the 81 points c + s * {-1, 0, 1}^4 (normalised parameters, c = 0, the
+    prior centre, unless u_start is given; s a number or one spacing per
+    parameter) as members of one batch; the best point becomes the new c,
+    and the spacing halves when c itself is best.
+    Returns the trajectory of estimates (the best point so far after every
+    call)."""
     centre = np.asarray(centre, float)
     grid = np.array(list(itertools.product((-1.0, 0.0, 1.0), repeat=4)))
     t0 = clock()
-    c = np.zeros(4)
-    s = float(s0)
+    c = np.zeros(4) if u_start is None else np.clip(np.asarray(u_start, float), -1.5, 1.5)
+    s = np.asarray(s0, float) * np.ones(4)  # spacing per parameter
     best_L, best_u = np.inf, c.copy()
     traj = []
     for call in range(max_calls):
@@ -82,8 +88,8 @@ def pattern_search(batch, centre, width, theta_true, err_target, s0=0.5, s_min=0
         th = from_u(best_u, centre, width)
         err = float(np.max(np.abs(th / theta_true - 1.0)))
         traj.append({"iter": call, "t": clock() - t0, "loss": best_L, "err": err,
-                     "theta": th.tolist(), "spacing": s})
-        if err <= err_target or s < s_min:
+                     "theta": th.tolist(), "spacing": s.tolist()})
+        if err <= err_target or np.max(s) < s_min:
             break
     return traj
 
@@ -108,7 +114,7 @@ def summary(tr, err_target, t_pre=0.0, extra=None):
 
 def run(n=10_000, t_end=100.0, err_target=0.05, n_train=3584, n_val=512, epochs=300,
         max_iters=200, lr=0.2, lr_warm=0.05, window=(1.0, 0.5), observations=F_OBS_LIST,
-        grid_s0=0.37, device="cuda:0"):
+        grid_s0=0.37, n_calib=16, device="cuda:0", n_random=0, random_seed=777):
     dev = torch.device(device)
     steps = int(round(t_end / 0.5))
     cfg = dataclasses.replace(C1, n=n, t_acc=float(t_end), n_steps=steps,
@@ -140,9 +146,23 @@ def run(n=10_000, t_end=100.0, err_target=0.05, n_train=3584, n_val=512, epochs=
                    U_val=U[n_train:], Y_val=Y[n_train:], log_every=max(1, epochs // 10))
     sync()
     t_train = time.perf_counter() - t0
+    # the surrogate's spread per parameter: rms inversion error (normalised
+    # units) on n_calib validation densities; the warm grid stage's spacing
+    t0 = time.perf_counter()
+    u_cal = np.array([net.invert(Y[n_train + i])[0] for i in range(n_calib)])
+    sigma_u = np.sqrt(np.mean((u_cal - U[n_train:n_train + n_calib]) ** 2, axis=0))
+    t_cal = time.perf_counter() - t0
+    s0_warm = np.clip(2.0 * sigma_u, 0.1, 0.6)
+    t_train += t_cal
     out["surrogate_training"] = {"data_generation_s": t_gen, "n_train": n_train,
                                  "n_val": n_val, "training_s": t_train,
+                                 "calibration_s": t_cal, "inversion_rms_u": sigma_u.tolist(),
+                                 "grid_spacing0_warm": s0_warm.tolist(),
                                  "val_mse": hist[-1].get("val_mse")}
+    if n_random:
+        observations = tuple(observations) + tuple(
+            tuple(float(v) for v in f) for f in
+            uniform_factors(n_random, 0.8 * width, 4, random_seed))
 
     model = StreamModel(cfg, xh, vh, device=device)
     runs = []
@@ -170,7 +190,6 @@ def run(n=10_000, t_end=100.0, err_target=0.05, n_train=3584, n_val=512, epochs=
         t0 = time.perf_counter()
         grid = pattern_search(sb, centre, width, theta_obs, err_target, s0=grid_s0)
         t_grid = time.perf_counter() - t0
-        sb.close()
         tr = descend(model, np.array(grid[-1]["theta"]), centre, width, lr=lr_warm,
                      max_iters=max_iters, theta_true=theta_obs, err_target=err_target)
         r["batched"] = summary(tr, err_target, t_pre=t_grid,
@@ -193,9 +212,29 @@ def run(n=10_000, t_end=100.0, err_target=0.05, n_train=3584, n_val=512, epochs=
                    "inversion_loss": inv_loss,
                    "time_incl_data_and_training_s":
                        None if t_hit is None else t_hit + t_inv + t_gen + t_train})
+
+        # surrogate + grid: the grid stage started at the inverted point with
+        # the smaller spacing, then the descent from its best point
+        sync()
+        t0 = time.perf_counter()
+        u0, _ = net.invert(rho_obs * DENSITY_SCALE)
+        grid = pattern_search(sb, centre, width, theta_obs, err_target, s0=s0_warm,
+                              u_start=u0)
+        t_pre = time.perf_counter() - t0
+        tr = descend(model, np.array(grid[-1]["theta"]), centre, width, lr=lr_warm,
+                     max_iters=max_iters, theta_true=theta_obs, err_target=err_target)
+        t_hit = time_to_err(tr, err_target)
+        r["surrogate_grid"] = summary(
+            tr, err_target, t_pre=t_pre,
+            extra={"grid_calls": len(grid), "members_per_call": 81,
+                   "inversion_and_grid_s": t_pre, "grid_err": grid[-1]["err"],
+                   "gradients": len(tr),
+                   "time_incl_data_and_training_s":
+                       None if t_hit is None else t_hit + t_pre + t_gen + t_train})
+        sb.close()
         runs.append(r)
     out["observations"] = runs
-    for k in ("plain", "batched", "surrogate"):
+    for k in ("plain", "batched", "surrogate", "surrogate_grid"):
         ts = [r[k]["time_to_target_s"] for r in runs]
         out[k + "_reached"] = sum(t is not None for t in ts)
         out[k + "_median_time_to_target_s"] = (float(np.median([t for t in ts if t is not None]))
@@ -215,11 +254,15 @@ def main():
     ap.add_argument("--epochs", type=int, default=300)
     ap.add_argument("--max-iters", type=int, default=200)
     ap.add_argument("--lr", type=float, default=0.2)
+    ap.add_argument("--n-random", type=int, default=0,
+                    help="observations drawn from the inner 80 %% of the prior, besides the three "
+                         "fixed ones")
     a = ap.parse_args()
     from . import build
     build.build()
     res = run(n=a.n, t_end=a.t_end, err_target=a.err_target, n_train=a.n_train,
-              n_val=a.n_val, epochs=a.epochs, max_iters=a.max_iters, lr=a.lr)
+              n_val=a.n_val, epochs=a.epochs, max_iters=a.max_iters, lr=a.lr,
+              n_random=a.n_random)
     print(json.dumps(res))
 
 

@@ -19,7 +19,8 @@ from oracle import core as orc  # noqa: E402
 from paper_2511_22468_gb300 import nbody as nb  # noqa: E402
 from paper_2511_22468_gb300.configs import C1, C3  # noqa: E402
 from paper_2511_22468_gb300.inputs import plummer_sphere  # noqa: E402
-from tolerances import per_particle_err  # noqa: E402
+from tolerances import (mass_grad_abs_terms, per_particle_err,  # noqa: E402
+                        per_particle_err_fp32_sum)
 
 pytestmark = pytest.mark.gpu
 
@@ -205,6 +206,79 @@ def test_tile_force_shapes_one_step(n):
         assert torch.equal(outs[0], outs[1]), (nt, r)
         got = (to_np(outs[0])[sel] - x[sel] - dt * v[sel]) / (0.5 * dt * dt)
         assert acc_err(got, a_ref) <= 1e-5, (nt, r)
+
+
+# warp-variant shapes (threads, per thread): pair force, pair VJP
+WARP_FWD = ((256, 4), (256, 8))
+WARP_VJP = ((256, 4), (256, 2))
+
+
+@pytest.mark.parametrize("n", [3001, 10000])
+@pytest.mark.parametrize("eqm", [False, True])
+def test_warp_shapes_force_vjp_and_mass_gradient(n, eqm):
+    """The split-j warp variants of the pair-force and pair-VJP kernels
+    (lanes split the j-range, fixed xor butterfly), each shape with the
+    automatic chunk count and with 5 chunks, general masses (spread over
+    [0.5, 1.5] of the mean) and equal masses, at N = 3001 (ragged, npad =
+    3072) and at the stream workload's N = 10^4: one kick-drift-kick step,
+    whose closed form x1 - x0 - dt v0 = (dt^2 / 2) a(x0) gives the
+    acceleration (1e-5 per particle), and its reverse sweep with xbar = W,
+    vbar = 0, whose closed forms are x0bar - W = (dt^2 / 2) ((J_pair +
+    J_ext)(x0)^T W) (1e-4 per particle) and mbar = (dt^2 / 2) sum_i W_i .
+    d a_i / d m_k (a sum of terms of either sign whose cancellation reaches
+    1e4 at some particles: 1e-4 relative plus the FP32 summation bound
+    8 u sum|terms|), against the oracle on every row (N = 3001) or 1024
+    sampled rows with the first and last; the pair energy of the forward
+    shape against the oracle's (1e-6 relative); repeated runs give the same
+    bits."""
+    dt, pot = 0.5, C1.pot
+    x, v, m = plummer_sphere(n, 51, C1.G, 1e5, 0.03, center=C1.X0, velocity=C1.V0)
+    if not eqm:
+        m = m * np.random.default_rng(52).uniform(0.5, 1.5, n)
+    rows = None if n < 5000 else np.unique(np.concatenate(
+        [[0, n - 1], np.random.default_rng(53).choice(n, 1024, replace=False)]))
+    sel = np.arange(n) if rows is None else rows
+    ph = orc.Physics(G=C1.G, eps=C1.eps, ext=orc.NFW | orc.MN, nfw_M=pot.nfw_M,
+                     nfw_rs=pot.nfw_rs, mn_M=pot.mn_M, mn_a=pot.mn_a, mn_b=pot.mn_b)
+    a_ref = orc.pair_accel(x, m, C1.G, C1.eps, rows=rows)
+    a_ref += np.array([orc.ext_accel(ph, x[k]) for k in sel])
+    W = np.random.default_rng(54).normal(size=(n, 3))
+    Jt = orc.pair_vjp(x, m, C1.G, C1.eps, W, rows=rows)
+    Jt += np.array([orc.ext_jac(ph, x[k]).T @ W[k] for k in sel])
+    mref = orc.pair_mass_vjp(x, C1.G, C1.eps, W, rows=rows)
+    mabs = mass_grad_abs_terms(x, C1.G, C1.eps, W, rows=rows)
+    W_pair = orc.energy(orc.Physics(G=C1.G, eps=C1.eps), x, v, m)["W_pair"]
+    X, V, M, WG = to_gpu(x), to_gpu(v), to_gpu(m), to_gpu(W)
+    for which, shapes in ((0, WARP_FWD), (1, WARP_VJP)):
+        for nt, r in shapes:
+            for chunks in (0, 5):
+                outs = []
+                for rep in range(2):
+                    sim = _sim(n, C1.G, C1.eps, dt, K=1, ext=3, pot=pot, center=C1.X0,
+                               center_vel=C1.V0, guide=True)
+                    nb.nbody_set_pair_shape(sim.h, which, 1, nt, r, chunks)
+                    assert tuple(nb.nbody_get_pair_shape(sim.h, which))[:3] == (1, nt, r)
+                    sim.set_state(X, V, M)
+                    if which == 0 and rep == 0:
+                        assert sim.energy()[1] == pytest.approx(W_pair, rel=1e-6), (nt, r)
+                    xo = torch.empty((3, n), dtype=torch.float64, device=DEV)
+                    sim.integrate(1, xo)
+                    x0b = torch.empty_like(xo)
+                    mb = torch.empty(n, dtype=torch.float64, device=DEV)
+                    sim.vjp(WG, None, x0b, None, mb)
+                    assert sim.status() == 0
+                    sim.close()
+                    outs.append((xo, x0b, mb))
+                key = (which, nt, r, chunks)
+                for a, b in zip(*outs):
+                    assert torch.equal(a, b), key
+                xo, x0b, mb = outs[0]
+                got = (to_np(xo)[sel] - x[sel] - dt * v[sel]) / (0.5 * dt * dt)
+                assert acc_err(got, a_ref) <= 1e-5, key
+                gb = (to_np(x0b)[sel] - W[sel]) / (0.5 * dt * dt)
+                assert per_particle_err(gb, Jt) <= 1e-4, key
+                gm = to_np(mb)[sel] / (0.5 * dt * dt)
+                assert per_particle_err_fp32_sum(gm, mref, mabs) <= 1.0, key
 
 
 # --------------------------------------------------------------- trajectory --
