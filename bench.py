@@ -351,7 +351,8 @@ def measure_stream_c1(dev, peak_max):
     t = time_pipeline(reps=2, autotune=True)
     out = {"workload": "gd1_stream_n10k_6000_steps", "forward_s": t["forward_s"],
            "gradient_s": t["gradient_s"], "forward_us_per_step": t["forward_us_per_step"],
-           "fwd_adjoint_us_per_step": t["forward_us_per_step"] + t["gradient_us_per_step"]}
+           "fwd_adjoint_us_per_step": t["forward_us_per_step"] + t["gradient_us_per_step"],
+           "pipeline_shapes": t.get("shapes")}
     n, steps = C1.n, 200
     x, v, m = plummer_sphere(n, C1.seed, C1.G, C1.M_prog, C1.a_prog, center=C1.X0,
                              velocity=C1.V0)
@@ -522,10 +523,12 @@ def run_ours(args):
     # O(N) FP64 kernels: algorithmic bytes per particle of an interior launch
     # (update: x, v read and written, S partial slices read, FP32 restage;
     # adjoint: cotangents, tape x, a_pair, v_half, x_prev, m read, cotangents
-    # written, S partial slices read, adjoint restage)
+    # written, S partial slices read, adjoint restage, and the external
+    # field's nine adjoint terms computed beside the pair VJP read)
     s_f = nb.nbody_get_pair_shape(sim.h, 0)[3]
     s_v = nb.nbody_get_pair_shape(sim.h, 1)[3]
-    bpp = {"update": 48 + 24 * s_f + 48 + 12, "adjoint": 48 + 72 + 24 * s_v + 56 + 48 + 32}
+    bpp = {"update": 48 + 24 * s_f + 48 + 12,
+           "adjoint": 48 + 72 + 24 * s_v + 56 + 48 + 32 + 72}
     hbm = hbm_peak()
     for name in ("update", "adjoint"):
         ms, cnt = kt[name]

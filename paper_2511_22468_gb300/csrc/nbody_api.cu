@@ -114,6 +114,12 @@ struct nbody_ctx {
   double* aext = nullptr;   // [3][npad]
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // likewise the FP64 external-field terms of the adjoint at a point run on
+  // a second side stream beside that point's pair VJP (allocated with the
+  // tape when the context has an external potential)
+  double* ea = nullptr;     // [kExtAdjCols][npad]
+  cudaStream_t aside = nullptr;
+  cudaEvent_t ev_afork = nullptr, ev_ajoin = nullptr;
   double* mbar = nullptr;   // dL/dm [npad], lazily
   bool want_mbar = false;   // the sweep being recorded accumulates dL/dm
   double pot_bar[6] = {0, 0, 0, 0, 0, 0};  // last sweep's potential-parameter gradient
@@ -358,6 +364,13 @@ int ensure_centers(nbody_ctx* c, int64_t n_steps) {
   return NBODY_OK;
 }
 
+// The adjoint's external-field terms run beside the pair VJP for systems
+// whose VJP launch is long enough to hide them (measured on GB300: at
+// npad = 3072 the 18 us VJP cannot cover the FP64 terms and the sweep
+// slows, at 10240 it gains 13 %); large systems keep them in the adjoint
+// kernel, where they are a small fraction of a point.
+bool ext_adjoint_beside(const nbody_ctx* c) { return c->npad >= 8192 && c->npad < 65536; }
+
 int ensure_tape(nbody_ctx* c, int64_t nseg, int64_t K) {
   const size_t slot = (size_t)3 * c->npad;
   if (c->cp_cap < nseg + 1 || !c->cp) {
@@ -382,6 +395,23 @@ int ensure_tape(nbody_ctx* c, int64_t nseg, int64_t K) {
     if (rc) return rc;
     rc = dalloc(&c->vw, slot);
     if (rc) return rc;
+  }
+  if (c->p.ext_flags && !c->ea && ext_adjoint_beside(c)) {  // field terms beside the VJP
+    drop_graphs(c);
+    int rc = dalloc(&c->ea, (size_t)nb::kExtAdjCols * c->npad);
+    if (rc) return rc;
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    if ((!c->ev_afork &&
+         cudaEventCreateWithFlags(&c->ev_afork, cudaEventDisableTiming) != cudaSuccess) ||
+        (!c->ev_ajoin &&
+         cudaEventCreateWithFlags(&c->ev_ajoin, cudaEventDisableTiming) != cudaSuccess) ||
+        cudaStreamCreateWithPriority(&c->aside, cudaStreamNonBlocking, prio_hi) != cudaSuccess) {
+      cudaGetLastError();
+      c->aside = nullptr;
+      dfree(c->ea);
+      return NBODY_ECUDA;
+    }
   }
   if (c->npad < 65536) {  // the overlapped reverse sweep's second buffer and scratch
     if (c->seg2_cap < K || !c->seg2) {
@@ -657,6 +687,12 @@ void free_all(nbody_ctx* c) {
   c->side = nullptr;
   c->ev_fork = c->ev_join = nullptr;
   dfree(c->aext);
+  if (c->aside) cudaStreamDestroy(c->aside);
+  if (c->ev_afork) cudaEventDestroy(c->ev_afork);
+  if (c->ev_ajoin) cudaEventDestroy(c->ev_ajoin);
+  c->aside = nullptr;
+  c->ev_afork = c->ev_ajoin = nullptr;
+  dfree(c->ea);
   for (auto& pool : c->ev)
     for (auto& pr : pool) {
       cudaEventDestroy(pr.first);
@@ -906,6 +942,27 @@ int nbody_integrate(nbody_ctx* c, int64_t n_steps, double* x_out,
 
 namespace {
 
+// The external potential's adjoint terms of the point a.xk (cotangents: the
+// current v-bar) on the side stream aside, beside the point's pair VJP on
+// stream s; the adjoint kernel then reads them (a.ea).  Without an external
+// potential or side stream, or outside the sizes where this pays, the
+// adjoint kernel computes them itself (the same arithmetic).
+int fork_ext_adjoint(nbody_ctx* c, nb::AdjointArgs& a, cudaStream_t s) {
+  a.ea = nullptr;
+  if (!c->p.ext_flags || !c->aside || !c->ea || !ext_adjoint_beside(c)) return NBODY_OK;
+  CK(cudaEventRecord(c->ev_afork, s));
+  CK(cudaStreamWaitEvent(c->aside, c->ev_afork, 0));
+  CK(nb::launch_ext_adjoint(c->dp, a.xk, c->vbar, c->n, c->npad, c->ea, c->aside));
+  CK(cudaEventRecord(c->ev_ajoin, c->aside));
+  a.ea = c->ea;
+  return NBODY_OK;
+}
+
+int join_ext_adjoint(nbody_ctx* c, const nb::AdjointArgs& a, cudaStream_t s) {
+  if (a.ea) CK(cudaStreamWaitEvent(s, c->ev_ajoin, 0));
+  return NBODY_OK;
+}
+
 // The launches of one reverse sweep over the recorded tape (on stream s):
 // cotangent scaling, segment recomputation, pair VJP and adjoint update at
 // every point, and the reduction of the parameter-gradient sums into red.
@@ -980,11 +1037,13 @@ int record_sweep(nbody_ctx* c, cudaStream_t s) {
     }
     for (int64_t j = Ks; j >= 1; --j) {
       const int64_t k = k0 + j;
+      a.xk = (j == Ks) ? T.cpx(sg + 1) : T.sx(j);
+      if (int r_ = fork_ext_adjoint(c, a, s)) return r_;
       CK(timed(c, NBODY_KCLASS_VJP, [&] {
         return nb::launch_pair_vjp_fin(c->vcfg, c->vst, c->npad, c->hp.eps2f, c->part, mp,
                                        vfin_p, c->pctr, s);
       }));
-      a.xk = (j == Ks) ? T.cpx(sg + 1) : T.sx(j);
+      if (int r_ = join_ext_adjoint(c, a, s)) return r_;
       a.ak = (j == Ks) ? T.cpa(sg + 1) : T.sa(j);
       a.ck = (k == n) ? 0.5 : 1.0;
       a.drift = 1;
@@ -997,11 +1056,13 @@ int record_sweep(nbody_ctx* c, cudaStream_t s) {
     }
   }
   // point 0: opening half kick of the first step
+  a.xk = T.cpx(0);
+  if (int r_ = fork_ext_adjoint(c, a, s)) return r_;
   CK(timed(c, NBODY_KCLASS_VJP, [&] {
     return nb::launch_pair_vjp_fin(c->vcfg, c->vst, c->npad, c->hp.eps2f, c->part, mp, vfin_p,
                                    c->pctr, s);
   }));
-  a.xk = T.cpx(0);
+  if (int r_ = join_ext_adjoint(c, a, s)) return r_;
   a.ak = T.cpa(0);
   a.ck = 0.5;
   a.drift = 0;

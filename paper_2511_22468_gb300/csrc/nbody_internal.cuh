@@ -203,8 +203,19 @@ struct AdjointArgs {
   double* lsc;           // cotangent scales (see kLscDoubles)
   int slot;              // parity of this point's index
   int* status;
+  const double* ea;      // the external field's adjoint terms at this point,
+                         // [kExtAdjCols][npad] from launch_ext_adjoint, or
+                         // NULL: computed by the adjoint kernel itself
 };
 cudaError_t launch_adjoint(const AdjointArgs& a, cudaStream_t s);
+// The external potential's adjoint terms at positions x with cotangents lam
+// (x, lam [3][npad]) into ea [kExtAdjCols][npad]: H_ext(x) lam (3), the
+// per-unit-mass products lam . a_NFW, lam . a_MN, lam . a_bulge (3) and the
+// shape-parameter terms (3), the same values the adjoint kernel computes
+// when it is given no ea (update.cu).
+constexpr int kExtAdjCols = 9;
+cudaError_t launch_ext_adjoint(const DevParams* P, const double* x, const double* lam,
+                               int64_t n, int64_t npad, double* ea, cudaStream_t s);
 int adjoint_blocks(int64_t n);
 
 // out[0..1] = min and max of m[0..n)

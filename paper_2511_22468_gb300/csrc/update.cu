@@ -177,7 +177,18 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
       g[d] = -P.G * a.mscale * (gs[d] / s_here);
     }
     ExtAdj ea;
-    ext_adjoint<true>(P, x[0], x[1], x[2], lam, ea);
+    if (a.ea) {  // computed beside this point's pair VJP (k_ext_adjoint)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        ea.jl[d] = a.ea[d * np + i];
+        ea.sh[d] = a.ea[(6 + d) * np + i];
+      }
+      ea.ln = a.ea[3 * np + i];
+      ea.lm = a.ea[4 * np + i];
+      ea.lb = a.ea[5 * np + i];
+    } else {
+      ext_adjoint<true>(P, x[0], x[1], x[2], lam, ea);
+    }
     const double ck = a.ck * P.dt;
     double xb[3];
     double la = 0.0, lp = 0.0;
@@ -233,6 +244,30 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
     if (i == 0) a.lsc[1 - a.slot] = s_next;
     block_absmax(vmax, reinterpret_cast<unsigned long long*>(a.lsc + 2) + (1 - a.slot));
   }
+}
+
+// the external potential's adjoint terms of every particle at one point
+// (positions x, cotangents lam): the FP64 part of the adjoint update, run
+// on a side stream beside that point's pair VJP; layout [kExtAdjCols][npad]
+// = H lam (3), lam . a_NFW, lam . a_MN, lam . a_bulge per unit mass, shape
+// terms (3)
+__global__ void __launch_bounds__(256)
+    k_ext_adjoint(const DevParams* __restrict__ Pp, const double* __restrict__ x,
+                  const double* __restrict__ lam, int64_t n, int64_t npad,
+                  double* __restrict__ ea) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double l[3] = {lam[i], lam[npad + i], lam[2 * npad + i]};
+  ExtAdj e;
+  ext_adjoint<true>(*Pp, x[i], x[npad + i], x[2 * npad + i], l, e);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    ea[d * npad + i] = e.jl[d];
+    ea[(6 + d) * npad + i] = e.sh[d];
+  }
+  ea[3 * npad + i] = e.ln;
+  ea[4 * npad + i] = e.lm;
+  ea[5 * npad + i] = e.lb;
 }
 
 // external acceleration of the state (x [3][npad]) into aext [3][npad]: the
@@ -416,6 +451,13 @@ cudaError_t launch_stage_vjp(const double* x, const double* m,
 }
 
 int adjoint_blocks(int64_t n) { return (int)blocks_for(n, particle_threads(n)); }
+
+cudaError_t launch_ext_adjoint(const DevParams* P, const double* x, const double* lam,
+                               int64_t n, int64_t npad, double* ea, cudaStream_t s) {
+  k_ext_adjoint<<<blocks_for(n, 64), 64, 0, s>>>(P, x, lam, n, npad, ea);
+  count_launch();
+  return cudaGetLastError();
+}
 
 void set_bulge(DevParams& d, double G, double M, double alpha, double rc) {
   const double s = 0.5 * (3.0 - alpha);

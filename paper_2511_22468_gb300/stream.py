@@ -233,10 +233,12 @@ def time_pipeline(reps=3, autotune=True):
         t2 = time.perf_counter()
         fw.append(t1 - t0)
         gr.append(t2 - t1)
+    shapes = {"pair": list(nb.nbody_stream_get_pair_shape(m.h, 0)),
+              "vjp": list(nb.nbody_stream_get_pair_shape(m.h, 1))}
     m.close()
     return {"workload": "stream_n1e4_6000_steps", "forward_s": min(fw), "gradient_s": min(gr),
             "forward_us_per_step": 1e6 * min(fw) / C1.n_steps,
-            "gradient_us_per_step": 1e6 * min(gr) / C1.n_steps, "loss": L}
+            "gradient_us_per_step": 1e6 * min(gr) / C1.n_steps, "loss": L, "shapes": shapes}
 
 
 if __name__ == "__main__":

@@ -17,7 +17,8 @@ chaotic growth of the progenitor's adjoint):
     at the minimum-loss estimate (Fig. 2 step 5);
   * plain: gradient descent (Adam on normalised parameters, simulator
     adjoint gradient, a step that raises the loss is undone and the rate
-    halved) from theta_c, one simulation per launch; a descent from a warm
+    halved) from theta_c, one simulation per launch with the launch shapes
+    tuned for its size; a descent from a warm
     start (the batched grid's best point, the surrogate's inversion) starts
     with a quarter of the rate, its start being several times closer;
   * batched: the paper's grid stage on the batched kernel -- every call one
@@ -165,6 +166,9 @@ def run(n=10_000, t_end=100.0, err_target=0.05, n_train=3584, n_val=512, epochs=
             uniform_factors(n_random, 0.8 * width, 4, random_seed))
 
     model = StreamModel(cfg, xh, vh, device=device)
+    # the single-system pipeline takes the launch shapes tuned for this size,
+    # as the batched stage does (one-off, not timed)
+    model.autotune(list(centre))
     runs = []
     for fo in observations:
         theta_obs = centre * np.array(fo)
