@@ -660,7 +660,8 @@ NBODY_API void nbody_orbitfit_destroy(nbody_orbitfit *h);
  *      coupled to the solver) ---- */
 
 /* y = W3 GELU(W2 GELU(W1 u + b1) + b2) + b3, GELU(z) = z Phi(z) with the
- * exact normal CDF, FP32.  Parameters are one flat FP32 array in the order
+ * exact normal CDF, FP32 (the contractions on the tensor cores as three
+ * TF32 products per FP32 product: a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi).  Parameters are one flat FP32 array in the order
  * W1 (h x in), b1 (h), W2 (h x h), b2 (h), W3 (out x h), b3 (out), weight
  * matrices row-major (one row per output unit).  Inputs u are (batch x in)
  * and outputs y, targets t (batch x out), row-major, in device memory.
@@ -710,6 +711,12 @@ NBODY_API int nbody_mlp_adam_step(nbody_mlp *m, float lr, float beta1,
 NBODY_API int nbody_mlp_invert(nbody_mlp *m, const float *target, int starts,
                                float *u, int iters, float lr, float lo, float hi,
                                float *loss);
+
+/* Sticky device status of the network's tensor-core GEMMs: NBODY_OK, or
+ * NBODY_ETIMEOUT when a bounded wait for the tensor cores' completion
+ * expired (that GEMM's output was not written).  Synchronises the network's
+ * stream.  Errors: EINVAL, ECUDA. */
+NBODY_API int nbody_mlp_get_status(nbody_mlp *m);
 
 /* Release the network; NULL is a no-op. */
 NBODY_API void nbody_mlp_destroy(nbody_mlp *m);

@@ -48,7 +48,7 @@ EXPORTED = ("nbody_create", "nbody_destroy", "nbody_set_params",
             "nbody_set_tuning", "nbody_get_tuning", "nbody_mlp_create",
             "nbody_mlp_num_params", "nbody_mlp_set_params", "nbody_mlp_get_params",
             "nbody_mlp_forward", "nbody_mlp_loss_grad", "nbody_mlp_adam_step",
-            "nbody_mlp_destroy", "nbody_mlp_invert", "nbody_set_pair_shape",
+            "nbody_mlp_destroy", "nbody_mlp_invert", "nbody_mlp_get_status", "nbody_set_pair_shape",
             "nbody_set_pair_finish", "nbody_get_pair_shape", "nbody_peaks", "nbody_autotune_pair",
             "nbody_potential_grad", "nbody_mmd_create", "nbody_mmd_eval",
             "nbody_mmd_eval_batch", "nbody_mmd_eval_cross", "nbody_mmd_target_stats",
@@ -185,6 +185,7 @@ def lib():
         L.nbody_mlp_adam_step.argtypes = [vp, C.c_float, C.c_float, C.c_float, C.c_float]
         L.nbody_mlp_invert.argtypes = [vp, vp, C.c_int, vp, C.c_int, C.c_float,
                                         C.c_float, C.c_float, vp]
+        L.nbody_mlp_get_status.argtypes = [vp]
         L.nbody_mlp_destroy.argtypes = [vp]
         L.nbody_mlp_destroy.restype = None
         L.nbody_set_pair_shape.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]
@@ -588,6 +589,11 @@ def nbody_mlp_invert(h, target, u, iters, lr, lo=-1.5, hi=1.5, loss=None):
     """Adam on the inputs u (starts, n_in) toward target (n_out,); in place."""
     _check(lib().nbody_mlp_invert(h, _fptr(target), u.shape[0], _fptr(u), iters, lr, lo,
                                   hi, _fptr(loss)), "nbody_mlp_invert")
+
+
+def nbody_mlp_get_status(h):
+    """NBODY_OK, or NBODY_ETIMEOUT after an expired tensor-core wait."""
+    return lib().nbody_mlp_get_status(h)
 
 
 def nbody_mlp_destroy(h):

@@ -138,7 +138,14 @@ class Surrogate:
                 if U_val is not None:
                     row["val_mse"] = self.mse(U_val, Y_val)
                 hist.append(row)
+        self.check()
         return hist
+
+    def check(self):
+        """Raise if a tensor-core GEMM of the network gave up waiting."""
+        rc = nb.nbody_mlp_get_status(self.h)
+        if rc != nb.NBODY_OK:
+            raise nb.NBodyError(rc, "surrogate network")
 
     def predict(self, U):
         U = torch.tensor(np.asarray(U, np.float32), device=self.dev)
@@ -161,6 +168,7 @@ class Surrogate:
         t = torch.tensor(np.asarray(y_obs, np.float32), device=self.dev)
         loss = torch.empty(starts, dtype=torch.float32, device=self.dev)
         nb.nbody_mlp_invert(self.h, t, u, iters, lr, lo, hi, loss)
+        self.check()
         k = int(torch.argmin(loss).item())
         return u[k].cpu().numpy().astype(float), float(loss[k].item())
 
