@@ -294,7 +294,8 @@ def measure_ensemble(dev, gpu_name, plain_subset=8, plain_steps=200):
     nb.nbody_destroy(h)
     inter = float(np.sum(np.asarray(sizes, float) ** 2)) * steps
 
-    # the same members, a subset, one simulation per launch sequence vs batched
+    # the same members, a subset, one simulation per launch sequence (each
+    # with the launch shapes tuned for its size, untimed) vs batched
     idx = np.argsort(sizes)[:: max(1, len(sizes) // plain_subset)][:plain_subset]
     sub = [mem[k] for k in idx]
     t_plain = 0.0
@@ -302,6 +303,7 @@ def measure_ensemble(dev, gpu_name, plain_subset=8, plain_steps=200):
         sim = nb.Simulation(x.shape[0], prm(th), stream)
         sim.set_state(torch.tensor(x.T.copy(), device=dev), torch.tensor(v.T.copy(), device=dev),
                       torch.tensor(m, device=dev))
+        nb.nbody_autotune_pair(sim.h)
         sim.step(5)
         torch.cuda.synchronize(dev)
         e0.record(stream)

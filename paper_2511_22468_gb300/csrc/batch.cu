@@ -508,6 +508,7 @@ __global__ void __launch_bounds__(kVNT, 4)
     // the scale this point's cotangents were staged with, and the one for
     // the staging of the previous point (from this point's largest |lambda|)
     const double s_here = lsc_here[w.x];
+    const double inv_here = 1.0 / s_here;  // a power of two: exact
     const double s_next = drift ? lam_scale(lmax_here[w.x]) : 1.0;
     if (drift && w.y == 0 && t == 0) lsc_next[w.x] = s_next;
     double vmax = 0.0;
@@ -524,7 +525,7 @@ __global__ void __launch_bounds__(kVNT, 4)
         lam[d] = vbar[d * ptot + g];
         x[d] = xk[d * ptot + g];
         ap[d] = ak[d * ptot + g];
-        gv[d] = -Q.G * M.mscale * (qs[d] / s_here);
+        gv[d] = -Q.G * M.mscale * (qs[d] * inv_here);
       }
       ExtAdj ea;
       ext_adjoint<SHAPE>(Q, x[0], x[1], x[2], lam, ea);

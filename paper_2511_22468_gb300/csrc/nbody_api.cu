@@ -413,7 +413,7 @@ int ensure_tape(nbody_ctx* c, int64_t nseg, int64_t K) {
       return NBODY_ECUDA;
     }
   }
-  if (c->npad < 65536) {  // the overlapped reverse sweep's second buffer and scratch
+  if (c->npad < 65536 && nseg >= 2) {  // the overlapped sweep's second buffer and scratch
     if (c->seg2_cap < K || !c->seg2) {
       drop_graphs(c);
       dfree(c->seg2);
@@ -946,13 +946,17 @@ namespace {
 // current v-bar) on the side stream aside, beside the point's pair VJP on
 // stream s; the adjoint kernel then reads them (a.ea).  Without an external
 // potential or side stream, or outside the sizes where this pays, the
-// adjoint kernel computes them itself (the same arithmetic).
-int fork_ext_adjoint(nbody_ctx* c, nb::AdjointArgs& a, cudaStream_t s) {
+// adjoint kernel computes them itself (the same arithmetic).  clear (may be
+// NULL): the cotangent-maximum slot the point's adjoint kernel accumulates
+// into, zeroed by the side kernel (which runs after the previous point's
+// adjoint kernel read it and before this point's writes it); when the side
+// kernel does not run, the caller clears it on stream s.
+int fork_ext_adjoint(nbody_ctx* c, nb::AdjointArgs& a, cudaStream_t s, double* clear) {
   a.ea = nullptr;
   if (!c->p.ext_flags || !c->aside || !c->ea || !ext_adjoint_beside(c)) return NBODY_OK;
   CK(cudaEventRecord(c->ev_afork, s));
   CK(cudaStreamWaitEvent(c->aside, c->ev_afork, 0));
-  CK(nb::launch_ext_adjoint(c->dp, a.xk, c->vbar, c->n, c->npad, c->ea, c->aside));
+  CK(nb::launch_ext_adjoint(c->dp, a.xk, c->vbar, c->n, c->npad, c->ea, clear, c->aside));
   CK(cudaEventRecord(c->ev_ajoin, c->aside));
   a.ea = c->ea;
   return NBODY_OK;
@@ -1038,7 +1042,9 @@ int record_sweep(nbody_ctx* c, cudaStream_t s) {
     for (int64_t j = Ks; j >= 1; --j) {
       const int64_t k = k0 + j;
       a.xk = (j == Ks) ? T.cpx(sg + 1) : T.sx(j);
-      if (int r_ = fork_ext_adjoint(c, a, s)) return r_;
+      a.slot = (int)(k & 1);
+      double* clear = c->lsc + 2 + (1 - a.slot);
+      if (int r_ = fork_ext_adjoint(c, a, s, clear)) return r_;
       CK(timed(c, NBODY_KCLASS_VJP, [&] {
         return nb::launch_pair_vjp_fin(c->vcfg, c->vst, c->npad, c->hp.eps2f, c->part, mp,
                                        vfin_p, c->pctr, s);
@@ -1050,14 +1056,13 @@ int record_sweep(nbody_ctx* c, cudaStream_t s) {
       a.vh_prev = T.svh(j);
       a.x_prev = T.sx(j - 1);
       a.c_prev = center_at(c, k - 1);
-      a.slot = (int)(k & 1);
-      CK(cudaMemsetAsync(c->lsc + 2 + (1 - a.slot), 0, sizeof(double), s));
+      if (!a.ea) CK(cudaMemsetAsync(clear, 0, sizeof(double), s));
       CK(timed(c, NBODY_KCLASS_ADJOINT, [&] { return nb::launch_adjoint(a, s); }));
     }
   }
   // point 0: opening half kick of the first step
   a.xk = T.cpx(0);
-  if (int r_ = fork_ext_adjoint(c, a, s)) return r_;
+  if (int r_ = fork_ext_adjoint(c, a, s, nullptr)) return r_;
   CK(timed(c, NBODY_KCLASS_VJP, [&] {
     return nb::launch_pair_vjp_fin(c->vcfg, c->vst, c->npad, c->hp.eps2f, c->part, mp, vfin_p,
                                    c->pctr, s);

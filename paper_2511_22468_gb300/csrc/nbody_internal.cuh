@@ -212,10 +212,13 @@ cudaError_t launch_adjoint(const AdjointArgs& a, cudaStream_t s);
 // (x, lam [3][npad]) into ea [kExtAdjCols][npad]: H_ext(x) lam (3), the
 // per-unit-mass products lam . a_NFW, lam . a_MN, lam . a_bulge (3) and the
 // shape-parameter terms (3), the same values the adjoint kernel computes
-// when it is given no ea (update.cu).
+// when it is given no ea (update.cu).  clear (may be NULL): one double the
+// kernel sets to zero (a cotangent-maximum slot the next adjoint kernel
+// accumulates into).
 constexpr int kExtAdjCols = 9;
 cudaError_t launch_ext_adjoint(const DevParams* P, const double* x, const double* lam,
-                               int64_t n, int64_t npad, double* ea, cudaStream_t s);
+                               int64_t n, int64_t npad, double* ea, double* clear,
+                               cudaStream_t s);
 int adjoint_blocks(int64_t n);
 
 // out[0..1] = min and max of m[0..n)

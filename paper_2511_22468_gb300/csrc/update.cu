@@ -162,6 +162,9 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
   // scale of the cotangents this point's VJP was computed with, and the one
   // for the cotangents staged now (from the largest |lambda| at this point)
   const double s_here = a.lsc[a.slot];
+  // the scale is a power of two, so multiplying by its reciprocal gives the
+  // quotient's bits without an FP64 division (slow at GB300's FP64 rate)
+  const double inv_here = 1.0 / s_here;
   const unsigned long long* maxbits =
       reinterpret_cast<const unsigned long long*>(a.lsc + 2);
   const double s_next = a.drift ? lam_scale_from(maxbits[a.slot]) : 1.0;
@@ -174,7 +177,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
       lam[d] = a.vbar[d * np + i];
       x[d] = a.xk[d * np + i];
       ap[d] = a.ak[d * np + i];
-      g[d] = -P.G * a.mscale * (gs[d] / s_here);
+      g[d] = -P.G * a.mscale * (gs[d] * inv_here);
     }
     ExtAdj ea;
     if (a.ea) {  // computed beside this point's pair VJP (k_ext_adjoint)
@@ -202,7 +205,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
     if (a.mpart) {  // per-particle mass gradient of this kick
       double sm[1];
       slice_sums<1>(a.mpart + i, a.S, np, 0, sm);
-      a.mbar[i] += ck * P.G * (sm[0] / s_here);
+      a.mbar[i] += ck * P.G * (sm[0] * inv_here);
     }
     contrib[0] = a.ck * la;          // dL/d dt from the kick(s)
     contrib[1] = ck * lp;            // sum_j m_j dL/dm_j
@@ -254,8 +257,9 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
 __global__ void __launch_bounds__(256)
     k_ext_adjoint(const DevParams* __restrict__ Pp, const double* __restrict__ x,
                   const double* __restrict__ lam, int64_t n, int64_t npad,
-                  double* __restrict__ ea) {
+                  double* __restrict__ ea, double* __restrict__ clear) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (clear && i == 0) *clear = 0.0;
   if (i >= n) return;
   const double l[3] = {lam[i], lam[npad + i], lam[2 * npad + i]};
   ExtAdj e;
@@ -453,8 +457,9 @@ cudaError_t launch_stage_vjp(const double* x, const double* m,
 int adjoint_blocks(int64_t n) { return (int)blocks_for(n, particle_threads(n)); }
 
 cudaError_t launch_ext_adjoint(const DevParams* P, const double* x, const double* lam,
-                               int64_t n, int64_t npad, double* ea, cudaStream_t s) {
-  k_ext_adjoint<<<blocks_for(n, 64), 64, 0, s>>>(P, x, lam, n, npad, ea);
+                               int64_t n, int64_t npad, double* ea, double* clear,
+                               cudaStream_t s) {
+  k_ext_adjoint<<<blocks_for(n, 64), 64, 0, s>>>(P, x, lam, n, npad, ea, clear);
   count_launch();
   return cudaGetLastError();
 }

@@ -17,12 +17,29 @@ import torch
 from . import nbody as nb
 
 
+# device memory the adjoint tape of one stream run may take before the run
+# is split into recomputed segments (bytes)
+TAPE_BUDGET = 16e9
+
+
+def tape_interval(n, n_steps, budget=TAPE_BUDGET):
+    """Checkpoint interval K for the stream run: the whole run as one kept
+    segment (K = n_steps: the reverse sweep recomputes nothing) when its
+    tape -- positions, accelerations and half-step velocities of every
+    step, 72 bytes per (padded) particle and step -- fits the budget, else
+    about sqrt(n_steps) steps per recomputed segment."""
+    npad = -(-int(n) // 1024) * 1024
+    if 72.0 * npad * n_steps <= budget:
+        return int(n_steps)
+    return max(1, int(round(math.sqrt(n_steps))))
+
+
 def stream_cfg(cfg, n=None, n_steps=None, checkpoint_every=None) -> nb.nbody_stream_cfg:
     """C config from a StreamC1-like dataclass (configs.py)."""
     c = nb.nbody_stream_cfg()
     c.n = int(cfg.n if n is None else n)
     c.n_steps = int(cfg.n_steps if n_steps is None else n_steps)
-    K = checkpoint_every or max(1, int(round(math.sqrt(c.n_steps))))
+    K = checkpoint_every or tape_interval(c.n, c.n_steps)
     c.checkpoint_every = int(K)
     c.G, c.eps, c.a_prog = cfg.G, cfg.eps, cfg.a_prog
     c.nfw_rs, c.mn_a, c.mn_b = cfg.pot.nfw_rs, cfg.pot.mn_a, cfg.pot.mn_b
