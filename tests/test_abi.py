@@ -88,3 +88,29 @@ def test_missing_library_raises(monkeypatch, tmp_path):
     monkeypatch.setattr(nbody, "LIB_PATH", str(tmp_path / "nope.so"))
     with pytest.raises(RuntimeError, match="not built"):
         nbody.lib()
+
+
+def test_empty_and_invalid_inputs_are_refused_before_any_device_work(libpath):
+    """Empty systems (n = 0), an empty batch member, a zero softening and
+    NULL outputs return NBODY_EINVAL from the argument checks, which come
+    before any device query or allocation (so this runs without a GPU)."""
+    from paper_2511_22468_gb300 import nbody
+    lib = nbody.lib()
+    p = nbody.make_params(1.0, 0.01, 1e-3)
+    h = ctypes.c_void_p()
+    assert lib.nbody_create(ctypes.byref(h), 0, ctypes.byref(p), None) == nbody.NBODY_EINVAL
+    assert lib.nbody_create(ctypes.byref(h), -5, ctypes.byref(p), None) == nbody.NBODY_EINVAL
+    assert not h.value
+    p0 = nbody.make_params(1.0, 0.0, 1e-3)           # eps = 0: the GPU path needs eps > 0
+    assert lib.nbody_create(ctypes.byref(h), 10, ctypes.byref(p0), None) == nbody.NBODY_EINVAL
+    offs = (ctypes.c_int64 * 3)(0, 5, 5)            # second member empty
+    ps = (nbody.nbody_params * 2)(p, p)
+    assert lib.nbody_create_batch(ctypes.byref(h), 2, offs, ps, None) == nbody.NBODY_EINVAL
+    offs = (ctypes.c_int64 * 2)(1, 5)                # offsets must start at 0
+    assert lib.nbody_create_batch(ctypes.byref(h), 1, offs, ps, None) == nbody.NBODY_EINVAL
+    cen = (ctypes.c_double * 3)(0.0, 0.0, 0.0)
+    buf = (ctypes.c_double * 3)()
+    assert lib.nbody_pair_accel(0, buf, buf, ctypes.c_double(1.0), ctypes.c_double(0.01), cen,
+                                buf, None) == nbody.NBODY_EINVAL
+    assert lib.nbody_pair_accel(1, buf, buf, ctypes.c_double(1.0), ctypes.c_double(0.01), cen,
+                                None, None) == nbody.NBODY_EINVAL
