@@ -277,6 +277,18 @@ NBODY_API int nbody_set_pair_shape(nbody_ctx *c, int vjp, int variant,
 /* Current shape {variant, threads, per_thread, chunks} (host, 4 ints). */
 NBODY_API int nbody_get_pair_shape(nbody_ctx *c, int vjp, int out[4]);
 
+/* j-pairs per shared-memory tile of the tile variant (variant 0) of the
+ * pair-force (vjp = 0) or pair-VJP (vjp = 1) kernel: the default (512
+ * forward, 256 VJP) or 128, whose finer j-chunks suit small systems
+ * (128-pair instances: forward 128 x {4, 2, 1} and 64 x {2, 4} threads x
+ * per_thread, VJP 128 x {2, 1} and 64 x 2).  Call after nbody_set_pair_shape,
+ * which restores the default; the chunk count is kept.  Results change only
+ * by the summation order.  Invalidates the tape and the cached
+ * acceleration.  nbody_get_pair_tile returns the current tile size.
+ * Errors: EINVAL. */
+NBODY_API int nbody_set_pair_tile(nbody_ctx *c, int vjp, int tile_pairs);
+NBODY_API int nbody_get_pair_tile(nbody_ctx *c, int vjp);
+
 /* Where the chunk sums of a tile-variant pair kernel split into chunks >= 2
  * are added up: mode 1 = by the block of each row tile that finishes last,
  * inside the pair kernel (the consumer then reads one slice); 0 = by the

@@ -946,17 +946,13 @@ namespace {
 // current v-bar) on the side stream aside, beside the point's pair VJP on
 // stream s; the adjoint kernel then reads them (a.ea).  Without an external
 // potential or side stream, or outside the sizes where this pays, the
-// adjoint kernel computes them itself (the same arithmetic).  clear (may be
-// NULL): the cotangent-maximum slot the point's adjoint kernel accumulates
-// into, zeroed by the side kernel (which runs after the previous point's
-// adjoint kernel read it and before this point's writes it); when the side
-// kernel does not run, the caller clears it on stream s.
-int fork_ext_adjoint(nbody_ctx* c, nb::AdjointArgs& a, cudaStream_t s, double* clear) {
+// adjoint kernel computes them itself (the same arithmetic).
+int fork_ext_adjoint(nbody_ctx* c, nb::AdjointArgs& a, cudaStream_t s) {
   a.ea = nullptr;
   if (!c->p.ext_flags || !c->aside || !c->ea || !ext_adjoint_beside(c)) return NBODY_OK;
   CK(cudaEventRecord(c->ev_afork, s));
   CK(cudaStreamWaitEvent(c->aside, c->ev_afork, 0));
-  CK(nb::launch_ext_adjoint(c->dp, a.xk, c->vbar, c->n, c->npad, c->ea, clear, c->aside));
+  CK(nb::launch_ext_adjoint(c->dp, a.xk, c->vbar, c->n, c->npad, c->ea, c->aside));
   CK(cudaEventRecord(c->ev_ajoin, c->aside));
   a.ea = c->ea;
   return NBODY_OK;
@@ -1042,9 +1038,7 @@ int record_sweep(nbody_ctx* c, cudaStream_t s) {
     for (int64_t j = Ks; j >= 1; --j) {
       const int64_t k = k0 + j;
       a.xk = (j == Ks) ? T.cpx(sg + 1) : T.sx(j);
-      a.slot = (int)(k & 1);
-      double* clear = c->lsc + 2 + (1 - a.slot);
-      if (int r_ = fork_ext_adjoint(c, a, s, clear)) return r_;
+      if (int r_ = fork_ext_adjoint(c, a, s)) return r_;
       CK(timed(c, NBODY_KCLASS_VJP, [&] {
         return nb::launch_pair_vjp_fin(c->vcfg, c->vst, c->npad, c->hp.eps2f, c->part, mp,
                                        vfin_p, c->pctr, s);
@@ -1056,13 +1050,14 @@ int record_sweep(nbody_ctx* c, cudaStream_t s) {
       a.vh_prev = T.svh(j);
       a.x_prev = T.sx(j - 1);
       a.c_prev = center_at(c, k - 1);
-      if (!a.ea) CK(cudaMemsetAsync(clear, 0, sizeof(double), s));
+      a.slot = (int)(k & 1);
+      CK(cudaMemsetAsync(c->lsc + 2 + (1 - a.slot), 0, sizeof(double), s));
       CK(timed(c, NBODY_KCLASS_ADJOINT, [&] { return nb::launch_adjoint(a, s); }));
     }
   }
   // point 0: opening half kick of the first step
   a.xk = T.cpx(0);
-  if (int r_ = fork_ext_adjoint(c, a, s, nullptr)) return r_;
+  if (int r_ = fork_ext_adjoint(c, a, s)) return r_;
   CK(timed(c, NBODY_KCLASS_VJP, [&] {
     return nb::launch_pair_vjp_fin(c->vcfg, c->vst, c->npad, c->hp.eps2f, c->part, mp, vfin_p,
                                    c->pctr, s);
@@ -1278,6 +1273,28 @@ int nbody_set_pair_shape(nbody_ctx* c, int vjp, int variant, int threads,
   return NBODY_OK;
 }
 
+int nbody_set_pair_tile(nbody_ctx* c, int vjp, int tile_pairs) {
+  if (!c || c->batch) return NBODY_EINVAL;
+  nb::PairCfg& cfg = vjp ? c->vcfg : c->fcfg;
+  if (cfg.variant != nb::kTile) return NBODY_EINVAL;
+  const int dflt = nb::choose_pair_cfg(c->npad, c->sm_count, vjp != 0, cfg.eqm).vjp_tile_pairs;
+  if (tile_pairs != dflt && tile_pairs != 128) return NBODY_EINVAL;
+  if (!nb::pair_tile_supported(cfg.nt, cfg.r, tile_pairs, vjp != 0)) return NBODY_EINVAL;
+  if (c->npad % (2 * tile_pairs) != 0) return NBODY_EINVAL;
+  cfg.vjp_tile_pairs = tile_pairs;
+  drop_graphs(c);
+  c->shape_fixed[vjp ? 1 : 0] = true;
+  c->acc_valid = false;
+  c->tape_steps = 0;
+  c->last_seg_valid = false;
+  return NBODY_OK;
+}
+
+int nbody_get_pair_tile(nbody_ctx* c, int vjp) {
+  if (!c || c->batch) return NBODY_EINVAL;
+  return (vjp ? c->vcfg : c->fcfg).vjp_tile_pairs;
+}
+
 int nbody_set_pair_finish(nbody_ctx* c, int vjp, int mode) {
   if (!c || c->batch || mode < -1 || mode > 1) return NBODY_EINVAL;
   (vjp ? c->vfin_mode : c->fin_mode) = mode;
@@ -1316,7 +1333,8 @@ int nbody_autotune_pair(nbody_ctx* c, int probe_launches, int fwd_best[4],
                        {0, 128, 4, 128}, {0, 128, 2, 128}, {0, 128, 1, 128},
                        {0, 64, 2, 128},  {0, 64, 4, 128},  {0, 64, 2, 0}};
   const Shape vjp[] = {{0, 256, 2, 0}, {0, 128, 4, 0}, {0, 128, 2, 0}, {0, 128, 1, 0},
-                       {1, 256, 4, 0}, {1, 256, 2, 0}, {0, 64, 2, 0}};
+                       {1, 256, 4, 0}, {1, 256, 2, 0}, {0, 64, 2, 0},
+                       {0, 128, 2, 128}, {0, 128, 1, 128}, {0, 64, 2, 128}};
   int rc = NBODY_OK;
   int best_fin[2] = {0, 0};
   for (int which = 0; which < 2 && rc == NBODY_OK; ++which) {

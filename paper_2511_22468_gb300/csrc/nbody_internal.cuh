@@ -94,6 +94,8 @@ int pair_blocks_per_sm(const PairCfg& c);
 int vjp_blocks_per_sm(const PairCfg& c);
 int vjp_tile_pairs();
 bool pair_shape_supported(int variant, int nt, int r, bool vjp);
+// the tile variant has an instance for this block shape and j-tile size
+bool pair_tile_supported(int nt, int r, int tile_pairs, bool vjp);
 int choose_chunks(const PairCfg& c, int64_t npad, int sm_count, int blocks_per_sm);
 
 // Raw sums R_i = sum_j m_j (x_j - x_i) s_ij^-3 (no G; with cfg.eqm the
@@ -212,13 +214,10 @@ cudaError_t launch_adjoint(const AdjointArgs& a, cudaStream_t s);
 // (x, lam [3][npad]) into ea [kExtAdjCols][npad]: H_ext(x) lam (3), the
 // per-unit-mass products lam . a_NFW, lam . a_MN, lam . a_bulge (3) and the
 // shape-parameter terms (3), the same values the adjoint kernel computes
-// when it is given no ea (update.cu).  clear (may be NULL): one double the
-// kernel sets to zero (a cotangent-maximum slot the next adjoint kernel
-// accumulates into).
+// when it is given no ea (update.cu).
 constexpr int kExtAdjCols = 9;
 cudaError_t launch_ext_adjoint(const DevParams* P, const double* x, const double* lam,
-                               int64_t n, int64_t npad, double* ea, double* clear,
-                               cudaStream_t s);
+                               int64_t n, int64_t npad, double* ea, cudaStream_t s);
 int adjoint_blocks(int64_t n);
 
 // out[0..1] = min and max of m[0..n)

@@ -311,6 +311,14 @@ int pair_blocks_per_sm(const PairCfg& c) {
   return occ > 0 ? occ : 1;
 }
 
+bool pair_tile_supported(int nt, int r, int tile_pairs, bool vjp) {
+  if (tile_pairs == 128) {  // the small-tile instances
+    if (vjp) return (nt == 128 && (r == 2 || r == 1)) || (nt == 64 && r == 2);
+    return (nt == 128 && (r == 4 || r == 2 || r == 1)) || (nt == 64 && (r == 2 || r == 4));
+  }
+  return pair_shape_supported(kTile, nt, r, vjp);
+}
+
 bool pair_shape_supported(int variant, int nt, int r, bool vjp) {
   if (variant == kWarp) return vjp ? (nt == 256 && (r == 4 || r == 2)) : (nt == 256 && (r == 4 || r == 8));
   if (vjp) return (nt == 256 && r == 2) || (nt == 128 && (r == 4 || r == 2 || r == 1)) ||

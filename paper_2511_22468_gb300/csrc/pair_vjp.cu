@@ -42,13 +42,15 @@ namespace {
 constexpr int kTJ = NB_VJP_TJ;  // j-pairs per shared-memory tile (4 float4 each)
 constexpr int kUnrollJ = NB_VJP_UNROLL;
 
-template <int NT, int R, bool EQM, bool MB>
+constexpr int kTJSmall = 128;   // small tiles: finer j-chunks for small systems
+
+template <int NT, int R, bool EQM, bool MB, int TJ = kTJ>
 __global__ void __launch_bounds__(NT, NB_VJP_MINB)
     k_vjp_tile(const float4* __restrict__ vst, int ntiles, float eps2,
                int64_t npad, double* __restrict__ part, double* __restrict__ mpart,
                double* __restrict__ fin, unsigned* __restrict__ ctr) {
   constexpr bool kAsync = NB_TILE_ASYNC != 0;
-  __shared__ __align__(16) float4 sbuf[kAsync ? 2 : 1][4 * kTJ];
+  __shared__ __align__(16) float4 sbuf[kAsync ? 2 : 1][4 * TJ];
   const int t = threadIdx.x;
   const int64_t k0 = (int64_t)blockIdx.x * (NT * R) + t;
   const int S = gridDim.y;
@@ -64,8 +66,8 @@ __global__ void __launch_bounds__(NT, NB_VJP_MINB)
   }
   const float2 e2 = make_float2(eps2, eps2);
   if (kAsync && tile_b < tile_e) {
-    const float4* src = vst + (int64_t)tile_b * (4 * kTJ);
-    for (int q = t; q < 4 * kTJ; q += NT) cp_async16(&sbuf[0][q], src + q);
+    const float4* src = vst + (int64_t)tile_b * (4 * TJ);
+    for (int q = t; q < 4 * TJ; q += NT) cp_async16(&sbuf[0][q], src + q);
     cp_async_commit();
   }
   for (int tile = tile_b; tile < tile_e; ++tile) {
@@ -74,17 +76,17 @@ __global__ void __launch_bounds__(NT, NB_VJP_MINB)
       cp_async_wait_all();
       __syncthreads();  // this tile visible; the previous one no longer read
       if (tile + 1 < tile_e) {
-        const float4* src = vst + (int64_t)(tile + 1) * (4 * kTJ);
+        const float4* src = vst + (int64_t)(tile + 1) * (4 * TJ);
         float4* dst = sbuf[(tile + 1 - tile_b) & 1];
-        for (int q = t; q < 4 * kTJ; q += NT) cp_async16(dst + q, src + q);
+        for (int q = t; q < 4 * TJ; q += NT) cp_async16(dst + q, src + q);
         cp_async_commit();
       }
       sj = sbuf[(tile - tile_b) & 1];
     } else {
       __syncthreads();
-      const float4* src = vst + (int64_t)tile * (4 * kTJ);
+      const float4* src = vst + (int64_t)tile * (4 * TJ);
 #pragma unroll
-      for (int q = t; q < 4 * kTJ; q += NT) sbuf[0][q] = src[q];
+      for (int q = t; q < 4 * TJ; q += NT) sbuf[0][q] = src[q];
       __syncthreads();
       sj = sbuf[0];
     }
@@ -96,7 +98,7 @@ __global__ void __launch_bounds__(NT, NB_VJP_MINB)
       for (int d = 0; d < 3; ++d) qa[r][d] = qb[r][d] = make_float2(0.f, 0.f);
     }
 #pragma unroll (kUnrollJ)
-    for (int jj = 0; jj < kTJ; ++jj) {
+    for (int jj = 0; jj < TJ; ++jj) {
       const float4 A = sj[4 * jj], B = sj[4 * jj + 1];
       const float4 L1 = sj[4 * jj + 2], L2 = sj[4 * jj + 3];
 #pragma unroll
@@ -197,7 +199,19 @@ template <bool EQM, bool MB>
 cudaError_t launch_vjp_impl(const PairCfg& c, const float4* vst, int64_t npad,
                             float eps2, double* part, double* mpart, double* fin,
                             unsigned* ctr, cudaStream_t s) {
-  if (c.variant == kTile) {
+  if (c.variant == kTile && c.vjp_tile_pairs == kTJSmall) {
+    const int ntiles = (int)(npad / (2 * kTJSmall));
+    dim3 grid((unsigned)(npad / (c.nt * c.r)), (unsigned)c.S);
+    if (c.nt == 128 && c.r == 2)
+      k_vjp_tile<128, 2, EQM, MB, kTJSmall><<<grid, 128, 0, s>>>(vst, ntiles, eps2, npad, part, mpart, fin, ctr);
+    else if (c.nt == 128 && c.r == 1)
+      k_vjp_tile<128, 1, EQM, MB, kTJSmall><<<grid, 128, 0, s>>>(vst, ntiles, eps2, npad, part, mpart, fin, ctr);
+    else if (c.nt == 64 && c.r == 2)
+      k_vjp_tile<64, 2, EQM, MB, kTJSmall><<<grid, 64, 0, s>>>(vst, ntiles, eps2, npad, part, mpart, fin, ctr);
+    else
+      return cudaErrorInvalidValue;
+  } else if (c.variant == kTile) {
+    if (c.vjp_tile_pairs != kTJ) return cudaErrorInvalidValue;
     const int ntiles = (int)(npad / (2 * kTJ));
     dim3 grid((unsigned)(npad / (c.nt * c.r)), (unsigned)c.S);
     if (c.nt == 256 && c.r == 2)
@@ -238,13 +252,22 @@ int vjp_blocks_per_sm(const PairCfg& c) {
                     &occ, k_vjp_tile<NT, R, true, false>, NT, 0)                  \
               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(                    \
                     &occ, k_vjp_tile<NT, R, false, false>, NT, 0);
-  if (c.variant == kTile) {
+#define NB_OCC_S(NT, R)                                                           \
+  if (c.nt == NT && c.r == R)                                                     \
+    e = c.eqm ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(                    \
+                    &occ, k_vjp_tile<NT, R, true, false, kTJSmall>, NT, 0)        \
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(                    \
+                    &occ, k_vjp_tile<NT, R, false, false, kTJSmall>, NT, 0);
+  if (c.variant == kTile && c.vjp_tile_pairs == kTJSmall) {
+    NB_OCC_S(128, 2) NB_OCC_S(128, 1) NB_OCC_S(64, 2)
+  } else if (c.variant == kTile) {
     NB_OCC(256, 2) NB_OCC(128, 4) NB_OCC(128, 2) NB_OCC(128, 1) NB_OCC(64, 2)
   } else {
     e = c.eqm ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_vjp_warp<4, true, false>, 256, 0)
               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_vjp_warp<4, false, false>, 256, 0);
   }
 #undef NB_OCC
+#undef NB_OCC_S
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 1;

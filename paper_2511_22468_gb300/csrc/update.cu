@@ -257,9 +257,8 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
 __global__ void __launch_bounds__(256)
     k_ext_adjoint(const DevParams* __restrict__ Pp, const double* __restrict__ x,
                   const double* __restrict__ lam, int64_t n, int64_t npad,
-                  double* __restrict__ ea, double* __restrict__ clear) {
+                  double* __restrict__ ea) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (clear && i == 0) *clear = 0.0;
   if (i >= n) return;
   const double l[3] = {lam[i], lam[npad + i], lam[2 * npad + i]};
   ExtAdj e;
@@ -457,9 +456,8 @@ cudaError_t launch_stage_vjp(const double* x, const double* m,
 int adjoint_blocks(int64_t n) { return (int)blocks_for(n, particle_threads(n)); }
 
 cudaError_t launch_ext_adjoint(const DevParams* P, const double* x, const double* lam,
-                               int64_t n, int64_t npad, double* ea, double* clear,
-                               cudaStream_t s) {
-  k_ext_adjoint<<<blocks_for(n, 64), 64, 0, s>>>(P, x, lam, n, npad, ea, clear);
+                               int64_t n, int64_t npad, double* ea, cudaStream_t s) {
+  k_ext_adjoint<<<blocks_for(n, 64), 64, 0, s>>>(P, x, lam, n, npad, ea);
   count_launch();
   return cudaGetLastError();
 }

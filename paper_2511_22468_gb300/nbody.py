@@ -49,7 +49,8 @@ EXPORTED = ("nbody_create", "nbody_destroy", "nbody_set_params",
             "nbody_mlp_num_params", "nbody_mlp_set_params", "nbody_mlp_get_params",
             "nbody_mlp_forward", "nbody_mlp_loss_grad", "nbody_mlp_adam_step",
             "nbody_mlp_destroy", "nbody_mlp_invert", "nbody_mlp_get_status", "nbody_set_pair_shape",
-            "nbody_set_pair_finish", "nbody_get_pair_shape", "nbody_peaks", "nbody_autotune_pair",
+            "nbody_set_pair_finish", "nbody_get_pair_shape", "nbody_set_pair_tile",
+            "nbody_get_pair_tile", "nbody_peaks", "nbody_autotune_pair",
             "nbody_potential_grad", "nbody_mmd_create", "nbody_mmd_eval",
             "nbody_mmd_eval_batch", "nbody_mmd_eval_cross", "nbody_mmd_target_stats",
             "nbody_mmd_destroy",
@@ -191,6 +192,8 @@ def lib():
         L.nbody_set_pair_shape.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]
         L.nbody_get_pair_shape.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
         L.nbody_set_pair_finish.argtypes = [vp, C.c_int, C.c_int]
+        L.nbody_set_pair_tile.argtypes = [vp, C.c_int, C.c_int]
+        L.nbody_get_pair_tile.argtypes = [vp, C.c_int]
         L.nbody_peaks.argtypes = [dp, vp]
         L.nbody_autotune_pair.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.nbody_set_timing.argtypes = [vp, C.c_int]
@@ -426,6 +429,17 @@ def nbody_set_pair_finish(h, vjp, mode):
     """Chunk sums added in the pair kernel (1), by the consumer (0) or by
     chunk count (-1); results are bitwise the same."""
     _check(lib().nbody_set_pair_finish(h, int(vjp), int(mode)), "nbody_set_pair_finish")
+
+
+def nbody_set_pair_tile(h, vjp, tile_pairs):
+    """j-pairs per shared-memory tile of the tile variant (default or 128)."""
+    _check(lib().nbody_set_pair_tile(h, int(vjp), int(tile_pairs)), "nbody_set_pair_tile")
+
+
+def nbody_get_pair_tile(h, vjp):
+    rc = lib().nbody_get_pair_tile(h, int(vjp))
+    _check(rc if rc < 0 else 0, "nbody_get_pair_tile")
+    return rc
 
 
 def nbody_get_pair_shape(h, vjp):

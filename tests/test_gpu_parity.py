@@ -120,9 +120,11 @@ def test_full_size_step_and_adjoint_sampled():
 
 
 # (variant, threads, per thread, chunks (0: automatic), where the chunk sums
-# are added (-1: automatic))
-VJP_SHAPES = [(0, 256, 2, 0, -1), (0, 128, 4, 0, -1), (0, 128, 2, 0, -1), (0, 128, 1, 0, -1),
-              (0, 128, 2, 9, 1), (0, 128, 2, 9, 0), (0, 64, 2, 0, -1), (0, 64, 2, 17, 1)]
+# are added (-1: automatic), j-pairs per tile (0: the default))
+VJP_SHAPES = [(0, 256, 2, 0, -1, 0), (0, 128, 4, 0, -1, 0), (0, 128, 2, 0, -1, 0),
+              (0, 128, 1, 0, -1, 0), (0, 128, 2, 9, 1, 0), (0, 128, 2, 9, 0, 0),
+              (0, 64, 2, 0, -1, 0), (0, 64, 2, 17, 1, 0), (0, 128, 2, 19, 1, 128),
+              (0, 128, 1, 20, 0, 128), (0, 64, 2, 13, 1, 128)]
 
 
 @pytest.mark.parametrize("eqm", [False, True])
@@ -130,7 +132,8 @@ def test_tile_vjp_and_mass_gradient_sampled(eqm):
     """The tile pair-VJP kernels, general masses (spread over
     [0.5, 1.5] of the mean) and equal masses, with and without the
     per-particle mass gradient, in every supported tile shape (and with the
-    chunk sums added by the pair kernel and by the consumer), at N = 70001
+    chunk sums added by the pair kernel and by the consumer, and with 128-pair
+    j-tiles), at N = 70001
     (npad = 70656, a ragged last tile): one kick-drift-kick step and its
     reverse sweep with
     xbar = W, vbar = 0, whose closed forms for sampled rows k are
@@ -150,10 +153,13 @@ def test_tile_vjp_and_mass_gradient_sampled(eqm):
     Jt += np.array([orc.ext_jac(ph, x[k]).T @ W[k] for k in rows])
     mref = orc.pair_mass_vjp(x, C1.G, C1.eps, W, rows=rows)
     X, V, M, WG = to_gpu(x), to_gpu(v), to_gpu(m), to_gpu(W)
-    for variant, nt, r, chunks, finish in VJP_SHAPES:
+    for variant, nt, r, chunks, finish, tile in VJP_SHAPES:
         sim = _sim(n, C1.G, C1.eps, dt, K=1, ext=3, pot=pot, center=C1.X0,
                    center_vel=C1.V0, guide=True)
         nb.nbody_set_pair_shape(sim.h, 1, variant, nt, r, chunks)
+        if tile:
+            nb.nbody_set_pair_tile(sim.h, 1, tile)
+            assert nb.nbody_get_pair_tile(sim.h, 1) == tile
         if finish >= 0:
             nb.nbody_set_pair_finish(sim.h, 1, finish)
         sim.set_state(X, V, M)
@@ -176,7 +182,8 @@ def test_tile_vjp_and_mass_gradient_sampled(eqm):
 @pytest.mark.parametrize("n", [10000, 70001])
 def test_tile_force_shapes_one_step(n):
     """Every tile shape of the pair-force kernel (including the 64-thread
-    blocks for small systems), general masses: one kick-drift-kick step,
+    blocks and the 128-pair j-tiles for small systems), general masses: one
+    kick-drift-kick step,
     whose closed form x1 - x0 - dt v0 = (dt^2 / 2) a(x0) gives the
     acceleration, against the oracle (1e-5 per particle; sampled rows for
     the larger n), the chunk sums added by the pair kernel and by the
@@ -190,12 +197,16 @@ def test_tile_force_shapes_one_step(n):
     sel = np.arange(n) if rows is None else rows
     a_ref = orc.pair_accel(x, m, C1.G, C1.eps, rows=rows)
     a_ref += np.array([orc.ext_accel(ph, x[k]) for k in sel])
-    for nt, r in ((128, 4), (128, 8), (256, 4), (256, 2), (128, 2), (128, 1), (64, 2), (64, 4)):
+    for nt, r, tile in ((128, 4, 0), (128, 8, 0), (256, 4, 0), (256, 2, 0), (128, 2, 0),
+                        (128, 1, 0), (64, 2, 0), (64, 4, 0), (128, 4, 128), (128, 2, 128),
+                        (128, 1, 128), (64, 2, 128), (64, 4, 128)):
         outs = []
         for fin in (0, 1):
             sim = _sim(n, C1.G, C1.eps, dt, ext=3, pot=pot, center=C1.X0, center_vel=C1.V0,
                        guide=True)
-            nb.nbody_set_pair_shape(sim.h, 0, 0, nt, r, 9)
+            nb.nbody_set_pair_shape(sim.h, 0, 0, nt, r, 9 if not tile else 19)
+            if tile:
+                nb.nbody_set_pair_tile(sim.h, 0, tile)
             nb.nbody_set_pair_finish(sim.h, 0, fin)
             sim.set_state(to_gpu(x), to_gpu(v), to_gpu(m))
             xo = torch.empty((3, n), dtype=torch.float64, device=DEV)
@@ -203,9 +214,9 @@ def test_tile_force_shapes_one_step(n):
             assert sim.status() == 0
             sim.close()
             outs.append(xo)
-        assert torch.equal(outs[0], outs[1]), (nt, r)
+        assert torch.equal(outs[0], outs[1]), (nt, r, tile)
         got = (to_np(outs[0])[sel] - x[sel] - dt * v[sel]) / (0.5 * dt * dt)
-        assert acc_err(got, a_ref) <= 1e-5, (nt, r)
+        assert acc_err(got, a_ref) <= 1e-5, (nt, r, tile)
 
 
 # warp-variant shapes (threads, per thread): pair force, pair VJP
