@@ -154,6 +154,11 @@ __global__ void __launch_bounds__(256) k_update(UpdateArgs a) {
 }
 
 // ------------------------------------------------------------------ adjoint
+// EA: the external field's adjoint terms come from a.ea (computed beside the
+// pair VJP); otherwise the kernel computes them.  Two instances, so that the
+// one reading a.ea carries none of the field's code (a smaller kernel:
+// instruction fetch, not arithmetic, was what stalled it).
+template <bool EA>
 __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const DevParams& P = *a.P;
@@ -180,7 +185,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
       g[d] = -P.G * a.mscale * (gs[d] * inv_here);
     }
     ExtAdj ea;
-    if (a.ea) {  // computed beside this point's pair VJP (k_ext_adjoint)
+    if (EA) {  // computed beside this point's pair VJP (k_ext_adjoint)
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         ea.jl[d] = a.ea[d * np + i];
@@ -493,7 +498,10 @@ cudaError_t launch_minmax(const double* m, int64_t n, double* out, cudaStream_t 
 }
 
 cudaError_t launch_adjoint(const AdjointArgs& a, cudaStream_t s) {
-  k_adjoint<<<adjoint_blocks(a.n), particle_threads(a.n), 0, s>>>(a);
+  if (a.ea)
+    k_adjoint<true><<<adjoint_blocks(a.n), particle_threads(a.n), 0, s>>>(a);
+  else
+    k_adjoint<false><<<adjoint_blocks(a.n), particle_threads(a.n), 0, s>>>(a);
   count_launch();
   return cudaGetLastError();
 }
