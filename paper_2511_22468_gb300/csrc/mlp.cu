@@ -43,8 +43,9 @@ constexpr uint32_t kStageBytes = 2 * kATile + 2 * kBTile;
 constexpr size_t kGemmSmem = (size_t)kStages * kStageBytes + 1024;  // + alignment slack
 // per-thread share of one slice: A values, B values
 constexpr int kAPer = TM * TK / 128, kBPer = TN * TK / 128;
-// mbarrier polls before a wait is given up (each poll may suspend briefly)
-constexpr uint32_t kWaitPolls = 1u << 22;
+// nanoseconds (of the GPU's global timer) before an mbarrier wait is given
+// up; the MMAs it waits for take microseconds
+constexpr uint64_t kWaitNs = 1000000000ull;
 
 __device__ __forceinline__ float gelu(float z) {
   return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
@@ -93,9 +94,18 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b
       : "memory");
 }
 
-// bounded wait for phase `parity` of the mbarrier; false when it expired
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// wait for phase `parity` of the mbarrier, at most kWaitNs of wall-clock
+// time (each poll returns within the hardware's own short suspend limit);
+// false when it expired
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kWaitPolls; ++i) {
+  const uint64_t t0 = global_ns();
+  for (;;) {
     uint32_t ok;
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -104,8 +114,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (ok) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
   }
-  return false;
 }
 
 // C[m][n] = sum_k A(m,k) B(k,n), A(m,k) = TA ? A[k lda + m] : A[m lda + k],

@@ -40,7 +40,11 @@ def from_u(u, centre, width):
 class EnsembleDensities:
     """Densities of one stream workload for many parameter vectors."""
 
-    def __init__(self, cfg, xhat, vhat, batch=64, device="cuda:0", tuning=None):
+    def __init__(self, cfg, xhat, vhat, batch=128, device="cuda:0", tuning=None):
+        """batch simulations per persistent launch; tuning: a batch launch
+        candidate, or None to time the candidates on the first batch's state
+        (128 members with the tuned candidate: 4.3 s per 512 simulations of
+        N = 1e4 over 200 steps on GB300, against 4.8 s for 64 untuned)."""
         self.dev = torch.device(device)
         self.cfg = cfg
         self.model = StreamModel(cfg, xhat, vhat, device=device)
@@ -52,6 +56,7 @@ class EnsembleDensities:
         self.h = nb.nbody_create_batch(offs, [self._params(cfg.theta_true, (0,) * 6)] * B)
         if tuning is not None:
             nb.nbody_set_tuning(self.h, tuning)
+        self.tune_pending = tuning is None
         self.X = torch.empty((3, B * n), dtype=torch.float64, device=self.dev)
         self.V = torch.empty_like(self.X)
         self.M = torch.empty(B * n, dtype=torch.float64, device=self.dev)
@@ -85,6 +90,9 @@ class EnsembleDensities:
                 prm.append(self._params(th, com))
             nb.nbody_set_params_batch(self.h, prm)
             nb.nbody_set_state(self.h, self.X, self.V, self.M)
+            if self.tune_pending:  # times the candidates; the state is not advanced
+                nb.nbody_autotune(self.h, 2)
+                self.tune_pending = False
             nb.nbody_integrate(self.h, self.steps)
             nb.nbody_get_state(self.h, self.XO, None)
             for j in range(len(chunk)):

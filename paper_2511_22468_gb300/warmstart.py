@@ -133,7 +133,7 @@ def run(n=10_000, t_end=100.0, err_target=0.05, n_train=3584, n_val=512, epochs=
 
     # the surrogate, once: training densities from the batched kernel, training
     f = uniform_factors(n_train + n_val, width, 4, C4.seed_params)
-    gen = EnsembleDensities(cfg, xh, vh, batch=64, device=device)
+    gen = EnsembleDensities(cfg, xh, vh, device=device)
     sync()
     t0 = time.perf_counter()
     Y = gen.densities(centre * f) * DENSITY_SCALE
