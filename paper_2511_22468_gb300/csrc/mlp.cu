@@ -22,6 +22,7 @@
 #include <stdint.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <new>
 
 #include "nbody_internal.cuh"
@@ -44,8 +45,10 @@ constexpr size_t kGemmSmem = (size_t)kStages * kStageBytes + 1024;  // + alignme
 // per-thread share of one slice: A values, B values
 constexpr int kAPer = TM * TK / 128, kBPer = TN * TK / 128;
 // nanoseconds (of the GPU's global timer) before an mbarrier wait is given
-// up; the MMAs it waits for take microseconds
+// up, and a cap on the polls as well (whichever comes first); the MMAs it
+// waits for take microseconds
 constexpr uint64_t kWaitNs = 1000000000ull;
+constexpr uint32_t kWaitPolls = 1u << 26;
 
 __device__ __forceinline__ float gelu(float z) {
   return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
@@ -105,7 +108,7 @@ __device__ __forceinline__ uint64_t global_ns() {
 // false when it expired
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   const uint64_t t0 = global_ns();
-  for (;;) {
+  for (uint32_t poll = 0; poll < kWaitPolls; ++poll) {
     uint32_t ok;
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -116,6 +119,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     if (ok) return true;
     if (global_ns() - t0 > kWaitNs) return false;
   }
+  return false;
 }
 
 // C[m][n] = sum_k A(m,k) B(k,n), A(m,k) = TA ? A[k lda + m] : A[m lda + k],
@@ -128,12 +132,14 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 // a stage is rewritten only after the MMAs that read it have completed.
 // Warp w reads accumulator rows 32 w .. 32 w + 31 (its tensor-memory lanes).
 // A wait that expires sets bit 1 of *status and skips the epilogue.
+// no_mma != 0 (the failure-detection test only) issues no MMA and no commit,
+// so that the waits expire.
 template <bool TA, bool TB, int EPI>
 __global__ void __launch_bounds__(128)
     k_gemm(int M, int N, int K, const float* __restrict__ A, int lda,
            const float* __restrict__ B, int ldb, const float* __restrict__ bias,
            float* __restrict__ C, int ldc, float* __restrict__ Zout,
-           const float* __restrict__ Zin, int* __restrict__ status) {
+           const float* __restrict__ Zin, int* __restrict__ status, int no_mma) {
   extern __shared__ unsigned char dsm[];
   __shared__ __align__(8) uint64_t bars[kStages];
   __shared__ uint32_t tmem_slot;
@@ -218,7 +224,7 @@ __global__ void __launch_bounds__(128)
     // the staged tiles become visible to the tensor cores' (async) proxy
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
-    if (t == 0) {
+    if (t == 0 && !no_mma) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t ah = smem_addr(sa_hi), al = smem_addr(sa_lo);
       const uint32_t bh = smem_addr(sb_hi), bl = smem_addr(sb_lo);
@@ -381,7 +387,7 @@ __global__ void k_row_mse(const float* __restrict__ y, const float* __restrict__
 template <bool TA, bool TB, int EPI>
 cudaError_t gemm(int M, int N, int K, const float* A, int lda, const float* B,
                  int ldb, const float* bias, float* C, int ldc, float* Zout,
-                 const float* Zin, int* status, cudaStream_t s) {
+                 const float* Zin, int* status, int no_mma, cudaStream_t s) {
   // the two stages take more than the default 48 KB of dynamic shared
   // memory: raise the kernel's limit once per device
   static unsigned long long attr_set = 0;
@@ -396,7 +402,7 @@ cudaError_t gemm(int M, int N, int K, const float* A, int lda, const float* B,
   }
   dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
   k_gemm<TA, TB, EPI><<<grid, 128, kGemmSmem, s>>>(M, N, K, A, lda, B, ldb, bias, C, ldc, Zout,
-                                                   Zin, status);
+                                                   Zin, status, no_mma);
   count_launch();
   return cudaGetLastError();
 }
@@ -417,6 +423,9 @@ struct nbody_mlp {
   double* blk = nullptr;
   float* loss = nullptr;
   int* status = nullptr;  // bit 1: a tensor-core GEMM's bounded wait expired
+  // failure-detection test only (environment NBODY_MLP_TEST_NO_MMA=1 at
+  // creation): the GEMMs issue no MMA, so their bounded waits expire
+  int no_mma = 0;
   int64_t step = 0;
   bool have_grad = false;
   // parameter views
@@ -463,11 +472,11 @@ int mlp_forward(nbody_mlp* m, const float* u, int B, float* y) {
   using namespace nb;
   cudaStream_t s = m->s;
   MCK((gemm<false, true, kEpiBiasGelu>(B, m->nh, m->nin, u, m->nin, m->W1(), m->nin,
-                                       m->b1(), m->h1, m->nh, m->z1, nullptr, m->status, s)));
+                                       m->b1(), m->h1, m->nh, m->z1, nullptr, m->status, m->no_mma, s)));
   MCK((gemm<false, true, kEpiBiasGelu>(B, m->nh, m->nh, m->h1, m->nh, m->W2(), m->nh,
-                                       m->b2(), m->h2, m->nh, m->z2, nullptr, m->status, s)));
+                                       m->b2(), m->h2, m->nh, m->z2, nullptr, m->status, m->no_mma, s)));
   MCK((gemm<false, true, kEpiBias>(B, m->nout, m->nh, m->h2, m->nh, m->W3(), m->nh,
-                                   m->b3(), y, m->nout, nullptr, nullptr, m->status, s)));
+                                   m->b3(), y, m->nout, nullptr, nullptr, m->status, m->no_mma, s)));
   return NBODY_OK;
 }
 
@@ -491,6 +500,10 @@ int nbody_mlp_create(nbody_mlp** out, int n_in, int n_hidden, int n_out,
   m->nout = n_out;
   m->maxb = max_batch;
   m->s = (cudaStream_t)cuda_stream;
+  {
+    const char* e = std::getenv("NBODY_MLP_TEST_NO_MMA");
+    m->no_mma = (e && e[0] == '1' && e[1] == '\0') ? 1 : 0;
+  }
   m->np = (int64_t)n_hidden * n_in + n_hidden + (int64_t)n_hidden * n_hidden + n_hidden +
           (int64_t)n_out * n_hidden + n_out;
   const size_t bh = (size_t)max_batch * n_hidden, bo = (size_t)max_batch * n_out;
@@ -569,29 +582,29 @@ int nbody_mlp_loss_grad(nbody_mlp* m, const float* u, const float* t, int batch,
   float* gb3 = gW3 + (int64_t)no * nh;
   // layer 3: dW3 = dY^T H2, db3 = colsum dY, dZ2 = (dY W3) * GELU'(Z2)
   MCK((gemm<true, false, kEpiNone>(no, nh, B, m->dy, no, m->h2, nh, nullptr, gW3, nh,
-                                   nullptr, nullptr, m->status, s)));
+                                   nullptr, nullptr, m->status, m->no_mma, s)));
   k_colsum<<<(no + 127) / 128, 128, 0, s>>>(m->dy, B, no, gb3);
   count_launch();
   MCK(cudaGetLastError());
   MCK((gemm<false, false, kEpiGeluBwd>(B, nh, no, m->dy, no, m->W3(), nh, nullptr, m->dz2,
-                                       nh, nullptr, m->z2, m->status, s)));
+                                       nh, nullptr, m->z2, m->status, m->no_mma, s)));
   // layer 2
   MCK((gemm<true, false, kEpiNone>(nh, nh, B, m->dz2, nh, m->h1, nh, nullptr, gW2, nh,
-                                   nullptr, nullptr, m->status, s)));
+                                   nullptr, nullptr, m->status, m->no_mma, s)));
   k_colsum<<<(nh + 127) / 128, 128, 0, s>>>(m->dz2, B, nh, gb2);
   count_launch();
   MCK(cudaGetLastError());
   MCK((gemm<false, false, kEpiGeluBwd>(B, nh, nh, m->dz2, nh, m->W2(), nh, nullptr, m->dz1,
-                                       nh, nullptr, m->z1, m->status, s)));
+                                       nh, nullptr, m->z1, m->status, m->no_mma, s)));
   // layer 1
   MCK((gemm<true, false, kEpiNone>(nh, nin, B, m->dz1, nh, u, nin, nullptr, gW1, nin,
-                                   nullptr, nullptr, m->status, s)));
+                                   nullptr, nullptr, m->status, m->no_mma, s)));
   k_colsum<<<(nh + 127) / 128, 128, 0, s>>>(m->dz1, B, nh, gb1);
   count_launch();
   MCK(cudaGetLastError());
   if (du)
     MCK((gemm<false, false, kEpiNone>(B, nin, nh, m->dz1, nh, m->W1(), nin, nullptr, du, nin,
-                                      nullptr, nullptr, m->status, s)));
+                                      nullptr, nullptr, m->status, m->no_mma, s)));
   if (grads)
     MCK(cudaMemcpyAsync(grads, m->g, m->np * sizeof(float), cudaMemcpyDeviceToDevice, s));
   m->have_grad = true;
