@@ -726,8 +726,11 @@ NBODY_API int nbody_mlp_invert(nbody_mlp *m, const float *target, int starts,
 
 /* Sticky device status of the network's tensor-core GEMMs: NBODY_OK, or
  * NBODY_ETIMEOUT when a bounded wait for the tensor cores' completion
- * expired (that GEMM's output was not written).  Synchronises the network's
- * stream.  Errors: EINVAL, ECUDA. */
+ * expired (that GEMM's output was not written; each wait gives up after 1 s).
+ * For failure-detection tests only, the environment variable
+ * NBODY_MLP_TEST_NO_MMA=1 at nbody_mlp_create makes that network's GEMMs
+ * issue no tensor-core work, so that every wait expires.  Synchronises the
+ * network's stream.  Errors: EINVAL, ECUDA. */
 NBODY_API int nbody_mlp_get_status(nbody_mlp *m);
 
 /* Release the network; NULL is a no-op. */
