@@ -531,8 +531,11 @@ def run_ours(args):
     s_v = nb.nbody_get_pair_shape(sim.h, 1)[3]
     bpp = {"update": 48 + 24 * s_f + 48 + 12,
            "adjoint": 48 + 72 + 24 * s_v + 56 + 48 + 32 + 72}
+    # field: the FP64 external field of a forward point (x read, field
+    # written), on the side stream beside the pair kernel
+    bpp["field"] = 48
     hbm = hbm_peak()
-    for name in ("update", "adjoint"):
+    for name in ("update", "adjoint", "field"):
         ms, cnt = kt[name]
         k = {"launches": cnt, "total_ms": ms, "avg_ms": ms / cnt if cnt else None,
              "algorithmic_bytes_per_particle": bpp[name], "bound": "fp64 alu / hbm"}

@@ -318,11 +318,15 @@ NBODY_API int nbody_autotune_pair(nbody_ctx *c, int probe_launches,
 #define NBODY_KCLASS_VJP 1     /* pair VJP kernel                             */
 #define NBODY_KCLASS_UPDATE 2  /* kick-drift-kick update kernel               */
 #define NBODY_KCLASS_ADJOINT 3 /* adjoint update kernel                       */
-#define NBODY_NKCLASS 4
+#define NBODY_KCLASS_FIELD 4   /* FP64 external field of a forward point (on a
+                                  side stream beside the pair kernel)       */
+#define NBODY_NKCLASS 5
 
 /* Enable (1) or disable (0) event timing of the context's kernels: when
- * enabled, every launch of the four classes above is bracketed by two CUDA
- * events recorded on the context stream.  Errors: EINVAL. */
+ * enabled, every launch of the classes above is bracketed by two CUDA
+ * events recorded on the context stream, and the external field of a
+ * forward point then runs on the context stream as well (not beside the
+ * pair kernel), so that its events time the kernel alone.  Errors: EINVAL. */
 NBODY_API int nbody_set_timing(nbody_ctx *c, int enable);
 
 /* Sum of the event-timed durations (ms) and launch counts per class since

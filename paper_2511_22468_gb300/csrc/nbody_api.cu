@@ -28,7 +28,6 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
-#include <utility>
 #include <vector>
 
 #include "nbody_internal.cuh"
@@ -500,8 +499,15 @@ nb::UpdateArgs base_update(nbody_ctx* c, double* x, double* v) {
 
 // The external field of the point x is computed on the side stream while
 // stream s runs that point's pair kernel; the update waits for both.
+// Under per-kernel timing the field runs on stream s itself, so that its
+// events time the kernel rather than its wait for SMs beside the pair kernel.
 int fork_field(nbody_ctx* c, const double* x, cudaStream_t s) {
   if (!c->p.ext_flags || !c->side) return NBODY_OK;
+  if (c->timing) {
+    CK(timed(c, NBODY_KCLASS_FIELD,
+             [&] { return nb::launch_field(c->dp, x, c->n, c->npad, c->aext, s); }));
+    return NBODY_OK;
+  }
   CK(cudaEventRecord(c->ev_fork, s));
   CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
   CK(nb::launch_field(c->dp, x, c->n, c->npad, c->aext, c->side));
@@ -511,7 +517,7 @@ int fork_field(nbody_ctx* c, const double* x, cudaStream_t s) {
 
 int join_field(nbody_ctx* c, cudaStream_t s, nb::UpdateArgs& a) {
   if (!c->p.ext_flags || !c->side) return NBODY_OK;
-  CK(cudaStreamWaitEvent(s, c->ev_join, 0));
+  if (!c->timing) CK(cudaStreamWaitEvent(s, c->ev_join, 0));
   a.aext = c->aext;
   return NBODY_OK;
 }

@@ -63,7 +63,7 @@ EXPORTED = ("nbody_create", "nbody_destroy", "nbody_set_params",
 
 NBODY_NTUNE = 8
 
-NBODY_KCLASS = ("pair", "vjp", "update", "adjoint")
+NBODY_KCLASS = ("pair", "vjp", "update", "adjoint", "field")
 
 
 class nbody_params(C.Structure):
@@ -472,8 +472,8 @@ def nbody_set_timing(h, enable: bool):
 
 def nbody_kernel_times(h):
     """{class: (ms, launches)} summed since the previous call."""
-    ms = (C.c_double * 4)()
-    cnt = (C.c_int64 * 4)()
+    ms = (C.c_double * len(NBODY_KCLASS))()
+    cnt = (C.c_int64 * len(NBODY_KCLASS))()
     _check(lib().nbody_kernel_times(h, ms, cnt), "nbody_kernel_times")
     return {k: (ms[i], cnt[i]) for i, k in enumerate(NBODY_KCLASS)}
 
