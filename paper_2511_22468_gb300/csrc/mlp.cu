@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <new>
@@ -390,15 +391,16 @@ cudaError_t gemm(int M, int N, int K, const float* A, int lda, const float* B,
                  const float* Zin, int* status, int no_mma, cudaStream_t s) {
   // the two stages take more than the default 48 KB of dynamic shared
   // memory: raise the kernel's limit once per device
-  static unsigned long long attr_set = 0;
+  static std::atomic<unsigned long long> attr_set{0};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev < 64 && !(attr_set & (1ull << dev))) {
+  const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+  if (!bit || !(attr_set.load(std::memory_order_acquire) & bit)) {
     e = cudaFuncSetAttribute(k_gemm<TA, TB, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kGemmSmem);
     if (e != cudaSuccess) return e;
-    attr_set |= 1ull << dev;
+    attr_set.fetch_or(bit, std::memory_order_release);
   }
   dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
   k_gemm<TA, TB, EPI><<<grid, 128, kGemmSmem, s>>>(M, N, K, A, lda, B, ldb, bias, C, ldc, Zout,
