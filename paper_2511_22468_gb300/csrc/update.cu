@@ -421,9 +421,10 @@ inline unsigned blocks_for(int64_t n, int t) {
 }
 
 // threads per block of the per-particle FP64 kernels: 256 when that still
-// gives several blocks per SM, 64 for small systems so that the (slow) FP64
-// work spreads over every SM
-inline int particle_threads(int64_t n) { return n >= 262144 ? 256 : 64; }
+// gives several blocks per SM, fewer for small systems so that the (slow)
+// FP64 work spreads over every SM -- one warp below 65 536 particles, where
+// the block reductions then need no barrier
+inline int particle_threads(int64_t n) { return n >= 262144 ? 256 : n >= 65536 ? 64 : 32; }
 
 }  // namespace
 
