@@ -168,7 +168,8 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
   // for the cotangents staged now (from the largest |lambda| at this point)
   const double s_here = a.lsc[a.slot];
   // the scale is a power of two, so multiplying by its reciprocal gives the
-  // quotient's bits without an FP64 division (slow at GB300's FP64 rate)
+  // quotient's bits: one FP64 division per thread instead of one per
+  // component (divisions are slow at GB300's FP64 rate)
   const double inv_here = 1.0 / s_here;
   const unsigned long long* maxbits =
       reinterpret_cast<const unsigned long long*>(a.lsc + 2);
